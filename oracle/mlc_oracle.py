@@ -1,0 +1,699 @@
+"""FP64 CPU oracle for the two-level Method of Local Corrections.
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+module.  It shares no code with the CUDA library; the only common module is
+the seeded input generator ``paper_1702_08111_gb300.inputs``.
+
+The oracle follows the fully discrete two-level algorithm of Sec. 4 step by
+step, in the paper's notation, with the plainest computation for each step:
+
+* the discrete Green's function (DGF) is built as in App. A.1 (Dirichlet
+  problem on [-zeta nD, zeta nD]^3 with the exact kernel as boundary values,
+  residual-correction form, DST-I), using scipy's DST-I;
+* every convolution is a direct sum (a dense matrix product with the
+  Green's-function lag matrix, or the plain loops of ``direct_sum.c``);
+* Legendre moments use composite Boole's rule (Sec. 4, Step 1);
+* the Dirichlet solves use dense DST-I matrices;
+* the boundary values are formed literally as in eqs. (philocmlcII) and
+  (mlcfulldiscr): phi^{loc,g} is accumulated at g and at every point of its
+  interpolation stencil, then phi^B = phi^loc + I^H(phi^H - phi^loc).
+
+Readings of points where the paper is silent or garbled (each is also listed
+in the design notes of the repository):
+
+R1  Grid: unit cube, h = 1/N, nodes [0, N]^3; patches are the closed cubes
+    n i + [0, n]^3, i in [0, N/n)^3 (Sec. 4).  The charge is given on
+    [0, N]^3 internally; the library's arrays hold [0, N)^3 and treat node N
+    as zero charge.
+R2  Support s: the local field box G(Omega_alpha, C b) is the patch grown by s,
+    so the alpha growth is g_alpha = s - C b; g_beta = ceil((beta-1) n / 2)
+    with beta = 3 for Q = 4 and 3.25 for Q = 6 (Sec. 7 settings).  MLC-0 is
+    g_beta = g_alpha.
+R3  Legendre basis: orthonormal Q^p(x) = R^{-3/2} prod_d sqrt((2p_d+1)/2)
+    P_{p_d}((x_d - c_d)/R), index set |p|_1 <= P-1 in lexicographic order
+    with p_2 fastest (eq. led3d, normalisation made orthonormal).  The
+    coefficients are the Boole-rule inner products of the unweighted f with
+    Q^p over the closed patch; the discrete Legendre charge is
+    P^h(f^{i,h}) = chi * sum_p c_p Q^p(gh).
+R4  Interpolant I^H (Sec. 4, Step 3): tensor-product Lagrange interpolation
+    in the face plane.  Along an axis where g is a coarse node the stencil is
+    that node alone; otherwise it is the 2b+2 coarse nodes k0-b .. k0+b+1,
+    k0 = floor(g/4).  Order q_I = 2b+2.
+R5  Region membership is by closed boxes; the ring is
+    Omega_beta \\ Omega_alpha at the fine level and C(Omega_beta) \\
+    C(Omega_alpha) at the coarse level.  Sums over patches run in ascending
+    patch linear index.
+R6  phi^H is evaluated on the coarse nodes [-b, N/4 + b]^3, the nodes the
+    interpolation reads.
+R7  Delta^H is the same Mehrstellen operator at spacing H = C h applied to the
+    fine field sampled at coarse nodes; G^H = H^{-1} G^{h=1}.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from dataclasses import dataclass
+from fractions import Fraction
+from functools import lru_cache
+
+import numpy as np
+import scipy.fft
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_CACHE = os.path.join(_HERE, "_cache")
+_BUILD = os.path.join(_HERE, "_build")
+
+# App. A.1: a_j = b_{|j|} / h^2, |j| = number of nonzero components of j.
+STENCIL_B = {
+    4: (-4.0, 1.0 / 3.0, 1.0 / 6.0, 0.0),  # L19, q = 4
+    6: (-64.0 / 15.0, 7.0 / 15.0, 1.0 / 10.0, 1.0 / 30.0),  # L27, q = 6
+}
+C2 = 1.0 / 12.0  # Sec. 2, eq. (msCorr4)
+
+
+# ---------------------------------------------------------------------------
+# Parameters (R2)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Params:
+    N: int
+    n: int
+    s: int
+    P: int = 4
+    Q: int = 4
+    C: int = 4
+    beta: float | None = None
+    b: int | None = None
+    mode: str = "mlc"  # "mlc" (alpha < beta) or "mlc0" (alpha = beta)
+    nD: int = 128
+    zeta: int = 2
+
+    def __post_init__(self):
+        if self.Q not in STENCIL_B:
+            raise ValueError("Q must be 4 or 6")
+        if self.C != 4:
+            raise ValueError("coarsening ratio is 4 (Sec. 2)")
+        if self.N % self.n or self.n % 4 or self.s % 4:
+            raise ValueError("need n | N, 4 | n, 4 | s")
+        if self.b is None:
+            self.b = 2 if self.Q == 4 else 3
+        if self.beta is None:
+            self.beta = 3.0 if self.Q == 4 else 3.25
+        self.h = 1.0 / self.N
+        self.H = self.C * self.h
+        self.R = self.n * self.h / 2.0
+        self.np_ = self.N // self.n
+        self.g_alpha = self.s - self.C * self.b
+        if self.g_alpha < 0:
+            raise ValueError("support smaller than C*b")
+        if self.mode == "mlc0":
+            self.g_beta = self.g_alpha
+        else:
+            self.g_beta = math.ceil((Fraction(self.beta) - 1) * self.n / 2)
+        if self.g_beta < self.g_alpha:
+            raise ValueError("g_beta < g_alpha")
+
+    # relative boxes (per axis, inclusive), relative to the patch origin n*i
+    @property
+    def alpha_box(self):
+        return (-self.g_alpha, self.n + self.g_alpha)
+
+    @property
+    def beta_box(self):
+        return (-self.g_beta, self.n + self.g_beta)
+
+    @property
+    def field_box(self):
+        return (-self.s, self.n + self.s)
+
+    # coarse boxes relative to the patch's coarse origin n*i/4 (Sec. 2, C(D))
+    @property
+    def c_alpha(self):
+        return (math.floor(-self.g_alpha / 4), math.ceil((self.n + self.g_alpha) / 4))
+
+    @property
+    def c_beta(self):
+        return (math.floor(-self.g_beta / 4), math.ceil((self.n + self.g_beta) / 4))
+
+    @property
+    def fh_extent(self):
+        lo, hi = self.c_beta
+        return (lo, (self.np_ - 1) * self.n // 4 + hi)
+
+    @property
+    def phih_extent(self):
+        return (-self.b, self.N // 4 + self.b)
+
+    @property
+    def npatch(self):
+        return self.np_ ** 3
+
+
+def patch_origin(prm: Params, i: int) -> np.ndarray:
+    i0, rem = divmod(i, prm.np_ * prm.np_)
+    i1, i2 = divmod(rem, prm.np_)
+    return np.array([i0, i1, i2], dtype=np.int64) * prm.n
+
+
+# ---------------------------------------------------------------------------
+# Mehrstellen operators (Sec. 2, App. A.1)
+# ---------------------------------------------------------------------------
+
+def stencil(Q: int):
+    """List of (offset, b_{|offset|}) over [-1,1]^3 with nonzero coefficient."""
+    b = STENCIL_B[Q]
+    out = []
+    for s0 in (-1, 0, 1):
+        for s1 in (-1, 0, 1):
+            for s2 in (-1, 0, 1):
+                nz = (s0 != 0) + (s1 != 0) + (s2 != 0)
+                if b[nz] != 0.0:
+                    out.append(((s0, s1, s2), b[nz]))
+    return out
+
+
+def apply_laplacian(phi: np.ndarray, Q: int, h: float) -> np.ndarray:
+    """Eq. (discreteLaplacian) on the interior G(D,-1) of the array's box."""
+    n0, n1, n2 = phi.shape
+    out = np.zeros((n0 - 2, n1 - 2, n2 - 2))
+    for (s0, s1, s2), c in stencil(Q):
+        out += c * phi[1 + s0:n0 - 1 + s0, 1 + s1:n1 - 1 + s1, 1 + s2:n2 - 1 + s2]
+    return out / (h * h)
+
+
+def symbol(Q: int, c0, c1, c2):
+    """Eigenvalue (h = 1) of the stencil on the product of 1D modes whose
+    shift-pair eigenvalues are 2 c_d."""
+    b0, b1, b2, b3 = STENCIL_B[Q]
+    return (b0 + 2 * b1 * (c0 + c1 + c2) + 4 * b2 * (c0 * c1 + c0 * c2 + c1 * c2)
+            + 8 * b3 * c0 * c1 * c2)
+
+
+# ---------------------------------------------------------------------------
+# Discrete Green's function (Sec. 2 eq. dgf; App. A.1)
+# ---------------------------------------------------------------------------
+
+def dgf_full(Q: int, nD: int, zeta: int) -> np.ndarray:
+    """Solve L G = delta_0 on G(D_zeta,-1), G = -1/(4 pi |g|) on the boundary of
+    D_zeta = [-zeta nD, zeta nD]^3; returns G on all of D_zeta."""
+    M = zeta * nD
+    x = np.arange(-M, M + 1, dtype=np.float64)
+    G = np.zeros((2 * M + 1,) * 3)
+    # boundary values: exact free-space Green's function
+    for axis in range(3):
+        for end in (0, 2 * M):
+            sl = [slice(None)] * 3
+            sl[axis] = end
+            grids = np.meshgrid(*[x if d != axis else x[end:end + 1] for d in range(3)], indexing="ij")
+            r = np.sqrt(grids[0] ** 2 + grids[1] ** 2 + grids[2] ** 2)
+            G[tuple(sl)] = (-1.0 / (4.0 * math.pi * r)).reshape(G[tuple(sl)].shape)
+    # residual-correction form: L u = delta - L(G_boundary), u = 0 on the boundary
+    rhs = -apply_laplacian(G, Q, 1.0)
+    rhs[M - 1, M - 1, M - 1] += 1.0
+    K = 2 * M - 1
+    c = np.cos(np.pi * np.arange(1, K + 1) / (2 * M))
+    lam = symbol(Q, c[:, None, None], c[None, :, None], c[None, None, :])
+    uh = scipy.fft.dstn(rhs, type=1, workers=os.cpu_count())
+    del rhs
+    uh /= lam
+    u = scipy.fft.idstn(uh, type=1, workers=os.cpu_count())
+    G[1:-1, 1:-1, 1:-1] += u
+    return G
+
+
+def dgf_octant(Q: int, nD: int = 128, zeta: int = 2) -> np.ndarray:
+    """G^{h=1} on the octant [0, nD]^3 (cached on disk)."""
+    return _dgf_octant_cached(Q, nD, zeta).copy()
+
+
+@lru_cache(maxsize=8)
+def _dgf_octant_cached(Q: int, nD: int, zeta: int) -> np.ndarray:
+    path = os.path.join(_CACHE, f"dgf_Q{Q}_nD{nD}_z{zeta}.npy")
+    if os.path.exists(path):
+        return np.load(path)
+    M = zeta * nD
+    G = dgf_full(Q, nD, zeta)
+    oct_ = np.ascontiguousarray(G[M:M + nD + 1, M:M + nD + 1, M:M + nD + 1])
+    del G
+    os.makedirs(_CACHE, exist_ok=True)
+    tmp = path + f".{os.getpid()}.tmp.npy"
+    np.save(tmp, oct_)
+    os.replace(tmp, path)
+    return oct_
+
+
+# ---------------------------------------------------------------------------
+# Direct sums
+# ---------------------------------------------------------------------------
+
+def _direct_lib():
+    so = os.path.join(_BUILD, "liboracle_direct.so")
+    src = os.path.join(_HERE, "direct_sum.c")
+    if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+        build_c()
+    lib = ctypes.CDLL(so)
+    lib.oracle_direct_sum.restype = ctypes.c_int
+    return lib
+
+
+def build_c():
+    """Compile the oracle's C helper (plain loops + OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    so = os.path.join(_BUILD, "liboracle_direct.so")
+    tmp = so + f".{os.getpid()}.tmp"
+    subprocess.check_call(["gcc", "-O3", "-fopenmp", "-shared", "-fPIC", "-o", tmp,
+                           os.path.join(_HERE, "direct_sum.c")])
+    os.replace(tmp, so)
+    return so
+
+
+def direct_sum(T: np.ndarray, src: np.ndarray, src_lo, out_lo, out_shape, scale: float) -> np.ndarray:
+    """out[o] = scale * sum_k T[|o-k|] src[k] by plain loops (direct_sum.c)."""
+    lib = _direct_lib()
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    src = np.ascontiguousarray(src, dtype=np.float64)
+    out = np.zeros(tuple(out_shape), dtype=np.float64)
+    L = T.shape[0] - 1
+    ia = ctypes.c_int * 3
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = lib.oracle_direct_sum(T.ctypes.data_as(dp), ctypes.c_int(L), src.ctypes.data_as(dp),
+                               ia(*src_lo), ia(*src.shape), out.ctypes.data_as(dp),
+                               ia(*out_lo), ia(*out_shape), ctypes.c_double(scale))
+    if rc != 0:
+        raise ValueError("lag beyond the DGF table")
+    return out
+
+
+def green_matrix(G1: np.ndarray, pts: np.ndarray, src: np.ndarray, chunk: int = 512) -> np.ndarray:
+    """Lag matrix M[a, j] = G1[|pts[a] - src[j]|] (per-axis absolute lags)."""
+    out = np.empty((pts.shape[0], src.shape[0]))
+    for a0 in range(0, pts.shape[0], chunk):
+        p = pts[a0:a0 + chunk]
+        d = np.abs(p[:, None, :] - src[None, :, :])
+        out[a0:a0 + chunk] = G1[d[..., 0], d[..., 1], d[..., 2]]
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Patch quantities: chi, Boole weights, Legendre basis (Sec. 3 eq. led3d, Sec. 4)
+# ---------------------------------------------------------------------------
+
+def box_points(lo, hi, step: int = 1) -> np.ndarray:
+    r = np.arange(lo, hi + 1, step, dtype=np.int64)
+    g = np.stack(np.meshgrid(r, r, r, indexing="ij"), axis=-1)
+    return g.reshape(-1, 3)
+
+
+def chi_1d(n: int) -> np.ndarray:
+    w = np.ones(n + 1)
+    w[0] = w[-1] = 0.5
+    return w
+
+
+def chi_patch(n: int) -> np.ndarray:
+    """Discrete characteristic function of the closed patch (Sec. 4): 1/8 at
+    corners, 1/4 on edges, 1/2 on faces, 1 inside -- flattened over [0,n]^3."""
+    w = chi_1d(n)
+    return (w[:, None, None] * w[None, :, None] * w[None, None, :]).reshape(-1)
+
+
+def boole_weights_1d(n: int, h: float) -> np.ndarray:
+    """Composite Boole's rule on [0, n h] with n/4 panels."""
+    if n % 4:
+        raise ValueError("Boole's rule needs 4 | n")
+    w = np.zeros(n + 1)
+    panel = (2.0 * h / 45.0) * np.array([7.0, 32.0, 12.0, 32.0, 7.0])
+    for p in range(n // 4):
+        w[4 * p:4 * p + 5] += panel
+    return w
+
+
+def legendre_index(P: int):
+    return [(p0, p1, p2) for p0 in range(P) for p1 in range(P) for p2 in range(P) if p0 + p1 + p2 < P]
+
+
+def legendre_1d(k: int, t: np.ndarray) -> np.ndarray:
+    """Orthonormal Legendre polynomial sqrt((2k+1)/2) P_k(t) on [-1, 1]."""
+    coef = np.zeros(k + 1)
+    coef[k] = 1.0
+    return math.sqrt((2 * k + 1) / 2.0) * np.polynomial.legendre.legval(t, coef)
+
+
+def legendre_patch(prm: Params) -> np.ndarray:
+    """Q^p at the closed-patch nodes m in [0,n]^3: array (npoly, (n+1)^3)."""
+    n = prm.n
+    t = 2.0 * np.arange(n + 1) / n - 1.0  # (x - c)/R at the nodes
+    vals = [legendre_1d(k, t) for k in range(prm.P)]
+    out = []
+    for p0, p1, p2 in legendre_index(prm.P):
+        v = vals[p0][:, None, None] * vals[p1][None, :, None] * vals[p2][None, None, :]
+        out.append(v.reshape(-1) * prm.R ** -1.5)
+    return np.array(out)
+
+
+def moment_matrix(prm: Params) -> np.ndarray:
+    """Row p: Boole weight times Q^p at the patch nodes, so c = M @ f_patch."""
+    w = boole_weights_1d(prm.n, prm.h)
+    W = (w[:, None, None] * w[None, :, None] * w[None, None, :]).reshape(-1)
+    return legendre_patch(prm) * W[None, :]
+
+
+# ---------------------------------------------------------------------------
+# Face lattice and interpolation stencils (R4)
+# ---------------------------------------------------------------------------
+
+def lagrange_weights(t: float, nodes: np.ndarray) -> np.ndarray:
+    w = np.ones(len(nodes))
+    for j in range(len(nodes)):
+        for l in range(len(nodes)):
+            if l != j:
+                w[j] *= (t - nodes[l]) / (nodes[j] - nodes[l])
+    return w
+
+
+def axis_stencil(g: int, b: int):
+    """(coarse nodes, weights) of the 1D factor of I^H at fine coordinate g."""
+    if g % 4 == 0:
+        return np.array([g // 4]), np.array([1.0])
+    k0 = g // 4
+    nodes = np.arange(k0 - b, k0 + b + 2)
+    return nodes, lagrange_weights(g / 4.0, nodes.astype(np.float64))
+
+
+def face_stencil(g, b: int):
+    """Stencil of I^H at a face-lattice node g, padded to (2b+2)^2 entries.
+
+    Returns (coarse points (S,3), weights (S,)).  Padding entries repeat the
+    first point with weight 0."""
+    per_axis = [axis_stencil(int(g[d]), b) for d in range(3)]
+    nontriv = [d for d in range(3) if len(per_axis[d][0]) > 1]
+    if len(nontriv) > 2:
+        raise ValueError("node is not on a face plane")
+    S = (2 * b + 2) ** 2
+    pts = np.zeros((S, 3), dtype=np.int64)
+    wts = np.zeros(S)
+    k = 0
+    for a0, w0 in zip(*per_axis[0]):
+        for a1, w1 in zip(*per_axis[1]):
+            for a2, w2 in zip(*per_axis[2]):
+                pts[k] = (a0, a1, a2)
+                wts[k] = w0 * w1 * w2
+                k += 1
+    pts[k:] = pts[0]
+    return pts, wts
+
+
+def face_nodes_in_box(prm: Params, lo: int, hi: int) -> np.ndarray:
+    """Face-lattice nodes (some coordinate a multiple of n) in the relative box [lo,hi]^3."""
+    pts = box_points(lo, hi)
+    on_face = np.any(pts % prm.n == 0, axis=1)
+    return pts[on_face]
+
+
+def stencils_for(prm: Params, nodes: np.ndarray):
+    """Vectorised I^H stencils (R4) for many face-lattice nodes.
+
+    The first axis on which the node sits on a face plane is taken as the face
+    normal (weight 1 there); the two in-plane axes carry 2b+2 entries each, a
+    trivial in-plane axis (node on a coarse line) having weights (1, 0, ...)
+    at one repeated node.  Returns coarse points (A, S, 3) and weights (A, S),
+    S = (2b+2)^2; the nonzero terms are the same as in face_stencil."""
+    b = prm.b
+    K = 2 * b + 2
+    g = np.asarray(nodes, dtype=np.int64)
+    A = g.shape[0]
+    onface = (g % prm.n) == 0
+    if not np.all(np.any(onface, axis=1)):
+        raise ValueError("node is not on a face plane")
+    dstar = np.argmax(onface, axis=1)
+    kn = np.zeros((A, 3, K), dtype=np.int64)
+    wt = np.zeros((A, 3, K))
+    j = np.arange(K)
+    for d in range(3):
+        gd = g[:, d]
+        triv = (gd % 4) == 0
+        k0 = gd // 4
+        nd = k0[:, None] - b + j[None, :]
+        r = (gd - 4 * k0).astype(np.float64) / 4.0  # t - k0 in [0, 1)
+        w = np.ones((A, K))
+        for jj in range(K):
+            for ll in range(K):
+                if ll != jj:
+                    w[:, jj] *= (r + b - ll) / float(jj - ll)
+        kn[:, d, :] = np.where(triv[:, None], k0[:, None], nd)
+        wt[:, d, :] = np.where(triv[:, None], (j[None, :] == 0).astype(np.float64), w)
+    a1 = np.where(dstar == 0, 1, 0)
+    a2 = np.where(dstar == 2, 1, 2)
+    rows = np.arange(A)
+    P = np.zeros((A, K, K, 3), dtype=np.int64)
+    P[:, :, :, :] = (g // 4)[:, None, None, :]
+    P[rows, :, :, a1] = kn[rows, a1, :][:, :, None]
+    P[rows, :, :, a2] = kn[rows, a2, :][:, None, :]
+    W = wt[rows, a1, :][:, :, None] * wt[rows, a2, :][:, None, :]
+    return P.reshape(A, K * K, 3), W.reshape(A, K * K)
+
+
+class PointSet:
+    """A set of relative integer points with a dense lookup map over a box."""
+
+    def __init__(self, pts: np.ndarray):
+        pts = np.unique(pts, axis=0)
+        self.pts = pts
+        self.lo = pts.min(axis=0)
+        self.hi = pts.max(axis=0)
+        shape = tuple(self.hi - self.lo + 1)
+        self.map = -np.ones(shape, dtype=np.int64)
+        q = pts - self.lo
+        self.map[q[:, 0], q[:, 1], q[:, 2]] = np.arange(len(pts))
+
+    def index(self, q: np.ndarray) -> np.ndarray:
+        r = q - self.lo
+        if np.any(r < 0) or np.any(r >= np.array(self.map.shape)):
+            raise IndexError("point outside the computed set")
+        idx = self.map[r[..., 0], r[..., 1], r[..., 2]]
+        if np.any(idx < 0):
+            raise IndexError("point not in the computed set")
+        return idx
+
+
+# ---------------------------------------------------------------------------
+# The two-level solve (Sec. 4)
+# ---------------------------------------------------------------------------
+
+def pad_charge(f: np.ndarray) -> np.ndarray:
+    """[0,N)^3 charge -> [0,N]^3 with zero charge on the nodes N (R1)."""
+    N = f.shape[0]
+    fc = np.zeros((N + 1,) * 3)
+    fc[:N, :N, :N] = f
+    return fc
+
+
+def required_dgf_extent(prm: Params) -> int:
+    n, s, gb, b = prm.n, prm.s, prm.g_beta, prm.b
+    local = n + s
+    basis = n + gb + 4 * b + 4 + 4 if gb > prm.g_alpha else 0
+    flo, fhi = prm.fh_extent
+    olo, ohi = prm.phih_extent
+    coarse = max(fhi - olo, ohi - flo)
+    return max(local, basis, coarse)
+
+
+def mlc_solve(prm: Params, f_closed: np.ndarray, G1: np.ndarray | None = None, stages: dict | None = None):
+    """Two-level MLC (Sec. 4) for the charge f on [0,N]^3 (shape (N+1)^3).
+
+    Returns phi^{MLC,h} on [0,N]^3.  If ``stages`` is a dict it is filled with
+    the intermediate results (moments, F^H, phi^H, phi^B)."""
+    N, n, h, H = prm.N, prm.n, prm.h, prm.H
+    if f_closed.shape != (N + 1,) * 3:
+        raise ValueError("charge must be given on [0,N]^3")
+    if G1 is None:
+        G1 = dgf_octant(prm.Q, prm.nD, prm.zeta)
+    if required_dgf_extent(prm) > G1.shape[0] - 1:
+        raise ValueError("DGF table too small for these parameters")
+    NP = prm.npatch
+    src = box_points(0, n)  # closed-patch nodes m
+    chi = chi_patch(n)
+    origins = np.array([patch_origin(prm, i) for i in range(NP)])
+    # charges of all patches as columns: f[n i + m]
+    Fcols = np.empty((src.shape[0], NP))
+    for i in range(NP):
+        g = origins[i][None, :] + src
+        Fcols[:, i] = f_closed[g[:, 0], g[:, 1], g[:, 2]]
+
+    lap = stencil(prm.Q)
+    ga_lo, ga_hi = prm.alpha_box
+    gb_lo, gb_hi = prm.beta_box
+
+    # ---- Step 1: local convolutions phi^{i,h} = G^h * f^{i,h} (eq. initiallocalproblemsmlcII)
+    fb_lo, fb_hi = prm.field_box
+    face_alpha = face_nodes_in_box(prm, ga_lo, ga_hi)
+    coarse_field = box_points(fb_lo, fb_hi, 4)
+    phi_set = PointSet(np.concatenate([coarse_field, face_alpha]))
+    Kphi = green_matrix(G1, phi_set.pts, src) * (h * h) * chi[None, :]
+    PHI = Kphi @ Fcols  # (points, patches)
+    del Kphi
+
+    # Legendre coefficients by composite Boole's rule (Sec. 4, Step 1)
+    Cmom = moment_matrix(prm) @ Fcols  # (npoly, patches)
+
+    ca_lo, ca_hi = prm.c_alpha
+    cb_lo, cb_hi = prm.c_beta
+    ck_alpha = box_points(ca_lo, ca_hi)
+    ring = prm.g_beta > prm.g_alpha
+    if ring:
+        ck_beta = box_points(cb_lo, cb_hi)
+        in_alpha = np.all((ck_beta >= ca_lo) & (ck_beta <= ca_hi), axis=1)
+        ck_ring = ck_beta[~in_alpha]
+        face_beta = face_nodes_in_box(prm, gb_lo, gb_hi)
+        inA = np.all((face_beta >= ga_lo) & (face_beta <= ga_hi), axis=1)
+        face_ring = face_beta[~inA]
+        st_ring_P, st_ring_W = stencils_for(prm, face_ring)
+        # points at which the basis fields G^h * P^h are needed
+        lap_pts = (4 * (ck_ring[:, None, :] + np.array([o for o, _ in lap])[None, :, :])).reshape(-1, 3)
+        B_set = PointSet(np.concatenate([lap_pts, face_ring, 4 * st_ring_P.reshape(-1, 3)]))
+        Lcharge = (legendre_patch(prm) * chi[None, :]).T  # (src, npoly)
+        BV = (green_matrix(G1, B_set.pts, src) * (h * h)) @ Lcharge  # (points, npoly)
+
+    # local coarse charges F^{i,H} (eq. FDLD) and their sum F^H (Step 2)
+    flo, fhi = prm.fh_extent
+    nf = fhi - flo + 1
+    FH = np.zeros((nf, nf, nf))
+    offs = np.array([o for o, _ in lap])
+    coefs = np.array([c for _, c in lap]) / (H * H)
+    idxA = phi_set.index(4 * (ck_alpha[:, None, :] + offs[None, :, :]))  # (|Calpha|, nst)
+    LapA = np.einsum("s,asp->ap", coefs, PHI[idxA])  # (|Calpha|, patches)
+    if ring:
+        idxR = B_set.index(4 * (ck_ring[:, None, :] + offs[None, :, :]))
+        T = np.einsum("s,asq->aq", coefs, BV[idxR])  # Delta^H (G^h * Q^p) on the ring, (|ring|, npoly)
+        LapR = T @ Cmom  # (|ring|, patches)
+    for i in range(NP):
+        co = origins[i] // 4
+        k = ck_alpha + co - flo
+        FH[k[:, 0], k[:, 1], k[:, 2]] += LapA[:, i]
+        if ring:
+            k = ck_ring + co - flo
+            FH[k[:, 0], k[:, 1], k[:, 2]] += LapR[:, i]
+
+    # ---- Step 2: global coarse solve phi^H = G^H * F^H, G^H = H^{-1} G^{h=1}
+    olo, ohi = prm.phih_extent
+    no = ohi - olo + 1
+    phiH = direct_sum(G1, FH, (flo,) * 3, (olo,) * 3, (no,) * 3, H * H)
+
+    # ---- Step 3: boundary values by local corrections (eqs. philocmlcII, mlcfulldiscr)
+    gpts = box_points(0, N)
+    gface = gpts[np.any(gpts % n == 0, axis=1)]
+    del gpts
+    gmap = -np.ones((N + 1,) * 3, dtype=np.int64)
+    gmap[gface[:, 0], gface[:, 1], gface[:, 2]] = np.arange(len(gface))
+    S = (2 * prm.b + 2) ** 2
+    # phi^{loc,g} at g itself and at the S points 4k of its stencil
+    loc_self = np.zeros(len(gface))
+    loc_st = np.zeros((len(gface), S))
+    stA_P, _ = stencils_for(prm, face_alpha)
+    idx_selfA = phi_set.index(face_alpha)
+    idx_stA = phi_set.index(4 * stA_P)  # (|faceA|, S)
+    if ring:
+        BV_self = BV[B_set.index(face_ring)]  # (|faceR|, npoly)
+        BV_st = BV[B_set.index(4 * st_ring_P)].reshape(-1, BV.shape[1])  # (|faceR| S, npoly)
+    chunk = 32
+    for c0 in range(0, NP, chunk):
+        c1 = min(NP, c0 + chunk)
+        if ring:
+            R_self = BV_self @ Cmom[:, c0:c1]  # (|faceR|, chunk)
+            R_st = (BV_st @ Cmom[:, c0:c1]).reshape(len(face_ring), S, c1 - c0)
+        for i in range(c0, c1):
+            org = origins[i]
+            g = face_alpha + org
+            ok = np.all((g >= 0) & (g <= N), axis=1)
+            gi = gmap[g[ok, 0], g[ok, 1], g[ok, 2]]
+            loc_self[gi] += PHI[idx_selfA[ok], i]
+            loc_st[gi] += PHI[idx_stA[ok], i]
+            if ring:
+                g = face_ring + org
+                ok = np.all((g >= 0) & (g <= N), axis=1)
+                gi = gmap[g[ok, 0], g[ok, 1], g[ok, 2]]
+                loc_self[gi] += R_self[ok, i - c0]
+                loc_st[gi] += R_st[ok, :, i - c0]
+    phiB = np.empty(len(gface))
+    for a0 in range(0, len(gface), 1 << 18):
+        a1 = min(len(gface), a0 + (1 << 18))
+        stG_P, stG_W = stencils_for(prm, gface[a0:a1])
+        q = stG_P - olo
+        phiH_at = phiH[q[..., 0], q[..., 1], q[..., 2]]
+        phiB[a0:a1] = loc_self[a0:a1] + np.sum(stG_W * (phiH_at - loc_st[a0:a1]), axis=1)
+    del loc_st
+
+    # ---- Dirichlet problems on each patch (eq. last_step_fulldiscr) and the
+    # ---- Mehrstellen correction (eq. mcapplicationfulldiscr)
+    U = np.zeros((NP,) + (n + 1,) * 3)
+    bnd = np.zeros((n + 1,) * 3, dtype=bool)
+    bnd[0, :, :] = bnd[-1, :, :] = bnd[:, 0, :] = bnd[:, -1, :] = bnd[:, :, 0] = bnd[:, :, -1] = True
+    bl = np.argwhere(bnd)
+    gb = origins[:, None, :] + bl[None, :, :]  # (NP, |bnd|, 3)
+    U[:, bnd] = phiB[gmap[gb[..., 0], gb[..., 1], gb[..., 2]]]
+    fp = np.empty_like(U)
+    for i in range(NP):
+        o = origins[i]
+        fp[i] = f_closed[o[0]:o[0] + n + 1, o[1]:o[1] + n + 1, o[2]:o[2] + n + 1]
+    U = dirichlet_solve(prm, U, fp)
+    U += C2 * h * h * fp
+    phi = np.zeros((N + 1,) * 3)
+    for i in range(NP):
+        o = origins[i]
+        phi[o[0]:o[0] + n + 1, o[1]:o[1] + n + 1, o[2]:o[2] + n + 1] = U[i]
+
+    if stages is not None:
+        stages["moments"] = Cmom.T.copy()
+        stages["FH"] = FH
+        stages["FH_lo"] = flo
+        stages["phiH"] = phiH
+        stages["phiH_lo"] = olo
+        stages["face_nodes"] = gface
+        stages["phiB"] = phiB
+    return phi
+
+
+def dirichlet_solve(prm: Params, U: np.ndarray, fp: np.ndarray) -> np.ndarray:
+    """Solve Delta^h u = f on the patch interiors with u = U on the patch
+    boundaries (eq. last_step_fulldiscr) by dense DST-I matrices.
+
+    U, fp: (patches, n+1, n+1, n+1); returns U with the interior filled."""
+    n, h = prm.n, prm.h
+    lap = stencil(prm.Q)
+    rhs = fp[:, 1:-1, 1:-1, 1:-1].copy()
+    for (s0, s1, s2), c in lap:
+        rhs -= (c / (h * h)) * U[:, 1 + s0:n + s0, 1 + s1:n + s1, 1 + s2:n + s2]
+    k = np.arange(1, n)
+    Sm = np.sin(np.pi * np.outer(k, k) / n)  # DST-I matrix, Sm @ Sm = (n/2) I
+    cth = np.cos(np.pi * k / n)
+    lam = symbol(prm.Q, cth[:, None, None], cth[None, :, None], cth[None, None, :]) / (h * h)
+
+    def dst3(x):
+        x = np.einsum("ai,pijk->pajk", Sm, x)
+        x = np.einsum("bj,pajk->pabk", Sm, x)
+        return np.einsum("ck,pabk->pabc", Sm, x)
+
+    out = U.copy()
+    out[:, 1:-1, 1:-1, 1:-1] = dst3(dst3(rhs) / lam[None]) * (2.0 / n) ** 3
+    return out
+
+
+def plain_solution(prm: Params, f_closed: np.ndarray, G1: np.ndarray | None = None) -> np.ndarray:
+    """The plain definition G^h * f^h + C2 h^2 f^h on [0,N]^3 (eq. msCorr4),
+    by a global direct sum."""
+    N, h = prm.N, prm.h
+    if G1 is None:
+        G1 = dgf_octant(prm.Q, prm.nD, prm.zeta)
+    conv = direct_sum(G1, f_closed, (0, 0, 0), (0, 0, 0), (N + 1,) * 3, h * h)
+    return conv + C2 * h * h * f_closed
+
+
+def solve_open(prm: Params, f: np.ndarray, **kw) -> np.ndarray:
+    """Oracle in the library's array convention: f on [0,N)^3 -> phi on [0,N)^3."""
+    N = prm.N
+    phi = mlc_solve(prm, pad_charge(np.asarray(f, dtype=np.float64)), **kw)
+    return phi[:N, :N, :N]
