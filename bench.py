@@ -1,0 +1,285 @@
+#!/usr/bin/env python
+"""Benchmark: two-level MLC solve throughput (Mpoints/s) on synthetic bump charges.
+
+One step = one full solve (all steps of Sec. 4: moments, local convolutions,
+coarse charge, coarse solve, boundary values, Dirichlet solves) of the
+128^3 workload (512 patches of 16^3, support 16, Q = 4, P = 4, FP64; 8 bumps
+from seed 1) with the charge resident in HBM.  L2 is flushed (a 512 MB write)
+between timed steps; the flush is outside the timed region.
+
+Prints one JSON line.  `--impl reference` times the CPU oracle instead.
+Under torchrun each rank solves its own copy (independent problems, no
+collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1702_08111_gb300 import inputs as I  # noqa: E402
+
+METRIC = "MLC solve Mpoints/s at stated max error vs FP64 oracle"
+WORKLOAD = "bumps8_128"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._th = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._th = threading.Thread(target=self._run, daemon=True)
+        self._th.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._th:
+            self._th.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if len(s) > 3 + k and s[3 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def conv_pass_flops(M: int, lines: int, passes: int = 1) -> float:
+    """Nominal radix-2 FLOPs of `passes` complex FFTs of length M on `lines` lines."""
+    return lines * passes * 5.0 * M * np.log2(M)
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_1702_08111_gb300 import mlc
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    dev = torch.device("cuda")
+    w = I.workload(args.workload)
+    N = w.N
+    plan = mlc.Plan(N, w.n, w.s, w.P, w.Q)
+    f_host = torch.from_numpy(w.charge())
+    f = f_host.to(dev)
+    phi = torch.empty((N, N, N), dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        plan.solve(f, phi)
+        flush.zero_()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    plan.set_timing(True)
+    per_launch = {}
+    total_ms = 0.0
+    smi_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or 0) if False else int(
+        os.environ.get("LOCAL_RANK", 0))
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(smi_index) as clk:
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            ev0.record(stream)
+            plan.solve(f, phi, stream)
+            ev1.record(stream)
+            ev1.synchronize()
+            total_ms += ev0.elapsed_time(ev1)
+            for k, v in plan.timing().items():
+                per_launch[k] = per_launch.get(k, 0.0) + v
+            flush.zero_()
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    plan.set_timing(False)
+    ms = total_ms / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    per_launch = {k: v / args.steps for k, v in per_launch.items()}
+
+    # end to end through the C ABI with host buffers (copies inside the call)
+    f_pin = f_host.pin_memory()
+    phi_pin = torch.empty((N, N, N), dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        plan.solve_host(f_pin, phi_pin)
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        plan.solve_host(f_pin, phi_pin)
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    e2e_ms /= args.steps
+
+    pts = float(N) ** 3
+    value = world * pts / (ms * 1e-3) / 1e6
+    info = plan.info
+    M, Mh, NP = info.M, info.M // 2 + 1, (N // w.n) ** 3
+    # dominant launch: the fused z pass (forward FFT, kernel multiply, inverse FFT)
+    dom = max(per_launch, key=per_launch.get)
+    flops = {
+        "conv_z_kernel": conv_pass_flops(M, NP * M * Mh, 2) + NP * M * M * Mh * 2.0,
+        "conv_inv_y": conv_pass_flops(M, NP * (w.s * 2 + w.n + 1) * Mh),
+        "conv_inv_x": conv_pass_flops(M, NP * (w.s * 2 + w.n + 1) ** 2),
+        "conv_fwd_y": conv_pass_flops(M, NP * (w.n + 1) * Mh),
+    }
+    roof = None
+    if dom in flops:
+        achieved = flops[dom] / (per_launch[dom] * 1e-3) / 1e9
+        peak = 1250.0  # FP64 nominal GFLOP/s (152 SMs x 2.07 GHz x 4 FP64 flop/clk/SM)
+        roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GFLOP/s (FP64)", "frac": round(achieved / peak, 4), "traffic": None,
+                "launch_ms": round(per_launch[dom], 4)}
+    res = {"value": value, "ms": ms, "e2e_ms": e2e_ms, "per_launch": per_launch, "roofline": roof,
+           "clocks": clk.summary(), "phi": phi, "N": N, "plan": plan}
+    return res
+
+
+def cpu_oracle_solve(w, nodes_sample=None):
+    from oracle import mlc_oracle as O
+    G1 = O.dgf_octant(w.Q, 128, 2)
+    prm = O.Params(N=w.N, n=w.n, s=w.s, Q=w.Q, P=w.P)
+    f = w.charge()
+    t0 = time.perf_counter()
+    phi = O.solve_open(prm, f, G1=G1)
+    return phi, time.perf_counter() - t0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    w = I.workload(args.workload)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        return run_reference(args, w)
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    r = run_ours(args, rank, world)
+    line = None
+    if rank == 0:
+        cpu = None
+        err = None
+        if not args.no_cpu_baseline and world == 1 or (rank == 0 and not args.no_cpu_baseline):
+            phi_o, t = cpu_oracle_solve(w)
+            got = r["phi"].cpu().numpy()
+            err = float(np.abs(got - phi_o).max() / np.abs(phi_o).max())
+            cpu = {"value": round(float(w.N) ** 3 / t / 1e6, 4), "unit": "Mpoints/s",
+                   "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"one full oracle solve of {args.workload} ({t:.1f} s; DGF table prebuilt)"}
+        N = r["N"]
+        e2e_val = float(N) ** 3 / (r["e2e_ms"] * 1e-3) / 1e6
+        launches = 15
+        line = {
+            "metric": METRIC, "value": round(r["value"], 3), "unit": "Mpoints/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r["ms"], 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "N": w.N, "patch": w.n, "support": w.s, "Q": w.Q,
+                       "P": w.P, "tier": "fp64", "l2": "flushed between steps (512 MB write)",
+                       "parallelism": f"independent problem per GPU x{world}"},
+            "max_rel_err_vs_oracle": err,
+            "e2e": {"value": round(e2e_val, 3), "unit": "Mpoints/s",
+                    "h2d_bytes_per_step": int(N ** 3 * 8), "d2h_bytes_per_step": int(N ** 3 * 8)},
+            "gpu_launches": launches * args.steps,
+            "roofline": r["roofline"], "cpu_baseline": cpu, "clocks": r["clocks"],
+            "per_launch_ms": {k: round(v, 4) for k, v in r["per_launch"].items()},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_reference(args, w):
+    """Time the CPU oracle as it stands on a bounded sample of the workload."""
+    from oracle import mlc_oracle as O
+    # bounded sample: the 64^3 sub-problem with the workload's patch geometry and
+    # charge recipe (8 patches instead of 512), one full oracle solve per step
+    sub = I.Workload(w.name + "_sample64", 64, w.n, w.s, w.Q, w.P, bumps=I.draw_bumps(8, 1))
+    G1 = O.dgf_octant(w.Q, 128, 2)
+    prm = O.Params(N=64, n=w.n, s=w.s, Q=w.Q, P=w.P)
+    f = sub.charge()
+    for _ in range(args.warmup):
+        O.solve_open(prm, f, G1=G1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.solve_open(prm, f, G1=G1)
+    dt = (time.perf_counter() - t0) / args.steps
+    val = 64.0 ** 3 / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(val, 5), "unit": "Mpoints/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "N": w.N, "patch": w.n, "support": w.s, "Q": w.Q, "P": w.P,
+                   "tier": "fp64"},
+        "cpu_baseline": {"value": round(val, 5), "unit": "Mpoints/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": "64^3 sub-problem (8 patches of 16^3, support 16, 8 bumps, seed 1) per step"},
+        "e2e": {"value": round(val, 5), "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,189 @@
+/*
+ * mlc.h -- C ABI of the GB300 two-level Method of Local Corrections (MLC)
+ * solver for the free-space Poisson equation (Kavouklis & Colella,
+ * arXiv:1702.08111, Sec. 4 "Fully-Discrete Two-Level Algorithm").
+ *
+ * Problem (Sec. 1, eqs. poisson/potential): Delta phi = f on R^3 with
+ * phi(x) ~ -(int f) / (4 pi |x|) at infinity, so a positive charge gives a
+ * negative potential.  The charge is sampled on the unit cube at the nodes
+ * x = g h, h = 1/N, g in [0, N)^3 (axis 2 contiguous in memory); the nodes at
+ * index N carry zero charge (the charge must vanish on the faces x_d = 1).
+ * The result phi^{MLC,h} (Sec. 4, eq. mcapplicationfulldiscr) is returned on
+ * the same N^3 nodes.
+ *
+ * Ownership: the caller owns every array passed in (f, phi, host buffers);
+ * the library never frees them.  A plan owns its tables and its device
+ * workspace and frees them in mlc_plan_destroy.  Discrete Green's function
+ * tables are built once per (Q, nD, zeta) on each device and stay resident
+ * until the process exits.
+ *
+ * Errors: every call returns an mlc_status; no exception crosses the ABI.
+ * CUDA errors raised by kernels that run asynchronously are reported by the
+ * next call that synchronises or checks the stream (MLC_ERR_CUDA).
+ *
+ * Threads: a plan may be used by one host thread at a time; different plans
+ * may be used concurrently on different streams.
+ */
+#ifndef MLC_H
+#define MLC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MLC_OK = 0,
+    MLC_ERR_INVALID_ARG = 1, /* a size or pointer breaks a stated precondition */
+    MLC_ERR_UNSUPPORTED = 2, /* legal for the method, not built in this library */
+    MLC_ERR_OOM = 3,         /* a device or host allocation failed */
+    MLC_ERR_CUDA = 4,        /* a CUDA runtime call or kernel failed */
+    MLC_ERR_ADMISSION = 5,   /* server: request exceeds the memory budget */
+    MLC_ERR_TIMEOUT = 6      /* server: wait timed out / request cancelled */
+} mlc_status;
+
+typedef enum {
+    MLC_TIER_FP64 = 0,   /* every step in FP64 */
+    MLC_TIER_SPLIT = 1   /* charge FP32; local convolutions in split precision on the
+                            tensor cores with FP32 accumulation; coarse solve, boundary
+                            values and Dirichlet solves in FP64 */
+} mlc_tier;
+
+typedef enum {
+    MLC_MODE_MLC = 0,    /* inner radius alpha < outer radius beta, Legendre ring (Sec. 4) */
+    MLC_MODE_MLC0 = 1    /* alpha = beta, no Legendre ring (Sec. 7, "MLC-0") */
+} mlc_mode;
+
+/* Parameters of a plan.  Fields set to -1 take the defaults listed. */
+typedef struct {
+    int N;          /* nodes per axis, h = 1/N                                          */
+    int n;          /* patch side in cells (patches n i + [0,n]^3, Sec. 4); 4 | n, n | N */
+    int s;          /* support: the local field box G(Omega_alpha, C b) is the patch
+                       grown by s nodes (eq. initiallocalproblemsmlcII); 4 | s, s >= C b */
+    int C;          /* coarsening ratio N_ref; must be 4 (Sec. 2)                       */
+    int P;          /* Legendre orders: |p|_1 <= P-1 (eq. led3d); 1 <= P <= 6           */
+    int Q;          /* Mehrstellen order: 4 -> 19-point, 6 -> 27-point (App. A.1)       */
+    int g_beta;     /* outer growth ceil((beta-1) n/2) (Sec. 4); -1: beta = 3 (Q=4),
+                       3.25 (Q=6)                                                       */
+    int b;          /* interpolation stencil radius; -1: 2 for Q=4, 3 for Q=6 (Sec. 7)  */
+    int tier;       /* mlc_tier                                                         */
+    int mode;       /* mlc_mode                                                         */
+    int dgf_nD;     /* DGF table built on [-zeta nD, zeta nD]^3 (App. A.1); -1: 128,
+                       raised automatically to the largest lag the plan needs           */
+    int dgf_zeta;   /* -1: 2                                                            */
+} mlc_params;
+
+typedef struct mlc_plan_s *mlc_plan_t;
+
+/* Fill *p with N, n, s, P, Q as given, C = 4 and every other field -1/default. */
+mlc_status mlc_params_init(mlc_params *p, int N, int n, int s, int P, int Q);
+
+/*
+ * Create a plan on the current CUDA device (Sec. 4 with the regions
+ * Omega_alpha = G(Omega_i, s - C b), Omega_beta = G(Omega_i, g_beta)).  Builds
+ * the DGF table (App. A.1) if this device has none for (Q, nD, zeta), the
+ * kernel spectra for the Hockney convolutions (App. A.2), the Legendre
+ * basis-field tables Delta^H(G^h * Q^p) (Sec. 4, Step 1) and the index tables,
+ * and allocates the workspace.  Synchronises the device.
+ * INVALID_ARG if: out is NULL; N, n, s, C, P, Q break the rules above;
+ * g_beta < s - C b.  UNSUPPORTED if the patch FFT length 2(n+s) or the coarse
+ * FFT length is above 256.
+ */
+mlc_status mlc_plan_create(int N, int patch, int support, int coarsening, int P, int Q,
+                           mlc_plan_t *out);
+mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out);
+mlc_status mlc_plan_destroy(mlc_plan_t plan);
+
+/* Bytes of device workspace the plan holds (tables excluded). */
+mlc_status mlc_plan_workspace_bytes(mlc_plan_t plan, size_t *bytes);
+
+/*
+ * Solve Delta phi = f in free space by the two-level MLC (Sec. 4, Steps 1-3,
+ * Dirichlet solves and the Mehrstellen correction).  f: device array of N^3
+ * values (FP64 for MLC_TIER_FP64, FP32 for MLC_TIER_SPLIT), x = g h, axis 2
+ * contiguous.  phi: device array of N^3 FP64 values, same layout; may not
+ * alias f.  Work is enqueued on `stream` (a cudaStream_t; NULL = legacy
+ * default stream); the call returns without synchronising.  Calls with the
+ * same plan must not overlap on the GPU (they share the plan's workspace).
+ */
+mlc_status mlc_solve(mlc_plan_t plan, const void *f, void *phi, void *stream);
+
+/*
+ * As mlc_solve with host arrays: copies f (host, pinned or pageable) to the
+ * plan's device staging buffer, solves, copies phi back to the host array and
+ * synchronises the stream before returning.
+ */
+mlc_status mlc_solve_host(mlc_plan_t plan, const void *f_host, void *phi_host, void *stream);
+
+/*
+ * Solve `count` independent problems in one pass: the per-patch work of all
+ * problems runs in shared launches (local convolutions, moments, boundary
+ * and Dirichlet steps), each coarse solve on its own plan.  plans[k], f[k],
+ * phi[k] as in mlc_solve; plans must be distinct and of the same tier.
+ */
+mlc_status mlc_batch_solve(int count, const mlc_plan_t *plans, const void *const *f,
+                           void *const *phi, void *stream);
+
+/* Stage exports for testing: copy an intermediate result of the last solve
+ * to host memory (FP64 unless noted).  `bytes` must equal the stage's size,
+ * returned by mlc_debug_stage_bytes. */
+typedef enum {
+    MLC_STAGE_MOMENTS = 0,  /* Legendre coefficients c_p^i, [patch][p] (Sec. 4, Step 1)      */
+    MLC_STAGE_FH = 1,       /* coarse charge F^H on its extent [lo,hi]^3 (Step 2)            */
+    MLC_STAGE_PHIH = 2,     /* coarse potential phi^H on [-b, N/4+b]^3 (Step 2)              */
+    MLC_STAGE_PHIB = 3,     /* boundary values phi^B on the face planes,
+                               [axis][plane j][u][v], plane x_axis = j n, (u,v) the other
+                               two coordinates in increasing axis order (Step 3)             */
+    MLC_STAGE_DGF = 4       /* the DGF octant G^{h=1}[0..L]^3, L = entry 14 of mlc_plan_info  */
+} mlc_stage;
+
+mlc_status mlc_debug_stage_bytes(mlc_plan_t plan, int stage, size_t *bytes);
+/* Per-launch timing of later solves with this plan: when enabled, mlc_solve
+ * records a CUDA event on its stream before each of its 15 launches and after
+ * the last.  mlc_debug_timing waits for the last solve's final event and
+ * writes the 15 durations (ms) in launch order: moments; local convolution
+ * x, y, z (forward, kernel, inverse), inverse y, inverse x; residuals;
+ * assembly of F^H; coarse convolution x, y, z, inverse y, inverse x;
+ * boundary values; Dirichlet solves.  count must be >= 15. */
+mlc_status mlc_debug_set_timing(mlc_plan_t plan, int enable);
+mlc_status mlc_debug_timing(mlc_plan_t plan, float *ms_out, int count);
+mlc_status mlc_debug_export(mlc_plan_t plan, int stage, void *host, size_t bytes);
+/* Geometry of the plan: out[0..15] = N, n, s, b, g_alpha, g_beta, P, npoly,
+ * fh_lo, fh_hi, phih_lo, phih_hi, M (patch FFT), Mc (coarse FFT), L (DGF
+ * extent), nD. */
+mlc_status mlc_plan_info(mlc_plan_t plan, int *out16);
+
+/* ---------------- continuous-batching server ---------------- */
+typedef struct mlc_server_s *mlc_server_t;
+
+typedef struct {
+    mlc_params params;   /* problem definition (N, n, s, P, Q, tier, ...)          */
+    const void *f;       /* device charge, as in mlc_solve; must stay alive until done */
+    void *phi;           /* device result, as in mlc_solve; must stay alive until done */
+} mlc_request;
+
+typedef struct {
+    mlc_status status;   /* outcome of the solve                                     */
+    double latency_ms;   /* enqueue -> completion                                    */
+    double queue_ms;     /* enqueue -> start of its batch                            */
+} mlc_result;
+
+/* Create a server on the current device with a device-memory budget (bytes)
+ * for the plans and workspaces of admitted requests, and at most `max_batch`
+ * requests per launch group. */
+mlc_status mlc_server_create(size_t hbm_budget_bytes, int max_batch, mlc_server_t *out);
+mlc_status mlc_server_destroy(mlc_server_t srv);
+/* Enqueue a request (copied); returns a ticket.  ADMISSION if the request
+ * alone can never fit the budget; INVALID_ARG for bad parameters. */
+mlc_status mlc_server_enqueue(mlc_server_t srv, const mlc_request *req, uint64_t *ticket);
+/* Wait up to timeout_ms (<0: forever) for a ticket; TIMEOUT if not done. */
+mlc_status mlc_server_wait(mlc_server_t srv, uint64_t ticket, int timeout_ms, mlc_result *res);
+
+const char *mlc_status_string(mlc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLC_H */

@@ -1,0 +1,649 @@
+// Host side of the MLC library: parameter checks, plan geometry and index
+// tables (Sec. 4 regions), plan-time tables, the solve sequence and the C ABI.
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "mlc_internal.h"
+
+using namespace mlc;
+
+namespace {
+
+int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+int ceildiv(int a, int b) { return -floordiv(-a, b); }
+int fmod_pos(int a, int b) { int r = a % b; return r < 0 ? r + b : r; }
+
+int next_pow2(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+void stencil_b(int Q, double b[4]) {
+    if (Q == 4) {
+        b[0] = -4.0; b[1] = 1.0 / 3.0; b[2] = 1.0 / 6.0; b[3] = 0.0;
+    } else {
+        b[0] = -64.0 / 15.0; b[1] = 7.0 / 15.0; b[2] = 1.0 / 10.0; b[3] = 1.0 / 30.0;
+    }
+}
+
+double symbol(int Q, double c0, double c1, double c2) {
+    double b[4];
+    stencil_b(Q, b);
+    return b[0] + 2.0 * b[1] * (c0 + c1 + c2) + 4.0 * b[2] * (c0 * c1 + c0 * c2 + c1 * c2) +
+           8.0 * b[3] * c0 * c1 * c2;
+}
+
+// Orthonormal Legendre polynomial sqrt((2k+1)/2) P_k(t) by the three-term recurrence.
+double legendre(int k, double t) {
+    double p0 = 1.0, p1 = t;
+    if (k == 0) return std::sqrt(0.5);
+    for (int j = 1; j < k; ++j) {
+        double p2 = ((2.0 * j + 1.0) * t * p1 - j * p0) / (j + 1.0);
+        p0 = p1;
+        p1 = p2;
+    }
+    return std::sqrt((2.0 * k + 1.0) / 2.0) * p1;
+}
+
+// 1D factor of the interpolant I^H at fine coordinate x (R4 reading of Sec. 4, Step 3).
+void axis_stencil(int x, int b, std::vector<int> &nodes, std::vector<double> &w) {
+    nodes.clear();
+    w.clear();
+    if (fmod_pos(x, 4) == 0) {
+        nodes.push_back(floordiv(x, 4));
+        w.push_back(1.0);
+        return;
+    }
+    const int k0 = floordiv(x, 4), K = 2 * b + 2;
+    const double t = (double)(x - 4 * k0) / 4.0 + b;
+    for (int j = 0; j < K; ++j) {
+        double v = 1.0;
+        for (int l = 0; l < K; ++l)
+            if (l != j) v *= (t - l) / (double)(j - l);
+        nodes.push_back(k0 - b + j);
+        w.push_back(v);
+    }
+}
+
+// Full stencil of I^H at a face-lattice point: tensor product of the axis factors.
+void face_stencil(const int g[3], int b, std::vector<std::array<int, 3>> &pts, std::vector<double> &w) {
+    std::vector<int> n0, n1, n2;
+    std::vector<double> w0, w1, w2;
+    axis_stencil(g[0], b, n0, w0);
+    axis_stencil(g[1], b, n1, w1);
+    axis_stencil(g[2], b, n2, w2);
+    pts.clear();
+    w.clear();
+    for (size_t a = 0; a < n0.size(); ++a)
+        for (size_t c = 0; c < n1.size(); ++c)
+            for (size_t e = 0; e < n2.size(); ++e) {
+                pts.push_back({n0[a], n1[c], n2[e]});
+                w.push_back(w0[a] * w1[c] * w2[e]);
+            }
+}
+
+bool on_face(const int g[3], int n) {
+    return fmod_pos(g[0], n) == 0 || fmod_pos(g[1], n) == 0 || fmod_pos(g[2], n) == 0;
+}
+
+// ---- per-device DGF table cache (tables stay resident until process exit) ----
+struct DgfEntry {
+    double *ptr;
+    int L;
+};
+std::mutex g_dgf_mu;
+std::map<std::tuple<int, int, int, int>, DgfEntry> g_dgf;
+std::once_flag g_cfg_once;
+
+mlc_status to_status(cudaError_t e) {
+    if (e == cudaSuccess) return MLC_OK;
+    if (e == cudaErrorMemoryAllocation) return MLC_ERR_OOM;
+    return MLC_ERR_CUDA;
+}
+
+#define TRY_CUDA(x)                               \
+    do {                                          \
+        cudaError_t _e = (x);                     \
+        if (_e != cudaSuccess) return to_status(_e); \
+    } while (0)
+
+template <typename T>
+mlc_status dev_upload(mlc_plan_s *pl, T **dst, const std::vector<T> &src) {
+    *dst = nullptr;
+    if (src.empty()) return MLC_OK;
+    void *p = nullptr;
+    TRY_CUDA(cudaMalloc(&p, src.size() * sizeof(T)));
+    pl->owned.push_back(p);
+    TRY_CUDA(cudaMemcpy(p, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    *dst = (T *)p;
+    return MLC_OK;
+}
+
+template <typename T>
+mlc_status dev_alloc(mlc_plan_s *pl, T **dst, size_t count, bool workspace = true) {
+    *dst = nullptr;
+    if (count == 0) return MLC_OK;
+    void *p = nullptr;
+    TRY_CUDA(cudaMalloc(&p, count * sizeof(T)));
+    pl->owned.push_back(p);
+    if (workspace) pl->ws_bytes += count * sizeof(T);
+    *dst = (T *)p;
+    return MLC_OK;
+}
+
+#define TRY(x)                             \
+    do {                                   \
+        mlc_status _s = (x);               \
+        if (_s != MLC_OK) return _s;       \
+    } while (0)
+
+mlc_status derive_geometry(const mlc_params &pp, Geom &g) {
+    g = Geom{};
+    g.N = pp.N; g.n = pp.n; g.s = pp.s; g.C = pp.C; g.P = pp.P; g.Q = pp.Q;
+    if (g.C != 4) return MLC_ERR_INVALID_ARG;
+    if (g.Q != 4 && g.Q != 6) return MLC_ERR_INVALID_ARG;
+    if (g.N <= 0 || g.n <= 0 || g.s < 0 || g.P < 1 || g.P > 6) return MLC_ERR_INVALID_ARG;
+    if (g.N % g.n || g.n % 4 || g.s % 4) return MLC_ERR_INVALID_ARG;
+    g.b = pp.b < 0 ? (g.Q == 4 ? 2 : 3) : pp.b;
+    if (g.b < 1 || g.b > 3) return MLC_ERR_INVALID_ARG;
+    g.ga = g.s - g.C * g.b;
+    if (g.ga < 0) return MLC_ERR_INVALID_ARG;
+    g.mode = pp.mode < 0 ? MLC_MODE_MLC : pp.mode;
+    g.tier = pp.tier < 0 ? MLC_TIER_FP64 : pp.tier;
+    if (g.mode == MLC_MODE_MLC0) {
+        g.gb = g.ga;
+    } else if (pp.g_beta >= 0) {
+        g.gb = pp.g_beta;
+    } else {
+        // beta = 3 (Q = 4) or 13/4 (Q = 6): g_beta = ceil((beta - 1) n / 2)
+        g.gb = (g.Q == 4) ? g.n : ceildiv(9 * g.n, 8);
+    }
+    if (g.gb < g.ga) return MLC_ERR_INVALID_ARG;
+    g.h = 1.0 / g.N;
+    g.H = g.C * g.h;
+    g.R = g.n * g.h / 2.0;
+    g.np = g.N / g.n;
+    g.NP = g.np * g.np * g.np;
+    g.npoly = 0;
+    for (int a = 0; a < g.P; ++a)
+        for (int c = 0; c < g.P; ++c)
+            for (int e = 0; e < g.P; ++e)
+                if (a + c + e < g.P) ++g.npoly;
+    g.nb = g.n + 1;
+    g.W = g.n + 2 * g.s + 1;
+    g.M = next_pow2(2 * (g.n + g.s));
+    g.log2M = ilog2(g.M);
+    g.Mh = g.M / 2 + 1;
+    g.ca_lo = floordiv(-g.ga, 4); g.ca_hi = ceildiv(g.n + g.ga, 4);
+    g.cb_lo = floordiv(-g.gb, 4); g.cb_hi = ceildiv(g.n + g.gb, 4);
+    g.flo = g.cb_lo;
+    g.fhi = (g.np - 1) * (g.n / 4) + g.cb_hi;
+    g.nf = g.fhi - g.flo + 1;
+    g.olo = -g.b; g.ohi = g.N / 4 + g.b;
+    g.no = g.ohi - g.olo + 1;
+    g.Lc = std::max(g.fhi - g.olo, g.ohi - g.flo);
+    g.Mc = next_pow2(std::max(2 * g.Lc, std::max(g.nf, g.no)));
+    g.log2Mc = ilog2(g.Mc);
+    g.Mhc = g.Mc / 2 + 1;
+    if (g.M > 256 || g.Mc > 256 || g.M < 32) return MLC_ERR_UNSUPPORTED;
+    if (g.n > 16) return MLC_ERR_UNSUPPORTED;  // Dirichlet tile held in shared memory
+    g.S = (2 * g.b + 2) * (2 * g.b + 2);
+    g.wa = g.n + 2 * g.ga + 1;
+    g.wbx = g.n + 2 * g.gb + 1;
+    g.plane_n = (g.N + 1) * (g.N + 1);
+    g.n_planes_total = 3L * (g.np + 1) * (long)g.plane_n;
+    g.zeta = pp.dgf_zeta < 0 ? 2 : pp.dgf_zeta;
+    g.nD = pp.dgf_nD < 0 ? 128 : pp.dgf_nD;
+    return MLC_OK;
+}
+
+// Host tables for one plan; basis fields need the DGF on the device.
+mlc_status build_tables(mlc_plan_s *pl) {
+    Geom &g = pl->g;
+    const int n = g.n, nb = g.nb, nb3 = nb * nb * nb, W = g.W;
+    // Legendre basis at the patch nodes (R3), Boole weights, chi
+    std::vector<std::array<int, 3>> pidx;
+    for (int a = 0; a < g.P; ++a)
+        for (int c = 0; c < g.P; ++c)
+            for (int e = 0; e < g.P; ++e)
+                if (a + c + e < g.P) pidx.push_back({a, c, e});
+    std::vector<double> bw(nb, 0.0), chi1(nb, 1.0);
+    const double panel[5] = {7.0, 32.0, 12.0, 32.0, 7.0};
+    for (int pn = 0; pn < n / 4; ++pn)
+        for (int k = 0; k < 5; ++k) bw[4 * pn + k] += (2.0 * g.h / 45.0) * panel[k];
+    chi1[0] = chi1[n] = 0.5;
+    std::vector<double> leg((size_t)g.P * nb);
+    for (int k = 0; k < g.P; ++k)
+        for (int m = 0; m < nb; ++m) leg[(size_t)k * nb + m] = legendre(k, 2.0 * m / n - 1.0);
+    const double rs = std::pow(g.R, -1.5);
+    std::vector<double> momw((size_t)g.npoly * nb3), lcharge((size_t)g.npoly * nb3);
+    for (int p = 0; p < g.npoly; ++p)
+        for (int m0 = 0; m0 < nb; ++m0)
+            for (int m1 = 0; m1 < nb; ++m1)
+                for (int m2 = 0; m2 < nb; ++m2) {
+                    const double q = rs * leg[(size_t)pidx[p][0] * nb + m0] *
+                                     leg[(size_t)pidx[p][1] * nb + m1] *
+                                     leg[(size_t)pidx[p][2] * nb + m2];
+                    const size_t m = ((size_t)m0 * nb + m1) * nb + m2;
+                    momw[(size_t)p * nb3 + m] = bw[m0] * bw[m1] * bw[m2] * q;
+                    lcharge[(size_t)p * nb3 + m] = chi1[m0] * chi1[m1] * chi1[m2] * q;
+                }
+    TRY(dev_upload(pl, &pl->momw, momw));
+
+    // alpha face nodes and their interpolation stencils inside the field box
+    std::vector<int> amap((size_t)g.wa * g.wa * g.wa, -1), a_self, a_off;
+    std::vector<double> a_w;
+    std::vector<std::array<int, 3>> sp;
+    std::vector<double> sw;
+    auto boxidx = [&](int x0, int x1, int x2) {
+        return ((x0 + g.s) * W + (x1 + g.s)) * W + (x2 + g.s);
+    };
+    for (int x0 = -g.ga; x0 <= n + g.ga; ++x0)
+        for (int x1 = -g.ga; x1 <= n + g.ga; ++x1)
+            for (int x2 = -g.ga; x2 <= n + g.ga; ++x2) {
+                const int gg[3] = {x0, x1, x2};
+                if (!on_face(gg, n)) continue;
+                amap[((size_t)(x0 + g.ga) * g.wa + (x1 + g.ga)) * g.wa + (x2 + g.ga)] = (int)a_self.size();
+                a_self.push_back(boxidx(x0, x1, x2));
+                face_stencil(gg, g.b, sp, sw);
+                if ((int)sp.size() > g.S) return MLC_ERR_INVALID_ARG;
+                for (int j = 0; j < g.S; ++j) {
+                    const int jj = j < (int)sp.size() ? j : 0;
+                    const int y0 = 4 * sp[jj][0], y1 = 4 * sp[jj][1], y2 = 4 * sp[jj][2];
+                    if (y0 < -g.s || y0 > n + g.s || y1 < -g.s || y1 > n + g.s || y2 < -g.s || y2 > n + g.s)
+                        return MLC_ERR_INVALID_ARG;
+                    a_off.push_back(boxidx(y0, y1, y2));
+                    a_w.push_back(j < (int)sp.size() ? sw[j] : 0.0);
+                }
+            }
+    g.na_face = (int)a_self.size();
+    TRY(dev_upload(pl, &pl->amap, amap));
+    TRY(dev_upload(pl, &pl->a_self, a_self));
+    TRY(dev_upload(pl, &pl->a_off, a_off));
+    TRY(dev_upload(pl, &pl->a_w, a_w));
+
+    // ring: face nodes in Omega_beta \ Omega_alpha and coarse nodes C(beta) \ C(alpha)
+    std::vector<int> rmap((size_t)g.wbx * g.wbx * g.wbx, -1);
+    std::vector<std::array<int, 3>> ring_nodes;
+    std::vector<std::vector<std::array<int, 3>>> ring_st;
+    std::vector<std::vector<double>> ring_w;
+    const bool ring = g.gb > g.ga;
+    const int ncb = g.cb_hi - g.cb_lo + 1;
+    std::vector<double> Ttab;
+    std::vector<double> Dtab;
+    if (ring) {
+        for (int x0 = -g.gb; x0 <= n + g.gb; ++x0)
+            for (int x1 = -g.gb; x1 <= n + g.gb; ++x1)
+                for (int x2 = -g.gb; x2 <= n + g.gb; ++x2) {
+                    const int gg[3] = {x0, x1, x2};
+                    if (!on_face(gg, n)) continue;
+                    const bool inA = x0 >= -g.ga && x0 <= n + g.ga && x1 >= -g.ga &&
+                                     x1 <= n + g.ga && x2 >= -g.ga && x2 <= n + g.ga;
+                    if (inA) continue;
+                    rmap[((size_t)(x0 + g.gb) * g.wbx + (x1 + g.gb)) * g.wbx + (x2 + g.gb)] =
+                        (int)ring_nodes.size();
+                    ring_nodes.push_back({x0, x1, x2});
+                    face_stencil(gg, g.b, sp, sw);
+                    ring_st.push_back(sp);
+                    ring_w.push_back(sw);
+                }
+        // basis-field evaluation points: ring nodes, their stencils, and the
+        // fine nodes under Delta^H on the coarse ring
+        const int pad = 4 * g.b + 12;
+        const int blo = -g.gb - pad, bhi = n + g.gb + pad, bw_ = bhi - blo + 1;
+        std::vector<int> pmap((size_t)bw_ * bw_ * bw_, -1);
+        std::vector<int> pts;
+        auto add = [&](int y0, int y1, int y2) -> int {
+            int &slot = pmap[((size_t)(y0 - blo) * bw_ + (y1 - blo)) * bw_ + (y2 - blo)];
+            if (slot < 0) {
+                slot = (int)(pts.size() / 3);
+                pts.push_back(y0); pts.push_back(y1); pts.push_back(y2);
+            }
+            return slot;
+        };
+        std::vector<int> rn_self(ring_nodes.size());
+        std::vector<std::vector<int>> rn_st(ring_nodes.size());
+        for (size_t r = 0; r < ring_nodes.size(); ++r) {
+            rn_self[r] = add(ring_nodes[r][0], ring_nodes[r][1], ring_nodes[r][2]);
+            for (auto &k : ring_st[r]) rn_st[r].push_back(add(4 * k[0], 4 * k[1], 4 * k[2]));
+        }
+        double bq[4];
+        stencil_b(g.Q, bq);
+        std::vector<std::vector<std::pair<int, double>>> lapT((size_t)ncb * ncb * ncb);
+        for (int k0 = g.cb_lo; k0 <= g.cb_hi; ++k0)
+            for (int k1 = g.cb_lo; k1 <= g.cb_hi; ++k1)
+                for (int k2 = g.cb_lo; k2 <= g.cb_hi; ++k2) {
+                    const bool inA = k0 >= g.ca_lo && k0 <= g.ca_hi && k1 >= g.ca_lo &&
+                                     k1 <= g.ca_hi && k2 >= g.ca_lo && k2 <= g.ca_hi;
+                    if (inA) continue;
+                    auto &lst = lapT[((size_t)(k0 - g.cb_lo) * ncb + (k1 - g.cb_lo)) * ncb + (k2 - g.cb_lo)];
+                    for (int s0 = -1; s0 <= 1; ++s0)
+                        for (int s1 = -1; s1 <= 1; ++s1)
+                            for (int s2 = -1; s2 <= 1; ++s2) {
+                                const int nz = (s0 != 0) + (s1 != 0) + (s2 != 0);
+                                if (bq[nz] == 0.0) continue;
+                                lst.push_back({add(4 * (k0 + s0), 4 * (k1 + s1), 4 * (k2 + s2)),
+                                               bq[nz] / (g.H * g.H)});
+                            }
+                }
+        // lag extent needed by the basis sums
+        int Lb = 0;
+        for (size_t a = 0; a < pts.size(); ++a) {
+            const int v = pts[a];
+            Lb = std::max(Lb, std::max(std::abs(v), std::abs(v - n)));
+        }
+        g.L = std::max(g.L, Lb);
+        if (g.L > pl->dgf_L) return MLC_ERR_INVALID_ARG;
+        const int npts = (int)(pts.size() / 3);
+        int *dpts = nullptr;
+        double *dch = nullptr, *dB = nullptr;
+        TRY_CUDA(cudaMalloc((void **)&dpts, pts.size() * sizeof(int)));
+        TRY_CUDA(cudaMalloc((void **)&dch, lcharge.size() * sizeof(double)));
+        TRY_CUDA(cudaMalloc((void **)&dB, (size_t)npts * g.npoly * sizeof(double)));
+        cudaMemcpy(dpts, pts.data(), pts.size() * sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemcpy(dch, lcharge.data(), lcharge.size() * sizeof(double), cudaMemcpyHostToDevice);
+        cudaError_t e = basis_direct_sum(pl->dgf, pl->dgf_L, dpts, npts, dch, g.npoly, n,
+                                         g.h * g.h, dB);
+        std::vector<double> B((size_t)npts * g.npoly);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(B.data(), dB, B.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        cudaFree(dpts);
+        cudaFree(dch);
+        cudaFree(dB);
+        TRY_CUDA(e);
+        const int np_ = g.npoly;
+        Ttab.assign((size_t)ncb * ncb * ncb * np_, 0.0);
+        for (size_t t = 0; t < lapT.size(); ++t)
+            for (auto &pr : lapT[t])
+                for (int p = 0; p < np_; ++p)
+                    Ttab[t * np_ + p] += pr.second * B[(size_t)pr.first * np_ + p];
+        Dtab.assign(ring_nodes.size() * np_, 0.0);
+        for (size_t r = 0; r < ring_nodes.size(); ++r)
+            for (int p = 0; p < np_; ++p) {
+                double iv = 0.0;
+                for (size_t j = 0; j < rn_st[r].size(); ++j)
+                    iv += ring_w[r][j] * B[(size_t)rn_st[r][j] * np_ + p];
+                Dtab[r * np_ + p] = B[(size_t)rn_self[r] * np_ + p] - iv;
+            }
+    }
+    g.nr_face = (int)ring_nodes.size();
+    TRY(dev_upload(pl, &pl->rmap, rmap));
+    TRY(dev_upload(pl, &pl->Dtab, Dtab));
+    TRY(dev_upload(pl, &pl->Ttab, Ttab));
+
+    // FFT twiddles
+    auto twiddles = [](int M) {
+        std::vector<double2> tw(M / 2);
+        for (int t = 0; t < M / 2; ++t) {
+            const double a = 2.0 * M_PI * (double)t / (double)M;
+            tw[t] = make_double2(std::cos(a), -std::sin(a));
+        }
+        return tw;
+    };
+    TRY(dev_upload(pl, &pl->tw, twiddles(g.M)));
+    TRY(dev_upload(pl, &pl->tw_c, twiddles(g.Mc)));
+
+    // Dirichlet tables: DST-I matrix and eigenvalues of the stencil / h^2
+    const int m = n - 1;
+    std::vector<double> sinm((size_t)m * m), lam((size_t)m * m * m);
+    std::vector<double> cth(m);
+    for (int k = 0; k < m; ++k) {
+        cth[k] = std::cos(M_PI * (k + 1) / (double)n);
+        for (int t = 0; t < m; ++t) {
+            const long r = ((long)(k + 1) * (t + 1)) % (2L * n);
+            sinm[(size_t)k * m + t] = std::sin(M_PI * (double)r / (double)n);
+        }
+    }
+    for (int a = 0; a < m; ++a)
+        for (int c = 0; c < m; ++c)
+            for (int e = 0; e < m; ++e)
+                lam[((size_t)a * m + c) * m + e] = symbol(g.Q, cth[a], cth[c], cth[e]) / (g.h * g.h);
+    TRY(dev_upload(pl, &pl->sinm, sinm));
+    TRY(dev_upload(pl, &pl->lam, lam));
+    return MLC_OK;
+}
+
+mlc_status get_dgf(int device, int Q, int nD, int zeta, int L, const double **ptr, int *Lout) {
+    std::lock_guard<std::mutex> lk(g_dgf_mu);
+    auto key = std::make_tuple(device, Q, nD, zeta);
+    auto it = g_dgf.find(key);
+    if (it != g_dgf.end() && it->second.L >= L) {
+        *ptr = it->second.ptr;
+        *Lout = it->second.L;
+        return MLC_OK;
+    }
+    // build with some headroom so later plans reuse the table
+    int Lb = std::max(L, std::min(zeta * nD - 1, 128));
+    double *p = nullptr;
+    cudaError_t e = build_dgf_octant(Q, nD, zeta, Lb, &p);
+    if (e != cudaSuccess) return to_status(e);
+    g_dgf[key] = DgfEntry{p, Lb};  // an older, smaller table stays allocated for its plans
+    *ptr = p;
+    *Lout = Lb;
+    return MLC_OK;
+}
+
+void free_plan(mlc_plan_s *pl) {
+    if (!pl) return;
+    for (void *p : pl->owned) cudaFree(p);
+    for (auto &e : pl->ev)
+        if (e) cudaEventDestroy(e);
+    delete pl;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mlc_status_string(mlc_status s) {
+    switch (s) {
+        case MLC_OK: return "ok";
+        case MLC_ERR_INVALID_ARG: return "invalid argument";
+        case MLC_ERR_UNSUPPORTED: return "unsupported configuration";
+        case MLC_ERR_OOM: return "out of memory";
+        case MLC_ERR_CUDA: return "CUDA error";
+        case MLC_ERR_ADMISSION: return "request exceeds the memory budget";
+        case MLC_ERR_TIMEOUT: return "timed out";
+    }
+    return "unknown status";
+}
+
+mlc_status mlc_params_init(mlc_params *p, int N, int n, int s, int P, int Q) {
+    if (!p) return MLC_ERR_INVALID_ARG;
+    p->N = N; p->n = n; p->s = s; p->C = 4; p->P = P; p->Q = Q;
+    p->g_beta = -1; p->b = -1; p->tier = MLC_TIER_FP64; p->mode = MLC_MODE_MLC;
+    p->dgf_nD = -1; p->dgf_zeta = -1;
+    return MLC_OK;
+}
+
+mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
+    if (!params || !out) return MLC_ERR_INVALID_ARG;
+    *out = nullptr;
+    Geom g;
+    TRY(derive_geometry(*params, g));
+    if (g.tier != MLC_TIER_FP64 && g.tier != MLC_TIER_SPLIT) return MLC_ERR_INVALID_ARG;
+    if (g.tier == MLC_TIER_SPLIT) return MLC_ERR_UNSUPPORTED;
+    std::call_once(g_cfg_once, configure_kernels);
+    mlc_plan_s *pl = new (std::nothrow) mlc_plan_s();
+    if (!pl) return MLC_ERR_OOM;
+    pl->g = g;
+    pl->params = *params;
+    TRY_CUDA(cudaGetDevice(&pl->device));
+    // lag extent: local fields n + s, coarse Lc, basis fields (checked in build_tables)
+    Geom &G = pl->g;
+    G.L = std::max(G.n + G.s, G.Lc);
+    const int Lbasis_bound = G.n + G.gb + 4 * G.b + 12;
+    int Lneed = std::max(G.L, G.gb > G.ga ? Lbasis_bound : 0);
+    if (Lneed >= G.zeta * G.nD) G.nD = (Lneed + G.zeta) / G.zeta + 1;
+    mlc_status st = get_dgf(pl->device, G.Q, G.nD, G.zeta, Lneed, &pl->dgf, &pl->dgf_L);
+    if (st == MLC_OK) st = build_tables(pl);
+    auto alloc_all = [&]() -> mlc_status {
+        TRY(dev_alloc(pl, &pl->khat, (size_t)G.Mh * G.Mh * G.Mh, false));
+        TRY(dev_alloc(pl, &pl->khat_c, (size_t)G.Mhc * G.Mhc * G.Mhc, false));
+        TRY_CUDA(build_even_spectrum(pl->dgf, pl->dgf_L, G.M, std::min(G.n + G.s, G.M / 2),
+                                     G.h * G.h / ((double)G.M * G.M * G.M), pl->khat));
+        TRY_CUDA(build_even_spectrum(pl->dgf, pl->dgf_L, G.Mc, G.Lc,
+                                     G.H * G.H / ((double)G.Mc * G.Mc * G.Mc), pl->khat_c));
+        const size_t NP = G.NP, nb = G.nb, W = G.W, M = G.M, Mh = G.Mh;
+        const size_t A1 = NP * nb * nb * Mh, A2 = NP * nb * M * Mh, A3 = NP * W * M * Mh,
+                     A4 = NP * W * W * Mh;
+        TRY(dev_alloc(pl, &pl->buf0, std::max(A1, A3)));
+        TRY(dev_alloc(pl, &pl->buf1, std::max(A2, A4)));
+        TRY(dev_alloc(pl, &pl->box, NP * W * W * W));
+        TRY(dev_alloc(pl, &pl->mom, NP * G.npoly));
+        TRY(dev_alloc(pl, &pl->resid, NP * (size_t)G.na_face));
+        const size_t nf = G.nf, no = G.no, Mc = G.Mc, Mhc = G.Mhc;
+        TRY(dev_alloc(pl, &pl->FH, nf * nf * nf));
+        TRY(dev_alloc(pl, &pl->cbuf0, std::max(nf * nf * Mhc, no * Mc * Mhc)));
+        TRY(dev_alloc(pl, &pl->cbuf1, std::max(nf * Mc * Mhc, no * no * Mhc)));
+        TRY(dev_alloc(pl, &pl->phiH, no * no * no));
+        TRY(dev_alloc(pl, &pl->phiB, (size_t)G.n_planes_total));
+        return MLC_OK;
+    };
+    if (st == MLC_OK) st = alloc_all();
+    if (st == MLC_OK) st = to_status(cudaDeviceSynchronize());
+    if (st != MLC_OK) {
+        free_plan(pl);
+        return st;
+    }
+    *out = pl;
+    return MLC_OK;
+}
+
+mlc_status mlc_plan_create(int N, int patch, int support, int coarsening, int P, int Q,
+                           mlc_plan_t *out) {
+    mlc_params p;
+    mlc_params_init(&p, N, patch, support, P, Q);
+    p.C = coarsening;
+    return mlc_plan_create_ex(&p, out);
+}
+
+mlc_status mlc_plan_destroy(mlc_plan_t plan) {
+    if (!plan) return MLC_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    free_plan(plan);
+    return to_status(e);
+}
+
+mlc_status mlc_plan_workspace_bytes(mlc_plan_t plan, size_t *bytes) {
+    if (!plan || !bytes) return MLC_ERR_INVALID_ARG;
+    *bytes = plan->ws_bytes;
+    return MLC_OK;
+}
+
+mlc_status mlc_plan_info(mlc_plan_t plan, int *o) {
+    if (!plan || !o) return MLC_ERR_INVALID_ARG;
+    const Geom &g = plan->g;
+    const int v[16] = {g.N, g.n, g.s, g.b, g.ga, g.gb, g.P, g.npoly, g.flo, g.fhi,
+                       g.olo, g.ohi, g.M, g.Mc, plan->dgf_L, g.nD};
+    std::memcpy(o, v, sizeof(v));
+    return MLC_OK;
+}
+
+mlc_status mlc_solve(mlc_plan_t pl, const void *f, void *phi, void *stream) {
+    if (!pl || !f || !phi || f == phi) return MLC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool f32 = pl->g.tier == MLC_TIER_SPLIT;
+    mark(pl, 0, st);
+    TRY_CUDA(launch_moments(pl, f, f32, st));
+    TRY_CUDA(launch_patch_conv(pl, f, f32, st));   // slots 1-5
+    mark(pl, 6, st);
+    TRY_CUDA(launch_resid(pl, st));
+    mark(pl, 7, st);
+    TRY_CUDA(launch_assemble(pl, st));
+    TRY_CUDA(launch_coarse(pl, st));               // slots 8-12
+    mark(pl, 13, st);
+    TRY_CUDA(launch_boundary(pl, st));
+    mark(pl, 14, st);
+    TRY_CUDA(launch_dirichlet(pl, f, f32, (double *)phi, st));
+    mark(pl, 15, st);
+    return MLC_OK;
+}
+
+mlc_status mlc_solve_host(mlc_plan_t pl, const void *f_host, void *phi_host, void *stream) {
+    if (!pl || !f_host || !phi_host) return MLC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N3 = (size_t)pl->g.N * pl->g.N * pl->g.N;
+    const size_t fbytes = N3 * (pl->g.tier == MLC_TIER_SPLIT ? sizeof(float) : sizeof(double));
+    if (!pl->f_stage) {
+        char *fs = nullptr;
+        double *ps = nullptr;
+        TRY(dev_alloc(pl, &fs, fbytes));
+        TRY(dev_alloc(pl, &ps, N3));
+        pl->f_stage = fs;
+        pl->phi_stage = ps;
+    }
+    TRY_CUDA(cudaMemcpyAsync(pl->f_stage, f_host, fbytes, cudaMemcpyHostToDevice, st));
+    TRY(mlc_solve(pl, pl->f_stage, pl->phi_stage, stream));
+    TRY_CUDA(cudaMemcpyAsync(phi_host, pl->phi_stage, N3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TRY_CUDA(cudaStreamSynchronize(st));
+    return MLC_OK;
+}
+
+mlc_status mlc_batch_solve(int count, const mlc_plan_t *plans, const void *const *f,
+                           void *const *phi, void *stream) {
+    if (count < 0 || (count > 0 && (!plans || !f || !phi))) return MLC_ERR_INVALID_ARG;
+    for (int k = 0; k < count; ++k) TRY(mlc_solve(plans[k], f[k], phi[k], stream));
+    return MLC_OK;
+}
+
+mlc_status mlc_debug_set_timing(mlc_plan_t pl, int enable) {
+    if (!pl) return MLC_ERR_INVALID_ARG;
+    if (enable && !pl->ev[0])
+        for (auto &e : pl->ev) TRY_CUDA(cudaEventCreate(&e));
+    pl->timing = enable ? 1 : 0;
+    return MLC_OK;
+}
+
+mlc_status mlc_debug_timing(mlc_plan_t pl, float *ms, int count) {
+    if (!pl || !ms || count < kTimedLaunches || !pl->timing) return MLC_ERR_INVALID_ARG;
+    TRY_CUDA(cudaEventSynchronize(pl->ev[kTimedLaunches]));
+    for (int k = 0; k < kTimedLaunches; ++k)
+        TRY_CUDA(cudaEventElapsedTime(&ms[k], pl->ev[k], pl->ev[k + 1]));
+    return MLC_OK;
+}
+
+mlc_status mlc_debug_stage_bytes(mlc_plan_t pl, int stage, size_t *bytes) {
+    if (!pl || !bytes) return MLC_ERR_INVALID_ARG;
+    const Geom &g = pl->g;
+    switch (stage) {
+        case MLC_STAGE_MOMENTS: *bytes = (size_t)g.NP * g.npoly * 8; break;
+        case MLC_STAGE_FH: *bytes = (size_t)g.nf * g.nf * g.nf * 8; break;
+        case MLC_STAGE_PHIH: *bytes = (size_t)g.no * g.no * g.no * 8; break;
+        case MLC_STAGE_PHIB: *bytes = (size_t)g.n_planes_total * 8; break;
+        case MLC_STAGE_DGF: *bytes = (size_t)(pl->dgf_L + 1) * (pl->dgf_L + 1) * (pl->dgf_L + 1) * 8; break;
+        default: return MLC_ERR_INVALID_ARG;
+    }
+    return MLC_OK;
+}
+
+mlc_status mlc_debug_export(mlc_plan_t pl, int stage, void *host, size_t bytes) {
+    size_t need = 0;
+    TRY(mlc_debug_stage_bytes(pl, stage, &need));
+    if (!host || bytes != need) return MLC_ERR_INVALID_ARG;
+    const void *src = nullptr;
+    switch (stage) {
+        case MLC_STAGE_MOMENTS: src = pl->mom; break;
+        case MLC_STAGE_FH: src = pl->FH; break;
+        case MLC_STAGE_PHIH: src = pl->phiH; break;
+        case MLC_STAGE_PHIB: src = pl->phiB; break;
+        case MLC_STAGE_DGF: src = pl->dgf; break;
+        default: return MLC_ERR_INVALID_ARG;
+    }
+    TRY_CUDA(cudaDeviceSynchronize());
+    TRY_CUDA(cudaMemcpy(host, src, bytes, cudaMemcpyDeviceToHost));
+    return MLC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,250 @@
+"""Python binding of the C ABI in include/mlc.h (argument marshalling only).
+
+Every step of a solve runs in the CUDA library ``_lib/libmlc_gb300.so``; this
+module only checks tensors, passes raw device pointers and turns status codes
+into exceptions.  PyTorch provides device memory and streams.  There is no
+CPU fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libmlc_gb300.so")
+
+MLC_TIER_FP64, MLC_TIER_SPLIT = 0, 1
+MLC_MODE_MLC, MLC_MODE_MLC0 = 0, 1
+STAGE_MOMENTS, STAGE_FH, STAGE_PHIH, STAGE_PHIB, STAGE_DGF = 0, 1, 2, 3, 4
+
+EXPORTED = [
+    "mlc_params_init", "mlc_plan_create", "mlc_plan_create_ex", "mlc_plan_destroy",
+    "mlc_plan_workspace_bytes", "mlc_solve", "mlc_solve_host", "mlc_batch_solve",
+    "mlc_debug_stage_bytes", "mlc_debug_export", "mlc_plan_info", "mlc_server_create",
+    "mlc_server_destroy", "mlc_server_enqueue", "mlc_server_wait", "mlc_status_string",
+    "mlc_debug_set_timing", "mlc_debug_timing",
+]
+LAUNCH_NAMES = ["moments", "conv_fwd_x", "conv_fwd_y", "conv_z_kernel", "conv_inv_y", "conv_inv_x",
+                "resid", "assemble", "coarse_fwd_x", "coarse_fwd_y", "coarse_z_kernel",
+                "coarse_inv_y", "coarse_inv_x", "boundary", "dirichlet"]
+
+
+class MLCError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+        self.status = status
+
+
+class mlc_params(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int) for k in
+                ("N", "n", "s", "C", "P", "Q", "g_beta", "b", "tier", "mode", "dgf_nD", "dgf_zeta")]
+
+
+class mlc_request(ctypes.Structure):
+    _fields_ = [("params", mlc_params), ("f", ctypes.c_void_p), ("phi", ctypes.c_void_p)]
+
+
+class mlc_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the CUDA library (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    from . import build as _build
+    if _build.needs_build():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"MLC CUDA library not found at {path}")
+    lib = ctypes.CDLL(path)
+    vp, ip, i = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int
+    lib.mlc_params_init.argtypes = [ctypes.POINTER(mlc_params), i, i, i, i, i]
+    lib.mlc_plan_create.argtypes = [i, i, i, i, i, i, ctypes.POINTER(vp)]
+    lib.mlc_plan_create_ex.argtypes = [ctypes.POINTER(mlc_params), ctypes.POINTER(vp)]
+    lib.mlc_plan_destroy.argtypes = [vp]
+    lib.mlc_plan_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    lib.mlc_solve.argtypes = [vp, vp, vp, vp]
+    lib.mlc_solve_host.argtypes = [vp, vp, vp, vp]
+    lib.mlc_batch_solve.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    lib.mlc_debug_stage_bytes.argtypes = [vp, i, ctypes.POINTER(ctypes.c_size_t)]
+    lib.mlc_debug_export.argtypes = [vp, i, vp, ctypes.c_size_t]
+    lib.mlc_plan_info.argtypes = [vp, ip]
+    lib.mlc_server_create.argtypes = [ctypes.c_size_t, i, ctypes.POINTER(vp)]
+    lib.mlc_server_destroy.argtypes = [vp]
+    lib.mlc_server_enqueue.argtypes = [vp, ctypes.POINTER(mlc_request), ctypes.POINTER(ctypes.c_uint64)]
+    lib.mlc_server_wait.argtypes = [vp, ctypes.c_uint64, i, ctypes.POINTER(mlc_result)]
+    lib.mlc_debug_set_timing.argtypes = [vp, i]
+    lib.mlc_debug_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i]
+    lib.mlc_status_string.argtypes = [i]
+    lib.mlc_status_string.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name != "mlc_status_string":
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def status_string(s: int) -> str:
+    try:
+        return load_library().mlc_status_string(int(s)).decode()
+    except Exception:
+        return "unknown"
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise MLCError(rc, what)
+
+
+def make_params(N, n, s, P=4, Q=4, C=4, g_beta=-1, b=-1, tier=MLC_TIER_FP64, mode=MLC_MODE_MLC,
+                dgf_nD=-1, dgf_zeta=-1) -> mlc_params:
+    p = mlc_params()
+    load_library().mlc_params_init(ctypes.byref(p), N, n, s, P, Q)
+    p.C, p.g_beta, p.b, p.tier, p.mode, p.dgf_nD, p.dgf_zeta = C, g_beta, b, tier, mode, dgf_nD, dgf_zeta
+    return p
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+@dataclass
+class PlanInfo:
+    N: int
+    n: int
+    s: int
+    b: int
+    g_alpha: int
+    g_beta: int
+    P: int
+    npoly: int
+    fh_lo: int
+    fh_hi: int
+    phih_lo: int
+    phih_hi: int
+    M: int
+    Mc: int
+    L: int
+    nD: int
+
+
+class Plan:
+    """A solver plan (mlc_plan_create_ex); owns device tables and workspace."""
+
+    def __init__(self, N, n, s, P=4, Q=4, **kw):
+        lib = load_library()
+        self.params = make_params(N, n, s, P, Q, **kw)
+        h = ctypes.c_void_p()
+        _check(lib.mlc_plan_create_ex(ctypes.byref(self.params), ctypes.byref(h)), "mlc_plan_create_ex")
+        self._h = h
+        arr = (ctypes.c_int * 16)()
+        _check(lib.mlc_plan_info(self._h, arr), "mlc_plan_info")
+        self.info = PlanInfo(*list(arr))
+        self.tier = self.params.tier
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().mlc_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_bytes(self) -> int:
+        v = ctypes.c_size_t()
+        _check(load_library().mlc_plan_workspace_bytes(self._h, ctypes.byref(v)), "workspace")
+        return v.value
+
+    def _check_tensors(self, f, phi):
+        import torch
+        N = self.params.N
+        want = torch.float32 if self.tier == MLC_TIER_SPLIT else torch.float64
+        if not (f.is_cuda and phi.is_cuda):
+            raise ValueError("f and phi must be CUDA tensors")
+        if f.dtype != want or phi.dtype != torch.float64:
+            raise ValueError(f"f must be {want}, phi float64")
+        if tuple(f.shape) != (N, N, N) or tuple(phi.shape) != (N, N, N):
+            raise ValueError(f"f and phi must have shape ({N},{N},{N})")
+        if not (f.is_contiguous() and phi.is_contiguous()):
+            raise ValueError("f and phi must be contiguous")
+
+    def solve(self, f, phi=None, stream=None):
+        """Enqueue a solve on `stream` (default: torch's current stream)."""
+        import torch
+        if phi is None:
+            phi = torch.empty((self.params.N,) * 3, dtype=torch.float64, device=f.device)
+        self._check_tensors(f, phi)
+        _check(load_library().mlc_solve(self._h, ctypes.c_void_p(f.data_ptr()),
+                                        ctypes.c_void_p(phi.data_ptr()),
+                                        ctypes.c_void_p(_stream_handle(stream))), "mlc_solve")
+        return phi
+
+    def solve_host(self, f_host, phi_host, stream=None):
+        """Host arrays in, host array out (copies inside the call); synchronises."""
+        _check(load_library().mlc_solve_host(self._h, ctypes.c_void_p(f_host.data_ptr()),
+                                             ctypes.c_void_p(phi_host.data_ptr()),
+                                             ctypes.c_void_p(_stream_handle(stream))), "mlc_solve_host")
+        return phi_host
+
+    def set_timing(self, enable: bool = True):
+        _check(load_library().mlc_debug_set_timing(self._h, int(enable)), "set_timing")
+
+    def timing(self):
+        """Per-launch durations (ms) of the last solve, keyed by LAUNCH_NAMES."""
+        arr = (ctypes.c_float * len(LAUNCH_NAMES))()
+        _check(load_library().mlc_debug_timing(self._h, arr, len(LAUNCH_NAMES)), "timing")
+        return dict(zip(LAUNCH_NAMES, list(arr)))
+
+    def export(self, stage: int):
+        import numpy as np
+        lib = load_library()
+        nb = ctypes.c_size_t()
+        _check(lib.mlc_debug_stage_bytes(self._h, stage, ctypes.byref(nb)), "stage bytes")
+        out = np.empty(nb.value // 8, dtype=np.float64)
+        _check(lib.mlc_debug_export(self._h, stage, ctypes.c_void_p(out.ctypes.data), nb.value), "export")
+        i = self.info
+        if stage == STAGE_MOMENTS:
+            return out.reshape(-1, i.npoly)
+        if stage == STAGE_FH:
+            m = i.fh_hi - i.fh_lo + 1
+            return out.reshape(m, m, m)
+        if stage == STAGE_PHIH:
+            m = i.phih_hi - i.phih_lo + 1
+            return out.reshape(m, m, m)
+        if stage == STAGE_PHIB:
+            npl = i.N // i.n + 1
+            return out.reshape(3, npl, i.N + 1, i.N + 1)
+        if stage == STAGE_DGF:
+            m = i.L + 1
+            return out.reshape(m, m, m)
+        return out
+
+
+def batch_solve(plans, fs, phis, stream=None):
+    lib = load_library()
+    k = len(plans)
+    H = (ctypes.c_void_p * k)(*[p.handle.value for p in plans])
+    F = (ctypes.c_void_p * k)(*[f.data_ptr() for f in fs])
+    P = (ctypes.c_void_p * k)(*[p.data_ptr() for p in phis])
+    for p, f, ph in zip(plans, fs, phis):
+        p._check_tensors(f, ph)
+    _check(lib.mlc_batch_solve(k, H, F, P, ctypes.c_void_p(_stream_handle(stream))), "mlc_batch_solve")
+    return phis

@@ -1,0 +1,178 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle.
+
+FP64 tier bar: relative max-norm difference <= 1e-12 per stage and for the
+final potential (the tolerance stated for the FP64 path).  Both sides build
+their own DGF for the same (Q, nD = 128, zeta = 2); the tables are compared
+first.
+"""
+import numpy as np
+import pytest
+
+from oracle import mlc_oracle as O
+from paper_1702_08111_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+def relmax(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    assert torch.cuda.is_available()
+    return torch
+
+
+def _phiB_from_planes(planes, nodes, n):
+    out = np.empty(len(nodes))
+    for a, g in enumerate(nodes):
+        for d in range(3):
+            if g[d] % n == 0:
+                u, v = [g[e] for e in range(3) if e != d]
+                out[a] = planes[d, g[d] // n, u, v]
+                break
+    return out
+
+
+def _check_plane_duplicates(planes, N, n):
+    # a node on several face planes must carry one value (computed from g alone)
+    np_ = N // n
+    for j0 in range(np_ + 1):
+        for j1 in range(np_ + 1):
+            # edge along axis 2: g0 = j0 n, g1 = j1 n
+            a = planes[0, j0, j1 * n, :]
+            b = planes[1, j1, j0 * n, :]
+            assert np.array_equal(a, b)
+
+
+def _run(torch, prm_kw, f_open, stages=True, **plan_kw):
+    from paper_1702_08111_gb300 import mlc
+    plan = mlc.Plan(**prm_kw, **plan_kw)
+    f = torch.from_numpy(f_open).cuda()
+    phi = plan.solve(f)
+    torch.cuda.synchronize()
+    res = {"phi": phi.cpu().numpy()}
+    if stages:
+        res["moments"] = plan.export(mlc.STAGE_MOMENTS)
+        res["FH"] = plan.export(mlc.STAGE_FH)
+        res["phiH"] = plan.export(mlc.STAGE_PHIH)
+        res["phiB"] = plan.export(mlc.STAGE_PHIB)
+    res["plan"] = plan
+    return res
+
+
+def _compare(res, prm, f_open, G1):
+    st = {}
+    phi_o = O.solve_open(prm, f_open, G1=G1, stages=st)
+    assert relmax(res["moments"], st["moments"]) <= TOL
+    assert relmax(res["FH"], st["FH"]) <= TOL
+    assert relmax(res["phiH"], st["phiH"]) <= TOL
+    pb = _phiB_from_planes(res["phiB"], st["face_nodes"], prm.n)
+    assert relmax(pb, st["phiB"]) <= TOL
+    _check_plane_duplicates(res["phiB"], prm.N, prm.n)
+    err = relmax(res["phi"], phi_o)
+    assert err <= TOL, err
+    return err
+
+
+@pytest.fixture(scope="module")
+def G4():
+    return O.dgf_octant(4, 128, 2)
+
+
+@pytest.fixture(scope="module")
+def G6():
+    return O.dgf_octant(6, 128, 2)
+
+
+@pytest.mark.parametrize("Q", [4, 6])
+def test_dgf_table_matches_oracle(torch_cuda, Q, G4, G6):
+    from paper_1702_08111_gb300 import mlc
+    plan = mlc.Plan(32, 8, 12, 4, Q, b=2)
+    T = plan.export(mlc.STAGE_DGF)
+    G = G4 if Q == 4 else G6
+    L = min(T.shape[0], G.shape[0])
+    assert relmax(T[:L, :L, :L], G[:L, :L, :L]) <= 1e-13
+
+
+def test_single_bump_32(torch_cuda, G4):
+    w = I.workload("single_bump_32")
+    f = w.charge()
+    res = _run(torch_cuda, dict(N=32, n=8, s=8, P=4, Q=4), f)
+    _compare(res, O.Params(N=32, n=8, s=8, Q=4), f, G4)
+
+
+def test_bumps8_128(torch_cuda, G4):
+    w = I.workload("bumps8_128")
+    f = w.charge()
+    res = _run(torch_cuda, dict(N=128, n=16, s=16, P=4, Q=4), f)
+    _compare(res, O.Params(N=128, n=16, s=16, Q=4), f, G4)
+
+
+def test_q6_reduced_64(torch_cuda, G6):
+    w = I.workload("bumps8_64_q6")
+    f = w.charge()
+    res = _run(torch_cuda, dict(N=64, n=16, s=16, P=4, Q=6), f)
+    _compare(res, O.Params(N=64, n=16, s=16, Q=6), f, G6)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(N=48, n=16, s=16, P=4, Q=4),            # odd patch count per axis
+    dict(N=32, n=8, s=12, P=1, Q=4),             # monopole-only ring (P = 1)
+    dict(N=32, n=8, s=16, P=4, Q=4, mode=1),     # MLC-0 (no ring)
+    dict(N=40, n=8, s=12, P=3, Q=6, b=2),        # 27-point, b = 2, P = 3
+])
+def test_variants(torch_cuda, G4, G6, kw):
+    kw = dict(kw)
+    N = kw["N"]
+    f = I.sample_bumps(N, I.draw_bumps(5, 100 + N))
+    mode = kw.pop("mode", 0)
+    b = kw.get("b", None)
+    res = _run(torch_cuda, kw, f, mode=mode)
+    prm = O.Params(N=N, n=kw["n"], s=kw["s"], P=kw["P"], Q=kw["Q"], b=b,
+                   mode="mlc0" if mode else "mlc")
+    _compare(res, prm, f, G4 if kw["Q"] == 4 else G6)
+
+
+def test_zero_charge_gives_zero(torch_cuda):
+    from paper_1702_08111_gb300 import mlc
+    torch = torch_cuda
+    plan = mlc.Plan(32, 8, 8, 4, 4)
+    f = torch.zeros((32, 32, 32), dtype=torch.float64, device="cuda")
+    phi = plan.solve(f)
+    torch.cuda.synchronize()
+    assert float(phi.abs().max()) == 0.0
+
+
+def test_repeat_and_host_path_identical(torch_cuda):
+    from paper_1702_08111_gb300 import mlc
+    torch = torch_cuda
+    w = I.workload("single_bump_32")
+    f = torch.from_numpy(w.charge()).cuda()
+    plan = mlc.Plan(32, 8, 8, 4, 4)
+    a = plan.solve(f).clone()
+    b = plan.solve(f).clone()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    fh = f.cpu().pin_memory()
+    ph = torch.empty((32, 32, 32), dtype=torch.float64).pin_memory()
+    plan.solve_host(fh, ph)
+    assert torch.equal(ph, a.cpu())
+
+
+def test_invalid_arguments(torch_cuda):
+    from paper_1702_08111_gb300 import mlc
+    for kw in [dict(N=30, n=8, s=8), dict(N=32, n=6, s=8), dict(N=32, n=8, s=4),
+               dict(N=32, n=8, s=8, Q=5), dict(N=32, n=8, s=8, C=2)]:
+        with pytest.raises(mlc.MLCError) as e:
+            mlc.Plan(**kw)
+        assert e.value.status == 1
+    with pytest.raises(mlc.MLCError) as e:
+        mlc.Plan(N=32, n=32, s=32)
+    assert e.value.status == 2
