@@ -93,6 +93,57 @@ def conv_pass_flops(M: int, lines: int, passes: int = 1) -> float:
     return lines * passes * 5.0 * M * np.log2(M)
 
 
+def time_plan(plan, f, phi, steps, warmup, flush, stream, world):
+    """Mean device time per solve (CUDA events on the launching stream, L2
+    flushed between steps outside the timed region) and per-launch means."""
+    import torch
+    for _ in range(warmup):
+        plan.solve(f, phi, stream)
+        flush.zero_()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    plan.set_timing(True)
+    per_launch, total_ms = {}, 0.0
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(steps):
+        ev0.record(stream)
+        plan.solve(f, phi, stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+        for k, v in plan.timing().items():
+            per_launch[k] = per_launch.get(k, 0.0) + v
+        flush.zero_()
+    torch.cuda.synchronize()
+    plan.set_timing(False)
+    return total_ms / steps, {k: v / steps for k, v in per_launch.items()}
+
+
+def roofline_for(w, plan, per_launch, tier):
+    info = plan.info
+    N = w.N
+    M, Mh, NP, W = info.M, info.M // 2 + 1, (N // w.n) ** 3, w.n + 2 * w.s + 1
+    flops = {
+        "conv_z_kernel": conv_pass_flops(M, NP * M * Mh, 2) + NP * M * M * Mh * 2.0,
+        "conv_inv_y": conv_pass_flops(M, NP * W * Mh),
+        "conv_inv_x": conv_pass_flops(M, NP * W * W),
+        "conv_fwd_y": conv_pass_flops(M, NP * (w.n + 1) * Mh),
+    }
+    dom = max(per_launch, key=per_launch.get)
+    if dom not in flops:
+        return None
+    achieved = flops[dom] / (per_launch[dom] * 1e-3) / 1e9
+    if tier == "fp64":
+        peak, unit = 1190.0, "GFLOP/s (FP64)"
+    else:
+        peak, unit = 69900.0, "GFLOP/s (FP32)"
+    return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": unit,
+            "frac": round(achieved / peak, 4), "traffic": None, "launch_ms": round(per_launch[dom], 4),
+            "flops_per_launch": flops[dom]}
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_1702_08111_gb300 import mlc
@@ -101,47 +152,19 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda")
     w = I.workload(args.workload)
     N = w.N
-    plan = mlc.Plan(N, w.n, w.s, w.P, w.Q)
+    tier = "split" if w.charge_dtype == "f32" else "fp64"
+    plan = mlc.Plan(N, w.n, w.s, w.P, w.Q, tier=mlc.MLC_TIER_SPLIT if tier == "split" else mlc.MLC_TIER_FP64)
     f_host = torch.from_numpy(w.charge())
     f = f_host.to(dev)
     phi = torch.empty((N, N, N), dtype=torch.float64, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-
-    for _ in range(args.warmup):
-        plan.solve(f, phi)
-        flush.zero_()
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    plan.set_timing(True)
-    per_launch = {}
-    total_ms = 0.0
-    smi_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or 0) if False else int(
-        os.environ.get("LOCAL_RANK", 0))
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(smi_index) as clk:
-        torch.cuda.synchronize()
-        for _ in range(args.steps):
-            ev0.record(stream)
-            plan.solve(f, phi, stream)
-            ev1.record(stream)
-            ev1.synchronize()
-            total_ms += ev0.elapsed_time(ev1)
-            for k, v in plan.timing().items():
-                per_launch[k] = per_launch.get(k, 0.0) + v
-            flush.zero_()
-        torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    plan.set_timing(False)
-    ms = total_ms / args.steps
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clk:
+        ms, per_launch = time_plan(plan, f, phi, args.steps, args.warmup, flush, stream, world)
     if world > 1:
         t = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
-    per_launch = {k: v / args.steps for k, v in per_launch.items()}
 
     # end to end through the C ABI with host buffers (copies inside the call)
     f_pin = f_host.pin_memory()
@@ -155,29 +178,45 @@ def run_ours(args, rank, world):
         plan.solve_host(f_pin, phi_pin)
         e2e_ms += (time.perf_counter() - t0) * 1e3
     e2e_ms /= args.steps
-
-    pts = float(N) ** 3
-    value = world * pts / (ms * 1e-3) / 1e6
-    info = plan.info
-    M, Mh, NP = info.M, info.M // 2 + 1, (N // w.n) ** 3
-    # dominant launch: the fused z pass (forward FFT, kernel multiply, inverse FFT)
-    dom = max(per_launch, key=per_launch.get)
-    flops = {
-        "conv_z_kernel": conv_pass_flops(M, NP * M * Mh, 2) + NP * M * M * Mh * 2.0,
-        "conv_inv_y": conv_pass_flops(M, NP * (w.s * 2 + w.n + 1) * Mh),
-        "conv_inv_x": conv_pass_flops(M, NP * (w.s * 2 + w.n + 1) ** 2),
-        "conv_fwd_y": conv_pass_flops(M, NP * (w.n + 1) * Mh),
-    }
-    roof = None
-    if dom in flops:
-        achieved = flops[dom] / (per_launch[dom] * 1e-3) / 1e9
-        peak = 1250.0  # FP64 nominal GFLOP/s (152 SMs x 2.07 GHz x 4 FP64 flop/clk/SM)
-        roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GFLOP/s (FP64)", "frac": round(achieved / peak, 4), "traffic": None,
-                "launch_ms": round(per_launch[dom], 4)}
-    res = {"value": value, "ms": ms, "e2e_ms": e2e_ms, "per_launch": per_launch, "roofline": roof,
-           "clocks": clk.summary(), "phi": phi, "N": N, "plan": plan}
+    value = world * float(N) ** 3 / (ms * 1e-3) / 1e6
+    res = {"value": value, "ms": ms, "e2e_ms": e2e_ms, "per_launch": per_launch,
+           "roofline": roofline_for(w, plan, per_launch, tier), "clocks": clk.summary(),
+           "phi": phi, "N": N, "tier": tier, "f_bytes": f_host.element_size() * N ** 3}
+    del plan
+    if args.extra and rank == 0:
+        res["extra"] = run_extra(args, flush, stream)
     return res
+
+
+def run_extra(args, flush, stream):
+    """Secondary lines: the 256^3 Q=6 workload in the split and FP64 tiers."""
+    import torch
+    from paper_1702_08111_gb300 import mlc
+    from oracle import closed_forms as CF
+    w = I.workload("bumps32_256_q6")
+    N = w.N
+    f32 = torch.from_numpy(w.charge()).cuda()
+    f64 = f32.double()
+    out = {}
+    phis = {}
+    for tier, f in (("split", f32), ("fp64", f64)):
+        plan = mlc.Plan(N, w.n, w.s, w.P, w.Q, tier=mlc.MLC_TIER_SPLIT if tier == "split" else mlc.MLC_TIER_FP64)
+        phi = torch.empty((N, N, N), dtype=torch.float64, device="cuda")
+        steps = max(3, args.steps // 2)
+        ms, pl = time_plan(plan, f, phi, steps, 3, flush, stream, 1)
+        phis[tier] = phi.cpu().numpy()
+        out[tier] = {"workload": "bumps32_256_q6", "tier": tier, "ms_per_step": round(ms, 3),
+                     "value": round(float(N) ** 3 / (ms * 1e-3) / 1e6, 2), "unit": "Mpoints/s",
+                     "roofline": roofline_for(w, plan, pl, tier),
+                     "per_launch_ms": {k: round(v, 4) for k, v in pl.items()}}
+        del plan
+    ex = CF.bumps_potential(N, w.bumps)
+    d = np.abs(phis["split"] - phis["fp64"]).max() / np.abs(phis["fp64"]).max()
+    out["split"]["max_rel_err_vs_fp64_gpu"] = float(d)
+    out["fp64"]["max_rel_err_vs_closed_form"] = float(np.abs(phis["fp64"] - ex).max() / np.abs(ex).max())
+    out["split"]["max_rel_err_vs_closed_form"] = float(np.abs(phis["split"] - ex).max() / np.abs(ex).max())
+    out["split_over_fp64_speedup"] = round(out["fp64"]["ms_per_step"] / out["split"]["ms_per_step"], 3)
+    return out
 
 
 def cpu_oracle_solve(w, nodes_sample=None):
@@ -198,6 +237,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", dest="extra", action="store_false")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -217,7 +257,7 @@ def main():
     if rank == 0:
         cpu = None
         err = None
-        if not args.no_cpu_baseline and world == 1 or (rank == 0 and not args.no_cpu_baseline):
+        if not args.no_cpu_baseline and world == 1:
             phi_o, t = cpu_oracle_solve(w)
             got = r["phi"].cpu().numpy()
             err = float(np.abs(got - phi_o).max() / np.abs(phi_o).max())
@@ -237,11 +277,13 @@ def main():
                        "parallelism": f"independent problem per GPU x{world}"},
             "max_rel_err_vs_oracle": err,
             "e2e": {"value": round(e2e_val, 3), "unit": "Mpoints/s",
-                    "h2d_bytes_per_step": int(N ** 3 * 8), "d2h_bytes_per_step": int(N ** 3 * 8)},
+                    "h2d_bytes_per_step": int(r["f_bytes"]), "d2h_bytes_per_step": int(N ** 3 * 8)},
             "gpu_launches": launches * args.steps,
             "roofline": r["roofline"], "cpu_baseline": cpu, "clocks": r["clocks"],
             "per_launch_ms": {k: round(v, 4) for k, v in r["per_launch"].items()},
         }
+        if "extra" in r:
+            line["extra"] = r["extra"]
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch

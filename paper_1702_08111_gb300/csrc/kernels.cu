@@ -29,14 +29,30 @@ __device__ __forceinline__ int floordiv(int a, int b) {  // b > 0
     return a >= 0 ? a / b : -((-a + b - 1) / b);
 }
 
+// Complex type of each working precision (FP64 tier: double; split tier: float).
+template <typename R> struct Cx;
+template <> struct Cx<double> {
+    using T = double2;
+    static __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+};
+template <> struct Cx<float> {
+    using T = float2;
+    static __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+};
+
 __device__ __forceinline__ double2 cmul(double2 a, double2 w) {
     return make_double2(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x));
 }
+__device__ __forceinline__ float2 cmul(float2 a, float2 w) {
+    return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
 
 // Decimation in frequency: natural-order input, bit-reversed output.
-template <int LOG2M>
-__device__ __forceinline__ void fft_dif(double2 *buf, int nlines, int lstride, int estride,
-                                        const double2 *tw, bool inv) {
+template <int LOG2M, typename C>
+__device__ __forceinline__ void fft_dif(C *buf, int nlines, int lstride, int estride,
+                                        const C *tw, bool inv) {
     constexpr int MH = 1 << (LOG2M - 1);
     const int total = nlines * MH;
 #pragma unroll 1
@@ -47,22 +63,22 @@ __device__ __forceinline__ void fft_dif(double2 *buf, int nlines, int lstride, i
             const int line = j % nlines, bf = j / nlines;
             const int grp = bf >> st, pos = bf & (hs - 1);
             const int i0 = (grp << (st + 1)) + pos;
-            double2 *p0 = buf + line * lstride + i0 * estride;
-            double2 *p1 = p0 + hs * estride;
-            double2 w = tw[pos << tsh];
+            C *p0 = buf + line * lstride + i0 * estride;
+            C *p1 = p0 + hs * estride;
+            C w = tw[pos << tsh];
             if (inv) w.y = -w.y;
-            const double2 a = *p0, b = *p1;
-            *p0 = make_double2(a.x + b.x, a.y + b.y);
-            *p1 = cmul(make_double2(a.x - b.x, a.y - b.y), w);
+            const C a = *p0, b = *p1;
+            *p0 = cadd(a, b);
+            *p1 = cmul(csub(a, b), w);
         }
         __syncthreads();
     }
 }
 
 // Decimation in time: bit-reversed input, natural-order output.
-template <int LOG2M>
-__device__ __forceinline__ void fft_dit(double2 *buf, int nlines, int lstride, int estride,
-                                        const double2 *tw, bool inv) {
+template <int LOG2M, typename C>
+__device__ __forceinline__ void fft_dit(C *buf, int nlines, int lstride, int estride,
+                                        const C *tw, bool inv) {
     constexpr int MH = 1 << (LOG2M - 1);
     const int total = nlines * MH;
 #pragma unroll 1
@@ -73,21 +89,21 @@ __device__ __forceinline__ void fft_dit(double2 *buf, int nlines, int lstride, i
             const int line = j % nlines, bf = j / nlines;
             const int grp = bf >> st, pos = bf & (hs - 1);
             const int i0 = (grp << (st + 1)) + pos;
-            double2 *p0 = buf + line * lstride + i0 * estride;
-            double2 *p1 = p0 + hs * estride;
-            double2 w = tw[pos << tsh];
+            C *p0 = buf + line * lstride + i0 * estride;
+            C *p1 = p0 + hs * estride;
+            C w = tw[pos << tsh];
             if (inv) w.y = -w.y;
-            const double2 a = *p0;
-            const double2 t = cmul(*p1, w);
-            *p0 = make_double2(a.x + t.x, a.y + t.y);
-            *p1 = make_double2(a.x - t.x, a.y - t.y);
+            const C a = *p0;
+            const C t = cmul(*p1, w);
+            *p0 = cadd(a, t);
+            *p1 = csub(a, t);
         }
         __syncthreads();
     }
 }
 
-template <int LOG2M>
-__device__ __forceinline__ void load_twiddles(double2 *s_tw, const double2 *tw) {
+template <int LOG2M, typename C>
+__device__ __forceinline__ void load_twiddles(C *s_tw, const C *tw) {
     for (int t = threadIdx.x; t < (1 << (LOG2M - 1)); t += blockDim.x) s_tw[t] = tw[t];
 }
 
@@ -98,52 +114,54 @@ __device__ __forceinline__ void load_twiddles(double2 *s_tw, const double2 *tw) 
 // ---------------------------------------------------------------------------
 struct FwdXArgs {
     const void *src;
-    double2 *out;
+    void *out;        // complex R: [slab][line][M/2+1]
     int N, n, np;     // patch geometry (PATCH)
     int nin;          // input nodes per axis
     int lines_cta;    // lines per CTA
-    const double2 *tw;
+    const void *tw;   // complex R twiddles
 };
 
-template <int LOG2M, typename TF, bool PATCH>
+template <int LOG2M, typename TF, bool PATCH, typename R>
 __global__ void __launch_bounds__(256) k_fwd_x(FwdXArgs a) {
+    using C = typename Cx<R>::T;
     constexpr int M = 1 << LOG2M, MH = M / 2 + 1, LS = M + 1;
-    extern __shared__ double2 smem[];
-    double2 *s_tw = smem;
-    double2 *buf = smem + M / 2;
-    const int slab = blockIdx.y;  // p * nin + zi
-    const int line0 = blockIdx.x * a.lines_cta;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *s_tw = (C *)smem_raw;
+    C *buf = s_tw + M / 2;
+    const int slab = blockIdx.x;  // p * nin + zi
+    const int line0 = blockIdx.y * a.lines_cta;
     const int nl = min(a.lines_cta, a.nin - line0);
-    load_twiddles<LOG2M>(s_tw, a.tw);
-    for (int e = threadIdx.x; e < nl * LS; e += blockDim.x) buf[e] = make_double2(0.0, 0.0);
+    load_twiddles<LOG2M>(s_tw, (const C *)a.tw);
+    for (int e = threadIdx.x; e < nl * LS; e += blockDim.x) buf[e] = Cx<R>::mk(0, 0);
     __syncthreads();
     const int zi = slab % a.nin, p = slab / a.nin;
     for (int e = threadIdx.x; e < nl * a.nin; e += blockDim.x) {
         const int l = e / a.nin, m = e % a.nin;
         const int yi = line0 + l;
-        double v;
+        R v;
         if (PATCH) {
             const int i2 = p % a.np, i1 = (p / a.np) % a.np, i0 = p / (a.np * a.np);
             const int z = i0 * a.n + zi, y = i1 * a.n + yi, x = i2 * a.n + m;
-            v = 0.0;
+            v = 0;
             if (z < a.N && y < a.N && x < a.N) {
                 const TF *f = (const TF *)a.src;
-                double w = (zi == 0 || zi == a.n) ? 0.5 : 1.0;
-                w *= (yi == 0 || yi == a.n) ? 0.5 : 1.0;
-                w *= (m == 0 || m == a.n) ? 0.5 : 1.0;
-                v = w * (double)f[((long)z * a.N + y) * a.N + x];
+                R w = (zi == 0 || zi == a.n) ? R(0.5) : R(1);
+                w *= (yi == 0 || yi == a.n) ? R(0.5) : R(1);
+                w *= (m == 0 || m == a.n) ? R(0.5) : R(1);
+                v = w * (R)f[((long)z * a.N + y) * a.N + x];
             }
         } else {
             const double *F = (const double *)a.src;
-            v = F[((long)zi * a.nin + yi) * a.nin + m];
+            v = (R)F[((long)zi * a.nin + yi) * a.nin + m];
         }
-        buf[l * LS + m] = make_double2(v, 0.0);
+        buf[l * LS + m] = Cx<R>::mk(v, 0);
     }
     __syncthreads();
     fft_dif<LOG2M>(buf, nl, LS, 1, s_tw, false);
+    C *out = (C *)a.out;
     for (int e = threadIdx.x; e < nl * MH; e += blockDim.x) {
         const int l = e / MH, kx = e % MH;
-        a.out[((long)slab * a.nin + line0 + l) * MH + kx] = buf[l * LS + brev_bits(kx, LOG2M)];
+        out[((long)slab * a.nin + line0 + l) * MH + kx] = buf[l * LS + brev_bits(kx, LOG2M)];
     }
 }
 
@@ -153,33 +171,34 @@ __global__ void __launch_bounds__(256) k_fwd_x(FwdXArgs a) {
 //   MODE 1: inverse; all M rows in; rows t < nout out from positions
 //           (out_off + t) mod M.
 //   MODE 2: forward, multiply by the real-even kernel spectrum, inverse.
-// slab = blockIdx.y = p * S2 + q.
+// slab = blockIdx.x = p * S2 + q; blockIdx.y = column chunk.
 // ---------------------------------------------------------------------------
 struct ColArgs {
-    const double2 *in;
-    double2 *out;
+    const void *in;
+    void *out;
     int S2;
     long in_sp, in_sq, in_row, out_sp, out_sq, out_row;
     int ncols, cols_cta, nin, nout, out_off;
-    const double *khat;  // MODE 2: octant (M/2+1)^3, index (kx, ky = q, kz = row)
-    const double2 *tw;
+    const void *khat;  // MODE 2: real R octant (M/2+1)^3, index (kx, ky = q, kz = row)
+    const void *tw;
 };
 
-template <int LOG2M, int MODE>
+template <int LOG2M, int MODE, typename R>
 __global__ void __launch_bounds__(256) k_col(ColArgs a) {
+    using C = typename Cx<R>::T;
     constexpr int M = 1 << LOG2M, MH = M / 2 + 1;
-    extern __shared__ double2 smem[];
-    double2 *s_tw = smem;
-    double2 *buf = smem + M / 2;
-    const int slab = blockIdx.y;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *s_tw = (C *)smem_raw;
+    C *buf = s_tw + M / 2;
+    const int slab = blockIdx.x;
     const int p = slab / a.S2, q = slab % a.S2;
-    const int c0 = blockIdx.x * a.cols_cta;
+    const int c0 = blockIdx.y * a.cols_cta;
     const int nc = min(a.cols_cta, a.ncols - c0);
     const int CC = a.cols_cta;  // row stride in shared memory
-    load_twiddles<LOG2M>(s_tw, a.tw);
-    const double2 *in = a.in + p * a.in_sp + q * a.in_sq + c0;
+    load_twiddles<LOG2M>(s_tw, (const C *)a.tw);
+    const C *in = (const C *)a.in + p * a.in_sp + q * a.in_sq + c0;
     if (MODE != 1)
-        for (int e = threadIdx.x; e < M * CC; e += blockDim.x) buf[e] = make_double2(0.0, 0.0);
+        for (int e = threadIdx.x; e < M * CC; e += blockDim.x) buf[e] = Cx<R>::mk(0, 0);
     __syncthreads();
     const int nrow_in = (MODE == 1) ? M : a.nin;
     for (int e = threadIdx.x; e < nrow_in * nc; e += blockDim.x) {
@@ -187,9 +206,9 @@ __global__ void __launch_bounds__(256) k_col(ColArgs a) {
         buf[r * CC + c] = in[r * a.in_row + c];
     }
     __syncthreads();
+    C *out = (C *)a.out + p * a.out_sp + q * a.out_sq + c0;
     if (MODE == 0) {
         fft_dif<LOG2M>(buf, nc, 1, CC, s_tw, false);
-        double2 *out = a.out + p * a.out_sp + q * a.out_sq + c0;
         for (int e = threadIdx.x; e < M * nc; e += blockDim.x) {
             const int r = e / nc, c = e % nc;
             out[r * a.out_row + c] = buf[brev_bits(r, LOG2M) * CC + c];
@@ -200,6 +219,7 @@ __global__ void __launch_bounds__(256) k_col(ColArgs a) {
         fft_dif<LOG2M>(buf, nc, 1, CC, s_tw, true);
     } else {
         fft_dif<LOG2M>(buf, nc, 1, CC, s_tw, false);
+        const R *khat = (const R *)a.khat;
         const int ky = q < M - q ? q : M - q;
         for (int e = threadIdx.x; e < M * nc; e += blockDim.x) {
             const int r = e / nc, c = e % nc;
@@ -207,14 +227,15 @@ __global__ void __launch_bounds__(256) k_col(ColArgs a) {
             const int kz = kz0 < M - kz0 ? kz0 : M - kz0;
             const int kx0 = c0 + c;
             const int kx = kx0 < M - kx0 ? kx0 : M - kx0;
-            const double k = a.khat[((long)kx * MH + ky) * MH + kz];
-            double2 v = buf[r * CC + c];
-            buf[r * CC + c] = make_double2(v.x * k, v.y * k);
+            const R k = khat[((long)kx * MH + ky) * MH + kz];
+            C v = buf[r * CC + c];
+            v.x *= k;
+            v.y *= k;
+            buf[r * CC + c] = v;
         }
         __syncthreads();
         fft_dit<LOG2M>(buf, nc, 1, CC, s_tw, true);
     }
-    double2 *out = a.out + p * a.out_sp + q * a.out_sq + c0;
     for (int e = threadIdx.x; e < a.nout * nc; e += blockDim.x) {
         const int t = e / nc, c = e % nc;
         int pos = (a.out_off + t) % M;
@@ -227,29 +248,30 @@ __global__ void __launch_bounds__(256) k_col(ColArgs a) {
 // ---------------------------------------------------------------------------
 // Inverse real transform along axis 2: lines are rows; the half spectrum
 // kx in [0, M/2] is extended by Hermitian symmetry; outputs t < nout from
-// positions (out_off + t) mod M.  out[(slab * nrow + row) * nout + t].
+// positions (out_off + t) mod M.  out[(slab * nrow + row) * nout + t] (type TO).
 // ---------------------------------------------------------------------------
 struct InvXArgs {
-    const double2 *in;
-    double *out;
+    const void *in;
+    void *out;
     int nrow, nout, out_off, lines_cta;
-    const double2 *tw;
+    const void *tw;
 };
 
-template <int LOG2M>
+template <int LOG2M, typename R, typename TO>
 __global__ void __launch_bounds__(256) k_inv_x(InvXArgs a) {
+    using C = typename Cx<R>::T;
     constexpr int M = 1 << LOG2M, MH = M / 2 + 1, LS = M + 1;
-    extern __shared__ double2 smem[];
-    double2 *s_tw = smem;
-    double2 *buf = smem + M / 2;
-    const int slab = blockIdx.y;
-    const int r0 = blockIdx.x * a.lines_cta;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *s_tw = (C *)smem_raw;
+    C *buf = s_tw + M / 2;
+    const int slab = blockIdx.x;
+    const int r0 = blockIdx.y * a.lines_cta;
     const int nl = min(a.lines_cta, a.nrow - r0);
-    load_twiddles<LOG2M>(s_tw, a.tw);
-    const double2 *in = a.in + ((long)slab * a.nrow + r0) * MH;
+    load_twiddles<LOG2M>(s_tw, (const C *)a.tw);
+    const C *in = (const C *)a.in + ((long)slab * a.nrow + r0) * MH;
     for (int e = threadIdx.x; e < nl * M; e += blockDim.x) {
         const int l = e / M, k = e % M;
-        double2 v;
+        C v;
         if (k < MH) {
             v = in[l * MH + k];
         } else {
@@ -260,12 +282,12 @@ __global__ void __launch_bounds__(256) k_inv_x(InvXArgs a) {
     }
     __syncthreads();
     fft_dif<LOG2M>(buf, nl, LS, 1, s_tw, true);
-    double *out = a.out + ((long)slab * a.nrow + r0) * a.nout;
+    TO *out = (TO *)a.out + ((long)slab * a.nrow + r0) * a.nout;
     for (int e = threadIdx.x; e < nl * a.nout; e += blockDim.x) {
         const int l = e / a.nout, t = e % a.nout;
         int pos = (a.out_off + t) % M;
         if (pos < 0) pos += M;
-        out[l * a.nout + t] = buf[l * LS + brev_bits(pos, LOG2M)].x;
+        out[l * a.nout + t] = (TO)buf[l * LS + brev_bits(pos, LOG2M)].x;
     }
 }
 
@@ -304,22 +326,24 @@ __global__ void __launch_bounds__(256) k_moments(const TF *__restrict__ f, int N
 }
 
 // r^i[a] = phi^i[g_a] - I^H(phi^i)(g_a) on the face nodes of Omega_alpha.
-__global__ void __launch_bounds__(256) k_resid(const double *__restrict__ box, long W3, int na,
+template <typename TB>
+__global__ void __launch_bounds__(256) k_resid(const TB *__restrict__ box, long W3, int na,
                                                int S, const int *__restrict__ a_self,
                                                const int *__restrict__ a_off,
                                                const double *__restrict__ a_w,
                                                double *__restrict__ resid) {
-    const int p = blockIdx.y;
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = blockIdx.x;
+    const int a = blockIdx.y * blockDim.x + threadIdx.x;
     if (a >= na) return;
-    const double *bx = box + (long)p * W3;
+    const TB *bx = box + (long)p * W3;
     double acc = 0.0;
-    for (int j = 0; j < S; ++j) acc = fma(a_w[(long)a * S + j], bx[a_off[(long)a * S + j]], acc);
-    resid[(long)p * na + a] = bx[a_self[a]] - acc;
+    for (int j = 0; j < S; ++j) acc = fma(a_w[(long)a * S + j], (double)bx[a_off[(long)a * S + j]], acc);
+    resid[(long)p * na + a] = (double)bx[a_self[a]] - acc;
 }
 
 struct AsmArgs {
-    const double *box, *mom, *T;
+    const void *box;
+    const double *mom, *T;
     double *FH;
     int np, n, s, W, npoly, flo, nf;
     int ca_lo, ca_hi, cb_lo, cb_hi;
@@ -328,6 +352,7 @@ struct AsmArgs {
 
 // F^H[k] = sum over patches i (ascending) of Delta^H phi^{i,h} on C(Omega_alpha(i))
 // or sum_p c_p^i Delta^H(G^h * Q^p) on C(Omega_beta(i)) \ C(Omega_alpha(i)).
+template <typename TB>
 __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const long tot = (long)a.nf * a.nf * a.nf;
@@ -353,7 +378,7 @@ __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
                 const bool inA = r0 >= a.ca_lo && r0 <= a.ca_hi && r1 >= a.ca_lo &&
                                  r1 <= a.ca_hi && r2 >= a.ca_lo && r2 <= a.ca_hi;
                 if (inA) {
-                    const double *bx = a.box + p * W * W * W;
+                    const TB *bx = (const TB *)a.box + p * W * W * W;
                     double lap = 0.0;
                     for (int s0 = -1; s0 <= 1; ++s0)
                         for (int s1 = -1; s1 <= 1; ++s1)
@@ -363,7 +388,7 @@ __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
                                 if (c == 0.0) continue;
                                 const long x0 = 4 * (r0 + s0) + a.s, x1 = 4 * (r1 + s1) + a.s,
                                            x2 = 4 * (r2 + s2) + a.s;
-                                lap = fma(c, bx[(x0 * W + x1) * W + x2], lap);
+                                lap = fma(c, (double)bx[(x0 * W + x1) * W + x2], lap);
                             }
                     acc += lap;
                 } else {
@@ -548,39 +573,40 @@ __global__ void __launch_bounds__(256) k_dirichlet(DirArgs a) {
     }
 }
 
+template <typename R>
 inline size_t fft_smem_bytes(int M, int lines, int ls) {
-    return (size_t)(M / 2) * sizeof(double2) + (size_t)lines * ls * sizeof(double2);
+    return ((size_t)(M / 2) + (size_t)lines * ls) * 2 * sizeof(R);
 }
 
-template <int LOG2M>
+template <int LOG2M, typename R>
 void set_smem_attrs() {
     const int big = 200 * 1024;
-    cudaFuncSetAttribute(k_fwd_x<LOG2M, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_fwd_x<LOG2M, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_fwd_x<LOG2M, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_col<LOG2M, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_col<LOG2M, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_col<LOG2M, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_inv_x<LOG2M>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_fwd_x<LOG2M, double, true, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_fwd_x<LOG2M, float, true, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_fwd_x<LOG2M, double, false, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_col<LOG2M, 0, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_col<LOG2M, 1, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_col<LOG2M, 2, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_inv_x<LOG2M, R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
 // One Hockney convolution pipeline (5 launches) for `nbatch` problems with
 // nin input nodes per axis at positions [0, nin) and nout outputs per axis
-// from positions out_off + t.
+// from positions out_off + t.  R: working precision; output array of type R.
 struct ConvDesc {
     int M, log2M, nbatch, nin, nout, out_off;
-    const void *src;     // fwd_x input (patch gather or dense)
+    const void *src;     // fwd_x input (patch gather or dense FP64)
     bool patch, f32;
     int N, n, np;
-    double2 *b0, *b1;    // ping-pong spectra
-    double *out;         // nbatch x nout^3 real
-    const double *khat;
-    const double2 *tw;
+    void *b0, *b1;       // ping-pong spectra (complex R)
+    void *out;           // nbatch x nout^3, type R
+    const void *khat;    // real R
+    const void *tw;      // complex R
     const mlc_plan_s *pl;  // timing events (slots ev0 .. ev0+4)
     int ev0;
 };
 
-template <int LOG2M>
+template <int LOG2M, typename R>
 cudaError_t run_conv_t(const ConvDesc &d, cudaStream_t st) {
     constexpr int M = 1 << LOG2M, MH = M / 2 + 1;
     const int nin = d.nin, W = d.nout;
@@ -590,18 +616,18 @@ cudaError_t run_conv_t(const ConvDesc &d, cudaStream_t st) {
         FwdXArgs a{d.src, d.b0, d.N, d.n, d.np, nin, 0, d.tw};
         a.lines_cta = (M <= 64) ? nin : 16;
         a.lines_cta = a.lines_cta > nin ? nin : a.lines_cta;
-        dim3 grid((nin + a.lines_cta - 1) / a.lines_cta, d.nbatch * nin);
-        size_t sm = fft_smem_bytes(M, a.lines_cta, M + 1);
+        dim3 grid(d.nbatch * nin, (nin + a.lines_cta - 1) / a.lines_cta);
+        size_t sm = fft_smem_bytes<R>(M, a.lines_cta, M + 1);
         if (d.patch) {
-            if (d.f32) k_fwd_x<LOG2M, float, true><<<grid, 256, sm, st>>>(a);
-            else k_fwd_x<LOG2M, double, true><<<grid, 256, sm, st>>>(a);
+            if (d.f32) k_fwd_x<LOG2M, float, true, R><<<grid, 256, sm, st>>>(a);
+            else k_fwd_x<LOG2M, double, true, R><<<grid, 256, sm, st>>>(a);
         } else {
-            k_fwd_x<LOG2M, double, false><<<grid, 256, sm, st>>>(a);
+            k_fwd_x<LOG2M, double, false, R><<<grid, 256, sm, st>>>(a);
         }
     }
     const int CC = (M <= 64) ? MH : 16;
     const int gx = (MH + CC - 1) / CC;
-    const size_t smc = fft_smem_bytes(M, M, CC);
+    const size_t smc = fft_smem_bytes<R>(M, M, CC);
     mark(d.pl, d.ev0 + 1, st);
     // 2. forward y: A1[p][zi][yi][kx] -> A2[p][zi][ky][kx]
     {
@@ -610,7 +636,7 @@ cudaError_t run_conv_t(const ConvDesc &d, cudaStream_t st) {
         a.in_sp = (long)nin * nin * MH; a.in_sq = (long)nin * MH; a.in_row = MH;
         a.out_sp = (long)nin * M * MH; a.out_sq = (long)M * MH; a.out_row = MH;
         a.ncols = MH; a.cols_cta = CC; a.nin = nin; a.nout = M; a.out_off = 0; a.tw = d.tw;
-        k_col<LOG2M, 0><<<dim3(gx, d.nbatch * nin), 256, smc, st>>>(a);
+        k_col<LOG2M, 0, R><<<dim3(d.nbatch * nin, gx), 256, smc, st>>>(a);
     }
     mark(d.pl, d.ev0 + 2, st);
     // 3. z: forward, x kernel, inverse: A2[p][zi][ky][kx] -> A3[p][zo][ky][kx]
@@ -621,7 +647,7 @@ cudaError_t run_conv_t(const ConvDesc &d, cudaStream_t st) {
         a.out_sp = (long)W * M * MH; a.out_sq = MH; a.out_row = (long)M * MH;
         a.ncols = MH; a.cols_cta = CC; a.nin = nin; a.nout = W; a.out_off = d.out_off;
         a.khat = d.khat; a.tw = d.tw;
-        k_col<LOG2M, 2><<<dim3(gx, d.nbatch * M), 256, smc, st>>>(a);
+        k_col<LOG2M, 2, R><<<dim3(d.nbatch * M, gx), 256, smc, st>>>(a);
     }
     mark(d.pl, d.ev0 + 3, st);
     // 4. inverse y: A3[p][zo][ky][kx] -> A4[p][zo][yo][kx]
@@ -631,25 +657,26 @@ cudaError_t run_conv_t(const ConvDesc &d, cudaStream_t st) {
         a.in_sp = (long)W * M * MH; a.in_sq = (long)M * MH; a.in_row = MH;
         a.out_sp = (long)W * W * MH; a.out_sq = (long)W * MH; a.out_row = MH;
         a.ncols = MH; a.cols_cta = CC; a.nin = M; a.nout = W; a.out_off = d.out_off; a.tw = d.tw;
-        k_col<LOG2M, 1><<<dim3(gx, d.nbatch * W), 256, smc, st>>>(a);
+        k_col<LOG2M, 1, R><<<dim3(d.nbatch * W, gx), 256, smc, st>>>(a);
     }
     mark(d.pl, d.ev0 + 4, st);
     // 5. inverse x (real): A4[p][zo][yo][kx] -> out[p][zo][yo][xo]
     {
         InvXArgs a{d.b1, d.out, W, W, d.out_off, 0, d.tw};
         a.lines_cta = (M <= 64) ? W : 16;
-        dim3 grid((W + a.lines_cta - 1) / a.lines_cta, d.nbatch * W);
-        k_inv_x<LOG2M><<<grid, 256, fft_smem_bytes(M, a.lines_cta, M + 1), st>>>(a);
+        dim3 grid(d.nbatch * W, (W + a.lines_cta - 1) / a.lines_cta);
+        k_inv_x<LOG2M, R, R><<<grid, 256, fft_smem_bytes<R>(M, a.lines_cta, M + 1), st>>>(a);
     }
     return cudaGetLastError();
 }
 
+template <typename R>
 cudaError_t run_conv(const ConvDesc &d, cudaStream_t st) {
     switch (d.log2M) {
-        case 5: return run_conv_t<5>(d, st);
-        case 6: return run_conv_t<6>(d, st);
-        case 7: return run_conv_t<7>(d, st);
-        case 8: return run_conv_t<8>(d, st);
+        case 5: return run_conv_t<5, R>(d, st);
+        case 6: return run_conv_t<6, R>(d, st);
+        case 7: return run_conv_t<7, R>(d, st);
+        case 8: return run_conv_t<8, R>(d, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -665,10 +692,12 @@ void stencil_b(int Q, double b[4]) {
 }  // namespace
 
 void configure_kernels() {
-    set_smem_attrs<5>();
-    set_smem_attrs<6>();
-    set_smem_attrs<7>();
-    set_smem_attrs<8>();
+    set_smem_attrs<5, double>();
+    set_smem_attrs<6, double>();
+    set_smem_attrs<7, double>();
+    set_smem_attrs<8, double>();
+    set_smem_attrs<5, float>();
+    set_smem_attrs<6, float>();
     cudaFuncSetAttribute(k_dirichlet<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_dirichlet<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
@@ -687,16 +716,24 @@ cudaError_t launch_patch_conv(const mlc_plan_s *pl, const void *f, bool f32, cud
     ConvDesc d{};
     d.M = g.M; d.log2M = g.log2M; d.nbatch = g.NP; d.nin = g.nb; d.nout = g.W; d.out_off = -g.s;
     d.src = f; d.patch = true; d.f32 = f32; d.N = g.N; d.n = g.n; d.np = g.np;
-    d.b0 = pl->buf0; d.b1 = pl->buf1; d.out = pl->box; d.khat = pl->khat; d.tw = pl->tw;
-    d.pl = pl; d.ev0 = 1;
-    return run_conv(d, st);
+    d.b0 = pl->buf0; d.b1 = pl->buf1; d.out = pl->box; d.pl = pl; d.ev0 = 1;
+    if (pl->g.tier == MLC_TIER_SPLIT) {
+        d.khat = pl->khat_f; d.tw = pl->tw_f;
+        return run_conv<float>(d, st);
+    }
+    d.khat = pl->khat; d.tw = pl->tw;
+    return run_conv<double>(d, st);
 }
 
 cudaError_t launch_resid(const mlc_plan_s *pl, cudaStream_t st) {
     const Geom &g = pl->g;
-    dim3 grid((g.na_face + 255) / 256, g.NP);
-    k_resid<<<grid, 256, 0, st>>>(pl->box, (long)g.W * g.W * g.W, g.na_face, g.S, pl->a_self,
-                                  pl->a_off, pl->a_w, pl->resid);
+    dim3 grid(g.NP, (g.na_face + 255) / 256);
+    if (g.tier == MLC_TIER_SPLIT)
+        k_resid<float><<<grid, 256, 0, st>>>((const float *)pl->box, (long)g.W * g.W * g.W, g.na_face,
+                                             g.S, pl->a_self, pl->a_off, pl->a_w, pl->resid);
+    else
+        k_resid<double><<<grid, 256, 0, st>>>((const double *)pl->box, (long)g.W * g.W * g.W, g.na_face,
+                                              g.S, pl->a_self, pl->a_off, pl->a_w, pl->resid);
     return cudaGetLastError();
 }
 
@@ -710,7 +747,10 @@ cudaError_t launch_assemble(const mlc_plan_s *pl, cudaStream_t st) {
     stencil_b(g.Q, b);
     for (int k = 0; k < 4; ++k) a.coef[k] = b[k] / (g.H * g.H);
     const long tot = (long)g.nf * g.nf * g.nf;
-    k_assemble<<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(a);
+    if (g.tier == MLC_TIER_SPLIT)
+        k_assemble<float><<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(a);
+    else
+        k_assemble<double><<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -722,7 +762,7 @@ cudaError_t launch_coarse(const mlc_plan_s *pl, cudaStream_t st) {
     d.src = pl->FH; d.patch = false; d.f32 = false;
     d.b0 = pl->cbuf0; d.b1 = pl->cbuf1; d.out = pl->phiH; d.khat = pl->khat_c; d.tw = pl->tw_c;
     d.pl = pl; d.ev0 = 8;
-    return run_conv(d, st);
+    return run_conv<double>(d, st);
 }
 
 cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st) {

@@ -69,11 +69,13 @@ struct mlc_plan_s {
     int *rmap;
     double *Dtab, *Ttab;
     double2 *tw, *tw_c;      // FFT twiddles exp(-2 pi i t / M), t < M/2
+    float *khat_f;           // split tier: FP32 copies of the patch spectrum and twiddles
+    float2 *tw_f;
     double *sinm;            // (n-1)^2 DST-I matrix sin(pi k m / n)
     double *lam;             // (n-1)^3 stencil eigenvalues / h^2
     // workspace (device)
-    double2 *buf0, *buf1;    // ping-pong spectra for the patch convolutions
-    double *box;             // NP x W^3 local fields phi^{i,h}
+    void *buf0, *buf1;       // ping-pong spectra for the patch convolutions (complex FP64 / FP32)
+    void *box;               // NP x W^3 local fields phi^{i,h} (FP64 / FP32)
     double *mom;             // NP x npoly
     double *resid;           // NP x na_face
     double *FH;              // nf^3

@@ -473,7 +473,6 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
     Geom g;
     TRY(derive_geometry(*params, g));
     if (g.tier != MLC_TIER_FP64 && g.tier != MLC_TIER_SPLIT) return MLC_ERR_INVALID_ARG;
-    if (g.tier == MLC_TIER_SPLIT) return MLC_ERR_UNSUPPORTED;
     std::call_once(g_cfg_once, configure_kernels);
     mlc_plan_s *pl = new (std::nothrow) mlc_plan_s();
     if (!pl) return MLC_ERR_OOM;
@@ -498,9 +497,28 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
         const size_t NP = G.NP, nb = G.nb, W = G.W, M = G.M, Mh = G.Mh;
         const size_t A1 = NP * nb * nb * Mh, A2 = NP * nb * M * Mh, A3 = NP * W * M * Mh,
                      A4 = NP * W * W * Mh;
-        TRY(dev_alloc(pl, &pl->buf0, std::max(A1, A3)));
-        TRY(dev_alloc(pl, &pl->buf1, std::max(A2, A4)));
-        TRY(dev_alloc(pl, &pl->box, NP * W * W * W));
+        const size_t rb = G.tier == MLC_TIER_SPLIT ? sizeof(float) : sizeof(double);
+        char *b0 = nullptr, *b1 = nullptr, *bx = nullptr;
+        TRY(dev_alloc(pl, &b0, std::max(A1, A3) * 2 * rb));
+        TRY(dev_alloc(pl, &b1, std::max(A2, A4) * 2 * rb));
+        TRY(dev_alloc(pl, &bx, NP * W * W * W * rb));
+        pl->buf0 = b0;
+        pl->buf1 = b1;
+        pl->box = bx;
+        if (G.tier == MLC_TIER_SPLIT) {
+            // FP32 copies of the patch kernel spectrum and twiddles
+            const size_t nk = (size_t)G.Mh * G.Mh * G.Mh;
+            std::vector<double> kd(nk);
+            TRY_CUDA(cudaMemcpy(kd.data(), pl->khat, nk * sizeof(double), cudaMemcpyDeviceToHost));
+            std::vector<float> kf(kd.begin(), kd.end());
+            std::vector<float2> tf(G.M / 2);
+            for (int t = 0; t < G.M / 2; ++t) {
+                const double a = 2.0 * M_PI * (double)t / (double)G.M;
+                tf[t] = make_float2((float)std::cos(a), (float)-std::sin(a));
+            }
+            TRY(dev_upload(pl, &pl->khat_f, kf));
+            TRY(dev_upload(pl, &pl->tw_f, tf));
+        }
         TRY(dev_alloc(pl, &pl->mom, NP * G.npoly));
         TRY(dev_alloc(pl, &pl->resid, NP * (size_t)G.na_face));
         const size_t nf = G.nf, no = G.no, Mc = G.Mc, Mhc = G.Mhc;

@@ -176,3 +176,49 @@ def test_invalid_arguments(torch_cuda):
     with pytest.raises(mlc.MLCError) as e:
         mlc.Plan(N=32, n=32, s=32)
     assert e.value.status == 2
+
+
+# ------------------------------------------------------------------ split tier
+SPLIT_TOL = 1e-6
+
+
+def test_split_tier_matches_fp64_and_oracle(torch_cuda, G6):
+    """Split tier (FP32 charge, FP32 local convolutions, FP64 elsewhere) within
+    1e-6 relative max-norm of the FP64 GPU path and of the oracle."""
+    from paper_1702_08111_gb300 import mlc
+    torch = torch_cuda
+    w = I.workload("bumps8_64_q6")
+    f32 = w.charge().astype(np.float32)
+    f64 = f32.astype(np.float64)
+    ps = mlc.Plan(64, 16, 16, 4, 6, tier=mlc.MLC_TIER_SPLIT)
+    pd = mlc.Plan(64, 16, 16, 4, 6)
+    a = ps.solve(torch.from_numpy(f32).cuda())
+    b = pd.solve(torch.from_numpy(f64).cuda())
+    torch.cuda.synchronize()
+    a, b = a.cpu().numpy(), b.cpu().numpy()
+    e_gpu = relmax(a, b)
+    ref = O.solve_open(O.Params(N=64, n=16, s=16, Q=6), f64, G1=G6)
+    assert relmax(b, ref) <= TOL
+    assert e_gpu <= SPLIT_TOL, e_gpu
+    assert relmax(a, ref) <= SPLIT_TOL
+
+
+def test_split_tier_256_below_discretisation_error(torch_cuda):
+    """256^3, 4096 patches, Q = 6, 32 bumps, FP32 charge: split vs FP64 GPU path
+    <= 1e-6 and below the FP64 path's error against the closed-form potential."""
+    from oracle import closed_forms as CF
+    from paper_1702_08111_gb300 import mlc
+    torch = torch_cuda
+    w = I.workload("bumps32_256_q6")
+    f32 = w.charge()
+    ps = mlc.Plan(256, 16, 16, 4, 6, tier=mlc.MLC_TIER_SPLIT)
+    a = ps.solve(torch.from_numpy(f32).cuda()).cpu().numpy()
+    del ps
+    pd = mlc.Plan(256, 16, 16, 4, 6)
+    b = pd.solve(torch.from_numpy(f32.astype(np.float64)).cuda()).cpu().numpy()
+    del pd
+    ex = CF.bumps_potential(256, w.bumps)
+    e_split = relmax(a, b)
+    e_disc = relmax(b, ex)
+    assert e_split <= SPLIT_TOL, e_split
+    assert e_split < e_disc, (e_split, e_disc)
