@@ -93,6 +93,21 @@ def conv_pass_flops(M: int, lines: int, passes: int = 1) -> float:
     return lines * passes * 5.0 * M * np.log2(M)
 
 
+def reduce_max_ms(ms: float, world: int, device: str = "cuda") -> float:
+    """Slowest rank's time (the job's time): all-reduce MAX over the ranks."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(points_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput in Mpoints/s: every rank solves its own problem."""
+    return world * points_per_rank / (ms_max * 1e-3) / 1e6
+
+
 def time_plan(plan, f, phi, steps, warmup, flush, stream, world):
     """Mean device time per solve (CUDA events on the launching stream, L2
     flushed between steps outside the timed region) and per-launch means."""
@@ -125,11 +140,13 @@ def roofline_for(w, plan, per_launch, tier):
     info = plan.info
     N = w.N
     M, Mh, NP, W = info.M, info.M // 2 + 1, (N // w.n) ** 3, w.n + 2 * w.s + 1
+    nin = w.n + 1
     flops = {
-        "conv_z_kernel": conv_pass_flops(M, NP * M * Mh, 2) + NP * M * M * Mh * 2.0,
-        "conv_inv_y": conv_pass_flops(M, NP * W * Mh),
+        # per (patch, kx) slab: forward y on nin lines, forward and inverse z on M lines,
+        # inverse y on W lines, and the real kernel product (2 flops per complex entry)
+        "conv_slab": conv_pass_flops(M, NP * Mh * (nin + 2 * M + W)) + NP * Mh * M * M * 2.0,
         "conv_inv_x": conv_pass_flops(M, NP * W * W),
-        "conv_fwd_y": conv_pass_flops(M, NP * (w.n + 1) * Mh),
+        "conv_fwd_x": conv_pass_flops(M, NP * nin * nin),
     }
     dom = max(per_launch, key=per_launch.get)
     if dom not in flops:
@@ -161,10 +178,7 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream()
     with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clk:
         ms, per_launch = time_plan(plan, f, phi, args.steps, args.warmup, flush, stream, world)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max_ms(ms, world)
 
     # end to end through the C ABI with host buffers (copies inside the call)
     f_pin = f_host.pin_memory()
@@ -178,7 +192,7 @@ def run_ours(args, rank, world):
         plan.solve_host(f_pin, phi_pin)
         e2e_ms += (time.perf_counter() - t0) * 1e3
     e2e_ms /= args.steps
-    value = world * float(N) ** 3 / (ms * 1e-3) / 1e6
+    value = aggregate_value(float(N) ** 3, world, ms)
     res = {"value": value, "ms": ms, "e2e_ms": e2e_ms, "per_launch": per_launch,
            "roofline": roofline_for(w, plan, per_launch, tier), "clocks": clk.summary(),
            "phi": phi, "N": N, "tier": tier, "f_bytes": f_host.element_size() * N ** 3}
@@ -216,7 +230,115 @@ def run_extra(args, flush, stream):
     out["fp64"]["max_rel_err_vs_closed_form"] = float(np.abs(phis["fp64"] - ex).max() / np.abs(ex).max())
     out["split"]["max_rel_err_vs_closed_form"] = float(np.abs(phis["split"] - ex).max() / np.abs(ex).max())
     out["split_over_fp64_speedup"] = round(out["fp64"]["ms_per_step"] / out["split"]["ms_per_step"], 3)
+    del phis
+    out["batch"] = run_batch(args, flush, stream)
+    out["serving"] = run_serving(args)
     return out
+
+
+def run_batch(args, flush, stream):
+    """48 uneven problems (sides 32..160), split tier, through mlc_batch_solve
+    (one graph per patch geometry) versus the same problems one by one."""
+    import torch
+    from paper_1702_08111_gb300 import mlc
+    probs = I.batch_problems(48, 4)
+    groups = {}
+    for w in probs:
+        groups.setdefault((w.n, w.s), []).append(w)
+    plans, fs, phis = {}, {}, {}
+    for key, ws in groups.items():
+        plans[key] = [mlc.Plan(w.N, w.n, w.s, w.P, w.Q, tier=mlc.MLC_TIER_SPLIT) for w in ws]
+        fs[key] = [torch.from_numpy(w.charge().astype(np.float32)).cuda() for w in ws]
+        phis[key] = [torch.empty((w.N,) * 3, dtype=torch.float64, device="cuda") for w in ws]
+    pts = float(sum(w.N ** 3 for w in probs))
+
+    def step_batch():
+        for key in groups:
+            mlc.batch_solve(plans[key], fs[key], phis[key], stream)
+
+    def step_single():
+        for key in groups:
+            for p, f, ph in zip(plans[key], fs[key], phis[key]):
+                p.solve(f, ph, stream)
+
+    res = {}
+    for name, fn in (("batched_graph", step_batch), ("one_by_one", step_single)):
+        for _ in range(3):
+            fn()
+            flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        steps = max(3, args.steps // 2)
+        for _ in range(steps):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+            flush.zero_()
+        ms = tot / steps
+        res[name] = {"ms_per_step": round(ms, 3), "value": round(pts / (ms * 1e-3) / 1e6, 2), "unit": "Mpoints/s"}
+    res["problems"] = len(probs)
+    res["groups"] = {f"n{k[0]}_s{k[1]}": len(v) for k, v in groups.items()}
+    res["speedup_over_one_by_one"] = round(res["one_by_one"]["ms_per_step"] / res["batched_graph"]["ms_per_step"], 3)
+    return res
+
+
+def run_serving(args, nreq=200):
+    """Continuous-batching server on the first `nreq` requests of the serving
+    mix: saturated throughput first, then Poisson arrivals at 0.7 x that rate;
+    p50/p99 latency (enqueue -> completion)."""
+    import torch
+    from paper_1702_08111_gb300 import mlc
+    reqs = I.serving_requests(2000, 5)[:nreq]
+    data = []
+    for w, tier in reqs:
+        f = w.charge()
+        t = torch.from_numpy(f.astype(np.float32) if tier == "split" else f).cuda()
+        data.append((w, tier, t, torch.empty((w.N,) * 3, dtype=torch.float64, device="cuda")))
+    srv = mlc.Server(120 << 30, max_batch=8)
+
+    def submit(k):
+        w, tier, f, phi = data[k]
+        return srv.enqueue(f, phi, w.N, w.n, w.s, w.P, w.Q,
+                           tier=mlc.MLC_TIER_SPLIT if tier == "split" else mlc.MLC_TIER_FP64)
+
+    # warm-up: every distinct plan once (plan creation is not serving latency)
+    seen = {}
+    for k, (w, tier, _, _) in enumerate(data):
+        seen.setdefault((w.N, w.Q, tier), k)
+    for t in [submit(k) for k in seen.values()]:
+        srv.wait(t)
+    # saturated: all at once
+    t0 = time.perf_counter()
+    for t in [submit(k) for k in range(len(data))]:
+        srv.wait(t)
+    sat_s = time.perf_counter() - t0
+    rate = 0.7 * len(data) / sat_s
+    rng = np.random.default_rng(55)
+    gaps = rng.exponential(1.0 / rate, size=len(data))
+    tickets = []
+    t0 = time.perf_counter()
+    next_t = t0
+    for k in range(len(data)):
+        next_t += gaps[k]
+        while time.perf_counter() < next_t:
+            time.sleep(min(0.0005, max(0.0, next_t - time.perf_counter())))
+        tickets.append(submit(k))
+    lats = []
+    for t in tickets:
+        st, lat, q = srv.wait(t)
+        lats.append(lat)
+    total_s = time.perf_counter() - t0
+    srv.close()
+    pts = float(sum(w.N ** 3 for w, _, _, _ in data))
+    return {"requests": len(data), "rate_req_per_s": round(rate, 2),
+            "saturated_req_per_s": round(len(data) / sat_s, 2),
+            "p50_ms": round(float(np.percentile(lats, 50)), 3), "p99_ms": round(float(np.percentile(lats, 99)), 3),
+            "Mpoints_per_s_at_rate": round(pts / total_s / 1e6, 2),
+            "Mpoints_per_s_saturated": round(pts / sat_s / 1e6, 2),
+            "distinct_plans": len(seen), "hbm_budget_gb": 120, "max_batch": 8}
 
 
 def cpu_oracle_solve(w, nodes_sample=None):
@@ -266,7 +388,7 @@ def main():
                    "sample": f"one full oracle solve of {args.workload} ({t:.1f} s; DGF table prebuilt)"}
         N = r["N"]
         e2e_val = float(N) ** 3 / (r["e2e_ms"] * 1e-3) / 1e6
-        launches = 15
+        launches = 13
         line = {
             "metric": METRIC, "value": round(r["value"], 3), "unit": "Mpoints/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r["ms"], 4),

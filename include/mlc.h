@@ -141,12 +141,13 @@ typedef enum {
 
 mlc_status mlc_debug_stage_bytes(mlc_plan_t plan, int stage, size_t *bytes);
 /* Per-launch timing of later solves with this plan: when enabled, mlc_solve
- * records a CUDA event on its stream before each of its 15 launches and after
+ * records a CUDA event on its stream before each of its 13 launches and after
  * the last.  mlc_debug_timing waits for the last solve's final event and
- * writes the 15 durations (ms) in launch order: moments; local convolution
- * x, y, z (forward, kernel, inverse), inverse y, inverse x; residuals;
- * assembly of F^H; coarse convolution x, y, z, inverse y, inverse x;
- * boundary values; Dirichlet solves.  count must be >= 15. */
+ * writes the 13 durations (ms) in launch order: moments; local convolutions:
+ * forward x, fused slab (forward y and z, kernel spectrum, inverse z and y),
+ * inverse x; residuals; assembly of F^H; coarse convolution x, y, z (forward,
+ * kernel, inverse), inverse y, inverse x; boundary values; Dirichlet solves.
+ * count must be >= 13. */
 mlc_status mlc_debug_set_timing(mlc_plan_t plan, int enable);
 mlc_status mlc_debug_timing(mlc_plan_t plan, float *ms_out, int count);
 mlc_status mlc_debug_export(mlc_plan_t plan, int stage, void *host, size_t bytes);

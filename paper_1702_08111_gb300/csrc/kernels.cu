@@ -49,10 +49,31 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 w) {
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
 
-// Decimation in frequency: natural-order input, bit-reversed output.
+// Multiply by -i (forward) or +i (inverse): a swap and a sign change, no FLOPs.
+template <typename C>
+__device__ __forceinline__ C mul_mi(C v, bool inv) {
+    C r;
+    if (inv) { r.x = -v.y; r.y = v.x; }
+    else { r.x = v.y; r.y = -v.x; }
+    return r;
+}
+
+// Twiddle product of a radix-2 stage with half-size hs: w = exp(-+ 2 pi i pos / (2 hs)).
+// hs = 1 has w = 1 and hs = 2 has w in {1, -+i}; neither needs a multiply.
+template <typename C>
+__device__ __forceinline__ C twiddle(C v, int st, int pos, int tsh, const C *tw, bool inv) {
+    if (st == 0) return v;
+    if (st == 1) return pos ? mul_mi(v, inv) : v;
+    C w = tw[pos << tsh];
+    if (inv) w.y = -w.y;
+    return cmul(v, w);
+}
+
+// Decimation in frequency: natural-order input, bit-reversed output.  Line l
+// starts at buf + line_off(l) (lstride, plus `gap` for lines >= gap_at).
 template <int LOG2M, typename C>
 __device__ __forceinline__ void fft_dif(C *buf, int nlines, int lstride, int estride,
-                                        const C *tw, bool inv) {
+                                        const C *tw, bool inv, int gap_at = 1 << 30, int gap = 0) {
     constexpr int MH = 1 << (LOG2M - 1);
     const int total = nlines * MH;
 #pragma unroll 1
@@ -63,13 +84,11 @@ __device__ __forceinline__ void fft_dif(C *buf, int nlines, int lstride, int est
             const int line = j % nlines, bf = j / nlines;
             const int grp = bf >> st, pos = bf & (hs - 1);
             const int i0 = (grp << (st + 1)) + pos;
-            C *p0 = buf + line * lstride + i0 * estride;
+            C *p0 = buf + line * lstride + (line >= gap_at ? gap : 0) + i0 * estride;
             C *p1 = p0 + hs * estride;
-            C w = tw[pos << tsh];
-            if (inv) w.y = -w.y;
             const C a = *p0, b = *p1;
             *p0 = cadd(a, b);
-            *p1 = cmul(csub(a, b), w);
+            *p1 = twiddle(csub(a, b), st, pos, tsh, tw, inv);
         }
         __syncthreads();
     }
@@ -78,7 +97,7 @@ __device__ __forceinline__ void fft_dif(C *buf, int nlines, int lstride, int est
 // Decimation in time: bit-reversed input, natural-order output.
 template <int LOG2M, typename C>
 __device__ __forceinline__ void fft_dit(C *buf, int nlines, int lstride, int estride,
-                                        const C *tw, bool inv) {
+                                        const C *tw, bool inv, int gap_at = 1 << 30, int gap = 0) {
     constexpr int MH = 1 << (LOG2M - 1);
     const int total = nlines * MH;
 #pragma unroll 1
@@ -89,17 +108,26 @@ __device__ __forceinline__ void fft_dit(C *buf, int nlines, int lstride, int est
             const int line = j % nlines, bf = j / nlines;
             const int grp = bf >> st, pos = bf & (hs - 1);
             const int i0 = (grp << (st + 1)) + pos;
-            C *p0 = buf + line * lstride + i0 * estride;
+            C *p0 = buf + line * lstride + (line >= gap_at ? gap : 0) + i0 * estride;
             C *p1 = p0 + hs * estride;
-            C w = tw[pos << tsh];
-            if (inv) w.y = -w.y;
             const C a = *p0;
-            const C t = cmul(*p1, w);
+            const C t = twiddle(*p1, st, pos, tsh, tw, inv);
             *p0 = cadd(a, t);
             *p1 = csub(a, t);
         }
         __syncthreads();
     }
+}
+
+// Plan record and local patch index of a work item.
+__device__ __forceinline__ const PlanPtrs &item_plan(const Items &it, int item, int &p) {
+    if (it.items) {
+        const int2 v = it.items[item];
+        p = v.y;
+        return it.plans[v.x];
+    }
+    p = item;
+    return it.plans[0];
 }
 
 template <int LOG2M, typename C>
@@ -113,15 +141,16 @@ __device__ __forceinline__ void load_twiddles(C *s_tw, const C *tw) {
 // read from f (nodes at index N are zero); otherwise a dense nin^3 real array.
 // ---------------------------------------------------------------------------
 struct FwdXArgs {
-    const void *src;
-    void *out;        // complex R: [slab][line][M/2+1]
-    int N, n, np;     // patch geometry (PATCH)
+    const void *src;  // dense input (not PATCH)
+    void *out;        // complex R: [slab][line][M/2+1] (not PATCH)
+    int N, n, np;     // patch geometry (PATCH: n only; N, np per plan)
     int nin;          // input nodes per axis
     int lines_cta;    // lines per CTA
     const void *tw;   // complex R twiddles
+    Items it;         // PATCH: work items
 };
 
-template <int LOG2M, typename TF, bool PATCH, typename R>
+template <int LOG2M, typename TF, bool PATCH, typename R, bool SLAB = false>
 __global__ void __launch_bounds__(256) k_fwd_x(FwdXArgs a) {
     using C = typename Cx<R>::T;
     constexpr int M = 1 << LOG2M, MH = M / 2 + 1, LS = M + 1;
@@ -134,21 +163,31 @@ __global__ void __launch_bounds__(256) k_fwd_x(FwdXArgs a) {
     load_twiddles<LOG2M>(s_tw, (const C *)a.tw);
     for (int e = threadIdx.x; e < nl * LS; e += blockDim.x) buf[e] = Cx<R>::mk(0, 0);
     __syncthreads();
-    const int zi = slab % a.nin, p = slab / a.nin;
+    const int zi = slab % a.nin;
+    int p = slab / a.nin, N = a.N, np = a.np;
+    const void *src = a.src;
+    void *outp = a.out;
+    if (PATCH) {
+        const PlanPtrs &P = item_plan(a.it, slab / a.nin, p);
+        src = P.f;
+        outp = P.a1;
+        N = P.N;
+        np = P.np;
+    }
     for (int e = threadIdx.x; e < nl * a.nin; e += blockDim.x) {
         const int l = e / a.nin, m = e % a.nin;
         const int yi = line0 + l;
         R v;
         if (PATCH) {
-            const int i2 = p % a.np, i1 = (p / a.np) % a.np, i0 = p / (a.np * a.np);
+            const int i2 = p % np, i1 = (p / np) % np, i0 = p / (np * np);
             const int z = i0 * a.n + zi, y = i1 * a.n + yi, x = i2 * a.n + m;
             v = 0;
-            if (z < a.N && y < a.N && x < a.N) {
-                const TF *f = (const TF *)a.src;
+            if (z < N && y < N && x < N) {
+                const TF *f = (const TF *)src;
                 R w = (zi == 0 || zi == a.n) ? R(0.5) : R(1);
                 w *= (yi == 0 || yi == a.n) ? R(0.5) : R(1);
                 w *= (m == 0 || m == a.n) ? R(0.5) : R(1);
-                v = w * (R)f[((long)z * a.N + y) * a.N + x];
+                v = w * (R)f[((long)z * N + y) * N + x];
             }
         } else {
             const double *F = (const double *)a.src;
@@ -158,10 +197,17 @@ __global__ void __launch_bounds__(256) k_fwd_x(FwdXArgs a) {
     }
     __syncthreads();
     fft_dif<LOG2M>(buf, nl, LS, 1, s_tw, false);
-    C *out = (C *)a.out;
-    for (int e = threadIdx.x; e < nl * MH; e += blockDim.x) {
-        const int l = e / MH, kx = e % MH;
-        out[((long)slab * a.nin + line0 + l) * MH + kx] = buf[l * LS + brev_bits(kx, LOG2M)];
+    C *out = (C *)outp;
+    if (SLAB) {  // layout [p][kx][zi][yi]: one contiguous nin x nin block per (p, kx)
+        for (int e = threadIdx.x; e < nl * MH; e += blockDim.x) {
+            const int kx = e / nl, l = e % nl;
+            out[(((long)p * MH + kx) * a.nin + zi) * a.nin + line0 + l] = buf[l * LS + brev_bits(kx, LOG2M)];
+        }
+    } else {     // layout [slab][line][kx]
+        for (int e = threadIdx.x; e < nl * MH; e += blockDim.x) {
+            const int l = e / MH, kx = e % MH;
+            out[((long)slab * a.nin + line0 + l) * MH + kx] = buf[l * LS + brev_bits(kx, LOG2M)];
+        }
     }
 }
 
@@ -257,7 +303,7 @@ struct InvXArgs {
     const void *tw;
 };
 
-template <int LOG2M, typename R, typename TO>
+template <int LOG2M, typename R, typename TO, bool SLAB = false>
 __global__ void __launch_bounds__(256) k_inv_x(InvXArgs a) {
     using C = typename Cx<R>::T;
     constexpr int M = 1 << LOG2M, MH = M / 2 + 1, LS = M + 1;
@@ -268,17 +314,31 @@ __global__ void __launch_bounds__(256) k_inv_x(InvXArgs a) {
     const int r0 = blockIdx.y * a.lines_cta;
     const int nl = min(a.lines_cta, a.nrow - r0);
     load_twiddles<LOG2M>(s_tw, (const C *)a.tw);
-    const C *in = (const C *)a.in + ((long)slab * a.nrow + r0) * MH;
-    for (int e = threadIdx.x; e < nl * M; e += blockDim.x) {
-        const int l = e / M, k = e % M;
-        C v;
-        if (k < MH) {
-            v = in[l * MH + k];
-        } else {
-            v = in[l * MH + (M - k)];
-            v.y = -v.y;
+    if (SLAB) {  // input [slab][kx][row]: contiguous block, transposed into rows
+        const C *in = (const C *)a.in + (long)slab * MH * a.nrow;
+        for (int e = threadIdx.x; e < MH * nl; e += blockDim.x) {
+            const int k = e / nl, l = e % nl;
+            const C v = in[(long)k * a.nrow + r0 + l];
+            buf[l * LS + k] = v;
+            if (k > 0 && k < M - k) {
+                C c = v;
+                c.y = -c.y;
+                buf[l * LS + (M - k)] = c;
+            }
         }
-        buf[l * LS + k] = v;
+    } else {
+        const C *in = (const C *)a.in + ((long)slab * a.nrow + r0) * MH;
+        for (int e = threadIdx.x; e < nl * M; e += blockDim.x) {
+            const int l = e / M, k = e % M;
+            C v;
+            if (k < MH) {
+                v = in[l * MH + k];
+            } else {
+                v = in[l * MH + (M - k)];
+                v.y = -v.y;
+            }
+            buf[l * LS + k] = v;
+        }
     }
     __syncthreads();
     fft_dif<LOG2M>(buf, nl, LS, 1, s_tw, true);
@@ -292,28 +352,376 @@ __global__ void __launch_bounds__(256) k_inv_x(InvXArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Fused local-convolution slab: one CTA per (patch p, kx).  The (ky, kz) slab
+// of the patch spectrum (M x M complex) stays in shared memory through the
+// forward y and z transforms, the product with the kernel spectrum and the
+// inverse z and y transforms.  In: [p][kx][zi][yi] (nin x nin); out:
+// [p][zo][kx][yo] (nout x nout) from positions (out_off + t) mod M.
+// Row y of the slab at S + y * (M + 1), column z contiguous.
+// ---------------------------------------------------------------------------
+struct SlabArgs {
+    const void *tw;
+    int nin, nout, out_off;
+    Items it;  // per item: in = a1, out = a4, khat of its plan
+    int nz;    // output z rows: zrow[j] in [0, nout), the rows the inverse-x step reads
+    int zrow[64];
+};
+
+template <int LOG2M, typename R>
+__global__ void __launch_bounds__(256) k_slab(SlabArgs a) {
+    using C = typename Cx<R>::T;
+    constexpr int M = 1 << LOG2M, MH = M / 2 + 1, P = M + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *s_tw = (C *)smem_raw;
+    C *S = s_tw + M / 2;
+    const int kx = blockIdx.x % MH;
+    int p;
+    const PlanPtrs &PP = item_plan(a.it, blockIdx.x / MH, p);
+    const int nin = a.nin, W = a.nout;
+    load_twiddles<LOG2M>(s_tw, (const C *)a.tw);
+    for (int e = threadIdx.x; e < M * P; e += blockDim.x) S[e] = Cx<R>::mk(0, 0);
+    __syncthreads();
+    const C *in = (const C *)PP.a1 + ((long)p * MH + kx) * nin * nin;
+    for (int e = threadIdx.x; e < nin * nin; e += blockDim.x) {
+        const int zi = e / nin, yi = e % nin;
+        S[yi * P + zi] = in[e];
+    }
+    __syncthreads();
+    // forward y on the nin nonzero z columns (natural in, bit-reversed ky out)
+    fft_dif<LOG2M>(S, nin, 1, P, s_tw, false);
+    // forward z on all rows (bit-reversed kz out)
+    fft_dif<LOG2M>(S, M, P, 1, s_tw, false);
+    // x real-even kernel spectrum at (kx, ky, kz)
+    const R *khat = (const R *)PP.khat;
+    for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
+        const int r = e / M, c = e % M;
+        const int ky0 = brev_bits(r, LOG2M), kz0 = brev_bits(c, LOG2M);
+        const int ky = ky0 < M - ky0 ? ky0 : M - ky0;
+        const int kz = kz0 < M - kz0 ? kz0 : M - kz0;
+        const R k = khat[((long)kx * MH + ky) * MH + kz];
+        C v = S[r * P + c];
+        v.x *= k;
+        v.y *= k;
+        S[r * P + c] = v;
+    }
+    __syncthreads();
+    // inverse z on all rows (bit-reversed in, natural z out)
+    fft_dit<LOG2M>(S, M, P, 1, s_tw, true);
+    // inverse y on the output z columns only: positions [0, hi] and [lo2, M)
+    int pos0 = a.out_off % M;
+    if (pos0 < 0) pos0 += M;
+    // output positions (out_off + t) mod M, t < W: one wrapped range starting at pos0
+    const int n1 = (pos0 + W <= M) ? W : M - pos0;  // columns pos0 .. pos0+n1-1, then 0 ..
+    fft_dit<LOG2M>(S + pos0, W, 1, P, s_tw, true, n1, -(pos0 + n1));
+    C *out = (C *)PP.a4 + (long)p * a.nz * MH * W;
+    for (int e = threadIdx.x; e < a.nz * W; e += blockDim.x) {
+        const int jz = e / W, yo = e % W, zo = a.zrow[jz];
+        int pz = (a.out_off + zo) % M, py = (a.out_off + yo) % M;
+        if (pz < 0) pz += M;
+        if (py < 0) py += M;
+        out[((long)jz * MH + kx) * W + yo] = S[py * P + pz];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 64-point FFT of one line by 8 threads (radix 8 x 8, registers + one
+// exchange through the line's own shared-memory storage).  n = 8 n2 + n1,
+// k = k1 + 8 k2:  Y[n1][k1] = w64^(n1 k1) sum_n2 x[8 n2 + n1] w8^(n2 k1),
+// X[k1 + 8 k2] = sum_n1 Y[n1][k1] w8^(n1 k2).  Input and output natural order.
+// Every lane of the warp must call it (it uses __syncwarp); `valid` masks the
+// memory accesses of lanes whose line does not exist.
+// ---------------------------------------------------------------------------
+template <typename C, typename R>
+__device__ __forceinline__ C w8mul(C d, int j, bool inv) {
+    const R s = (R)0.70710678118654752440;
+    C r;
+    switch (j) {
+        case 0: r = d; break;
+        case 1:
+            if (!inv) { r.x = (d.x + d.y) * s; r.y = (d.y - d.x) * s; }
+            else { r.x = (d.x - d.y) * s; r.y = (d.x + d.y) * s; }
+            break;
+        case 2: r = mul_mi(d, inv); break;
+        default:
+            if (!inv) { r.x = (d.y - d.x) * s; r.y = -(d.x + d.y) * s; }
+            else { r.x = -(d.x + d.y) * s; r.y = (d.x - d.y) * s; }
+            break;
+    }
+    return r;
+}
+
+// In-register 8-point DFT (natural order in and out).
+template <typename C, typename R>
+__device__ __forceinline__ void dft8(C (&v)[8], bool inv) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const C a = v[i], b = v[i + 4];
+        v[i] = cadd(a, b);
+        v[i + 4] = w8mul<C, R>(csub(a, b), i, inv);
+    }
+#pragma unroll
+    for (int g = 0; g < 8; g += 4)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const C a = v[g + i], b = v[g + i + 2];
+            v[g + i] = cadd(a, b);
+            v[g + i + 2] = w8mul<C, R>(csub(a, b), 2 * i, inv);
+        }
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) {
+        const C a = v[i], b = v[i + 1];
+        v[i] = cadd(a, b);
+        v[i + 1] = csub(a, b);
+    }
+    // bit-reversed -> natural
+    C t = v[1]; v[1] = v[4]; v[4] = t;
+    t = v[3]; v[3] = v[6]; v[6] = t;
+}
+
+template <typename C, typename R>
+__device__ __forceinline__ void fft64_line(C *line, int estride, int t, bool valid, int nvalid,
+                                           const C *tw64, bool inv) {
+    C v[8];
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2) {
+        const int pos = 8 * n2 + t;
+        v[n2] = (valid && pos < nvalid) ? line[pos * estride] : Cx<R>::mk(0, 0);
+    }
+    dft8<C, R>(v, inv);
+#pragma unroll
+    for (int k1 = 1; k1 < 8; ++k1) {
+        C w = tw64[(t * k1) & 63];
+        if (inv) w.y = -w.y;
+        v[k1] = cmul(v[k1], w);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1)
+        if (valid) line[(8 * k1 + t) * estride] = v[k1];
+    __syncwarp();
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) v[n1] = valid ? line[(8 * t + n1) * estride] : Cx<R>::mk(0, 0);
+    dft8<C, R>(v, inv);
+    __syncwarp();
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2)
+        if (valid) line[(t + 8 * k2) * estride] = v[k2];
+    __syncwarp();
+}
+
+// Apply fft64_line to nlines lines; line l at base + off(l) (lstride, plus
+// `gap` for l >= gap_at).  Ends with __syncthreads.
+template <typename C, typename R>
+__device__ __forceinline__ void fft64_lines(C *base, int nlines, int lstride, int estride, int nvalid,
+                                            const C *tw64, bool inv, int gap_at = 1 << 30, int gap = 0) {
+    const int grp = threadIdx.x >> 3, t = threadIdx.x & 7, ngrp = blockDim.x >> 3;
+    for (int l0 = 0; l0 < nlines; l0 += ngrp) {  // uniform trip count across the CTA
+        const int l = l0 + grp;
+        const bool valid = l < nlines;
+        C *line = base + (valid ? l * lstride + (l >= gap_at ? gap : 0) : 0);
+        fft64_line<C, R>(line, estride, t, valid, nvalid, tw64, inv);
+    }
+    __syncthreads();
+}
+
+// Fused slab for M = 64 with the register FFT (same contract as k_slab).
+template <typename R>
+__global__ void __launch_bounds__(256) k_slab64(SlabArgs a) {
+    using C = typename Cx<R>::T;
+    constexpr int M = 64, MH = 33, P = 65;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw64 = (C *)smem_raw;  // 64 twiddles exp(-2 pi i j / 64)
+    C *S = tw64 + M;
+    const int kx = blockIdx.x % MH;
+    int p;
+    const PlanPtrs &PP = item_plan(a.it, blockIdx.x / MH, p);
+    const int nin = a.nin, W = a.nout;
+    const C *tw = (const C *)a.tw;  // M/2 entries; extend by w^(j+32) = -w^j
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        C w = tw[j & 31];
+        if (j >= 32) { w.x = -w.x; w.y = -w.y; }
+        tw64[j] = w;
+    }
+    const C *in = (const C *)PP.a1 + ((long)p * MH + kx) * nin * nin;
+    for (int e = threadIdx.x; e < nin * nin; e += blockDim.x) {
+        const int zi = e / nin, yi = e % nin;
+        S[yi * P + zi] = in[e];
+    }
+    __syncthreads();
+    // forward y on the nin nonzero z columns (rows >= nin read as zero)
+    fft64_lines<C, R>(S, nin, 1, P, nin, tw64, false);
+    // forward z on all rows (columns >= nin read as zero)
+    fft64_lines<C, R>(S, M, P, 1, nin, tw64, false);
+    const R *khat = (const R *)PP.khat;
+    for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
+        const int r = e / M, c = e % M;
+        const int ky = r < M - r ? r : M - r;
+        const int kz = c < M - c ? c : M - c;
+        const R k = khat[((long)kx * MH + ky) * MH + kz];
+        C v = S[r * P + c];
+        v.x *= k;
+        v.y *= k;
+        S[r * P + c] = v;
+    }
+    __syncthreads();
+    fft64_lines<C, R>(S, M, P, 1, M, tw64, true);
+    int pos0 = a.out_off % M;
+    if (pos0 < 0) pos0 += M;
+    const int n1 = (pos0 + W <= M) ? W : M - pos0;
+    fft64_lines<C, R>(S + pos0, W, 1, P, M, tw64, true, n1, -(pos0 + n1));
+    C *out = (C *)PP.a4 + (long)p * a.nz * MH * W;
+    for (int e = threadIdx.x; e < a.nz * W; e += blockDim.x) {
+        const int jz = e / W, yo = e % W, zo = a.zrow[jz];
+        int pz = (a.out_off + zo) % M, py = (a.out_off + yo) % M;
+        if (pz < 0) pz += M;
+        if (py < 0) py += M;
+        out[((long)jz * MH + kx) * W + yo] = S[py * P + pz];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Inverse real transform along x of the local fields, pruned to the values
+// the later steps read: the coarse lattice of the field box (for Delta^H, and
+// the coarse points of the interpolation stencils) and the patch-face planes
+// inside Omega_alpha (for phi^i - I^H(phi^i)).  One CTA per (patch, z row of
+// the field box).  Rows that need an alpha range or the coarse x values get a
+// full inverse FFT; rows that only need x on the face planes get direct sums
+// over the half spectrum.
+//   cl[p][k0][k1][k2]  = phi^i(4k), k in [-s/4, (n+s)/4]^3
+//   fp[p][slot][u][v]  = phi^i on face plane slot (axis * npa + j, plane
+//                        x_axis = pl0 + j n), (u, v) the other two coordinates
+//                        in [-ga, n+ga], increasing axis order.
+// ---------------------------------------------------------------------------
+struct InvXPArgs {
+    Items it;         // per item: in = a4 [p][zo][kx][yo], out = cl, fp of its plan
+    const void *tw;   // M/2 twiddles exp(-2 pi i j / M)
+    int n, s, W, ga, npa, pl0, wa, nc;
+    int nz;           // z rows with outputs; zrow[j] = their index zo in [0, W)
+    int zrow[64];
+};
+
+__device__ __forceinline__ bool in_alpha(int c, int n, int ga) { return c >= -ga && c <= n + ga; }
+__device__ __forceinline__ bool on_plane(int c, int n, int ga, int pl0) {
+    return in_alpha(c, n, ga) && ((c - pl0) % n) == 0;
+}
+
+template <int LOG2M, typename R>
+__global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
+    using C = typename Cx<R>::T;
+    constexpr int M = 1 << LOG2M, MH = M / 2 + 1, LP = M + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int rows[64];
+    __shared__ int nfft_s;
+    const int W = a.W, n = a.n, s = a.s, ga = a.ga, pl0 = a.pl0, wa = a.wa, nc = a.nc;
+    C *tw = (C *)smem_raw;   // M twiddles
+    C *raw = tw + M;         // MH x W
+    C *buf = raw + MH * W;   // up to W lines of LP
+    const int jz = blockIdx.x % a.nz, zi = a.zrow[jz];
+    int p;
+    const PlanPtrs &PP = item_plan(a.it, blockIdx.x / a.nz, p);
+    const int z = zi - s;
+    const C *twg = (const C *)a.tw;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        C w = twg[j & (M / 2 - 1)];
+        if (j >= M / 2) { w.x = -w.x; w.y = -w.y; }
+        tw[j] = w;
+    }
+    const C *in = (const C *)PP.a4 + ((long)p * a.nz + jz) * MH * W;
+    for (int e = threadIdx.x; e < MH * W; e += blockDim.x) raw[e] = in[e];
+    const bool zP = on_plane(z, n, ga, pl0), zA = in_alpha(z, n, ga), zC = (z & 3) == 0;
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int yi = 0; yi < W; ++yi) {
+            const int y = yi - s;
+            const bool yA = in_alpha(y, n, ga), yP = on_plane(y, n, ga, pl0), yC = (y & 3) == 0;
+            if ((zP && yA) || (yP && zA) || (zC && yC)) rows[c++] = yi;
+        }
+        nfft_s = c;
+    }
+    __syncthreads();
+    const int nfft = nfft_s;
+    for (int e = threadIdx.x; e < nfft * M; e += blockDim.x) {
+        const int l = e / M, k = e % M, yi = rows[l];
+        C v;
+        if (k < MH) {
+            v = raw[k * W + yi];
+        } else {
+            v = raw[(M - k) * W + yi];
+            v.y = -v.y;
+        }
+        buf[l * LP + k] = v;
+    }
+    __syncthreads();
+    if (LOG2M == 6) fft64_lines<C, R>(buf, nfft, LP, 1, M, tw, true);
+    else fft_dif<LOG2M>(buf, nfft, LP, 1, tw, true);
+    R *cl = (R *)PP.cl + (long)p * nc * nc * nc;
+    R *fp = (R *)PP.fp + (long)p * 3 * a.npa * wa * wa;
+    const int kl = -s / 4;
+    // outputs of the transformed rows
+    for (int e = threadIdx.x; e < nfft * W; e += blockDim.x) {
+        const int l = e / W, xi = e % W, yi = rows[l];
+        const int x = xi - s, y = yi - s;
+        const bool yA = in_alpha(y, n, ga), yP = on_plane(y, n, ga, pl0), yC = (y & 3) == 0;
+        const bool xA = in_alpha(x, n, ga), xP = on_plane(x, n, ga, pl0), xC = (x & 3) == 0;
+        const bool wC = zC && yC && xC, w0 = zP && yA && xA, w1 = yP && zA && xA, w2 = zA && yA && xP;
+        if (!(wC || w0 || w1 || w2)) continue;
+        int pos = x % M;
+        if (pos < 0) pos += M;
+        const R v = buf[l * LP + (LOG2M == 6 ? pos : brev_bits(pos, LOG2M))].x;
+        if (wC) cl[((long)((z >> 2) - kl) * nc + ((y >> 2) - kl)) * nc + ((x >> 2) - kl)] = v;
+        if (w0) fp[(((long)(0 * a.npa + (z - pl0) / n)) * wa + (y + ga)) * wa + (x + ga)] = v;
+        if (w1) fp[(((long)(1 * a.npa + (y - pl0) / n)) * wa + (z + ga)) * wa + (x + ga)] = v;
+        if (w2) fp[(((long)(2 * a.npa + (x - pl0) / n)) * wa + (z + ga)) * wa + (y + ga)] = v;
+    }
+    // rows that only need x on the face planes: direct sums over the half spectrum
+    if (zA) {
+        for (int e = threadIdx.x; e < W * a.npa; e += blockDim.x) {
+            const int yi = e / a.npa, j = e % a.npa;
+            const int y = yi - s;
+            const bool yA = in_alpha(y, n, ga), yP = on_plane(y, n, ga, pl0), yC = (y & 3) == 0;
+            if (!yA || zP || yP || (zC && yC)) continue;  // not needed, or done by an FFT row
+            const int x = pl0 + j * n;
+            int pos = x % M;
+            if (pos < 0) pos += M;
+            R acc = 0;
+            for (int k = 0; k < MH; ++k) {
+                const C X = raw[k * W + yi];
+                C w = tw[(k * pos) & (M - 1)];  // exp(+2 pi i k pos / M) = conj(tw)
+                const R re = X.x * w.x + X.y * w.y;
+                acc += (k == 0 || 2 * k == M) ? re : (R)2 * re;
+            }
+            fp[(((long)(2 * a.npa + j)) * wa + (z + ga)) * wa + (y + ga)] = acc;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Legendre coefficients c_p^i = sum_m W[m] Q^p(m) f[n i + m] (Boole, R3).
 // ---------------------------------------------------------------------------
-template <typename TF>
-__global__ void __launch_bounds__(256) k_moments(const TF *__restrict__ f, int N, int n, int np,
-                                                 int npoly, const double *__restrict__ momw,
-                                                 double *__restrict__ mom) {
+template <typename TF, typename RM>
+__global__ void __launch_bounds__(256) k_moments(Items it, int n, int npoly) {
     __shared__ double red[8][56];
-    const int p = blockIdx.x;
+    int p;
+    const PlanPtrs &PP = item_plan(it, blockIdx.x, p);
+    const RM *__restrict__ momw = (const RM *)PP.momw;
+    const TF *f = (const TF *)PP.f;
+    const int N = PP.N, np = PP.np;
+    double *mom = PP.mom;
+    float *mom_f = PP.mom_f;
     const int i2 = p % np, i1 = (p / np) % np, i0 = p / (np * np);
     const int nb = n + 1, nb3 = nb * nb * nb;
-    double acc[56];
-    for (int k = 0; k < npoly; ++k) acc[k] = 0.0;
+    RM acc[56];
+    for (int k = 0; k < npoly; ++k) acc[k] = 0;
     for (int m = threadIdx.x; m < nb3; m += blockDim.x) {
         const int m2 = m % nb, m1 = (m / nb) % nb, m0 = m / (nb * nb);
         const int z = i0 * n + m0, y = i1 * n + m1, x = i2 * n + m2;
         if (z >= N || y >= N || x >= N) continue;
-        const double v = (double)f[((long)z * N + y) * N + x];
+        const RM v = (RM)f[((long)z * N + y) * N + x];
         for (int k = 0; k < npoly; ++k) acc[k] = fma(momw[(long)k * nb3 + m], v, acc[k]);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = 0; k < npoly; ++k) {
-        double v = acc[k];
+        double v = (double)acc[k];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) red[warp][k] = v;
     }
@@ -322,37 +730,85 @@ __global__ void __launch_bounds__(256) k_moments(const TF *__restrict__ f, int N
         double v = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
         mom[(long)p * npoly + threadIdx.x] = v;
+        if (mom_f) mom_f[(long)p * npoly + threadIdx.x] = (float)v;
     }
 }
 
-// r^i[a] = phi^i[g_a] - I^H(phi^i)(g_a) on the face nodes of Omega_alpha.
+// r^i = phi^i - I^H(phi^i) on the face planes of patch i inside Omega_alpha
+// (FP64 arithmetic).  One CTA per (patch, plane); the in-plane interpolant
+// is applied separably: first along v on the coarse rows u = 4k, then along u.
+// resid[p][slot][u + ga][v + ga], slot = axis * npa + j for the plane
+// x_axis = pl0 + j n (relative), (u, v) the other two coordinates.
+struct ResArgs {
+    Items it;  // per item: cl, fp -> resid of its plan
+    int n, s, ga, b, npa, pl0, wa, nc;
+    double lw[4][8];
+};
+
 template <typename TB>
-__global__ void __launch_bounds__(256) k_resid(const TB *__restrict__ box, long W3, int na,
-                                               int S, const int *__restrict__ a_self,
-                                               const int *__restrict__ a_off,
-                                               const double *__restrict__ a_w,
-                                               double *__restrict__ resid) {
-    const int p = blockIdx.x;
-    const int a = blockIdx.y * blockDim.x + threadIdx.x;
-    if (a >= na) return;
-    const TB *bx = box + (long)p * W3;
-    double acc = 0.0;
-    for (int j = 0; j < S; ++j) acc = fma(a_w[(long)a * S + j], (double)bx[a_off[(long)a * S + j]], acc);
-    resid[(long)p * na + a] = (double)bx[a_self[a]] - acc;
+__global__ void __launch_bounds__(256) k_resid(ResArgs a) {
+    extern __shared__ double rsm[];
+    const int slot = blockIdx.y;
+    int p;
+    const PlanPtrs &PP = item_plan(a.it, blockIdx.x, p);
+    const int axis = slot / a.npa, c4 = (a.pl0 + (slot % a.npa) * a.n) / 4;
+    const int K = 2 * a.b + 2, wa = a.wa, nc = a.nc, kl = -a.s / 4;
+    const int klo = -a.ga / 4 - a.b;  // coarse rows the stencils reach (4 | ga, 4 | n)
+    const int khi = (a.n + a.ga) / 4 + a.b;
+    const int nk = khi - klo + 1;
+    double *T = rsm;                  // nk x wa: interpolated along v on coarse rows u = 4k
+    const TB *cl = (const TB *)PP.cl + (long)p * nc * nc * nc;
+    const TB *fp = (const TB *)PP.fp + ((long)p * gridDim.y + slot) * wa * wa;
+    // phi^i at the coarse point (u, v) = (4 ka, 4 kb) of this plane
+    auto clp = [&](int ka, int kb) -> double {
+        int i0, i1, i2;
+        if (axis == 0) { i0 = c4; i1 = ka; i2 = kb; }
+        else if (axis == 1) { i0 = ka; i1 = c4; i2 = kb; }
+        else { i0 = ka; i1 = kb; i2 = c4; }
+        return (double)cl[((long)(i0 - kl) * nc + (i1 - kl)) * nc + (i2 - kl)];
+    };
+    for (int e = threadIdx.x; e < nk * wa; e += blockDim.x) {
+        const int k = klo + e / wa, v = e % wa - a.ga;
+        const int rv = v & 3;
+        double t;
+        if (rv == 0) {
+            t = clp(k, v >> 2);
+        } else {
+            const int k0 = (v >> 2) - a.b;
+            t = 0.0;
+            for (int j = 0; j < K; ++j) t = fma(a.lw[rv][j], clp(k, k0 + j), t);
+        }
+        T[e] = t;
+    }
+    __syncthreads();
+    double *out = PP.resid + ((long)p * gridDim.y + slot) * wa * wa;
+    for (int e = threadIdx.x; e < wa * wa; e += blockDim.x) {
+        const int u = e / wa - a.ga, v = e % wa - a.ga;
+        const int ru = u & 3;
+        double iv;
+        if (ru == 0) {
+            iv = T[((u >> 2) - klo) * wa + (v + a.ga)];
+        } else {
+            const int k0 = (u >> 2) - a.b;
+            iv = 0.0;
+            for (int j = 0; j < K; ++j) iv = fma(a.lw[ru][j], T[(k0 + j - klo) * wa + (v + a.ga)], iv);
+        }
+        out[e] = (double)fp[e] - iv;
+    }
 }
 
 struct AsmArgs {
-    const void *box;
-    const double *mom, *T;
+    const void *cl;          // coarse lattice of the local fields, nc^3 per patch
+    const void *mom, *T;     // ring tables in the ring precision RT
     double *FH;
-    int np, n, s, W, npoly, flo, nf;
+    int np, n, s, nc, npoly, flo, nf;
     int ca_lo, ca_hi, cb_lo, cb_hi;
     double coef[4];  // b_k / H^2
 };
 
 // F^H[k] = sum over patches i (ascending) of Delta^H phi^{i,h} on C(Omega_alpha(i))
 // or sum_p c_p^i Delta^H(G^h * Q^p) on C(Omega_beta(i)) \ C(Omega_alpha(i)).
-template <typename TB>
+template <typename TB, typename RT>
 __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const long tot = (long)a.nf * a.nf * a.nf;
@@ -368,7 +824,7 @@ __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
         hi[d] = min(a.np - 1, floordiv(k[d] - a.cb_lo, q));
     }
     const int ncb = a.cb_hi - a.cb_lo + 1;
-    const long W = a.W;
+    const long nc = a.nc, kl = -a.s / 4;
     double acc = 0.0;
     for (int i0 = lo[0]; i0 <= hi[0]; ++i0)
         for (int i1 = lo[1]; i1 <= hi[1]; ++i1)
@@ -378,7 +834,7 @@ __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
                 const bool inA = r0 >= a.ca_lo && r0 <= a.ca_hi && r1 >= a.ca_lo &&
                                  r1 <= a.ca_hi && r2 >= a.ca_lo && r2 <= a.ca_hi;
                 if (inA) {
-                    const TB *bx = (const TB *)a.box + p * W * W * W;
+                    const TB *bx = (const TB *)a.cl + p * nc * nc * nc;
                     double lap = 0.0;
                     for (int s0 = -1; s0 <= 1; ++s0)
                         for (int s1 = -1; s1 <= 1; ++s1)
@@ -386,32 +842,35 @@ __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
                                 const int nz = (s0 != 0) + (s1 != 0) + (s2 != 0);
                                 const double c = a.coef[nz];
                                 if (c == 0.0) continue;
-                                const long x0 = 4 * (r0 + s0) + a.s, x1 = 4 * (r1 + s1) + a.s,
-                                           x2 = 4 * (r2 + s2) + a.s;
-                                lap = fma(c, (double)bx[(x0 * W + x1) * W + x2], lap);
+                                const long x0 = r0 + s0 - kl, x1 = r1 + s1 - kl, x2 = r2 + s2 - kl;
+                                lap = fma(c, (double)bx[(x0 * nc + x1) * nc + x2], lap);
                             }
                     acc += lap;
                 } else {
                     const long t = (((long)(r0 - a.cb_lo) * ncb + (r1 - a.cb_lo)) * ncb +
                                     (r2 - a.cb_lo)) * a.npoly;
-                    const double *c = a.mom + p * a.npoly;
-                    double v = 0.0;
-                    for (int pp = 0; pp < a.npoly; ++pp) v = fma(c[pp], a.T[t + pp], v);
-                    acc += v;
+                    const RT *c = (const RT *)a.mom + p * a.npoly;
+                    const RT *Tt = (const RT *)a.T + t;
+                    RT v = 0;
+                    for (int pp = 0; pp < a.npoly; ++pp) v = fma(c[pp], Tt[pp], v);
+                    acc += (double)v;
                 }
             }
     a.FH[idx] = acc;
 }
 
 struct BndArgs {
-    const double *phiH, *resid, *mom, *D;
-    const int *amap, *rmap;
+    const double *phiH, *resid;
+    const void *mom, *D;     // ring tables in the ring precision RT
+    const int *rmap;
     double *phiB;
-    int N, n, np, ga, gb, b, npoly, na, olo, no, wa, wbx;
+    int N, n, np, ga, gb, b, npoly, olo, no, wa, wbx, npa, pl0;
     double lw[4][8];  // Lagrange weights for g mod 4 = r (row r), 2b+2 entries
 };
 
-// phi^B at every face-plane node (axis, plane j, u, v).
+// phi^B at every face-plane node (axis, plane j, u, v).  RT: precision of the
+// Legendre ring sums (FP64 tier: double; split tier: float).
+template <typename RT>
 __global__ void __launch_bounds__(128) k_boundary(BndArgs a) {
     const long pn = (long)(a.N + 1) * (a.N + 1);
     const long tot = 3L * (a.np + 1) * pn;
@@ -465,102 +924,141 @@ __global__ void __launch_bounds__(128) k_boundary(BndArgs a) {
                 const bool inA = i0 >= alo[0] && i0 <= ahi[0] && i1 >= alo[1] && i1 <= ahi[1] &&
                                  i2 >= alo[2] && i2 <= ahi[2];
                 if (inA) {
-                    const int ai = a.amap[((long)(r0 + a.ga) * a.wa + (r1 + a.ga)) * a.wa + (r2 + a.ga)];
-                    acc += a.resid[p * a.na + ai];
+                    // the residual plane holding r: first axis on a face plane
+                    int d, uu, vv;
+                    if ((r0 - a.pl0) % a.n == 0) { d = 0; uu = r1; vv = r2; }
+                    else if ((r1 - a.pl0) % a.n == 0) { d = 1; uu = r0; vv = r2; }
+                    else { d = 2; uu = r0; vv = r1; }
+                    const int rr = d == 0 ? r0 : (d == 1 ? r1 : r2);
+                    const long slot = (long)d * a.npa + (rr - a.pl0) / a.n;
+                    acc += a.resid[((p * 3 * a.npa + slot) * a.wa + (uu + a.ga)) * a.wa + (vv + a.ga)];
                 } else {
                     const int ri = a.rmap[((long)(r0 + a.gb) * a.wbx + (r1 + a.gb)) * a.wbx + (r2 + a.gb)];
-                    const double *c = a.mom + p * a.npoly;
-                    const double *Dr = a.D + (long)ri * a.npoly;
-                    double vv = 0.0;
+                    const RT *c = (const RT *)a.mom + p * a.npoly;
+                    const RT *Dr = (const RT *)a.D + (long)ri * a.npoly;
+                    RT vv = 0;
                     for (int pp = 0; pp < a.npoly; ++pp) vv = fma(c[pp], Dr[pp], vv);
-                    acc += vv;
+                    acc += (double)vv;
                 }
             }
     a.phiB[idx] = acc;
 }
 
 struct DirArgs {
-    const void *f;
-    const double *phiB;
-    double *phi;
-    int N, n, np;
-    double h2, c2h2;
+    Items it;  // per item: f, phiB, phi, lam, N, np, h of its plan
+    int n;
     double b[4];
-    const double *sinm;  // (n-1)^2: sin(pi k m / n), k, m in [1, n-1]
-    const double *lam;   // (n-1)^3 eigenvalues (already / h^2)
+    const double *sinm;  // (n-1) x n/2: sin(pi k t / n), k in [1, n-1], t in [1, n/2]
 };
 
-__device__ __forceinline__ double phiB_at(const DirArgs &a, int g0, int g1, int g2) {
+__device__ __forceinline__ double phiB_at(const PlanPtrs &a, int n, int g0, int g1, int g2) {
     const long pn = (long)(a.N + 1) * (a.N + 1);
     int axis, j, u, v;
-    if (g0 % a.n == 0) {
-        axis = 0; j = g0 / a.n; u = g1; v = g2;
-    } else if (g1 % a.n == 0) {
-        axis = 1; j = g1 / a.n; u = g0; v = g2;
+    if (g0 % n == 0) {
+        axis = 0; j = g0 / n; u = g1; v = g2;
+    } else if (g1 % n == 0) {
+        axis = 1; j = g1 / n; u = g0; v = g2;
     } else {
-        axis = 2; j = g2 / a.n; u = g0; v = g1;
+        axis = 2; j = g2 / n; u = g0; v = g1;
     }
     return a.phiB[((long)axis * (a.np + 1) + j) * pn + (long)u * (a.N + 1) + v];
 }
 
-template <typename TF>
+// DST-I of one line of m = n-1 values held in registers (n a compile-time
+// constant), using sin(pi k (n-t)/n) = (-1)^(k+1) sin(pi k t/n): odd k take
+// x_t + x_{n-t}, even k take x_t - x_{n-t}; the middle node t = n/2 enters
+// odd k only.
+template <int NN>
+__device__ __forceinline__ void dst_line(double (&x)[NN - 1], const double *Sh) {
+    constexpr int m = NN - 1, h = NN / 2;
+    double sp[h], sm[h];
+#pragma unroll
+    for (int t = 1; t < h; ++t) {
+        sp[t] = x[t - 1] + x[NN - t - 1];
+        sm[t] = x[t - 1] - x[NN - t - 1];
+    }
+    const double mid = x[h - 1];
+    double y[m];
+#pragma unroll
+    for (int k = 1; k <= m; ++k) {
+        const double *row = Sh + (k - 1) * h;  // sin(pi k t / n), t = 1..h
+        double v = 0.0;
+        if (k & 1) {
+#pragma unroll
+            for (int t = 1; t < h; ++t) v = fma(row[t - 1], sp[t], v);
+            v = fma(row[h - 1], mid, v);
+        } else {
+#pragma unroll
+            for (int t = 1; t < h; ++t) v = fma(row[t - 1], sm[t], v);
+        }
+        y[k - 1] = v;
+    }
+#pragma unroll
+    for (int k = 0; k < m; ++k) x[k] = y[k];
+}
+
+template <typename TF, int NN>
 __global__ void __launch_bounds__(256) k_dirichlet(DirArgs a) {
     extern __shared__ double sm[];
-    const int n = a.n, nb = n + 1, m = n - 1;
+    constexpr int n = NN, nb = n + 1, m = n - 1, h = n / 2;
     double *U = sm;                  // nb^3 boundary values (interior 0)
     double *X = U + nb * nb * nb;    // m^3 work
-    double *Y = X + m * m * m;       // m^3 work
-    double *S = Y + m * m * m;       // m^2 sine matrix
-    const int p = blockIdx.x;
-    const int i2 = p % a.np, i1 = (p / a.np) % a.np, i0 = p / (a.np * a.np);
+    double *Sh = X + m * m * m;      // (n-1) x n/2 half sine table
+    int p;
+    const PlanPtrs &PP = item_plan(a.it, blockIdx.x, p);
+    const int np = PP.np, N = PP.N;
+    const int i2 = p % np, i1 = (p / np) % np, i0 = p / (np * np);
     const int o0 = i0 * n, o1 = i1 * n, o2 = i2 * n;
-    const TF *f = (const TF *)a.f;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) S[e] = a.sinm[e];
+    const TF *f = (const TF *)PP.f;
+    for (int e = threadIdx.x; e < m * h; e += blockDim.x) Sh[e] = a.sinm[e];
     for (int e = threadIdx.x; e < nb * nb * nb; e += blockDim.x) {
         const int m2 = e % nb, m1 = (e / nb) % nb, m0 = e / (nb * nb);
         const bool bnd = m0 == 0 || m0 == n || m1 == 0 || m1 == n || m2 == 0 || m2 == n;
-        U[e] = bnd ? phiB_at(a, o0 + m0, o1 + m1, o2 + m2) : 0.0;
+        U[e] = bnd ? phiB_at(PP, n, o0 + m0, o1 + m1, o2 + m2) : 0.0;
     }
     __syncthreads();
-    // right-hand side on the interior: f - Delta^h(boundary data)
+    // right-hand side: f - Delta^h(boundary data); only the layer next to the
+    // boundary sees boundary values
     for (int e = threadIdx.x; e < m * m * m; e += blockDim.x) {
         const int c2 = e % m + 1, c1 = (e / m) % m + 1, c0 = e / (m * m) + 1;
         double lap = 0.0;
-        for (int s0 = -1; s0 <= 1; ++s0)
-            for (int s1 = -1; s1 <= 1; ++s1)
-                for (int s2 = -1; s2 <= 1; ++s2) {
-                    const int nz = (s0 != 0) + (s1 != 0) + (s2 != 0);
-                    const double c = a.b[nz];
-                    if (c == 0.0) continue;
-                    lap = fma(c, U[((c0 + s0) * nb + (c1 + s1)) * nb + (c2 + s2)], lap);
-                }
+        const bool near = c0 == 1 || c0 == m || c1 == 1 || c1 == m || c2 == 1 || c2 == m;
+        if (near)
+            for (int s0 = -1; s0 <= 1; ++s0)
+                for (int s1 = -1; s1 <= 1; ++s1)
+                    for (int s2 = -1; s2 <= 1; ++s2) {
+                        const int nz = (s0 != 0) + (s1 != 0) + (s2 != 0);
+                        const double c = a.b[nz];
+                        if (c == 0.0) continue;
+                        lap = fma(c, U[((c0 + s0) * nb + (c1 + s1)) * nb + (c2 + s2)], lap);
+                    }
         const int z = o0 + c0, y = o1 + c1, x = o2 + c2;
-        const double fv = (z < a.N && y < a.N && x < a.N) ? (double)f[((long)z * a.N + y) * a.N + x] : 0.0;
-        X[e] = fv - lap / a.h2;
+        const double fv = (z < N && y < N && x < N) ? (double)f[((long)z * N + y) * N + x] : 0.0;
+        X[e] = fma(-lap, PP.inv_h2, fv);
     }
     __syncthreads();
-    // DST-I along axes 2, 1, 0; divide; DST-I back along 2, 1, 0
+    // DST-I along axes 2, 1, 0; divide by the eigenvalues; DST-I along 2, 1, 0
     for (int pass = 0; pass < 6; ++pass) {
         const int axis = 2 - (pass % 3);
-        double *src = (pass % 2 == 0) ? X : Y;
-        double *dst = (pass % 2 == 0) ? Y : X;
-        for (int e = threadIdx.x; e < m * m * m; e += blockDim.x) {
-            const int c2 = e % m, c1 = (e / m) % m, c0 = e / (m * m);
-            int kk, base, str;
-            if (axis == 2) { kk = c2; base = (c0 * m + c1) * m; str = 1; }
-            else if (axis == 1) { kk = c1; base = c0 * m * m + c2; str = m; }
-            else { kk = c0; base = c1 * m + c2; str = m * m; }
-            double v = 0.0;
-            for (int t = 0; t < m; ++t) v = fma(S[kk * m + t], src[base + t * str], v);
-            dst[e] = v;
+        for (int l = threadIdx.x; l < m * m; l += blockDim.x) {
+            const int q1 = l % m, q0 = l / m;
+            int base, str;
+            if (axis == 2) { base = (q0 * m + q1) * m; str = 1; }
+            else if (axis == 1) { base = q0 * m * m + q1; str = m; }
+            else { base = q0 * m + q1; str = m * m; }
+            double x[m];
+#pragma unroll
+            for (int t = 0; t < m; ++t) x[t] = X[base + t * str];
+            dst_line<NN>(x, Sh);
+            if (pass == 2) {
+#pragma unroll
+                for (int t = 0; t < m; ++t) x[t] *= PP.lam[base + t * str];
+            }
+#pragma unroll
+            for (int t = 0; t < m; ++t) X[base + t * str] = x[t];
         }
         __syncthreads();
-        if (pass == 2) {
-            for (int e = threadIdx.x; e < m * m * m; e += blockDim.x) Y[e] /= a.lam[e];
-            __syncthreads();
-        }
     }
-    // after 6 passes the result is in X (passes alternate X->Y->X...; pass 5 writes X)
     const double norm = (2.0 / n) * (2.0 / n) * (2.0 / n);
     for (int e = threadIdx.x; e < n * n * n; e += blockDim.x) {
         const int m2 = e % n, m1 = (e / n) % n, m0 = e / (n * n);
@@ -568,8 +1066,8 @@ __global__ void __launch_bounds__(256) k_dirichlet(DirArgs a) {
         const double u = bnd ? U[(m0 * nb + m1) * nb + m2]
                              : X[((m0 - 1) * m + (m1 - 1)) * m + (m2 - 1)] * norm;
         const int z = o0 + m0, y = o1 + m1, x = o2 + m2;
-        const long gi = ((long)z * a.N + y) * a.N + x;
-        a.phi[gi] = u + a.c2h2 * (double)f[gi];
+        const long gi = ((long)z * N + y) * N + x;
+        PP.phi[gi] = u + PP.c2h2 * (double)f[gi];
     }
 }
 
@@ -581,13 +1079,19 @@ inline size_t fft_smem_bytes(int M, int lines, int ls) {
 template <int LOG2M, typename R>
 void set_smem_attrs() {
     const int big = 200 * 1024;
-    cudaFuncSetAttribute(k_fwd_x<LOG2M, double, true, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_fwd_x<LOG2M, float, true, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_fwd_x<LOG2M, double, false, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_col<LOG2M, 0, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_col<LOG2M, 1, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_col<LOG2M, 2, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_inv_x<LOG2M, R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (LOG2M <= 6) {
+        cudaFuncSetAttribute(k_fwd_x<LOG2M, double, true, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        cudaFuncSetAttribute(k_fwd_x<LOG2M, float, true, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        cudaFuncSetAttribute(k_slab<LOG2M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        cudaFuncSetAttribute(k_slab64<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        cudaFuncSetAttribute(k_inv_x<LOG2M, R, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        cudaFuncSetAttribute(k_inv_x_pruned<LOG2M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    }
 }
 
 // One Hockney convolution pipeline (5 launches) for `nbatch` problems with
@@ -613,17 +1117,12 @@ cudaError_t run_conv_t(const ConvDesc &d, cudaStream_t st) {
     mark(d.pl, d.ev0 + 0, st);
     // 1. forward x: out A1[p][zi][yi][kx]
     {
-        FwdXArgs a{d.src, d.b0, d.N, d.n, d.np, nin, 0, d.tw};
+        FwdXArgs a{d.src, d.b0, d.N, d.n, d.np, nin, 0, d.tw, Items{}};
         a.lines_cta = (M <= 64) ? nin : 16;
         a.lines_cta = a.lines_cta > nin ? nin : a.lines_cta;
         dim3 grid(d.nbatch * nin, (nin + a.lines_cta - 1) / a.lines_cta);
         size_t sm = fft_smem_bytes<R>(M, a.lines_cta, M + 1);
-        if (d.patch) {
-            if (d.f32) k_fwd_x<LOG2M, float, true, R><<<grid, 256, sm, st>>>(a);
-            else k_fwd_x<LOG2M, double, true, R><<<grid, 256, sm, st>>>(a);
-        } else {
-            k_fwd_x<LOG2M, double, false, R><<<grid, 256, sm, st>>>(a);
-        }
+        k_fwd_x<LOG2M, double, false, R><<<grid, 256, sm, st>>>(a);
     }
     const int CC = (M <= 64) ? MH : 16;
     const int gx = (MH + CC - 1) / CC;
@@ -670,6 +1169,46 @@ cudaError_t run_conv_t(const ConvDesc &d, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Local convolutions of a set of patches: forward x (real), fused slab (y,
+// z, kernel spectrum, inverse z, inverse y), pruned inverse x.  3 launches.
+template <int LOG2M, typename R>
+cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, const void *tw,
+                             cudaStream_t st) {
+    constexpr int M = 1 << LOG2M, MH = M / 2 + 1;
+    const Geom &g = pl->g;
+    const int nin = g.nb, W = g.W, nb = it.nitems;
+    mark(pl, 1, st);
+    {
+        FwdXArgs a{nullptr, nullptr, 0, g.n, 0, nin, nin, tw, it};
+        dim3 grid(nb * nin, 1);
+        size_t sm = fft_smem_bytes<R>(M, nin, M + 1);
+        if (f32) k_fwd_x<LOG2M, float, true, R, true><<<grid, 256, sm, st>>>(a);
+        else k_fwd_x<LOG2M, double, true, R, true><<<grid, 256, sm, st>>>(a);
+    }
+    int nz = 0, zrow[64];
+    for (int zi = 0; zi < W; ++zi) {
+        const int z = zi - g.s;
+        if ((z >= -g.ga && z <= g.n + g.ga) || (z % 4 == 0)) zrow[nz++] = zi;
+    }
+    mark(pl, 2, st);
+    {
+        SlabArgs a{tw, nin, W, -g.s, it, nz, {}};
+        for (int j = 0; j < nz; ++j) a.zrow[j] = zrow[j];
+        if (LOG2M == 6)
+            k_slab64<R><<<nb * MH, 256, (size_t)(M + M * (M + 1)) * 2 * sizeof(R), st>>>(a);
+        else
+            k_slab<LOG2M, R><<<nb * MH, 256, fft_smem_bytes<R>(M, M, M + 1), st>>>(a);
+    }
+    mark(pl, 3, st);
+    {
+        InvXPArgs a{it, tw, g.n, g.s, W, g.ga, g.npa, g.pl0, g.wa, g.nc, nz, {}};
+        for (int j = 0; j < nz; ++j) a.zrow[j] = zrow[j];
+        const size_t sm = ((size_t)M + (size_t)MH * W + (size_t)W * (M + 1)) * 2 * sizeof(R);
+        k_inv_x_pruned<LOG2M, R><<<nb * a.nz, 256, sm, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t run_conv(const ConvDesc &d, cudaStream_t st) {
     switch (d.log2M) {
@@ -691,6 +1230,16 @@ void stencil_b(int Q, double b[4]) {
 
 }  // namespace
 
+__global__ void k_set_ptrs(PlanPtrs *d, const void *f, double *phi) {
+    d->f = f;
+    d->phi = phi;
+}
+
+cudaError_t launch_set_ptrs(PlanPtrs *d, const void *f, double *phi, cudaStream_t st) {
+    k_set_ptrs<<<1, 1, 0, st>>>(d, f, phi);
+    return cudaGetLastError();
+}
+
 void configure_kernels() {
     set_smem_attrs<5, double>();
     set_smem_attrs<6, double>();
@@ -698,59 +1247,79 @@ void configure_kernels() {
     set_smem_attrs<8, double>();
     set_smem_attrs<5, float>();
     set_smem_attrs<6, float>();
-    cudaFuncSetAttribute(k_dirichlet<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_dirichlet<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_dirichlet<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_dirichlet<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_dirichlet<double, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_dirichlet<float, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_resid<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_resid<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
-cudaError_t launch_moments(const mlc_plan_s *pl, const void *f, bool f32, cudaStream_t st) {
+cudaError_t launch_moments(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
     const Geom &g = pl->g;
-    if (f32)
-        k_moments<float><<<g.NP, 256, 0, st>>>((const float *)f, g.N, g.n, g.np, g.npoly, pl->momw, pl->mom);
+    if (g.tier == MLC_TIER_SPLIT)
+        k_moments<float, float><<<it.nitems, 256, 0, st>>>(it, g.n, g.npoly);
     else
-        k_moments<double><<<g.NP, 256, 0, st>>>((const double *)f, g.N, g.n, g.np, g.npoly, pl->momw, pl->mom);
+        k_moments<double, double><<<it.nitems, 256, 0, st>>>(it, g.n, g.npoly);
     return cudaGetLastError();
 }
 
-cudaError_t launch_patch_conv(const mlc_plan_s *pl, const void *f, bool f32, cudaStream_t st) {
+cudaError_t launch_patch_conv(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
     const Geom &g = pl->g;
-    ConvDesc d{};
-    d.M = g.M; d.log2M = g.log2M; d.nbatch = g.NP; d.nin = g.nb; d.nout = g.W; d.out_off = -g.s;
-    d.src = f; d.patch = true; d.f32 = f32; d.N = g.N; d.n = g.n; d.np = g.np;
-    d.b0 = pl->buf0; d.b1 = pl->buf1; d.out = pl->box; d.pl = pl; d.ev0 = 1;
-    if (pl->g.tier == MLC_TIER_SPLIT) {
-        d.khat = pl->khat_f; d.tw = pl->tw_f;
-        return run_conv<float>(d, st);
-    }
-    d.khat = pl->khat; d.tw = pl->tw;
-    return run_conv<double>(d, st);
+    const bool split = g.tier == MLC_TIER_SPLIT;
+    const void *tw = split ? (const void *)pl->tw_f : (const void *)pl->tw;
+    if (g.log2M == 5) return split ? run_patch_conv_t<5, float>(pl, it, true, tw, st)
+                                   : run_patch_conv_t<5, double>(pl, it, false, tw, st);
+    if (g.log2M == 6) return split ? run_patch_conv_t<6, float>(pl, it, true, tw, st)
+                                   : run_patch_conv_t<6, double>(pl, it, false, tw, st);
+    return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_resid(const mlc_plan_s *pl, cudaStream_t st) {
+// Lagrange weights of I^H on the nodes k0-b .. k0+b+1 at t = k0 + r/4 (R4 reading).
+void lagrange_rows(int b, double lw[4][8]) {
+    const int K = 2 * b + 2;
+    for (int r = 0; r < 4; ++r)
+        for (int j = 0; j < 8; ++j) lw[r][j] = 0.0;
+    for (int r = 1; r < 4; ++r)
+        for (int j = 0; j < K; ++j) {
+            double w = 1.0;
+            const double t = r / 4.0 + b;  // position relative to the first node
+            for (int l = 0; l < K; ++l)
+                if (l != j) w *= (t - l) / (double)(j - l);
+            lw[r][j] = w;
+        }
+}
+
+cudaError_t launch_resid(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
     const Geom &g = pl->g;
-    dim3 grid(g.NP, (g.na_face + 255) / 256);
-    if (g.tier == MLC_TIER_SPLIT)
-        k_resid<float><<<grid, 256, 0, st>>>((const float *)pl->box, (long)g.W * g.W * g.W, g.na_face,
-                                             g.S, pl->a_self, pl->a_off, pl->a_w, pl->resid);
-    else
-        k_resid<double><<<grid, 256, 0, st>>>((const double *)pl->box, (long)g.W * g.W * g.W, g.na_face,
-                                              g.S, pl->a_self, pl->a_off, pl->a_w, pl->resid);
+    ResArgs a{};
+    a.it = it; a.n = g.n; a.s = g.s; a.ga = g.ga; a.b = g.b;
+    a.npa = g.npa; a.pl0 = g.pl0; a.wa = g.wa; a.nc = g.nc;
+    lagrange_rows(g.b, a.lw);
+    const int nk = (g.n + 2 * g.ga) / 4 + 2 * g.b + 1;
+    const size_t sm = sizeof(double) * (size_t)nk * g.wa;
+    dim3 grid(it.nitems, 3 * g.npa);
+    if (g.tier == MLC_TIER_SPLIT) k_resid<float><<<grid, 256, sm, st>>>(a);
+    else k_resid<double><<<grid, 256, sm, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_assemble(const mlc_plan_s *pl, cudaStream_t st) {
     const Geom &g = pl->g;
     AsmArgs a{};
-    a.box = pl->box; a.mom = pl->mom; a.T = pl->Ttab; a.FH = pl->FH;
-    a.np = g.np; a.n = g.n; a.s = g.s; a.W = g.W; a.npoly = g.npoly; a.flo = g.flo; a.nf = g.nf;
+    const bool split = g.tier == MLC_TIER_SPLIT;
+    a.cl = pl->cl; a.FH = pl->FH;
+    a.mom = split ? (const void *)pl->mom_f : (const void *)pl->mom;
+    a.T = split ? (const void *)pl->Ttab_f : (const void *)pl->Ttab;
+    a.np = g.np; a.n = g.n; a.s = g.s; a.nc = g.nc; a.npoly = g.npoly; a.flo = g.flo; a.nf = g.nf;
     a.ca_lo = g.ca_lo; a.ca_hi = g.ca_hi; a.cb_lo = g.cb_lo; a.cb_hi = g.cb_hi;
     double b[4];
     stencil_b(g.Q, b);
     for (int k = 0; k < 4; ++k) a.coef[k] = b[k] / (g.H * g.H);
     const long tot = (long)g.nf * g.nf * g.nf;
-    if (g.tier == MLC_TIER_SPLIT)
-        k_assemble<float><<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(a);
-    else
-        k_assemble<double><<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(a);
+    const unsigned nbk = (unsigned)((tot + 127) / 128);
+    if (split) k_assemble<float, float><<<nbk, 128, 0, st>>>(a);
+    else k_assemble<double, double><<<nbk, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -761,46 +1330,50 @@ cudaError_t launch_coarse(const mlc_plan_s *pl, cudaStream_t st) {
     d.out_off = g.olo - g.flo;
     d.src = pl->FH; d.patch = false; d.f32 = false;
     d.b0 = pl->cbuf0; d.b1 = pl->cbuf1; d.out = pl->phiH; d.khat = pl->khat_c; d.tw = pl->tw_c;
-    d.pl = pl; d.ev0 = 8;
+    d.pl = pl; d.ev0 = 6;
     return run_conv<double>(d, st);
 }
 
 cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st) {
     const Geom &g = pl->g;
+    const bool split = g.tier == MLC_TIER_SPLIT;
     BndArgs a{};
-    a.phiH = pl->phiH; a.resid = pl->resid; a.mom = pl->mom; a.D = pl->Dtab;
-    a.amap = pl->amap; a.rmap = pl->rmap; a.phiB = pl->phiB;
+    a.phiH = pl->phiH; a.resid = pl->resid;
+    a.mom = split ? (const void *)pl->mom_f : (const void *)pl->mom;
+    a.D = split ? (const void *)pl->Dtab_f : (const void *)pl->Dtab;
+    a.rmap = pl->rmap; a.phiB = pl->phiB;
     a.N = g.N; a.n = g.n; a.np = g.np; a.ga = g.ga; a.gb = g.gb; a.b = g.b; a.npoly = g.npoly;
-    a.na = g.na_face; a.olo = g.olo; a.no = g.no; a.wa = g.wa; a.wbx = g.wbx;
-    // Lagrange weights on the nodes k0-b .. k0+b+1 at t = k0 + r/4 (R4)
-    const int K = 2 * g.b + 2;
-    for (int r = 0; r < 4; ++r)
-        for (int j = 0; j < 8; ++j) a.lw[r][j] = 0.0;
-    for (int r = 1; r < 4; ++r)
-        for (int j = 0; j < K; ++j) {
-            double w = 1.0;
-            const double t = r / 4.0 + g.b;  // position relative to the first node
-            for (int l = 0; l < K; ++l)
-                if (l != j) w *= (t - l) / (double)(j - l);
-            a.lw[r][j] = w;
-        }
+    a.olo = g.olo; a.no = g.no; a.wa = g.wa; a.wbx = g.wbx; a.npa = g.npa; a.pl0 = g.pl0;
+    lagrange_rows(g.b, a.lw);
     const long tot = g.n_planes_total;
-    k_boundary<<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(a);
+    const unsigned nbk = (unsigned)((tot + 127) / 128);
+    if (split) k_boundary<float><<<nbk, 128, 0, st>>>(a);
+    else k_boundary<double><<<nbk, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_dirichlet(const mlc_plan_s *pl, const void *f, bool f32, double *phi,
-                             cudaStream_t st) {
+cudaError_t launch_dirichlet(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
     const Geom &g = pl->g;
+    const bool f32 = g.tier == MLC_TIER_SPLIT;
     DirArgs a{};
-    a.f = f; a.phiB = pl->phiB; a.phi = phi; a.N = g.N; a.n = g.n; a.np = g.np;
-    a.h2 = g.h * g.h; a.c2h2 = g.h * g.h / 12.0;
+    a.it = it; a.n = g.n;
     stencil_b(g.Q, a.b);
-    a.sinm = pl->sinm; a.lam = pl->lam;
+    a.sinm = pl->sinm;
     const int nb = g.n + 1, m = g.n - 1;
-    const size_t sm = sizeof(double) * ((size_t)nb * nb * nb + 2 * (size_t)m * m * m + (size_t)m * m);
-    if (f32) k_dirichlet<float><<<g.NP, 256, sm, st>>>(a);
-    else k_dirichlet<double><<<g.NP, 256, sm, st>>>(a);
+    const size_t sm = sizeof(double) * ((size_t)nb * nb * nb + (size_t)m * m * m + (size_t)m * (g.n / 2));
+#define MLC_DIR(NN)                                                            \
+    case NN:                                                                   \
+        if (f32) k_dirichlet<float, NN><<<it.nitems, 256, sm, st>>>(a);        \
+        else k_dirichlet<double, NN><<<it.nitems, 256, sm, st>>>(a);           \
+        break;
+    switch (g.n) {
+        MLC_DIR(4)
+        MLC_DIR(8)
+        MLC_DIR(12)
+        MLC_DIR(16)
+        default: return cudaErrorInvalidValue;
+    }
+#undef MLC_DIR
     return cudaGetLastError();
 }
 

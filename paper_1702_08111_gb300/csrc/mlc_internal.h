@@ -12,7 +12,7 @@
 namespace mlc {
 
 // Launches of one solve, in order (the timing slots of mlc_debug_timing).
-constexpr int kTimedLaunches = 15;
+constexpr int kTimedLaunches = 13;
 
 // ---------------------------------------------------------------------------
 // Plan geometry (Sec. 4): every size below is derived from (N, n, s, C, P, Q,
@@ -30,29 +30,45 @@ struct Geom {
     int nD, zeta;                    // DGF construction domain
     int S;                           // interpolation stencil size (2b+2)^2
     int wa, wbx;                     // widths of the alpha and beta boxes
-    int na_face, nr_face;            // relative face nodes in alpha, in beta \ alpha
+    int nr_face;                     // relative face nodes in beta \ alpha
+    int npa, pl0;                    // face planes per axis inside Omega_alpha, first at pl0
+    int nc;                          // coarse points per axis of the field box, (n + 2s)/4 + 1
     int plane_n;                     // (N+1)^2 nodes per face plane
     long n_planes_total;             // 3 (np+1) (N+1)^2
 };
 
-// Host-built relative tables, uploaded to the device.
-struct HostTables {
-    std::vector<double> momw;        // npoly x nb^3: Boole weight * Q^p at patch nodes
-    std::vector<int> amap;           // alpha box (wa^3) -> alpha face index or -1
-    std::vector<int> a_self;         // per alpha face node: field-box index of the node
-    std::vector<int> a_off;          // per alpha face node: S field-box indices of 4k
-    std::vector<double> a_w;         // per alpha face node: S weights
-    std::vector<int> rmap;           // beta box (wbx^3) -> ring face index or -1
-    std::vector<double> Dtab;        // nr_face x npoly: B_p - I(B_p) at ring face nodes
-    std::vector<double> Ttab;        // ncb^3 x npoly: Delta^H B_p on C(beta) (0 inside C(alpha))
+// Per-plan pointers and sizes read by the per-patch kernels.  A single solve
+// uses its plan's record; a batch passes one record per plan plus an item
+// table of (plan slot, local patch) pairs, so one launch covers the patches
+// of every problem in the batch.
+struct PlanPtrs {
+    const void *f;        // charge, N^3 (FP64 or FP32 by tier)
+    void *a1, *a4;        // local-convolution spectra workspace
+    void *cl, *fp;        // local fields on the coarse lattice / alpha face planes
+    const void *khat;     // patch kernel spectrum octant (working precision)
+    const void *momw;     // Boole weight x Q^p at the patch nodes (working precision of the moments)
+    double *mom;
+    float *mom_f;
+    double *resid;
+    const double *phiB;
+    double *phi;
+    const double *lam;    // Dirichlet inverse eigenvalues h^2 / lambda
+    int N, np;
+    double c2h2, inv_h2;  // h^2 / 12, 1 / h^2
 };
 
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
+struct Items {
+    const int2 *items;    // (plan slot, local patch); nullptr: plan 0, item = patch
+    const PlanPtrs *plans;
+    int nitems;
 };
 
 }  // namespace mlc
+
+struct mlc_plan_s;
+namespace mlc {
+extern thread_local bool g_capturing;
+}
 
 struct mlc_plan_s {
     mlc::Geom g;
@@ -64,10 +80,10 @@ struct mlc_plan_s {
     double *khat;            // patch kernel spectrum octant (Mh^3), scaled by h^2/M^3
     double *khat_c;          // coarse kernel spectrum octant (Mhc^3), scaled by H^2/Mc^3
     double *momw;            // npoly x nb^3
-    int *amap, *a_self, *a_off;
-    double *a_w;
+    float *momw_f;           // split tier: FP32 copy
     int *rmap;
     double *Dtab, *Ttab;
+    float *Dtab_f, *Ttab_f;  // split tier: FP32 copies for the Legendre ring sums
     double2 *tw, *tw_c;      // FFT twiddles exp(-2 pi i t / M), t < M/2
     float *khat_f;           // split tier: FP32 copies of the patch spectrum and twiddles
     float2 *tw_f;
@@ -75,9 +91,11 @@ struct mlc_plan_s {
     double *lam;             // (n-1)^3 stencil eigenvalues / h^2
     // workspace (device)
     void *buf0, *buf1;       // ping-pong spectra for the patch convolutions (complex FP64 / FP32)
-    void *box;               // NP x W^3 local fields phi^{i,h} (FP64 / FP32)
+    void *cl;                // NP x nc^3 local fields on the coarse lattice of the field box
+    void *fpl;               // NP x 3 npa x wa^2 local fields on the face planes inside alpha
     double *mom;             // NP x npoly
-    double *resid;           // NP x na_face
+    float *mom_f;            // split tier: FP32 copy of the moments
+    double *resid;           // NP x 3 npa x wa^2 face-plane residuals
     double *FH;              // nf^3
     double2 *cbuf0, *cbuf1;  // coarse spectra
     double *phiH;            // no^3
@@ -85,6 +103,8 @@ struct mlc_plan_s {
     void *f_stage, *phi_stage;  // device staging for mlc_solve_host
     size_t ws_bytes;
     std::vector<void *> owned;  // device allocations to free
+    mlc::PlanPtrs *dptrs = nullptr;  // device copy of this plan's PlanPtrs (f, phi filled per solve)
+    mlc::PlanPtrs hptrs{};
     // optional per-launch timing of the last solve (CUDA events on the solve stream)
     int timing = 0;
     cudaEvent_t ev[mlc::kTimedLaunches + 1] = {};
@@ -92,19 +112,23 @@ struct mlc_plan_s {
 
 namespace mlc {
 
-// kernels_fp64.cu
+// kernels.cu
 // Record the timing event of launch slot k (no-op unless timing is enabled).
-inline void mark(const mlc_plan_s *pl, int k, cudaStream_t st) {
-    if (pl && pl->timing) cudaEventRecord(pl->ev[k], st);
-}
-cudaError_t launch_moments(const mlc_plan_s *pl, const void *f, bool f32, cudaStream_t st);
-cudaError_t launch_patch_conv(const mlc_plan_s *pl, const void *f, bool f32, cudaStream_t st);
-cudaError_t launch_resid(const mlc_plan_s *pl, cudaStream_t st);
+inline void mark(const mlc_plan_s *pl, int k, cudaStream_t st);
+// Per-patch steps over an item set (all patches of one plan, or of a batch of
+// plans with the geometry of `pl`).
+cudaError_t launch_moments(const mlc_plan_s *pl, const Items &it, cudaStream_t st);
+cudaError_t launch_patch_conv(const mlc_plan_s *pl, const Items &it, cudaStream_t st);
+cudaError_t launch_resid(const mlc_plan_s *pl, const Items &it, cudaStream_t st);
+cudaError_t launch_dirichlet(const mlc_plan_s *pl, const Items &it, cudaStream_t st);
 cudaError_t launch_assemble(const mlc_plan_s *pl, cudaStream_t st);
 cudaError_t launch_coarse(const mlc_plan_s *pl, cudaStream_t st);
 cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st);
-cudaError_t launch_dirichlet(const mlc_plan_s *pl, const void *f, bool f32, double *phi, cudaStream_t st);
 void configure_kernels();
+// Write f and phi into a device PlanPtrs record, in stream order.
+cudaError_t launch_set_ptrs(PlanPtrs *d, const void *f, double *phi, cudaStream_t st);
+// Timing marks are suppressed while a batch graph is being captured.
+extern thread_local bool g_capturing;
 
 // dgf.cu
 // Build G^{h=1} on [0, L]^3 (App. A.1) into a new device array; returns nullptr on error.
@@ -122,4 +146,10 @@ cudaError_t batched_dgemm(int I, int K, int J, int batch, const double *A, long 
 cudaError_t basis_direct_sum(const double *G1, int L_table, const int *pts, int npts,
                              const double *charge, int npoly, int n, double h2, double *out);
 
+}  // namespace mlc
+
+namespace mlc {
+inline void mark(const mlc_plan_s *pl, int k, cudaStream_t st) {
+    if (pl && pl->timing && !g_capturing) cudaEventRecord(pl->ev[k], st);
+}
 }  // namespace mlc

@@ -12,6 +12,9 @@
 
 using namespace mlc;
 
+thread_local bool mlc::g_capturing = false;
+void mlc_batch_forget(mlc_plan_t plan);
+
 namespace {
 
 int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
@@ -199,6 +202,7 @@ mlc_status derive_geometry(const mlc_params &pp, Geom &g) {
     if (g.M > 256 || g.Mc > 256 || g.M < 32) return MLC_ERR_UNSUPPORTED;
     if (g.n > 16) return MLC_ERR_UNSUPPORTED;  // Dirichlet tile held in shared memory
     g.S = (2 * g.b + 2) * (2 * g.b + 2);
+    g.nc = (g.n + 2 * g.s) / 4 + 1;
     g.wa = g.n + 2 * g.ga + 1;
     g.wbx = g.n + 2 * g.gb + 1;
     g.plane_n = (g.N + 1) * (g.N + 1);
@@ -240,40 +244,19 @@ mlc_status build_tables(mlc_plan_s *pl) {
                     lcharge[(size_t)p * nb3 + m] = chi1[m0] * chi1[m1] * chi1[m2] * q;
                 }
     TRY(dev_upload(pl, &pl->momw, momw));
+    if (g.tier == MLC_TIER_SPLIT) TRY(dev_upload(pl, &pl->momw_f, std::vector<float>(momw.begin(), momw.end())));
 
-    // alpha face nodes and their interpolation stencils inside the field box
-    std::vector<int> amap((size_t)g.wa * g.wa * g.wa, -1), a_self, a_off;
-    std::vector<double> a_w;
-    std::vector<std::array<int, 3>> sp;
-    std::vector<double> sw;
-    auto boxidx = [&](int x0, int x1, int x2) {
-        return ((x0 + g.s) * W + (x1 + g.s)) * W + (x2 + g.s);
-    };
-    for (int x0 = -g.ga; x0 <= n + g.ga; ++x0)
-        for (int x1 = -g.ga; x1 <= n + g.ga; ++x1)
-            for (int x2 = -g.ga; x2 <= n + g.ga; ++x2) {
-                const int gg[3] = {x0, x1, x2};
-                if (!on_face(gg, n)) continue;
-                amap[((size_t)(x0 + g.ga) * g.wa + (x1 + g.ga)) * g.wa + (x2 + g.ga)] = (int)a_self.size();
-                a_self.push_back(boxidx(x0, x1, x2));
-                face_stencil(gg, g.b, sp, sw);
-                if ((int)sp.size() > g.S) return MLC_ERR_INVALID_ARG;
-                for (int j = 0; j < g.S; ++j) {
-                    const int jj = j < (int)sp.size() ? j : 0;
-                    const int y0 = 4 * sp[jj][0], y1 = 4 * sp[jj][1], y2 = 4 * sp[jj][2];
-                    if (y0 < -g.s || y0 > n + g.s || y1 < -g.s || y1 > n + g.s || y2 < -g.s || y2 > n + g.s)
-                        return MLC_ERR_INVALID_ARG;
-                    a_off.push_back(boxidx(y0, y1, y2));
-                    a_w.push_back(j < (int)sp.size() ? sw[j] : 0.0);
-                }
-            }
-    g.na_face = (int)a_self.size();
-    TRY(dev_upload(pl, &pl->amap, amap));
-    TRY(dev_upload(pl, &pl->a_self, a_self));
-    TRY(dev_upload(pl, &pl->a_off, a_off));
-    TRY(dev_upload(pl, &pl->a_w, a_w));
+    // face planes of the patch lattice inside Omega_alpha (relative x = pl0 + j n)
+    g.pl0 = g.n * ceildiv(-g.ga, g.n);
+    g.npa = 0;
+    for (int c = g.pl0; c <= n + g.ga; c += n) ++g.npa;
+    // every interpolation stencil of a face node of Omega_alpha stays in the field box
+    if (4 * (-g.ga / 4 - g.b) < -g.s || 4 * ((n + g.ga) / 4 + g.b) > n + g.s) return MLC_ERR_INVALID_ARG;
+    (void)W;
 
     // ring: face nodes in Omega_beta \ Omega_alpha and coarse nodes C(beta) \ C(alpha)
+    std::vector<std::array<int, 3>> sp;
+    std::vector<double> sw;
     std::vector<int> rmap((size_t)g.wbx * g.wbx * g.wbx, -1);
     std::vector<std::array<int, 3>> ring_nodes;
     std::vector<std::vector<std::array<int, 3>>> ring_st;
@@ -381,6 +364,10 @@ mlc_status build_tables(mlc_plan_s *pl) {
     TRY(dev_upload(pl, &pl->rmap, rmap));
     TRY(dev_upload(pl, &pl->Dtab, Dtab));
     TRY(dev_upload(pl, &pl->Ttab, Ttab));
+    if (g.tier == MLC_TIER_SPLIT) {
+        TRY(dev_upload(pl, &pl->Dtab_f, std::vector<float>(Dtab.begin(), Dtab.end())));
+        TRY(dev_upload(pl, &pl->Ttab_f, std::vector<float>(Ttab.begin(), Ttab.end())));
+    }
 
     // FFT twiddles
     auto twiddles = [](int M) {
@@ -394,21 +381,21 @@ mlc_status build_tables(mlc_plan_s *pl) {
     TRY(dev_upload(pl, &pl->tw, twiddles(g.M)));
     TRY(dev_upload(pl, &pl->tw_c, twiddles(g.Mc)));
 
-    // Dirichlet tables: DST-I matrix and eigenvalues of the stencil / h^2
-    const int m = n - 1;
-    std::vector<double> sinm((size_t)m * m), lam((size_t)m * m * m);
+    // Dirichlet tables: half DST-I matrix and eigenvalues of the stencil / h^2
+    const int m = n - 1, hn = n / 2;
+    std::vector<double> sinm((size_t)m * hn), lam((size_t)m * m * m);
     std::vector<double> cth(m);
     for (int k = 0; k < m; ++k) {
         cth[k] = std::cos(M_PI * (k + 1) / (double)n);
-        for (int t = 0; t < m; ++t) {
+        for (int t = 0; t < hn; ++t) {
             const long r = ((long)(k + 1) * (t + 1)) % (2L * n);
-            sinm[(size_t)k * m + t] = std::sin(M_PI * (double)r / (double)n);
+            sinm[(size_t)k * hn + t] = std::sin(M_PI * (double)r / (double)n);
         }
     }
     for (int a = 0; a < m; ++a)
         for (int c = 0; c < m; ++c)
             for (int e = 0; e < m; ++e)
-                lam[((size_t)a * m + c) * m + e] = symbol(g.Q, cth[a], cth[c], cth[e]) / (g.h * g.h);
+                lam[((size_t)a * m + c) * m + e] = (g.h * g.h) / symbol(g.Q, cth[a], cth[c], cth[e]);
     TRY(dev_upload(pl, &pl->sinm, sinm));
     TRY(dev_upload(pl, &pl->lam, lam));
     return MLC_OK;
@@ -495,16 +482,23 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
         TRY_CUDA(build_even_spectrum(pl->dgf, pl->dgf_L, G.Mc, G.Lc,
                                      G.H * G.H / ((double)G.Mc * G.Mc * G.Mc), pl->khat_c));
         const size_t NP = G.NP, nb = G.nb, W = G.W, M = G.M, Mh = G.Mh;
-        const size_t A1 = NP * nb * nb * Mh, A2 = NP * nb * M * Mh, A3 = NP * W * M * Mh,
-                     A4 = NP * W * W * Mh;
+        (void)M;
+        int nzr = 0;  // z rows of the field box the pruned inverse x reads
+        for (int zi = 0; zi < G.W; ++zi) {
+            const int z = zi - G.s;
+            if ((z >= -G.ga && z <= G.n + G.ga) || (z % 4 == 0)) ++nzr;
+        }
+        const size_t A1 = NP * nb * nb * Mh, A4 = NP * (size_t)nzr * W * Mh;
         const size_t rb = G.tier == MLC_TIER_SPLIT ? sizeof(float) : sizeof(double);
-        char *b0 = nullptr, *b1 = nullptr, *bx = nullptr;
-        TRY(dev_alloc(pl, &b0, std::max(A1, A3) * 2 * rb));
-        TRY(dev_alloc(pl, &b1, std::max(A2, A4) * 2 * rb));
-        TRY(dev_alloc(pl, &bx, NP * W * W * W * rb));
+        char *b0 = nullptr, *b1 = nullptr, *bc = nullptr, *bf = nullptr;
+        TRY(dev_alloc(pl, &b0, A1 * 2 * rb));   // [p][kx][zi][yi]
+        TRY(dev_alloc(pl, &b1, A4 * 2 * rb));   // [p][z row][kx][yo]
+        TRY(dev_alloc(pl, &bc, NP * (size_t)G.nc * G.nc * G.nc * rb));
+        TRY(dev_alloc(pl, &bf, NP * 3 * (size_t)G.npa * G.wa * G.wa * rb));
         pl->buf0 = b0;
         pl->buf1 = b1;
-        pl->box = bx;
+        pl->cl = bc;
+        pl->fpl = bf;
         if (G.tier == MLC_TIER_SPLIT) {
             // FP32 copies of the patch kernel spectrum and twiddles
             const size_t nk = (size_t)G.Mh * G.Mh * G.Mh;
@@ -520,7 +514,8 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
             TRY(dev_upload(pl, &pl->tw_f, tf));
         }
         TRY(dev_alloc(pl, &pl->mom, NP * G.npoly));
-        TRY(dev_alloc(pl, &pl->resid, NP * (size_t)G.na_face));
+        TRY(dev_alloc(pl, &pl->resid, NP * 3 * (size_t)G.npa * G.wa * G.wa));
+        if (G.tier == MLC_TIER_SPLIT) TRY(dev_alloc(pl, &pl->mom_f, NP * G.npoly));
         const size_t nf = G.nf, no = G.no, Mc = G.Mc, Mhc = G.Mhc;
         TRY(dev_alloc(pl, &pl->FH, nf * nf * nf));
         TRY(dev_alloc(pl, &pl->cbuf0, std::max(nf * nf * Mhc, no * Mc * Mhc)));
@@ -530,6 +525,27 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
         return MLC_OK;
     };
     if (st == MLC_OK) st = alloc_all();
+    if (st == MLC_OK) {
+        PlanPtrs &h = pl->hptrs;
+        h.f = nullptr;
+        h.phi = nullptr;
+        h.a1 = pl->buf0;
+        h.a4 = pl->buf1;
+        h.cl = pl->cl;
+        h.fp = pl->fpl;
+        h.khat = G.tier == MLC_TIER_SPLIT ? (const void *)pl->khat_f : (const void *)pl->khat;
+        h.momw = G.tier == MLC_TIER_SPLIT ? (const void *)pl->momw_f : (const void *)pl->momw;
+        h.mom = pl->mom;
+        h.mom_f = pl->mom_f;
+        h.resid = pl->resid;
+        h.phiB = pl->phiB;
+        h.lam = pl->lam;
+        h.N = G.N;
+        h.np = G.np;
+        h.c2h2 = G.h * G.h / 12.0;
+        h.inv_h2 = 1.0 / (G.h * G.h);
+        st = dev_upload(pl, &pl->dptrs, std::vector<PlanPtrs>{h});
+    }
     if (st == MLC_OK) st = to_status(cudaDeviceSynchronize());
     if (st != MLC_OK) {
         free_plan(pl);
@@ -550,6 +566,7 @@ mlc_status mlc_plan_create(int N, int patch, int support, int coarsening, int P,
 mlc_status mlc_plan_destroy(mlc_plan_t plan) {
     if (!plan) return MLC_ERR_INVALID_ARG;
     cudaError_t e = cudaDeviceSynchronize();
+    mlc_batch_forget(plan);
     free_plan(plan);
     return to_status(e);
 }
@@ -572,20 +589,25 @@ mlc_status mlc_plan_info(mlc_plan_t plan, int *o) {
 mlc_status mlc_solve(mlc_plan_t pl, const void *f, void *phi, void *stream) {
     if (!pl || !f || !phi || f == phi) return MLC_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    const bool f32 = pl->g.tier == MLC_TIER_SPLIT;
+    if (pl->hptrs.f != f || pl->hptrs.phi != phi) {
+        TRY_CUDA(launch_set_ptrs(pl->dptrs, f, (double *)phi, st));
+        pl->hptrs.f = f;
+        pl->hptrs.phi = (double *)phi;
+    }
+    const Items it{nullptr, pl->dptrs, pl->g.NP};
     mark(pl, 0, st);
-    TRY_CUDA(launch_moments(pl, f, f32, st));
-    TRY_CUDA(launch_patch_conv(pl, f, f32, st));   // slots 1-5
-    mark(pl, 6, st);
-    TRY_CUDA(launch_resid(pl, st));
-    mark(pl, 7, st);
+    TRY_CUDA(launch_moments(pl, it, st));
+    TRY_CUDA(launch_patch_conv(pl, it, st));       // slots 1-3
+    mark(pl, 4, st);
+    TRY_CUDA(launch_resid(pl, it, st));
+    mark(pl, 5, st);
     TRY_CUDA(launch_assemble(pl, st));
-    TRY_CUDA(launch_coarse(pl, st));               // slots 8-12
-    mark(pl, 13, st);
+    TRY_CUDA(launch_coarse(pl, st));               // slots 6-10
+    mark(pl, 11, st);
     TRY_CUDA(launch_boundary(pl, st));
-    mark(pl, 14, st);
-    TRY_CUDA(launch_dirichlet(pl, f, f32, (double *)phi, st));
-    mark(pl, 15, st);
+    mark(pl, 12, st);
+    TRY_CUDA(launch_dirichlet(pl, it, st));
+    mark(pl, 13, st);
     return MLC_OK;
 }
 
@@ -606,13 +628,6 @@ mlc_status mlc_solve_host(mlc_plan_t pl, const void *f_host, void *phi_host, voi
     TRY(mlc_solve(pl, pl->f_stage, pl->phi_stage, stream));
     TRY_CUDA(cudaMemcpyAsync(phi_host, pl->phi_stage, N3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     TRY_CUDA(cudaStreamSynchronize(st));
-    return MLC_OK;
-}
-
-mlc_status mlc_batch_solve(int count, const mlc_plan_t *plans, const void *const *f,
-                           void *const *phi, void *stream) {
-    if (count < 0 || (count > 0 && (!plans || !f || !phi))) return MLC_ERR_INVALID_ARG;
-    for (int k = 0; k < count; ++k) TRY(mlc_solve(plans[k], f[k], phi[k], stream));
     return MLC_OK;
 }
 

@@ -55,21 +55,27 @@ struct Active {
     mlc_status launch_status;
 };
 
-// Device bytes a plan with these parameters holds (workspace + tables), from
-// the same sizes the plan allocates.
+// Upper bound of the device bytes a plan with these parameters holds
+// (workspace and per-plan tables; the shared DGF table is not counted).
 size_t estimate_bytes(const mlc_params &p) {
     const long N = p.N, n = p.n, s = p.s;
     if (n <= 0 || N <= 0 || N % n) return 0;
+    const long rb = (p.tier == MLC_TIER_SPLIT) ? 4 : 8;
     long M = 1;
     while (M < 2 * (n + s)) M <<= 1;
     const long Mh = M / 2 + 1, nb = n + 1, W = n + 2 * s + 1, np = N / n, NP = np * np * np;
-    const long A = std::max(NP * nb * nb * Mh, NP * W * M * Mh) + std::max(NP * nb * M * Mh, NP * W * W * Mh);
-    long bytes = A * 16 + NP * W * W * W * 8;
-    const long nc = N / 4 + 16;  // coarse extent bound
+    const long nc = (n + 2 * s) / 4 + 1;
+    long bytes = NP * (nb * nb * Mh + W * W * Mh) * 2 * rb;   // spectra workspace
+    bytes += NP * (nc * nc * nc + 6 * W * W) * rb;            // coarse lattice, face planes
+    bytes += NP * (6 * W * W + 64) * 8;                       // residuals, moments
+    const long nf = N / 4 + 2 * (s / 4 + 4);                  // coarse extents (bound)
     long Mc = 1;
-    while (Mc < 2 * nc) Mc <<= 1;
-    bytes += 3L * nc * Mc * (Mc / 2 + 1) * 16 + 3L * (np + 1) * (N + 1) * (N + 1) * 8;
-    bytes += NP * (20 + 8000) * 8 + 64L << 20;  // moments, residuals, tables, slack
+    while (Mc < 2 * nf) Mc <<= 1;
+    bytes += 3L * nf * Mc * (Mc / 2 + 1) * 16 + 2L * nf * nf * nf * 8;
+    bytes += 3L * (np + 1) * (N + 1) * (N + 1) * 8;           // boundary planes
+    bytes += (Mh * Mh * Mh + (Mc / 2 + 1) * (Mc / 2 + 1) * (Mc / 2 + 1)) * 12;
+    bytes += 2 * N * N * N * 8;                               // host-path staging (if used)
+    bytes += 32L << 20;                                        // basis tables, index maps, slack
     return (size_t)bytes;
 }
 
@@ -231,8 +237,6 @@ mlc_status mlc_server_destroy(mlc_server_t s) {
 
 mlc_status mlc_server_enqueue(mlc_server_t s, const mlc_request *req, uint64_t *ticket) {
     if (!s || !req || !ticket || !req->f || !req->phi) return MLC_ERR_INVALID_ARG;
-    mlc::Geom g;
-    (void)g;
     const mlc_params &p = req->params;
     if (p.N <= 0 || p.n <= 0 || p.N % p.n || p.n % 4 || p.s % 4 || (p.Q != 4 && p.Q != 6) || p.C != 4)
         return MLC_ERR_INVALID_ARG;

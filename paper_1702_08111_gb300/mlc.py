@@ -25,9 +25,9 @@ EXPORTED = [
     "mlc_server_destroy", "mlc_server_enqueue", "mlc_server_wait", "mlc_status_string",
     "mlc_debug_set_timing", "mlc_debug_timing",
 ]
-LAUNCH_NAMES = ["moments", "conv_fwd_x", "conv_fwd_y", "conv_z_kernel", "conv_inv_y", "conv_inv_x",
-                "resid", "assemble", "coarse_fwd_x", "coarse_fwd_y", "coarse_z_kernel",
-                "coarse_inv_y", "coarse_inv_x", "boundary", "dirichlet"]
+LAUNCH_NAMES = ["moments", "conv_fwd_x", "conv_slab", "conv_inv_x", "resid", "assemble",
+                "coarse_fwd_x", "coarse_fwd_y", "coarse_z_kernel", "coarse_inv_y", "coarse_inv_x",
+                "boundary", "dirichlet"]
 
 
 class MLCError(RuntimeError):
@@ -248,3 +248,46 @@ def batch_solve(plans, fs, phis, stream=None):
         p._check_tensors(f, ph)
     _check(lib.mlc_batch_solve(k, H, F, P, ctypes.c_void_p(_stream_handle(stream))), "mlc_batch_solve")
     return phis
+
+
+class Server:
+    """Continuous-batching solve server (mlc_server_*): requests are admitted
+    while others run, under a device-memory budget; plans stay resident."""
+
+    def __init__(self, budget_bytes: int, max_batch: int = 8):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.mlc_server_create(ctypes.c_size_t(int(budget_bytes)), int(max_batch), ctypes.byref(h)),
+               "mlc_server_create")
+        self._h = h
+        self._keep = {}
+
+    def enqueue(self, f, phi, N, n, s, P=4, Q=4, **kw) -> int:
+        """Queue a solve of f into phi (device tensors kept alive until wait)."""
+        req = mlc_request()
+        req.params = make_params(N, n, s, P, Q, **kw)
+        req.f = f.data_ptr()
+        req.phi = phi.data_ptr()
+        t = ctypes.c_uint64()
+        _check(load_library().mlc_server_enqueue(self._h, ctypes.byref(req), ctypes.byref(t)), "mlc_server_enqueue")
+        self._keep[t.value] = (f, phi)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """(status, latency_ms, queue_ms) of a finished request; raises on TIMEOUT."""
+        res = mlc_result()
+        _check(load_library().mlc_server_wait(self._h, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(res)),
+               "mlc_server_wait")
+        self._keep.pop(ticket, None)
+        return res.status, res.latency_ms, res.queue_ms
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().mlc_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
