@@ -59,8 +59,9 @@ def test_batch_small_patches_and_errors(torch_cuda):
         mlc.batch_solve([plans[0], other], [fs[0], _charge(torch, 64, 3)],
                         [phis[0], torch.empty((64,) * 3, dtype=torch.float64, device="cuda")])
     assert e.value.status == 1
-    with pytest.raises(mlc.MLCError):
-        mlc.batch_solve([plans[0], plans[0]], [fs[0], fs[0]], [phis[0], phis[1]])
+    with pytest.raises(mlc.MLCError) as e:
+        mlc.batch_solve([plans[0], plans[0]], [fs[0], fs[0]], [phis[0], torch.empty_like(phis[0])])
+    assert e.value.status == 1
 
 
 def test_server_results_same_alone_and_in_mix(torch_cuda):
