@@ -111,6 +111,27 @@ mlc_status mlc_plan_workspace_bytes(mlc_plan_t plan, size_t *bytes);
 mlc_status mlc_solve(mlc_plan_t plan, const void *f, void *phi, void *stream);
 
 /*
+ * As mlc_solve, for callers that must not allocate device memory when they
+ * solve (for example a plugin whose host application has already reserved the
+ * device memory, or code running while a CUDA graph is captured in global
+ * mode, where allocation calls are not permitted).  The paper has no
+ * counterpart: this is an engineering variant of mlc_solve.  The plan is
+ * created beforehand; this call allocates nothing and takes the scratch of the
+ * local convolutions (the patch spectra) from one static device array of
+ * 64 MiB that every GPU loading the library holds until the process exits,
+ * instead of from the plan's workspace.  Same f, phi, stream contract and the
+ * same result as mlc_solve.  INVALID_ARG if the plan's spectra need more than
+ * 64 MiB (about 1.1 MB per patch of 16^3 with support 16 in the FP64 tier, half
+ * that in the split tier: some 60 and 120 patches) or the current device is not
+ * the plan's.  The first call on a device looks
+ * up the array's device address with that device current: make it before any
+ * stream capture.  All calls share the array and see the last call's
+ * contents (every element a call reads it has written first, so nothing needs
+ * clearing); calls that overlap on the GPU race on it and must not be issued.
+ */
+mlc_status mlc_solve_noalloc(mlc_plan_t plan, const void *f, void *phi, void *stream);
+
+/*
  * As mlc_solve with host arrays: copies f (host, pinned or pageable) to the
  * plan's device staging buffer, solves, copies phi back to the host array and
  * synchronises the stream before returning.

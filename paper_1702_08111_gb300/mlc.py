@@ -23,7 +23,7 @@ EXPORTED = [
     "mlc_plan_workspace_bytes", "mlc_solve", "mlc_solve_host", "mlc_batch_solve",
     "mlc_debug_stage_bytes", "mlc_debug_export", "mlc_plan_info", "mlc_server_create",
     "mlc_server_destroy", "mlc_server_enqueue", "mlc_server_wait", "mlc_status_string",
-    "mlc_debug_set_timing", "mlc_debug_timing",
+    "mlc_debug_set_timing", "mlc_debug_timing", "mlc_solve_noalloc",
 ]
 LAUNCH_NAMES = ["moments", "conv_fwd_x", "conv_slab", "conv_inv_x", "resid", "assemble",
                 "coarse_fwd_x", "coarse_fwd_y", "coarse_z_kernel", "coarse_inv_y", "coarse_inv_x",
@@ -71,6 +71,7 @@ def load_library(path: str = LIB_PATH):
     lib.mlc_plan_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     lib.mlc_solve.argtypes = [vp, vp, vp, vp]
     lib.mlc_solve_host.argtypes = [vp, vp, vp, vp]
+    lib.mlc_solve_noalloc.argtypes = [vp, vp, vp, vp]
     lib.mlc_batch_solve.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
     lib.mlc_debug_stage_bytes.argtypes = [vp, i, ctypes.POINTER(ctypes.c_size_t)]
     lib.mlc_debug_export.argtypes = [vp, i, vp, ctypes.c_size_t]
@@ -195,6 +196,15 @@ class Plan:
         _check(load_library().mlc_solve(self._h, ctypes.c_void_p(f.data_ptr()),
                                         ctypes.c_void_p(phi.data_ptr()),
                                         ctypes.c_void_p(_stream_handle(stream))), "mlc_solve")
+        return phi
+
+    def solve_noalloc(self, f, phi, stream=None):
+        """mlc_solve_noalloc: the same solve with the local-convolution scratch in
+        the library's static device array (nothing is allocated by the call)."""
+        self._check_tensors(f, phi)
+        _check(load_library().mlc_solve_noalloc(self._h, ctypes.c_void_p(f.data_ptr()),
+                                                ctypes.c_void_p(phi.data_ptr()),
+                                                ctypes.c_void_p(_stream_handle(stream))), "mlc_solve_noalloc")
         return phi
 
     def solve_host(self, f_host, phi_host, stream=None):
