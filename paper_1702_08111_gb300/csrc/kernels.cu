@@ -478,9 +478,12 @@ __device__ __forceinline__ void dft8(C (&v)[8], bool inv) {
     t = v[3]; v[3] = v[6]; v[6] = t;
 }
 
+// Exchange through `xs` (72 entries per 8-thread group, row pitch 9) when it
+// is non-null, otherwise through the line's own storage.  With a line pitch of
+// 4 (mod 16) complex FP32 entries, all four phases are free of bank conflicts.
 template <typename C, typename R>
 __device__ __forceinline__ void fft64_line(C *line, int estride, int t, bool valid, int nvalid,
-                                           const C *tw64, bool inv) {
+                                           const C (&wt)[8], bool inv, C *xs) {
     C v[8];
 #pragma unroll
     for (int n2 = 0; n2 < 8; ++n2) {
@@ -490,19 +493,29 @@ __device__ __forceinline__ void fft64_line(C *line, int estride, int t, bool val
     dft8<C, R>(v, inv);
 #pragma unroll
     for (int k1 = 1; k1 < 8; ++k1) {
-        C w = tw64[(t * k1) & 63];
+        C w = wt[k1];  // w64^(t k1), held in registers by the caller
         if (inv) w.y = -w.y;
         v[k1] = cmul(v[k1], w);
     }
-    __syncwarp();
+    if (xs) {
+        // no __syncwarp needed before: xs is private to the group and idle here
 #pragma unroll
-    for (int k1 = 0; k1 < 8; ++k1)
-        if (valid) line[(8 * k1 + t) * estride] = v[k1];
-    __syncwarp();
+        for (int k1 = 0; k1 < 8; ++k1) xs[9 * k1 + t] = v[k1];
+        __syncwarp();
 #pragma unroll
-    for (int n1 = 0; n1 < 8; ++n1) v[n1] = valid ? line[(8 * t + n1) * estride] : Cx<R>::mk(0, 0);
+        for (int n1 = 0; n1 < 8; ++n1) v[n1] = xs[9 * t + n1];
+        __syncwarp();
+    } else {
+        __syncwarp();
+#pragma unroll
+        for (int k1 = 0; k1 < 8; ++k1)
+            if (valid) line[(8 * k1 + t) * estride] = v[k1];
+        __syncwarp();
+#pragma unroll
+        for (int n1 = 0; n1 < 8; ++n1) v[n1] = valid ? line[(8 * t + n1) * estride] : Cx<R>::mk(0, 0);
+        __syncwarp();
+    }
     dft8<C, R>(v, inv);
-    __syncwarp();
 #pragma unroll
     for (int k2 = 0; k2 < 8; ++k2)
         if (valid) line[(t + 8 * k2) * estride] = v[k2];
@@ -510,28 +523,47 @@ __device__ __forceinline__ void fft64_line(C *line, int estride, int t, bool val
 }
 
 // Apply fft64_line to nlines lines; line l at base + off(l) (lstride, plus
-// `gap` for l >= gap_at).  Ends with __syncthreads.
+// `gap` for l >= gap_at).  xs: exchange scratch of blockDim/8 x 72 entries or
+// nullptr.  Ends with __syncthreads.
 template <typename C, typename R>
 __device__ __forceinline__ void fft64_lines(C *base, int nlines, int lstride, int estride, int nvalid,
-                                            const C *tw64, bool inv, int gap_at = 1 << 30, int gap = 0) {
+                                            const C *tw64, bool inv, C *xs, int gap_at = 1 << 30,
+                                            int gap = 0) {
     const int grp = threadIdx.x >> 3, t = threadIdx.x & 7, ngrp = blockDim.x >> 3;
+    C *gx = xs ? xs + grp * 72 : nullptr;
+    C wt[8];  // this lane's twiddles w64^(t k1), k1 = 0..7
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) wt[k1] = tw64[(t * k1) & 63];
     for (int l0 = 0; l0 < nlines; l0 += ngrp) {  // uniform trip count across the CTA
         const int l = l0 + grp;
         const bool valid = l < nlines;
         C *line = base + (valid ? l * lstride + (l >= gap_at ? gap : 0) : 0);
-        fft64_line<C, R>(line, estride, t, valid, nvalid, tw64, inv);
+        // every lane of a group takes the same exchange path (uniform __syncwarp
+        // sites); an invalid group only writes zeros into its own scratch rows
+        fft64_line<C, R>(line, estride, t, valid, nvalid, wt, inv, gx);
     }
     __syncthreads();
 }
 
+// Row pitch of the 64-point line buffers: 68 (4 mod 16) for FP32, 65 for FP64
+// (both conflict-free for the line loads and stores).
+template <typename R> struct Pitch64 { static constexpr int P = sizeof(R) == 4 ? 68 : 65; };
+// FP32 lines exchange through a separate padded buffer; FP64 lines in place
+// (the extra buffer would cost a resident CTA per SM on the FP64 pipe).
+template <typename R> struct UseXs { static constexpr bool v = sizeof(R) == 4; };
+
 // Fused slab for M = 64 with the register FFT (same contract as k_slab).
+// The slab is held as S[z][y] (row z, pitch P), so the global block
+// [zi][yi] loads and the [z row][y] output stores are contiguous in both
+// memories.
 template <typename R>
 __global__ void __launch_bounds__(256) k_slab64(SlabArgs a) {
     using C = typename Cx<R>::T;
-    constexpr int M = 64, MH = 33, P = 65;
+    constexpr int M = 64, MH = 33, P = Pitch64<R>::P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw64 = (C *)smem_raw;  // 64 twiddles exp(-2 pi i j / 64)
     C *S = tw64 + M;
+    C *xs = UseXs<R>::v ? S + M * P : nullptr;  // blockDim/8 x 72 exchange entries
     const int kx = blockIdx.x % MH;
     int p;
     const PlanPtrs &PP = item_plan(a.it, blockIdx.x / MH, p);
@@ -545,37 +577,40 @@ __global__ void __launch_bounds__(256) k_slab64(SlabArgs a) {
     const C *in = (const C *)PP.a1 + ((long)p * MH + kx) * nin * nin;
     for (int e = threadIdx.x; e < nin * nin; e += blockDim.x) {
         const int zi = e / nin, yi = e % nin;
-        S[yi * P + zi] = in[e];
+        S[zi * P + yi] = in[e];
     }
     __syncthreads();
-    // forward y on the nin nonzero z columns (rows >= nin read as zero)
-    fft64_lines<C, R>(S, nin, 1, P, nin, tw64, false);
-    // forward z on all rows (columns >= nin read as zero)
-    fft64_lines<C, R>(S, M, P, 1, nin, tw64, false);
+    // forward y on the nin nonzero z rows (y >= nin read as zero)
+    fft64_lines<C, R>(S, nin, P, 1, nin, tw64, false, xs);
+    // forward z on all 64 y columns (z >= nin read as zero)
+    fft64_lines<C, R>(S, M, 1, P, nin, tw64, false, xs);
     const R *khat = (const R *)PP.khat;
     for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
-        const int r = e / M, c = e % M;
-        const int ky = r < M - r ? r : M - r;
-        const int kz = c < M - c ? c : M - c;
+        const int kz0 = e / M, ky0 = e % M;
+        const int ky = ky0 < M - ky0 ? ky0 : M - ky0;
+        const int kz = kz0 < M - kz0 ? kz0 : M - kz0;
         const R k = khat[((long)kx * MH + ky) * MH + kz];
-        C v = S[r * P + c];
+        C v = S[kz0 * P + ky0];
         v.x *= k;
         v.y *= k;
-        S[r * P + c] = v;
+        S[kz0 * P + ky0] = v;
     }
     __syncthreads();
-    fft64_lines<C, R>(S, M, P, 1, M, tw64, true);
+    // inverse z on all 64 ky columns
+    fft64_lines<C, R>(S, M, 1, P, M, tw64, true, xs);
+    // inverse y on the output z rows only: the wrapped range of positions
+    // pos0 .. pos0+n1-1, then 0 .. W-n1-1
     int pos0 = a.out_off % M;
     if (pos0 < 0) pos0 += M;
     const int n1 = (pos0 + W <= M) ? W : M - pos0;
-    fft64_lines<C, R>(S + pos0, W, 1, P, M, tw64, true, n1, -(pos0 + n1));
+    fft64_lines<C, R>(S + pos0 * P, W, P, 1, M, tw64, true, xs, n1, -(pos0 + n1) * P);
     C *out = (C *)PP.a4 + (long)p * a.nz * MH * W;
     for (int e = threadIdx.x; e < a.nz * W; e += blockDim.x) {
         const int jz = e / W, yo = e % W, zo = a.zrow[jz];
         int pz = (a.out_off + zo) % M, py = (a.out_off + yo) % M;
         if (pz < 0) pz += M;
         if (py < 0) py += M;
-        out[((long)jz * MH + kx) * W + yo] = S[py * P + pz];
+        out[((long)jz * MH + kx) * W + yo] = S[pz * P + py];
     }
 }
 
@@ -598,6 +633,7 @@ struct InvXPArgs {
     int n, s, W, ga, npa, pl0, wa, nc;
     int nz;           // z rows with outputs; zrow[j] = their index zo in [0, W)
     int zrow[64];
+    int maxfft;       // most transformed rows of any z row (sizes the line buffer)
 };
 
 __device__ __forceinline__ bool in_alpha(int c, int n, int ga) { return c >= -ga && c <= n + ga; }
@@ -608,14 +644,17 @@ __device__ __forceinline__ bool on_plane(int c, int n, int ga, int pl0) {
 template <int LOG2M, typename R>
 __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
     using C = typename Cx<R>::T;
-    constexpr int M = 1 << LOG2M, MH = M / 2 + 1, LP = M + 1;
+    constexpr int M = 1 << LOG2M, MH = M / 2 + 1;
+    constexpr int LP = LOG2M == 6 ? Pitch64<R>::P : M + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int rows[64];
     __shared__ int nfft_s;
+    __shared__ unsigned wmask[2];
     const int W = a.W, n = a.n, s = a.s, ga = a.ga, pl0 = a.pl0, wa = a.wa, nc = a.nc;
-    C *tw = (C *)smem_raw;   // M twiddles
-    C *raw = tw + M;         // MH x W
-    C *buf = raw + MH * W;   // up to W lines of LP
+    C *tw = (C *)smem_raw;        // M twiddles
+    C *raw = tw + M;              // MH x W
+    C *buf = raw + MH * W;        // up to a.maxfft lines of LP
+    C *xs = (LOG2M == 6 && UseXs<R>::v) ? buf + a.maxfft * LP : nullptr;
     const int jz = blockIdx.x % a.nz, zi = a.zrow[jz];
     int p;
     const PlanPtrs &PP = item_plan(a.it, blockIdx.x / a.nz, p);
@@ -627,16 +666,28 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
         tw[j] = w;
     }
     const C *in = (const C *)PP.a4 + ((long)p * a.nz + jz) * MH * W;
+#pragma unroll 4
     for (int e = threadIdx.x; e < MH * W; e += blockDim.x) raw[e] = in[e];
     const bool zP = on_plane(z, n, ga, pl0), zA = in_alpha(z, n, ga), zC = (z & 3) == 0;
-    if (threadIdx.x == 0) {
-        int c = 0;
-        for (int yi = 0; yi < W; ++yi) {
-            const int y = yi - s;
-            const bool yA = in_alpha(y, n, ga), yP = on_plane(y, n, ga, pl0), yC = (y & 3) == 0;
-            if ((zP && yA) || (yP && zA) || (zC && yC)) rows[c++] = yi;
+    // rows of this z that need a full transform, compacted with warp ballots (W <= 64)
+    if (threadIdx.x < 64) {
+        const int yi = threadIdx.x, y = yi - s;
+        const bool yA = in_alpha(y, n, ga), yP = on_plane(y, n, ga, pl0), yC = (y & 3) == 0;
+        const bool need = yi < W && ((zP && yA) || (yP && zA) || (zC && yC));
+        const unsigned m = __ballot_sync(0xffffffffu, need);
+        if ((threadIdx.x & 31) == 0) wmask[threadIdx.x >> 5] = m;
+    }
+    __syncthreads();
+    if (threadIdx.x < 64) {
+        const int yi = threadIdx.x;
+        const unsigned m0 = wmask[0], m1 = wmask[1];
+        const unsigned mine = yi < 32 ? m0 : m1;
+        const int lane = yi & 31;
+        if ((mine >> lane) & 1u) {
+            const int before = (yi < 32 ? 0 : __popc(m0)) + __popc(mine & ((1u << lane) - 1u));
+            rows[before] = yi;
         }
-        nfft_s = c;
+        if (yi == 0) nfft_s = __popc(m0) + __popc(m1);
     }
     __syncthreads();
     const int nfft = nfft_s;
@@ -652,7 +703,7 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
         buf[l * LP + k] = v;
     }
     __syncthreads();
-    if (LOG2M == 6) fft64_lines<C, R>(buf, nfft, LP, 1, M, tw, true);
+    if (LOG2M == 6) fft64_lines<C, R>(buf, nfft, LP, 1, M, tw, true, xs);
     else fft_dif<LOG2M>(buf, nfft, LP, 1, tw, true);
     R *cl = (R *)PP.cl + (long)p * nc * nc * nc;
     R *fp = (R *)PP.fp + (long)p * 3 * a.npa * wa * wa;
@@ -699,7 +750,7 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
 // Legendre coefficients c_p^i = sum_m W[m] Q^p(m) f[n i + m] (Boole, R3).
 // ---------------------------------------------------------------------------
 template <typename TF, typename RM>
-__global__ void __launch_bounds__(256) k_moments(Items it, int n, int npoly) {
+__global__ void __launch_bounds__(256) k_moments(Items it, int n, int npoly, int npad) {
     __shared__ double red[8][56];
     int p;
     const PlanPtrs &PP = item_plan(it, blockIdx.x, p);
@@ -729,8 +780,8 @@ __global__ void __launch_bounds__(256) k_moments(Items it, int n, int npoly) {
     if (threadIdx.x < npoly) {
         double v = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
-        mom[(long)p * npoly + threadIdx.x] = v;
-        if (mom_f) mom_f[(long)p * npoly + threadIdx.x] = (float)v;
+        mom[(long)p * npad + threadIdx.x] = v;
+        if (mom_f) mom_f[(long)p * npad + threadIdx.x] = (float)v;
     }
 }
 
@@ -801,7 +852,7 @@ struct AsmArgs {
     const void *cl;          // coarse lattice of the local fields, nc^3 per patch
     const void *mom, *T;     // ring tables in the ring precision RT
     double *FH;
-    int np, n, s, nc, npoly, flo, nf;
+    int np, n, s, nc, npoly, npad, flo, nf;
     int ca_lo, ca_hi, cb_lo, cb_hi;
     double coef[4];  // b_k / H^2
 };
@@ -849,7 +900,7 @@ __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
                 } else {
                     const long t = (((long)(r0 - a.cb_lo) * ncb + (r1 - a.cb_lo)) * ncb +
                                     (r2 - a.cb_lo)) * a.npoly;
-                    const RT *c = (const RT *)a.mom + p * a.npoly;
+                    const RT *c = (const RT *)a.mom + p * a.npad;
                     const RT *Tt = (const RT *)a.T + t;
                     RT v = 0;
                     for (int pp = 0; pp < a.npoly; ++pp) v = fma(c[pp], Tt[pp], v);
@@ -865,8 +916,29 @@ struct BndArgs {
     const int *rmap;
     double *phiB;
     int N, n, np, ga, gb, b, npoly, olo, no, wa, wbx, npa, pl0;
+    int npad;         // row stride of the ring tables (npoly rounded up to 4; zero padding)
     double lw[4][8];  // Lagrange weights for g mod 4 = r (row r), 2b+2 entries
 };
+
+// Dot product of two ring-table rows of n (a multiple of 4) elements.
+__device__ __forceinline__ void ring_dot(const float *c, const float *d, int n, float &acc) {
+    const float4 *c4 = (const float4 *)c, *d4 = (const float4 *)d;
+    for (int q = 0; q < n / 4; ++q) {
+        const float4 x = c4[q], y = d4[q];
+        acc = fmaf(x.x, y.x, acc);
+        acc = fmaf(x.y, y.y, acc);
+        acc = fmaf(x.z, y.z, acc);
+        acc = fmaf(x.w, y.w, acc);
+    }
+}
+__device__ __forceinline__ void ring_dot(const double *c, const double *d, int n, double &acc) {
+    const double2 *c2 = (const double2 *)c, *d2 = (const double2 *)d;
+    for (int q = 0; q < n / 2; ++q) {
+        const double2 x = c2[q], y = d2[q];
+        acc = fma(x.x, y.x, acc);
+        acc = fma(x.y, y.y, acc);
+    }
+}
 
 // phi^B at every face-plane node (axis, plane j, u, v).  RT: precision of the
 // Legendre ring sums (FP64 tier: double; split tier: float).
@@ -883,7 +955,8 @@ __global__ void __launch_bounds__(128) k_boundary(BndArgs a) {
     g[axis] = j * a.n;
     g[axis == 0 ? 1 : 0] = u;
     g[axis == 2 ? 1 : 2] = v;
-    // I^H(phi^H)(g): tensor Lagrange over the in-plane axes (R4)
+    // I^H(phi^H)(g): tensor Lagrange over the in-plane axes (R4), applied as
+    // nested 1D sums (K^2 + K + 1 FMAs for two nontrivial axes)
     const int K = 2 * a.b + 2;
     int kb[3], cnt[3], rr[3];
     for (int d = 0; d < 3; ++d) {
@@ -898,17 +971,24 @@ __global__ void __launch_bounds__(128) k_boundary(BndArgs a) {
     }
     double acc = 0.0;
     for (int e0 = 0; e0 < cnt[0]; ++e0) {
-        const double w0 = rr[0] ? a.lw[rr[0]][e0] : 1.0;
+        double s1 = 0.0;
         for (int e1 = 0; e1 < cnt[1]; ++e1) {
-            const double w1 = w0 * (rr[1] ? a.lw[rr[1]][e1] : 1.0);
-            const long base = ((long)(kb[0] + e0 - a.olo) * a.no + (kb[1] + e1 - a.olo)) * a.no;
-            for (int e2 = 0; e2 < cnt[2]; ++e2) {
-                const double w = w1 * (rr[2] ? a.lw[rr[2]][e2] : 1.0);
-                acc = fma(w, a.phiH[base + (kb[2] + e2 - a.olo)], acc);
+            const double *row = a.phiH + ((long)(kb[0] + e0 - a.olo) * a.no + (kb[1] + e1 - a.olo)) * a.no +
+                                (kb[2] - a.olo);
+            double s2;
+            if (rr[2]) {
+                s2 = 0.0;
+                for (int e2 = 0; e2 < K; ++e2) s2 = fma(a.lw[rr[2]][e2], row[e2], s2);
+            } else {
+                s2 = row[0];
             }
+            s1 = rr[1] ? fma(a.lw[rr[1]][e1], s2, s1) : s2;
         }
+        acc = rr[0] ? fma(a.lw[rr[0]][e0], s1, acc) : s1;
     }
-    // local corrections of the patches whose Omega_beta holds g (ascending index)
+    // local corrections of the patches whose Omega_beta holds g (ascending index);
+    // the Legendre ring terms accumulate in the ring precision RT
+    RT ring = 0;
     int lo[3], hi[3], alo[3], ahi[3];
     for (int d = 0; d < 3; ++d) {
         lo[d] = max(0, -floordiv(-(g[d] - a.n - a.gb), a.n));
@@ -934,14 +1014,12 @@ __global__ void __launch_bounds__(128) k_boundary(BndArgs a) {
                     acc += a.resid[((p * 3 * a.npa + slot) * a.wa + (uu + a.ga)) * a.wa + (vv + a.ga)];
                 } else {
                     const int ri = a.rmap[((long)(r0 + a.gb) * a.wbx + (r1 + a.gb)) * a.wbx + (r2 + a.gb)];
-                    const RT *c = (const RT *)a.mom + p * a.npoly;
-                    const RT *Dr = (const RT *)a.D + (long)ri * a.npoly;
-                    RT vv = 0;
-                    for (int pp = 0; pp < a.npoly; ++pp) vv = fma(c[pp], Dr[pp], vv);
-                    acc += (double)vv;
+                    const RT *c = (const RT *)a.mom + p * a.npad;
+                    const RT *Dr = (const RT *)a.D + (long)ri * a.npad;
+                    ring_dot(c, Dr, a.npad, ring);
                 }
             }
-    a.phiB[idx] = acc;
+    a.phiB[idx] = acc + (double)ring;
 }
 
 struct DirArgs {
@@ -1195,15 +1273,31 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
         SlabArgs a{tw, nin, W, -g.s, it, nz, {}};
         for (int j = 0; j < nz; ++j) a.zrow[j] = zrow[j];
         if (LOG2M == 6)
-            k_slab64<R><<<nb * MH, 256, (size_t)(M + M * (M + 1)) * 2 * sizeof(R), st>>>(a);
+            k_slab64<R><<<nb * MH, 256,
+                          (size_t)(M + M * Pitch64<R>::P + (UseXs<R>::v ? 32 * 72 : 0)) * 2 * sizeof(R),
+                          st>>>(a);
         else
             k_slab<LOG2M, R><<<nb * MH, 256, fft_smem_bytes<R>(M, M, M + 1), st>>>(a);
     }
     mark(pl, 3, st);
     {
-        InvXPArgs a{it, tw, g.n, g.s, W, g.ga, g.npa, g.pl0, g.wa, g.nc, nz, {}};
+        InvXPArgs a{it, tw, g.n, g.s, W, g.ga, g.npa, g.pl0, g.wa, g.nc, nz, {}, 0};
         for (int j = 0; j < nz; ++j) a.zrow[j] = zrow[j];
-        const size_t sm = ((size_t)M + (size_t)MH * W + (size_t)W * (M + 1)) * 2 * sizeof(R);
+        // rows needing a full transform, per z row (the same rule as the kernel)
+        auto inA = [&](int c) { return c >= -g.ga && c <= g.n + g.ga; };
+        auto onP = [&](int c) { return inA(c) && ((c - g.pl0) % g.n) == 0; };
+        for (int j = 0; j < nz; ++j) {
+            const int z = zrow[j] - g.s;
+            int cnt = 0;
+            for (int yi = 0; yi < W; ++yi) {
+                const int y = yi - g.s;
+                if ((onP(z) && inA(y)) || (onP(y) && inA(z)) || ((z & 3) == 0 && (y & 3) == 0)) ++cnt;
+            }
+            a.maxfft = cnt > a.maxfft ? cnt : a.maxfft;
+        }
+        const int LPh = LOG2M == 6 ? Pitch64<R>::P : M + 1;
+        const size_t xsn = (LOG2M == 6 && UseXs<R>::v) ? 32 * 72 : 0;
+        const size_t sm = ((size_t)M + (size_t)MH * W + (size_t)a.maxfft * LPh + xsn) * 2 * sizeof(R);
         k_inv_x_pruned<LOG2M, R><<<nb * a.nz, 256, sm, st>>>(a);
     }
     return cudaGetLastError();
@@ -1258,9 +1352,9 @@ void configure_kernels() {
 cudaError_t launch_moments(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
     const Geom &g = pl->g;
     if (g.tier == MLC_TIER_SPLIT)
-        k_moments<float, float><<<it.nitems, 256, 0, st>>>(it, g.n, g.npoly);
+        k_moments<float, float><<<it.nitems, 256, 0, st>>>(it, g.n, g.npoly, g.npad);
     else
-        k_moments<double, double><<<it.nitems, 256, 0, st>>>(it, g.n, g.npoly);
+        k_moments<double, double><<<it.nitems, 256, 0, st>>>(it, g.n, g.npoly, g.npad);
     return cudaGetLastError();
 }
 
@@ -1311,7 +1405,7 @@ cudaError_t launch_assemble(const mlc_plan_s *pl, cudaStream_t st) {
     a.cl = pl->cl; a.FH = pl->FH;
     a.mom = split ? (const void *)pl->mom_f : (const void *)pl->mom;
     a.T = split ? (const void *)pl->Ttab_f : (const void *)pl->Ttab;
-    a.np = g.np; a.n = g.n; a.s = g.s; a.nc = g.nc; a.npoly = g.npoly; a.flo = g.flo; a.nf = g.nf;
+    a.np = g.np; a.n = g.n; a.s = g.s; a.nc = g.nc; a.npoly = g.npoly; a.npad = g.npad; a.flo = g.flo; a.nf = g.nf;
     a.ca_lo = g.ca_lo; a.ca_hi = g.ca_hi; a.cb_lo = g.cb_lo; a.cb_hi = g.cb_hi;
     double b[4];
     stencil_b(g.Q, b);
@@ -1344,6 +1438,7 @@ cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st) {
     a.rmap = pl->rmap; a.phiB = pl->phiB;
     a.N = g.N; a.n = g.n; a.np = g.np; a.ga = g.ga; a.gb = g.gb; a.b = g.b; a.npoly = g.npoly;
     a.olo = g.olo; a.no = g.no; a.wa = g.wa; a.wbx = g.wbx; a.npa = g.npa; a.pl0 = g.pl0;
+    a.npad = g.npad;
     lagrange_rows(g.b, a.lw);
     const long tot = g.n_planes_total;
     const unsigned nbk = (unsigned)((tot + 127) / 128);

@@ -20,6 +20,7 @@ constexpr int kTimedLaunches = 13;
 // ---------------------------------------------------------------------------
 struct Geom {
     int N, n, s, C, P, Q, b, ga, gb, np, NP, npoly, nb, W, M, log2M, Mh;
+    int npad;                        // npoly rounded up to a multiple of 4 (row stride of moments, D)
     int tier, mode;
     double h, H, R;
     int ca_lo, ca_hi, cb_lo, cb_hi;  // coarse boxes C(Omega_alpha), C(Omega_beta), relative

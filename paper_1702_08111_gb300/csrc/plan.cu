@@ -183,6 +183,7 @@ mlc_status derive_geometry(const mlc_params &pp, Geom &g) {
         for (int c = 0; c < g.P; ++c)
             for (int e = 0; e < g.P; ++e)
                 if (a + c + e < g.P) ++g.npoly;
+    g.npad = (g.npoly + 3) & ~3;
     g.nb = g.n + 1;
     g.W = g.n + 2 * g.s + 1;
     g.M = next_pow2(2 * (g.n + g.s));
@@ -351,13 +352,13 @@ mlc_status build_tables(mlc_plan_s *pl) {
             for (auto &pr : lapT[t])
                 for (int p = 0; p < np_; ++p)
                     Ttab[t * np_ + p] += pr.second * B[(size_t)pr.first * np_ + p];
-        Dtab.assign(ring_nodes.size() * np_, 0.0);
+        Dtab.assign(ring_nodes.size() * g.npad, 0.0);  // rows padded with zeros to npad
         for (size_t r = 0; r < ring_nodes.size(); ++r)
             for (int p = 0; p < np_; ++p) {
                 double iv = 0.0;
                 for (size_t j = 0; j < rn_st[r].size(); ++j)
                     iv += ring_w[r][j] * B[(size_t)rn_st[r][j] * np_ + p];
-                Dtab[r * np_ + p] = B[(size_t)rn_self[r] * np_ + p] - iv;
+                Dtab[r * g.npad + p] = B[(size_t)rn_self[r] * np_ + p] - iv;
             }
     }
     g.nr_face = (int)ring_nodes.size();
@@ -513,9 +514,13 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
             TRY(dev_upload(pl, &pl->khat_f, kf));
             TRY(dev_upload(pl, &pl->tw_f, tf));
         }
-        TRY(dev_alloc(pl, &pl->mom, NP * G.npoly));
+        TRY(dev_alloc(pl, &pl->mom, NP * G.npad));  // padding stays zero (memset below)
+        TRY_CUDA(cudaMemset(pl->mom, 0, NP * G.npad * sizeof(double)));
         TRY(dev_alloc(pl, &pl->resid, NP * 3 * (size_t)G.npa * G.wa * G.wa));
-        if (G.tier == MLC_TIER_SPLIT) TRY(dev_alloc(pl, &pl->mom_f, NP * G.npoly));
+        if (G.tier == MLC_TIER_SPLIT) {
+            TRY(dev_alloc(pl, &pl->mom_f, NP * G.npad));
+            TRY_CUDA(cudaMemset(pl->mom_f, 0, NP * G.npad * sizeof(float)));
+        }
         const size_t nf = G.nf, no = G.no, Mc = G.Mc, Mhc = G.Mhc;
         TRY(dev_alloc(pl, &pl->FH, nf * nf * nf));
         TRY(dev_alloc(pl, &pl->cbuf0, std::max(nf * nf * Mhc, no * Mc * Mhc)));
@@ -675,6 +680,11 @@ mlc_status mlc_debug_export(mlc_plan_t pl, int stage, void *host, size_t bytes) 
         default: return MLC_ERR_INVALID_ARG;
     }
     TRY_CUDA(cudaDeviceSynchronize());
+    if (stage == MLC_STAGE_MOMENTS) {  // rows are stored with stride npad
+        TRY_CUDA(cudaMemcpy2D(host, pl->g.npoly * sizeof(double), src, pl->g.npad * sizeof(double),
+                              pl->g.npoly * sizeof(double), pl->g.NP, cudaMemcpyDeviceToHost));
+        return MLC_OK;
+    }
     TRY_CUDA(cudaMemcpy(host, src, bytes, cudaMemcpyDeviceToHost));
     return MLC_OK;
 }
