@@ -96,6 +96,13 @@ mlc_status mlc_plan_create(int N, int patch, int support, int coarsening, int P,
 mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out);
 mlc_status mlc_plan_destroy(mlc_plan_t plan);
 
+/* Synchronise the device and report kernel-side failures of this plan's
+ * solves since the last check: TIMEOUT if a bounded wait inside a kernel (the
+ * staging of a block by an asynchronous bulk copy) gave up, so the result of
+ * that solve is not valid; the flag is then cleared.  mlc_solve_host calls it
+ * before returning. */
+mlc_status mlc_plan_status(mlc_plan_t plan);
+
 /* Bytes of device workspace the plan holds (tables excluded). */
 mlc_status mlc_plan_workspace_bytes(mlc_plan_t plan, size_t *bytes);
 
@@ -171,6 +178,11 @@ mlc_status mlc_debug_stage_bytes(mlc_plan_t plan, int stage, size_t *bytes);
  * count must be >= 13. */
 mlc_status mlc_debug_set_timing(mlc_plan_t plan, int enable);
 mlc_status mlc_debug_timing(mlc_plan_t plan, float *ms_out, int count);
+/* Configuration the batch autotuner chose for these arrays (as passed to
+ * mlc_batch_solve): 2 x (parallel branches of the per-problem coarse steps)
+ * + 1 if the local-convolution slab kernel runs persistently; 0 if this set
+ * has not been solved yet. */
+int mlc_debug_batch_choice(int count, const mlc_plan_t *plans, const void *const *f, void *const *phi);
 mlc_status mlc_debug_export(mlc_plan_t plan, int stage, void *host, size_t bytes);
 /* Geometry of the plan: out[0..15] = N, n, s, b, g_alpha, g_beta, P, npoly,
  * fh_lo, fh_hi, phih_lo, phih_hi, M (patch FFT), Mc (coarse FFT), L (DGF

@@ -25,6 +25,7 @@ struct BatchCtx {
     int nitems = 0;
     cudaGraphExec_t exec = nullptr;
     int branches = 0;
+    int persist = 0;
     float tuned_ms = 0.f;
 };
 
@@ -37,7 +38,7 @@ std::map<std::vector<uintptr_t>, BatchCtx *> g_cache;
         if (_e != cudaSuccess) return _e;  \
     } while (0)
 
-cudaError_t capture(BatchCtx &c, int branches, cudaGraphExec_t *out) {
+cudaError_t capture(BatchCtx &c, int branches, int persist, cudaGraphExec_t *out) {
     cudaStream_t cap;
     TRYE(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     std::vector<cudaStream_t> side(branches);
@@ -45,7 +46,8 @@ cudaError_t capture(BatchCtx &c, int branches, cudaGraphExec_t *out) {
     for (auto &s : side) cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     for (auto &e : ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
     const mlc_plan_s *rep = c.plans[0];
-    const Items it{c.d_items, c.d_plans, c.nitems};
+    Items it{c.d_items, c.d_plans, c.nitems};
+    it.persist = persist;
     cudaError_t err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     g_capturing = true;
     if (err == cudaSuccess) err = launch_moments(rep, it, cap);
@@ -76,19 +78,23 @@ cudaError_t capture(BatchCtx &c, int branches, cudaGraphExec_t *out) {
     return err;
 }
 
-// Time a few replays of each candidate and keep the fastest.
+// Time a few replays of each candidate (parallel branches for the coarse
+// steps x persistent or one-CTA-per-slab local convolutions) and keep the
+// fastest.
 cudaError_t build_and_tune(BatchCtx &c, cudaStream_t st) {
     const int nplans = (int)c.plans.size();
-    std::vector<int> cand;
+    std::vector<std::pair<int, int>> cand;
     for (int b : {1, 4, 16})
-        if (b == 1 || b <= nplans) cand.push_back(b);
+        if (b == 1 || b <= nplans)
+            for (int ps : {0, 1}) cand.push_back({b, ps});
     cudaEvent_t e0, e1;
     TRYE(cudaEventCreate(&e0));
     TRYE(cudaEventCreate(&e1));
     cudaError_t err = cudaSuccess;
-    for (int b : cand) {
+    for (auto bp : cand) {
+        const int b = bp.first;
         cudaGraphExec_t ex = nullptr;
-        err = capture(c, b, &ex);
+        err = capture(c, b, bp.second, &ex);
         if (err != cudaSuccess) break;
         float best = 1e30f;
         for (int r = 0; r < 4 && err == cudaSuccess; ++r) {
@@ -108,6 +114,7 @@ cudaError_t build_and_tune(BatchCtx &c, cudaStream_t st) {
             if (c.exec) cudaGraphExecDestroy(c.exec);
             c.exec = ex;
             c.branches = b;
+            c.persist = bp.second;
             c.tuned_ms = best;
         } else {
             cudaGraphExecDestroy(ex);
@@ -199,9 +206,10 @@ void mlc_batch_forget(mlc_plan_t plan) {
     }
 }
 
-// Number of parallel branches the autotuner chose for the batch of `plans`
-// last solved with these arrays (0 if none).
-int mlc_batch_branches(int count, const mlc_plan_t *plans, const void *const *f, void *const *phi) {
+// Configuration the autotuner chose for the batch of `plans` solved with these
+// arrays: parallel branches * 2 + persistent flag (0 if the batch is unknown).
+extern "C" int mlc_debug_batch_choice(int count, const mlc_plan_t *plans, const void *const *f,
+                                      void *const *phi) {
     std::vector<uintptr_t> key;
     for (int k = 0; k < count; ++k) {
         key.push_back((uintptr_t)plans[k]);
@@ -210,5 +218,5 @@ int mlc_batch_branches(int count, const mlc_plan_t *plans, const void *const *f,
     }
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_cache.find(key);
-    return it == g_cache.end() ? 0 : it->second->branches;
+    return it == g_cache.end() ? 0 : it->second->branches * 2 + it->second->persist;
 }

@@ -119,6 +119,42 @@ __device__ __forceinline__ void fft_dit(C *buf, int nlines, int lstride, int est
     }
 }
 
+// ---- TMA bulk copy (global -> shared) completing on an mbarrier -------------
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for phase `parity` of an mbarrier; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
+    for (int i = 0; i < (1 << 22); ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
 // Plan record and local patch index of a work item.
 __device__ __forceinline__ const PlanPtrs &item_plan(const Items &it, int item, int &p) {
     if (it.items) {
@@ -365,6 +401,7 @@ struct SlabArgs {
     Items it;  // per item: in = a1, out = a4, khat of its plan
     int nz;    // output z rows: zrow[j] in [0, nout), the rows the inverse-x step reads
     int zrow[64];
+    int blk;   // complex entries per (patch, z row) output block (16-byte multiple)
 };
 
 template <int LOG2M, typename R>
@@ -413,13 +450,13 @@ __global__ void __launch_bounds__(256) k_slab(SlabArgs a) {
     // output positions (out_off + t) mod M, t < W: one wrapped range starting at pos0
     const int n1 = (pos0 + W <= M) ? W : M - pos0;  // columns pos0 .. pos0+n1-1, then 0 ..
     fft_dit<LOG2M>(S + pos0, W, 1, P, s_tw, true, n1, -(pos0 + n1));
-    C *out = (C *)PP.a4 + (long)p * a.nz * MH * W;
+    C *out = (C *)PP.a4 + (long)p * a.nz * a.blk;
     for (int e = threadIdx.x; e < a.nz * W; e += blockDim.x) {
         const int jz = e / W, yo = e % W, zo = a.zrow[jz];
         int pz = (a.out_off + zo) % M, py = (a.out_off + yo) % M;
         if (pz < 0) pz += M;
         if (py < 0) py += M;
-        out[((long)jz * MH + kx) * W + yo] = S[py * P + pz];
+        out[(long)jz * a.blk + kx * W + yo] = S[py * P + pz];
     }
 }
 
@@ -564,9 +601,6 @@ __global__ void __launch_bounds__(256) k_slab64(SlabArgs a) {
     C *tw64 = (C *)smem_raw;  // 64 twiddles exp(-2 pi i j / 64)
     C *S = tw64 + M;
     C *xs = UseXs<R>::v ? S + M * P : nullptr;  // blockDim/8 x 72 exchange entries
-    const int kx = blockIdx.x % MH;
-    int p;
-    const PlanPtrs &PP = item_plan(a.it, blockIdx.x / MH, p);
     const int nin = a.nin, W = a.nout;
     const C *tw = (const C *)a.tw;  // M/2 entries; extend by w^(j+32) = -w^j
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
@@ -574,6 +608,12 @@ __global__ void __launch_bounds__(256) k_slab64(SlabArgs a) {
         if (j >= 32) { w.x = -w.x; w.y = -w.y; }
         tw64[j] = w;
     }
+    // one slab per CTA, or (persistent launch) a grid-stride loop over slabs
+    const int nunits = a.it.nitems * MH;
+    for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
+    const int kx = unit % MH;
+    int p;
+    const PlanPtrs &PP = item_plan(a.it, unit / MH, p);
     const C *in = (const C *)PP.a1 + ((long)p * MH + kx) * nin * nin;
     for (int e = threadIdx.x; e < nin * nin; e += blockDim.x) {
         const int zi = e / nin, yi = e % nin;
@@ -604,13 +644,15 @@ __global__ void __launch_bounds__(256) k_slab64(SlabArgs a) {
     if (pos0 < 0) pos0 += M;
     const int n1 = (pos0 + W <= M) ? W : M - pos0;
     fft64_lines<C, R>(S + pos0 * P, W, P, 1, M, tw64, true, xs, n1, -(pos0 + n1) * P);
-    C *out = (C *)PP.a4 + (long)p * a.nz * MH * W;
+    C *out = (C *)PP.a4 + (long)p * a.nz * a.blk;
     for (int e = threadIdx.x; e < a.nz * W; e += blockDim.x) {
         const int jz = e / W, yo = e % W, zo = a.zrow[jz];
         int pz = (a.out_off + zo) % M, py = (a.out_off + yo) % M;
         if (pz < 0) pz += M;
         if (py < 0) py += M;
-        out[((long)jz * MH + kx) * W + yo] = S[pz * P + py];
+        out[(long)jz * a.blk + kx * W + yo] = S[pz * P + py];
+    }
+    __syncthreads();  // S is rewritten by the next unit
     }
 }
 
@@ -634,6 +676,7 @@ struct InvXPArgs {
     int nz;           // z rows with outputs; zrow[j] = their index zo in [0, W)
     int zrow[64];
     int maxfft;       // most transformed rows of any z row (sizes the line buffer)
+    int blk;          // complex entries per (patch, z row) input block (16-byte multiple)
 };
 
 __device__ __forceinline__ bool in_alpha(int c, int n, int ga) { return c >= -ga && c <= n + ga; }
@@ -652,8 +695,8 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
     __shared__ unsigned wmask[2];
     const int W = a.W, n = a.n, s = a.s, ga = a.ga, pl0 = a.pl0, wa = a.wa, nc = a.nc;
     C *tw = (C *)smem_raw;        // M twiddles
-    C *raw = tw + M;              // MH x W
-    C *buf = raw + MH * W;        // up to a.maxfft lines of LP
+    C *raw = tw + M;              // MH x W (block of a.blk entries, 16-byte aligned)
+    C *buf = raw + a.blk;         // up to a.maxfft lines of LP
     C *xs = (LOG2M == 6 && UseXs<R>::v) ? buf + a.maxfft * LP : nullptr;
     const int jz = blockIdx.x % a.nz, zi = a.zrow[jz];
     int p;
@@ -665,9 +708,24 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
         if (j >= M / 2) { w.x = -w.x; w.y = -w.y; }
         tw[j] = w;
     }
-    const C *in = (const C *)PP.a4 + ((long)p * a.nz + jz) * MH * W;
-#pragma unroll 4
-    for (int e = threadIdx.x; e < MH * W; e += blockDim.x) raw[e] = in[e];
+    const C *in = (const C *)PP.a4 + ((long)p * a.nz + jz) * a.blk;
+    // stage the contiguous block with one TMA bulk copy
+    __shared__ unsigned long long bar;
+    const unsigned bytes = (unsigned)(a.blk * sizeof(C));
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_expect_tx(&bar, bytes);
+        bulk_g2s(raw, in, bytes, &bar);
+    }
+    __syncthreads();
+    const bool arrived = mbar_wait_bounded(&bar, 0);
+    if (__syncthreads_or(!arrived)) {  // uniform decision for the whole CTA
+        if (threadIdx.x == 0) {
+            atomicExch(PP.err, 1);
+            mbar_wait_bounded(&bar, 0);  // one more bounded wait for the copy in flight
+        }
+        return;
+    }
     const bool zP = on_plane(z, n, ga, pl0), zA = in_alpha(z, n, ga), zC = (z & 3) == 0;
     // rows of this z that need a full transform, compacted with warp ballots (W <= 64)
     if (threadIdx.x < 64) {
@@ -1270,18 +1328,27 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
     }
     mark(pl, 2, st);
     {
-        SlabArgs a{tw, nin, W, -g.s, it, nz, {}};
+        SlabArgs a{tw, nin, W, -g.s, it, nz, {}, g.a4blk};
         for (int j = 0; j < nz; ++j) a.zrow[j] = zrow[j];
-        if (LOG2M == 6)
-            k_slab64<R><<<nb * MH, 256,
-                          (size_t)(M + M * Pitch64<R>::P + (UseXs<R>::v ? 32 * 72 : 0)) * 2 * sizeof(R),
-                          st>>>(a);
+        if (LOG2M == 6) {
+            const size_t sm = (size_t)(M + M * Pitch64<R>::P + (UseXs<R>::v ? 32 * 72 : 0)) * 2 * sizeof(R);
+            int grid = nb * MH;
+            if (it.persist) {  // one wave of resident CTAs walking all slabs
+                int dev = 0, nsm = 0, occ = 0;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_slab64<R>, 256, sm);
+                const int wave = nsm * (occ > 0 ? occ : 1);
+                grid = grid < wave ? grid : wave;
+            }
+            k_slab64<R><<<grid, 256, sm, st>>>(a);
+        }
         else
             k_slab<LOG2M, R><<<nb * MH, 256, fft_smem_bytes<R>(M, M, M + 1), st>>>(a);
     }
     mark(pl, 3, st);
     {
-        InvXPArgs a{it, tw, g.n, g.s, W, g.ga, g.npa, g.pl0, g.wa, g.nc, nz, {}, 0};
+        InvXPArgs a{it, tw, g.n, g.s, W, g.ga, g.npa, g.pl0, g.wa, g.nc, nz, {}, 0, g.a4blk};
         for (int j = 0; j < nz; ++j) a.zrow[j] = zrow[j];
         // rows needing a full transform, per z row (the same rule as the kernel)
         auto inA = [&](int c) { return c >= -g.ga && c <= g.n + g.ga; };
@@ -1297,7 +1364,7 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
         }
         const int LPh = LOG2M == 6 ? Pitch64<R>::P : M + 1;
         const size_t xsn = (LOG2M == 6 && UseXs<R>::v) ? 32 * 72 : 0;
-        const size_t sm = ((size_t)M + (size_t)MH * W + (size_t)a.maxfft * LPh + xsn) * 2 * sizeof(R);
+        const size_t sm = ((size_t)M + (size_t)g.a4blk + (size_t)a.maxfft * LPh + xsn) * 2 * sizeof(R);
         k_inv_x_pruned<LOG2M, R><<<nb * a.nz, 256, sm, st>>>(a);
     }
     return cudaGetLastError();

@@ -34,6 +34,9 @@ struct Geom {
     int nr_face;                     // relative face nodes in beta \ alpha
     int npa, pl0;                    // face planes per axis inside Omega_alpha, first at pl0
     int nc;                          // coarse points per axis of the field box, (n + 2s)/4 + 1
+    int nzr;                         // z rows of the field box the pruned inverse x reads
+    int a4blk;                       // complex entries per (patch, z row) block of the slab output,
+                                     // (M/2+1) W rounded up to a multiple of 16 bytes
     int plane_n;                     // (N+1)^2 nodes per face plane
     long n_planes_total;             // 3 (np+1) (N+1)^2
 };
@@ -56,12 +59,14 @@ struct PlanPtrs {
     const double *lam;    // Dirichlet inverse eigenvalues h^2 / lambda
     int N, np;
     double c2h2, inv_h2;  // h^2 / 12, 1 / h^2
+    int *err;             // the plan's error word
 };
 
 struct Items {
     const int2 *items;    // (plan slot, local patch); nullptr: plan 0, item = patch
     const PlanPtrs *plans;
     int nitems;
+    int persist = 0;      // 1: launch the slab kernel persistently (one wave of resident CTAs)
 };
 
 }  // namespace mlc
@@ -102,6 +107,7 @@ struct mlc_plan_s {
     double *phiH;            // no^3
     double *phiB;            // face planes
     void *f_stage, *phi_stage;  // device staging for mlc_solve_host
+    int *err;                // device error word: nonzero if a bounded wait in a kernel gave up
     size_t ws_bytes;
     std::vector<void *> owned;  // device allocations to free
     mlc::PlanPtrs *dptrs = nullptr;  // device copy of this plan's PlanPtrs (f, phi filled per solve)

@@ -204,6 +204,16 @@ mlc_status derive_geometry(const mlc_params &pp, Geom &g) {
     if (g.n > 16) return MLC_ERR_UNSUPPORTED;  // Dirichlet tile held in shared memory
     g.S = (2 * g.b + 2) * (2 * g.b + 2);
     g.nc = (g.n + 2 * g.s) / 4 + 1;
+    g.nzr = 0;
+    for (int zi = 0; zi < g.W; ++zi) {
+        const int z = zi - g.s;
+        if ((z >= -g.ga && z <= g.n + g.ga) || (z % 4 == 0)) ++g.nzr;
+    }
+    {
+        const int cb = g.tier == MLC_TIER_SPLIT ? 8 : 16;  // bytes per complex entry
+        const int per16 = 16 / cb;                          // entries per 16 bytes
+        g.a4blk = ((g.Mh * g.W + per16 - 1) / per16) * per16;
+    }
     g.wa = g.n + 2 * g.ga + 1;
     g.wbx = g.n + 2 * g.gb + 1;
     g.plane_n = (g.N + 1) * (g.N + 1);
@@ -484,13 +494,9 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
                                      G.H * G.H / ((double)G.Mc * G.Mc * G.Mc), pl->khat_c));
         const size_t NP = G.NP, nb = G.nb, W = G.W, M = G.M, Mh = G.Mh;
         (void)M;
-        int nzr = 0;  // z rows of the field box the pruned inverse x reads
-        for (int zi = 0; zi < G.W; ++zi) {
-            const int z = zi - G.s;
-            if ((z >= -G.ga && z <= G.n + G.ga) || (z % 4 == 0)) ++nzr;
-        }
-        const size_t A1 = NP * nb * nb * Mh, A4 = NP * (size_t)nzr * W * Mh;
+        (void)W;
         const size_t rb = G.tier == MLC_TIER_SPLIT ? sizeof(float) : sizeof(double);
+        const size_t A1 = NP * nb * nb * Mh, A4 = NP * (size_t)G.nzr * G.a4blk;
         char *b0 = nullptr, *b1 = nullptr, *bc = nullptr, *bf = nullptr;
         TRY(dev_alloc(pl, &b0, A1 * 2 * rb));   // [p][kx][zi][yi]
         TRY(dev_alloc(pl, &b1, A4 * 2 * rb));   // [p][z row][kx][yo]
@@ -527,6 +533,8 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
         TRY(dev_alloc(pl, &pl->cbuf1, std::max(nf * Mc * Mhc, no * no * Mhc)));
         TRY(dev_alloc(pl, &pl->phiH, no * no * no));
         TRY(dev_alloc(pl, &pl->phiB, (size_t)G.n_planes_total));
+        TRY(dev_alloc(pl, &pl->err, 1, false));
+        TRY_CUDA(cudaMemset(pl->err, 0, sizeof(int)));
         return MLC_OK;
     };
     if (st == MLC_OK) st = alloc_all();
@@ -549,6 +557,7 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
         h.np = G.np;
         h.c2h2 = G.h * G.h / 12.0;
         h.inv_h2 = 1.0 / (G.h * G.h);
+        h.err = pl->err;
         st = dev_upload(pl, &pl->dptrs, std::vector<PlanPtrs>{h});
     }
     if (st == MLC_OK) st = to_status(cudaDeviceSynchronize());
@@ -633,6 +642,18 @@ mlc_status mlc_solve_host(mlc_plan_t pl, const void *f_host, void *phi_host, voi
     TRY(mlc_solve(pl, pl->f_stage, pl->phi_stage, stream));
     TRY_CUDA(cudaMemcpyAsync(phi_host, pl->phi_stage, N3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     TRY_CUDA(cudaStreamSynchronize(st));
+    return mlc_plan_status(pl);
+}
+
+mlc_status mlc_plan_status(mlc_plan_t pl) {
+    if (!pl) return MLC_ERR_INVALID_ARG;
+    TRY_CUDA(cudaDeviceSynchronize());
+    int e = 0;
+    TRY_CUDA(cudaMemcpy(&e, pl->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        TRY_CUDA(cudaMemset(pl->err, 0, sizeof(int)));
+        return MLC_ERR_TIMEOUT;
+    }
     return MLC_OK;
 }
 

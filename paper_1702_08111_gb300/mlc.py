@@ -23,7 +23,8 @@ EXPORTED = [
     "mlc_plan_workspace_bytes", "mlc_solve", "mlc_solve_host", "mlc_batch_solve",
     "mlc_debug_stage_bytes", "mlc_debug_export", "mlc_plan_info", "mlc_server_create",
     "mlc_server_destroy", "mlc_server_enqueue", "mlc_server_wait", "mlc_status_string",
-    "mlc_debug_set_timing", "mlc_debug_timing", "mlc_solve_noalloc",
+    "mlc_debug_set_timing", "mlc_debug_timing", "mlc_solve_noalloc", "mlc_plan_status",
+    "mlc_debug_batch_choice",
 ]
 LAUNCH_NAMES = ["moments", "conv_fwd_x", "conv_slab", "conv_inv_x", "resid", "assemble",
                 "coarse_fwd_x", "coarse_fwd_y", "coarse_z_kernel", "coarse_inv_y", "coarse_inv_x",
@@ -72,6 +73,8 @@ def load_library(path: str = LIB_PATH):
     lib.mlc_solve.argtypes = [vp, vp, vp, vp]
     lib.mlc_solve_host.argtypes = [vp, vp, vp, vp]
     lib.mlc_solve_noalloc.argtypes = [vp, vp, vp, vp]
+    lib.mlc_plan_status.argtypes = [vp]
+    lib.mlc_debug_batch_choice.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]
     lib.mlc_batch_solve.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
     lib.mlc_debug_stage_bytes.argtypes = [vp, i, ctypes.POINTER(ctypes.c_size_t)]
     lib.mlc_debug_export.argtypes = [vp, i, vp, ctypes.c_size_t]
@@ -169,6 +172,10 @@ class Plan:
         except Exception:
             pass
 
+    def status(self):
+        """mlc_plan_status: synchronise; raise MLCError(TIMEOUT) if a kernel's bounded wait gave up."""
+        _check(load_library().mlc_plan_status(self._h), "mlc_plan_status")
+
     def workspace_bytes(self) -> int:
         v = ctypes.c_size_t()
         _check(load_library().mlc_plan_workspace_bytes(self._h, ctypes.byref(v)), "workspace")
@@ -246,6 +253,16 @@ class Plan:
             m = i.L + 1
             return out.reshape(m, m, m)
         return out
+
+
+def batch_choice(plans, fs, phis) -> dict:
+    """The batch autotuner's choice for these arrays: branches and persistence."""
+    k = len(plans)
+    H = (ctypes.c_void_p * k)(*[p.handle.value for p in plans])
+    F = (ctypes.c_void_p * k)(*[f.data_ptr() for f in fs])
+    P = (ctypes.c_void_p * k)(*[p.data_ptr() for p in phis])
+    v = load_library().mlc_debug_batch_choice(k, H, F, P)
+    return {"branches": v // 2, "persistent_slab": bool(v & 1)}
 
 
 def batch_solve(plans, fs, phis, stream=None):

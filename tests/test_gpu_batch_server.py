@@ -41,6 +41,10 @@ def test_batch_equals_standalone(torch_cuda, tier):
     torch.cuda.synchronize()
     for a, b in zip(alone, phis):
         assert torch.equal(a, b)
+    for p in plans:
+        p.status()
+    ch = mlc.batch_choice(plans, fs, phis)
+    assert ch["branches"] in (1, 4, 16)
 
 
 def test_batch_small_patches_and_errors(torch_cuda):

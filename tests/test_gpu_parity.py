@@ -57,6 +57,7 @@ def _run(torch, prm_kw, f_open, stages=True, **plan_kw):
     f = torch.from_numpy(f_open).cuda()
     phi = plan.solve(f)
     torch.cuda.synchronize()
+    plan.status()  # no kernel-side bounded wait gave up
     res = {"phi": phi.cpu().numpy()}
     if stages:
         res["moments"] = plan.export(mlc.STAGE_MOMENTS)
