@@ -657,6 +657,199 @@ __global__ void __launch_bounds__(256) k_slab64(SlabArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Double-float arithmetic: a value is an unevaluated sum hi + lo of two FP32
+// numbers (|lo| <= ulp(hi)/2), about 48 significand bits.  Sums use the
+// error-free two-sum of Knuth, products the FMA-based two-product; the FFT
+// error bound is relative to the data norm, so the additions need not
+// renormalise the low parts twice.  GB300 issues FP32 on ~67x more lanes than
+// FP64, so the FP64 tier's local-convolution slab runs in this arithmetic.
+// ---------------------------------------------------------------------------
+struct dfl {
+    float hi, lo;
+};
+struct dcx {
+    dfl x, y;
+};
+
+__device__ __forceinline__ dfl df_from(double v) {
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ double df_to(dfl a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ dfl two_sum(float a, float b) {
+    const float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dfl fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+    dfl s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ dcx dc_add(dcx a, dcx b) { return {df_add(a.x, b.x), df_add(a.y, b.y)}; }
+__device__ __forceinline__ dcx dc_sub(dcx a, dcx b) { return {df_sub(a.x, b.x), df_sub(a.y, b.y)}; }
+__device__ __forceinline__ dcx dc_mul(dcx a, dcx w) {
+    return {df_sub(df_mul(a.x, w.x), df_mul(a.y, w.y)), df_add(df_mul(a.x, w.y), df_mul(a.y, w.x))};
+}
+__device__ __forceinline__ dcx dc_mul_mi(dcx v, bool inv) {  // x (-i) forward, x (+i) inverse
+    return inv ? dcx{df_neg(v.y), v.x} : dcx{v.y, df_neg(v.x)};
+}
+__device__ __forceinline__ dcx dc_scale(dcx v, dfl k) { return {df_mul(v.x, k), df_mul(v.y, k)}; }
+
+__device__ __forceinline__ dcx dc_w8mul(dcx d, int j, bool inv, dfl s) {  // x w8^j, s = 1/sqrt(2)
+    switch (j) {
+        case 0: return d;
+        case 1:
+            return inv ? dcx{df_mul(df_sub(d.x, d.y), s), df_mul(df_add(d.x, d.y), s)}
+                       : dcx{df_mul(df_add(d.x, d.y), s), df_mul(df_sub(d.y, d.x), s)};
+        case 2: return dc_mul_mi(d, inv);
+        default:
+            return inv ? dcx{df_neg(df_mul(df_add(d.x, d.y), s)), df_mul(df_sub(d.x, d.y), s)}
+                       : dcx{df_mul(df_sub(d.y, d.x), s), df_neg(df_mul(df_add(d.x, d.y), s))};
+    }
+}
+
+__device__ __forceinline__ void dc_dft8(dcx (&v)[8], bool inv, dfl s) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const dcx a = v[i], b = v[i + 4];
+        v[i] = dc_add(a, b);
+        v[i + 4] = dc_w8mul(dc_sub(a, b), i, inv, s);
+    }
+#pragma unroll
+    for (int g = 0; g < 8; g += 4)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const dcx a = v[g + i], b = v[g + i + 2];
+            v[g + i] = dc_add(a, b);
+            v[g + i + 2] = dc_w8mul(dc_sub(a, b), 2 * i, inv, s);
+        }
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) {
+        const dcx a = v[i], b = v[i + 1];
+        v[i] = dc_add(a, b);
+        v[i + 1] = dc_sub(a, b);
+    }
+    dcx t = v[1]; v[1] = v[4]; v[4] = t;
+    t = v[3]; v[3] = v[6]; v[6] = t;
+}
+
+// 64-point transform of one line by 8 threads in double-float (the radix
+// 8 x 8 scheme of fft64_line, exchange through the line's storage).
+__device__ __forceinline__ void dc_fft64_line(dcx *line, int estride, int t, bool valid, int nvalid,
+                                              const dcx (&wt)[8], bool inv, dfl s) {
+    dcx v[8];
+    const dcx zero{{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2) {
+        const int pos = 8 * n2 + t;
+        v[n2] = (valid && pos < nvalid) ? line[pos * estride] : zero;
+    }
+    dc_dft8(v, inv, s);
+#pragma unroll
+    for (int k1 = 1; k1 < 8; ++k1) {
+        dcx w = wt[k1];
+        if (inv) w.y = df_neg(w.y);
+        v[k1] = dc_mul(v[k1], w);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1)
+        if (valid) line[(8 * k1 + t) * estride] = v[k1];
+    __syncwarp();
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) v[n1] = valid ? line[(8 * t + n1) * estride] : zero;
+    __syncwarp();
+    dc_dft8(v, inv, s);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2)
+        if (valid) line[(t + 8 * k2) * estride] = v[k2];
+    __syncwarp();
+}
+
+__device__ __forceinline__ void dc_fft64_lines(dcx *base, int nlines, int lstride, int estride, int nvalid,
+                                               const dcx *tw64, bool inv, int gap_at = 1 << 30,
+                                               int gap = 0) {
+    const int grp = threadIdx.x >> 3, t = threadIdx.x & 7, ngrp = blockDim.x >> 3;
+    const dfl s = df_from(0.70710678118654752440);
+    dcx wt[8];
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) wt[k1] = tw64[(t * k1) & 63];
+    for (int l0 = 0; l0 < nlines; l0 += ngrp) {
+        const int l = l0 + grp;
+        const bool valid = l < nlines;
+        dcx *line = base + (valid ? l * lstride + (l >= gap_at ? gap : 0) : 0);
+        dc_fft64_line(line, estride, t, valid, nvalid, wt, inv, s);
+    }
+    __syncthreads();
+}
+
+// Fused slab (M = 64) of the FP64 tier in double-float arithmetic: FP64 data
+// in and out (A1, kernel spectrum, A4 as in k_slab64<double>).
+__global__ void __launch_bounds__(256) k_slab64_df(SlabArgs a) {
+    constexpr int M = 64, MH = 33, P = 65;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    dcx *tw64 = (dcx *)smem_raw;
+    dcx *S = tw64 + M;
+    const int nin = a.nin, W = a.nout;
+    const double2 *tw = (const double2 *)a.tw;  // exp(-2 pi i j / 64), j < 32
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        double2 w = tw[j & 31];
+        if (j >= 32) { w.x = -w.x; w.y = -w.y; }
+        tw64[j] = dcx{df_from(w.x), df_from(w.y)};
+    }
+    const int nunits = a.it.nitems * MH;
+    for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
+        const int kx = unit % MH;
+        int p;
+        const PlanPtrs &PP = item_plan(a.it, unit / MH, p);
+        const double2 *in = (const double2 *)PP.a1 + ((long)p * MH + kx) * nin * nin;
+        for (int e = threadIdx.x; e < nin * nin; e += blockDim.x) {
+            const int zi = e / nin, yi = e % nin;
+            const double2 v = in[e];
+            S[zi * P + yi] = dcx{df_from(v.x), df_from(v.y)};
+        }
+        __syncthreads();
+        dc_fft64_lines(S, nin, P, 1, nin, tw64, false);
+        dc_fft64_lines(S, M, 1, P, nin, tw64, false);
+        const double *khat = (const double *)PP.khat;
+        for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
+            const int kz0 = e / M, ky0 = e % M;
+            const int ky = ky0 < M - ky0 ? ky0 : M - ky0;
+            const int kz = kz0 < M - kz0 ? kz0 : M - kz0;
+            S[kz0 * P + ky0] = dc_scale(S[kz0 * P + ky0], df_from(khat[((long)kx * MH + ky) * MH + kz]));
+        }
+        __syncthreads();
+        dc_fft64_lines(S, M, 1, P, M, tw64, true);
+        int pos0 = a.out_off % M;
+        if (pos0 < 0) pos0 += M;
+        const int n1 = (pos0 + W <= M) ? W : M - pos0;
+        dc_fft64_lines(S + pos0 * P, W, P, 1, M, tw64, true, n1, -(pos0 + n1) * P);
+        double2 *out = (double2 *)PP.a4 + (long)p * a.nz * a.blk;
+        for (int e = threadIdx.x; e < a.nz * W; e += blockDim.x) {
+            const int jz = e / W, yo = e % W, zo = a.zrow[jz];
+            int pz = (a.out_off + zo) % M, py = (a.out_off + yo) % M;
+            if (pz < 0) pz += M;
+            if (py < 0) py += M;
+            const dcx v = S[pz * P + py];
+            out[(long)jz * a.blk + kx * W + yo] = make_double2(df_to(v.x), df_to(v.y));
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Inverse real transform along x of the local fields, pruned to the values
 // the later steps read: the coarse lattice of the field box (for Delta^H, and
 // the coarse points of the interpolation stencils) and the patch-face planes
@@ -1225,6 +1418,7 @@ void set_smem_attrs() {
         cudaFuncSetAttribute(k_fwd_x<LOG2M, float, true, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
         cudaFuncSetAttribute(k_slab<LOG2M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
         cudaFuncSetAttribute(k_slab64<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        cudaFuncSetAttribute(k_slab64_df, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
         cudaFuncSetAttribute(k_inv_x<LOG2M, R, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
         cudaFuncSetAttribute(k_inv_x_pruned<LOG2M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     }
@@ -1341,7 +1535,12 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
                 const int wave = nsm * (occ > 0 ? occ : 1);
                 grid = grid < wave ? grid : wave;
             }
-            k_slab64<R><<<grid, 256, sm, st>>>(a);
+            if (sizeof(R) == 8) {  // FP64 tier: the slab in double-float arithmetic
+                const size_t smd = (size_t)(M + M * 65) * sizeof(dcx);
+                k_slab64_df<<<it.persist ? grid : nb * MH, 256, smd, st>>>(a);
+            } else {
+                k_slab64<R><<<grid, 256, sm, st>>>(a);
+            }
         }
         else
             k_slab<LOG2M, R><<<nb * MH, 256, fft_smem_bytes<R>(M, M, M + 1), st>>>(a);
