@@ -29,6 +29,68 @@ __device__ __forceinline__ int floordiv(int a, int b) {  // b > 0
     return a >= 0 ? a / b : -((-a + b - 1) / b);
 }
 
+// ---------------------------------------------------------------------------
+// Double-float arithmetic: a value is an unevaluated sum hi + lo of two FP32
+// numbers (|lo| <= ulp(hi)/2), about 48 significand bits.  Sums use the
+// error-free two-sum of Knuth, products the FMA-based two-product; the FFT
+// error bound is relative to the data norm, so the additions need not
+// renormalise the low parts twice.  GB300 issues FP32 on ~67x more lanes than
+// FP64, so the FP64 tier's local-convolution slab runs in this arithmetic.
+// ---------------------------------------------------------------------------
+struct dfl {
+    float hi, lo;
+    dfl() = default;
+    __host__ __device__ constexpr dfl(float h, float l) : hi(h), lo(l) {}
+    __device__ explicit dfl(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+    __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+struct dcx {
+    dfl x, y;
+};
+
+__device__ __forceinline__ dfl df_from(double v) {
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ double df_to(dfl a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ dfl two_sum(float a, float b) {
+    const float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dfl fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+    dfl s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ dcx dc_add(dcx a, dcx b) { return {df_add(a.x, b.x), df_add(a.y, b.y)}; }
+__device__ __forceinline__ dcx dc_sub(dcx a, dcx b) { return {df_sub(a.x, b.x), df_sub(a.y, b.y)}; }
+__device__ __forceinline__ dcx dc_mul(dcx a, dcx w) {
+    return {df_sub(df_mul(a.x, w.x), df_mul(a.y, w.y)), df_add(df_mul(a.x, w.y), df_mul(a.y, w.x))};
+}
+__device__ __forceinline__ dcx dc_mul_mi(dcx v, bool inv) {  // x (-i) forward, x (+i) inverse
+    return inv ? dcx{df_neg(v.y), v.x} : dcx{v.y, df_neg(v.x)};
+}
+__device__ __forceinline__ dcx dc_scale(dcx v, dfl k) { return {df_mul(v.x, k), df_mul(v.y, k)}; }
+
+__device__ __forceinline__ dfl operator+(dfl a, dfl b) { return df_add(a, b); }
+__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return df_sub(a, b); }
+__device__ __forceinline__ dfl operator-(dfl a) { return df_neg(a); }
+__device__ __forceinline__ dfl operator*(dfl a, dfl b) { return df_mul(a, b); }
+__device__ __forceinline__ dfl &operator*=(dfl &a, dfl b) { return a = df_mul(a, b); }
+__device__ __forceinline__ dcx cmul(dcx a, dcx w) { return dc_mul(a, w); }
+
 // Complex type of each working precision (FP64 tier: double; split tier: float).
 template <typename R> struct Cx;
 template <> struct Cx<double> {
@@ -38,6 +100,10 @@ template <> struct Cx<double> {
 template <> struct Cx<float> {
     using T = float2;
     static __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+};
+template <> struct Cx<dfl> {  // double-float complex
+    using T = dcx;
+    static __device__ __forceinline__ dcx mk(float a, float b) { return dcx{dfl(a, 0.f), dfl(b, 0.f)}; }
 };
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 w) {
@@ -203,7 +269,7 @@ __global__ void __launch_bounds__(256) k_fwd_x(FwdXArgs a) {
     int p = slab / a.nin, N = a.N, np = a.np;
     const void *src = a.src;
     void *outp = a.out;
-    if (PATCH) {
+    if constexpr (PATCH) {
         const PlanPtrs &P = item_plan(a.it, slab / a.nin, p);
         src = P.f;
         outp = P.a1;
@@ -214,10 +280,10 @@ __global__ void __launch_bounds__(256) k_fwd_x(FwdXArgs a) {
         const int l = e / a.nin, m = e % a.nin;
         const int yi = line0 + l;
         R v;
-        if (PATCH) {
+        if constexpr (PATCH) {
             const int i2 = p % np, i1 = (p / np) % np, i0 = p / (np * np);
             const int z = i0 * a.n + zi, y = i1 * a.n + yi, x = i2 * a.n + m;
-            v = 0;
+            v = R(0.0);
             if (z < N && y < N && x < N) {
                 const TF *f = (const TF *)src;
                 R w = (zi == 0 || zi == a.n) ? R(0.5) : R(1);
@@ -229,7 +295,10 @@ __global__ void __launch_bounds__(256) k_fwd_x(FwdXArgs a) {
             const double *F = (const double *)a.src;
             v = (R)F[((long)zi * a.nin + yi) * a.nin + m];
         }
-        buf[l * LS + m] = Cx<R>::mk(v, 0);
+        C c;
+        c.x = v;
+        c.y = R(0.0);
+        buf[l * LS + m] = c;
     }
     __syncthreads();
     fft_dif<LOG2M>(buf, nl, LS, 1, s_tw, false);
@@ -339,7 +408,7 @@ struct InvXArgs {
     const void *tw;
 };
 
-template <int LOG2M, typename R, typename TO, bool SLAB = false>
+template <int LOG2M, typename R, typename TO>
 __global__ void __launch_bounds__(256) k_inv_x(InvXArgs a) {
     using C = typename Cx<R>::T;
     constexpr int M = 1 << LOG2M, MH = M / 2 + 1, LS = M + 1;
@@ -350,19 +419,7 @@ __global__ void __launch_bounds__(256) k_inv_x(InvXArgs a) {
     const int r0 = blockIdx.y * a.lines_cta;
     const int nl = min(a.lines_cta, a.nrow - r0);
     load_twiddles<LOG2M>(s_tw, (const C *)a.tw);
-    if (SLAB) {  // input [slab][kx][row]: contiguous block, transposed into rows
-        const C *in = (const C *)a.in + (long)slab * MH * a.nrow;
-        for (int e = threadIdx.x; e < MH * nl; e += blockDim.x) {
-            const int k = e / nl, l = e % nl;
-            const C v = in[(long)k * a.nrow + r0 + l];
-            buf[l * LS + k] = v;
-            if (k > 0 && k < M - k) {
-                C c = v;
-                c.y = -c.y;
-                buf[l * LS + (M - k)] = c;
-            }
-        }
-    } else {
+    {
         const C *in = (const C *)a.in + ((long)slab * a.nrow + r0) * MH;
         for (int e = threadIdx.x; e < nl * M; e += blockDim.x) {
             const int l = e / M, k = e % M;
@@ -655,57 +712,6 @@ __global__ void __launch_bounds__(256) k_slab64(SlabArgs a) {
     __syncthreads();  // S is rewritten by the next unit
     }
 }
-
-// ---------------------------------------------------------------------------
-// Double-float arithmetic: a value is an unevaluated sum hi + lo of two FP32
-// numbers (|lo| <= ulp(hi)/2), about 48 significand bits.  Sums use the
-// error-free two-sum of Knuth, products the FMA-based two-product; the FFT
-// error bound is relative to the data norm, so the additions need not
-// renormalise the low parts twice.  GB300 issues FP32 on ~67x more lanes than
-// FP64, so the FP64 tier's local-convolution slab runs in this arithmetic.
-// ---------------------------------------------------------------------------
-struct dfl {
-    float hi, lo;
-};
-struct dcx {
-    dfl x, y;
-};
-
-__device__ __forceinline__ dfl df_from(double v) {
-    const float h = (float)v;
-    return {h, (float)(v - (double)h)};
-}
-__device__ __forceinline__ double df_to(dfl a) { return (double)a.hi + (double)a.lo; }
-__device__ __forceinline__ dfl two_sum(float a, float b) {
-    const float s = a + b, bb = s - a;
-    return {s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ dfl fast_two_sum(float a, float b) {
-    const float s = a + b;
-    return {s, b - (s - a)};
-}
-__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
-    dfl s = two_sum(a.hi, b.hi);
-    return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
-}
-__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
-__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
-    const float p = a.hi * b.hi;
-    float e = fmaf(a.hi, b.hi, -p);
-    e = fmaf(a.hi, b.lo, e);
-    e = fmaf(a.lo, b.hi, e);
-    return fast_two_sum(p, e);
-}
-__device__ __forceinline__ dcx dc_add(dcx a, dcx b) { return {df_add(a.x, b.x), df_add(a.y, b.y)}; }
-__device__ __forceinline__ dcx dc_sub(dcx a, dcx b) { return {df_sub(a.x, b.x), df_sub(a.y, b.y)}; }
-__device__ __forceinline__ dcx dc_mul(dcx a, dcx w) {
-    return {df_sub(df_mul(a.x, w.x), df_mul(a.y, w.y)), df_add(df_mul(a.x, w.y), df_mul(a.y, w.x))};
-}
-__device__ __forceinline__ dcx dc_mul_mi(dcx v, bool inv) {  // x (-i) forward, x (+i) inverse
-    return inv ? dcx{df_neg(v.y), v.x} : dcx{v.y, df_neg(v.x)};
-}
-__device__ __forceinline__ dcx dc_scale(dcx v, dfl k) { return {df_mul(v.x, k), df_mul(v.y, k)}; }
 
 __device__ __forceinline__ dcx dc_w8mul(dcx d, int j, bool inv, dfl s) {  // x w8^j, s = 1/sqrt(2)
     switch (j) {
@@ -1294,31 +1300,31 @@ __device__ __forceinline__ double phiB_at(const PlanPtrs &a, int n, int g0, int 
 }
 
 // DST-I of one line of m = n-1 values held in registers (n a compile-time
-// constant), using sin(pi k (n-t)/n) = (-1)^(k+1) sin(pi k t/n): odd k take
-// x_t + x_{n-t}, even k take x_t - x_{n-t}; the middle node t = n/2 enters
-// odd k only.
+// constant), in double-float arithmetic, using sin(pi k (n-t)/n) =
+// (-1)^(k+1) sin(pi k t/n): odd k take x_t + x_{n-t}, even k take
+// x_t - x_{n-t}; the middle node t = n/2 enters odd k only.
 template <int NN>
-__device__ __forceinline__ void dst_line(double (&x)[NN - 1], const double *Sh) {
+__device__ __forceinline__ void dst_line_df(dfl (&x)[NN - 1], const dfl *Sh) {
     constexpr int m = NN - 1, h = NN / 2;
-    double sp[h], sm[h];
+    dfl sp[h], sm[h];
 #pragma unroll
     for (int t = 1; t < h; ++t) {
-        sp[t] = x[t - 1] + x[NN - t - 1];
-        sm[t] = x[t - 1] - x[NN - t - 1];
+        sp[t] = df_add(x[t - 1], x[NN - t - 1]);
+        sm[t] = df_sub(x[t - 1], x[NN - t - 1]);
     }
-    const double mid = x[h - 1];
-    double y[m];
+    const dfl mid = x[h - 1];
+    dfl y[m];
 #pragma unroll
     for (int k = 1; k <= m; ++k) {
-        const double *row = Sh + (k - 1) * h;  // sin(pi k t / n), t = 1..h
-        double v = 0.0;
+        const dfl *row = Sh + (k - 1) * h;
+        dfl v = {0.f, 0.f};
         if (k & 1) {
 #pragma unroll
-            for (int t = 1; t < h; ++t) v = fma(row[t - 1], sp[t], v);
-            v = fma(row[h - 1], mid, v);
+            for (int t = 1; t < h; ++t) v = df_add(v, df_mul(row[t - 1], sp[t]));
+            v = df_add(v, df_mul(row[h - 1], mid));
         } else {
 #pragma unroll
-            for (int t = 1; t < h; ++t) v = fma(row[t - 1], sm[t], v);
+            for (int t = 1; t < h; ++t) v = df_add(v, df_mul(row[t - 1], sm[t]));
         }
         y[k - 1] = v;
     }
@@ -1330,16 +1336,16 @@ template <typename TF, int NN>
 __global__ void __launch_bounds__(256) k_dirichlet(DirArgs a) {
     extern __shared__ double sm[];
     constexpr int n = NN, nb = n + 1, m = n - 1, h = n / 2;
-    double *U = sm;                  // nb^3 boundary values (interior 0)
-    double *X = U + nb * nb * nb;    // m^3 work
-    double *Sh = X + m * m * m;      // (n-1) x n/2 half sine table
+    double *U = sm;                    // nb^3 boundary values (interior 0)
+    dfl *X = (dfl *)(U + nb * nb * nb);  // m^3 work, double-float
+    dfl *Sh = X + m * m * m;           // (n-1) x n/2 half sine table, double-float
     int p;
     const PlanPtrs &PP = item_plan(a.it, blockIdx.x, p);
     const int np = PP.np, N = PP.N;
     const int i2 = p % np, i1 = (p / np) % np, i0 = p / (np * np);
     const int o0 = i0 * n, o1 = i1 * n, o2 = i2 * n;
     const TF *f = (const TF *)PP.f;
-    for (int e = threadIdx.x; e < m * h; e += blockDim.x) Sh[e] = a.sinm[e];
+    for (int e = threadIdx.x; e < m * h; e += blockDim.x) Sh[e] = df_from(a.sinm[e]);
     for (int e = threadIdx.x; e < nb * nb * nb; e += blockDim.x) {
         const int m2 = e % nb, m1 = (e / nb) % nb, m0 = e / (nb * nb);
         const bool bnd = m0 == 0 || m0 == n || m1 == 0 || m1 == n || m2 == 0 || m2 == n;
@@ -1363,7 +1369,7 @@ __global__ void __launch_bounds__(256) k_dirichlet(DirArgs a) {
                     }
         const int z = o0 + c0, y = o1 + c1, x = o2 + c2;
         const double fv = (z < N && y < N && x < N) ? (double)f[((long)z * N + y) * N + x] : 0.0;
-        X[e] = fma(-lap, PP.inv_h2, fv);
+        X[e] = df_from(fma(-lap, PP.inv_h2, fv));
     }
     __syncthreads();
     // DST-I along axes 2, 1, 0; divide by the eigenvalues; DST-I along 2, 1, 0
@@ -1375,13 +1381,13 @@ __global__ void __launch_bounds__(256) k_dirichlet(DirArgs a) {
             if (axis == 2) { base = (q0 * m + q1) * m; str = 1; }
             else if (axis == 1) { base = q0 * m * m + q1; str = m; }
             else { base = q0 * m + q1; str = m * m; }
-            double x[m];
+            dfl x[m];
 #pragma unroll
             for (int t = 0; t < m; ++t) x[t] = X[base + t * str];
-            dst_line<NN>(x, Sh);
+            dst_line_df<NN>(x, Sh);
             if (pass == 2) {
 #pragma unroll
-                for (int t = 0; t < m; ++t) x[t] *= PP.lam[base + t * str];
+                for (int t = 0; t < m; ++t) x[t] = df_mul(x[t], df_from(PP.lam[base + t * str]));
             }
 #pragma unroll
             for (int t = 0; t < m; ++t) X[base + t * str] = x[t];
@@ -1393,7 +1399,7 @@ __global__ void __launch_bounds__(256) k_dirichlet(DirArgs a) {
         const int m2 = e % n, m1 = (e / n) % n, m0 = e / (n * n);
         const bool bnd = m0 == 0 || m1 == 0 || m2 == 0;
         const double u = bnd ? U[(m0 * nb + m1) * nb + m2]
-                             : X[((m0 - 1) * m + (m1 - 1)) * m + (m2 - 1)] * norm;
+                             : df_to(X[((m0 - 1) * m + (m1 - 1)) * m + (m2 - 1)]) * norm;
         const int z = o0 + m0, y = o1 + m1, x = o2 + m2;
         const long gi = ((long)z * N + y) * N + x;
         PP.phi[gi] = u + PP.c2h2 * (double)f[gi];
@@ -1405,23 +1411,26 @@ inline size_t fft_smem_bytes(int M, int lines, int ls) {
     return ((size_t)(M / 2) + (size_t)lines * ls) * 2 * sizeof(R);
 }
 
+// Dense (coarse-grid) convolution pipeline kernels in working precision R.
 template <int LOG2M, typename R>
-void set_smem_attrs() {
+void set_coarse_attrs() {
     const int big = 200 * 1024;
     cudaFuncSetAttribute(k_fwd_x<LOG2M, double, false, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_col<LOG2M, 0, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_col<LOG2M, 1, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_col<LOG2M, 2, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_inv_x<LOG2M, R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (LOG2M <= 6) {
-        cudaFuncSetAttribute(k_fwd_x<LOG2M, double, true, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-        cudaFuncSetAttribute(k_fwd_x<LOG2M, float, true, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-        cudaFuncSetAttribute(k_slab<LOG2M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-        cudaFuncSetAttribute(k_slab64<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-        cudaFuncSetAttribute(k_slab64_df, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-        cudaFuncSetAttribute(k_inv_x<LOG2M, R, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-        cudaFuncSetAttribute(k_inv_x_pruned<LOG2M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    }
+    cudaFuncSetAttribute(k_inv_x<LOG2M, R, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
+
+// Local-convolution (patch) kernels in working precision R.
+template <int LOG2M, typename R>
+void set_patch_attrs() {
+    const int big = 200 * 1024;
+    cudaFuncSetAttribute(k_fwd_x<LOG2M, double, true, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_fwd_x<LOG2M, float, true, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_slab<LOG2M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_slab64<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_inv_x_pruned<LOG2M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
 // One Hockney convolution pipeline (5 launches) for `nbatch` problems with
@@ -1494,7 +1503,7 @@ cudaError_t run_conv_t(const ConvDesc &d, cudaStream_t st) {
         InvXArgs a{d.b1, d.out, W, W, d.out_off, 0, d.tw};
         a.lines_cta = (M <= 64) ? W : 16;
         dim3 grid(d.nbatch * W, (W + a.lines_cta - 1) / a.lines_cta);
-        k_inv_x<LOG2M, R, R><<<grid, 256, fft_smem_bytes<R>(M, a.lines_cta, M + 1), st>>>(a);
+        k_inv_x<LOG2M, R, double><<<grid, 256, fft_smem_bytes<R>(M, a.lines_cta, M + 1), st>>>(a);
     }
     return cudaGetLastError();
 }
@@ -1601,12 +1610,15 @@ cudaError_t launch_set_ptrs(PlanPtrs *d, const void *f, double *phi, cudaStream_
 }
 
 void configure_kernels() {
-    set_smem_attrs<5, double>();
-    set_smem_attrs<6, double>();
-    set_smem_attrs<7, double>();
-    set_smem_attrs<8, double>();
-    set_smem_attrs<5, float>();
-    set_smem_attrs<6, float>();
+    set_patch_attrs<5, double>();
+    set_patch_attrs<6, double>();
+    set_patch_attrs<5, float>();
+    set_patch_attrs<6, float>();
+    cudaFuncSetAttribute(k_slab64_df, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    set_coarse_attrs<5, dfl>();
+    set_coarse_attrs<6, dfl>();
+    set_coarse_attrs<7, dfl>();
+    set_coarse_attrs<8, dfl>();
     cudaFuncSetAttribute(k_dirichlet<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_dirichlet<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_dirichlet<double, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -1689,9 +1701,9 @@ cudaError_t launch_coarse(const mlc_plan_s *pl, cudaStream_t st) {
     d.M = g.Mc; d.log2M = g.log2Mc; d.nbatch = 1; d.nin = g.nf; d.nout = g.no;
     d.out_off = g.olo - g.flo;
     d.src = pl->FH; d.patch = false; d.f32 = false;
-    d.b0 = pl->cbuf0; d.b1 = pl->cbuf1; d.out = pl->phiH; d.khat = pl->khat_c; d.tw = pl->tw_c;
+    d.b0 = pl->cbuf0; d.b1 = pl->cbuf1; d.out = pl->phiH; d.khat = pl->khat_c_df; d.tw = pl->tw_c_df;
     d.pl = pl; d.ev0 = 6;
-    return run_conv<double>(d, st);
+    return run_conv<dfl>(d, st);  // coarse FFTs in double-float arithmetic
 }
 
 cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st) {

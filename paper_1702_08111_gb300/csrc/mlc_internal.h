@@ -93,6 +93,8 @@ struct mlc_plan_s {
     double2 *tw, *tw_c;      // FFT twiddles exp(-2 pi i t / M), t < M/2
     float *khat_f;           // split tier: FP32 copies of the patch spectrum and twiddles
     float2 *tw_f;
+    float2 *khat_c_df;       // coarse spectrum and twiddles as double-float (hi, lo) pairs
+    float4 *tw_c_df;
     double *sinm;            // (n-1)^2 DST-I matrix sin(pi k m / n)
     double *lam;             // (n-1)^3 stencil eigenvalues / h^2
     // workspace (device)

@@ -492,6 +492,25 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
                                      G.h * G.h / ((double)G.M * G.M * G.M), pl->khat));
         TRY_CUDA(build_even_spectrum(pl->dgf, pl->dgf_L, G.Mc, G.Lc,
                                      G.H * G.H / ((double)G.Mc * G.Mc * G.Mc), pl->khat_c));
+        {   // double-float copies for the coarse convolution: v = hi + lo
+            auto split = [](double v) {
+                const float h = (float)v;
+                return make_float2(h, (float)(v - (double)h));
+            };
+            const size_t nk = (size_t)G.Mhc * G.Mhc * G.Mhc;
+            std::vector<double> kd(nk);
+            TRY_CUDA(cudaMemcpy(kd.data(), pl->khat_c, nk * sizeof(double), cudaMemcpyDeviceToHost));
+            std::vector<float2> kf(nk);
+            for (size_t i = 0; i < nk; ++i) kf[i] = split(kd[i]);
+            TRY(dev_upload(pl, &pl->khat_c_df, kf));
+            std::vector<float4> tf(G.Mc / 2);
+            for (int t = 0; t < G.Mc / 2; ++t) {
+                const double a = 2.0 * M_PI * (double)t / (double)G.Mc;
+                const float2 re = split(std::cos(a)), im = split(-std::sin(a));
+                tf[t] = make_float4(re.x, re.y, im.x, im.y);
+            }
+            TRY(dev_upload(pl, &pl->tw_c_df, tf));
+        }
         const size_t NP = G.NP, nb = G.nb, W = G.W, M = G.M, Mh = G.Mh;
         (void)M;
         (void)W;
