@@ -14,6 +14,7 @@
 //   dirichlet   patch Dirichlet solves by DST-I (eq. last_step_fulldiscr) and
 //               the Mehrstellen correction (eq. mcapplicationfulldiscr)
 #include <cmath>
+#include <type_traits>
 
 #include "mlc_internal.h"
 
@@ -89,6 +90,7 @@ __device__ __forceinline__ dfl operator-(dfl a, dfl b) { return df_sub(a, b); }
 __device__ __forceinline__ dfl operator-(dfl a) { return df_neg(a); }
 __device__ __forceinline__ dfl operator*(dfl a, dfl b) { return df_mul(a, b); }
 __device__ __forceinline__ dfl &operator*=(dfl &a, dfl b) { return a = df_mul(a, b); }
+__device__ __forceinline__ dfl &operator+=(dfl &a, dfl b) { return a = df_add(a, b); }
 __device__ __forceinline__ dcx cmul(dcx a, dcx w) { return dc_mul(a, w); }
 
 // Complex type of each working precision (FP64 tier: double; split tier: float).
@@ -809,32 +811,31 @@ __global__ void __launch_bounds__(256) k_slab64_df(SlabArgs a) {
     dcx *tw64 = (dcx *)smem_raw;
     dcx *S = tw64 + M;
     const int nin = a.nin, W = a.nout;
-    const double2 *tw = (const double2 *)a.tw;  // exp(-2 pi i j / 64), j < 32
+    const dcx *tw = (const dcx *)a.tw;  // exp(-2 pi i j / 64), j < 32, double-float
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        double2 w = tw[j & 31];
-        if (j >= 32) { w.x = -w.x; w.y = -w.y; }
-        tw64[j] = dcx{df_from(w.x), df_from(w.y)};
+        dcx w = tw[j & 31];
+        if (j >= 32) { w.x = df_neg(w.x); w.y = df_neg(w.y); }
+        tw64[j] = w;
     }
     const int nunits = a.it.nitems * MH;
     for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
         const int kx = unit % MH;
         int p;
         const PlanPtrs &PP = item_plan(a.it, unit / MH, p);
-        const double2 *in = (const double2 *)PP.a1 + ((long)p * MH + kx) * nin * nin;
+        const dcx *in = (const dcx *)PP.a1 + ((long)p * MH + kx) * nin * nin;
         for (int e = threadIdx.x; e < nin * nin; e += blockDim.x) {
             const int zi = e / nin, yi = e % nin;
-            const double2 v = in[e];
-            S[zi * P + yi] = dcx{df_from(v.x), df_from(v.y)};
+            S[zi * P + yi] = in[e];
         }
         __syncthreads();
         dc_fft64_lines(S, nin, P, 1, nin, tw64, false);
         dc_fft64_lines(S, M, 1, P, nin, tw64, false);
-        const double *khat = (const double *)PP.khat;
+        const dfl *khat = (const dfl *)PP.khat;
         for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
             const int kz0 = e / M, ky0 = e % M;
             const int ky = ky0 < M - ky0 ? ky0 : M - ky0;
             const int kz = kz0 < M - kz0 ? kz0 : M - kz0;
-            S[kz0 * P + ky0] = dc_scale(S[kz0 * P + ky0], df_from(khat[((long)kx * MH + ky) * MH + kz]));
+            S[kz0 * P + ky0] = dc_scale(S[kz0 * P + ky0], khat[((long)kx * MH + ky) * MH + kz]);
         }
         __syncthreads();
         dc_fft64_lines(S, M, 1, P, M, tw64, true);
@@ -842,14 +843,13 @@ __global__ void __launch_bounds__(256) k_slab64_df(SlabArgs a) {
         if (pos0 < 0) pos0 += M;
         const int n1 = (pos0 + W <= M) ? W : M - pos0;
         dc_fft64_lines(S + pos0 * P, W, P, 1, M, tw64, true, n1, -(pos0 + n1) * P);
-        double2 *out = (double2 *)PP.a4 + (long)p * a.nz * a.blk;
+        dcx *out = (dcx *)PP.a4 + (long)p * a.nz * a.blk;
         for (int e = threadIdx.x; e < a.nz * W; e += blockDim.x) {
             const int jz = e / W, yo = e % W, zo = a.zrow[jz];
             int pz = (a.out_off + zo) % M, py = (a.out_off + yo) % M;
             if (pz < 0) pz += M;
             if (py < 0) py += M;
-            const dcx v = S[pz * P + py];
-            out[(long)jz * a.blk + kx * W + yo] = make_double2(df_to(v.x), df_to(v.y));
+            out[(long)jz * a.blk + kx * W + yo] = S[pz * P + py];
         }
         __syncthreads();
     }
@@ -883,7 +883,7 @@ __device__ __forceinline__ bool on_plane(int c, int n, int ga, int pl0) {
     return in_alpha(c, n, ga) && ((c - pl0) % n) == 0;
 }
 
-template <int LOG2M, typename R>
+template <int LOG2M, typename R, typename TO>
 __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
     using C = typename Cx<R>::T;
     constexpr int M = 1 << LOG2M, MH = M / 2 + 1;
@@ -962,8 +962,8 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
     __syncthreads();
     if (LOG2M == 6) fft64_lines<C, R>(buf, nfft, LP, 1, M, tw, true, xs);
     else fft_dif<LOG2M>(buf, nfft, LP, 1, tw, true);
-    R *cl = (R *)PP.cl + (long)p * nc * nc * nc;
-    R *fp = (R *)PP.fp + (long)p * 3 * a.npa * wa * wa;
+    TO *cl = (TO *)PP.cl + (long)p * nc * nc * nc;
+    TO *fp = (TO *)PP.fp + (long)p * 3 * a.npa * wa * wa;
     const int kl = -s / 4;
     // outputs of the transformed rows
     for (int e = threadIdx.x; e < nfft * W; e += blockDim.x) {
@@ -975,7 +975,7 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
         if (!(wC || w0 || w1 || w2)) continue;
         int pos = x % M;
         if (pos < 0) pos += M;
-        const R v = buf[l * LP + (LOG2M == 6 ? pos : brev_bits(pos, LOG2M))].x;
+        const TO v = (TO)buf[l * LP + (LOG2M == 6 ? pos : brev_bits(pos, LOG2M))].x;
         if (wC) cl[((long)((z >> 2) - kl) * nc + ((y >> 2) - kl)) * nc + ((x >> 2) - kl)] = v;
         if (w0) fp[(((long)(0 * a.npa + (z - pl0) / n)) * wa + (y + ga)) * wa + (x + ga)] = v;
         if (w1) fp[(((long)(1 * a.npa + (y - pl0) / n)) * wa + (z + ga)) * wa + (x + ga)] = v;
@@ -991,14 +991,14 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
             const int x = pl0 + j * n;
             int pos = x % M;
             if (pos < 0) pos += M;
-            R acc = 0;
+            R acc = R(0.0);
             for (int k = 0; k < MH; ++k) {
                 const C X = raw[k * W + yi];
                 C w = tw[(k * pos) & (M - 1)];  // exp(+2 pi i k pos / M) = conj(tw)
                 const R re = X.x * w.x + X.y * w.y;
-                acc += (k == 0 || 2 * k == M) ? re : (R)2 * re;
+                acc += (k == 0 || 2 * k == M) ? re : R(2.0) * re;
             }
-            fp[(((long)(2 * a.npa + j)) * wa + (z + ga)) * wa + (y + ga)] = acc;
+            fp[(((long)(2 * a.npa + j)) * wa + (z + ga)) * wa + (y + ga)] = (TO)acc;
         }
     }
 }
@@ -1430,7 +1430,8 @@ void set_patch_attrs() {
     cudaFuncSetAttribute(k_fwd_x<LOG2M, float, true, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_slab<LOG2M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_slab64<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_inv_x_pruned<LOG2M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    using TO = typename std::conditional<std::is_same<R, float>::value, float, double>::type;
+    cudaFuncSetAttribute(k_inv_x_pruned<LOG2M, R, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
 // One Hockney convolution pipeline (5 launches) for `nbatch` problems with
@@ -1544,7 +1545,7 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
                 const int wave = nsm * (occ > 0 ? occ : 1);
                 grid = grid < wave ? grid : wave;
             }
-            if (sizeof(R) == 8) {  // FP64 tier: the slab in double-float arithmetic
+            if (std::is_same<R, dfl>::value) {  // FP64 tier: the slab in double-float arithmetic
                 const size_t smd = (size_t)(M + M * 65) * sizeof(dcx);
                 k_slab64_df<<<it.persist ? grid : nb * MH, 256, smd, st>>>(a);
             } else {
@@ -1573,7 +1574,9 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
         const int LPh = LOG2M == 6 ? Pitch64<R>::P : M + 1;
         const size_t xsn = (LOG2M == 6 && UseXs<R>::v) ? 32 * 72 : 0;
         const size_t sm = ((size_t)M + (size_t)g.a4blk + (size_t)a.maxfft * LPh + xsn) * 2 * sizeof(R);
-        k_inv_x_pruned<LOG2M, R><<<nb * a.nz, 256, sm, st>>>(a);
+        // local fields leave in FP32 (split tier) or FP64 (FP64 tier)
+        using TO = typename std::conditional<std::is_same<R, float>::value, float, double>::type;
+        k_inv_x_pruned<LOG2M, R, TO><<<nb * a.nz, 256, sm, st>>>(a);
     }
     return cudaGetLastError();
 }
@@ -1610,8 +1613,8 @@ cudaError_t launch_set_ptrs(PlanPtrs *d, const void *f, double *phi, cudaStream_
 }
 
 void configure_kernels() {
-    set_patch_attrs<5, double>();
-    set_patch_attrs<6, double>();
+    set_patch_attrs<5, dfl>();
+    set_patch_attrs<6, dfl>();
     set_patch_attrs<5, float>();
     set_patch_attrs<6, float>();
     cudaFuncSetAttribute(k_slab64_df, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -1639,11 +1642,12 @@ cudaError_t launch_moments(const mlc_plan_s *pl, const Items &it, cudaStream_t s
 cudaError_t launch_patch_conv(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
     const Geom &g = pl->g;
     const bool split = g.tier == MLC_TIER_SPLIT;
-    const void *tw = split ? (const void *)pl->tw_f : (const void *)pl->tw;
+    // split tier: FP32; FP64 tier: double-float (tables tw_df, khat_df)
+    const void *tw = split ? (const void *)pl->tw_f : (const void *)pl->tw_df;
     if (g.log2M == 5) return split ? run_patch_conv_t<5, float>(pl, it, true, tw, st)
-                                   : run_patch_conv_t<5, double>(pl, it, false, tw, st);
+                                   : run_patch_conv_t<5, dfl>(pl, it, false, tw, st);
     if (g.log2M == 6) return split ? run_patch_conv_t<6, float>(pl, it, true, tw, st)
-                                   : run_patch_conv_t<6, double>(pl, it, false, tw, st);
+                                   : run_patch_conv_t<6, dfl>(pl, it, false, tw, st);
     return cudaErrorInvalidValue;
 }
 

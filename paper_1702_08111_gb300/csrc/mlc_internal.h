@@ -95,6 +95,8 @@ struct mlc_plan_s {
     float2 *tw_f;
     float2 *khat_c_df;       // coarse spectrum and twiddles as double-float (hi, lo) pairs
     float4 *tw_c_df;
+    float2 *khat_df;         // FP64 tier: patch spectrum and twiddles as double-float pairs
+    float4 *tw_df;
     double *sinm;            // (n-1)^2 DST-I matrix sin(pi k m / n)
     double *lam;             // (n-1)^3 stencil eigenvalues / h^2
     // workspace (device)

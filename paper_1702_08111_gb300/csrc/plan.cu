@@ -525,6 +525,26 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
         pl->buf1 = b1;
         pl->cl = bc;
         pl->fpl = bf;
+        if (G.tier == MLC_TIER_FP64) {
+            // double-float copies of the patch kernel spectrum and twiddles
+            auto split = [](double v) {
+                const float h = (float)v;
+                return make_float2(h, (float)(v - (double)h));
+            };
+            const size_t nk = (size_t)G.Mh * G.Mh * G.Mh;
+            std::vector<double> kd(nk);
+            TRY_CUDA(cudaMemcpy(kd.data(), pl->khat, nk * sizeof(double), cudaMemcpyDeviceToHost));
+            std::vector<float2> kf(nk);
+            for (size_t i = 0; i < nk; ++i) kf[i] = split(kd[i]);
+            TRY(dev_upload(pl, &pl->khat_df, kf));
+            std::vector<float4> tf(G.M / 2);
+            for (int t = 0; t < G.M / 2; ++t) {
+                const double a = 2.0 * M_PI * (double)t / (double)G.M;
+                const float2 re = split(std::cos(a)), im = split(-std::sin(a));
+                tf[t] = make_float4(re.x, re.y, im.x, im.y);
+            }
+            TRY(dev_upload(pl, &pl->tw_df, tf));
+        }
         if (G.tier == MLC_TIER_SPLIT) {
             // FP32 copies of the patch kernel spectrum and twiddles
             const size_t nk = (size_t)G.Mh * G.Mh * G.Mh;
@@ -565,7 +585,7 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
         h.a4 = pl->buf1;
         h.cl = pl->cl;
         h.fp = pl->fpl;
-        h.khat = G.tier == MLC_TIER_SPLIT ? (const void *)pl->khat_f : (const void *)pl->khat;
+        h.khat = G.tier == MLC_TIER_SPLIT ? (const void *)pl->khat_f : (const void *)pl->khat_df;
         h.momw = G.tier == MLC_TIER_SPLIT ? (const void *)pl->momw_f : (const void *)pl->momw;
         h.mom = pl->mom;
         h.mom_f = pl->mom_f;
