@@ -644,9 +644,9 @@ __device__ __forceinline__ void fft64_lines(C *base, int nlines, int lstride, in
 // Row pitch of the 64-point line buffers: 68 (4 mod 16) for FP32, 65 for FP64
 // (both conflict-free for the line loads and stores).
 template <typename R> struct Pitch64 { static constexpr int P = sizeof(R) == 4 ? 68 : 65; };
-// FP32 lines exchange through a separate padded buffer; FP64 lines in place
-// (the extra buffer would cost a resident CTA per SM on the FP64 pipe).
-template <typename R> struct UseXs { static constexpr bool v = sizeof(R) == 4; };
+// Lines exchange through a separate padded buffer (FP32 and double-float
+// complex entries); plain FP64 lines exchange in place.
+template <typename R> struct UseXs { static constexpr bool v = !std::is_same<R, double>::value; };
 
 // Fused slab for M = 64 with the register FFT (same contract as k_slab).
 // The slab is held as S[z][y] (row z, pitch P), so the global block
@@ -756,7 +756,7 @@ __device__ __forceinline__ void dc_dft8(dcx (&v)[8], bool inv, dfl s) {
 // 64-point transform of one line by 8 threads in double-float (the radix
 // 8 x 8 scheme of fft64_line, exchange through the line's storage).
 __device__ __forceinline__ void dc_fft64_line(dcx *line, int estride, int t, bool valid, int nvalid,
-                                              const dcx (&wt)[8], bool inv, dfl s) {
+                                              const dcx (&wt)[8], bool inv, dfl s, dcx *xs) {
     dcx v[8];
     const dcx zero{{0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll
@@ -771,13 +771,13 @@ __device__ __forceinline__ void dc_fft64_line(dcx *line, int estride, int t, boo
         if (inv) w.y = df_neg(w.y);
         v[k1] = dc_mul(v[k1], w);
     }
+    // exchange through the group's padded scratch (row pitch 9): the 8 lanes of
+    // a quarter-warp phase hit 8 different 16-byte bank quads on both sides
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) xs[9 * k1 + t] = v[k1];
     __syncwarp();
 #pragma unroll
-    for (int k1 = 0; k1 < 8; ++k1)
-        if (valid) line[(8 * k1 + t) * estride] = v[k1];
-    __syncwarp();
-#pragma unroll
-    for (int n1 = 0; n1 < 8; ++n1) v[n1] = valid ? line[(8 * t + n1) * estride] : zero;
+    for (int n1 = 0; n1 < 8; ++n1) v[n1] = xs[9 * t + n1];
     __syncwarp();
     dc_dft8(v, inv, s);
 #pragma unroll
@@ -787,9 +787,10 @@ __device__ __forceinline__ void dc_fft64_line(dcx *line, int estride, int t, boo
 }
 
 __device__ __forceinline__ void dc_fft64_lines(dcx *base, int nlines, int lstride, int estride, int nvalid,
-                                               const dcx *tw64, bool inv, int gap_at = 1 << 30,
+                                               const dcx *tw64, bool inv, dcx *xs, int gap_at = 1 << 30,
                                                int gap = 0) {
     const int grp = threadIdx.x >> 3, t = threadIdx.x & 7, ngrp = blockDim.x >> 3;
+    dcx *gx = xs + grp * 72;
     const dfl s = df_from(0.70710678118654752440);
     dcx wt[8];
 #pragma unroll
@@ -798,7 +799,7 @@ __device__ __forceinline__ void dc_fft64_lines(dcx *base, int nlines, int lstrid
         const int l = l0 + grp;
         const bool valid = l < nlines;
         dcx *line = base + (valid ? l * lstride + (l >= gap_at ? gap : 0) : 0);
-        dc_fft64_line(line, estride, t, valid, nvalid, wt, inv, s);
+        dc_fft64_line(line, estride, t, valid, nvalid, wt, inv, s, gx);
     }
     __syncthreads();
 }
@@ -810,6 +811,7 @@ __global__ void __launch_bounds__(256) k_slab64_df(SlabArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     dcx *tw64 = (dcx *)smem_raw;
     dcx *S = tw64 + M;
+    dcx *xs = S + M * P;  // 32 groups x 72 exchange entries
     const int nin = a.nin, W = a.nout;
     const dcx *tw = (const dcx *)a.tw;  // exp(-2 pi i j / 64), j < 32, double-float
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
@@ -828,8 +830,8 @@ __global__ void __launch_bounds__(256) k_slab64_df(SlabArgs a) {
             S[zi * P + yi] = in[e];
         }
         __syncthreads();
-        dc_fft64_lines(S, nin, P, 1, nin, tw64, false);
-        dc_fft64_lines(S, M, 1, P, nin, tw64, false);
+        dc_fft64_lines(S, nin, P, 1, nin, tw64, false, xs);
+        dc_fft64_lines(S, M, 1, P, nin, tw64, false, xs);
         const dfl *khat = (const dfl *)PP.khat;
         for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
             const int kz0 = e / M, ky0 = e % M;
@@ -838,11 +840,11 @@ __global__ void __launch_bounds__(256) k_slab64_df(SlabArgs a) {
             S[kz0 * P + ky0] = dc_scale(S[kz0 * P + ky0], khat[((long)kx * MH + ky) * MH + kz]);
         }
         __syncthreads();
-        dc_fft64_lines(S, M, 1, P, M, tw64, true);
+        dc_fft64_lines(S, M, 1, P, M, tw64, true, xs);
         int pos0 = a.out_off % M;
         if (pos0 < 0) pos0 += M;
         const int n1 = (pos0 + W <= M) ? W : M - pos0;
-        dc_fft64_lines(S + pos0 * P, W, P, 1, M, tw64, true, n1, -(pos0 + n1) * P);
+        dc_fft64_lines(S + pos0 * P, W, P, 1, M, tw64, true, xs, n1, -(pos0 + n1) * P);
         dcx *out = (dcx *)PP.a4 + (long)p * a.nz * a.blk;
         for (int e = threadIdx.x; e < a.nz * W; e += blockDim.x) {
             const int jz = e / W, yo = e % W, zo = a.zrow[jz];
@@ -1006,39 +1008,63 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
 // ---------------------------------------------------------------------------
 // Legendre coefficients c_p^i = sum_m W[m] Q^p(m) f[n i + m] (Boole, R3).
 // ---------------------------------------------------------------------------
+// Legendre coefficients c_p^i by composite Boole's rule, using the product
+// structure of the weights and the basis: with a_k(m) = w_m q_k(2m/n - 1)
+// (Boole weight times orthonormal Legendre polynomial, one axis),
+//   c_p = R^{-3/2} sum_m0 a_p0(m0) sum_m1 a_p1(m1) sum_m2 a_p2(m2) f(m0,m1,m2),
+// evaluated as three 1D contractions.  RM: arithmetic precision (FP64 or FP32
+// for the split tier, whose last stage and output are FP64).
 template <typename TF, typename RM>
-__global__ void __launch_bounds__(256) k_moments(Items it, int n, int npoly, int npad) {
-    __shared__ double red[8][56];
-    int p;
-    const PlanPtrs &PP = item_plan(it, blockIdx.x, p);
-    const RM *__restrict__ momw = (const RM *)PP.momw;
+__global__ void __launch_bounds__(256) k_moments(Items it, int n, int P, int npoly, int npad) {
+    extern __shared__ double msm[];
+    int pch;
+    const PlanPtrs &PP = item_plan(it, blockIdx.x, pch);
+    const int nb = n + 1, N = PP.N, np = PP.np;
+    const int i2 = pch % np, i1 = (pch / np) % np, i0 = pch / (np * np);
+    RM *F = (RM *)msm;                 // nb^3 charge of the closed patch
+    RM *T1 = F + nb * nb * nb;         // [p2][m0][m1]
+    RM *T2 = T1 + P * nb * nb;         // [p1][p2][m0]
+    RM *A = T2 + P * P * nb;           // [k][m] 1D weights
+    const double *a1d = (const double *)PP.momw;
+    for (int e = threadIdx.x; e < P * nb; e += blockDim.x) A[e] = (RM)a1d[e];
     const TF *f = (const TF *)PP.f;
-    const int N = PP.N, np = PP.np;
-    double *mom = PP.mom;
-    float *mom_f = PP.mom_f;
-    const int i2 = p % np, i1 = (p / np) % np, i0 = p / (np * np);
-    const int nb = n + 1, nb3 = nb * nb * nb;
-    RM acc[56];
-    for (int k = 0; k < npoly; ++k) acc[k] = 0;
-    for (int m = threadIdx.x; m < nb3; m += blockDim.x) {
-        const int m2 = m % nb, m1 = (m / nb) % nb, m0 = m / (nb * nb);
+    for (int e = threadIdx.x; e < nb * nb * nb; e += blockDim.x) {
+        const int m2 = e % nb, m1 = (e / nb) % nb, m0 = e / (nb * nb);
         const int z = i0 * n + m0, y = i1 * n + m1, x = i2 * n + m2;
-        if (z >= N || y >= N || x >= N) continue;
-        const RM v = (RM)f[((long)z * N + y) * N + x];
-        for (int k = 0; k < npoly; ++k) acc[k] = fma(momw[(long)k * nb3 + m], v, acc[k]);
+        F[e] = (z < N && y < N && x < N) ? (RM)f[((long)z * N + y) * N + x] : (RM)0;
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int k = 0; k < npoly; ++k) {
-        double v = (double)acc[k];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp][k] = v;
+    __syncthreads();
+    for (int e = threadIdx.x; e < P * nb * nb; e += blockDim.x) {
+        const int p2 = e / (nb * nb), r = e % (nb * nb);
+        RM acc = 0;
+        for (int m2 = 0; m2 < nb; ++m2) acc = fma(A[p2 * nb + m2], F[r * nb + m2], acc);
+        T1[e] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < P * P * nb; e += blockDim.x) {
+        const int p1 = e / (P * nb), p2 = (e / nb) % P, m0 = e % nb;
+        if (p1 + p2 >= P) continue;
+        RM acc = 0;
+        for (int m1 = 0; m1 < nb; ++m1) acc = fma(A[p1 * nb + m1], T1[(p2 * nb + m0) * nb + m1], acc);
+        T2[e] = acc;
     }
     __syncthreads();
     if (threadIdx.x < npoly) {
-        double v = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
-        mom[(long)p * npad + threadIdx.x] = v;
-        if (mom_f) mom_f[(long)p * npad + threadIdx.x] = (float)v;
+        // index -> (p0, p1, p2) in lexicographic order, |p|_1 < P, p2 fastest
+        int q = threadIdx.x, p0 = 0, p1 = 0, p2 = 0;
+        for (int a0 = 0, k = 0; a0 < P; ++a0)
+            for (int a1 = 0; a1 < P; ++a1)
+                for (int a2 = 0; a2 < P; ++a2)
+                    if (a0 + a1 + a2 < P) {
+                        if (k == q) { p0 = a0; p1 = a1; p2 = a2; }
+                        ++k;
+                    }
+        double acc = 0.0;
+        for (int m0 = 0; m0 < nb; ++m0)
+            acc = fma((double)A[p0 * nb + m0], (double)T2[(p1 * P + p2) * nb + m0], acc);
+        acc *= PP.mom_scale;
+        PP.mom[(long)pch * npad + q] = acc;
+        if (PP.mom_f) PP.mom_f[(long)pch * npad + q] = (float)acc;
     }
 }
 
@@ -1546,7 +1572,7 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
                 grid = grid < wave ? grid : wave;
             }
             if (std::is_same<R, dfl>::value) {  // FP64 tier: the slab in double-float arithmetic
-                const size_t smd = (size_t)(M + M * 65) * sizeof(dcx);
+                const size_t smd = (size_t)(M + M * 65 + 32 * 72) * sizeof(dcx);
                 k_slab64_df<<<it.persist ? grid : nb * MH, 256, smd, st>>>(a);
             } else {
                 k_slab64<R><<<grid, 256, sm, st>>>(a);
@@ -1627,15 +1653,19 @@ void configure_kernels() {
     cudaFuncSetAttribute(k_dirichlet<double, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_dirichlet<float, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_resid<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_moments<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_moments<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_resid<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 cudaError_t launch_moments(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
     const Geom &g = pl->g;
+    const int nb = g.n + 1;
+    const size_t words = (size_t)nb * nb * nb + (size_t)g.P * nb * nb + (size_t)g.P * g.P * nb + (size_t)g.P * nb;
     if (g.tier == MLC_TIER_SPLIT)
-        k_moments<float, float><<<it.nitems, 256, 0, st>>>(it, g.n, g.npoly, g.npad);
+        k_moments<float, float><<<it.nitems, 256, words * sizeof(float), st>>>(it, g.n, g.P, g.npoly, g.npad);
     else
-        k_moments<double, double><<<it.nitems, 256, 0, st>>>(it, g.n, g.npoly, g.npad);
+        k_moments<double, double><<<it.nitems, 256, words * sizeof(double), st>>>(it, g.n, g.P, g.npoly, g.npad);
     return cudaGetLastError();
 }
 

@@ -50,7 +50,8 @@ struct PlanPtrs {
     void *a1, *a4;        // local-convolution spectra workspace
     void *cl, *fp;        // local fields on the coarse lattice / alpha face planes
     const void *khat;     // patch kernel spectrum octant (working precision)
-    const void *momw;     // Boole weight x Q^p at the patch nodes (working precision of the moments)
+    const void *momw;     // 1D moment weights a_k(m) = w_m q_k(2m/n - 1), P x (n+1), FP64
+    double mom_scale;     // R^{-3/2}
     double *mom;
     float *mom_f;
     double *resid;
@@ -85,8 +86,7 @@ struct mlc_plan_s {
     int dgf_L;
     double *khat;            // patch kernel spectrum octant (Mh^3), scaled by h^2/M^3
     double *khat_c;          // coarse kernel spectrum octant (Mhc^3), scaled by H^2/Mc^3
-    double *momw;            // npoly x nb^3
-    float *momw_f;           // split tier: FP32 copy
+    double *momw;            // P x nb 1D moment weights (Boole weight x orthonormal Legendre)
     int *rmap;
     double *Dtab, *Ttab;
     float *Dtab_f, *Ttab_f;  // split tier: FP32 copies for the Legendre ring sums

@@ -242,7 +242,7 @@ mlc_status build_tables(mlc_plan_s *pl) {
     for (int k = 0; k < g.P; ++k)
         for (int m = 0; m < nb; ++m) leg[(size_t)k * nb + m] = legendre(k, 2.0 * m / n - 1.0);
     const double rs = std::pow(g.R, -1.5);
-    std::vector<double> momw((size_t)g.npoly * nb3), lcharge((size_t)g.npoly * nb3);
+    std::vector<double> lcharge((size_t)g.npoly * nb3);
     for (int p = 0; p < g.npoly; ++p)
         for (int m0 = 0; m0 < nb; ++m0)
             for (int m1 = 0; m1 < nb; ++m1)
@@ -251,11 +251,13 @@ mlc_status build_tables(mlc_plan_s *pl) {
                                      leg[(size_t)pidx[p][1] * nb + m1] *
                                      leg[(size_t)pidx[p][2] * nb + m2];
                     const size_t m = ((size_t)m0 * nb + m1) * nb + m2;
-                    momw[(size_t)p * nb3 + m] = bw[m0] * bw[m1] * bw[m2] * q;
                     lcharge[(size_t)p * nb3 + m] = chi1[m0] * chi1[m1] * chi1[m2] * q;
                 }
-    TRY(dev_upload(pl, &pl->momw, momw));
-    if (g.tier == MLC_TIER_SPLIT) TRY(dev_upload(pl, &pl->momw_f, std::vector<float>(momw.begin(), momw.end())));
+    // moments are separable: 1D weights a_k(m) = w_m q_k(m), R^{-3/2} applied in the kernel
+    std::vector<double> a1d((size_t)g.P * nb);
+    for (int k = 0; k < g.P; ++k)
+        for (int m = 0; m < nb; ++m) a1d[(size_t)k * nb + m] = bw[m] * leg[(size_t)k * nb + m];
+    TRY(dev_upload(pl, &pl->momw, a1d));
 
     // face planes of the patch lattice inside Omega_alpha (relative x = pl0 + j n)
     g.pl0 = g.n * ceildiv(-g.ga, g.n);
@@ -586,7 +588,8 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
         h.cl = pl->cl;
         h.fp = pl->fpl;
         h.khat = G.tier == MLC_TIER_SPLIT ? (const void *)pl->khat_f : (const void *)pl->khat_df;
-        h.momw = G.tier == MLC_TIER_SPLIT ? (const void *)pl->momw_f : (const void *)pl->momw;
+        h.momw = pl->momw;
+        h.mom_scale = std::pow(G.R, -1.5);
         h.mom = pl->mom;
         h.mom_f = pl->mom_f;
         h.resid = pl->resid;
