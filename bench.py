@@ -41,32 +41,96 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """SM clock, power and clock-event reasons sampled during the timed region:
+    through NVML (ctypes, every 2 ms) when the device's PCI bus id is known,
+    else nvidia-smi every 200 ms.  Only samples inside begin()/end() count."""
 
+    REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
+               0x4: "sw_power_cap", 0x80: "hw_power_brake_slowdown"}
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
-        self.index = index
-        self.samples = []
+    def __init__(self, cuda_index: int):
+        self.cuda_index = cuda_index
+        self.samples = []  # (time, sm_mhz, max_mhz, power_w, reason names)
+        self.t0 = self.t1 = None
+        self.source = None
         self._stop = threading.Event()
         self._th = None
 
-    def _run(self):
+    def begin(self):
+        self.t0 = time.perf_counter()
+
+    def end(self):
+        self.t1 = time.perf_counter()
+
+    def _pci_bus_id(self):
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(self.cuda_index)
+            return "%08x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+        except Exception:
+            return None
+
+    def _nvml(self):
+        import ctypes
+        bus = self._pci_bus_id()
+        if bus is None:
+            return None
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None
+            h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) != 0:
+                return None
+            try:
+                reasons = lib.nvmlDeviceGetCurrentClocksEventReasons
+            except AttributeError:
+                reasons = lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            return lib, h, reasons
+        except OSError:
+            return None
+
+    def _run_nvml(self, lib, h, reasons):
+        import ctypes
+        clk, mx, pw, bits = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            t = time.perf_counter()
+            if (lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0 and
+                    lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0 and
+                    reasons(h, ctypes.byref(bits)) == 0):
+                power = pw.value / 1e3 if lib.nvmlDeviceGetPowerUsage(h, ctypes.byref(pw)) == 0 else None
+                names = [v for k, v in self.REASONS.items() if bits.value & k]
+                self.samples.append((t, float(clk.value), float(mx.value), power, names))
+            self._stop.wait(0.002)
+
+    def _run_smi(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         while not self._stop.is_set():
             try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                t = time.perf_counter()
+                out = subprocess.run(["nvidia-smi", "-i", str(self.cuda_index), f"--query-gpu={self.FIELDS}",
                                       "--format=csv,noheader,nounits"], capture_output=True, text=True,
                                      timeout=5).stdout.strip()
-                if out:
-                    self.samples.append([x.strip() for x in out.split(",")])
+                f = [x.strip() for x in out.split(",")]
+                if len(f) >= 7 and f[0].replace(".", "").isdigit():
+                    act = [names[k] for k in range(4) if f[3 + k].lower() == "active"]
+                    power = float(f[2]) if f[2].replace(".", "").isdigit() else None
+                    self.samples.append((t, float(f[0]), float(f[1]), power, act))
             except Exception:
                 pass
             self._stop.wait(0.2)
 
     def __enter__(self):
-        self._th = threading.Thread(target=self._run, daemon=True)
+        nv = self._nvml()
+        if nv is not None:
+            self.source = "nvml, 2 ms"
+            self._th = threading.Thread(target=self._run_nvml, args=nv, daemon=True)
+        else:
+            self.source = "nvidia-smi, 200 ms"
+            self._th = threading.Thread(target=self._run_smi, daemon=True)
         self._th.start()
         return self
 
@@ -76,21 +140,16 @@ class ClockSampler:
             self._th.join(timeout=10)
 
     def summary(self):
-        if not self.samples:
+        sel = [x for x in self.samples
+               if self.t0 is None or (x[0] >= self.t0 and (self.t1 is None or x[0] <= self.t1))]
+        if not sel:  # region shorter than the sampling period: nearest samples
+            sel = self.samples[-2:]
+        if not sel:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for s in self.samples for k in range(4)
-                          if len(s) > 3 + k and s[3 + k].lower() == "active"})
-        return {"sm_mhz": float(np.median(sm)) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.samples)}
-
-
-def conv_pass_flops(M: int, lines: int, passes: int = 1) -> float:
-    """Nominal radix-2 FLOPs of `passes` complex FFTs of length M on `lines` lines."""
-    return lines * passes * 5.0 * M * np.log2(M)
+        pw = [x[3] for x in sel if x[3] is not None]
+        return {"sm_mhz": float(np.median([x[1] for x in sel])), "sm_max_mhz": max(x[2] for x in sel),
+                "reasons": sorted({r for x in sel for r in x[4]}), "samples": len(sel),
+                "power_w_median": float(np.median(pw)) if pw else None, "source": self.source}
 
 
 def reduce_max_ms(ms: float, world: int, device: str = "cuda") -> float:
@@ -108,7 +167,7 @@ def aggregate_value(points_per_rank: float, world: int, ms_max: float) -> float:
     return world * points_per_rank / (ms_max * 1e-3) / 1e6
 
 
-def time_plan(plan, f, phi, steps, warmup, flush, stream, world):
+def time_plan(plan, f, phi, steps, warmup, flush, stream, world, clk=None):
     """Mean device time per solve (CUDA events on the launching stream, L2
     flushed between steps outside the timed region) and per-launch means."""
     import torch
@@ -122,6 +181,8 @@ def time_plan(plan, f, phi, steps, warmup, flush, stream, world):
     per_launch, total_ms = {}, 0.0
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    if clk is not None:
+        clk.begin()
     for _ in range(steps):
         ev0.record(stream)
         plan.solve(f, phi, stream)
@@ -132,33 +193,75 @@ def time_plan(plan, f, phi, steps, warmup, flush, stream, world):
             per_launch[k] = per_launch.get(k, 0.0) + v
         flush.zero_()
     torch.cuda.synchronize()
+    if clk is not None:
+        clk.end()
     plan.set_timing(False)
     return total_ms / steps, {k: v / steps for k, v in per_launch.items()}
 
 
+# FP32 pipe lane-instruction rate of one GB300 from its unit counts and
+# maximum clock: 152 SMs x 128 FP32 lanes x 2.07 GHz (FADD, FMUL and FFMA
+# issue at the same rate).  Both tiers run their FFTs on this pipe: the split
+# tier in FP32, the FP64 tier in double-float (hi + lo FP32 pairs).
+FP32_LANE_INST_PER_S = 152 * 128 * 2.07e9
+
+# FP32 instructions of one (unnormalised) double-float operation: add =
+# two-sum (6) + low parts (2); multiply = FMUL + 3 FFMA.
+DF_ADD_INST, DF_MUL_INST = 8, 4
+
+
+def fft64_schedule_inst(tier: str, sparse: bool) -> float:
+    """FP32 instructions of one 64-point line in the radix-8 x 8 schedule of the
+    slab kernel: 16 radix-8 butterflies (52 real adds + 4 real multiplies each;
+    26 adds + 2 multiplies for a first-stage butterfly whose inputs 3..7 are
+    zero, `sparse`) and 56 twiddle products (7 per thread of the line group)."""
+    first = (26, 2) if sparse else (52, 4)
+    adds = 8 * first[0] + 8 * 52
+    muls = 8 * first[1] + 8 * 4
+    if tier == "fp64":  # twiddle = 4 multiplies + 2 adds, all double-float
+        return (adds + 56 * 2) * DF_ADD_INST + (muls + 56 * 4) * DF_MUL_INST
+    return adds + muls + 56 * 4  # FP32: twiddle = 2 FMUL + 2 FFMA
+
+
+def slab_rows(w, ga):
+    """z rows of the field box the inverse-x step reads (Omega_alpha rows and
+    coarse rows), i.e. the inverse-y lines of a slab."""
+    W = w.n + 2 * w.s + 1
+    return sum(1 for zi in range(W) if (-ga <= zi - w.s <= w.n + ga) or (zi - w.s) % 4 == 0)
+
+
 def roofline_for(w, plan, per_launch, tier):
+    """Roofline of the dominant launch (the slab kernel).  Algorithmic work =
+    nominal radix-2 FFT FLOPs (5 M log2 M per complex line) over the lines the
+    pruned transform must produce (forward y on the n+1 nonzero z rows, forward
+    and inverse z on all M columns, inverse y on the z rows read later), plus 2
+    FLOPs per entry of the real-kernel product; FP64-equivalent FLOPs in the
+    FP64 tier.  Peak = the FP32 pipe's instruction rate times the nominal FLOPs
+    one FP32 instruction of the kernel's schedule carries: the rate the kernel
+    would reach if the pipe issued nothing but its arithmetic."""
     info = plan.info
     N = w.N
-    M, Mh, NP, W = info.M, info.M // 2 + 1, (N // w.n) ** 3, w.n + 2 * w.s + 1
+    M, Mh, NP = info.M, info.M // 2 + 1, (N // w.n) ** 3
     nin = w.n + 1
-    flops = {
-        # per (patch, kx) slab: forward y on nin lines, forward and inverse z on M lines,
-        # inverse y on W lines, and the real kernel product (2 flops per complex entry)
-        "conv_slab": conv_pass_flops(M, NP * Mh * (nin + 2 * M + W)) + NP * Mh * M * M * 2.0,
-        "conv_inv_x": conv_pass_flops(M, NP * W * W),
-        "conv_fwd_x": conv_pass_flops(M, NP * nin * nin),
-    }
     dom = max(per_launch, key=per_launch.get)
-    if dom not in flops:
+    if dom != "conv_slab" or M != 64:
         return None
-    achieved = flops[dom] / (per_launch[dom] * 1e-3) / 1e9
-    if tier == "fp64":
-        peak, unit = 1190.0, "GFLOP/s (FP64)"
-    else:
-        peak, unit = 69900.0, "GFLOP/s (FP32)"
-    return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": unit,
-            "frac": round(achieved / peak, 4), "traffic": None, "launch_ms": round(per_launch[dom], 4),
-            "flops_per_launch": flops[dom]}
+    nz = slab_rows(w, info.g_alpha)
+    line_flops = 5.0 * M * np.log2(M)
+    nominal = (nin + 2 * M + nz) * line_flops + 2.0 * M * M
+    prod_inst = M * M * (2 * DF_MUL_INST if tier == "fp64" else 2)
+    inst = ((nin + M) * fft64_schedule_inst(tier, True) + (M + nz) * fft64_schedule_inst(tier, False)
+            + prod_inst)
+    flops = NP * Mh * nominal
+    achieved = flops / (per_launch[dom] * 1e-3) / 1e12
+    peak = FP32_LANE_INST_PER_S * nominal / inst / 1e12
+    basis = ("FP32 pipe 152 SMs x 128 lanes x 2.07 GHz = 40.27 T inst/s x %.4f nominal %s FLOP per FP32 "
+             "instruction of the radix-8x8 %s schedule" % (nominal / inst, "FP64-equivalent" if tier == "fp64"
+                                                           else "FP32", "double-float" if tier == "fp64" else "FP32"))
+    return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 3),
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "launch_ms": round(per_launch[dom], 4), "flops_per_launch": flops,
+            "fp32_inst_per_launch": NP * Mh * inst, "peak_basis": basis}
 
 
 def run_ours(args, rank, world):
@@ -177,7 +280,7 @@ def run_ours(args, rank, world):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clk:
-        ms, per_launch = time_plan(plan, f, phi, args.steps, args.warmup, flush, stream, world)
+        ms, per_launch = time_plan(plan, f, phi, args.steps, args.warmup, flush, stream, world, clk)
     ms = reduce_max_ms(ms, world)
 
     # end to end through the C ABI with host buffers (copies inside the call)

@@ -32,11 +32,11 @@ __device__ __forceinline__ int floordiv(int a, int b) {  // b > 0
 
 // ---------------------------------------------------------------------------
 // Double-float arithmetic: a value is an unevaluated sum hi + lo of two FP32
-// numbers (|lo| <= ulp(hi)/2), about 48 significand bits.  Sums use the
-// error-free two-sum of Knuth, products the FMA-based two-product; the FFT
-// error bound is relative to the data norm, so the additions need not
-// renormalise the low parts twice.  GB300 issues FP32 on ~67x more lanes than
-// FP64, so the FP64 tier's local-convolution slab runs in this arithmetic.
+// numbers (|lo| a few ulp(hi) at most), about 48 significand bits.  Sums use
+// the error-free two-sum of Knuth, products the FMA-based two-product; the
+// FFT and DST error bounds are relative to the data norm, so no operation
+// renormalises the pair.  GB300 issues FP32 on ~67x more lanes than FP64, so
+// the FP64 tier's transforms and ring sums run in this arithmetic.
 // ---------------------------------------------------------------------------
 struct dfl {
     float hi, lo;
@@ -62,9 +62,14 @@ __device__ __forceinline__ dfl fast_two_sum(float a, float b) {
     const float s = a + b;
     return {s, b - (s - a)};
 }
+// Sum and product are left unnormalised: (hi, lo) stays an unevaluated sum
+// whose |lo| is a few ulp(hi) at most.  two_sum of the high parts is exact for
+// any pair, and the product's residual is already of order 2^-24 |p|, so the
+// pair keeps its ~2^-48 relative accuracy while each operation saves the
+// three instructions of a fast two-sum.
 __device__ __forceinline__ dfl df_add(dfl a, dfl b) {
-    dfl s = two_sum(a.hi, b.hi);
-    return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+    const dfl s = two_sum(a.hi, b.hi);
+    return {s.hi, s.lo + (a.lo + b.lo)};
 }
 __device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
@@ -73,18 +78,11 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
     float e = fmaf(a.hi, b.hi, -p);
     e = fmaf(a.hi, b.lo, e);
     e = fmaf(a.lo, b.hi, e);
-    return fast_two_sum(p, e);
+    return {p, e};
 }
-__device__ __forceinline__ dcx dc_add(dcx a, dcx b) { return {df_add(a.x, b.x), df_add(a.y, b.y)}; }
-__device__ __forceinline__ dcx dc_sub(dcx a, dcx b) { return {df_sub(a.x, b.x), df_sub(a.y, b.y)}; }
 __device__ __forceinline__ dcx dc_mul(dcx a, dcx w) {
     return {df_sub(df_mul(a.x, w.x), df_mul(a.y, w.y)), df_add(df_mul(a.x, w.y), df_mul(a.y, w.x))};
 }
-__device__ __forceinline__ dcx dc_mul_mi(dcx v, bool inv) {  // x (-i) forward, x (+i) inverse
-    return inv ? dcx{df_neg(v.y), v.x} : dcx{v.y, df_neg(v.x)};
-}
-__device__ __forceinline__ dcx dc_scale(dcx v, dfl k) { return {df_mul(v.x, k), df_mul(v.y, k)}; }
-
 __device__ __forceinline__ dfl operator+(dfl a, dfl b) { return df_add(a, b); }
 __device__ __forceinline__ dfl operator-(dfl a, dfl b) { return df_sub(a, b); }
 __device__ __forceinline__ dfl operator-(dfl a) { return df_neg(a); }
@@ -92,6 +90,15 @@ __device__ __forceinline__ dfl operator*(dfl a, dfl b) { return df_mul(a, b); }
 __device__ __forceinline__ dfl &operator*=(dfl &a, dfl b) { return a = df_mul(a, b); }
 __device__ __forceinline__ dfl &operator+=(dfl &a, dfl b) { return a = df_add(a, b); }
 __device__ __forceinline__ dcx cmul(dcx a, dcx w) { return dc_mul(a, w); }
+
+// Renormalise a double-float complex value (|lo| <= ulp(hi)/2 again).  The
+// transforms do it where a line is loaded (and every other radix-2 stage), so
+// the unnormalised low parts grow over a few butterfly stages at most; FP32
+// and FP64 values pass through.
+__device__ __forceinline__ dfl renorm(dfl v) { return fast_two_sum(v.hi, v.lo); }
+__device__ __forceinline__ dcx renorm(dcx v) { return {fast_two_sum(v.x.hi, v.x.lo), fast_two_sum(v.y.hi, v.y.lo)}; }
+__device__ __forceinline__ float2 renorm(float2 v) { return v; }
+__device__ __forceinline__ double2 renorm(double2 v) { return v; }
 
 // Complex type of each working precision (FP64 tier: double; split tier: float).
 template <typename R> struct Cx;
@@ -154,7 +161,8 @@ __device__ __forceinline__ void fft_dif(C *buf, int nlines, int lstride, int est
             const int i0 = (grp << (st + 1)) + pos;
             C *p0 = buf + line * lstride + (line >= gap_at ? gap : 0) + i0 * estride;
             C *p1 = p0 + hs * estride;
-            const C a = *p0, b = *p1;
+            C a = *p0, b = *p1;
+            if (st & 1) { a = renorm(a); b = renorm(b); }
             *p0 = cadd(a, b);
             *p1 = twiddle(csub(a, b), st, pos, tsh, tw, inv);
         }
@@ -178,8 +186,9 @@ __device__ __forceinline__ void fft_dit(C *buf, int nlines, int lstride, int est
             const int i0 = (grp << (st + 1)) + pos;
             C *p0 = buf + line * lstride + (line >= gap_at ? gap : 0) + i0 * estride;
             C *p1 = p0 + hs * estride;
-            const C a = *p0;
-            const C t = twiddle(*p1, st, pos, tsh, tw, inv);
+            C a = *p0, b = *p1;
+            if (!(st & 1)) { a = renorm(a); b = renorm(b); }
+            const C t = twiddle(b, st, pos, tsh, tw, inv);
             *p0 = cadd(a, t);
             *p1 = csub(a, t);
         }
@@ -584,7 +593,7 @@ __device__ __forceinline__ void fft64_line(C *line, int estride, int t, bool val
 #pragma unroll
     for (int n2 = 0; n2 < 8; ++n2) {
         const int pos = 8 * n2 + t;
-        v[n2] = (valid && pos < nvalid) ? line[pos * estride] : Cx<R>::mk(0, 0);
+        v[n2] = (valid && pos < nvalid) ? renorm(line[pos * estride]) : Cx<R>::mk(0, 0);
     }
     dft8<C, R>(v, inv);
 #pragma unroll
@@ -648,10 +657,66 @@ template <typename R> struct Pitch64 { static constexpr int P = sizeof(R) == 4 ?
 // complex entries); plain FP64 lines exchange in place.
 template <typename R> struct UseXs { static constexpr bool v = !std::is_same<R, double>::value; };
 
-// Fused slab for M = 64 with the register FFT (same contract as k_slab).
-// The slab is held as S[z][y] (row z, pitch P), so the global block
-// [zi][yi] loads and the [z row][y] output stores are contiguous in both
-// memories.
+// First radix-8 butterfly of a line whose inputs 3..7 are zero (the forward
+// passes, whose n+1 <= 24 nonzero samples sit at positions 8 n2 + t, n2 < 3):
+// the stage sums with a zero operand are left out (26 complex additions and
+// one w8 product fewer than dft8).
+template <typename C, typename R>
+__device__ __forceinline__ void dft8_in3(C (&v)[8], bool inv) {
+    const C v0 = v[0], v1 = v[1], v2 = v[2];
+    const C u5 = w8mul<C, R>(v1, 1, inv), u6 = mul_mi(v2, inv);
+    v[0] = cadd(v0, v2);
+    v[2] = csub(v0, v2);
+    v[1] = v1;
+    v[3] = mul_mi(v1, inv);
+    v[4] = cadd(v0, u6);
+    v[6] = csub(v0, u6);
+    v[5] = u5;
+    v[7] = mul_mi(u5, inv);
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) {
+        const C a = v[i], b = v[i + 1];
+        v[i] = cadd(a, b);
+        v[i + 1] = csub(a, b);
+    }
+    C t = v[1]; v[1] = v[4]; v[4] = t;
+    t = v[3]; v[3] = v[6]; v[6] = t;
+}
+
+// The register part of a 64-point line transform (radix 8 x 8, as fft64_line):
+// lane t holds x[8 n2 + t] in v[n2] on entry and X[t + 8 k2] in v[k2] on exit,
+// exchanging once through the group's padded scratch xs (row pitch 9).  The
+// exit layout is the entry layout of the next transform of the same line, so
+// a forward transform, a pointwise product and an inverse transform chain in
+// registers.  SPARSE: v[3..7] are zero on entry.  Double-float inputs are
+// renormalised first.
+template <typename C, typename R, bool SPARSE>
+__device__ __forceinline__ void line64_regs(C (&v)[8], int t, const C (&wt)[8], bool inv, C *xs) {
+#pragma unroll
+    for (int n2 = 0; n2 < (SPARSE ? 3 : 8); ++n2) v[n2] = renorm(v[n2]);
+    if (SPARSE) dft8_in3<C, R>(v, inv);
+    else dft8<C, R>(v, inv);
+#pragma unroll
+    for (int k1 = 1; k1 < 8; ++k1) {
+        C w = wt[k1];
+        if (inv) w.y = -w.y;
+        v[k1] = cmul(v[k1], w);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) xs[9 * k1 + t] = v[k1];
+    __syncwarp();
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) v[n1] = xs[9 * t + n1];
+    __syncwarp();
+    dft8<C, R>(v, inv);
+}
+
+// Fused slab for M = 64 (same contract as k_slab): R = float (split tier) or
+// dfl (FP64 tier, double-float arithmetic on FP64 data).  The slab is S[z][y]
+// (row pitch P).  Passes: forward y on the nin nonzero z rows; per y column,
+// forward z, product with the real kernel spectrum and inverse z in registers
+// (only the z rows the inverse-x step reads are stored back); inverse y on
+// those rows only.  Requires nin <= 24.
 template <typename R>
 __global__ void __launch_bounds__(256) k_slab64(SlabArgs a) {
     using C = typename Cx<R>::T;
@@ -659,7 +724,8 @@ __global__ void __launch_bounds__(256) k_slab64(SlabArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw64 = (C *)smem_raw;  // 64 twiddles exp(-2 pi i j / 64)
     C *S = tw64 + M;
-    C *xs = UseXs<R>::v ? S + M * P : nullptr;  // blockDim/8 x 72 exchange entries
+    C *xs = S + M * P;        // blockDim/8 x 72 exchange entries
+    int *rowoff = (int *)(xs + 32 * 72);
     const int nin = a.nin, W = a.nout;
     const C *tw = (const C *)a.tw;  // M/2 entries; extend by w^(j+32) = -w^j
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
@@ -667,195 +733,103 @@ __global__ void __launch_bounds__(256) k_slab64(SlabArgs a) {
         if (j >= 32) { w.x = -w.x; w.y = -w.y; }
         tw64[j] = w;
     }
-    // one slab per CTA, or (persistent launch) a grid-stride loop over slabs
-    const int nunits = a.it.nitems * MH;
-    for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
-    const int kx = unit % MH;
-    int p;
-    const PlanPtrs &PP = item_plan(a.it, unit / MH, p);
-    const C *in = (const C *)PP.a1 + ((long)p * MH + kx) * nin * nin;
-    for (int e = threadIdx.x; e < nin * nin; e += blockDim.x) {
-        const int zi = e / nin, yi = e % nin;
-        S[zi * P + yi] = in[e];
-    }
-    __syncthreads();
-    // forward y on the nin nonzero z rows (y >= nin read as zero)
-    fft64_lines<C, R>(S, nin, P, 1, nin, tw64, false, xs);
-    // forward z on all 64 y columns (z >= nin read as zero)
-    fft64_lines<C, R>(S, M, 1, P, nin, tw64, false, xs);
-    const R *khat = (const R *)PP.khat;
-    for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
-        const int kz0 = e / M, ky0 = e % M;
-        const int ky = ky0 < M - ky0 ? ky0 : M - ky0;
-        const int kz = kz0 < M - kz0 ? kz0 : M - kz0;
-        const R k = khat[((long)kx * MH + ky) * MH + kz];
-        C v = S[kz0 * P + ky0];
-        v.x *= k;
-        v.y *= k;
-        S[kz0 * P + ky0] = v;
-    }
-    __syncthreads();
-    // inverse z on all 64 ky columns
-    fft64_lines<C, R>(S, M, 1, P, M, tw64, true, xs);
-    // inverse y on the output z rows only: the wrapped range of positions
-    // pos0 .. pos0+n1-1, then 0 .. W-n1-1
-    int pos0 = a.out_off % M;
-    if (pos0 < 0) pos0 += M;
-    const int n1 = (pos0 + W <= M) ? W : M - pos0;
-    fft64_lines<C, R>(S + pos0 * P, W, P, 1, M, tw64, true, xs, n1, -(pos0 + n1) * P);
-    C *out = (C *)PP.a4 + (long)p * a.nz * a.blk;
-    for (int e = threadIdx.x; e < a.nz * W; e += blockDim.x) {
-        const int jz = e / W, yo = e % W, zo = a.zrow[jz];
-        int pz = (a.out_off + zo) % M, py = (a.out_off + yo) % M;
+    // output z rows as slab rows (the field box starts at out_off, wrapped mod M)
+    unsigned long long rowmask = 0;
+    for (int j = 0; j < a.nz; ++j) {
+        int pz = (a.out_off + a.zrow[j]) % M;
         if (pz < 0) pz += M;
-        if (py < 0) py += M;
-        out[(long)jz * a.blk + kx * W + yo] = S[pz * P + py];
+        rowmask |= 1ull << pz;
+        if (threadIdx.x == 0) rowoff[j] = pz * P;
     }
-    __syncthreads();  // S is rewritten by the next unit
-    }
-}
-
-__device__ __forceinline__ dcx dc_w8mul(dcx d, int j, bool inv, dfl s) {  // x w8^j, s = 1/sqrt(2)
-    switch (j) {
-        case 0: return d;
-        case 1:
-            return inv ? dcx{df_mul(df_sub(d.x, d.y), s), df_mul(df_add(d.x, d.y), s)}
-                       : dcx{df_mul(df_add(d.x, d.y), s), df_mul(df_sub(d.y, d.x), s)};
-        case 2: return dc_mul_mi(d, inv);
-        default:
-            return inv ? dcx{df_neg(df_mul(df_add(d.x, d.y), s)), df_mul(df_sub(d.x, d.y), s)}
-                       : dcx{df_mul(df_sub(d.y, d.x), s), df_neg(df_mul(df_add(d.x, d.y), s))};
-    }
-}
-
-__device__ __forceinline__ void dc_dft8(dcx (&v)[8], bool inv, dfl s) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const dcx a = v[i], b = v[i + 4];
-        v[i] = dc_add(a, b);
-        v[i + 4] = dc_w8mul(dc_sub(a, b), i, inv, s);
-    }
-#pragma unroll
-    for (int g = 0; g < 8; g += 4)
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const dcx a = v[g + i], b = v[g + i + 2];
-            v[g + i] = dc_add(a, b);
-            v[g + i + 2] = dc_w8mul(dc_sub(a, b), 2 * i, inv, s);
-        }
-#pragma unroll
-    for (int i = 0; i < 8; i += 2) {
-        const dcx a = v[i], b = v[i + 1];
-        v[i] = dc_add(a, b);
-        v[i + 1] = dc_sub(a, b);
-    }
-    dcx t = v[1]; v[1] = v[4]; v[4] = t;
-    t = v[3]; v[3] = v[6]; v[6] = t;
-}
-
-// 64-point transform of one line by 8 threads in double-float (the radix
-// 8 x 8 scheme of fft64_line, exchange through the line's storage).
-__device__ __forceinline__ void dc_fft64_line(dcx *line, int estride, int t, bool valid, int nvalid,
-                                              const dcx (&wt)[8], bool inv, dfl s, dcx *xs) {
-    dcx v[8];
-    const dcx zero{{0.f, 0.f}, {0.f, 0.f}};
-#pragma unroll
-    for (int n2 = 0; n2 < 8; ++n2) {
-        const int pos = 8 * n2 + t;
-        v[n2] = (valid && pos < nvalid) ? line[pos * estride] : zero;
-    }
-    dc_dft8(v, inv, s);
-#pragma unroll
-    for (int k1 = 1; k1 < 8; ++k1) {
-        dcx w = wt[k1];
-        if (inv) w.y = df_neg(w.y);
-        v[k1] = dc_mul(v[k1], w);
-    }
-    // exchange through the group's padded scratch (row pitch 9): the 8 lanes of
-    // a quarter-warp phase hit 8 different 16-byte bank quads on both sides
-#pragma unroll
-    for (int k1 = 0; k1 < 8; ++k1) xs[9 * k1 + t] = v[k1];
-    __syncwarp();
-#pragma unroll
-    for (int n1 = 0; n1 < 8; ++n1) v[n1] = xs[9 * t + n1];
-    __syncwarp();
-    dc_dft8(v, inv, s);
-#pragma unroll
-    for (int k2 = 0; k2 < 8; ++k2)
-        if (valid) line[(t + 8 * k2) * estride] = v[k2];
-    __syncwarp();
-}
-
-__device__ __forceinline__ void dc_fft64_lines(dcx *base, int nlines, int lstride, int estride, int nvalid,
-                                               const dcx *tw64, bool inv, dcx *xs, int gap_at = 1 << 30,
-                                               int gap = 0) {
     const int grp = threadIdx.x >> 3, t = threadIdx.x & 7, ngrp = blockDim.x >> 3;
-    dcx *gx = xs + grp * 72;
-    const dfl s = df_from(0.70710678118654752440);
-    dcx wt[8];
+    C *gx = xs + grp * 72;
+    __syncthreads();
+    C wt[8];
 #pragma unroll
     for (int k1 = 0; k1 < 8; ++k1) wt[k1] = tw64[(t * k1) & 63];
-    for (int l0 = 0; l0 < nlines; l0 += ngrp) {
-        const int l = l0 + grp;
-        const bool valid = l < nlines;
-        dcx *line = base + (valid ? l * lstride + (l >= gap_at ? gap : 0) : 0);
-        dc_fft64_line(line, estride, t, valid, nvalid, wt, inv, s, gx);
-    }
-    __syncthreads();
-}
-
-// Fused slab (M = 64) of the FP64 tier in double-float arithmetic: FP64 data
-// in and out (A1, kernel spectrum, A4 as in k_slab64<double>).
-__global__ void __launch_bounds__(256) k_slab64_df(SlabArgs a) {
-    constexpr int M = 64, MH = 33, P = 65;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    dcx *tw64 = (dcx *)smem_raw;
-    dcx *S = tw64 + M;
-    dcx *xs = S + M * P;  // 32 groups x 72 exchange entries
-    const int nin = a.nin, W = a.nout;
-    const dcx *tw = (const dcx *)a.tw;  // exp(-2 pi i j / 64), j < 32, double-float
-    for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        dcx w = tw[j & 31];
-        if (j >= 32) { w.x = df_neg(w.x); w.y = df_neg(w.y); }
-        tw64[j] = w;
-    }
+    const C zero = Cx<R>::mk(0, 0);
+    // one slab per CTA, or (persistent launch) a grid-stride loop over slabs
     const int nunits = a.it.nitems * MH;
     for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
         const int kx = unit % MH;
         int p;
         const PlanPtrs &PP = item_plan(a.it, unit / MH, p);
-        const dcx *in = (const dcx *)PP.a1 + ((long)p * MH + kx) * nin * nin;
+        const C *in = (const C *)PP.a1 + ((long)p * MH + kx) * nin * nin;
         for (int e = threadIdx.x; e < nin * nin; e += blockDim.x) {
             const int zi = e / nin, yi = e % nin;
             S[zi * P + yi] = in[e];
         }
         __syncthreads();
-        dc_fft64_lines(S, nin, P, 1, nin, tw64, false, xs);
-        dc_fft64_lines(S, M, 1, P, nin, tw64, false, xs);
-        const dfl *khat = (const dfl *)PP.khat;
-        for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
-            const int kz0 = e / M, ky0 = e % M;
-            const int ky = ky0 < M - ky0 ? ky0 : M - ky0;
-            const int kz = kz0 < M - kz0 ? kz0 : M - kz0;
-            S[kz0 * P + ky0] = dc_scale(S[kz0 * P + ky0], khat[((long)kx * MH + ky) * MH + kz]);
+        // forward y on the nin nonzero z rows
+        for (int l0 = 0; l0 < nin; l0 += ngrp) {
+            const int l = l0 + grp;
+            const bool valid = l < nin;
+            C *line = S + (valid ? l * P : 0);
+            C v[8];
+#pragma unroll
+            for (int n2 = 0; n2 < 8; ++n2) {
+                const int pos = 8 * n2 + t;
+                v[n2] = (n2 < 3 && valid && pos < nin) ? line[pos] : zero;
+            }
+            line64_regs<C, R, true>(v, t, wt, false, gx);
+#pragma unroll
+            for (int k2 = 0; k2 < 8; ++k2)
+                if (valid) line[t + 8 * k2] = v[k2];
         }
         __syncthreads();
-        dc_fft64_lines(S, M, 1, P, M, tw64, true, xs);
-        int pos0 = a.out_off % M;
-        if (pos0 < 0) pos0 += M;
-        const int n1 = (pos0 + W <= M) ? W : M - pos0;
-        dc_fft64_lines(S + pos0 * P, W, P, 1, M, tw64, true, xs, n1, -(pos0 + n1) * P);
-        dcx *out = (dcx *)PP.a4 + (long)p * a.nz * a.blk;
+        // per y column: forward z, kernel product, inverse z (64 columns)
+        const R *khat = (const R *)PP.khat + (long)kx * MH * MH;
+        for (int ky0 = grp; ky0 < M; ky0 += ngrp) {
+            C *col = S + ky0;
+            C v[8];
+#pragma unroll
+            for (int n2 = 0; n2 < 8; ++n2) {
+                const int pos = 8 * n2 + t;
+                v[n2] = (n2 < 3 && pos < nin) ? col[pos * P] : zero;
+            }
+            line64_regs<C, R, true>(v, t, wt, false, gx);
+            const R *kk = khat + (ky0 < M - ky0 ? ky0 : M - ky0) * MH;
+#pragma unroll
+            for (int k2 = 0; k2 < 8; ++k2) {
+                const int kz0 = t + 8 * k2;
+                const R k = kk[kz0 < M - kz0 ? kz0 : M - kz0];
+                v[k2].x *= k;
+                v[k2].y *= k;
+            }
+            line64_regs<C, R, false>(v, t, wt, true, gx);
+#pragma unroll
+            for (int k2 = 0; k2 < 8; ++k2) {
+                const int z = t + 8 * k2;
+                if ((rowmask >> z) & 1ull) col[z * P] = v[k2];
+            }
+        }
+        __syncthreads();
+        // inverse y on the output z rows
+        for (int l0 = 0; l0 < a.nz; l0 += ngrp) {
+            const int l = l0 + grp;
+            const bool valid = l < a.nz;
+            C *line = S + (valid ? rowoff[l] : 0);
+            C v[8];
+#pragma unroll
+            for (int n2 = 0; n2 < 8; ++n2) v[n2] = valid ? line[8 * n2 + t] : zero;
+            line64_regs<C, R, false>(v, t, wt, true, gx);
+#pragma unroll
+            for (int k2 = 0; k2 < 8; ++k2)
+                if (valid) line[t + 8 * k2] = v[k2];
+        }
+        __syncthreads();
+        C *out = (C *)PP.a4 + (long)p * a.nz * a.blk;
         for (int e = threadIdx.x; e < a.nz * W; e += blockDim.x) {
-            const int jz = e / W, yo = e % W, zo = a.zrow[jz];
-            int pz = (a.out_off + zo) % M, py = (a.out_off + yo) % M;
-            if (pz < 0) pz += M;
+            const int jz = e / W, yo = e % W;
+            int py = (a.out_off + yo) % M;
             if (py < 0) py += M;
-            out[(long)jz * a.blk + kx * W + yo] = S[pz * P + py];
+            out[(long)jz * a.blk + kx * W + yo] = S[rowoff[jz] + py];
         }
-        __syncthreads();
+        __syncthreads();  // S is rewritten by the next unit
     }
 }
+
+
 
 // ---------------------------------------------------------------------------
 // Inverse real transform along x of the local fields, pruned to the values
@@ -1065,6 +1039,10 @@ __global__ void __launch_bounds__(256) k_moments(Items it, int n, int P, int npo
         acc *= PP.mom_scale;
         PP.mom[(long)pch * npad + q] = acc;
         if (PP.mom_f) PP.mom_f[(long)pch * npad + q] = (float)acc;
+        if (PP.mom_df) {
+            const float hi = (float)acc;
+            PP.mom_df[(long)pch * npad + q] = make_float2(hi, (float)(acc - (double)hi));
+        }
     }
 }
 
@@ -1131,6 +1109,59 @@ __global__ void __launch_bounds__(256) k_resid(ResArgs a) {
     }
 }
 
+// One step of a compensated dot product of double-float operands: the product
+// of the high parts is split exactly (FMA residual) and added to the running
+// sum s by two-sum; the rounding errors and the low-part cross terms gather in
+// the FP32 compensation e (the Dot2 scheme of Ogita, Rump and Oishi, SIAM J.
+// Sci. Comput. 26, 2005, with double-float inputs).  Error about n u^2 sum|x y|
+// for u = 2^-24, against n u_64 sum|x y| in FP64 with u_64 = 2^-53.
+__device__ __forceinline__ void dot2_step(float &s, float &e, float xh, float xl, float yh, float yl) {
+    const float p = xh * yh;
+    float pe = fmaf(xh, yh, -p);
+    pe = fmaf(xh, yl, pe);
+    pe = fmaf(xl, yh, pe);
+    const float t = s + p, bb = t - s;
+    e += ((s - (t - bb)) + (p - bb)) + pe;
+    s = t;
+}
+
+// Ring term of one patch: dot product of two rows of n ring-table entries.
+// FP32 / FP64 rows accumulate into acc; double-float rows take the
+// compensated product.
+template <typename RT> __device__ __forceinline__ double ring_row(const RT *c, const RT *t, int n) {
+    RT v = 0;
+    for (int q = 0; q < n; ++q) v = fma(c[q], t[q], v);
+    return (double)v;
+}
+__device__ __forceinline__ double ring_row(const dfl *c, const dfl *t, int n) {
+    float s = 0.f, e = 0.f;
+    for (int q = 0; q < n; ++q) dot2_step(s, e, c[q].hi, c[q].lo, t[q].hi, t[q].lo);
+    return (double)s + (double)e;
+}
+
+// Dot product of two ring-table rows of n (a multiple of 4) elements, rows
+// 16-byte aligned.
+__device__ __forceinline__ void ring_dot(const dfl *c, const dfl *d, int n, dfl &acc) {
+    const float4 *c4 = (const float4 *)c, *d4 = (const float4 *)d;
+    float s = 0.f, e = 0.f;
+    for (int q = 0; q < n / 2; ++q) {
+        const float4 x = c4[q], y = d4[q];
+        dot2_step(s, e, x.x, x.y, y.x, y.y);
+        dot2_step(s, e, x.z, x.w, y.z, y.w);
+    }
+    acc = df_add(acc, two_sum(s, e));
+}
+__device__ __forceinline__ void ring_dot(const float *c, const float *d, int n, float &acc) {
+    const float4 *c4 = (const float4 *)c, *d4 = (const float4 *)d;
+    for (int q = 0; q < n / 4; ++q) {
+        const float4 x = c4[q], y = d4[q];
+        acc = fmaf(x.x, y.x, acc);
+        acc = fmaf(x.y, y.y, acc);
+        acc = fmaf(x.z, y.z, acc);
+        acc = fmaf(x.w, y.w, acc);
+    }
+}
+
 struct AsmArgs {
     const void *cl;          // coarse lattice of the local fields, nc^3 per patch
     const void *mom, *T;     // ring tables in the ring precision RT
@@ -1183,11 +1214,7 @@ __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
                 } else {
                     const long t = (((long)(r0 - a.cb_lo) * ncb + (r1 - a.cb_lo)) * ncb +
                                     (r2 - a.cb_lo)) * a.npoly;
-                    const RT *c = (const RT *)a.mom + p * a.npad;
-                    const RT *Tt = (const RT *)a.T + t;
-                    RT v = 0;
-                    for (int pp = 0; pp < a.npoly; ++pp) v = fma(c[pp], Tt[pp], v);
-                    acc += (double)v;
+                    acc += ring_row((const RT *)a.mom + p * a.npad, (const RT *)a.T + t, a.npoly);
                 }
             }
     a.FH[idx] = acc;
@@ -1203,28 +1230,8 @@ struct BndArgs {
     double lw[4][8];  // Lagrange weights for g mod 4 = r (row r), 2b+2 entries
 };
 
-// Dot product of two ring-table rows of n (a multiple of 4) elements.
-__device__ __forceinline__ void ring_dot(const float *c, const float *d, int n, float &acc) {
-    const float4 *c4 = (const float4 *)c, *d4 = (const float4 *)d;
-    for (int q = 0; q < n / 4; ++q) {
-        const float4 x = c4[q], y = d4[q];
-        acc = fmaf(x.x, y.x, acc);
-        acc = fmaf(x.y, y.y, acc);
-        acc = fmaf(x.z, y.z, acc);
-        acc = fmaf(x.w, y.w, acc);
-    }
-}
-__device__ __forceinline__ void ring_dot(const double *c, const double *d, int n, double &acc) {
-    const double2 *c2 = (const double2 *)c, *d2 = (const double2 *)d;
-    for (int q = 0; q < n / 2; ++q) {
-        const double2 x = c2[q], y = d2[q];
-        acc = fma(x.x, y.x, acc);
-        acc = fma(x.y, y.y, acc);
-    }
-}
-
 // phi^B at every face-plane node (axis, plane j, u, v).  RT: precision of the
-// Legendre ring sums (FP64 tier: double; split tier: float).
+// Legendre ring sums (FP64 tier: double-float; split tier: float).
 template <typename RT>
 __global__ void __launch_bounds__(128) k_boundary(BndArgs a) {
     const long pn = (long)(a.N + 1) * (a.N + 1);
@@ -1234,10 +1241,8 @@ __global__ void __launch_bounds__(128) k_boundary(BndArgs a) {
     const int axis = (int)(idx / ((a.np + 1) * pn));
     const int j = (int)((idx / pn) % (a.np + 1));
     const int u = (int)((idx % pn) / (a.N + 1)), v = (int)(idx % (a.N + 1));
-    int g[3];
-    g[axis] = j * a.n;
-    g[axis == 0 ? 1 : 0] = u;
-    g[axis == 2 ? 1 : 2] = v;
+    const int jn = j * a.n;
+    const int g[3] = {axis == 0 ? jn : u, axis == 0 ? u : (axis == 1 ? jn : v), axis == 2 ? jn : v};
     // I^H(phi^H)(g): tensor Lagrange over the in-plane axes (R4), applied as
     // nested 1D sums (K^2 + K + 1 FMAs for two nontrivial axes)
     const int K = 2 * a.b + 2;
@@ -1271,7 +1276,7 @@ __global__ void __launch_bounds__(128) k_boundary(BndArgs a) {
     }
     // local corrections of the patches whose Omega_beta holds g (ascending index);
     // the Legendre ring terms accumulate in the ring precision RT
-    RT ring = 0;
+    RT ring(0.0);
     int lo[3], hi[3], alo[3], ahi[3];
     for (int d = 0; d < 3; ++d) {
         lo[d] = max(0, -floordiv(-(g[d] - a.n - a.gb), a.n));
@@ -1297,9 +1302,7 @@ __global__ void __launch_bounds__(128) k_boundary(BndArgs a) {
                     acc += a.resid[((p * 3 * a.npa + slot) * a.wa + (uu + a.ga)) * a.wa + (vv + a.ga)];
                 } else {
                     const int ri = a.rmap[((long)(r0 + a.gb) * a.wbx + (r1 + a.gb)) * a.wbx + (r2 + a.gb)];
-                    const RT *c = (const RT *)a.mom + p * a.npad;
-                    const RT *Dr = (const RT *)a.D + (long)ri * a.npad;
-                    ring_dot(c, Dr, a.npad, ring);
+                    ring_dot((const RT *)a.mom + p * a.npad, (const RT *)a.D + (long)ri * a.npad, a.npad, ring);
                 }
             }
     a.phiB[idx] = acc + (double)ring;
@@ -1409,7 +1412,7 @@ __global__ void __launch_bounds__(256) k_dirichlet(DirArgs a) {
             else { base = q0 * m + q1; str = m * m; }
             dfl x[m];
 #pragma unroll
-            for (int t = 0; t < m; ++t) x[t] = X[base + t * str];
+            for (int t = 0; t < m; ++t) x[t] = renorm(X[base + t * str]);
             dst_line_df<NN>(x, Sh);
             if (pass == 2) {
 #pragma unroll
@@ -1561,7 +1564,8 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
         SlabArgs a{tw, nin, W, -g.s, it, nz, {}, g.a4blk};
         for (int j = 0; j < nz; ++j) a.zrow[j] = zrow[j];
         if (LOG2M == 6) {
-            const size_t sm = (size_t)(M + M * Pitch64<R>::P + (UseXs<R>::v ? 32 * 72 : 0)) * 2 * sizeof(R);
+            if (nin > 24) return cudaErrorInvalidValue;  // k_slab64's sparse forward passes
+            const size_t sm = (size_t)(M + M * Pitch64<R>::P + 32 * 72) * sizeof(typename Cx<R>::T) + 64 * sizeof(int);
             int grid = nb * MH;
             if (it.persist) {  // one wave of resident CTAs walking all slabs
                 int dev = 0, nsm = 0, occ = 0;
@@ -1571,12 +1575,7 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
                 const int wave = nsm * (occ > 0 ? occ : 1);
                 grid = grid < wave ? grid : wave;
             }
-            if (std::is_same<R, dfl>::value) {  // FP64 tier: the slab in double-float arithmetic
-                const size_t smd = (size_t)(M + M * 65 + 32 * 72) * sizeof(dcx);
-                k_slab64_df<<<it.persist ? grid : nb * MH, 256, smd, st>>>(a);
-            } else {
-                k_slab64<R><<<grid, 256, sm, st>>>(a);
-            }
+            k_slab64<R><<<grid, 256, sm, st>>>(a);
         }
         else
             k_slab<LOG2M, R><<<nb * MH, 256, fft_smem_bytes<R>(M, M, M + 1), st>>>(a);
@@ -1643,7 +1642,6 @@ void configure_kernels() {
     set_patch_attrs<6, dfl>();
     set_patch_attrs<5, float>();
     set_patch_attrs<6, float>();
-    cudaFuncSetAttribute(k_slab64_df, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     set_coarse_attrs<5, dfl>();
     set_coarse_attrs<6, dfl>();
     set_coarse_attrs<7, dfl>();
@@ -1715,8 +1713,8 @@ cudaError_t launch_assemble(const mlc_plan_s *pl, cudaStream_t st) {
     AsmArgs a{};
     const bool split = g.tier == MLC_TIER_SPLIT;
     a.cl = pl->cl; a.FH = pl->FH;
-    a.mom = split ? (const void *)pl->mom_f : (const void *)pl->mom;
-    a.T = split ? (const void *)pl->Ttab_f : (const void *)pl->Ttab;
+    a.mom = split ? (const void *)pl->mom_f : (const void *)pl->mom_df;
+    a.T = split ? (const void *)pl->Ttab_f : (const void *)pl->Ttab_df;
     a.np = g.np; a.n = g.n; a.s = g.s; a.nc = g.nc; a.npoly = g.npoly; a.npad = g.npad; a.flo = g.flo; a.nf = g.nf;
     a.ca_lo = g.ca_lo; a.ca_hi = g.ca_hi; a.cb_lo = g.cb_lo; a.cb_hi = g.cb_hi;
     double b[4];
@@ -1725,7 +1723,7 @@ cudaError_t launch_assemble(const mlc_plan_s *pl, cudaStream_t st) {
     const long tot = (long)g.nf * g.nf * g.nf;
     const unsigned nbk = (unsigned)((tot + 127) / 128);
     if (split) k_assemble<float, float><<<nbk, 128, 0, st>>>(a);
-    else k_assemble<double, double><<<nbk, 128, 0, st>>>(a);
+    else k_assemble<double, dfl><<<nbk, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1745,8 +1743,8 @@ cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st) {
     const bool split = g.tier == MLC_TIER_SPLIT;
     BndArgs a{};
     a.phiH = pl->phiH; a.resid = pl->resid;
-    a.mom = split ? (const void *)pl->mom_f : (const void *)pl->mom;
-    a.D = split ? (const void *)pl->Dtab_f : (const void *)pl->Dtab;
+    a.mom = split ? (const void *)pl->mom_f : (const void *)pl->mom_df;
+    a.D = split ? (const void *)pl->Dtab_f : (const void *)pl->Dtab_df;
     a.rmap = pl->rmap; a.phiB = pl->phiB;
     a.N = g.N; a.n = g.n; a.np = g.np; a.ga = g.ga; a.gb = g.gb; a.b = g.b; a.npoly = g.npoly;
     a.olo = g.olo; a.no = g.no; a.wa = g.wa; a.wbx = g.wbx; a.npa = g.npa; a.pl0 = g.pl0;
@@ -1755,7 +1753,7 @@ cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st) {
     const long tot = g.n_planes_total;
     const unsigned nbk = (unsigned)((tot + 127) / 128);
     if (split) k_boundary<float><<<nbk, 128, 0, st>>>(a);
-    else k_boundary<double><<<nbk, 128, 0, st>>>(a);
+    else k_boundary<dfl><<<nbk, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -53,7 +53,8 @@ struct PlanPtrs {
     const void *momw;     // 1D moment weights a_k(m) = w_m q_k(2m/n - 1), P x (n+1), FP64
     double mom_scale;     // R^{-3/2}
     double *mom;
-    float *mom_f;
+    float *mom_f;         // split tier: FP32 copy of the moments
+    float2 *mom_df;       // FP64 tier: moments as double-float (hi, lo) pairs
     double *resid;
     const double *phiB;
     double *phi;
@@ -87,9 +88,10 @@ struct mlc_plan_s {
     double *khat;            // patch kernel spectrum octant (Mh^3), scaled by h^2/M^3
     double *khat_c;          // coarse kernel spectrum octant (Mhc^3), scaled by H^2/Mc^3
     double *momw;            // P x nb 1D moment weights (Boole weight x orthonormal Legendre)
-    int *rmap;
-    double *Dtab, *Ttab;
-    float *Dtab_f, *Ttab_f;  // split tier: FP32 copies for the Legendre ring sums
+    int *rmap;               // relative face node in Omega_beta -> ring row (-1: none)
+    // Legendre ring tables: D [ring row][npad], T [coarse cell][npoly]
+    float *Dtab_f, *Ttab_f;  // split tier: FP32
+    float2 *Dtab_df, *Ttab_df;  // FP64 tier: double-float (hi, lo) pairs
     double2 *tw, *tw_c;      // FFT twiddles exp(-2 pi i t / M), t < M/2
     float *khat_f;           // split tier: FP32 copies of the patch spectrum and twiddles
     float2 *tw_f;
@@ -105,6 +107,7 @@ struct mlc_plan_s {
     void *fpl;               // NP x 3 npa x wa^2 local fields on the face planes inside alpha
     double *mom;             // NP x npoly
     float *mom_f;            // split tier: FP32 copy of the moments
+    float2 *mom_df;          // FP64 tier: double-float copy of the moments
     double *resid;           // NP x 3 npa x wa^2 face-plane residuals
     double *FH;              // nf^3
     double2 *cbuf0, *cbuf1;  // coarse spectra

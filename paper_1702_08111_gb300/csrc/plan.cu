@@ -375,11 +375,20 @@ mlc_status build_tables(mlc_plan_s *pl) {
     }
     g.nr_face = (int)ring_nodes.size();
     TRY(dev_upload(pl, &pl->rmap, rmap));
-    TRY(dev_upload(pl, &pl->Dtab, Dtab));
-    TRY(dev_upload(pl, &pl->Ttab, Ttab));
     if (g.tier == MLC_TIER_SPLIT) {
         TRY(dev_upload(pl, &pl->Dtab_f, std::vector<float>(Dtab.begin(), Dtab.end())));
         TRY(dev_upload(pl, &pl->Ttab_f, std::vector<float>(Ttab.begin(), Ttab.end())));
+    } else {
+        auto split_df = [](const std::vector<double> &v) {
+            std::vector<float2> o(v.size());
+            for (size_t i = 0; i < v.size(); ++i) {
+                const float hi = (float)v[i];
+                o[i] = make_float2(hi, (float)(v[i] - (double)hi));
+            }
+            return o;
+        };
+        TRY(dev_upload(pl, &pl->Dtab_df, split_df(Dtab)));
+        TRY(dev_upload(pl, &pl->Ttab_df, split_df(Ttab)));
     }
 
     // FFT twiddles
@@ -567,6 +576,9 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
         if (G.tier == MLC_TIER_SPLIT) {
             TRY(dev_alloc(pl, &pl->mom_f, NP * G.npad));
             TRY_CUDA(cudaMemset(pl->mom_f, 0, NP * G.npad * sizeof(float)));
+        } else {
+            TRY(dev_alloc(pl, &pl->mom_df, NP * G.npad));
+            TRY_CUDA(cudaMemset(pl->mom_df, 0, NP * G.npad * sizeof(float2)));
         }
         const size_t nf = G.nf, no = G.no, Mc = G.Mc, Mhc = G.Mhc;
         TRY(dev_alloc(pl, &pl->FH, nf * nf * nf));
@@ -592,6 +604,7 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
         h.mom_scale = std::pow(G.R, -1.5);
         h.mom = pl->mom;
         h.mom_f = pl->mom_f;
+        h.mom_df = pl->mom_df;
         h.resid = pl->resid;
         h.phiB = pl->phiB;
         h.lam = pl->lam;
