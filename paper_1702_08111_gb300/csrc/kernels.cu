@@ -1312,7 +1312,7 @@ struct DirArgs {
     Items it;  // per item: f, phiB, phi, lam, N, np, h of its plan
     int n;
     double b[4];
-    const double *sinm;  // (n-1) x n/2: sin(pi k t / n), k in [1, n-1], t in [1, n/2]
+    const float2 *sinm;  // (n-1) x n/2: sin(pi k t / n), k in [1, n-1], t in [1, n/2], double-float
 };
 
 __device__ __forceinline__ double phiB_at(const PlanPtrs &a, int n, int g0, int g1, int g2) {
@@ -1361,47 +1361,75 @@ __device__ __forceinline__ void dst_line_df(dfl (&x)[NN - 1], const dfl *Sh) {
     for (int k = 0; k < m; ++k) x[k] = y[k];
 }
 
+// Double-float value of a charge sample (FP32 charges are exact).
+__device__ __forceinline__ dfl df_of(float v) { return {v, 0.f}; }
+__device__ __forceinline__ dfl df_of(double v) { return df_from(v); }
+
+// Local Dirichlet solve of one patch (Sec. 4, final step): the (Q-th order)
+// stencil problem on the closed patch with boundary data phi^B, by DST-I in
+// all three axes, then phi = u + (h^2/12) f.  All arithmetic between the loads
+// and the final FP64 store is double-float on the FP32 pipe (GB300 issues
+// FP64 on ~1/67 of the FP32 lanes): boundary data and, in the FP64 tier, the
+// charge are converted once on load, and one conversion per output node
+// forms the FP64 result.
 template <typename TF, int NN>
 __global__ void __launch_bounds__(256) k_dirichlet(DirArgs a) {
     extern __shared__ double sm[];
     constexpr int n = NN, nb = n + 1, m = n - 1, h = n / 2;
-    double *U = sm;                    // nb^3 boundary values (interior 0)
-    dfl *X = (dfl *)(U + nb * nb * nb);  // m^3 work, double-float
-    dfl *Sh = X + m * m * m;           // (n-1) x n/2 half sine table, double-float
+    dfl *U = (dfl *)sm;                // nb^3 boundary values (interior 0)
+    dfl *X = U + nb * nb * nb;         // m^3 work
+    dfl *Sh = X + m * m * m;           // (n-1) x n/2 half sine table
     int p;
     const PlanPtrs &PP = item_plan(a.it, blockIdx.x, p);
     const int np = PP.np, N = PP.N;
     const int i2 = p % np, i1 = (p / np) % np, i0 = p / (np * np);
     const int o0 = i0 * n, o1 = i1 * n, o2 = i2 * n;
     const TF *f = (const TF *)PP.f;
-    for (int e = threadIdx.x; e < m * h; e += blockDim.x) Sh[e] = df_from(a.sinm[e]);
+    const dfl *sinm = (const dfl *)a.sinm;
+    const dfl *lam = (const dfl *)PP.lam;
+    for (int e = threadIdx.x; e < m * h; e += blockDim.x) Sh[e] = sinm[e];
     for (int e = threadIdx.x; e < nb * nb * nb; e += blockDim.x) {
         const int m2 = e % nb, m1 = (e / nb) % nb, m0 = e / (nb * nb);
         const bool bnd = m0 == 0 || m0 == n || m1 == 0 || m1 == n || m2 == 0 || m2 == n;
-        U[e] = bnd ? phiB_at(PP, n, o0 + m0, o1 + m1, o2 + m2) : 0.0;
+        U[e] = bnd ? df_from(phiB_at(PP, n, o0 + m0, o1 + m1, o2 + m2)) : dfl(0.f, 0.f);
+    }
+    // stencil weights b_k / h^2 and h^2/12 of this plan (converted once per CTA)
+    __shared__ dfl s_w[5];
+    if (threadIdx.x < 5) {
+        double w = PP.c2h2;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)  // static indices: the parameter array stays out of local memory
+            if (threadIdx.x == k) w = a.b[k] * PP.inv_h2;
+        s_w[threadIdx.x] = df_from(w);
     }
     __syncthreads();
+    dfl cw[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cw[k] = s_w[k];
+    const dfl c2h2 = s_w[4];
     // right-hand side: f - Delta^h(boundary data); only the layer next to the
     // boundary sees boundary values
     for (int e = threadIdx.x; e < m * m * m; e += blockDim.x) {
         const int c2 = e % m + 1, c1 = (e / m) % m + 1, c0 = e / (m * m) + 1;
-        double lap = 0.0;
+        const int z = o0 + c0, y = o1 + c1, x = o2 + c2;
+        dfl v = (z < N && y < N && x < N) ? df_of(f[((long)z * N + y) * N + x]) : dfl(0.f, 0.f);
         const bool near = c0 == 1 || c0 == m || c1 == 1 || c1 == m || c2 == 1 || c2 == m;
-        if (near)
+        if (near) {
+#pragma unroll
             for (int s0 = -1; s0 <= 1; ++s0)
+#pragma unroll
                 for (int s1 = -1; s1 <= 1; ++s1)
+#pragma unroll
                     for (int s2 = -1; s2 <= 1; ++s2) {
                         const int nz = (s0 != 0) + (s1 != 0) + (s2 != 0);
-                        const double c = a.b[nz];
-                        if (c == 0.0) continue;
-                        lap = fma(c, U[((c0 + s0) * nb + (c1 + s1)) * nb + (c2 + s2)], lap);
+                        const dfl u = U[((c0 + s0) * nb + (c1 + s1)) * nb + (c2 + s2)];
+                        if (cw[nz].hi != 0.f && u.hi != 0.f) v = df_sub(v, df_mul(cw[nz], u));
                     }
-        const int z = o0 + c0, y = o1 + c1, x = o2 + c2;
-        const double fv = (z < N && y < N && x < N) ? (double)f[((long)z * N + y) * N + x] : 0.0;
-        X[e] = df_from(fma(-lap, PP.inv_h2, fv));
+        }
+        X[e] = v;
     }
     __syncthreads();
-    // DST-I along axes 2, 1, 0; divide by the eigenvalues; DST-I along 2, 1, 0
+    // DST-I along axes 2, 1, 0; scale by the inverse eigenvalues; DST-I along 2, 1, 0
     for (int pass = 0; pass < 6; ++pass) {
         const int axis = 2 - (pass % 3);
         for (int l = threadIdx.x; l < m * m; l += blockDim.x) {
@@ -1416,22 +1444,20 @@ __global__ void __launch_bounds__(256) k_dirichlet(DirArgs a) {
             dst_line_df<NN>(x, Sh);
             if (pass == 2) {
 #pragma unroll
-                for (int t = 0; t < m; ++t) x[t] = df_mul(x[t], df_from(PP.lam[base + t * str]));
+                for (int t = 0; t < m; ++t) x[t] = df_mul(x[t], lam[base + t * str]);
             }
 #pragma unroll
             for (int t = 0; t < m; ++t) X[base + t * str] = x[t];
         }
         __syncthreads();
     }
-    const double norm = (2.0 / n) * (2.0 / n) * (2.0 / n);
     for (int e = threadIdx.x; e < n * n * n; e += blockDim.x) {
         const int m2 = e % n, m1 = (e / n) % n, m0 = e / (n * n);
         const bool bnd = m0 == 0 || m1 == 0 || m2 == 0;
-        const double u = bnd ? U[(m0 * nb + m1) * nb + m2]
-                             : df_to(X[((m0 - 1) * m + (m1 - 1)) * m + (m2 - 1)]) * norm;
         const int z = o0 + m0, y = o1 + m1, x = o2 + m2;
         const long gi = ((long)z * N + y) * N + x;
-        PP.phi[gi] = u + PP.c2h2 * (double)f[gi];
+        const dfl u = bnd ? U[(m0 * nb + m1) * nb + m2] : X[((m0 - 1) * m + (m1 - 1)) * m + (m2 - 1)];
+        PP.phi[gi] = df_to(df_add(u, df_mul(c2h2, df_of(f[gi]))));
     }
 }
 
@@ -1765,7 +1791,7 @@ cudaError_t launch_dirichlet(const mlc_plan_s *pl, const Items &it, cudaStream_t
     stencil_b(g.Q, a.b);
     a.sinm = pl->sinm;
     const int nb = g.n + 1, m = g.n - 1;
-    const size_t sm = sizeof(double) * ((size_t)nb * nb * nb + (size_t)m * m * m + (size_t)m * (g.n / 2));
+    const size_t sm = sizeof(dfl) * ((size_t)nb * nb * nb + (size_t)m * m * m + (size_t)m * (g.n / 2));
 #define MLC_DIR(NN)                                                            \
     case NN:                                                                   \
         if (f32) k_dirichlet<float, NN><<<it.nitems, 256, sm, st>>>(a);        \

@@ -58,7 +58,7 @@ struct PlanPtrs {
     double *resid;
     const double *phiB;
     double *phi;
-    const double *lam;    // Dirichlet inverse eigenvalues h^2 / lambda
+    const float2 *lam;    // Dirichlet inverse eigenvalues (2/n)^3 h^2 / lambda, double-float pairs
     int N, np;
     double c2h2, inv_h2;  // h^2 / 12, 1 / h^2
     int *err;             // the plan's error word
@@ -99,8 +99,8 @@ struct mlc_plan_s {
     float4 *tw_c_df;
     float2 *khat_df;         // FP64 tier: patch spectrum and twiddles as double-float pairs
     float4 *tw_df;
-    double *sinm;            // (n-1)^2 DST-I matrix sin(pi k m / n)
-    double *lam;             // (n-1)^3 stencil eigenvalues / h^2
+    float2 *sinm;            // (n-1) x n/2 half DST-I matrix sin(pi k t / n), double-float
+    float2 *lam;             // (n-1)^3 (2/n)^3 h^2 / stencil eigenvalue, double-float
     // workspace (device)
     void *buf0, *buf1;       // ping-pong spectra for the patch convolutions (complex FP64 / FP32)
     void *cl;                // NP x nc^3 local fields on the coarse lattice of the field box

@@ -418,8 +418,19 @@ mlc_status build_tables(mlc_plan_s *pl) {
         for (int c = 0; c < m; ++c)
             for (int e = 0; e < m; ++e)
                 lam[((size_t)a * m + c) * m + e] = (g.h * g.h) / symbol(g.Q, cth[a], cth[c], cth[e]);
-    TRY(dev_upload(pl, &pl->sinm, sinm));
-    TRY(dev_upload(pl, &pl->lam, lam));
+    // as double-float pairs; the DST-I normalisation (2/n)^3 is folded into lam
+    const double dnorm = std::pow(2.0 / n, 3);
+    for (double &v : lam) v *= dnorm;
+    auto to_df = [](const std::vector<double> &v) {
+        std::vector<float2> o(v.size());
+        for (size_t i = 0; i < v.size(); ++i) {
+            const float hi = (float)v[i];
+            o[i] = make_float2(hi, (float)(v[i] - (double)hi));
+        }
+        return o;
+    };
+    TRY(dev_upload(pl, &pl->sinm, to_df(sinm)));
+    TRY(dev_upload(pl, &pl->lam, to_df(lam)));
     return MLC_OK;
 }
 
