@@ -90,6 +90,13 @@ __device__ __forceinline__ dfl operator*(dfl a, dfl b) { return df_mul(a, b); }
 __device__ __forceinline__ dfl &operator*=(dfl &a, dfl b) { return a = df_mul(a, b); }
 __device__ __forceinline__ dfl &operator+=(dfl &a, dfl b) { return a = df_add(a, b); }
 __device__ __forceinline__ dcx cmul(dcx a, dcx w) { return dc_mul(a, w); }
+// Double-float value of a stored sample: FP32 values are exact, FP64 values
+// are split (FP64 pipe), double-float values pass through.
+__device__ __forceinline__ dfl df_of(float v) { return {v, 0.f}; }
+__device__ __forceinline__ dfl df_of(double v) { return df_from(v); }
+__device__ __forceinline__ dfl df_of(dfl v) { return v; }
+// a + w x in double-float (one product, one sum)
+__device__ __forceinline__ dfl df_fma(dfl w, dfl x, dfl a) { return df_add(a, df_mul(w, x)); }
 
 // Renormalise a double-float complex value (|lo| <= ulp(hi)/2 again).  The
 // transforms do it where a line is loaded (and every other radix-2 stage), so
@@ -1054,9 +1061,14 @@ __global__ void __launch_bounds__(256) k_moments(Items it, int n, int P, int npo
 struct ResArgs {
     Items it;  // per item: cl, fp -> resid of its plan
     int n, s, ga, b, npa, pl0, wa, nc;
-    double lw[4][8];
+    dfl lw[4][8];  // Lagrange weights for g mod 4 = r (row r), double-float
 };
 
+// r^i = phi^i - I^H(phi^i) on the face planes inside Omega_alpha (one CTA per
+// patch and plane).  TB: storage of the local fields (FP32 in the split tier,
+// double-float in the FP64 tier); the interpolation and the difference, where
+// cancellation needs the extra bits, are double-float on the FP32 pipe.  The
+// residual leaves as double-float pairs.
 template <typename TB>
 __global__ void __launch_bounds__(256) k_resid(ResArgs a) {
     extern __shared__ double rsm[];
@@ -1068,44 +1080,44 @@ __global__ void __launch_bounds__(256) k_resid(ResArgs a) {
     const int klo = -a.ga / 4 - a.b;  // coarse rows the stencils reach (4 | ga, 4 | n)
     const int khi = (a.n + a.ga) / 4 + a.b;
     const int nk = khi - klo + 1;
-    double *T = rsm;                  // nk x wa: interpolated along v on coarse rows u = 4k
+    dfl *T = (dfl *)rsm;              // nk x wa: interpolated along v on coarse rows u = 4k
     const TB *cl = (const TB *)PP.cl + (long)p * nc * nc * nc;
     const TB *fp = (const TB *)PP.fp + ((long)p * gridDim.y + slot) * wa * wa;
     // phi^i at the coarse point (u, v) = (4 ka, 4 kb) of this plane
-    auto clp = [&](int ka, int kb) -> double {
+    auto clp = [&](int ka, int kb) -> dfl {
         int i0, i1, i2;
         if (axis == 0) { i0 = c4; i1 = ka; i2 = kb; }
         else if (axis == 1) { i0 = ka; i1 = c4; i2 = kb; }
         else { i0 = ka; i1 = kb; i2 = c4; }
-        return (double)cl[((long)(i0 - kl) * nc + (i1 - kl)) * nc + (i2 - kl)];
+        return df_of(cl[((long)(i0 - kl) * nc + (i1 - kl)) * nc + (i2 - kl)]);
     };
     for (int e = threadIdx.x; e < nk * wa; e += blockDim.x) {
         const int k = klo + e / wa, v = e % wa - a.ga;
         const int rv = v & 3;
-        double t;
+        dfl t;
         if (rv == 0) {
             t = clp(k, v >> 2);
         } else {
             const int k0 = (v >> 2) - a.b;
-            t = 0.0;
-            for (int j = 0; j < K; ++j) t = fma(a.lw[rv][j], clp(k, k0 + j), t);
+            t = dfl(0.f, 0.f);
+            for (int j = 0; j < K; ++j) t = df_fma(a.lw[rv][j], clp(k, k0 + j), t);
         }
         T[e] = t;
     }
     __syncthreads();
-    double *out = PP.resid + ((long)p * gridDim.y + slot) * wa * wa;
+    dfl *out = (dfl *)PP.resid + ((long)p * gridDim.y + slot) * wa * wa;
     for (int e = threadIdx.x; e < wa * wa; e += blockDim.x) {
         const int u = e / wa - a.ga, v = e % wa - a.ga;
         const int ru = u & 3;
-        double iv;
+        dfl iv;
         if (ru == 0) {
             iv = T[((u >> 2) - klo) * wa + (v + a.ga)];
         } else {
             const int k0 = (u >> 2) - a.b;
-            iv = 0.0;
-            for (int j = 0; j < K; ++j) iv = fma(a.lw[ru][j], T[(k0 + j - klo) * wa + (v + a.ga)], iv);
+            iv = dfl(0.f, 0.f);
+            for (int j = 0; j < K; ++j) iv = df_fma(a.lw[ru][j], renorm(T[(k0 + j - klo) * wa + (v + a.ga)]), iv);
         }
-        out[e] = (double)fp[e] - iv;
+        out[e] = renorm(df_sub(df_of(fp[e]), iv));
     }
 }
 
@@ -1128,15 +1140,15 @@ __device__ __forceinline__ void dot2_step(float &s, float &e, float xh, float xl
 // Ring term of one patch: dot product of two rows of n ring-table entries.
 // FP32 / FP64 rows accumulate into acc; double-float rows take the
 // compensated product.
-template <typename RT> __device__ __forceinline__ double ring_row(const RT *c, const RT *t, int n) {
+template <typename RT> __device__ __forceinline__ dfl ring_row(const RT *c, const RT *t, int n) {
     RT v = 0;
     for (int q = 0; q < n; ++q) v = fma(c[q], t[q], v);
-    return (double)v;
+    return df_of(v);
 }
-__device__ __forceinline__ double ring_row(const dfl *c, const dfl *t, int n) {
+__device__ __forceinline__ dfl ring_row(const dfl *c, const dfl *t, int n) {
     float s = 0.f, e = 0.f;
     for (int q = 0; q < n; ++q) dot2_step(s, e, c[q].hi, c[q].lo, t[q].hi, t[q].lo);
-    return (double)s + (double)e;
+    return two_sum(s, e);
 }
 
 // Dot product of two ring-table rows of n (a multiple of 4) elements, rows
@@ -1163,12 +1175,12 @@ __device__ __forceinline__ void ring_dot(const float *c, const float *d, int n, 
 }
 
 struct AsmArgs {
-    const void *cl;          // coarse lattice of the local fields, nc^3 per patch
+    const void *cl;          // coarse lattice of the local fields, nc^3 per patch (TB)
     const void *mom, *T;     // ring tables in the ring precision RT
     double *FH;
     int np, n, s, nc, npoly, npad, flo, nf;
     int ca_lo, ca_hi, cb_lo, cb_hi;
-    double coef[4];  // b_k / H^2
+    dfl coef[4];  // b_k / H^2, double-float
 };
 
 // F^H[k] = sum over patches i (ascending) of Delta^H phi^{i,h} on C(Omega_alpha(i))
@@ -1190,7 +1202,7 @@ __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
     }
     const int ncb = a.cb_hi - a.cb_lo + 1;
     const long nc = a.nc, kl = -a.s / 4;
-    double acc = 0.0;
+    dfl acc(0.f, 0.f);  // sums in double-float on the FP32 pipe
     for (int i0 = lo[0]; i0 <= hi[0]; ++i0)
         for (int i1 = lo[1]; i1 <= hi[1]; ++i1)
             for (int i2 = lo[2]; i2 <= hi[2]; ++i2) {
@@ -1200,34 +1212,34 @@ __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
                                  r1 <= a.ca_hi && r2 >= a.ca_lo && r2 <= a.ca_hi;
                 if (inA) {
                     const TB *bx = (const TB *)a.cl + p * nc * nc * nc;
-                    double lap = 0.0;
+#pragma unroll
                     for (int s0 = -1; s0 <= 1; ++s0)
+#pragma unroll
                         for (int s1 = -1; s1 <= 1; ++s1)
+#pragma unroll
                             for (int s2 = -1; s2 <= 1; ++s2) {
                                 const int nz = (s0 != 0) + (s1 != 0) + (s2 != 0);
-                                const double c = a.coef[nz];
-                                if (c == 0.0) continue;
+                                if (a.coef[nz].hi == 0.f) continue;
                                 const long x0 = r0 + s0 - kl, x1 = r1 + s1 - kl, x2 = r2 + s2 - kl;
-                                lap = fma(c, (double)bx[(x0 * nc + x1) * nc + x2], lap);
+                                acc = df_fma(a.coef[nz], df_of(bx[(x0 * nc + x1) * nc + x2]), acc);
                             }
-                    acc += lap;
                 } else {
                     const long t = (((long)(r0 - a.cb_lo) * ncb + (r1 - a.cb_lo)) * ncb +
                                     (r2 - a.cb_lo)) * a.npoly;
-                    acc += ring_row((const RT *)a.mom + p * a.npad, (const RT *)a.T + t, a.npoly);
+                    acc = df_add(acc, ring_row((const RT *)a.mom + p * a.npad, (const RT *)a.T + t, a.npoly));
                 }
             }
-    a.FH[idx] = acc;
+    a.FH[idx] = df_to(acc);
 }
 
 struct BndArgs {
-    const double *phiH, *resid;
+    const dfl *phiH, *resid;  // double-float
     const void *mom, *D;     // ring tables in the ring precision RT
     const int *rmap;
-    double *phiB;
+    dfl *phiB;        // double-float
     int N, n, np, ga, gb, b, npoly, olo, no, wa, wbx, npa, pl0;
     int npad;         // row stride of the ring tables (npoly rounded up to 4; zero padding)
-    double lw[4][8];  // Lagrange weights for g mod 4 = r (row r), 2b+2 entries
+    dfl lw[4][8];     // Lagrange weights for g mod 4 = r (row r), 2b+2 entries
 };
 
 // phi^B at every face-plane node (axis, plane j, u, v).  RT: precision of the
@@ -1257,22 +1269,22 @@ __global__ void __launch_bounds__(128) k_boundary(BndArgs a) {
             cnt[d] = K;
         }
     }
-    double acc = 0.0;
+    dfl acc(0.f, 0.f);
     for (int e0 = 0; e0 < cnt[0]; ++e0) {
-        double s1 = 0.0;
+        dfl s1(0.f, 0.f);
         for (int e1 = 0; e1 < cnt[1]; ++e1) {
-            const double *row = a.phiH + ((long)(kb[0] + e0 - a.olo) * a.no + (kb[1] + e1 - a.olo)) * a.no +
-                                (kb[2] - a.olo);
-            double s2;
+            const dfl *row = a.phiH + ((long)(kb[0] + e0 - a.olo) * a.no + (kb[1] + e1 - a.olo)) * a.no +
+                             (kb[2] - a.olo);
+            dfl s2;
             if (rr[2]) {
-                s2 = 0.0;
-                for (int e2 = 0; e2 < K; ++e2) s2 = fma(a.lw[rr[2]][e2], row[e2], s2);
+                s2 = dfl(0.f, 0.f);
+                for (int e2 = 0; e2 < K; ++e2) s2 = df_fma(a.lw[rr[2]][e2], row[e2], s2);
             } else {
                 s2 = row[0];
             }
-            s1 = rr[1] ? fma(a.lw[rr[1]][e1], s2, s1) : s2;
+            s1 = rr[1] ? df_fma(a.lw[rr[1]][e1], renorm(s2), s1) : s2;
         }
-        acc = rr[0] ? fma(a.lw[rr[0]][e0], s1, acc) : s1;
+        acc = rr[0] ? df_fma(a.lw[rr[0]][e0], renorm(s1), acc) : s1;
     }
     // local corrections of the patches whose Omega_beta holds g (ascending index);
     // the Legendre ring terms accumulate in the ring precision RT
@@ -1299,13 +1311,13 @@ __global__ void __launch_bounds__(128) k_boundary(BndArgs a) {
                     else { d = 2; uu = r0; vv = r1; }
                     const int rr = d == 0 ? r0 : (d == 1 ? r1 : r2);
                     const long slot = (long)d * a.npa + (rr - a.pl0) / a.n;
-                    acc += a.resid[((p * 3 * a.npa + slot) * a.wa + (uu + a.ga)) * a.wa + (vv + a.ga)];
+                    acc = df_add(acc, a.resid[((p * 3 * a.npa + slot) * a.wa + (uu + a.ga)) * a.wa + (vv + a.ga)]);
                 } else {
                     const int ri = a.rmap[((long)(r0 + a.gb) * a.wbx + (r1 + a.gb)) * a.wbx + (r2 + a.gb)];
                     ring_dot((const RT *)a.mom + p * a.npad, (const RT *)a.D + (long)ri * a.npad, a.npad, ring);
                 }
             }
-    a.phiB[idx] = acc + (double)ring;
+    a.phiB[idx] = renorm(df_add(acc, df_of(ring)));
 }
 
 struct DirArgs {
@@ -1315,7 +1327,7 @@ struct DirArgs {
     const float2 *sinm;  // (n-1) x n/2: sin(pi k t / n), k in [1, n-1], t in [1, n/2], double-float
 };
 
-__device__ __forceinline__ double phiB_at(const PlanPtrs &a, int n, int g0, int g1, int g2) {
+__device__ __forceinline__ dfl phiB_at(const PlanPtrs &a, int n, int g0, int g1, int g2) {
     const long pn = (long)(a.N + 1) * (a.N + 1);
     int axis, j, u, v;
     if (g0 % n == 0) {
@@ -1325,7 +1337,7 @@ __device__ __forceinline__ double phiB_at(const PlanPtrs &a, int n, int g0, int 
     } else {
         axis = 2; j = g2 / n; u = g0; v = g1;
     }
-    return a.phiB[((long)axis * (a.np + 1) + j) * pn + (long)u * (a.N + 1) + v];
+    return ((const dfl *)a.phiB)[((long)axis * (a.np + 1) + j) * pn + (long)u * (a.N + 1) + v];
 }
 
 // DST-I of one line of m = n-1 values held in registers (n a compile-time
@@ -1361,17 +1373,14 @@ __device__ __forceinline__ void dst_line_df(dfl (&x)[NN - 1], const dfl *Sh) {
     for (int k = 0; k < m; ++k) x[k] = y[k];
 }
 
-// Double-float value of a charge sample (FP32 charges are exact).
-__device__ __forceinline__ dfl df_of(float v) { return {v, 0.f}; }
-__device__ __forceinline__ dfl df_of(double v) { return df_from(v); }
 
 // Local Dirichlet solve of one patch (Sec. 4, final step): the (Q-th order)
 // stencil problem on the closed patch with boundary data phi^B, by DST-I in
 // all three axes, then phi = u + (h^2/12) f.  All arithmetic between the loads
 // and the final FP64 store is double-float on the FP32 pipe (GB300 issues
-// FP64 on ~1/67 of the FP32 lanes): boundary data and, in the FP64 tier, the
-// charge are converted once on load, and one conversion per output node
-// forms the FP64 result.
+// FP64 on ~1/67 of the FP32 lanes): the boundary data arrive as double-float,
+// the FP64 tier's charge is converted once on load, and one conversion per
+// output node forms the FP64 result.
 template <typename TF, int NN>
 __global__ void __launch_bounds__(256) k_dirichlet(DirArgs a) {
     extern __shared__ double sm[];
@@ -1391,7 +1400,7 @@ __global__ void __launch_bounds__(256) k_dirichlet(DirArgs a) {
     for (int e = threadIdx.x; e < nb * nb * nb; e += blockDim.x) {
         const int m2 = e % nb, m1 = (e / nb) % nb, m0 = e / (nb * nb);
         const bool bnd = m0 == 0 || m0 == n || m1 == 0 || m1 == n || m2 == 0 || m2 == n;
-        U[e] = bnd ? df_from(phiB_at(PP, n, o0 + m0, o1 + m1, o2 + m2)) : dfl(0.f, 0.f);
+        U[e] = bnd ? phiB_at(PP, n, o0 + m0, o1 + m1, o2 + m2) : dfl(0.f, 0.f);
     }
     // stencil weights b_k / h^2 and h^2/12 of this plan (converted once per CTA)
     __shared__ dfl s_w[5];
@@ -1474,7 +1483,7 @@ void set_coarse_attrs() {
     cudaFuncSetAttribute(k_col<LOG2M, 0, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_col<LOG2M, 1, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_col<LOG2M, 2, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_inv_x<LOG2M, R, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_inv_x<LOG2M, R, dfl>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
 // Local-convolution (patch) kernels in working precision R.
@@ -1485,8 +1494,7 @@ void set_patch_attrs() {
     cudaFuncSetAttribute(k_fwd_x<LOG2M, float, true, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_slab<LOG2M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_slab64<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    using TO = typename std::conditional<std::is_same<R, float>::value, float, double>::type;
-    cudaFuncSetAttribute(k_inv_x_pruned<LOG2M, R, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_inv_x_pruned<LOG2M, R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
 // One Hockney convolution pipeline (5 launches) for `nbatch` problems with
@@ -1559,7 +1567,7 @@ cudaError_t run_conv_t(const ConvDesc &d, cudaStream_t st) {
         InvXArgs a{d.b1, d.out, W, W, d.out_off, 0, d.tw};
         a.lines_cta = (M <= 64) ? W : 16;
         dim3 grid(d.nbatch * W, (W + a.lines_cta - 1) / a.lines_cta);
-        k_inv_x<LOG2M, R, double><<<grid, 256, fft_smem_bytes<R>(M, a.lines_cta, M + 1), st>>>(a);
+        k_inv_x<LOG2M, R, dfl><<<grid, 256, fft_smem_bytes<R>(M, a.lines_cta, M + 1), st>>>(a);  // phi^H as double-float
     }
     return cudaGetLastError();
 }
@@ -1625,9 +1633,9 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
         const int LPh = LOG2M == 6 ? Pitch64<R>::P : M + 1;
         const size_t xsn = (LOG2M == 6 && UseXs<R>::v) ? 32 * 72 : 0;
         const size_t sm = ((size_t)M + (size_t)g.a4blk + (size_t)a.maxfft * LPh + xsn) * 2 * sizeof(R);
-        // local fields leave in FP32 (split tier) or FP64 (FP64 tier)
-        using TO = typename std::conditional<std::is_same<R, float>::value, float, double>::type;
-        k_inv_x_pruned<LOG2M, R, TO><<<nb * a.nz, 256, sm, st>>>(a);
+        // local fields leave in the working precision: FP32 (split tier) or
+        // double-float pairs (FP64 tier)
+        k_inv_x_pruned<LOG2M, R, R><<<nb * a.nz, 256, sm, st>>>(a);
     }
     return cudaGetLastError();
 }
@@ -1676,7 +1684,7 @@ void configure_kernels() {
     cudaFuncSetAttribute(k_dirichlet<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_dirichlet<double, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_dirichlet<float, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_resid<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_resid<dfl>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_moments<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_moments<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_resid<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -1720,17 +1728,32 @@ void lagrange_rows(int b, double lw[4][8]) {
         }
 }
 
+// Lagrange weights as double-float pairs (host).
+void lagrange_rows_df(int b, dfl out[4][8]) {
+    double lw[4][8];
+    lagrange_rows(b, lw);
+    for (int r = 0; r < 4; ++r)
+        for (int j = 0; j < 8; ++j) {
+            const float hi = (float)lw[r][j];
+            out[r][j] = dfl(hi, (float)(lw[r][j] - (double)hi));
+        }
+}
+dfl host_df(double v) {
+    const float hi = (float)v;
+    return dfl(hi, (float)(v - (double)hi));
+}
+
 cudaError_t launch_resid(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
     const Geom &g = pl->g;
     ResArgs a{};
     a.it = it; a.n = g.n; a.s = g.s; a.ga = g.ga; a.b = g.b;
     a.npa = g.npa; a.pl0 = g.pl0; a.wa = g.wa; a.nc = g.nc;
-    lagrange_rows(g.b, a.lw);
+    lagrange_rows_df(g.b, a.lw);
     const int nk = (g.n + 2 * g.ga) / 4 + 2 * g.b + 1;
-    const size_t sm = sizeof(double) * (size_t)nk * g.wa;
+    const size_t sm = sizeof(dfl) * (size_t)nk * g.wa;
     dim3 grid(it.nitems, 3 * g.npa);
     if (g.tier == MLC_TIER_SPLIT) k_resid<float><<<grid, 256, sm, st>>>(a);
-    else k_resid<double><<<grid, 256, sm, st>>>(a);
+    else k_resid<dfl><<<grid, 256, sm, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1745,11 +1768,11 @@ cudaError_t launch_assemble(const mlc_plan_s *pl, cudaStream_t st) {
     a.ca_lo = g.ca_lo; a.ca_hi = g.ca_hi; a.cb_lo = g.cb_lo; a.cb_hi = g.cb_hi;
     double b[4];
     stencil_b(g.Q, b);
-    for (int k = 0; k < 4; ++k) a.coef[k] = b[k] / (g.H * g.H);
+    for (int k = 0; k < 4; ++k) a.coef[k] = host_df(b[k] / (g.H * g.H));
     const long tot = (long)g.nf * g.nf * g.nf;
     const unsigned nbk = (unsigned)((tot + 127) / 128);
     if (split) k_assemble<float, float><<<nbk, 128, 0, st>>>(a);
-    else k_assemble<double, dfl><<<nbk, 128, 0, st>>>(a);
+    else k_assemble<dfl, dfl><<<nbk, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1768,14 +1791,14 @@ cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st) {
     const Geom &g = pl->g;
     const bool split = g.tier == MLC_TIER_SPLIT;
     BndArgs a{};
-    a.phiH = pl->phiH; a.resid = pl->resid;
+    a.phiH = (const dfl *)pl->phiH; a.resid = (const dfl *)pl->resid;
     a.mom = split ? (const void *)pl->mom_f : (const void *)pl->mom_df;
     a.D = split ? (const void *)pl->Dtab_f : (const void *)pl->Dtab_df;
-    a.rmap = pl->rmap; a.phiB = pl->phiB;
+    a.rmap = pl->rmap; a.phiB = (dfl *)pl->phiB;
     a.N = g.N; a.n = g.n; a.np = g.np; a.ga = g.ga; a.gb = g.gb; a.b = g.b; a.npoly = g.npoly;
     a.olo = g.olo; a.no = g.no; a.wa = g.wa; a.wbx = g.wbx; a.npa = g.npa; a.pl0 = g.pl0;
     a.npad = g.npad;
-    lagrange_rows(g.b, a.lw);
+    lagrange_rows_df(g.b, a.lw);
     const long tot = g.n_planes_total;
     const unsigned nbk = (unsigned)((tot + 127) / 128);
     if (split) k_boundary<float><<<nbk, 128, 0, st>>>(a);

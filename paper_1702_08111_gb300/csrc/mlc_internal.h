@@ -55,8 +55,8 @@ struct PlanPtrs {
     double *mom;
     float *mom_f;         // split tier: FP32 copy of the moments
     float2 *mom_df;       // FP64 tier: moments as double-float (hi, lo) pairs
-    double *resid;
-    const double *phiB;
+    float2 *resid;        // face-plane residuals, double-float pairs
+    const float2 *phiB;   // boundary values on the face planes, double-float pairs
     double *phi;
     const float2 *lam;    // Dirichlet inverse eigenvalues (2/n)^3 h^2 / lambda, double-float pairs
     int N, np;
@@ -103,16 +103,16 @@ struct mlc_plan_s {
     float2 *lam;             // (n-1)^3 (2/n)^3 h^2 / stencil eigenvalue, double-float
     // workspace (device)
     void *buf0, *buf1;       // ping-pong spectra for the patch convolutions (complex FP64 / FP32)
-    void *cl;                // NP x nc^3 local fields on the coarse lattice of the field box
-    void *fpl;               // NP x 3 npa x wa^2 local fields on the face planes inside alpha
+    void *cl;                // NP x nc^3 local fields on the coarse lattice of the field box (FP32 / double-float)
+    void *fpl;               // NP x 3 npa x wa^2 local fields on the face planes inside alpha (FP32 / double-float)
     double *mom;             // NP x npoly
     float *mom_f;            // split tier: FP32 copy of the moments
     float2 *mom_df;          // FP64 tier: double-float copy of the moments
-    double *resid;           // NP x 3 npa x wa^2 face-plane residuals
+    float2 *resid;           // NP x 3 npa x wa^2 face-plane residuals (double-float)
     double *FH;              // nf^3
     double2 *cbuf0, *cbuf1;  // coarse spectra
-    double *phiH;            // no^3
-    double *phiB;            // face planes
+    float2 *phiH;            // no^3, double-float pairs
+    float2 *phiB;            // face planes, double-float pairs
     void *f_stage, *phi_stage;  // device staging for mlc_solve_host
     int *err;                // device error word: nonzero if a bounded wait in a kernel gave up
     size_t ws_bytes;

@@ -772,6 +772,13 @@ mlc_status mlc_debug_export(mlc_plan_t pl, int stage, void *host, size_t bytes) 
                               pl->g.npoly * sizeof(double), pl->g.NP, cudaMemcpyDeviceToHost));
         return MLC_OK;
     }
+    if (stage == MLC_STAGE_PHIH || stage == MLC_STAGE_PHIB) {  // double-float pairs on the device
+        std::vector<float2> tmp(bytes / sizeof(double));
+        TRY_CUDA(cudaMemcpy(tmp.data(), src, tmp.size() * sizeof(float2), cudaMemcpyDeviceToHost));
+        double *out = (double *)host;
+        for (size_t i = 0; i < tmp.size(); ++i) out[i] = (double)tmp[i].x + (double)tmp[i].y;
+        return MLC_OK;
+    }
     TRY_CUDA(cudaMemcpy(host, src, bytes, cudaMemcpyDeviceToHost));
     return MLC_OK;
 }
