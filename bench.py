@@ -223,6 +223,12 @@ def fft64_schedule_inst(tier: str, sparse: bool) -> float:
     return adds + muls + 56 * 4  # FP32: twiddle = 2 FMUL + 2 FFMA
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one slab launch,
+# from the ncu captures summarised in profiles/ (slab kernel unchanged since):
+# the A1 spectra read and the A4 spectra written, no re-reads.
+SLAB_DRAM_BYTES = {("bumps8_128", "fp64"): 508.69e6, ("bumps32_256_q6", "split"): 1.9005e9}
+
+
 def slab_rows(w, ga):
     """z rows of the field box the inverse-x step reads (Omega_alpha rows and
     coarse rows), i.e. the inverse-y lines of a slab."""
@@ -259,7 +265,8 @@ def roofline_for(w, plan, per_launch, tier):
              "instruction of the radix-8x8 %s schedule" % (nominal / inst, "FP64-equivalent" if tier == "fp64"
                                                            else "FP32", "double-float" if tier == "fp64" else "FP32"))
     return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 3),
-            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+            "traffic": SLAB_DRAM_BYTES.get((w.name, tier)),
             "launch_ms": round(per_launch[dom], 4), "flops_per_launch": flops,
             "fp32_inst_per_launch": NP * Mh * inst, "peak_basis": basis}
 
