@@ -838,6 +838,101 @@ __global__ void __launch_bounds__(256) k_slab64(SlabArgs a) {
 
 
 
+// Lane shuffles of complex values within the 8-thread line group.
+__device__ __forceinline__ float2 shfl8(float2 v, int src) {
+    return make_float2(__shfl_sync(0xffffffffu, v.x, src, 8), __shfl_sync(0xffffffffu, v.y, src, 8));
+}
+__device__ __forceinline__ dcx shfl8(dcx v, int src) {
+    dcx r;
+    r.x = dfl(__shfl_sync(0xffffffffu, v.x.hi, src, 8), __shfl_sync(0xffffffffu, v.x.lo, src, 8));
+    r.y = dfl(__shfl_sync(0xffffffffu, v.y.hi, src, 8), __shfl_sync(0xffffffffu, v.y.lo, src, 8));
+    return r;
+}
+
+// Forward real transform along x of the patch charges for M = 64 (the first
+// pass of the local convolution): one CTA per patch.  The chi-weighted
+// closed-patch charge lines (zi, yi) go in pairs as the real and imaginary
+// parts of one complex 64-point transform in an 8-thread group (radix 8 x 8 in
+// registers, sparse first butterflies: the n+1 <= 24 nonzero samples), and
+// the pair is split with X_a[k] = (Z[k] + conj Z[M-k]) / 2 and
+// X_b[k] = (Z[k] - conj Z[M-k]) / 2i; the conjugate partners come from the
+// group's lanes by shuffles.  Output A1 [p][kx][zi][yi], kx <= M/2.
+template <typename TF, typename R>
+__global__ void __launch_bounds__(256) k_fwd_x64(FwdXArgs a) {
+    using C = typename Cx<R>::T;
+    constexpr int M = 64, MH = 33;
+    __shared__ C tw64[M];
+    __shared__ C xs_all[32 * 72];
+    const int grp = threadIdx.x >> 3, t = threadIdx.x & 7, ngrp = blockDim.x >> 3;
+    int p;
+    const PlanPtrs &PP = item_plan(a.it, blockIdx.x, p);
+    const int n = a.n, nin = n + 1, N = PP.N, np = PP.np;
+    const int i2 = p % np, i1 = (p / np) % np, i0 = p / (np * np);
+    const TF *f = (const TF *)PP.f;
+    C *out = (C *)PP.a1 + (long)p * MH * nin * nin;
+    const C *tw = (const C *)a.tw;  // M/2 entries; extend by w^(j+32) = -w^j
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        C w = tw[j & 31];
+        if (j >= 32) { w.x = -w.x; w.y = -w.y; }
+        tw64[j] = w;
+    }
+    __syncthreads();
+    C wt[8];
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) wt[k1] = tw64[(t * k1) & 63];
+    C *gx = xs_all + grp * 72;
+    const C zero = Cx<R>::mk(0, 0);
+    const R half = R(0.5);
+    const int nl = nin * nin, npair = (nl + 1) / 2;
+    // chi-weighted charge of line l (= zi nin + yi) at x (nodes at index N are zero)
+    auto charge = [&](int l, int x) -> R {
+        const int zi = l / nin, yi = l - zi * nin;
+        const int z = i0 * n + zi, y = i1 * n + yi, xg = i2 * n + x;
+        if (z >= N || y >= N || xg >= N) return R(0.0);
+        R w = R((zi == 0 || zi == n) ? 0.5 : 1.0);
+        if (yi == 0 || yi == n) w = w * half;
+        if (x == 0 || x == n) w = w * half;
+        return w * R(f[((long)z * N + y) * N + xg]);
+    };
+    for (int q0 = 0; q0 < npair; q0 += ngrp) {  // uniform trip count across the CTA
+        const int q = q0 + grp;
+        const bool valid = q < npair;
+        const int la = 2 * q, lb = 2 * q + 1;
+        C v[8];
+#pragma unroll
+        for (int n2 = 0; n2 < 8; ++n2) {
+            v[n2] = zero;
+            const int x = 8 * n2 + t;
+            if (n2 < 3 && valid && x < nin) {
+                v[n2].x = charge(la, x);
+                if (lb < nl) v[n2].y = charge(lb, x);
+            }
+        }
+        line64_regs<C, R, true>(v, t, wt, false, gx);
+        // v[k2] = Z[t + 8 k2]; Z[M - k] sits in lane (8 - t) & 7, register
+        // 7 - k2 (t > 0) or (8 - k2) & 7 (t = 0)
+        C w[8];
+        const int src = (8 - t) & 7;
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) w[k2] = shfl8(v[k2], src);
+        if (!valid) continue;
+        const int zia = la / nin, yia = la - zia * nin, zib = lb / nin, yib = lb - zib * nin;
+#pragma unroll
+        for (int k2 = 0; k2 < 5; ++k2) {
+            const int kx = t + 8 * k2;
+            if (kx > M / 2) continue;
+            const C Z = v[k2], Zp = (t == 0) ? w[(8 - k2) & 7] : w[7 - k2];
+            C xa, xb;
+            xa.x = (Z.x + Zp.x) * half;
+            xa.y = (Z.y - Zp.y) * half;
+            xb.x = (Z.y + Zp.y) * half;
+            xb.y = (Zp.x - Z.x) * half;
+            out[((long)kx * nin + zia) * nin + yia] = xa;
+            if (lb < nl) out[((long)kx * nin + zib) * nin + yib] = xb;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Inverse real transform along x of the local fields, pruned to the values
 // the later steps read: the coarse lattice of the field box (for Delta^H, and
@@ -1583,10 +1678,15 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
     mark(pl, 1, st);
     {
         FwdXArgs a{nullptr, nullptr, 0, g.n, 0, nin, nin, tw, it};
-        dim3 grid(nb * nin, 1);
-        size_t sm = fft_smem_bytes<R>(M, nin, M + 1);
-        if (f32) k_fwd_x<LOG2M, float, true, R, true><<<grid, 256, sm, st>>>(a);
-        else k_fwd_x<LOG2M, double, true, R, true><<<grid, 256, sm, st>>>(a);
+        if (LOG2M == 6 && nin <= 24) {  // register transform of line pairs
+            if (f32) k_fwd_x64<float, R><<<nb, 256, 0, st>>>(a);
+            else k_fwd_x64<double, R><<<nb, 256, 0, st>>>(a);
+        } else {
+            dim3 grid(nb * nin, 1);
+            size_t sm = fft_smem_bytes<R>(M, nin, M + 1);
+            if (f32) k_fwd_x<LOG2M, float, true, R, true><<<grid, 256, sm, st>>>(a);
+            else k_fwd_x<LOG2M, double, true, R, true><<<grid, 256, sm, st>>>(a);
+        }
     }
     int nz = 0, zrow[64];
     for (int zi = 0; zi < W; ++zi) {
