@@ -1081,6 +1081,169 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
     }
 }
 
+// Pruned inverse real transform along x for M = 64 (same contract as
+// k_inv_x_pruned; local fields leave in the working precision R).  The needed
+// rows go in pairs: with A, B the Hermitian half spectra of two rows,
+// Z = A + iB transforms to a + ib, so one complex 64-point register transform
+// (radix 8 x 8, 8-thread group) yields both real rows; the Hermitian expansion
+// happens in the loads.  The per-x output classification comes from a
+// 64-entry table built once per CTA.
+template <typename R>
+__global__ void __launch_bounds__(256) k_inv_x64(InvXPArgs a) {
+    using C = typename Cx<R>::T;
+    constexpr int M = 64, MH = 33;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int rows[64];
+    __shared__ int nfft_s;
+    __shared__ unsigned wmask[2];
+    __shared__ int xflag[M], xplane[M], xcoarse[M];  // per x position: class bits, face-plane slot, coarse index
+    const int W = a.W, n = a.n, s = a.s, ga = a.ga, pl0 = a.pl0, wa = a.wa, nc = a.nc;
+    C *tw = (C *)smem_raw;        // M twiddles
+    C *raw = tw + M;              // MH x W (block of a.blk entries, 16-byte aligned)
+    C *xs = raw + a.blk;          // 32 groups x 72 exchange entries
+    constexpr int RP = 68;           // row pitch of rbuf: 4 (mod 16) keeps the group stores conflict-free
+    R *rbuf = (R *)(xs + 32 * 72);  // transformed real rows (up to maxfft rows)
+    const int jz = blockIdx.x % a.nz, zi = a.zrow[jz];
+    int p;
+    const PlanPtrs &PP = item_plan(a.it, blockIdx.x / a.nz, p);
+    const int z = zi - s;
+    const C *twg = (const C *)a.tw;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        C w = twg[j & (M / 2 - 1)];
+        if (j >= M / 2) { w.x = -w.x; w.y = -w.y; }
+        tw[j] = w;
+    }
+    const C *in = (const C *)PP.a4 + ((long)p * a.nz + jz) * a.blk;
+    // stage the contiguous block with one TMA bulk copy
+    __shared__ unsigned long long bar;
+    const unsigned bytes = (unsigned)(a.blk * sizeof(C));
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_expect_tx(&bar, bytes);
+        bulk_g2s(raw, in, bytes, &bar);
+    }
+    const int kl = -s / 4;
+    // x classification: bit 0 in the field box, 1 in alpha, 2 on a face plane, 3 coarse
+    if (threadIdx.x < M) {
+        const int pos = threadIdx.x;
+        const int x = pos <= n + s ? pos : pos - M;
+        const bool box = x >= -s && x <= n + s;
+        const bool xA = in_alpha(x, n, ga), xP = on_plane(x, n, ga, pl0), xC = (x & 3) == 0;
+        xflag[pos] = box ? (1 | (xA ? 2 : 0) | (xP ? 4 : 0) | (xC ? 8 : 0)) : 0;
+        xplane[pos] = xP ? (x - pl0) / n : 0;
+        xcoarse[pos] = (x >> 2) - kl;
+    }
+    __syncthreads();
+    const bool arrived = mbar_wait_bounded(&bar, 0);
+    if (__syncthreads_or(!arrived)) {  // uniform decision for the whole CTA
+        if (threadIdx.x == 0) {
+            atomicExch(PP.err, 1);
+            mbar_wait_bounded(&bar, 0);  // one more bounded wait for the copy in flight
+        }
+        return;
+    }
+    const bool zP = on_plane(z, n, ga, pl0), zA = in_alpha(z, n, ga), zC = (z & 3) == 0;
+    // rows of this z that need a full transform, compacted with warp ballots (W <= 64)
+    if (threadIdx.x < 64) {
+        const int yi = threadIdx.x, y = yi - s;
+        const bool yA = in_alpha(y, n, ga), yP = on_plane(y, n, ga, pl0), yC = (y & 3) == 0;
+        const bool need = yi < W && ((zP && yA) || (yP && zA) || (zC && yC));
+        const unsigned m = __ballot_sync(0xffffffffu, need);
+        if ((threadIdx.x & 31) == 0) wmask[threadIdx.x >> 5] = m;
+    }
+    __syncthreads();
+    if (threadIdx.x < 64) {
+        const int yi = threadIdx.x;
+        const unsigned m0 = wmask[0], m1 = wmask[1];
+        const unsigned mine = yi < 32 ? m0 : m1;
+        const int lane = yi & 31;
+        if ((mine >> lane) & 1u) {
+            const int before = (yi < 32 ? 0 : __popc(m0)) + __popc(mine & ((1u << lane) - 1u));
+            rows[before] = yi;
+        }
+        if (yi == 0) nfft_s = __popc(m0) + __popc(m1);
+    }
+    __syncthreads();
+    const int nfft = nfft_s, npair = (nfft + 1) / 2;
+    R *cl = (R *)PP.cl + (long)p * nc * nc * nc;
+    R *fp = (R *)PP.fp + (long)p * 3 * a.npa * wa * wa;
+    const int zc = (z >> 2) - kl, jz0 = zP ? (z - pl0) / n : 0;
+    const int grp = threadIdx.x >> 3, t = threadIdx.x & 7, ngrp = blockDim.x >> 3;
+    C *gx = xs + grp * 72;
+    C wt[8];
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) wt[k1] = tw[(t * k1) & 63];
+    const C zero = Cx<R>::mk(0, 0);
+    for (int q0 = 0; q0 < npair; q0 += ngrp) {  // uniform trip count across the CTA
+        const int q = q0 + grp;
+        const bool valid = q < npair;
+        const int ya = valid ? rows[2 * q] : 0;
+        const bool hasb = valid && 2 * q + 1 < nfft;
+        const int yb = hasb ? rows[2 * q + 1] : 0;
+        C v[8];
+#pragma unroll
+        for (int n2 = 0; n2 < 8; ++n2) {
+            const int k = 8 * n2 + t;
+            C A = zero, B = zero;
+            if (valid) {
+                if (k < MH) {
+                    A = raw[k * W + ya];
+                    if (hasb) B = raw[k * W + yb];
+                } else {
+                    A = raw[(M - k) * W + ya];
+                    A.y = -A.y;
+                    if (hasb) { B = raw[(M - k) * W + yb]; B.y = -B.y; }
+                }
+            }
+            v[n2].x = A.x - B.y;  // Z = A + i B
+            v[n2].y = A.y + B.x;
+        }
+        line64_regs<C, R, false>(v, t, wt, true, gx);
+        if (valid) {
+#pragma unroll
+            for (int k2 = 0; k2 < 8; ++k2) {
+                rbuf[(2 * q) * RP + t + 8 * k2] = v[k2].x;
+                if (hasb) rbuf[(2 * q + 1) * RP + t + 8 * k2] = v[k2].y;
+            }
+        }
+    }
+    __syncthreads();
+    // outputs of the transformed rows (consecutive x per thread: coalesced stores)
+    for (int e = threadIdx.x; e < nfft * W; e += blockDim.x) {
+        const int l = e / W, xi = e % W, yi = rows[l];
+        const int x = xi - s, y = yi - s;
+        const int pos = x & (M - 1), xf = xflag[pos];
+        const bool yA = in_alpha(y, n, ga), yP = on_plane(y, n, ga, pl0), yC = (y & 3) == 0;
+        const bool xA = xf & 2, xP = xf & 4, xC = xf & 8;
+        const bool wC = zC && yC && xC, w0 = zP && yA && xA, w1 = yP && zA && xA, w2 = zA && yA && xP;
+        if (!(wC || w0 || w1 || w2)) continue;
+        const R val = rbuf[l * RP + pos];
+        if (wC) cl[((long)zc * nc + ((y >> 2) - kl)) * nc + xcoarse[pos]] = val;
+        if (w0) fp[(((long)jz0) * wa + (y + ga)) * wa + (x + ga)] = val;
+        if (w1) fp[(((long)(a.npa + (y - pl0) / n)) * wa + (z + ga)) * wa + (x + ga)] = val;
+        if (w2) fp[(((long)(2 * a.npa + xplane[pos])) * wa + (z + ga)) * wa + (y + ga)] = val;
+    }
+    // rows that only need x on the face planes: direct sums over the half spectrum
+    if (zA) {
+        for (int e = threadIdx.x; e < W * a.npa; e += blockDim.x) {
+            const int yi = e / a.npa, j = e % a.npa;
+            const int y = yi - s;
+            const bool yA = in_alpha(y, n, ga), yP = on_plane(y, n, ga, pl0), yC = (y & 3) == 0;
+            if (!yA || zP || yP || (zC && yC)) continue;  // not needed, or done by an FFT row
+            const int x = pl0 + j * n;
+            const int pos = x & (M - 1);
+            R acc = R(0.0);
+            for (int k = 0; k < MH; ++k) {
+                const C X = raw[k * W + yi];
+                C w = tw[(k * pos) & (M - 1)];  // exp(+2 pi i k pos / M) = conj(tw)
+                const R re = X.x * w.x + X.y * w.y;
+                acc += (k == 0 || 2 * k == M) ? re : R(2.0) * re;
+            }
+            fp[(((long)(2 * a.npa + j)) * wa + (z + ga)) * wa + (y + ga)] = acc;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Legendre coefficients c_p^i = sum_m W[m] Q^p(m) f[n i + m] (Boole, R3).
 // ---------------------------------------------------------------------------
@@ -1590,6 +1753,7 @@ void set_patch_attrs() {
     cudaFuncSetAttribute(k_slab<LOG2M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_slab64<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_inv_x_pruned<LOG2M, R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_inv_x64<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
 // One Hockney convolution pipeline (5 launches) for `nbatch` problems with
@@ -1735,7 +1899,13 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
         const size_t sm = ((size_t)M + (size_t)g.a4blk + (size_t)a.maxfft * LPh + xsn) * 2 * sizeof(R);
         // local fields leave in the working precision: FP32 (split tier) or
         // double-float pairs (FP64 tier)
-        k_inv_x_pruned<LOG2M, R, R><<<nb * a.nz, 256, sm, st>>>(a);
+        if (LOG2M == 6) {
+            const size_t sm64 = ((size_t)M + (size_t)g.a4blk + 32 * 72) * sizeof(typename Cx<R>::T) +
+                                (size_t)a.maxfft * 68 * sizeof(R);
+            k_inv_x64<R><<<nb * a.nz, 256, sm64, st>>>(a);
+        } else {
+            k_inv_x_pruned<LOG2M, R, R><<<nb * a.nz, 256, sm, st>>>(a);
+        }
     }
     return cudaGetLastError();
 }
