@@ -725,7 +725,7 @@ __device__ __forceinline__ void line64_regs(C (&v)[8], int t, const C (&wt)[8], 
 // (only the z rows the inverse-x step reads are stored back); inverse y on
 // those rows only.  Requires nin <= 24.
 template <typename R>
-__global__ void __launch_bounds__(256) k_slab64(SlabArgs a) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_slab64(SlabArgs a) {
     using C = typename Cx<R>::T;
     constexpr int M = 64, MH = 33, P = Pitch64<R>::P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -750,6 +750,9 @@ __global__ void __launch_bounds__(256) k_slab64(SlabArgs a) {
     }
     const int grp = threadIdx.x >> 3, t = threadIdx.x & 7, ngrp = blockDim.x >> 3;
     C *gx = xs + grp * 72;
+    // blockDim.x steps in (row, column) of the nin x nin input and nz x W output blocks
+    const int d_in_z = blockDim.x / nin, d_in_y = blockDim.x - d_in_z * nin;
+    const int d_out_z = blockDim.x / W, d_out_y = blockDim.x - d_out_z * W;
     __syncthreads();
     C wt[8];
 #pragma unroll
@@ -762,9 +765,12 @@ __global__ void __launch_bounds__(256) k_slab64(SlabArgs a) {
         int p;
         const PlanPtrs &PP = item_plan(a.it, unit / MH, p);
         const C *in = (const C *)PP.a1 + ((long)p * MH + kx) * nin * nin;
-        for (int e = threadIdx.x; e < nin * nin; e += blockDim.x) {
-            const int zi = e / nin, yi = e % nin;
+        // (zi, yi) of element e stepped incrementally (one division per thread)
+        for (int e = threadIdx.x, zi = e / nin, yi = e - zi * nin; e < nin * nin; e += blockDim.x) {
             S[zi * P + yi] = in[e];
+            yi += d_in_y;
+            zi += d_in_z;
+            if (yi >= nin) { yi -= nin; ++zi; }
         }
         __syncthreads();
         // forward y on the nin nonzero z rows
@@ -825,18 +831,185 @@ __global__ void __launch_bounds__(256) k_slab64(SlabArgs a) {
                 if (valid) line[t + 8 * k2] = v[k2];
         }
         __syncthreads();
-        C *out = (C *)PP.a4 + (long)p * a.nz * a.blk;
-        for (int e = threadIdx.x; e < a.nz * W; e += blockDim.x) {
-            const int jz = e / W, yo = e % W;
-            int py = (a.out_off + yo) % M;
-            if (py < 0) py += M;
-            out[(long)jz * a.blk + kx * W + yo] = S[rowoff[jz] + py];
+        C *out = (C *)PP.a4 + (long)p * a.nz * a.blk + kx * W;
+        for (int e = threadIdx.x, jz = e / W, yo = e - jz * W; jz < a.nz; e += blockDim.x) {
+            out[(long)jz * a.blk + yo] = S[rowoff[jz] + ((a.out_off + yo) & (M - 1))];
+            yo += d_out_y;
+            jz += d_out_z;
+            if (yo >= W) { yo -= W; ++jz; }
         }
         __syncthreads();  // S is rewritten by the next unit
     }
 }
 
 
+
+// ---------------------------------------------------------------------------
+// Split tier slab with one 64-point line per thread: the whole transform of a
+// line sits in 64 complex registers (radix 2, fully unrolled, twiddles as
+// immediates), so a line pass costs one shared-memory load and one store per
+// point and no exchange.  Twiddles w64^k = exp(-2 pi i k / 64), k < 32, FP32
+// (cos and -sin of 2 pi k / 64 rounded to nearest); w^(k+32) = -w^k.
+// ---------------------------------------------------------------------------
+__device__ constexpr float kW64Re[32] = {
+    1.000000000e+00f, 9.951847196e-01f, 9.807852507e-01f, 9.569403529e-01f,
+    9.238795042e-01f, 8.819212914e-01f, 8.314695954e-01f, 7.730104327e-01f,
+    7.071067691e-01f, 6.343932748e-01f, 5.555702448e-01f, 4.713967443e-01f,
+    3.826834261e-01f, 2.902846634e-01f, 1.950903237e-01f, 9.801714122e-02f,
+    6.123234263e-17f, -9.801714122e-02f, -1.950903237e-01f, -2.902846634e-01f,
+    -3.826834261e-01f, -4.713967443e-01f, -5.555702448e-01f, -6.343932748e-01f,
+    -7.071067691e-01f, -7.730104327e-01f, -8.314695954e-01f, -8.819212914e-01f,
+    -9.238795042e-01f, -9.569403529e-01f, -9.807852507e-01f, -9.951847196e-01f,
+};
+__device__ constexpr float kW64Im[32] = {
+    -0.000000000e+00f, -9.801714122e-02f, -1.950903237e-01f, -2.902846634e-01f,
+    -3.826834261e-01f, -4.713967443e-01f, -5.555702448e-01f, -6.343932748e-01f,
+    -7.071067691e-01f, -7.730104327e-01f, -8.314695954e-01f, -8.819212914e-01f,
+    -9.238795042e-01f, -9.569403529e-01f, -9.807852507e-01f, -9.951847196e-01f,
+    -1.000000000e+00f, -9.951847196e-01f, -9.807852507e-01f, -9.569403529e-01f,
+    -9.238795042e-01f, -8.819212914e-01f, -8.314695954e-01f, -7.730104327e-01f,
+    -7.071067691e-01f, -6.343932748e-01f, -5.555702448e-01f, -4.713967443e-01f,
+    -3.826834261e-01f, -2.902846634e-01f, -1.950903237e-01f, -9.801714122e-02f,
+};
+
+// x * w64^k (conjugate twiddle for the inverse), k a compile-time constant
+// after unrolling: k = 0 and 16 need no multiply, 8 and 24 two.
+__device__ __forceinline__ float2 tw64_mul(float2 x, int k, bool inv) {
+    if (k == 0) return x;
+    if (k == 16) return inv ? make_float2(-x.y, x.x) : make_float2(x.y, -x.x);
+    const float wr = kW64Re[k], wi = inv ? -kW64Im[k] : kW64Im[k];
+    return make_float2(fmaf(x.x, wr, -x.y * wi), fmaf(x.x, wi, x.y * wr));
+}
+
+// One radix-2 stage of half size 2^ST over the 32 butterflies of a 64-point
+// line held in registers (one loop of 32, unrolled; all indices constant).
+template <int ST, bool INV, bool ZERO_HI>
+__device__ __forceinline__ void dif_stage64(float2 (&v)[64]) {
+    constexpr int hs = 1 << ST;
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+        const int j = b & (hs - 1), i0 = ((b >> ST) << (ST + 1)) + j, i1 = i0 + hs, k = j << (5 - ST);
+        if (ZERO_HI) {  // v[i1] is zero: the butterfly is a twiddle product
+            v[i1] = tw64_mul(v[i0], k, INV);
+        } else {
+            const float2 x = v[i0], y = v[i1];
+            v[i0] = make_float2(x.x + y.x, x.y + y.y);
+            v[i1] = tw64_mul(make_float2(x.x - y.x, x.y - y.y), k, INV);
+        }
+    }
+}
+template <int ST, bool INV>
+__device__ __forceinline__ void dit_stage64(float2 (&v)[64]) {
+    constexpr int hs = 1 << ST;
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+        const int j = b & (hs - 1), i0 = ((b >> ST) << (ST + 1)) + j, i1 = i0 + hs, k = j << (5 - ST);
+        const float2 x = v[i0], y = tw64_mul(v[i1], k, INV);
+        v[i0] = make_float2(x.x + y.x, x.y + y.y);
+        v[i1] = make_float2(x.x - y.x, x.y - y.y);
+    }
+}
+
+// Decimation in frequency, natural order in, bit-reversed out.  ZERO_HI: the
+// inputs 32..63 are zero (the forward passes over n+1 <= 32 samples), so the
+// first stage is a twiddle product only.
+template <bool INV, bool ZERO_HI>
+__device__ __forceinline__ void fft64_dif_reg(float2 (&v)[64]) {
+    dif_stage64<5, INV, ZERO_HI>(v);
+    dif_stage64<4, INV, false>(v);
+    dif_stage64<3, INV, false>(v);
+    dif_stage64<2, INV, false>(v);
+    dif_stage64<1, INV, false>(v);
+    dif_stage64<0, INV, false>(v);
+}
+
+// Decimation in time, bit-reversed order in, natural out.
+template <bool INV>
+__device__ __forceinline__ void fft64_dit_reg(float2 (&v)[64]) {
+    dit_stage64<0, INV>(v);
+    dit_stage64<1, INV>(v);
+    dit_stage64<2, INV>(v);
+    dit_stage64<3, INV>(v);
+    dit_stage64<4, INV>(v);
+    dit_stage64<5, INV>(v);
+}
+
+__host__ __device__ constexpr int brev6(int i) {
+    return ((i & 1) << 5) | ((i & 2) << 3) | ((i & 4) << 1) | ((i & 8) >> 1) | ((i & 16) >> 3) | ((i & 32) >> 5);
+}
+
+// Same contract as k_slab64<float> (64 threads: one line each).  Passes:
+// forward y on the nin nonzero z rows; per y column, forward z (bit-reversed
+// result), product with the real kernel spectrum, inverse z back to natural
+// order, all in registers, storing only the z rows read later; inverse y on
+// those rows.  Requires nin <= 32.
+__global__ void __launch_bounds__(64) k_slab64r(SlabArgs a) {
+    constexpr int M = 64, MH = 33, P = 65;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *S = (float2 *)smem_raw;  // S[z][y], pitch 65 (conflict-free rows and columns)
+    __shared__ int rowoff[64];
+    const int nin = a.nin, W = a.nout, c = threadIdx.x;
+    unsigned long long rowmask = 0;
+    for (int j = 0; j < a.nz; ++j) {
+        int pz = (a.out_off + a.zrow[j]) % M;
+        if (pz < 0) pz += M;
+        rowmask |= 1ull << pz;
+        if (threadIdx.x == 0) rowoff[j] = pz * P;
+    }
+    __syncthreads();
+    const int nunits = a.it.nitems * MH;
+    for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
+        const int kx = unit % MH;
+        int p;
+        const PlanPtrs &PP = item_plan(a.it, unit / MH, p);
+        const float2 *in = (const float2 *)PP.a1 + ((long)p * MH + kx) * nin * nin;
+        float2 v[64];
+        // forward y: thread c < nin takes z row c
+        if (c < nin) {
+#pragma unroll
+            for (int i = 0; i < 64; ++i) v[i] = (i < 32 && i < nin) ? in[c * nin + i] : make_float2(0.f, 0.f);
+            fft64_dif_reg<false, true>(v);
+#pragma unroll
+            for (int i = 0; i < 64; ++i) S[c * P + brev6(i)] = v[i];
+        }
+        __syncthreads();
+        // column ky0 = c: forward z, kernel product, inverse z
+        {
+#pragma unroll
+            for (int i = 0; i < 64; ++i) v[i] = (i < 32 && i < nin) ? S[i * P + c] : make_float2(0.f, 0.f);
+            fft64_dif_reg<false, true>(v);
+            const float *kk = (const float *)PP.khat + ((long)kx * MH + (c < M - c ? c : M - c)) * MH;
+#pragma unroll
+            for (int i = 0; i < 64; ++i) {
+                const int kz0 = brev6(i), kz = kz0 < M - kz0 ? kz0 : M - kz0;
+                const float k = kk[kz];
+                v[i].x *= k;
+                v[i].y *= k;
+            }
+            fft64_dit_reg<true>(v);
+#pragma unroll
+            for (int i = 0; i < 64; ++i)
+                if ((rowmask >> i) & 1ull) S[i * P + c] = v[i];
+        }
+        __syncthreads();
+        // inverse y on the output z rows: thread c < nz takes row rowoff[c]
+        if (c < a.nz) {
+            float2 *row = S + rowoff[c];
+#pragma unroll
+            for (int i = 0; i < 64; ++i) v[i] = row[brev6(i)];
+            fft64_dit_reg<true>(v);
+#pragma unroll
+            for (int i = 0; i < 64; ++i) row[i] = v[i];
+        }
+        __syncthreads();
+        float2 *out = (float2 *)PP.a4 + (long)p * a.nz * a.blk + kx * W;
+        for (int e = threadIdx.x; e < a.nz * W; e += blockDim.x) {
+            const int jz = e / W, yo = e - jz * W;
+            out[(long)jz * a.blk + yo] = S[rowoff[jz] + ((a.out_off + yo) & (M - 1))];
+        }
+        __syncthreads();  // S is rewritten by the next unit
+    }
+}
 
 // Lane shuffles of complex values within the 8-thread line group.
 __device__ __forceinline__ float2 shfl8(float2 v, int src) {
@@ -1093,7 +1266,7 @@ __global__ void __launch_bounds__(256) k_inv_x64(InvXPArgs a) {
     using C = typename Cx<R>::T;
     constexpr int M = 64, MH = 33;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int rows[64];
+    __shared__ int rows[64], rinfo[64];  // needed rows; their class bits (1 alpha, 2 plane, 4 coarse) | slot << 3
     __shared__ int nfft_s;
     __shared__ unsigned wmask[2];
     __shared__ int xflag[M], xplane[M], xcoarse[M];  // per x position: class bits, face-plane slot, coarse index
@@ -1159,7 +1332,10 @@ __global__ void __launch_bounds__(256) k_inv_x64(InvXPArgs a) {
         const int lane = yi & 31;
         if ((mine >> lane) & 1u) {
             const int before = (yi < 32 ? 0 : __popc(m0)) + __popc(mine & ((1u << lane) - 1u));
+            const int y = yi - s;
+            const bool yA = in_alpha(y, n, ga), yP = on_plane(y, n, ga, pl0), yC = (y & 3) == 0;
             rows[before] = yi;
+            rinfo[before] = (yA ? 1 : 0) | (yP ? 2 : 0) | (yC ? 4 : 0) | ((yP ? (y - pl0) / n : 0) << 3);
         }
         if (yi == 0) nfft_s = __popc(m0) + __popc(m1);
     }
@@ -1209,18 +1385,20 @@ __global__ void __launch_bounds__(256) k_inv_x64(InvXPArgs a) {
     }
     __syncthreads();
     // outputs of the transformed rows (consecutive x per thread: coalesced stores)
-    for (int e = threadIdx.x; e < nfft * W; e += blockDim.x) {
-        const int l = e / W, xi = e % W, yi = rows[l];
+    const int dl = blockDim.x / W, dxi = blockDim.x - dl * W;
+    for (int e = threadIdx.x, l = e / W, xi = e - l * W; l < nfft; xi += dxi, l += dl) {
+        if (xi >= W) { xi -= W; ++l; if (l >= nfft) break; }
+        const int yi = rows[l], yf = rinfo[l];
         const int x = xi - s, y = yi - s;
         const int pos = x & (M - 1), xf = xflag[pos];
-        const bool yA = in_alpha(y, n, ga), yP = on_plane(y, n, ga, pl0), yC = (y & 3) == 0;
+        const bool yA = yf & 1, yP = yf & 2, yC = yf & 4;
         const bool xA = xf & 2, xP = xf & 4, xC = xf & 8;
         const bool wC = zC && yC && xC, w0 = zP && yA && xA, w1 = yP && zA && xA, w2 = zA && yA && xP;
         if (!(wC || w0 || w1 || w2)) continue;
         const R val = rbuf[l * RP + pos];
         if (wC) cl[((long)zc * nc + ((y >> 2) - kl)) * nc + xcoarse[pos]] = val;
         if (w0) fp[(((long)jz0) * wa + (y + ga)) * wa + (x + ga)] = val;
-        if (w1) fp[(((long)(a.npa + (y - pl0) / n)) * wa + (z + ga)) * wa + (x + ga)] = val;
+        if (w1) fp[(((long)(a.npa + (yf >> 3))) * wa + (z + ga)) * wa + (x + ga)] = val;
         if (w2) fp[(((long)(2 * a.npa + xplane[pos])) * wa + (z + ga)) * wa + (y + ga)] = val;
     }
     // rows that only need x on the face planes: direct sums over the half spectrum
@@ -1752,6 +1930,7 @@ void set_patch_attrs() {
     cudaFuncSetAttribute(k_fwd_x<LOG2M, float, true, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_slab<LOG2M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_slab64<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_slab64r, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_inv_x_pruned<LOG2M, R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_inv_x64<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
@@ -1873,7 +2052,21 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
                 const int wave = nsm * (occ > 0 ? occ : 1);
                 grid = grid < wave ? grid : wave;
             }
-            k_slab64<R><<<grid, 256, sm, st>>>(a);
+            if (std::is_same<R, float>::value) {  // split tier: one line per thread
+                const size_t smr = (size_t)M * 65 * sizeof(float2);
+                int gr = nb * MH;
+                if (it.persist) {
+                    int dev = 0, nsm = 0, occ = 0;
+                    cudaGetDevice(&dev);
+                    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_slab64r, 64, smr);
+                    const int wave = nsm * (occ > 0 ? occ : 1);
+                    gr = gr < wave ? gr : wave;
+                }
+                k_slab64r<<<gr, 64, smr, st>>>(a);
+            } else {
+                k_slab64<R><<<grid, 256, sm, st>>>(a);
+            }
         }
         else
             k_slab<LOG2M, R><<<nb * MH, 256, fft_smem_bytes<R>(M, M, M + 1), st>>>(a);
