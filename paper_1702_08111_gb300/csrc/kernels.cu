@@ -1262,7 +1262,7 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
 // happens in the loads.  The per-x output classification comes from a
 // 64-entry table built once per CTA.
 template <typename R>
-__global__ void __launch_bounds__(256) k_inv_x64(InvXPArgs a) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_inv_x64(InvXPArgs a) {
     using C = typename Cx<R>::T;
     constexpr int M = 64, MH = 33;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1671,17 +1671,18 @@ __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
 struct BndArgs {
     const dfl *phiH, *resid;  // double-float
     const void *mom, *D;     // ring tables in the ring precision RT
-    const int *rmap;
     dfl *phiB;        // double-float
     int N, n, np, ga, gb, b, npoly, olo, no, wa, wbx, npa, pl0;
+    int pb0, npb;     // face planes of Omega_beta (relative): pb0 + j n, j < npb
     int npad;         // row stride of the ring tables (npoly rounded up to 4; zero padding)
     dfl lw[4][8];     // Lagrange weights for g mod 4 = r (row r), 2b+2 entries
 };
 
 // phi^B at every face-plane node (axis, plane j, u, v).  RT: precision of the
 // Legendre ring sums (FP64 tier: double-float; split tier: float).
-template <typename RT>
-__global__ void __launch_bounds__(128) k_boundary(BndArgs a) {
+template <typename RT, int NN>
+__global__ void __launch_bounds__(128, sizeof(RT) == 4 ? 8 : 6) k_boundary(BndArgs a) {
+    constexpr int n = NN;  // patch size as a constant: the index divisions become multiplies
     const long pn = (long)(a.N + 1) * (a.N + 1);
     const long tot = 3L * (a.np + 1) * pn;
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1689,7 +1690,7 @@ __global__ void __launch_bounds__(128) k_boundary(BndArgs a) {
     const int axis = (int)(idx / ((a.np + 1) * pn));
     const int j = (int)((idx / pn) % (a.np + 1));
     const int u = (int)((idx % pn) / (a.N + 1)), v = (int)(idx % (a.N + 1));
-    const int jn = j * a.n;
+    const int jn = j * n;
     const int g[3] = {axis == 0 ? jn : u, axis == 0 ? u : (axis == 1 ? jn : v), axis == 2 ? jn : v};
     // I^H(phi^H)(g): tensor Lagrange over the in-plane axes (R4), applied as
     // nested 1D sums (K^2 + K + 1 FMAs for two nontrivial axes)
@@ -1727,30 +1728,33 @@ __global__ void __launch_bounds__(128) k_boundary(BndArgs a) {
     RT ring(0.0);
     int lo[3], hi[3], alo[3], ahi[3];
     for (int d = 0; d < 3; ++d) {
-        lo[d] = max(0, -floordiv(-(g[d] - a.n - a.gb), a.n));
-        hi[d] = min(a.np - 1, floordiv(g[d] + a.gb, a.n));
-        alo[d] = max(0, -floordiv(-(g[d] - a.n - a.ga), a.n));
-        ahi[d] = min(a.np - 1, floordiv(g[d] + a.ga, a.n));
+        lo[d] = max(0, -floordiv(-(g[d] - n - a.gb), n));
+        hi[d] = min(a.np - 1, floordiv(g[d] + a.gb, n));
+        alo[d] = max(0, -floordiv(-(g[d] - n - a.ga), n));
+        ahi[d] = min(a.np - 1, floordiv(g[d] + a.ga, n));
     }
     for (int i0 = lo[0]; i0 <= hi[0]; ++i0)
         for (int i1 = lo[1]; i1 <= hi[1]; ++i1)
             for (int i2 = lo[2]; i2 <= hi[2]; ++i2) {
                 const long p = ((long)i0 * a.np + i1) * a.np + i2;
-                const int r0 = g[0] - a.n * i0, r1 = g[1] - a.n * i1, r2 = g[2] - a.n * i2;
+                const int r0 = g[0] - n * i0, r1 = g[1] - n * i1, r2 = g[2] - n * i2;
                 const bool inA = i0 >= alo[0] && i0 <= ahi[0] && i1 >= alo[1] && i1 <= ahi[1] &&
                                  i2 >= alo[2] && i2 <= ahi[2];
                 if (inA) {
                     // the residual plane holding r: first axis on a face plane
                     int d, uu, vv;
-                    if ((r0 - a.pl0) % a.n == 0) { d = 0; uu = r1; vv = r2; }
-                    else if ((r1 - a.pl0) % a.n == 0) { d = 1; uu = r0; vv = r2; }
+                    if ((r0 - a.pl0) % n == 0) { d = 0; uu = r1; vv = r2; }
+                    else if ((r1 - a.pl0) % n == 0) { d = 1; uu = r0; vv = r2; }
                     else { d = 2; uu = r0; vv = r1; }
                     const int rr = d == 0 ? r0 : (d == 1 ? r1 : r2);
-                    const long slot = (long)d * a.npa + (rr - a.pl0) / a.n;
+                    const long slot = (long)d * a.npa + (rr - a.pl0) / n;
                     acc = df_add(acc, a.resid[((p * 3 * a.npa + slot) * a.wa + (uu + a.ga)) * a.wa + (vv + a.ga)]);
                 } else {
-                    const int ri = a.rmap[((long)(r0 + a.gb) * a.wbx + (r1 + a.gb)) * a.wbx + (r2 + a.gb)];
-                    ring_dot((const RT *)a.mom + p * a.npad, (const RT *)a.D + (long)ri * a.npad, a.npad, ring);
+                    // dense ring row of (axis, plane, u, v): no index map to read
+                    const int ra = axis == 0 ? r0 : (axis == 1 ? r1 : r2);
+                    const int ru = axis == 0 ? r1 : r0, rv = axis == 2 ? r1 : r2;
+                    const long row = (((long)axis * a.npb + (ra - a.pb0) / n) * a.wbx + (ru + a.gb)) * a.wbx + (rv + a.gb);
+                    ring_dot((const RT *)a.mom + p * a.npad, (const RT *)a.D + row * a.npad, a.npad, ring);
                 }
             }
     a.phiB[idx] = renorm(df_add(acc, df_of(ring)));
@@ -1875,24 +1879,46 @@ __global__ void __launch_bounds__(256) k_dirichlet(DirArgs a) {
     }
     __syncthreads();
     // DST-I along axes 2, 1, 0; scale by the inverse eigenvalues; DST-I along 2, 1, 0
+    // Two threads per line (adjacent lanes): lane parity 0 forms the odd
+    // outputs k = 1, 3, .. from the sums x_t + x_{n-t} (and the middle node),
+    // parity 1 the even outputs from the differences x_t - x_{n-t}; both run
+    // the same instruction stream (the middle node enters with weight 0 for
+    // even k).
+    const int par = threadIdx.x & 1, ntl = blockDim.x >> 1;
     for (int pass = 0; pass < 6; ++pass) {
         const int axis = 2 - (pass % 3);
-        for (int l = threadIdx.x; l < m * m; l += blockDim.x) {
+        for (int l0 = 0; l0 < m * m; l0 += ntl) {  // uniform trip count across the CTA
+            const int l = l0 + (threadIdx.x >> 1);
+            const bool valid = l < m * m;
             const int q1 = l % m, q0 = l / m;
-            int base, str;
+            int base = 0, str = 1;
             if (axis == 2) { base = (q0 * m + q1) * m; str = 1; }
             else if (axis == 1) { base = q0 * m * m + q1; str = m; }
             else { base = q0 * m + q1; str = m * m; }
             dfl x[m];
 #pragma unroll
-            for (int t = 0; t < m; ++t) x[t] = renorm(X[base + t * str]);
-            dst_line_df<NN>(x, Sh);
-            if (pass == 2) {
+            for (int t = 0; t < m; ++t) x[t] = valid ? renorm(X[base + t * str]) : dfl(0.f, 0.f);
+            dfl u[h + 1];
 #pragma unroll
-                for (int t = 0; t < m; ++t) x[t] = df_mul(x[t], lam[base + t * str]);
+            for (int t = 1; t < h; ++t) {
+                const dfl b = x[n - t - 1];
+                u[t] = df_add(x[t - 1], par ? df_neg(b) : b);
             }
+            u[h] = par ? dfl(0.f, 0.f) : x[h - 1];
+            __syncwarp();  // both lanes of the line have read it before either writes
+            if (valid) {
 #pragma unroll
-            for (int t = 0; t < m; ++t) X[base + t * str] = x[t];
+                for (int j = 0; j < (m + 1) / 2; ++j) {
+                    const int k = 2 * j + 1 + par;  // output index 1..m
+                    if (k > m) break;
+                    const dfl *row = Sh + (k - 1) * h;
+                    dfl v = {0.f, 0.f};
+#pragma unroll
+                    for (int t = 1; t <= h; ++t) v = df_add(v, df_mul(row[t - 1], u[t]));
+                    if (pass == 2) v = df_mul(v, lam[base + (k - 1) * str]);
+                    X[base + (k - 1) * str] = v;
+                }
+            }
         }
         __syncthreads();
     }
@@ -2257,15 +2283,27 @@ cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st) {
     a.phiH = (const dfl *)pl->phiH; a.resid = (const dfl *)pl->resid;
     a.mom = split ? (const void *)pl->mom_f : (const void *)pl->mom_df;
     a.D = split ? (const void *)pl->Dtab_f : (const void *)pl->Dtab_df;
-    a.rmap = pl->rmap; a.phiB = (dfl *)pl->phiB;
+    a.phiB = (dfl *)pl->phiB;
+    a.pb0 = g.pb0; a.npb = g.npb;
     a.N = g.N; a.n = g.n; a.np = g.np; a.ga = g.ga; a.gb = g.gb; a.b = g.b; a.npoly = g.npoly;
     a.olo = g.olo; a.no = g.no; a.wa = g.wa; a.wbx = g.wbx; a.npa = g.npa; a.pl0 = g.pl0;
     a.npad = g.npad;
     lagrange_rows_df(g.b, a.lw);
     const long tot = g.n_planes_total;
     const unsigned nbk = (unsigned)((tot + 127) / 128);
-    if (split) k_boundary<float><<<nbk, 128, 0, st>>>(a);
-    else k_boundary<dfl><<<nbk, 128, 0, st>>>(a);
+#define MLC_BND(NN)                                                  \
+    case NN:                                                         \
+        if (split) k_boundary<float, NN><<<nbk, 128, 0, st>>>(a);    \
+        else k_boundary<dfl, NN><<<nbk, 128, 0, st>>>(a);            \
+        break;
+    switch (g.n) {
+        MLC_BND(4)
+        MLC_BND(8)
+        MLC_BND(12)
+        MLC_BND(16)
+        default: return cudaErrorInvalidValue;
+    }
+#undef MLC_BND
     return cudaGetLastError();
 }
 

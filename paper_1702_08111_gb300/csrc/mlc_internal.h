@@ -32,6 +32,7 @@ struct Geom {
     int S;                           // interpolation stencil size (2b+2)^2
     int wa, wbx;                     // widths of the alpha and beta boxes
     int nr_face;                     // relative face nodes in beta \ alpha
+    int pb0, npb;                    // face planes of Omega_beta per axis (relative): pb0 + j n, j < npb
     int npa, pl0;                    // face planes per axis inside Omega_alpha, first at pl0
     int nc;                          // coarse points per axis of the field box, (n + 2s)/4 + 1
     int nzr;                         // z rows of the field box the pruned inverse x reads
@@ -88,8 +89,8 @@ struct mlc_plan_s {
     double *khat;            // patch kernel spectrum octant (Mh^3), scaled by h^2/M^3
     double *khat_c;          // coarse kernel spectrum octant (Mhc^3), scaled by H^2/Mc^3
     double *momw;            // P x nb 1D moment weights (Boole weight x orthonormal Legendre)
-    int *rmap;               // relative face node in Omega_beta -> ring row (-1: none)
-    // Legendre ring tables: D [ring row][npad], T [coarse cell][npoly]
+    // Legendre ring tables: D [axis][plane][u][v][npad] (dense over the beta
+    // box face planes, zero rows off the ring), T [coarse cell][npoly]
     float *Dtab_f, *Ttab_f;  // split tier: FP32
     float2 *Dtab_df, *Ttab_df;  // FP64 tier: double-float (hi, lo) pairs
     double2 *tw, *tw_c;      // FFT twiddles exp(-2 pi i t / M), t < M/2

@@ -374,7 +374,30 @@ mlc_status build_tables(mlc_plan_s *pl) {
             }
     }
     g.nr_face = (int)ring_nodes.size();
-    TRY(dev_upload(pl, &pl->rmap, rmap));
+    // dense ring table per face-plane axis: rows [axis][plane j][u][v] (relative
+    // plane coordinate pb0 + j n, in-plane offsets u, v in [-gb, n+gb], v the
+    // faster axis), npad coefficients each; zero rows where a position is no
+    // ring node.  Consecutive v are consecutive rows and no index map is read.
+    g.pb0 = g.n * ceildiv(-g.gb, g.n);
+    g.npb = 0;
+    for (int c = g.pb0; c <= n + g.gb; c += n) ++g.npb;
+    if (ring) {
+        std::vector<double> Dd((size_t)3 * g.npb * g.wbx * g.wbx * g.npad, 0.0);
+        for (int ax = 0; ax < 3; ++ax)
+            for (int j = 0; j < g.npb; ++j)
+                for (int u = 0; u < g.wbx; ++u)
+                    for (int v = 0; v < g.wbx; ++v) {
+                        int r[3];
+                        r[ax] = g.pb0 + j * n;
+                        r[ax == 0 ? 1 : 0] = u - g.gb;
+                        r[ax == 2 ? 1 : 2] = v - g.gb;
+                        const int ri = rmap[((size_t)(r[0] + g.gb) * g.wbx + (r[1] + g.gb)) * g.wbx + (r[2] + g.gb)];
+                        if (ri < 0) continue;
+                        const size_t row = (((size_t)ax * g.npb + j) * g.wbx + u) * g.wbx + v;
+                        for (int k = 0; k < g.npad; ++k) Dd[row * g.npad + k] = Dtab[(size_t)ri * g.npad + k];
+                    }
+        Dtab.swap(Dd);
+    }
     if (g.tier == MLC_TIER_SPLIT) {
         TRY(dev_upload(pl, &pl->Dtab_f, std::vector<float>(Dtab.begin(), Dtab.end())));
         TRY(dev_upload(pl, &pl->Ttab_f, std::vector<float>(Ttab.begin(), Ttab.end())));
