@@ -169,7 +169,9 @@ def aggregate_value(points_per_rank: float, world: int, ms_max: float) -> float:
 
 def time_plan(plan, f, phi, steps, warmup, flush, stream, world, clk=None):
     """Mean device time per solve (CUDA events on the launching stream, L2
-    flushed between steps outside the timed region) and per-launch means."""
+    flushed between steps outside the timed region), then per-launch means
+    from as many further solves run with per-launch timing on (the launches in
+    sequence on one stream; not part of the timed region)."""
     import torch
     for _ in range(warmup):
         plan.solve(f, phi, stream)
@@ -177,8 +179,7 @@ def time_plan(plan, f, phi, steps, warmup, flush, stream, world, clk=None):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    plan.set_timing(True)
-    per_launch, total_ms = {}, 0.0
+    total_ms = 0.0
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     if clk is not None:
@@ -189,12 +190,18 @@ def time_plan(plan, f, phi, steps, warmup, flush, stream, world, clk=None):
         ev1.record(stream)
         ev1.synchronize()
         total_ms += ev0.elapsed_time(ev1)
-        for k, v in plan.timing().items():
-            per_launch[k] = per_launch.get(k, 0.0) + v
         flush.zero_()
     torch.cuda.synchronize()
     if clk is not None:
         clk.end()
+    plan.set_timing(True)
+    per_launch = {}
+    for _ in range(steps):
+        plan.solve(f, phi, stream)
+        for k, v in plan.timing().items():
+            per_launch[k] = per_launch.get(k, 0.0) + v
+        flush.zero_()
+    torch.cuda.synchronize()
     plan.set_timing(False)
     return total_ms / steps, {k: v / steps for k, v in per_launch.items()}
 

@@ -112,8 +112,12 @@ mlc_status mlc_plan_workspace_bytes(mlc_plan_t plan, size_t *bytes);
  * values (FP64 for MLC_TIER_FP64, FP32 for MLC_TIER_SPLIT), x = g h, axis 2
  * contiguous.  phi: device array of N^3 FP64 values, same layout; may not
  * alias f.  Work is enqueued on `stream` (a cudaStream_t; NULL = legacy
- * default stream); the call returns without synchronising.  Calls with the
- * same plan must not overlap on the GPU (they share the plan's workspace).
+ * default stream); the call returns without synchronising.  Two steps that
+ * do not depend on the local convolutions' chain (the moments, then the
+ * face-plane residuals) run on a stream the plan owns, forked from and joined
+ * back to `stream` with events, so all of the solve's work follows earlier
+ * work on `stream` and precedes later work on it.  Calls with the same plan
+ * must not overlap on the GPU (they share the plan's workspace).
  */
 mlc_status mlc_solve(mlc_plan_t plan, const void *f, void *phi, void *stream);
 
@@ -169,8 +173,8 @@ typedef enum {
 
 mlc_status mlc_debug_stage_bytes(mlc_plan_t plan, int stage, size_t *bytes);
 /* Per-launch timing of later solves with this plan: when enabled, mlc_solve
- * records a CUDA event on its stream before each of its 13 launches and after
- * the last.  mlc_debug_timing waits for the last solve's final event and
+ * runs its 13 launches in sequence on its stream (no side stream) and records
+ * a CUDA event before each launch and after the last.  mlc_debug_timing waits for the last solve's final event and
  * writes the 13 durations (ms) in launch order: moments; local convolutions:
  * forward x, fused slab (forward y and z, kernel spectrum, inverse z and y),
  * inverse x; residuals; assembly of F^H; coarse convolution x, y, z (forward,

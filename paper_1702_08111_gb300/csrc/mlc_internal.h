@@ -123,6 +123,9 @@ struct mlc_plan_s {
     // optional per-launch timing of the last solve (CUDA events on the solve stream)
     int timing = 0;
     cudaEvent_t ev[mlc::kTimedLaunches + 1] = {};
+    // side stream of a solve: moments, then residuals, beside the main chain
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork[4] = {};
 };
 
 namespace mlc {

@@ -482,6 +482,9 @@ void free_plan(mlc_plan_s *pl) {
     for (void *p : pl->owned) cudaFree(p);
     for (auto &e : pl->ev)
         if (e) cudaEventDestroy(e);
+    for (auto &e : pl->fork)
+        if (e) cudaEventDestroy(e);
+    if (pl->side) cudaStreamDestroy(pl->side);
     delete pl;
 }
 
@@ -698,6 +701,34 @@ mlc_status mlc_solve(mlc_plan_t pl, const void *f, void *phi, void *stream) {
         pl->hptrs.phi = (double *)phi;
     }
     const Items it{nullptr, pl->dptrs, pl->g.NP};
+    if (!pl->timing) {
+        // Two streams: the moments (they read only f) and, once the local
+        // fields exist, the face-plane residuals run on a side stream beside
+        // the local convolutions and the coarse-charge assembly and coarse
+        // solve; the boundary step joins both.
+        if (!pl->side) {
+            TRY_CUDA(cudaStreamCreateWithFlags(&pl->side, cudaStreamNonBlocking));
+            for (auto &e : pl->fork) TRY_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        }
+        cudaStream_t s2 = pl->side;
+        TRY_CUDA(cudaEventRecord(pl->fork[0], st));
+        TRY_CUDA(cudaStreamWaitEvent(s2, pl->fork[0], 0));
+        TRY_CUDA(launch_moments(pl, it, s2));
+        TRY_CUDA(cudaEventRecord(pl->fork[1], s2));
+        TRY_CUDA(launch_patch_conv(pl, it, st));
+        TRY_CUDA(cudaEventRecord(pl->fork[2], st));
+        TRY_CUDA(cudaStreamWaitEvent(s2, pl->fork[2], 0));
+        TRY_CUDA(launch_resid(pl, it, s2));
+        TRY_CUDA(cudaEventRecord(pl->fork[3], s2));
+        TRY_CUDA(cudaStreamWaitEvent(st, pl->fork[1], 0));
+        TRY_CUDA(launch_assemble(pl, st));
+        TRY_CUDA(launch_coarse(pl, st));
+        TRY_CUDA(cudaStreamWaitEvent(st, pl->fork[3], 0));
+        TRY_CUDA(launch_boundary(pl, st));
+        TRY_CUDA(launch_dirichlet(pl, it, st));
+        return MLC_OK;
+    }
+    // per-launch timing: the same launches in sequence on one stream
     mark(pl, 0, st);
     TRY_CUDA(launch_moments(pl, it, st));
     TRY_CUDA(launch_patch_conv(pl, it, st));       // slots 1-3
