@@ -943,7 +943,7 @@ __host__ __device__ constexpr int brev6(int i) {
 // result), product with the real kernel spectrum, inverse z back to natural
 // order, all in registers, storing only the z rows read later; inverse y on
 // those rows.  Requires nin <= 32.
-__global__ void __launch_bounds__(64) k_slab64r(SlabArgs a) {
+__global__ void __launch_bounds__(64, 6) k_slab64r(SlabArgs a) {
     constexpr int M = 64, MH = 33, P = 65;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *S = (float2 *)smem_raw;  // S[z][y], pitch 65 (conflict-free rows and columns)
@@ -1262,7 +1262,7 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
 // happens in the loads.  The per-x output classification comes from a
 // 64-entry table built once per CTA.
 template <typename R>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_inv_x64(InvXPArgs a) {
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 8 : 4) k_inv_x64(InvXPArgs a) {
     using C = typename Cx<R>::T;
     constexpr int M = 64, MH = 33;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1273,9 +1273,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_inv_x64(InvXPAr
     const int W = a.W, n = a.n, s = a.s, ga = a.ga, pl0 = a.pl0, wa = a.wa, nc = a.nc;
     C *tw = (C *)smem_raw;        // M twiddles
     C *raw = tw + M;              // MH x W (block of a.blk entries, 16-byte aligned)
-    C *xs = raw + a.blk;          // 32 groups x 72 exchange entries
+    C *xs = raw + a.blk;          // blockDim/8 groups x 72 exchange entries
     constexpr int RP = 68;           // row pitch of rbuf: 4 (mod 16) keeps the group stores conflict-free
-    R *rbuf = (R *)(xs + 32 * 72);  // transformed real rows (up to maxfft rows)
+    R *rbuf = (R *)(xs + (blockDim.x >> 3) * 72);  // transformed real rows (up to maxfft rows)
     const int jz = blockIdx.x % a.nz, zi = a.zrow[jz];
     int p;
     const PlanPtrs &PP = item_plan(a.it, blockIdx.x / a.nz, p);
@@ -2119,9 +2119,10 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
         // local fields leave in the working precision: FP32 (split tier) or
         // double-float pairs (FP64 tier)
         if (LOG2M == 6) {
-            const size_t sm64 = ((size_t)M + (size_t)g.a4blk + 32 * 72) * sizeof(typename Cx<R>::T) +
+            const int thr = 128;  // 16 line groups: one pass over the row pairs of a z row
+            const size_t sm64 = ((size_t)M + (size_t)g.a4blk + (thr / 8) * 72) * sizeof(typename Cx<R>::T) +
                                 (size_t)a.maxfft * 68 * sizeof(R);
-            k_inv_x64<R><<<nb * a.nz, 256, sm64, st>>>(a);
+            k_inv_x64<R><<<nb * a.nz, thr, sm64, st>>>(a);
         } else {
             k_inv_x_pruned<LOG2M, R, R><<<nb * a.nz, 256, sm, st>>>(a);
         }
