@@ -1825,9 +1825,15 @@ template <typename TF, int NN>
 __global__ void __launch_bounds__(256) k_dirichlet(DirArgs a) {
     extern __shared__ double sm[];
     constexpr int n = NN, nb = n + 1, m = n - 1, h = n / 2;
-    dfl *U = (dfl *)sm;                // nb^3 boundary values (interior 0)
-    dfl *X = U + nb * nb * nb;         // m^3 work
+    dfl *U = (dfl *)sm;                // boundary values on the 6 faces, nb^2 each (face 2 axis + side)
+    dfl *X = U + 6 * nb * nb;          // m^3 work
     dfl *Sh = X + m * m * m;           // (n-1) x n/2 half sine table
+    // boundary value at node (c0, c1, c2) of the closed patch, one coordinate 0 or n
+    auto Uat = [&](int c0, int c1, int c2) -> dfl {
+        if (c0 == 0 || c0 == n) return U[((c0 ? 1 : 0) * nb + c1) * nb + c2];
+        if (c1 == 0 || c1 == n) return U[((2 + (c1 ? 1 : 0)) * nb + c0) * nb + c2];
+        return U[((4 + (c2 ? 1 : 0)) * nb + c0) * nb + c1];
+    };
     int p;
     const PlanPtrs &PP = item_plan(a.it, blockIdx.x, p);
     const int np = PP.np, N = PP.N;
@@ -1837,10 +1843,14 @@ __global__ void __launch_bounds__(256) k_dirichlet(DirArgs a) {
     const dfl *sinm = (const dfl *)a.sinm;
     const dfl *lam = (const dfl *)PP.lam;
     for (int e = threadIdx.x; e < m * h; e += blockDim.x) Sh[e] = sinm[e];
-    for (int e = threadIdx.x; e < nb * nb * nb; e += blockDim.x) {
-        const int m2 = e % nb, m1 = (e / nb) % nb, m0 = e / (nb * nb);
-        const bool bnd = m0 == 0 || m0 == n || m1 == 0 || m1 == n || m2 == 0 || m2 == n;
-        U[e] = bnd ? phiB_at(PP, n, o0 + m0, o1 + m1, o2 + m2) : dfl(0.f, 0.f);
+    for (int e = threadIdx.x; e < 6 * nb * nb; e += blockDim.x) {
+        const int b = e % nb, a2 = (e / nb) % nb, fc = e / (nb * nb);  // face fc: axis fc/2, side fc%2
+        const int side = (fc & 1) ? n : 0;
+        int m0, m1, m2;
+        if (fc < 2) { m0 = side; m1 = a2; m2 = b; }
+        else if (fc < 4) { m0 = a2; m1 = side; m2 = b; }
+        else { m0 = a2; m1 = b; m2 = side; }
+        U[e] = phiB_at(PP, n, o0 + m0, o1 + m1, o2 + m2);
     }
     // stencil weights b_k / h^2 and h^2/12 of this plan (converted once per CTA)
     __shared__ dfl s_w[5];
@@ -1871,8 +1881,11 @@ __global__ void __launch_bounds__(256) k_dirichlet(DirArgs a) {
 #pragma unroll
                     for (int s2 = -1; s2 <= 1; ++s2) {
                         const int nz = (s0 != 0) + (s1 != 0) + (s2 != 0);
-                        const dfl u = U[((c0 + s0) * nb + (c1 + s1)) * nb + (c2 + s2)];
-                        if (cw[nz].hi != 0.f && u.hi != 0.f) v = df_sub(v, df_mul(cw[nz], u));
+                        const int d0 = c0 + s0, d1 = c1 + s1, d2 = c2 + s2;
+                        const bool bd = d0 == 0 || d0 == n || d1 == 0 || d1 == n || d2 == 0 || d2 == n;
+                        if (cw[nz].hi == 0.f || !bd) continue;  // interior neighbours carry no boundary data
+                        const dfl u = Uat(d0, d1, d2);
+                        if (u.hi != 0.f) v = df_sub(v, df_mul(cw[nz], u));
                     }
         }
         X[e] = v;
@@ -1927,7 +1940,7 @@ __global__ void __launch_bounds__(256) k_dirichlet(DirArgs a) {
         const bool bnd = m0 == 0 || m1 == 0 || m2 == 0;
         const int z = o0 + m0, y = o1 + m1, x = o2 + m2;
         const long gi = ((long)z * N + y) * N + x;
-        const dfl u = bnd ? U[(m0 * nb + m1) * nb + m2] : X[((m0 - 1) * m + (m1 - 1)) * m + (m2 - 1)];
+        const dfl u = bnd ? Uat(m0, m1, m2) : X[((m0 - 1) * m + (m1 - 1)) * m + (m2 - 1)];
         PP.phi[gi] = df_to(df_add(u, df_mul(c2h2, df_of(f[gi]))));
     }
 }
@@ -2316,7 +2329,7 @@ cudaError_t launch_dirichlet(const mlc_plan_s *pl, const Items &it, cudaStream_t
     stencil_b(g.Q, a.b);
     a.sinm = pl->sinm;
     const int nb = g.n + 1, m = g.n - 1;
-    const size_t sm = sizeof(dfl) * ((size_t)nb * nb * nb + (size_t)m * m * m + (size_t)m * (g.n / 2));
+    const size_t sm = sizeof(dfl) * (6 * (size_t)nb * nb + (size_t)m * m * m + (size_t)m * (g.n / 2));
 #define MLC_DIR(NN)                                                            \
     case NN:                                                                   \
         if (f32) k_dirichlet<float, NN><<<it.nitems, 256, sm, st>>>(a);        \
