@@ -1925,9 +1925,15 @@ __global__ void __launch_bounds__(256) k_dirichlet(DirArgs a) {
                     const int k = 2 * j + 1 + par;  // output index 1..m
                     if (k > m) break;
                     const dfl *row = Sh + (k - 1) * h;
-                    dfl v = {0.f, 0.f};
+                    // h products summed as a balanced tree: independent chains
+                    dfl pr[h];
 #pragma unroll
-                    for (int t = 1; t <= h; ++t) v = df_add(v, df_mul(row[t - 1], u[t]));
+                    for (int t = 1; t <= h; ++t) pr[t - 1] = df_mul(row[t - 1], u[t]);
+#pragma unroll
+                    for (int w = 1; w < h; w *= 2)
+#pragma unroll
+                        for (int t = 0; t + w < h; t += 2 * w) pr[t] = df_add(pr[t], pr[t + w]);
+                    dfl v = pr[0];
                     if (pass == 2) v = df_mul(v, lam[base + (k - 1) * str]);
                     X[base + (k - 1) * str] = v;
                 }
