@@ -348,9 +348,47 @@ def run_extra(args, flush, stream):
     out["split"]["max_rel_err_vs_closed_form"] = float(np.abs(phis["split"] - ex).max() / np.abs(ex).max())
     out["split_over_fp64_speedup"] = round(out["fp64"]["ms_per_step"] / out["split"]["ms_per_step"], 3)
     del phis
+    out["split_batched"] = run_batched_256(args, flush, stream, w)
+    out["split_batched_over_fp64_speedup"] = round(
+        out["split_batched"]["value"] / out["fp64"]["value"], 3)
     out["batch"] = run_batch(args, flush, stream)
     out["serving"] = run_serving(args)
     return out
+
+
+def run_batched_256(args, flush, stream, w, nprob=4):
+    """The split tier at 256^3 in its batched form: nprob problems of the
+    256^3 Q = 6 geometry (32 bumps each; seeds 3, 13, 23, 33) in one
+    mlc_batch_solve (shared per-patch launches, per-problem coarse steps on
+    parallel graph branches).  Mpoints/s over all problems."""
+    import torch
+    from paper_1702_08111_gb300 import mlc
+    ws = [I.Workload(w.name, w.N, w.n, w.s, w.Q, bumps=I.draw_bumps(32, 3 + 10 * k), charge_dtype="f32")
+          for k in range(nprob)]
+    plans = [mlc.Plan(x.N, x.n, x.s, x.P, x.Q, tier=mlc.MLC_TIER_SPLIT) for x in ws]
+    fs = [torch.from_numpy(x.charge()).cuda() for x in ws]
+    phis = [torch.empty((x.N,) * 3, dtype=torch.float64, device="cuda") for x in ws]
+    for _ in range(3):
+        mlc.batch_solve(plans, fs, phis, stream)
+        flush.zero_()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(3, args.steps // 2)
+    tot = 0.0
+    for _ in range(steps):
+        e0.record(stream)
+        mlc.batch_solve(plans, fs, phis, stream)
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+        flush.zero_()
+    ms = tot / steps
+    res = {"workload": f"{nprob} x bumps32_256_q6 (seeds 3, 13, 23, 33)", "problems": nprob,
+           "ms_per_batch": round(ms, 3), "ms_per_problem": round(ms / nprob, 3),
+           "value": round(nprob * float(w.N) ** 3 / (ms * 1e-3) / 1e6, 2), "unit": "Mpoints/s",
+           "batch_choice": mlc.batch_choice(plans, fs, phis)}
+    del plans, fs, phis
+    return res
 
 
 def run_batch(args, flush, stream):
