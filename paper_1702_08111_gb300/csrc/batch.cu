@@ -2,7 +2,8 @@
 // one pass.  The per-patch steps (moments, local convolutions, residuals,
 // Dirichlet solves) of all problems run in shared launches over an item table
 // of (problem, patch) pairs; the per-problem coarse steps (F^H assembly,
-// coarse solve, boundary values) run on parallel branches.  The sequence is
+// coarse solve, boundary values) run on parallel branches, the moments beside
+// the local convolutions and the residuals beside the coarse steps.  The sequence is
 // captured once as a CUDA graph per (plans, f, phi) set and replayed; the
 // number of parallel branches is picked by timing the candidates on the
 // first call (autotuning).
@@ -41,26 +42,42 @@ std::map<std::vector<uintptr_t>, BatchCtx *> g_cache;
 cudaError_t capture(BatchCtx &c, int branches, int persist, cudaGraphExec_t *out) {
     cudaStream_t cap;
     TRYE(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-    std::vector<cudaStream_t> side(branches);
-    std::vector<cudaEvent_t> ev(branches + 1);
+    std::vector<cudaStream_t> side(branches + 1);  // coarse branches, then the moments / residual stream
+    std::vector<cudaEvent_t> ev(branches + 4);
     for (auto &s : side) cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     for (auto &e : ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    cudaStream_t aux = side[branches];
+    cudaEvent_t ev_start = ev[branches], ev_mom = ev[branches + 1], ev_conv = ev[branches + 2],
+                ev_res = ev[branches + 3];
     const mlc_plan_s *rep = c.plans[0];
     Items it{c.d_items, c.d_plans, c.nitems};
     it.persist = persist;
     cudaError_t err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     g_capturing = true;
-    if (err == cudaSuccess) err = launch_moments(rep, it, cap);
+    // moments beside the local convolutions; residuals beside the coarse steps
+    if (err == cudaSuccess) err = cudaEventRecord(ev_start, cap);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(aux, ev_start, 0);
+    if (err == cudaSuccess) err = launch_moments(rep, it, aux);
+    if (err == cudaSuccess) err = cudaEventRecord(ev_mom, aux);
     if (err == cudaSuccess) err = launch_patch_conv(rep, it, cap);
-    if (err == cudaSuccess) err = launch_resid(rep, it, cap);
-    if (err == cudaSuccess) err = cudaEventRecord(ev[branches], cap);
-    for (int b = 0; b < branches && err == cudaSuccess; ++b) err = cudaStreamWaitEvent(side[b], ev[branches], 0);
+    if (err == cudaSuccess) err = cudaEventRecord(ev_conv, cap);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(aux, ev_conv, 0);
+    if (err == cudaSuccess) err = launch_resid(rep, it, aux);
+    if (err == cudaSuccess) err = cudaEventRecord(ev_res, aux);
+    for (int b = 0; b < branches && err == cudaSuccess; ++b) {
+        err = cudaStreamWaitEvent(side[b], ev_conv, 0);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(side[b], ev_mom, 0);
+    }
+    // per branch: the coarse charges and coarse solves of its problems, then
+    // (after the residuals) their boundary values
     for (size_t k = 0; k < c.plans.size() && err == cudaSuccess; ++k) {
         cudaStream_t s = side[k % branches];
         err = launch_assemble(c.plans[k], s);
         if (err == cudaSuccess) err = launch_coarse(c.plans[k], s);
-        if (err == cudaSuccess) err = launch_boundary(c.plans[k], s);
     }
+    for (int b = 0; b < branches && err == cudaSuccess; ++b) err = cudaStreamWaitEvent(side[b], ev_res, 0);
+    for (size_t k = 0; k < c.plans.size() && err == cudaSuccess; ++k)
+        err = launch_boundary(c.plans[k], side[k % branches]);
     for (int b = 0; b < branches && err == cudaSuccess; ++b) {
         err = cudaEventRecord(ev[b], side[b]);
         if (err == cudaSuccess) err = cudaStreamWaitEvent(cap, ev[b], 0);
