@@ -217,17 +217,26 @@ FP32_LANE_INST_PER_S = 152 * 128 * 2.07e9
 DF_ADD_INST, DF_MUL_INST = 8, 4
 
 
-def fft64_schedule_inst(tier: str, sparse: bool) -> float:
-    """FP32 instructions of one 64-point line in the radix-8 x 8 schedule of the
-    slab kernel: 16 radix-8 butterflies (52 real adds + 4 real multiplies each;
-    26 adds + 2 multiplies for a first-stage butterfly whose inputs 3..7 are
-    zero, `sparse`) and 56 twiddle products (7 per thread of the line group)."""
-    first = (26, 2) if sparse else (52, 4)
-    adds = 8 * first[0] + 8 * 52
-    muls = 8 * first[1] + 8 * 4
-    if tier == "fp64":  # twiddle = 4 multiplies + 2 adds, all double-float
+def fft64_schedule_inst(tier: str, sparse: bool, nin: int = 17) -> float:
+    """FP32 instructions of one 64-point line transform in the slab kernel's
+    schedule.  FP64 tier (double-float, radix 8 x 8 over an 8-thread group):
+    16 radix-8 butterflies (52 real adds + 4 real multiplies each; 26 + 2 for
+    a first-stage butterfly whose inputs 3..7 are zero, `sparse`) and 56
+    twiddle products (7 per thread).  Split tier (FP32, radix 2 in one
+    thread's registers): 6 stages of 32 butterflies (4 adds each; for inputs
+    zero from nin <= 17 on, none in the first stage and 2 in the second) and 98
+    nontrivial twiddle products (2 FMUL + 2 FFMA; twiddles 1 and -i cost
+    nothing)."""
+    if tier == "fp64":
+        first = (26, 2) if sparse else (52, 4)
+        adds = 8 * first[0] + 8 * 52
+        muls = 8 * first[1] + 8 * 4
+        # twiddle = 4 multiplies + 2 adds, all double-float
         return (adds + 56 * 2) * DF_ADD_INST + (muls + 56 * 4) * DF_MUL_INST
-    return adds + muls + 56 * 4  # FP32: twiddle = 2 FMUL + 2 FFMA
+    if not sparse:
+        return 6 * 32 * 4 + 98 * 4
+    stage2 = 2 * max(0, min(nin, 32) - 16) if nin <= 17 else 32  # butterflies with two nonzero inputs
+    return 4 * 32 * 4 + stage2 * 4 + 98 * 4
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one slab launch,
@@ -263,14 +272,15 @@ def roofline_for(w, plan, per_launch, tier):
     line_flops = 5.0 * M * np.log2(M)
     nominal = (nin + 2 * M + nz) * line_flops + 2.0 * M * M
     prod_inst = M * M * (2 * DF_MUL_INST if tier == "fp64" else 2)
-    inst = ((nin + M) * fft64_schedule_inst(tier, True) + (M + nz) * fft64_schedule_inst(tier, False)
+    inst = ((nin + M) * fft64_schedule_inst(tier, True, nin) + (M + nz) * fft64_schedule_inst(tier, False)
             + prod_inst)
     flops = NP * Mh * nominal
     achieved = flops / (per_launch[dom] * 1e-3) / 1e12
     peak = FP32_LANE_INST_PER_S * nominal / inst / 1e12
     basis = ("FP32 pipe 152 SMs x 128 lanes x 2.07 GHz = 40.27 T inst/s x %.4f nominal %s FLOP per FP32 "
-             "instruction of the radix-8x8 %s schedule" % (nominal / inst, "FP64-equivalent" if tier == "fp64"
-                                                           else "FP32", "double-float" if tier == "fp64" else "FP32"))
+             "instruction of the slab's %s schedule" % (nominal / inst, "FP64-equivalent" if tier == "fp64"
+                                                        else "FP32", "double-float radix-8x8" if tier == "fp64"
+                                                        else "FP32 radix-2 register"))
     return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 3),
             "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
             "traffic": SLAB_DRAM_BYTES.get((w.name, tier)),

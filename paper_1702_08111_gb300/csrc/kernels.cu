@@ -883,13 +883,16 @@ __device__ __forceinline__ float2 tw64_mul(float2 x, int k, bool inv) {
 
 // One radix-2 stage of half size 2^ST over the 32 butterflies of a 64-point
 // line held in registers (one loop of 32, unrolled; all indices constant).
-template <int ST, bool INV, bool ZERO_HI>
+template <int ST, bool INV, bool ZERO_HI, int NZ = 64>
 __device__ __forceinline__ void dif_stage64(float2 (&v)[64]) {
     constexpr int hs = 1 << ST;
 #pragma unroll
     for (int b = 0; b < 32; ++b) {
         const int j = b & (hs - 1), i0 = ((b >> ST) << (ST + 1)) + j, i1 = i0 + hs, k = j << (5 - ST);
-        if (ZERO_HI) {  // v[i1] is zero: the butterfly is a twiddle product
+        // v[i1] is zero: the butterfly is a twiddle product.  Stage 5 with
+        // ZERO_HI; stage 4 when the inputs at NZ..31 were zero as well (after
+        // stage 5 entry i is zero iff i mod 32 >= NZ)
+        if (ZERO_HI || (ST == 4 && NZ <= 32 && ((i1 & 31) >= NZ))) {
             v[i1] = tw64_mul(v[i0], k, INV);
         } else {
             const float2 x = v[i0], y = v[i1];
@@ -913,10 +916,10 @@ __device__ __forceinline__ void dit_stage64(float2 (&v)[64]) {
 // Decimation in frequency, natural order in, bit-reversed out.  ZERO_HI: the
 // inputs 32..63 are zero (the forward passes over n+1 <= 32 samples), so the
 // first stage is a twiddle product only.
-template <bool INV, bool ZERO_HI>
+template <bool INV, bool ZERO_HI, int NZ = 64>
 __device__ __forceinline__ void fft64_dif_reg(float2 (&v)[64]) {
     dif_stage64<5, INV, ZERO_HI>(v);
-    dif_stage64<4, INV, false>(v);
+    dif_stage64<4, INV, false, ZERO_HI ? NZ : 64>(v);
     dif_stage64<3, INV, false>(v);
     dif_stage64<2, INV, false>(v);
     dif_stage64<1, INV, false>(v);
@@ -942,7 +945,9 @@ __host__ __device__ constexpr int brev6(int i) {
 // forward y on the nin nonzero z rows; per y column, forward z (bit-reversed
 // result), product with the real kernel spectrum, inverse z back to natural
 // order, all in registers, storing only the z rows read later; inverse y on
-// those rows.  Requires nin <= 32.
+// those rows.  Requires nin <= NZ <= 32 (NZ: compile-time bound on the
+// nonzero inputs of the forward passes; their first two stages are pruned).
+template <int NZ>
 __global__ void __launch_bounds__(64, 6) k_slab64r(SlabArgs a) {
     constexpr int M = 64, MH = 33, P = 65;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -967,8 +972,8 @@ __global__ void __launch_bounds__(64, 6) k_slab64r(SlabArgs a) {
         // forward y: thread c < nin takes z row c
         if (c < nin) {
 #pragma unroll
-            for (int i = 0; i < 64; ++i) v[i] = (i < 32 && i < nin) ? in[c * nin + i] : make_float2(0.f, 0.f);
-            fft64_dif_reg<false, true>(v);
+            for (int i = 0; i < 64; ++i) v[i] = (i < NZ && i < nin) ? in[c * nin + i] : make_float2(0.f, 0.f);
+            fft64_dif_reg<false, true, NZ>(v);
 #pragma unroll
             for (int i = 0; i < 64; ++i) S[c * P + brev6(i)] = v[i];
         }
@@ -976,8 +981,8 @@ __global__ void __launch_bounds__(64, 6) k_slab64r(SlabArgs a) {
         // column ky0 = c: forward z, kernel product, inverse z
         {
 #pragma unroll
-            for (int i = 0; i < 64; ++i) v[i] = (i < 32 && i < nin) ? S[i * P + c] : make_float2(0.f, 0.f);
-            fft64_dif_reg<false, true>(v);
+            for (int i = 0; i < 64; ++i) v[i] = (i < NZ && i < nin) ? S[i * P + c] : make_float2(0.f, 0.f);
+            fft64_dif_reg<false, true, NZ>(v);
             const float *kk = (const float *)PP.khat + ((long)kx * MH + (c < M - c ? c : M - c)) * MH;
 #pragma unroll
             for (int i = 0; i < 64; ++i) {
@@ -1975,7 +1980,8 @@ void set_patch_attrs() {
     cudaFuncSetAttribute(k_fwd_x<LOG2M, float, true, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_slab<LOG2M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_slab64<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_slab64r, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_slab64r<17>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_slab64r<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_inv_x_pruned<LOG2M, R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_inv_x64<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
@@ -2104,11 +2110,12 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
                     int dev = 0, nsm = 0, occ = 0;
                     cudaGetDevice(&dev);
                     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_slab64r, 64, smr);
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_slab64r<32>, 64, smr);
                     const int wave = nsm * (occ > 0 ? occ : 1);
                     gr = gr < wave ? gr : wave;
                 }
-                k_slab64r<<<gr, 64, smr, st>>>(a);
+                if (nin <= 17) k_slab64r<17><<<gr, 64, smr, st>>>(a);
+                else k_slab64r<32><<<gr, 64, smr, st>>>(a);
             } else {
                 k_slab64<R><<<grid, 256, sm, st>>>(a);
             }
