@@ -1819,6 +1819,85 @@ __device__ __forceinline__ void dst_line_df(dfl (&x)[NN - 1], const dfl *Sh) {
 }
 
 
+// sin(pi m / 16) for integer m as (index into sv[0..8] = sin(pi i / 16), sign),
+// resolved at compile time.
+__host__ __device__ constexpr int sin16_idx(int m) {
+    return ((m % 32 + 32) % 32) % 16 <= 8 ? ((m % 32 + 32) % 32) % 16 : 16 - ((m % 32 + 32) % 32) % 16;
+}
+__host__ __device__ constexpr bool sin16_neg(int m) { return ((m % 32 + 32) % 32) >= 16; }
+template <int M16>
+__device__ __forceinline__ dfl mul_sin16(dfl v, const dfl (&sv)[9]) {
+    const dfl r = df_mul(v, sv[sin16_idx(M16)]);
+    return sin16_neg(M16) ? df_neg(r) : r;
+}
+
+// DST-I of 15 values (n = 16) in double-float, y_k = sum_t x_t sin(pi k t / 16),
+// by symmetric splitting: with s_t = x_t + x_{16-t} and d_t = x_t - x_{16-t},
+// the even outputs are the length-7 DST-I of d (split once more into
+// e_t = d_t - d_{8-t}, f_t = d_t + d_{8-t}), and the odd outputs pair up as
+// y_{2j+1} = P_j + Q_j + (-1)^j x_8, y_{15-2j} = P_j - Q_j - (-1)^j x_8 with
+// P_j, Q_j the sums of s_t sin(pi (2j+1) t / 16) over odd and even t (using
+// sin(pi (16 - k) t / 16) = -(-1)^t sin(pi k t / 16)).  29 products and 68
+// sums instead of 105 and 98 for the direct sums.  x[t-1] = x_t in, y_k out.
+__device__ __forceinline__ void dst15_fast(dfl (&x)[15], const dfl (&sv)[9]) {
+    dfl sp[8], dm[8];
+#pragma unroll
+    for (int t = 1; t < 8; ++t) {
+        sp[t] = df_add(x[t - 1], x[15 - t]);
+        dm[t] = df_sub(x[t - 1], x[15 - t]);
+    }
+    const dfl x8 = x[7];
+    dfl y[16];
+    // even outputs
+    {
+        dfl e[4], f[4];
+#pragma unroll
+        for (int t = 1; t < 4; ++t) {
+            e[t] = df_sub(dm[t], dm[8 - t]);
+            f[t] = df_add(dm[t], dm[8 - t]);
+        }
+        const dfl d4 = dm[4];
+        const dfl ec = mul_sin16<4>(df_add(e[1], e[3]), sv);
+        y[4] = df_add(ec, e[2]);
+        y[8] = df_sub(e[1], e[3]);
+        y[12] = df_sub(ec, e[2]);
+        // kk = 0: sin(pi t / 8) -> m = 2t; kk = 1: sin(3 pi t / 8) -> m = 6t
+        const dfl po0 = df_add(mul_sin16<2>(f[1], sv), mul_sin16<6>(f[3], sv));
+        const dfl qe0 = mul_sin16<4>(f[2], sv);
+        const dfl po1 = df_add(mul_sin16<6>(f[1], sv), mul_sin16<18>(f[3], sv));
+        const dfl qe1 = mul_sin16<12>(f[2], sv);
+        y[2] = df_add(df_add(po0, qe0), d4);
+        y[14] = df_sub(df_sub(po0, qe0), d4);   // kk' = 3: (-1)^3
+        y[6] = df_sub(df_add(po1, qe1), d4);    // kk = 1
+        y[10] = df_add(df_sub(po1, qe1), d4);   // kk' = 2
+    }
+    // odd outputs
+    {
+        const dfl qo0 = df_add(mul_sin16<2>(sp[2], sv), mul_sin16<6>(sp[6], sv));
+        const dfl qe0 = mul_sin16<4>(sp[4], sv);
+        const dfl qo1 = df_add(mul_sin16<6>(sp[2], sv), mul_sin16<18>(sp[6], sv));
+        const dfl qe1 = mul_sin16<12>(sp[4], sv);
+        const dfl Q[4] = {df_add(qo0, qe0), df_add(qo1, qe1), df_sub(qo1, qe1), df_sub(qo0, qe0)};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int k = 2 * j + 1;
+            dfl p1, p3, p5, p7;
+            switch (j) {  // compile-time after unrolling
+                case 0: p1 = mul_sin16<1>(sp[1], sv); p3 = mul_sin16<3>(sp[3], sv); p5 = mul_sin16<5>(sp[5], sv); p7 = mul_sin16<7>(sp[7], sv); break;
+                case 1: p1 = mul_sin16<3>(sp[1], sv); p3 = mul_sin16<9>(sp[3], sv); p5 = mul_sin16<15>(sp[5], sv); p7 = mul_sin16<21>(sp[7], sv); break;
+                case 2: p1 = mul_sin16<5>(sp[1], sv); p3 = mul_sin16<15>(sp[3], sv); p5 = mul_sin16<25>(sp[5], sv); p7 = mul_sin16<35>(sp[7], sv); break;
+                default: p1 = mul_sin16<7>(sp[1], sv); p3 = mul_sin16<21>(sp[3], sv); p5 = mul_sin16<35>(sp[5], sv); p7 = mul_sin16<49>(sp[7], sv); break;
+            }
+            const dfl Pj = df_add(df_add(p1, p3), df_add(p5, p7));
+            const dfl xs = (j & 1) ? df_neg(x8) : x8;
+            y[k] = df_add(df_add(Pj, Q[j]), xs);
+            y[15 - 2 * j] = df_sub(df_sub(Pj, Q[j]), xs);
+        }
+    }
+#pragma unroll
+    for (int k = 1; k < 16; ++k) x[k - 1] = y[k];
+}
+
 // Local Dirichlet solve of one patch (Sec. 4, final step): the (Q-th order)
 // stencil problem on the closed patch with boundary data phi^B, by DST-I in
 // all three axes, then phi = u + (h^2/12) f.  All arithmetic between the loads
@@ -1827,7 +1906,7 @@ __device__ __forceinline__ void dst_line_df(dfl (&x)[NN - 1], const dfl *Sh) {
 // the FP64 tier's charge is converted once on load, and one conversion per
 // output node forms the FP64 result.
 template <typename TF, int NN>
-__global__ void __launch_bounds__(256) k_dirichlet(DirArgs a) {
+__global__ void __launch_bounds__(256, 4) k_dirichlet(DirArgs a) {
     extern __shared__ double sm[];
     constexpr int n = NN, nb = n + 1, m = n - 1, h = n / 2;
     dfl *U = (dfl *)sm;                // boundary values on the 6 faces, nb^2 each (face 2 axis + side)
@@ -1902,6 +1981,34 @@ __global__ void __launch_bounds__(256) k_dirichlet(DirArgs a) {
     // parity 1 the even outputs from the differences x_t - x_{n-t}; both run
     // the same instruction stream (the middle node enters with weight 0 for
     // even k).
+    if constexpr (NN == 16) {
+        // n = 16: one thread per line with the split-radix DST (dst15_fast)
+        dfl sv[9];
+        sv[0] = dfl(0.f, 0.f);
+#pragma unroll
+        for (int i = 1; i <= 8; ++i) sv[i] = Sh[i - 1];  // sin(pi i / 16)
+        for (int pass = 0; pass < 6; ++pass) {
+            const int axis = 2 - (pass % 3);
+            for (int l = threadIdx.x; l < m * m; l += blockDim.x) {
+                const int q1 = l % m, q0 = l / m;
+                int base, str;
+                if (axis == 2) { base = (q0 * m + q1) * m; str = 1; }
+                else if (axis == 1) { base = q0 * m * m + q1; str = m; }
+                else { base = q0 * m + q1; str = m * m; }
+                dfl x[15];
+#pragma unroll
+                for (int t = 0; t < 15; ++t) x[t] = renorm(X[base + t * str]);
+                dst15_fast(x, sv);
+                if (pass == 2) {
+#pragma unroll
+                    for (int t = 0; t < 15; ++t) x[t] = df_mul(x[t], lam[base + t * str]);
+                }
+#pragma unroll
+                for (int t = 0; t < 15; ++t) X[base + t * str] = x[t];
+            }
+            __syncthreads();
+        }
+    } else {
     const int par = threadIdx.x & 1, ntl = blockDim.x >> 1;
     for (int pass = 0; pass < 6; ++pass) {
         const int axis = 2 - (pass % 3);
@@ -1945,6 +2052,7 @@ __global__ void __launch_bounds__(256) k_dirichlet(DirArgs a) {
             }
         }
         __syncthreads();
+    }
     }
     for (int e = threadIdx.x; e < n * n * n; e += blockDim.x) {
         const int m2 = e % n, m1 = (e / n) % n, m0 = e / (n * n);
