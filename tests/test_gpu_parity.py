@@ -141,6 +141,36 @@ def test_variants(torch_cuda, G4, G6, kw):
     _compare(res, prm, f, G4 if kw["Q"] == 4 else G6)
 
 
+@pytest.mark.parametrize("kw", [
+    dict(N=32, n=8, s=8, P=4, Q=4),
+    dict(N=128, n=16, s=16, P=4, Q=4),
+    dict(N=256, n=16, s=16, P=4, Q=6),
+    dict(N=40, n=8, s=12, P=3, Q=6, b=2),
+    dict(N=32, n=8, s=16, P=4, Q=4, mode=1),
+])
+def test_plan_geometry_matches_oracle(torch_cuda, kw):
+    # patch decomposition and coarse extents, integer for integer (Sec. 4:
+    # g_alpha = s - C b, g_beta = ceil((beta - 1) n / 2), F^H on the union of
+    # C(Omega_beta), phi^H on [-b, N/4 + b], Hockney length M >= 2 (n + s))
+    from paper_1702_08111_gb300 import mlc
+    kw = dict(kw)
+    mode = kw.pop("mode", 0)
+    b = kw.get("b", None)
+    plan = mlc.Plan(**kw, mode=mode)
+    info = plan.info
+    prm = O.Params(N=kw["N"], n=kw["n"], s=kw["s"], P=kw["P"], Q=kw["Q"], b=b,
+                   mode="mlc0" if mode else "mlc")
+    assert (info.N, info.n, info.s, info.b) == (prm.N, prm.n, prm.s, prm.b)
+    assert (info.g_alpha, info.g_beta) == (prm.g_alpha, prm.g_beta)
+    assert (info.fh_lo, info.fh_hi) == tuple(prm.fh_extent)
+    assert (info.phih_lo, info.phih_hi) == tuple(prm.phih_extent)
+    assert info.npoly == prm.P * (prm.P + 1) * (prm.P + 2) // 6  # |p|_1 <= P - 1 in 3D
+    M = 1
+    while M < 2 * (prm.n + prm.s):
+        M *= 2
+    assert info.M == M
+
+
 def test_zero_charge_gives_zero(torch_cuda):
     from paper_1702_08111_gb300 import mlc
     torch = torch_cuda
