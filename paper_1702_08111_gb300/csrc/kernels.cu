@@ -696,11 +696,13 @@ __device__ __forceinline__ void dft8_in3(C (&v)[8], bool inv) {
 // exit layout is the entry layout of the next transform of the same line, so
 // a forward transform, a pointwise product and an inverse transform chain in
 // registers.  SPARSE: v[3..7] are zero on entry.  Double-float inputs are
-// renormalised first.
-template <typename C, typename R, bool SPARSE>
+// renormalised first unless RENORM is false.
+template <typename C, typename R, bool SPARSE, bool RENORM = true>
 __device__ __forceinline__ void line64_regs(C (&v)[8], int t, const C (&wt)[8], bool inv, C *xs) {
+    if (RENORM) {
 #pragma unroll
-    for (int n2 = 0; n2 < (SPARSE ? 3 : 8); ++n2) v[n2] = renorm(v[n2]);
+        for (int n2 = 0; n2 < (SPARSE ? 3 : 8); ++n2) v[n2] = renorm(v[n2]);
+    }
     if (SPARSE) dft8_in3<C, R>(v, inv);
     else dft8<C, R>(v, inv);
 #pragma unroll
@@ -809,7 +811,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_slab64(SlabArgs
                 v[k2].x *= k;
                 v[k2].y *= k;
             }
-            line64_regs<C, R, false>(v, t, wt, true, gx);
+            // the kernel products are nearly normalised already (residual ~2^-24 |p|)
+            line64_regs<C, R, false, false>(v, t, wt, true, gx);
 #pragma unroll
             for (int k2 = 0; k2 < 8; ++k2) {
                 const int z = t + 8 * k2;
