@@ -43,7 +43,6 @@ struct dfl {
     dfl() = default;
     __host__ __device__ constexpr dfl(float h, float l) : hi(h), lo(l) {}
     __device__ explicit dfl(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
-    __device__ explicit operator double() const { return (double)hi + (double)lo; }
 };
 struct dcx {
     dfl x, y;
@@ -105,14 +104,9 @@ __device__ __forceinline__ dfl df_fma(dfl w, dfl x, dfl a) { return df_add(a, df
 __device__ __forceinline__ dfl renorm(dfl v) { return fast_two_sum(v.hi, v.lo); }
 __device__ __forceinline__ dcx renorm(dcx v) { return {fast_two_sum(v.x.hi, v.x.lo), fast_two_sum(v.y.hi, v.y.lo)}; }
 __device__ __forceinline__ float2 renorm(float2 v) { return v; }
-__device__ __forceinline__ double2 renorm(double2 v) { return v; }
 
-// Complex type of each working precision (FP64 tier: double; split tier: float).
+// Complex type of each working precision (FP64 tier: double-float; split tier: float).
 template <typename R> struct Cx;
-template <> struct Cx<double> {
-    using T = double2;
-    static __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
-};
 template <> struct Cx<float> {
     using T = float2;
     static __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
@@ -122,9 +116,6 @@ template <> struct Cx<dfl> {  // double-float complex
     static __device__ __forceinline__ dcx mk(float a, float b) { return dcx{dfl(a, 0.f), dfl(b, 0.f)}; }
 };
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 w) {
-    return make_double2(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x));
-}
 __device__ __forceinline__ float2 cmul(float2 a, float2 w) {
     return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
 }
@@ -720,8 +711,9 @@ __device__ __forceinline__ void line64_regs(C (&v)[8], int t, const C (&wt)[8], 
     dft8<C, R>(v, inv);
 }
 
-// Fused slab for M = 64 (same contract as k_slab): R = float (split tier) or
-// dfl (FP64 tier, double-float arithmetic on FP64 data).  The slab is S[z][y]
+// Fused slab for M = 64 (same contract as k_slab), radix 8 x 8 over 8-thread
+// line groups: the FP64 tier runs it with R = dfl (double-float arithmetic on
+// FP64 data); the split tier uses k_slab64r instead.  The slab is S[z][y]
 // (row pitch P).  Passes: forward y on the nin nonzero z rows; per y column,
 // forward z, product with the real kernel spectrum and inverse z in registers
 // (only the z rows the inverse-x step reads are stored back); inverse y on
@@ -944,7 +936,7 @@ __host__ __device__ constexpr int brev6(int i) {
     return ((i & 1) << 5) | ((i & 2) << 3) | ((i & 4) << 1) | ((i & 8) >> 1) | ((i & 16) >> 3) | ((i & 32) >> 5);
 }
 
-// Same contract as k_slab64<float> (64 threads: one line each).  Passes:
+// Same contract as k_slab64, for the split tier (FP32; 64 threads: one line each).  Passes:
 // forward y on the nin nonzero z rows; per y column, forward z (bit-reversed
 // result), product with the real kernel spectrum, inverse z back to natural
 // order, all in registers, storing only the z rows read later; inverse y on
@@ -2090,7 +2082,8 @@ void set_patch_attrs() {
     cudaFuncSetAttribute(k_fwd_x<LOG2M, double, true, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_fwd_x<LOG2M, float, true, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_slab<LOG2M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_slab64<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if constexpr (!std::is_same<R, float>::value)
+        cudaFuncSetAttribute(k_slab64<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_slab64r<17>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_slab64r<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_inv_x_pruned<LOG2M, R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -2204,30 +2197,29 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
         for (int j = 0; j < nz; ++j) a.zrow[j] = zrow[j];
         if (LOG2M == 6) {
             if (nin > 24) return cudaErrorInvalidValue;  // k_slab64's sparse forward passes
-            const size_t sm = (size_t)(M + M * Pitch64<R>::P + 32 * 72) * sizeof(typename Cx<R>::T) + 64 * sizeof(int);
-            int grid = nb * MH;
+            int dev = 0, nsm = 0, occ = 0;
             if (it.persist) {  // one wave of resident CTAs walking all slabs
-                int dev = 0, nsm = 0, occ = 0;
                 cudaGetDevice(&dev);
                 cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_slab64<R>, 256, sm);
-                const int wave = nsm * (occ > 0 ? occ : 1);
-                grid = grid < wave ? grid : wave;
             }
-            if (std::is_same<R, float>::value) {  // split tier: one line per thread
+            if constexpr (std::is_same<R, float>::value) {  // split tier: one line per thread
                 const size_t smr = (size_t)M * 65 * sizeof(float2);
                 int gr = nb * MH;
                 if (it.persist) {
-                    int dev = 0, nsm = 0, occ = 0;
-                    cudaGetDevice(&dev);
-                    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
                     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_slab64r<32>, 64, smr);
                     const int wave = nsm * (occ > 0 ? occ : 1);
                     gr = gr < wave ? gr : wave;
                 }
                 if (nin <= 17) k_slab64r<17><<<gr, 64, smr, st>>>(a);
                 else k_slab64r<32><<<gr, 64, smr, st>>>(a);
-            } else {
+            } else {  // FP64 tier: double-float radix-8 x 8 over 8-thread groups
+                const size_t sm = (size_t)(M + M * Pitch64<R>::P + 32 * 72) * sizeof(typename Cx<R>::T) + 64 * sizeof(int);
+                int grid = nb * MH;
+                if (it.persist) {
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_slab64<R>, 256, sm);
+                    const int wave = nsm * (occ > 0 ? occ : 1);
+                    grid = grid < wave ? grid : wave;
+                }
                 k_slab64<R><<<grid, 256, sm, st>>>(a);
             }
         }
