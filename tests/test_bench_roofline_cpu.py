@@ -1,0 +1,64 @@
+"""The roofline arithmetic of bench.py, recounted by enumerating the slab
+kernels' transform schedules (host logic only; no GPU)."""
+import importlib.util
+import os
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _radix2_fp32_count(nin=None):
+    """FP32 instructions of a 64-point radix-2 line transform, counted butterfly
+    by butterfly: 4 adds per butterfly with two live inputs, 4 instructions per
+    twiddle other than 1 and -i.  nin: inputs nin..63 are zero (forward passes)."""
+    live = np.ones(64, bool) if nin is None else np.arange(64) < nin
+    inst = 0
+    for st in range(5, -1, -1):  # decimation in frequency, half size 2^st
+        hs = 1 << st
+        new = live.copy()
+        for g in range(0, 64, 2 * hs):
+            for j in range(hs):
+                i0, i1 = g + j, g + j + hs
+                k = j << (5 - st)
+                if live[i0] and live[i1]:
+                    inst += 4
+                if k not in (0, 16):
+                    inst += 4
+                new[i0] = new[i1] = live[i0] or live[i1]
+        live = new
+    return inst
+
+
+def test_split_schedule_counts_match_enumeration():
+    b = _bench()
+    assert b.fft64_schedule_inst("split", False) == _radix2_fp32_count()
+    assert b.fft64_schedule_inst("split", True, 17) == _radix2_fp32_count(17)
+
+
+def test_fp64_schedule_counts():
+    # radix 8 x 8: 16 butterflies of 52 adds + 4 multiplies, 56 twiddle
+    # products (4 multiplies + 2 adds); double-float add = 8, multiply = 4
+    b = _bench()
+    adds, muls = 16 * 52 + 56 * 2, 16 * 4 + 56 * 4
+    assert b.fft64_schedule_inst("fp64", False) == adds * 8 + muls * 4
+    adds_s, muls_s = 8 * 26 + 8 * 52 + 56 * 2, 8 * 2 + 8 * 4 + 56 * 4
+    assert b.fft64_schedule_inst("fp64", True) == adds_s * 8 + muls_s * 4
+
+
+def test_slab_rows_and_fp32_peak():
+    b = _bench()
+
+    class W:
+        n, s = 16, 16
+    # z rows of the field box read later: Omega_alpha rows plus coarse rows
+    assert b.slab_rows(W, 8) == 37   # Q = 4, g_alpha = 8
+    assert b.slab_rows(W, 4) == 31   # Q = 6, g_alpha = 4
+    assert abs(b.FP32_LANE_INST_PER_S - 152 * 128 * 2.07e9) < 1.0
