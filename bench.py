@@ -557,10 +557,13 @@ def main():
         line = {
             "metric": METRIC, "value": round(r["value"], 3), "unit": "Mpoints/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r["ms"], 4),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32x2",
             "data": "synthetic",
             "config": {"workload": args.workload, "N": w.N, "patch": w.n, "support": w.s, "Q": w.Q,
-                       "P": w.P, "tier": "fp64", "l2": "flushed between steps (512 MB write)",
+                       "P": w.P, "tier": "fp64",
+                       "arithmetic": "double-float (pairs of f32, ~48-bit significand) on the FP32 pipe; "
+                                     "f64 in the moments, the plan tables and the f/phi conversions",
+                       "l2": "flushed between steps (512 MB write)",
                        "parallelism": f"independent problem per GPU x{world}"},
             "max_rel_err_vs_oracle": err,
             "e2e": {"value": round(e2e_val, 3), "unit": "Mpoints/s",
