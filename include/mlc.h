@@ -44,11 +44,21 @@ typedef enum {
     MLC_ERR_TIMEOUT = 6      /* server: wait timed out / request cancelled */
 } mlc_status;
 
+/* Arithmetic of a plan.  "Double-float" is an unevaluated sum hi + lo of two
+ * FP32 numbers (about 48 significand bits, FP32's exponent range) computed on
+ * the FP32 pipe; GB300 issues FP64 on about 1/67 of its FP32 lanes. */
 typedef enum {
-    MLC_TIER_FP64 = 0,   /* every step in FP64 */
-    MLC_TIER_SPLIT = 1   /* charge FP32; local convolutions in split precision on the
-                            tensor cores with FP32 accumulation; coarse solve, boundary
-                            values and Dirichlet solves in FP64 */
+    MLC_TIER_FP64 = 0,     /* FP64 charge and result; every step in FP64 arithmetic on
+                              the FP64 pipe (the plain FP64 solve)                        */
+    MLC_TIER_SPLIT = 1,    /* FP32 charge; local convolutions (FFTs on the CUDA cores) and
+                              the Legendre ring sums in FP32, the moments in FP32 with an
+                              FP64 last contraction; coarse charge, coarse solve, boundary
+                              values (subtract, interpolate, accumulate) and Dirichlet
+                              solves in FP64; FP64 result                                 */
+    MLC_TIER_DF = 2,       /* FP64 charge and result; moments in FP64, every other step in
+                              double-float arithmetic                                     */
+    MLC_TIER_SPLIT_DF = 3  /* as MLC_TIER_SPLIT with double-float in place of FP64 in the
+                              steps after the local convolutions                          */
 } mlc_tier;
 
 typedef enum {

@@ -89,11 +89,6 @@ __device__ __forceinline__ dfl operator*(dfl a, dfl b) { return df_mul(a, b); }
 __device__ __forceinline__ dfl &operator*=(dfl &a, dfl b) { return a = df_mul(a, b); }
 __device__ __forceinline__ dfl &operator+=(dfl &a, dfl b) { return a = df_add(a, b); }
 __device__ __forceinline__ dcx cmul(dcx a, dcx w) { return dc_mul(a, w); }
-// Double-float value of a stored sample: FP32 values are exact, FP64 values
-// are split (FP64 pipe), double-float values pass through.
-__device__ __forceinline__ dfl df_of(float v) { return {v, 0.f}; }
-__device__ __forceinline__ dfl df_of(double v) { return df_from(v); }
-__device__ __forceinline__ dfl df_of(dfl v) { return v; }
 // a + w x in double-float (one product, one sum)
 __device__ __forceinline__ dfl df_fma(dfl w, dfl x, dfl a) { return df_add(a, df_mul(w, x)); }
 
@@ -104,6 +99,7 @@ __device__ __forceinline__ dfl df_fma(dfl w, dfl x, dfl a) { return df_add(a, df
 __device__ __forceinline__ dfl renorm(dfl v) { return fast_two_sum(v.hi, v.lo); }
 __device__ __forceinline__ dcx renorm(dcx v) { return {fast_two_sum(v.x.hi, v.x.lo), fast_two_sum(v.y.hi, v.y.lo)}; }
 __device__ __forceinline__ float2 renorm(float2 v) { return v; }
+__device__ __forceinline__ double2 renorm(double2 v) { return v; }
 
 // Complex type of each working precision (FP64 tier: double-float; split tier: float).
 template <typename R> struct Cx;
@@ -115,10 +111,42 @@ template <> struct Cx<dfl> {  // double-float complex
     using T = dcx;
     static __device__ __forceinline__ dcx mk(float a, float b) { return dcx{dfl(a, 0.f), dfl(b, 0.f)}; }
 };
+template <> struct Cx<double> {  // FP64 complex
+    using T = double2;
+    static __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+};
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 w) {
     return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
 }
+__device__ __forceinline__ double2 cmul(double2 a, double2 w) {
+    return make_double2(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x));
+}
+
+// Arithmetic of the steps after the local convolutions ("fine" precision):
+// FP64 (the FP64 pipe) or double-float (the FP32 pipe).  Both store 8 bytes
+// per value, so the arrays between these steps have one layout.
+template <typename T> struct FT;
+template <> struct FT<dfl> {
+    static __device__ __forceinline__ dfl of(float v) { return {v, 0.f}; }
+    static __device__ __forceinline__ dfl of(double v) { return df_from(v); }
+    static __device__ __forceinline__ dfl of(dfl v) { return v; }
+    static __device__ __forceinline__ double to(dfl v) { return df_to(v); }
+    static __device__ __forceinline__ dfl rn(dfl v) { return renorm(v); }
+    static __device__ __forceinline__ dfl zero() { return {0.f, 0.f}; }
+    static __device__ __forceinline__ bool is0(dfl v) { return v.hi == 0.f; }
+    static __device__ __forceinline__ dfl fma(dfl w, dfl x, dfl a) { return df_fma(w, x, a); }
+};
+template <> struct FT<double> {
+    static __device__ __forceinline__ double of(float v) { return (double)v; }
+    static __device__ __forceinline__ double of(double v) { return v; }
+    static __device__ __forceinline__ double of(dfl v) { return df_to(v); }
+    static __device__ __forceinline__ double to(double v) { return v; }
+    static __device__ __forceinline__ double rn(double v) { return v; }
+    static __device__ __forceinline__ double zero() { return 0.0; }
+    static __device__ __forceinline__ bool is0(double v) { return v == 0.0; }
+    static __device__ __forceinline__ double fma(double w, double x, double a) { return ::fma(w, x, a); }
+};
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
 
@@ -1015,6 +1043,9 @@ __global__ void __launch_bounds__(64, 6) k_slab64r(SlabArgs a) {
 __device__ __forceinline__ float2 shfl8(float2 v, int src) {
     return make_float2(__shfl_sync(0xffffffffu, v.x, src, 8), __shfl_sync(0xffffffffu, v.y, src, 8));
 }
+__device__ __forceinline__ double2 shfl8(double2 v, int src) {
+    return make_double2(__shfl_sync(0xffffffffu, v.x, src, 8), __shfl_sync(0xffffffffu, v.y, src, 8));
+}
 __device__ __forceinline__ dcx shfl8(dcx v, int src) {
     dcx r;
     r.x = dfl(__shfl_sync(0xffffffffu, v.x.hi, src, 8), __shfl_sync(0xffffffffu, v.x.lo, src, 8));
@@ -1489,23 +1520,29 @@ __global__ void __launch_bounds__(256) k_moments(Items it, int n, int P, int npo
     }
 }
 
-// r^i = phi^i - I^H(phi^i) on the face planes of patch i inside Omega_alpha
-// (FP64 arithmetic).  One CTA per (patch, plane); the in-plane interpolant
-// is applied separably: first along v on the coarse rows u = 4k, then along u.
+// Weight table entry in the fine precision T: double-float pairs or FP64.
+template <typename T> __device__ __forceinline__ T pick(const dfl &a, const double &b);
+template <> __device__ __forceinline__ dfl pick<dfl>(const dfl &a, const double &) { return a; }
+template <> __device__ __forceinline__ double pick<double>(const dfl &, const double &b) { return b; }
+
+// r^i = phi^i - I^H(phi^i) on the face planes of patch i inside Omega_alpha.
+// One CTA per (patch, plane); the in-plane interpolant is applied separably:
+// first along v on the coarse rows u = 4k, then along u.
 // resid[p][slot][u + ga][v + ga], slot = axis * npa + j for the plane
 // x_axis = pl0 + j n (relative), (u, v) the other two coordinates.
 struct ResArgs {
     Items it;  // per item: cl, fp -> resid of its plan
     int n, s, ga, b, npa, pl0, wa, nc;
-    dfl lw[4][8];  // Lagrange weights for g mod 4 = r (row r), double-float
+    dfl lw[4][8];     // Lagrange weights for g mod 4 = r (row r), double-float
+    double lwd[4][8]; // the same in FP64
 };
 
 // r^i = phi^i - I^H(phi^i) on the face planes inside Omega_alpha (one CTA per
-// patch and plane).  TB: storage of the local fields (FP32 in the split tier,
-// double-float in the FP64 tier); the interpolation and the difference, where
-// cancellation needs the extra bits, are double-float on the FP32 pipe.  The
-// residual leaves as double-float pairs.
-template <typename TB>
+// patch and plane).  TB: storage of the local fields (FP32, double-float or
+// FP64 by tier); T: arithmetic of the interpolation and the difference, where
+// cancellation needs the extra bits (FP64 or double-float).  The residual
+// leaves in T.
+template <typename TB, typename T>
 __global__ void __launch_bounds__(256) k_resid(ResArgs a) {
     extern __shared__ double rsm[];
     const int slot = blockIdx.y;
@@ -1516,44 +1553,45 @@ __global__ void __launch_bounds__(256) k_resid(ResArgs a) {
     const int klo = -a.ga / 4 - a.b;  // coarse rows the stencils reach (4 | ga, 4 | n)
     const int khi = (a.n + a.ga) / 4 + a.b;
     const int nk = khi - klo + 1;
-    dfl *T = (dfl *)rsm;              // nk x wa: interpolated along v on coarse rows u = 4k
+    T *Tv = (T *)rsm;                 // nk x wa: interpolated along v on coarse rows u = 4k
     const TB *cl = (const TB *)PP.cl + (long)p * nc * nc * nc;
     const TB *fp = (const TB *)PP.fp + ((long)p * gridDim.y + slot) * wa * wa;
     // phi^i at the coarse point (u, v) = (4 ka, 4 kb) of this plane
-    auto clp = [&](int ka, int kb) -> dfl {
+    auto clp = [&](int ka, int kb) -> T {
         int i0, i1, i2;
         if (axis == 0) { i0 = c4; i1 = ka; i2 = kb; }
         else if (axis == 1) { i0 = ka; i1 = c4; i2 = kb; }
         else { i0 = ka; i1 = kb; i2 = c4; }
-        return df_of(cl[((long)(i0 - kl) * nc + (i1 - kl)) * nc + (i2 - kl)]);
+        return FT<T>::of(cl[((long)(i0 - kl) * nc + (i1 - kl)) * nc + (i2 - kl)]);
     };
     for (int e = threadIdx.x; e < nk * wa; e += blockDim.x) {
         const int k = klo + e / wa, v = e % wa - a.ga;
         const int rv = v & 3;
-        dfl t;
+        T t;
         if (rv == 0) {
             t = clp(k, v >> 2);
         } else {
             const int k0 = (v >> 2) - a.b;
-            t = dfl(0.f, 0.f);
-            for (int j = 0; j < K; ++j) t = df_fma(a.lw[rv][j], clp(k, k0 + j), t);
+            t = FT<T>::zero();
+            for (int j = 0; j < K; ++j) t = FT<T>::fma(pick<T>(a.lw[rv][j], a.lwd[rv][j]), clp(k, k0 + j), t);
         }
-        T[e] = t;
+        Tv[e] = t;
     }
     __syncthreads();
-    dfl *out = (dfl *)PP.resid + ((long)p * gridDim.y + slot) * wa * wa;
+    T *out = (T *)PP.resid + ((long)p * gridDim.y + slot) * wa * wa;
     for (int e = threadIdx.x; e < wa * wa; e += blockDim.x) {
         const int u = e / wa - a.ga, v = e % wa - a.ga;
         const int ru = u & 3;
-        dfl iv;
+        T iv;
         if (ru == 0) {
-            iv = T[((u >> 2) - klo) * wa + (v + a.ga)];
+            iv = Tv[((u >> 2) - klo) * wa + (v + a.ga)];
         } else {
             const int k0 = (u >> 2) - a.b;
-            iv = dfl(0.f, 0.f);
-            for (int j = 0; j < K; ++j) iv = df_fma(a.lw[ru][j], renorm(T[(k0 + j - klo) * wa + (v + a.ga)]), iv);
+            iv = FT<T>::zero();
+            for (int j = 0; j < K; ++j)
+                iv = FT<T>::fma(pick<T>(a.lw[ru][j], a.lwd[ru][j]), FT<T>::rn(Tv[(k0 + j - klo) * wa + (v + a.ga)]), iv);
         }
-        out[e] = renorm(df_sub(df_of(fp[e]), iv));
+        out[e] = FT<T>::rn(FT<T>::of(fp[e]) - iv);
     }
 }
 
@@ -1573,22 +1611,22 @@ __device__ __forceinline__ void dot2_step(float &s, float &e, float xh, float xl
     s = t;
 }
 
-// Ring term of one patch: dot product of two rows of n ring-table entries.
-// FP32 / FP64 rows accumulate into acc; double-float rows take the
-// compensated product.
-template <typename RT> __device__ __forceinline__ dfl ring_row(const RT *c, const RT *t, int n) {
+// Ring term of one patch: dot product of two rows of n ring-table entries,
+// returned in the fine precision T.  FP32 / FP64 rows accumulate in their own
+// precision; double-float rows take the compensated product.
+template <typename T, typename RT> __device__ __forceinline__ T ring_row(const RT *c, const RT *t, int n) {
     RT v = 0;
     for (int q = 0; q < n; ++q) v = fma(c[q], t[q], v);
-    return df_of(v);
+    return FT<T>::of(v);
 }
-__device__ __forceinline__ dfl ring_row(const dfl *c, const dfl *t, int n) {
+template <typename T> __device__ __forceinline__ T ring_row(const dfl *c, const dfl *t, int n) {
     float s = 0.f, e = 0.f;
     for (int q = 0; q < n; ++q) dot2_step(s, e, c[q].hi, c[q].lo, t[q].hi, t[q].lo);
-    return two_sum(s, e);
+    return FT<T>::of(two_sum(s, e));
 }
 
 // Dot product of two ring-table rows of n (a multiple of 4) elements, rows
-// 16-byte aligned.
+// 16-byte aligned, added to acc.
 __device__ __forceinline__ void ring_dot(const dfl *c, const dfl *d, int n, dfl &acc) {
     const float4 *c4 = (const float4 *)c, *d4 = (const float4 *)d;
     float s = 0.f, e = 0.f;
@@ -1609,6 +1647,14 @@ __device__ __forceinline__ void ring_dot(const float *c, const float *d, int n, 
         acc = fmaf(x.w, y.w, acc);
     }
 }
+__device__ __forceinline__ void ring_dot(const double *c, const double *d, int n, double &acc) {
+    const double2 *c2 = (const double2 *)c, *d2 = (const double2 *)d;
+    for (int q = 0; q < n / 2; ++q) {
+        const double2 x = c2[q], y = d2[q];
+        acc = fma(x.x, y.x, acc);
+        acc = fma(x.y, y.y, acc);
+    }
+}
 
 struct AsmArgs {
     const void *cl;          // coarse lattice of the local fields, nc^3 per patch (TB)
@@ -1616,12 +1662,14 @@ struct AsmArgs {
     double *FH;
     int np, n, s, nc, npoly, npad, flo, nf;
     int ca_lo, ca_hi, cb_lo, cb_hi;
-    dfl coef[4];  // b_k / H^2, double-float
+    dfl coef[4];      // b_k / H^2, double-float
+    double coefd[4];  // the same in FP64
 };
 
 // F^H[k] = sum over patches i (ascending) of Delta^H phi^{i,h} on C(Omega_alpha(i))
 // or sum_p c_p^i Delta^H(G^h * Q^p) on C(Omega_beta(i)) \ C(Omega_alpha(i)).
-template <typename TB, typename RT>
+// TB: local-field storage, RT: ring tables, T: accumulation (FP64 or double-float).
+template <typename TB, typename RT, typename T>
 __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const long tot = (long)a.nf * a.nf * a.nf;
@@ -1638,7 +1686,7 @@ __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
     }
     const int ncb = a.cb_hi - a.cb_lo + 1;
     const long nc = a.nc, kl = -a.s / 4;
-    dfl acc(0.f, 0.f);  // sums in double-float on the FP32 pipe
+    T acc = FT<T>::zero();
     for (int i0 = lo[0]; i0 <= hi[0]; ++i0)
         for (int i1 = lo[1]; i1 <= hi[1]; ++i1)
             for (int i2 = lo[2]; i2 <= hi[2]; ++i2) {
@@ -1655,38 +1703,42 @@ __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
 #pragma unroll
                             for (int s2 = -1; s2 <= 1; ++s2) {
                                 const int nz = (s0 != 0) + (s1 != 0) + (s2 != 0);
-                                if (a.coef[nz].hi == 0.f) continue;
+                                if (a.coefd[nz] == 0.0) continue;
                                 const long x0 = r0 + s0 - kl, x1 = r1 + s1 - kl, x2 = r2 + s2 - kl;
-                                acc = df_fma(a.coef[nz], df_of(bx[(x0 * nc + x1) * nc + x2]), acc);
+                                acc = FT<T>::fma(pick<T>(a.coef[nz], a.coefd[nz]), FT<T>::of(bx[(x0 * nc + x1) * nc + x2]), acc);
                             }
                 } else {
                     const long t = (((long)(r0 - a.cb_lo) * ncb + (r1 - a.cb_lo)) * ncb +
                                     (r2 - a.cb_lo)) * a.npoly;
-                    acc = df_add(acc, ring_row((const RT *)a.mom + p * a.npad, (const RT *)a.T + t, a.npoly));
+                    acc = acc + ring_row<T>((const RT *)a.mom + p * a.npad, (const RT *)a.T + t, a.npoly);
                 }
             }
-    a.FH[idx] = df_to(acc);
+    a.FH[idx] = FT<T>::to(acc);
 }
 
 struct BndArgs {
-    const dfl *phiH, *resid;  // double-float
-    const void *mom, *D;     // ring tables in the ring precision RT
-    dfl *phiB;        // double-float
+    const void *phiH, *resid;  // fine precision T
+    const void *mom, *D;       // ring tables in the ring precision RT
+    void *phiB;                // fine precision T
     int N, n, np, ga, gb, b, npoly, olo, no, wa, wbx, npa, pl0;
     int pb0, npb;     // face planes of Omega_beta (relative): pb0 + j n, j < npb
     int npad;         // row stride of the ring tables (npoly rounded up to 4; zero padding)
     dfl lw[4][8];     // Lagrange weights for g mod 4 = r (row r), 2b+2 entries
+    double lwd[4][8];
 };
 
 // phi^B at every face-plane node (axis, plane j, u, v).  RT: precision of the
-// Legendre ring sums (FP64 tier: double-float; split tier: float).
-template <typename RT, int NN>
+// Legendre ring sums (the local-convolution precision: FP32, double-float or
+// FP64); T: the interpolation and the accumulation (FP64 or double-float).
+template <typename RT, int NN, typename T>
 __global__ void __launch_bounds__(128, sizeof(RT) == 4 ? 8 : 6) k_boundary(BndArgs a) {
     constexpr int n = NN;  // patch size as a constant: the index divisions become multiplies
     const long pn = (long)(a.N + 1) * (a.N + 1);
     const long tot = 3L * (a.np + 1) * pn;
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= tot) return;
+    const T *phiH = (const T *)a.phiH;
+    const T *resid = (const T *)a.resid;
     const int axis = (int)(idx / ((a.np + 1) * pn));
     const int j = (int)((idx / pn) % (a.np + 1));
     const int u = (int)((idx % pn) / (a.N + 1)), v = (int)(idx % (a.N + 1));
@@ -1706,22 +1758,22 @@ __global__ void __launch_bounds__(128, sizeof(RT) == 4 ? 8 : 6) k_boundary(BndAr
             cnt[d] = K;
         }
     }
-    dfl acc(0.f, 0.f);
+    T acc = FT<T>::zero();
     for (int e0 = 0; e0 < cnt[0]; ++e0) {
-        dfl s1(0.f, 0.f);
+        T s1 = FT<T>::zero();
         for (int e1 = 0; e1 < cnt[1]; ++e1) {
-            const dfl *row = a.phiH + ((long)(kb[0] + e0 - a.olo) * a.no + (kb[1] + e1 - a.olo)) * a.no +
-                             (kb[2] - a.olo);
-            dfl s2;
+            const T *row = phiH + ((long)(kb[0] + e0 - a.olo) * a.no + (kb[1] + e1 - a.olo)) * a.no +
+                           (kb[2] - a.olo);
+            T s2;
             if (rr[2]) {
-                s2 = dfl(0.f, 0.f);
-                for (int e2 = 0; e2 < K; ++e2) s2 = df_fma(a.lw[rr[2]][e2], row[e2], s2);
+                s2 = FT<T>::zero();
+                for (int e2 = 0; e2 < K; ++e2) s2 = FT<T>::fma(pick<T>(a.lw[rr[2]][e2], a.lwd[rr[2]][e2]), row[e2], s2);
             } else {
                 s2 = row[0];
             }
-            s1 = rr[1] ? df_fma(a.lw[rr[1]][e1], renorm(s2), s1) : s2;
+            s1 = rr[1] ? FT<T>::fma(pick<T>(a.lw[rr[1]][e1], a.lwd[rr[1]][e1]), FT<T>::rn(s2), s1) : s2;
         }
-        acc = rr[0] ? df_fma(a.lw[rr[0]][e0], renorm(s1), acc) : s1;
+        acc = rr[0] ? FT<T>::fma(pick<T>(a.lw[rr[0]][e0], a.lwd[rr[0]][e0]), FT<T>::rn(s1), acc) : s1;
     }
     // local corrections of the patches whose Omega_beta holds g (ascending index);
     // the Legendre ring terms accumulate in the ring precision RT
@@ -1748,7 +1800,7 @@ __global__ void __launch_bounds__(128, sizeof(RT) == 4 ? 8 : 6) k_boundary(BndAr
                     else { d = 2; uu = r0; vv = r1; }
                     const int rr = d == 0 ? r0 : (d == 1 ? r1 : r2);
                     const long slot = (long)d * a.npa + (rr - a.pl0) / n;
-                    acc = df_add(acc, a.resid[((p * 3 * a.npa + slot) * a.wa + (uu + a.ga)) * a.wa + (vv + a.ga)]);
+                    acc = acc + resid[((p * 3 * a.npa + slot) * a.wa + (uu + a.ga)) * a.wa + (vv + a.ga)];
                 } else {
                     // dense ring row of (axis, plane, u, v): no index map to read
                     const int ra = axis == 0 ? r0 : (axis == 1 ? r1 : r2);
@@ -1757,17 +1809,18 @@ __global__ void __launch_bounds__(128, sizeof(RT) == 4 ? 8 : 6) k_boundary(BndAr
                     ring_dot((const RT *)a.mom + p * a.npad, (const RT *)a.D + row * a.npad, a.npad, ring);
                 }
             }
-    a.phiB[idx] = renorm(df_add(acc, df_of(ring)));
+    ((T *)a.phiB)[idx] = FT<T>::rn(acc + FT<T>::of(ring));
 }
 
 struct DirArgs {
     Items it;  // per item: f, phiB, phi, lam, N, np, h of its plan
     int n;
     double b[4];
-    const float2 *sinm;  // (n-1) x n/2: sin(pi k t / n), k in [1, n-1], t in [1, n/2], double-float
+    const void *sinm;  // (n-1) x n/2: sin(pi k t / n), k in [1, n-1], t in [1, n/2], fine precision
 };
 
-__device__ __forceinline__ dfl phiB_at(const PlanPtrs &a, int n, int g0, int g1, int g2) {
+template <typename T>
+__device__ __forceinline__ T phiB_at(const PlanPtrs &a, int n, int g0, int g1, int g2) {
     const long pn = (long)(a.N + 1) * (a.N + 1);
     int axis, j, u, v;
     if (g0 % n == 0) {
@@ -1777,42 +1830,8 @@ __device__ __forceinline__ dfl phiB_at(const PlanPtrs &a, int n, int g0, int g1,
     } else {
         axis = 2; j = g2 / n; u = g0; v = g1;
     }
-    return ((const dfl *)a.phiB)[((long)axis * (a.np + 1) + j) * pn + (long)u * (a.N + 1) + v];
+    return ((const T *)a.phiB)[((long)axis * (a.np + 1) + j) * pn + (long)u * (a.N + 1) + v];
 }
-
-// DST-I of one line of m = n-1 values held in registers (n a compile-time
-// constant), in double-float arithmetic, using sin(pi k (n-t)/n) =
-// (-1)^(k+1) sin(pi k t/n): odd k take x_t + x_{n-t}, even k take
-// x_t - x_{n-t}; the middle node t = n/2 enters odd k only.
-template <int NN>
-__device__ __forceinline__ void dst_line_df(dfl (&x)[NN - 1], const dfl *Sh) {
-    constexpr int m = NN - 1, h = NN / 2;
-    dfl sp[h], sm[h];
-#pragma unroll
-    for (int t = 1; t < h; ++t) {
-        sp[t] = df_add(x[t - 1], x[NN - t - 1]);
-        sm[t] = df_sub(x[t - 1], x[NN - t - 1]);
-    }
-    const dfl mid = x[h - 1];
-    dfl y[m];
-#pragma unroll
-    for (int k = 1; k <= m; ++k) {
-        const dfl *row = Sh + (k - 1) * h;
-        dfl v = {0.f, 0.f};
-        if (k & 1) {
-#pragma unroll
-            for (int t = 1; t < h; ++t) v = df_add(v, df_mul(row[t - 1], sp[t]));
-            v = df_add(v, df_mul(row[h - 1], mid));
-        } else {
-#pragma unroll
-            for (int t = 1; t < h; ++t) v = df_add(v, df_mul(row[t - 1], sm[t]));
-        }
-        y[k - 1] = v;
-    }
-#pragma unroll
-    for (int k = 0; k < m; ++k) x[k] = y[k];
-}
-
 
 // sin(pi m / 16) for integer m as (index into sv[0..8] = sin(pi i / 16), sign),
 // resolved at compile time.
@@ -1820,73 +1839,75 @@ __host__ __device__ constexpr int sin16_idx(int m) {
     return ((m % 32 + 32) % 32) % 16 <= 8 ? ((m % 32 + 32) % 32) % 16 : 16 - ((m % 32 + 32) % 32) % 16;
 }
 __host__ __device__ constexpr bool sin16_neg(int m) { return ((m % 32 + 32) % 32) >= 16; }
-template <int M16>
-__device__ __forceinline__ dfl mul_sin16(dfl v, const dfl (&sv)[9]) {
-    const dfl r = df_mul(v, sv[sin16_idx(M16)]);
-    return sin16_neg(M16) ? df_neg(r) : r;
+template <int M16, typename T>
+__device__ __forceinline__ T mul_sin16(T v, const T (&sv)[9]) {
+    const T r = v * sv[sin16_idx(M16)];
+    return sin16_neg(M16) ? -r : r;
 }
 
-// DST-I of 15 values (n = 16) in double-float, y_k = sum_t x_t sin(pi k t / 16),
-// by symmetric splitting: with s_t = x_t + x_{16-t} and d_t = x_t - x_{16-t},
-// the even outputs are the length-7 DST-I of d (split once more into
-// e_t = d_t - d_{8-t}, f_t = d_t + d_{8-t}), and the odd outputs pair up as
-// y_{2j+1} = P_j + Q_j + (-1)^j x_8, y_{15-2j} = P_j - Q_j - (-1)^j x_8 with
-// P_j, Q_j the sums of s_t sin(pi (2j+1) t / 16) over odd and even t (using
+// DST-I of 15 values (n = 16) in the fine precision T, y_k = sum_t x_t
+// sin(pi k t / 16), by symmetric splitting: with s_t = x_t + x_{16-t} and
+// d_t = x_t - x_{16-t}, the even outputs are the length-7 DST-I of d (split
+// once more into e_t = d_t - d_{8-t}, f_t = d_t + d_{8-t}), and the odd
+// outputs pair up as y_{2j+1} = P_j + Q_j + (-1)^j x_8,
+// y_{15-2j} = P_j - Q_j - (-1)^j x_8 with P_j, Q_j the sums of
+// s_t sin(pi (2j+1) t / 16) over odd and even t (using
 // sin(pi (16 - k) t / 16) = -(-1)^t sin(pi k t / 16)).  29 products and 68
 // sums instead of 105 and 98 for the direct sums.  x[t-1] = x_t in, y_k out.
-__device__ __forceinline__ void dst15_fast(dfl (&x)[15], const dfl (&sv)[9]) {
-    dfl sp[8], dm[8];
+template <typename T>
+__device__ __forceinline__ void dst15_fast(T (&x)[15], const T (&sv)[9]) {
+    T sp[8], dm[8];
 #pragma unroll
     for (int t = 1; t < 8; ++t) {
-        sp[t] = df_add(x[t - 1], x[15 - t]);
-        dm[t] = df_sub(x[t - 1], x[15 - t]);
+        sp[t] = x[t - 1] + x[15 - t];
+        dm[t] = x[t - 1] - x[15 - t];
     }
-    const dfl x8 = x[7];
-    dfl y[16];
+    const T x8 = x[7];
+    T y[16];
     // even outputs
     {
-        dfl e[4], f[4];
+        T e[4], f[4];
 #pragma unroll
         for (int t = 1; t < 4; ++t) {
-            e[t] = df_sub(dm[t], dm[8 - t]);
-            f[t] = df_add(dm[t], dm[8 - t]);
+            e[t] = dm[t] - dm[8 - t];
+            f[t] = dm[t] + dm[8 - t];
         }
-        const dfl d4 = dm[4];
-        const dfl ec = mul_sin16<4>(df_add(e[1], e[3]), sv);
-        y[4] = df_add(ec, e[2]);
-        y[8] = df_sub(e[1], e[3]);
-        y[12] = df_sub(ec, e[2]);
+        const T d4 = dm[4];
+        const T ec = mul_sin16<4>(e[1] + e[3], sv);
+        y[4] = ec + e[2];
+        y[8] = e[1] - e[3];
+        y[12] = ec - e[2];
         // kk = 0: sin(pi t / 8) -> m = 2t; kk = 1: sin(3 pi t / 8) -> m = 6t
-        const dfl po0 = df_add(mul_sin16<2>(f[1], sv), mul_sin16<6>(f[3], sv));
-        const dfl qe0 = mul_sin16<4>(f[2], sv);
-        const dfl po1 = df_add(mul_sin16<6>(f[1], sv), mul_sin16<18>(f[3], sv));
-        const dfl qe1 = mul_sin16<12>(f[2], sv);
-        y[2] = df_add(df_add(po0, qe0), d4);
-        y[14] = df_sub(df_sub(po0, qe0), d4);   // kk' = 3: (-1)^3
-        y[6] = df_sub(df_add(po1, qe1), d4);    // kk = 1
-        y[10] = df_add(df_sub(po1, qe1), d4);   // kk' = 2
+        const T po0 = mul_sin16<2>(f[1], sv) + mul_sin16<6>(f[3], sv);
+        const T qe0 = mul_sin16<4>(f[2], sv);
+        const T po1 = mul_sin16<6>(f[1], sv) + mul_sin16<18>(f[3], sv);
+        const T qe1 = mul_sin16<12>(f[2], sv);
+        y[2] = (po0 + qe0) + d4;
+        y[14] = (po0 - qe0) - d4;   // kk' = 3: (-1)^3
+        y[6] = (po1 + qe1) - d4;    // kk = 1
+        y[10] = (po1 - qe1) + d4;   // kk' = 2
     }
     // odd outputs
     {
-        const dfl qo0 = df_add(mul_sin16<2>(sp[2], sv), mul_sin16<6>(sp[6], sv));
-        const dfl qe0 = mul_sin16<4>(sp[4], sv);
-        const dfl qo1 = df_add(mul_sin16<6>(sp[2], sv), mul_sin16<18>(sp[6], sv));
-        const dfl qe1 = mul_sin16<12>(sp[4], sv);
-        const dfl Q[4] = {df_add(qo0, qe0), df_add(qo1, qe1), df_sub(qo1, qe1), df_sub(qo0, qe0)};
+        const T qo0 = mul_sin16<2>(sp[2], sv) + mul_sin16<6>(sp[6], sv);
+        const T qe0 = mul_sin16<4>(sp[4], sv);
+        const T qo1 = mul_sin16<6>(sp[2], sv) + mul_sin16<18>(sp[6], sv);
+        const T qe1 = mul_sin16<12>(sp[4], sv);
+        const T Q[4] = {qo0 + qe0, qo1 + qe1, qo1 - qe1, qo0 - qe0};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int k = 2 * j + 1;
-            dfl p1, p3, p5, p7;
+            T p1, p3, p5, p7;
             switch (j) {  // compile-time after unrolling
                 case 0: p1 = mul_sin16<1>(sp[1], sv); p3 = mul_sin16<3>(sp[3], sv); p5 = mul_sin16<5>(sp[5], sv); p7 = mul_sin16<7>(sp[7], sv); break;
                 case 1: p1 = mul_sin16<3>(sp[1], sv); p3 = mul_sin16<9>(sp[3], sv); p5 = mul_sin16<15>(sp[5], sv); p7 = mul_sin16<21>(sp[7], sv); break;
                 case 2: p1 = mul_sin16<5>(sp[1], sv); p3 = mul_sin16<15>(sp[3], sv); p5 = mul_sin16<25>(sp[5], sv); p7 = mul_sin16<35>(sp[7], sv); break;
                 default: p1 = mul_sin16<7>(sp[1], sv); p3 = mul_sin16<21>(sp[3], sv); p5 = mul_sin16<35>(sp[5], sv); p7 = mul_sin16<49>(sp[7], sv); break;
             }
-            const dfl Pj = df_add(df_add(p1, p3), df_add(p5, p7));
-            const dfl xs = (j & 1) ? df_neg(x8) : x8;
-            y[k] = df_add(df_add(Pj, Q[j]), xs);
-            y[15 - 2 * j] = df_sub(df_sub(Pj, Q[j]), xs);
+            const T Pj = (p1 + p3) + (p5 + p7);
+            const T xs = (j & 1) ? -x8 : x8;
+            y[k] = (Pj + Q[j]) + xs;
+            y[15 - 2 * j] = (Pj - Q[j]) - xs;
         }
     }
 #pragma unroll
@@ -1895,20 +1916,18 @@ __device__ __forceinline__ void dst15_fast(dfl (&x)[15], const dfl (&sv)[9]) {
 
 // Local Dirichlet solve of one patch (Sec. 4, final step): the (Q-th order)
 // stencil problem on the closed patch with boundary data phi^B, by DST-I in
-// all three axes, then phi = u + (h^2/12) f.  All arithmetic between the loads
-// and the final FP64 store is double-float on the FP32 pipe (GB300 issues
-// FP64 on ~1/67 of the FP32 lanes): the boundary data arrive as double-float,
-// the FP64 tier's charge is converted once on load, and one conversion per
-// output node forms the FP64 result.
-template <typename TF, int NN>
+// all three axes, then phi = u + (h^2/12) f.  T: the arithmetic between the
+// loads and the final FP64 store, FP64 (the FP64 pipe) or double-float (the
+// FP32 pipe; GB300 issues FP64 on ~1/67 of the FP32 lanes).  TF: the charge.
+template <typename TF, int NN, typename T>
 __global__ void __launch_bounds__(256, 4) k_dirichlet(DirArgs a) {
     extern __shared__ double sm[];
     constexpr int n = NN, nb = n + 1, m = n - 1, h = n / 2;
-    dfl *U = (dfl *)sm;                // boundary values on the 6 faces, nb^2 each (face 2 axis + side)
-    dfl *X = U + 6 * nb * nb;          // m^3 work
-    dfl *Sh = X + m * m * m;           // (n-1) x n/2 half sine table
+    T *U = (T *)sm;                    // boundary values on the 6 faces, nb^2 each (face 2 axis + side)
+    T *X = U + 6 * nb * nb;            // m^3 work
+    T *Sh = X + m * m * m;             // (n-1) x n/2 half sine table
     // boundary value at node (c0, c1, c2) of the closed patch, one coordinate 0 or n
-    auto Uat = [&](int c0, int c1, int c2) -> dfl {
+    auto Uat = [&](int c0, int c1, int c2) -> T {
         if (c0 == 0 || c0 == n) return U[((c0 ? 1 : 0) * nb + c1) * nb + c2];
         if (c1 == 0 || c1 == n) return U[((2 + (c1 ? 1 : 0)) * nb + c0) * nb + c2];
         return U[((4 + (c2 ? 1 : 0)) * nb + c0) * nb + c1];
@@ -1919,8 +1938,8 @@ __global__ void __launch_bounds__(256, 4) k_dirichlet(DirArgs a) {
     const int i2 = p % np, i1 = (p / np) % np, i0 = p / (np * np);
     const int o0 = i0 * n, o1 = i1 * n, o2 = i2 * n;
     const TF *f = (const TF *)PP.f;
-    const dfl *sinm = (const dfl *)a.sinm;
-    const dfl *lam = (const dfl *)PP.lam;
+    const T *sinm = (const T *)a.sinm;
+    const T *lam = (const T *)PP.lam;
     for (int e = threadIdx.x; e < m * h; e += blockDim.x) Sh[e] = sinm[e];
     for (int e = threadIdx.x; e < 6 * nb * nb; e += blockDim.x) {
         const int b = e % nb, a2 = (e / nb) % nb, fc = e / (nb * nb);  // face fc: axis fc/2, side fc%2
@@ -1929,28 +1948,28 @@ __global__ void __launch_bounds__(256, 4) k_dirichlet(DirArgs a) {
         if (fc < 2) { m0 = side; m1 = a2; m2 = b; }
         else if (fc < 4) { m0 = a2; m1 = side; m2 = b; }
         else { m0 = a2; m1 = b; m2 = side; }
-        U[e] = phiB_at(PP, n, o0 + m0, o1 + m1, o2 + m2);
+        U[e] = phiB_at<T>(PP, n, o0 + m0, o1 + m1, o2 + m2);
     }
     // stencil weights b_k / h^2 and h^2/12 of this plan (converted once per CTA)
-    __shared__ dfl s_w[5];
+    __shared__ T s_w[5];
     if (threadIdx.x < 5) {
         double w = PP.c2h2;
 #pragma unroll
         for (int k = 0; k < 4; ++k)  // static indices: the parameter array stays out of local memory
             if (threadIdx.x == k) w = a.b[k] * PP.inv_h2;
-        s_w[threadIdx.x] = df_from(w);
+        s_w[threadIdx.x] = FT<T>::of(w);
     }
     __syncthreads();
-    dfl cw[4];
+    T cw[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) cw[k] = s_w[k];
-    const dfl c2h2 = s_w[4];
+    const T c2h2 = s_w[4];
     // right-hand side: f - Delta^h(boundary data); only the layer next to the
     // boundary sees boundary values
     for (int e = threadIdx.x; e < m * m * m; e += blockDim.x) {
         const int c2 = e % m + 1, c1 = (e / m) % m + 1, c0 = e / (m * m) + 1;
         const int z = o0 + c0, y = o1 + c1, x = o2 + c2;
-        dfl v = (z < N && y < N && x < N) ? df_of(f[((long)z * N + y) * N + x]) : dfl(0.f, 0.f);
+        T v = (z < N && y < N && x < N) ? FT<T>::of(f[((long)z * N + y) * N + x]) : FT<T>::zero();
         const bool near = c0 == 1 || c0 == m || c1 == 1 || c1 == m || c2 == 1 || c2 == m;
         if (near) {
 #pragma unroll
@@ -1962,24 +1981,19 @@ __global__ void __launch_bounds__(256, 4) k_dirichlet(DirArgs a) {
                         const int nz = (s0 != 0) + (s1 != 0) + (s2 != 0);
                         const int d0 = c0 + s0, d1 = c1 + s1, d2 = c2 + s2;
                         const bool bd = d0 == 0 || d0 == n || d1 == 0 || d1 == n || d2 == 0 || d2 == n;
-                        if (cw[nz].hi == 0.f || !bd) continue;  // interior neighbours carry no boundary data
-                        const dfl u = Uat(d0, d1, d2);
-                        if (u.hi != 0.f) v = df_sub(v, df_mul(cw[nz], u));
+                        if (FT<T>::is0(cw[nz]) || !bd) continue;  // interior neighbours carry no boundary data
+                        const T u = Uat(d0, d1, d2);
+                        if (!FT<T>::is0(u)) v = v - cw[nz] * u;
                     }
         }
         X[e] = v;
     }
     __syncthreads();
     // DST-I along axes 2, 1, 0; scale by the inverse eigenvalues; DST-I along 2, 1, 0
-    // Two threads per line (adjacent lanes): lane parity 0 forms the odd
-    // outputs k = 1, 3, .. from the sums x_t + x_{n-t} (and the middle node),
-    // parity 1 the even outputs from the differences x_t - x_{n-t}; both run
-    // the same instruction stream (the middle node enters with weight 0 for
-    // even k).
     if constexpr (NN == 16) {
         // n = 16: one thread per line with the split-radix DST (dst15_fast)
-        dfl sv[9];
-        sv[0] = dfl(0.f, 0.f);
+        T sv[9];
+        sv[0] = FT<T>::zero();
 #pragma unroll
         for (int i = 1; i <= 8; ++i) sv[i] = Sh[i - 1];  // sin(pi i / 16)
         for (int pass = 0; pass < 6; ++pass) {
@@ -1990,13 +2004,13 @@ __global__ void __launch_bounds__(256, 4) k_dirichlet(DirArgs a) {
                 if (axis == 2) { base = (q0 * m + q1) * m; str = 1; }
                 else if (axis == 1) { base = q0 * m * m + q1; str = m; }
                 else { base = q0 * m + q1; str = m * m; }
-                dfl x[15];
+                T x[15];
 #pragma unroll
-                for (int t = 0; t < 15; ++t) x[t] = renorm(X[base + t * str]);
+                for (int t = 0; t < 15; ++t) x[t] = FT<T>::rn(X[base + t * str]);
                 dst15_fast(x, sv);
                 if (pass == 2) {
 #pragma unroll
-                    for (int t = 0; t < 15; ++t) x[t] = df_mul(x[t], lam[base + t * str]);
+                    for (int t = 0; t < 15; ++t) x[t] = x[t] * lam[base + t * str];
                 }
 #pragma unroll
                 for (int t = 0; t < 15; ++t) X[base + t * str] = x[t];
@@ -2004,6 +2018,11 @@ __global__ void __launch_bounds__(256, 4) k_dirichlet(DirArgs a) {
             __syncthreads();
         }
     } else {
+    // Two threads per line (adjacent lanes): lane parity 0 forms the odd
+    // outputs k = 1, 3, .. from the sums x_t + x_{n-t} (and the middle node),
+    // parity 1 the even outputs from the differences x_t - x_{n-t}; both run
+    // the same instruction stream (the middle node enters with weight 0 for
+    // even k).
     const int par = threadIdx.x & 1, ntl = blockDim.x >> 1;
     for (int pass = 0; pass < 6; ++pass) {
         const int axis = 2 - (pass % 3);
@@ -2015,33 +2034,33 @@ __global__ void __launch_bounds__(256, 4) k_dirichlet(DirArgs a) {
             if (axis == 2) { base = (q0 * m + q1) * m; str = 1; }
             else if (axis == 1) { base = q0 * m * m + q1; str = m; }
             else { base = q0 * m + q1; str = m * m; }
-            dfl x[m];
+            T x[m];
 #pragma unroll
-            for (int t = 0; t < m; ++t) x[t] = valid ? renorm(X[base + t * str]) : dfl(0.f, 0.f);
-            dfl u[h + 1];
+            for (int t = 0; t < m; ++t) x[t] = valid ? FT<T>::rn(X[base + t * str]) : FT<T>::zero();
+            T u[h + 1];
 #pragma unroll
             for (int t = 1; t < h; ++t) {
-                const dfl b = x[n - t - 1];
-                u[t] = df_add(x[t - 1], par ? df_neg(b) : b);
+                const T b = x[n - t - 1];
+                u[t] = x[t - 1] + (par ? -b : b);
             }
-            u[h] = par ? dfl(0.f, 0.f) : x[h - 1];
+            u[h] = par ? FT<T>::zero() : x[h - 1];
             __syncwarp();  // both lanes of the line have read it before either writes
             if (valid) {
 #pragma unroll
                 for (int j = 0; j < (m + 1) / 2; ++j) {
                     const int k = 2 * j + 1 + par;  // output index 1..m
                     if (k > m) break;
-                    const dfl *row = Sh + (k - 1) * h;
+                    const T *row = Sh + (k - 1) * h;
                     // h products summed as a balanced tree: independent chains
-                    dfl pr[h];
+                    T pr[h];
 #pragma unroll
-                    for (int t = 1; t <= h; ++t) pr[t - 1] = df_mul(row[t - 1], u[t]);
+                    for (int t = 1; t <= h; ++t) pr[t - 1] = row[t - 1] * u[t];
 #pragma unroll
                     for (int w = 1; w < h; w *= 2)
 #pragma unroll
-                        for (int t = 0; t + w < h; t += 2 * w) pr[t] = df_add(pr[t], pr[t + w]);
-                    dfl v = pr[0];
-                    if (pass == 2) v = df_mul(v, lam[base + (k - 1) * str]);
+                        for (int t = 0; t + w < h; t += 2 * w) pr[t] = pr[t] + pr[t + w];
+                    T v = pr[0];
+                    if (pass == 2) v = v * lam[base + (k - 1) * str];
                     X[base + (k - 1) * str] = v;
                 }
             }
@@ -2054,8 +2073,8 @@ __global__ void __launch_bounds__(256, 4) k_dirichlet(DirArgs a) {
         const bool bnd = m0 == 0 || m1 == 0 || m2 == 0;
         const int z = o0 + m0, y = o1 + m1, x = o2 + m2;
         const long gi = ((long)z * N + y) * N + x;
-        const dfl u = bnd ? Uat(m0, m1, m2) : X[((m0 - 1) * m + (m1 - 1)) * m + (m2 - 1)];
-        PP.phi[gi] = df_to(df_add(u, df_mul(c2h2, df_of(f[gi]))));
+        const T u = bnd ? Uat(m0, m1, m2) : X[((m0 - 1) * m + (m1 - 1)) * m + (m2 - 1)];
+        PP.phi[gi] = FT<T>::to(u + c2h2 * FT<T>::of(f[gi]));
     }
 }
 
@@ -2072,7 +2091,7 @@ void set_coarse_attrs() {
     cudaFuncSetAttribute(k_col<LOG2M, 0, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_col<LOG2M, 1, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_col<LOG2M, 2, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_inv_x<LOG2M, R, dfl>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_inv_x<LOG2M, R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
 // Local-convolution (patch) kernels in working precision R.
@@ -2160,7 +2179,7 @@ cudaError_t run_conv_t(const ConvDesc &d, cudaStream_t st) {
         InvXArgs a{d.b1, d.out, W, W, d.out_off, 0, d.tw};
         a.lines_cta = (M <= 64) ? W : 16;
         dim3 grid(d.nbatch * W, (W + a.lines_cta - 1) / a.lines_cta);
-        k_inv_x<LOG2M, R, dfl><<<grid, 256, fft_smem_bytes<R>(M, a.lines_cta, M + 1), st>>>(a);  // phi^H as double-float
+        k_inv_x<LOG2M, R, R><<<grid, 256, fft_smem_bytes<R>(M, a.lines_cta, M + 1), st>>>(a);  // phi^H in R
     }
     return cudaGetLastError();
 }
@@ -2295,25 +2314,40 @@ void configure_kernels() {
     set_patch_attrs<6, dfl>();
     set_patch_attrs<5, float>();
     set_patch_attrs<6, float>();
+    set_patch_attrs<5, double>();
+    set_patch_attrs<6, double>();
     set_coarse_attrs<5, dfl>();
     set_coarse_attrs<6, dfl>();
     set_coarse_attrs<7, dfl>();
     set_coarse_attrs<8, dfl>();
-    cudaFuncSetAttribute(k_dirichlet<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_dirichlet<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_dirichlet<double, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_dirichlet<float, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_resid<dfl>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_moments<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_moments<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_resid<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    set_coarse_attrs<5, double>();
+    set_coarse_attrs<6, double>();
+    set_coarse_attrs<7, double>();
+    set_coarse_attrs<8, double>();
+    const int big = 200 * 1024;
+#define MLC_DIR_ATTR(NN)                                                                          \
+    cudaFuncSetAttribute(k_dirichlet<double, NN, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
+    cudaFuncSetAttribute(k_dirichlet<float, NN, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);  \
+    cudaFuncSetAttribute(k_dirichlet<double, NN, dfl>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);    \
+    cudaFuncSetAttribute(k_dirichlet<float, NN, dfl>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    MLC_DIR_ATTR(4)
+    MLC_DIR_ATTR(8)
+    MLC_DIR_ATTR(12)
+    MLC_DIR_ATTR(16)
+#undef MLC_DIR_ATTR
+    cudaFuncSetAttribute(k_resid<dfl, dfl>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_resid<float, dfl>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_resid<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_resid<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_moments<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_moments<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
 cudaError_t launch_moments(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
     const Geom &g = pl->g;
     const int nb = g.n + 1;
     const size_t words = (size_t)nb * nb * nb + (size_t)g.P * nb * nb + (size_t)g.P * g.P * nb + (size_t)g.P * nb;
-    if (g.tier == MLC_TIER_SPLIT)
+    if (g.f32in)
         k_moments<float, float><<<it.nitems, 256, words * sizeof(float), st>>>(it, g.n, g.P, g.npoly, g.npad);
     else
         k_moments<double, double><<<it.nitems, 256, words * sizeof(double), st>>>(it, g.n, g.P, g.npoly, g.npad);
@@ -2322,13 +2356,17 @@ cudaError_t launch_moments(const mlc_plan_s *pl, const Items &it, cudaStream_t s
 
 cudaError_t launch_patch_conv(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
     const Geom &g = pl->g;
-    const bool split = g.tier == MLC_TIER_SPLIT;
-    // split tier: FP32; FP64 tier: double-float (tables tw_df, khat_df)
-    const void *tw = split ? (const void *)pl->tw_f : (const void *)pl->tw_df;
-    if (g.log2M == 5) return split ? run_patch_conv_t<5, float>(pl, it, true, tw, st)
-                                   : run_patch_conv_t<5, dfl>(pl, it, false, tw, st);
-    if (g.log2M == 6) return split ? run_patch_conv_t<6, float>(pl, it, true, tw, st)
-                                   : run_patch_conv_t<6, dfl>(pl, it, false, tw, st);
+    const bool f32 = g.f32in;
+    if (g.conv == CONV_F32) {  // split tiers: FP32 (tables tw_f, khat_f)
+        if (g.log2M == 5) return run_patch_conv_t<5, float>(pl, it, f32, pl->tw_f, st);
+        if (g.log2M == 6) return run_patch_conv_t<6, float>(pl, it, f32, pl->tw_f, st);
+    } else if (g.conv == CONV_DF) {  // double-float (tables tw_df, khat_df)
+        if (g.log2M == 5) return run_patch_conv_t<5, dfl>(pl, it, f32, pl->tw_df, st);
+        if (g.log2M == 6) return run_patch_conv_t<6, dfl>(pl, it, f32, pl->tw_df, st);
+    } else {  // FP64 (tables tw, khat)
+        if (g.log2M == 5) return run_patch_conv_t<5, double>(pl, it, f32, pl->tw, st);
+        if (g.log2M == 6) return run_patch_conv_t<6, double>(pl, it, f32, pl->tw, st);
+    }
     return cudaErrorInvalidValue;
 }
 
@@ -2362,36 +2400,57 @@ dfl host_df(double v) {
     return dfl(hi, (float)(v - (double)hi));
 }
 
+// Moments in the ring precision of the tier (the local-convolution arithmetic).
+const void *ring_moments(const mlc_plan_s *pl) {
+    const Geom &g = pl->g;
+    return g.conv == CONV_F32 ? (const void *)pl->mom_f
+           : (g.conv == CONV_DF ? (const void *)pl->mom_df : (const void *)pl->mom);
+}
+
 cudaError_t launch_resid(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
     const Geom &g = pl->g;
     ResArgs a{};
     a.it = it; a.n = g.n; a.s = g.s; a.ga = g.ga; a.b = g.b;
     a.npa = g.npa; a.pl0 = g.pl0; a.wa = g.wa; a.nc = g.nc;
     lagrange_rows_df(g.b, a.lw);
+    lagrange_rows(g.b, a.lwd);
     const int nk = (g.n + 2 * g.ga) / 4 + 2 * g.b + 1;
-    const size_t sm = sizeof(dfl) * (size_t)nk * g.wa;
+    const size_t sm = 8 * (size_t)nk * g.wa;
     dim3 grid(it.nitems, 3 * g.npa);
-    if (g.tier == MLC_TIER_SPLIT) k_resid<float><<<grid, 256, sm, st>>>(a);
-    else k_resid<dfl><<<grid, 256, sm, st>>>(a);
+    if (g.fine == FINE_F64) {
+        if (g.conv == CONV_F32) k_resid<float, double><<<grid, 256, sm, st>>>(a);
+        else k_resid<double, double><<<grid, 256, sm, st>>>(a);
+    } else {
+        if (g.conv == CONV_F32) k_resid<float, dfl><<<grid, 256, sm, st>>>(a);
+        else k_resid<dfl, dfl><<<grid, 256, sm, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_assemble(const mlc_plan_s *pl, cudaStream_t st) {
     const Geom &g = pl->g;
     AsmArgs a{};
-    const bool split = g.tier == MLC_TIER_SPLIT;
     a.cl = pl->cl; a.FH = pl->FH;
-    a.mom = split ? (const void *)pl->mom_f : (const void *)pl->mom_df;
-    a.T = split ? (const void *)pl->Ttab_f : (const void *)pl->Ttab_df;
+    a.mom = ring_moments(pl);
+    a.T = pl->Ttab;
     a.np = g.np; a.n = g.n; a.s = g.s; a.nc = g.nc; a.npoly = g.npoly; a.npad = g.npad; a.flo = g.flo; a.nf = g.nf;
     a.ca_lo = g.ca_lo; a.ca_hi = g.ca_hi; a.cb_lo = g.cb_lo; a.cb_hi = g.cb_hi;
     double b[4];
     stencil_b(g.Q, b);
-    for (int k = 0; k < 4; ++k) a.coef[k] = host_df(b[k] / (g.H * g.H));
+    for (int k = 0; k < 4; ++k) {
+        a.coef[k] = host_df(b[k] / (g.H * g.H));
+        a.coefd[k] = b[k] / (g.H * g.H);
+    }
     const long tot = (long)g.nf * g.nf * g.nf;
     const unsigned nbk = (unsigned)((tot + 127) / 128);
-    if (split) k_assemble<float, float><<<nbk, 128, 0, st>>>(a);
-    else k_assemble<dfl, dfl><<<nbk, 128, 0, st>>>(a);
+    if (g.conv == CONV_F32) {
+        if (g.fine == FINE_F64) k_assemble<float, float, double><<<nbk, 128, 0, st>>>(a);
+        else k_assemble<float, float, dfl><<<nbk, 128, 0, st>>>(a);
+    } else if (g.conv == CONV_DF) {
+        k_assemble<dfl, dfl, dfl><<<nbk, 128, 0, st>>>(a);
+    } else {
+        k_assemble<double, double, double><<<nbk, 128, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -2401,30 +2460,37 @@ cudaError_t launch_coarse(const mlc_plan_s *pl, cudaStream_t st) {
     d.M = g.Mc; d.log2M = g.log2Mc; d.nbatch = 1; d.nin = g.nf; d.nout = g.no;
     d.out_off = g.olo - g.flo;
     d.src = pl->FH; d.patch = false; d.f32 = false;
-    d.b0 = pl->cbuf0; d.b1 = pl->cbuf1; d.out = pl->phiH; d.khat = pl->khat_c_df; d.tw = pl->tw_c_df;
+    d.b0 = pl->cbuf0; d.b1 = pl->cbuf1; d.out = pl->phiH;
     d.pl = pl; d.ev0 = 6;
+    if (g.fine == FINE_F64) {  // coarse FFTs in FP64
+        d.khat = pl->khat_c; d.tw = pl->tw_c;
+        return run_conv<double>(d, st);
+    }
+    d.khat = pl->khat_c_df; d.tw = pl->tw_c_df;
     return run_conv<dfl>(d, st);  // coarse FFTs in double-float arithmetic
 }
 
 cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st) {
     const Geom &g = pl->g;
-    const bool split = g.tier == MLC_TIER_SPLIT;
     BndArgs a{};
-    a.phiH = (const dfl *)pl->phiH; a.resid = (const dfl *)pl->resid;
-    a.mom = split ? (const void *)pl->mom_f : (const void *)pl->mom_df;
-    a.D = split ? (const void *)pl->Dtab_f : (const void *)pl->Dtab_df;
-    a.phiB = (dfl *)pl->phiB;
+    a.phiH = pl->phiH; a.resid = pl->resid;
+    a.mom = ring_moments(pl);
+    a.D = pl->Dtab;
+    a.phiB = pl->phiB;
     a.pb0 = g.pb0; a.npb = g.npb;
     a.N = g.N; a.n = g.n; a.np = g.np; a.ga = g.ga; a.gb = g.gb; a.b = g.b; a.npoly = g.npoly;
     a.olo = g.olo; a.no = g.no; a.wa = g.wa; a.wbx = g.wbx; a.npa = g.npa; a.pl0 = g.pl0;
     a.npad = g.npad;
     lagrange_rows_df(g.b, a.lw);
+    lagrange_rows(g.b, a.lwd);
     const long tot = g.n_planes_total;
     const unsigned nbk = (unsigned)((tot + 127) / 128);
-#define MLC_BND(NN)                                                  \
-    case NN:                                                         \
-        if (split) k_boundary<float, NN><<<nbk, 128, 0, st>>>(a);    \
-        else k_boundary<dfl, NN><<<nbk, 128, 0, st>>>(a);            \
+#define MLC_BND(NN)                                                                   \
+    case NN:                                                                          \
+        if (g.conv == CONV_F32 && g.fine == FINE_F64) k_boundary<float, NN, double><<<nbk, 128, 0, st>>>(a); \
+        else if (g.conv == CONV_F32) k_boundary<float, NN, dfl><<<nbk, 128, 0, st>>>(a);                      \
+        else if (g.conv == CONV_DF) k_boundary<dfl, NN, dfl><<<nbk, 128, 0, st>>>(a);                         \
+        else k_boundary<double, NN, double><<<nbk, 128, 0, st>>>(a);                                          \
         break;
     switch (g.n) {
         MLC_BND(4)
@@ -2439,17 +2505,21 @@ cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st) {
 
 cudaError_t launch_dirichlet(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
     const Geom &g = pl->g;
-    const bool f32 = g.tier == MLC_TIER_SPLIT;
     DirArgs a{};
     a.it = it; a.n = g.n;
     stencil_b(g.Q, a.b);
     a.sinm = pl->sinm;
     const int nb = g.n + 1, m = g.n - 1;
-    const size_t sm = sizeof(dfl) * (6 * (size_t)nb * nb + (size_t)m * m * m + (size_t)m * (g.n / 2));
-#define MLC_DIR(NN)                                                            \
-    case NN:                                                                   \
-        if (f32) k_dirichlet<float, NN><<<it.nitems, 256, sm, st>>>(a);        \
-        else k_dirichlet<double, NN><<<it.nitems, 256, sm, st>>>(a);           \
+    const size_t sm = 8 * (6 * (size_t)nb * nb + (size_t)m * m * m + (size_t)m * (g.n / 2));
+#define MLC_DIR(NN)                                                                               \
+    case NN:                                                                                      \
+        if (g.fine == FINE_F64) {                                                                 \
+            if (g.f32in) k_dirichlet<float, NN, double><<<it.nitems, 256, sm, st>>>(a);           \
+            else k_dirichlet<double, NN, double><<<it.nitems, 256, sm, st>>>(a);                  \
+        } else {                                                                                  \
+            if (g.f32in) k_dirichlet<float, NN, dfl><<<it.nitems, 256, sm, st>>>(a);              \
+            else k_dirichlet<double, NN, dfl><<<it.nitems, 256, sm, st>>>(a);                     \
+        }                                                                                         \
         break;
     switch (g.n) {
         MLC_DIR(4)

@@ -14,6 +14,20 @@ namespace mlc {
 // Launches of one solve, in order (the timing slots of mlc_debug_timing).
 constexpr int kTimedLaunches = 13;
 
+// Arithmetic of each tier (include/mlc.h): the local convolutions ("conv":
+// spectra, twiddles, local fields) and the steps after them ("fine": coarse
+// charge, coarse solve, residuals, boundary values, Dirichlet solves).
+enum ConvPrec { CONV_F64 = 0, CONV_DF = 1, CONV_F32 = 2 };
+enum FinePrec { FINE_F64 = 0, FINE_DF = 1 };
+inline bool tier_valid(int t) { return t >= MLC_TIER_FP64 && t <= MLC_TIER_SPLIT_DF; }
+inline int tier_conv(int t) {
+    return t == MLC_TIER_FP64 ? CONV_F64 : (t == MLC_TIER_DF ? CONV_DF : CONV_F32);
+}
+inline int tier_fine(int t) { return (t == MLC_TIER_FP64 || t == MLC_TIER_SPLIT) ? FINE_F64 : FINE_DF; }
+inline bool tier_f32_charge(int t) { return t == MLC_TIER_SPLIT || t == MLC_TIER_SPLIT_DF; }
+// Bytes of one real value of the local-convolution arithmetic (complex: twice).
+inline int conv_real_bytes(int t) { return tier_conv(t) == CONV_F32 ? 4 : 8; }
+
 // ---------------------------------------------------------------------------
 // Plan geometry (Sec. 4): every size below is derived from (N, n, s, C, P, Q,
 // g_beta, b) on the host and is identical for every patch.
@@ -22,6 +36,8 @@ struct Geom {
     int N, n, s, C, P, Q, b, ga, gb, np, NP, npoly, nb, W, M, log2M, Mh;
     int npad;                        // npoly rounded up to a multiple of 4 (row stride of moments, D)
     int tier, mode;
+    int conv, fine;                  // ConvPrec, FinePrec of the tier
+    bool f32in;                      // FP32 charge
     double h, H, R;
     int ca_lo, ca_hi, cb_lo, cb_hi;  // coarse boxes C(Omega_alpha), C(Omega_beta), relative
     int flo, fhi, nf;                // F^H extent (union of C(Omega_beta))
@@ -54,12 +70,12 @@ struct PlanPtrs {
     const void *momw;     // 1D moment weights a_k(m) = w_m q_k(2m/n - 1), P x (n+1), FP64
     double mom_scale;     // R^{-3/2}
     double *mom;
-    float *mom_f;         // split tier: FP32 copy of the moments
-    float2 *mom_df;       // FP64 tier: moments as double-float (hi, lo) pairs
-    float2 *resid;        // face-plane residuals, double-float pairs
-    const float2 *phiB;   // boundary values on the face planes, double-float pairs
+    float *mom_f;         // split tiers: FP32 copy of the moments
+    float2 *mom_df;       // double-float tier: moments as double-float (hi, lo) pairs
+    void *resid;          // face-plane residuals (FP64 or double-float pairs, 8 bytes each)
+    const void *phiB;     // boundary values on the face planes (FP64 or double-float pairs)
     double *phi;
-    const float2 *lam;    // Dirichlet inverse eigenvalues (2/n)^3 h^2 / lambda, double-float pairs
+    const void *lam;      // Dirichlet inverse eigenvalues (2/n)^3 h^2 / lambda (FP64 or double-float)
     int N, np;
     double c2h2, inv_h2;  // h^2 / 12, 1 / h^2
     int *err;             // the plan's error word
@@ -90,30 +106,30 @@ struct mlc_plan_s {
     double *khat_c;          // coarse kernel spectrum octant (Mhc^3), scaled by H^2/Mc^3
     double *momw;            // P x nb 1D moment weights (Boole weight x orthonormal Legendre)
     // Legendre ring tables: D [axis][plane][u][v][npad] (dense over the beta
-    // box face planes, zero rows off the ring), T [coarse cell][npoly]
-    float *Dtab_f, *Ttab_f;  // split tier: FP32
-    float2 *Dtab_df, *Ttab_df;  // FP64 tier: double-float (hi, lo) pairs
-    double2 *tw, *tw_c;      // FFT twiddles exp(-2 pi i t / M), t < M/2
-    float *khat_f;           // split tier: FP32 copies of the patch spectrum and twiddles
+    // box face planes, zero rows off the ring), T [coarse cell][npoly], in the
+    // ring precision of the tier (FP32 split tiers, double-float pairs, FP64)
+    void *Dtab, *Ttab;
+    double2 *tw, *tw_c;      // FFT twiddles exp(-2 pi i t / M), t < M/2 (FP64 tier)
+    float *khat_f;           // split tiers: FP32 copies of the patch spectrum and twiddles
     float2 *tw_f;
     float2 *khat_c_df;       // coarse spectrum and twiddles as double-float (hi, lo) pairs
     float4 *tw_c_df;
-    float2 *khat_df;         // FP64 tier: patch spectrum and twiddles as double-float pairs
+    float2 *khat_df;         // double-float tier: patch spectrum and twiddles as double-float pairs
     float4 *tw_df;
-    float2 *sinm;            // (n-1) x n/2 half DST-I matrix sin(pi k t / n), double-float
-    float2 *lam;             // (n-1)^3 (2/n)^3 h^2 / stencil eigenvalue, double-float
+    void *sinm;              // (n-1) x n/2 half DST-I matrix sin(pi k t / n), fine precision
+    void *lam;               // (n-1)^3 (2/n)^3 h^2 / stencil eigenvalue, fine precision
     // workspace (device)
     void *buf0, *buf1;       // ping-pong spectra for the patch convolutions (complex FP64 / FP32)
     void *cl;                // NP x nc^3 local fields on the coarse lattice of the field box (FP32 / double-float)
     void *fpl;               // NP x 3 npa x wa^2 local fields on the face planes inside alpha (FP32 / double-float)
-    double *mom;             // NP x npoly
-    float *mom_f;            // split tier: FP32 copy of the moments
-    float2 *mom_df;          // FP64 tier: double-float copy of the moments
-    float2 *resid;           // NP x 3 npa x wa^2 face-plane residuals (double-float)
+    double *mom;             // NP x npad
+    float *mom_f;            // split tiers: FP32 copy of the moments
+    float2 *mom_df;          // double-float tier: double-float copy of the moments
+    double *resid;           // NP x 3 npa x wa^2 face-plane residuals (fine precision, 8 bytes)
     double *FH;              // nf^3
     double2 *cbuf0, *cbuf1;  // coarse spectra
-    float2 *phiH;            // no^3, double-float pairs
-    float2 *phiB;            // face planes, double-float pairs
+    double *phiH;            // no^3 (fine precision, 8 bytes)
+    double *phiB;            // face planes (fine precision, 8 bytes)
     void *f_stage, *phi_stage;  // device staging for mlc_solve_host
     int *err;                // device error word: nonzero if a bounded wait in a kernel gave up
     size_t ws_bytes;

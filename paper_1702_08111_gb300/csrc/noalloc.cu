@@ -47,7 +47,7 @@ __global__ void k_store_record(PlanPtrs *dst, PlanPtrs rec) { *dst = rec; }
 // Bytes of the two spectra buffers for this plan (as the plan sizes them),
 // each rounded up to 256 bytes.
 size_t scratch_bytes(const Geom &G, size_t *a1_bytes) {
-    const size_t rb = G.tier == MLC_TIER_SPLIT ? sizeof(float) : sizeof(double);
+    const size_t rb = conv_real_bytes(G.tier);
     const size_t A1 = (size_t)G.NP * G.nb * G.nb * G.Mh * 2 * rb;
     const size_t A4 = (size_t)G.NP * G.nzr * G.a4blk * 2 * rb;
     const size_t a1r = (A1 + 255) & ~(size_t)255;

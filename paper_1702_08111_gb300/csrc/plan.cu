@@ -164,6 +164,10 @@ mlc_status derive_geometry(const mlc_params &pp, Geom &g) {
     if (g.ga < 0) return MLC_ERR_INVALID_ARG;
     g.mode = pp.mode < 0 ? MLC_MODE_MLC : pp.mode;
     g.tier = pp.tier < 0 ? MLC_TIER_FP64 : pp.tier;
+    if (!tier_valid(g.tier)) return MLC_ERR_INVALID_ARG;
+    g.conv = tier_conv(g.tier);
+    g.fine = tier_fine(g.tier);
+    g.f32in = tier_f32_charge(g.tier);
     if (g.mode == MLC_MODE_MLC0) {
         g.gb = g.ga;
     } else if (pp.g_beta >= 0) {
@@ -210,7 +214,7 @@ mlc_status derive_geometry(const mlc_params &pp, Geom &g) {
         if ((z >= -g.ga && z <= g.n + g.ga) || (z % 4 == 0)) ++g.nzr;
     }
     {
-        const int cb = g.tier == MLC_TIER_SPLIT ? 8 : 16;  // bytes per complex entry
+        const int cb = 2 * conv_real_bytes(g.tier);         // bytes per complex entry
         const int per16 = 16 / cb;                          // entries per 16 bytes
         g.a4blk = ((g.Mh * g.W + per16 - 1) / per16) * per16;
     }
@@ -398,20 +402,33 @@ mlc_status build_tables(mlc_plan_s *pl) {
                     }
         Dtab.swap(Dd);
     }
-    if (g.tier == MLC_TIER_SPLIT) {
-        TRY(dev_upload(pl, &pl->Dtab_f, std::vector<float>(Dtab.begin(), Dtab.end())));
-        TRY(dev_upload(pl, &pl->Ttab_f, std::vector<float>(Ttab.begin(), Ttab.end())));
+    auto to_df = [](const std::vector<double> &v) {  // double-float (hi, lo) pairs
+        std::vector<float2> o(v.size());
+        for (size_t i = 0; i < v.size(); ++i) {
+            const float hi = (float)v[i];
+            o[i] = make_float2(hi, (float)(v[i] - (double)hi));
+        }
+        return o;
+    };
+    // ring tables in the ring precision: the local-convolution arithmetic
+    if (g.conv == CONV_F32) {
+        float *d = nullptr, *t = nullptr;
+        TRY(dev_upload(pl, &d, std::vector<float>(Dtab.begin(), Dtab.end())));
+        TRY(dev_upload(pl, &t, std::vector<float>(Ttab.begin(), Ttab.end())));
+        pl->Dtab = d;
+        pl->Ttab = t;
+    } else if (g.conv == CONV_DF) {
+        float2 *d = nullptr, *t = nullptr;
+        TRY(dev_upload(pl, &d, to_df(Dtab)));
+        TRY(dev_upload(pl, &t, to_df(Ttab)));
+        pl->Dtab = d;
+        pl->Ttab = t;
     } else {
-        auto split_df = [](const std::vector<double> &v) {
-            std::vector<float2> o(v.size());
-            for (size_t i = 0; i < v.size(); ++i) {
-                const float hi = (float)v[i];
-                o[i] = make_float2(hi, (float)(v[i] - (double)hi));
-            }
-            return o;
-        };
-        TRY(dev_upload(pl, &pl->Dtab_df, split_df(Dtab)));
-        TRY(dev_upload(pl, &pl->Ttab_df, split_df(Ttab)));
+        double *d = nullptr, *t = nullptr;
+        TRY(dev_upload(pl, &d, Dtab));
+        TRY(dev_upload(pl, &t, Ttab));
+        pl->Dtab = d;
+        pl->Ttab = t;
     }
 
     // FFT twiddles
@@ -441,19 +458,23 @@ mlc_status build_tables(mlc_plan_s *pl) {
         for (int c = 0; c < m; ++c)
             for (int e = 0; e < m; ++e)
                 lam[((size_t)a * m + c) * m + e] = (g.h * g.h) / symbol(g.Q, cth[a], cth[c], cth[e]);
-    // as double-float pairs; the DST-I normalisation (2/n)^3 is folded into lam
+    // in the fine precision (FP64 or double-float pairs); the DST-I
+    // normalisation (2/n)^3 is folded into lam
     const double dnorm = std::pow(2.0 / n, 3);
     for (double &v : lam) v *= dnorm;
-    auto to_df = [](const std::vector<double> &v) {
-        std::vector<float2> o(v.size());
-        for (size_t i = 0; i < v.size(); ++i) {
-            const float hi = (float)v[i];
-            o[i] = make_float2(hi, (float)(v[i] - (double)hi));
-        }
-        return o;
-    };
-    TRY(dev_upload(pl, &pl->sinm, to_df(sinm)));
-    TRY(dev_upload(pl, &pl->lam, to_df(lam)));
+    if (g.fine == FINE_DF) {
+        float2 *a = nullptr, *c = nullptr;
+        TRY(dev_upload(pl, &a, to_df(sinm)));
+        TRY(dev_upload(pl, &c, to_df(lam)));
+        pl->sinm = a;
+        pl->lam = c;
+    } else {
+        double *a = nullptr, *c = nullptr;
+        TRY(dev_upload(pl, &a, sinm));
+        TRY(dev_upload(pl, &c, lam));
+        pl->sinm = a;
+        pl->lam = c;
+    }
     return MLC_OK;
 }
 
@@ -518,7 +539,6 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
     *out = nullptr;
     Geom g;
     TRY(derive_geometry(*params, g));
-    if (g.tier != MLC_TIER_FP64 && g.tier != MLC_TIER_SPLIT) return MLC_ERR_INVALID_ARG;
     std::call_once(g_cfg_once, configure_kernels);
     mlc_plan_s *pl = new (std::nothrow) mlc_plan_s();
     if (!pl) return MLC_ERR_OOM;
@@ -540,7 +560,7 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
                                      G.h * G.h / ((double)G.M * G.M * G.M), pl->khat));
         TRY_CUDA(build_even_spectrum(pl->dgf, pl->dgf_L, G.Mc, G.Lc,
                                      G.H * G.H / ((double)G.Mc * G.Mc * G.Mc), pl->khat_c));
-        {   // double-float copies for the coarse convolution: v = hi + lo
+        if (G.fine == FINE_DF) {   // double-float copies for the coarse convolution: v = hi + lo
             auto split = [](double v) {
                 const float h = (float)v;
                 return make_float2(h, (float)(v - (double)h));
@@ -562,7 +582,7 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
         const size_t NP = G.NP, nb = G.nb, W = G.W, M = G.M, Mh = G.Mh;
         (void)M;
         (void)W;
-        const size_t rb = G.tier == MLC_TIER_SPLIT ? sizeof(float) : sizeof(double);
+        const size_t rb = conv_real_bytes(G.tier);
         const size_t A1 = NP * nb * nb * Mh, A4 = NP * (size_t)G.nzr * G.a4blk;
         char *b0 = nullptr, *b1 = nullptr, *bc = nullptr, *bf = nullptr;
         TRY(dev_alloc(pl, &b0, A1 * 2 * rb));   // [p][kx][zi][yi]
@@ -573,7 +593,7 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
         pl->buf1 = b1;
         pl->cl = bc;
         pl->fpl = bf;
-        if (G.tier == MLC_TIER_FP64) {
+        if (G.conv == CONV_DF) {
             // double-float copies of the patch kernel spectrum and twiddles
             auto split = [](double v) {
                 const float h = (float)v;
@@ -593,7 +613,7 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
             }
             TRY(dev_upload(pl, &pl->tw_df, tf));
         }
-        if (G.tier == MLC_TIER_SPLIT) {
+        if (G.conv == CONV_F32) {
             // FP32 copies of the patch kernel spectrum and twiddles
             const size_t nk = (size_t)G.Mh * G.Mh * G.Mh;
             std::vector<double> kd(nk);
@@ -610,10 +630,10 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
         TRY(dev_alloc(pl, &pl->mom, NP * G.npad));  // padding stays zero (memset below)
         TRY_CUDA(cudaMemset(pl->mom, 0, NP * G.npad * sizeof(double)));
         TRY(dev_alloc(pl, &pl->resid, NP * 3 * (size_t)G.npa * G.wa * G.wa));
-        if (G.tier == MLC_TIER_SPLIT) {
+        if (G.conv == CONV_F32) {
             TRY(dev_alloc(pl, &pl->mom_f, NP * G.npad));
             TRY_CUDA(cudaMemset(pl->mom_f, 0, NP * G.npad * sizeof(float)));
-        } else {
+        } else if (G.conv == CONV_DF) {
             TRY(dev_alloc(pl, &pl->mom_df, NP * G.npad));
             TRY_CUDA(cudaMemset(pl->mom_df, 0, NP * G.npad * sizeof(float2)));
         }
@@ -636,7 +656,8 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
         h.a4 = pl->buf1;
         h.cl = pl->cl;
         h.fp = pl->fpl;
-        h.khat = G.tier == MLC_TIER_SPLIT ? (const void *)pl->khat_f : (const void *)pl->khat_df;
+        h.khat = G.conv == CONV_F32 ? (const void *)pl->khat_f
+                 : (G.conv == CONV_DF ? (const void *)pl->khat_df : (const void *)pl->khat);
         h.momw = pl->momw;
         h.mom_scale = std::pow(G.R, -1.5);
         h.mom = pl->mom;
@@ -749,7 +770,7 @@ mlc_status mlc_solve_host(mlc_plan_t pl, const void *f_host, void *phi_host, voi
     if (!pl || !f_host || !phi_host) return MLC_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t N3 = (size_t)pl->g.N * pl->g.N * pl->g.N;
-    const size_t fbytes = N3 * (pl->g.tier == MLC_TIER_SPLIT ? sizeof(float) : sizeof(double));
+    const size_t fbytes = N3 * (pl->g.f32in ? sizeof(float) : sizeof(double));
     if (!pl->f_stage) {
         char *fs = nullptr;
         double *ps = nullptr;
@@ -826,7 +847,8 @@ mlc_status mlc_debug_export(mlc_plan_t pl, int stage, void *host, size_t bytes) 
                               pl->g.npoly * sizeof(double), pl->g.NP, cudaMemcpyDeviceToHost));
         return MLC_OK;
     }
-    if (stage == MLC_STAGE_PHIH || stage == MLC_STAGE_PHIB) {  // double-float pairs on the device
+    if ((stage == MLC_STAGE_PHIH || stage == MLC_STAGE_PHIB) && pl->g.fine == FINE_DF) {
+        // double-float pairs on the device
         std::vector<float2> tmp(bytes / sizeof(double));
         TRY_CUDA(cudaMemcpy(tmp.data(), src, tmp.size() * sizeof(float2), cudaMemcpyDeviceToHost));
         double *out = (double *)host;

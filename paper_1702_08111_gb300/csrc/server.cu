@@ -60,7 +60,7 @@ struct Active {
 size_t estimate_bytes(const mlc_params &p) {
     const long N = p.N, n = p.n, s = p.s;
     if (n <= 0 || N <= 0 || N % n) return 0;
-    const long rb = (p.tier == MLC_TIER_SPLIT) ? 4 : 8;
+    const long rb = mlc::conv_real_bytes(p.tier < 0 ? MLC_TIER_FP64 : p.tier);
     long M = 1;
     while (M < 2 * (n + s)) M <<= 1;
     const long Mh = M / 2 + 1, nb = n + 1, W = n + 2 * s + 1, np = N / n, NP = np * np * np;

@@ -14,7 +14,9 @@ from dataclasses import dataclass
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libmlc_gb300.so")
 
-MLC_TIER_FP64, MLC_TIER_SPLIT = 0, 1
+MLC_TIER_FP64, MLC_TIER_SPLIT, MLC_TIER_DF, MLC_TIER_SPLIT_DF = 0, 1, 2, 3
+F32_CHARGE_TIERS = (MLC_TIER_SPLIT, MLC_TIER_SPLIT_DF)
+TIER_NAMES = {MLC_TIER_FP64: "fp64", MLC_TIER_SPLIT: "split", MLC_TIER_DF: "df", MLC_TIER_SPLIT_DF: "split_df"}
 MLC_MODE_MLC, MLC_MODE_MLC0 = 0, 1
 STAGE_MOMENTS, STAGE_FH, STAGE_PHIH, STAGE_PHIB, STAGE_DGF = 0, 1, 2, 3, 4
 
@@ -184,7 +186,7 @@ class Plan:
     def _check_tensors(self, f, phi):
         import torch
         N = self.params.N
-        want = torch.float32 if self.tier == MLC_TIER_SPLIT else torch.float64
+        want = torch.float32 if self.tier in F32_CHARGE_TIERS else torch.float64
         if not (f.is_cuda and phi.is_cuda):
             raise ValueError("f and phi must be CUDA tensors")
         if f.dtype != want or phi.dtype != torch.float64:

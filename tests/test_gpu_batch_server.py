@@ -27,13 +27,13 @@ def _charge(torch, N, seed, f32=False):
     return t
 
 
-@pytest.mark.parametrize("tier", [0, 1])
+@pytest.mark.parametrize("tier", [0, 1, 2, 3])
 def test_batch_equals_standalone(torch_cuda, tier):
     from paper_1702_08111_gb300 import mlc
     torch = torch_cuda
     sides = [32, 64, 48, 96, 32, 80]
     plans = [mlc.Plan(N, 16, 16, 4, 4, tier=tier) for N in sides]
-    fs = [_charge(torch, N, k, f32=(tier == 1)) for k, N in enumerate(sides)]
+    fs = [_charge(torch, N, k, f32=(tier in (1, 3))) for k, N in enumerate(sides)]
     alone = [p.solve(f).clone() for p, f in zip(plans, fs)]
     phis = [torch.empty_like(a) for a in alone]
     mlc.batch_solve(plans, fs, phis)
@@ -72,9 +72,9 @@ def test_server_results_same_alone_and_in_mix(torch_cuda):
     from paper_1702_08111_gb300 import mlc
     torch = torch_cuda
     reqs = []
-    for k, (N, Q, tier) in enumerate([(64, 4, 0), (48, 6, 1), (96, 4, 1), (64, 6, 0), (32, 4, 0),
-                                      (80, 4, 0), (64, 4, 1), (48, 4, 0), (112, 6, 0), (64, 4, 0)]):
-        f = _charge(torch, N, 20 + k, f32=(tier == 1))
+    for k, (N, Q, tier) in enumerate([(64, 4, 0), (48, 6, 1), (96, 4, 3), (64, 6, 2), (32, 4, 0),
+                                      (80, 4, 2), (64, 4, 1), (48, 4, 0), (112, 6, 0), (64, 4, 3)]):
+        f = _charge(torch, N, 20 + k, f32=(tier in (1, 3)))
         reqs.append((N, Q, tier, f))
     srv = mlc.Server(64 << 30, max_batch=4)
     outs, tickets = [], []
@@ -92,7 +92,7 @@ def test_server_results_same_alone_and_in_mix(torch_cuda):
     for (N, Q, tier, f), phi in zip(reqs, outs):
         alone = mlc.Plan(N, 16, 16, 4, Q, tier=tier).solve(f)
         torch.cuda.synchronize()
-        tol = 1e-12 if tier == 0 else 1e-6
+        tol = 1e-12 if tier in (0, 2) else 1e-6
         err = float((phi - alone).abs().max() / alone.abs().max())
         assert err <= tol
         assert torch.equal(phi, alone)

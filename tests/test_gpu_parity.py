@@ -1,9 +1,11 @@
 """GPU parity: the CUDA library (through the C ABI) against the CPU oracle.
 
-FP64 tier bar: relative max-norm difference <= 1e-12 per stage and for the
-final potential (the tolerance stated for the FP64 path).  Both sides build
-their own DGF for the same (Q, nD = 128, zeta = 2); the tables are compared
-first.
+FP64-accurate tiers (MLC_TIER_FP64: FP64 arithmetic; MLC_TIER_DF:
+double-float arithmetic): relative max-norm difference <= 1e-12 per stage and
+for the final potential (the tolerance stated for the FP64 path).  Split
+tiers (FP32 local convolutions): <= 1e-6 against the oracle and the FP64 GPU
+path.  Both sides build their own DGF for the same (Q, nD = 128, zeta = 2);
+the tables are compared first.
 """
 import numpy as np
 import pytest
@@ -51,6 +53,21 @@ def _check_plane_duplicates(planes, N, n):
             assert np.array_equal(a, b)
 
 
+FP64, SPLIT, DF, SPLIT_DF = 0, 1, 2, 3
+EXACT_TIERS = [FP64, DF]  # FP64-accurate: the 1e-12 bar
+
+_ORACLE = {}
+
+
+def _oracle(key, prm, f_open, G1):
+    """Oracle solve (and its stages) once per case, shared by the tiers."""
+    if key not in _ORACLE:
+        st = {}
+        phi = O.solve_open(prm, f_open, G1=G1, stages=st)
+        _ORACLE[key] = (phi, st)
+    return _ORACLE[key]
+
+
 def _run(torch, prm_kw, f_open, stages=True, **plan_kw):
     from paper_1702_08111_gb300 import mlc
     plan = mlc.Plan(**prm_kw, **plan_kw)
@@ -68,9 +85,12 @@ def _run(torch, prm_kw, f_open, stages=True, **plan_kw):
     return res
 
 
-def _compare(res, prm, f_open, G1):
-    st = {}
-    phi_o = O.solve_open(prm, f_open, G1=G1, stages=st)
+def _compare(res, prm, f_open, G1, key=None):
+    if key is None:
+        st = {}
+        phi_o = O.solve_open(prm, f_open, G1=G1, stages=st)
+    else:
+        phi_o, st = _oracle(key, prm, f_open, G1)
     assert relmax(res["moments"], st["moments"]) <= TOL
     assert relmax(res["FH"], st["FH"]) <= TOL
     assert relmax(res["phiH"], st["phiH"]) <= TOL
@@ -102,43 +122,48 @@ def test_dgf_table_matches_oracle(torch_cuda, Q, G4, G6):
     assert relmax(T[:L, :L, :L], G[:L, :L, :L]) <= 1e-13
 
 
-def test_single_bump_32(torch_cuda, G4):
+@pytest.mark.parametrize("tier", EXACT_TIERS)
+def test_single_bump_32(torch_cuda, G4, tier):
     w = I.workload("single_bump_32")
     f = w.charge()
-    res = _run(torch_cuda, dict(N=32, n=8, s=8, P=4, Q=4), f)
-    _compare(res, O.Params(N=32, n=8, s=8, Q=4), f, G4)
+    res = _run(torch_cuda, dict(N=32, n=8, s=8, P=4, Q=4), f, tier=tier)
+    _compare(res, O.Params(N=32, n=8, s=8, Q=4), f, G4, key="single_bump_32")
 
 
-def test_bumps8_128(torch_cuda, G4):
+@pytest.mark.parametrize("tier", EXACT_TIERS)
+def test_bumps8_128(torch_cuda, G4, tier):
     w = I.workload("bumps8_128")
     f = w.charge()
-    res = _run(torch_cuda, dict(N=128, n=16, s=16, P=4, Q=4), f)
-    _compare(res, O.Params(N=128, n=16, s=16, Q=4), f, G4)
+    res = _run(torch_cuda, dict(N=128, n=16, s=16, P=4, Q=4), f, tier=tier)
+    _compare(res, O.Params(N=128, n=16, s=16, Q=4), f, G4, key="bumps8_128")
 
 
-def test_q6_reduced_64(torch_cuda, G6):
+@pytest.mark.parametrize("tier", EXACT_TIERS)
+def test_q6_reduced_64(torch_cuda, G6, tier):
     w = I.workload("bumps8_64_q6")
     f = w.charge()
-    res = _run(torch_cuda, dict(N=64, n=16, s=16, P=4, Q=6), f)
-    _compare(res, O.Params(N=64, n=16, s=16, Q=6), f, G6)
+    res = _run(torch_cuda, dict(N=64, n=16, s=16, P=4, Q=6), f, tier=tier)
+    _compare(res, O.Params(N=64, n=16, s=16, Q=6), f, G6, key="bumps8_64_q6")
 
 
+@pytest.mark.parametrize("tier", EXACT_TIERS)
 @pytest.mark.parametrize("kw", [
     dict(N=48, n=16, s=16, P=4, Q=4),            # odd patch count per axis
     dict(N=32, n=8, s=12, P=1, Q=4),             # monopole-only ring (P = 1)
     dict(N=32, n=8, s=16, P=4, Q=4, mode=1),     # MLC-0 (no ring)
     dict(N=40, n=8, s=12, P=3, Q=6, b=2),        # 27-point, b = 2, P = 3
 ])
-def test_variants(torch_cuda, G4, G6, kw):
+def test_variants(torch_cuda, G4, G6, kw, tier):
     kw = dict(kw)
+    key = repr(sorted(kw.items()))
     N = kw["N"]
     f = I.sample_bumps(N, I.draw_bumps(5, 100 + N))
     mode = kw.pop("mode", 0)
     b = kw.get("b", None)
-    res = _run(torch_cuda, kw, f, mode=mode)
+    res = _run(torch_cuda, kw, f, mode=mode, tier=tier)
     prm = O.Params(N=N, n=kw["n"], s=kw["s"], P=kw["P"], Q=kw["Q"], b=b,
                    mode="mlc0" if mode else "mlc")
-    _compare(res, prm, f, G4 if kw["Q"] == 4 else G6)
+    _compare(res, prm, f, G4 if kw["Q"] == 4 else G6, key=key)
 
 
 @pytest.mark.parametrize("kw", [
@@ -209,20 +234,22 @@ def test_invalid_arguments(torch_cuda):
     assert e.value.status == 2
 
 
-# ------------------------------------------------------------------ split tier
+# ------------------------------------------------------------------ split tiers
 SPLIT_TOL = 1e-6
 
 
-def test_split_tier_matches_fp64_and_oracle(torch_cuda, G6):
-    """Split tier (FP32 charge, FP32 local convolutions, FP64 elsewhere) within
-    1e-6 relative max-norm of the FP64 GPU path and of the oracle."""
+@pytest.mark.parametrize("tier", [SPLIT, SPLIT_DF])
+def test_split_tier_matches_fp64_and_oracle(torch_cuda, G6, tier):
+    """Split tiers (FP32 charge, FP32 local convolutions and ring sums; FP64 or
+    double-float after them) within 1e-6 relative max-norm of the FP64 GPU
+    path and of the oracle."""
     from paper_1702_08111_gb300 import mlc
     torch = torch_cuda
     w = I.workload("bumps8_64_q6")
     f32 = w.charge().astype(np.float32)
     f64 = f32.astype(np.float64)
-    ps = mlc.Plan(64, 16, 16, 4, 6, tier=mlc.MLC_TIER_SPLIT)
-    pd = mlc.Plan(64, 16, 16, 4, 6)
+    ps = mlc.Plan(64, 16, 16, 4, 6, tier=tier)
+    pd = mlc.Plan(64, 16, 16, 4, 6, tier=FP64)
     a = ps.solve(torch.from_numpy(f32).cuda())
     b = pd.solve(torch.from_numpy(f64).cuda())
     torch.cuda.synchronize()
@@ -234,22 +261,41 @@ def test_split_tier_matches_fp64_and_oracle(torch_cuda, G6):
     assert relmax(a, ref) <= SPLIT_TOL
 
 
+@pytest.mark.parametrize("tier", [SPLIT, SPLIT_DF])
+def test_split_tier_small_patches_vs_oracle(torch_cuda, G4, tier):
+    """n = 8 patches (M = 32 transforms) in the split tiers against the oracle."""
+    from paper_1702_08111_gb300 import mlc
+    torch = torch_cuda
+    w = I.workload("single_bump_32")
+    f32 = w.charge().astype(np.float32)
+    a = mlc.Plan(32, 8, 8, 4, 4, tier=tier).solve(torch.from_numpy(f32).cuda())
+    torch.cuda.synchronize()
+    ref = O.solve_open(O.Params(N=32, n=8, s=8, Q=4), f32.astype(np.float64), G1=G4)
+    assert relmax(a.cpu().numpy(), ref) <= SPLIT_TOL
+
+
 def test_split_tier_256_below_discretisation_error(torch_cuda):
-    """256^3, 4096 patches, Q = 6, 32 bumps, FP32 charge: split vs FP64 GPU path
-    <= 1e-6 and below the FP64 path's error against the closed-form potential."""
+    """256^3, 4096 patches, Q = 6, 32 bumps, FP32 charge: both split tiers and
+    the double-float tier against the FP64 GPU path (<= 1e-6; <= 1e-12 for
+    double-float), the split tiers below the FP64 path's error against the
+    closed-form potential."""
     from oracle import closed_forms as CF
     from paper_1702_08111_gb300 import mlc
     torch = torch_cuda
     w = I.workload("bumps32_256_q6")
     f32 = w.charge()
-    ps = mlc.Plan(256, 16, 16, 4, 6, tier=mlc.MLC_TIER_SPLIT)
-    a = ps.solve(torch.from_numpy(f32).cuda()).cpu().numpy()
-    del ps
-    pd = mlc.Plan(256, 16, 16, 4, 6)
-    b = pd.solve(torch.from_numpy(f32.astype(np.float64)).cuda()).cpu().numpy()
-    del pd
+    f64 = f32.astype(np.float64)
+    out = {}
+    for tier in (FP64, DF, SPLIT, SPLIT_DF):
+        p = mlc.Plan(256, 16, 16, 4, 6, tier=tier)
+        f = torch.from_numpy(f32 if tier in (SPLIT, SPLIT_DF) else f64).cuda()
+        out[tier] = p.solve(f).cpu().numpy()
+        del p, f
+    b = out[FP64]
     ex = CF.bumps_potential(256, w.bumps)
-    e_split = relmax(a, b)
     e_disc = relmax(b, ex)
-    assert e_split <= SPLIT_TOL, e_split
-    assert e_split < e_disc, (e_split, e_disc)
+    assert relmax(out[DF], b) <= TOL
+    for tier in (SPLIT, SPLIT_DF):
+        e_split = relmax(out[tier], b)
+        assert e_split <= SPLIT_TOL, (tier, e_split)
+        assert e_split < e_disc, (tier, e_split, e_disc)
