@@ -83,6 +83,9 @@ typedef struct {
     int dgf_nD;     /* DGF table built on [-zeta nD, zeta nD]^3 (App. A.1); -1: 128,
                        raised automatically to the largest lag the plan needs           */
     int dgf_zeta;   /* -1: 2                                                            */
+    int conv_chunk; /* patches per launch group of the local convolutions: their spectra
+                       (the scratch between the forward and inverse transforms) exist
+                       for one group at a time; -1: the library's choice (1024)        */
 } mlc_params;
 
 typedef struct mlc_plan_s *mlc_plan_t;
@@ -113,16 +116,35 @@ mlc_status mlc_plan_destroy(mlc_plan_t plan);
  * before returning. */
 mlc_status mlc_plan_status(mlc_plan_t plan);
 
-/* Bytes of device workspace the plan holds (tables excluded). */
+/* Bytes of device workspace the plan holds now (tables excluded; the plan's
+ * own local-convolution scratch counts once a solve has allocated it). */
 mlc_status mlc_plan_workspace_bytes(mlc_plan_t plan, size_t *bytes);
+
+/*
+ * Scratch of the local convolutions (Sec. 4, Step 1: the patch spectra
+ * between the forward and the inverse transforms of Hockney's method, App.
+ * A.2).  The convolutions run in launch groups of conv_chunk patches, so a
+ * solve needs scratch for min(conv_chunk, patches) patches: *bytes.  By
+ * default the first mlc_solve with a plan allocates it and the plan keeps it.
+ * mlc_plan_set_scratch hands the plan caller-owned device memory instead
+ * (scratch: 256-byte aligned, at least mlc_plan_scratch_bytes bytes, owned by
+ * the caller and alive while solves that use it run; NULL returns to the
+ * plan's own scratch).  Contents need no initialisation and are not kept.
+ * Solves that share one scratch must not overlap on the GPU.  INVALID_ARG if
+ * scratch is too small or misaligned.
+ */
+mlc_status mlc_plan_scratch_bytes(mlc_plan_t plan, size_t *bytes);
+mlc_status mlc_plan_set_scratch(mlc_plan_t plan, void *scratch, size_t bytes);
 
 /*
  * Solve Delta phi = f in free space by the two-level MLC (Sec. 4, Steps 1-3,
  * Dirichlet solves and the Mehrstellen correction).  f: device array of N^3
- * values (FP64 for MLC_TIER_FP64, FP32 for MLC_TIER_SPLIT), x = g h, axis 2
+ * values (FP32 for the split tiers, FP64 for the others), x = g h, axis 2
  * contiguous.  phi: device array of N^3 FP64 values, same layout; may not
  * alias f.  Work is enqueued on `stream` (a cudaStream_t; NULL = legacy
- * default stream); the call returns without synchronising.  Two steps that
+ * default stream); the call returns without synchronising.  The first call
+ * with a plan that has no caller-owned scratch allocates the plan's
+ * local-convolution scratch (see mlc_plan_set_scratch).  Two steps that
  * do not depend on the local convolutions' chain (the moments, then the
  * face-plane residuals) run on a stream the plan owns, forked from and joined
  * back to `stream` with events, so all of the solve's work follows earlier
@@ -141,10 +163,13 @@ mlc_status mlc_solve(mlc_plan_t plan, const void *f, void *phi, void *stream);
  * local convolutions (the patch spectra) from one static device array of
  * 64 MiB that every GPU loading the library holds until the process exits,
  * instead of from the plan's workspace.  Same f, phi, stream contract and the
- * same result as mlc_solve.  INVALID_ARG if the plan's spectra need more than
- * 64 MiB (about 1.1 MB per patch of 16^3 with support 16 in the FP64 tier, half
- * that in the split tier: some 60 and 120 patches) or the current device is not
- * the plan's.  The first call on a device looks
+ * same result as mlc_solve, but every step runs on `stream` (no side stream:
+ * the moments and residuals do not overlap the convolution chain).
+ * INVALID_ARG if the spectra of one launch group (min(conv_chunk, patches)
+ * patches) need more than 64 MiB (about 1.1 MB per patch of 16^3 with support
+ * 16 in the FP64 and double-float tiers, half that in the split tiers: some
+ * 60 and 120 patches; lower conv_chunk to fit more) or the current device is
+ * not the plan's.  The first call on a device looks
  * up the array's device address with that device current: make it before any
  * stream capture.  All calls share the array and see the last call's
  * contents (every element a call reads it has written first, so nothing needs

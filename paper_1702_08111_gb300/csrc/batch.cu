@@ -1,12 +1,16 @@
-// mlc_batch_solve: many independent problems with the same patch geometry in
-// one pass.  The per-patch steps (moments, local convolutions, residuals,
-// Dirichlet solves) of all problems run in shared launches over an item table
-// of (problem, patch) pairs; the per-problem coarse steps (F^H assembly,
-// coarse solve, boundary values) run on parallel branches, the moments beside
-// the local convolutions and the residuals beside the coarse steps.  The sequence is
-// captured once as a CUDA graph per (plans, f, phi) set and replayed; the
-// number of parallel branches is picked by timing the candidates on the
-// first call (autotuning).
+// mlc_batch_solve: many independent problems in one pass.  Problems are
+// grouped by patch geometry and tier (n, s, Q, P, b, g_alpha, g_beta, M,
+// tier); the per-patch steps (moments, local convolutions, residuals,
+// Dirichlet solves) of all problems of a group run in shared launches over an
+// item table of (problem, patch) pairs, the groups on concurrent streams; the
+// per-problem coarse steps (F^H assembly, coarse solve, boundary values) run
+// on parallel branches, the moments beside the local convolutions and the
+// residuals beside the coarse steps.  The sequence is captured once as a CUDA
+// graph per (plans, f, phi) set and replayed; the number of parallel branches
+// and the slab launch shape are picked by timing the candidates on the first
+// call (autotuning).  The same launch sequence runs uncaptured for the
+// continuous-batching server (batch_enqueue).
+#include <algorithm>
 #include <chrono>
 #include <cstring>
 #include <map>
@@ -17,13 +21,166 @@
 
 using namespace mlc;
 
+namespace mlc {
+
+bool same_patch_geometry(const Geom &a, const Geom &b) {
+    return a.n == b.n && a.s == b.s && a.Q == b.Q && a.P == b.P && a.b == b.b && a.ga == b.ga &&
+           a.gb == b.gb && a.tier == b.tier && a.M == b.M;
+}
+
+void batch_layout(int count, const mlc_plan_t *plans, const void *const *f, void *const *phi,
+                  BatchLayout &L) {
+    L.order.clear();
+    L.plan_group.clear();
+    L.groups.clear();
+    L.items.clear();
+    L.recs.clear();
+    // groups in order of first appearance; problems keep their order inside a group
+    std::vector<int> gof(count, -1);
+    std::vector<int> reps;
+    for (int k = 0; k < count; ++k) {
+        for (size_t g = 0; g < reps.size(); ++g)
+            if (same_patch_geometry(plans[reps[g]]->g, plans[k]->g)) {
+                gof[k] = (int)g;
+                break;
+            }
+        if (gof[k] < 0) {
+            gof[k] = (int)reps.size();
+            reps.push_back(k);
+        }
+    }
+    for (size_t g = 0; g < reps.size(); ++g) {
+        BatchLayout::Group G;
+        G.rep = plans[reps[g]];
+        G.item0 = (int)L.items.size();
+        for (int k = 0; k < count; ++k) {
+            if (gof[k] != (int)g) continue;
+            const int slot = (int)L.recs.size();
+            PlanPtrs r = plans[k]->hptrs;
+            r.f = f[k];
+            r.phi = (double *)phi[k];
+            L.recs.push_back(r);
+            L.order.push_back(k);
+            L.plan_group.push_back((int)g);
+            for (int p = 0; p < plans[k]->g.NP; ++p) L.items.push_back(make_int2(slot, p));
+        }
+        G.nitems = (int)L.items.size() - G.item0;
+        L.groups.push_back(G);
+    }
+}
+
+cudaError_t BatchStreams::ensure(int ngroups, int nbranches) {
+    auto mk_s = [](std::vector<cudaStream_t> &v, size_t n) -> cudaError_t {
+        while (v.size() < n) {
+            cudaStream_t s;
+            cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return e;
+            v.push_back(s);
+        }
+        return cudaSuccess;
+    };
+    auto mk_e = [](std::vector<cudaEvent_t> &v, size_t n) -> cudaError_t {
+        while (v.size() < n) {
+            cudaEvent_t e;
+            cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+            if (r != cudaSuccess) return r;
+            v.push_back(e);
+        }
+        return cudaSuccess;
+    };
+    cudaError_t e = mk_s(conv, ngroups);
+    if (e == cudaSuccess) e = mk_s(aux, ngroups);
+    if (e == cudaSuccess) e = mk_s(side, nbranches);
+    if (e == cudaSuccess) e = mk_e(ev, 1 + 4 * (size_t)ngroups + nbranches);
+    return e;
+}
+
+void BatchStreams::release() {
+    for (auto v : {&conv, &aux, &side})
+        for (auto s : *v) cudaStreamDestroy(s);
+    for (auto e : ev) cudaEventDestroy(e);
+    conv.clear();
+    aux.clear();
+    side.clear();
+    ev.clear();
+}
+
+cudaError_t batch_enqueue(const std::vector<mlc_plan_t> &plans, const BatchLayout &L, const int2 *d_items,
+                          const PlanPtrs *d_recs, BatchStreams &S, int branches, int persist,
+                          cudaStream_t st) {
+    const int G = (int)L.groups.size();
+    cudaError_t err = S.ensure(G, branches);
+    if (err != cudaSuccess) return err;
+    cudaEvent_t ev_start = S.ev[0];
+    auto ev_mom = [&](int g) { return S.ev[1 + 4 * g]; };
+    auto ev_conv = [&](int g) { return S.ev[2 + 4 * g]; };
+    auto ev_res = [&](int g) { return S.ev[3 + 4 * g]; };
+    auto ev_dir = [&](int g) { return S.ev[4 + 4 * g]; };
+    auto ev_br = [&](int b) { return S.ev[1 + 4 * G + b]; };
+#define TRYE(x)                              \
+    do {                                     \
+        err = (x);                           \
+        if (err != cudaSuccess) return err;  \
+    } while (0)
+    TRYE(cudaEventRecord(ev_start, st));
+    // per group: moments beside the local convolutions, then the residuals
+    for (int g = 0; g < G; ++g) {
+        const BatchLayout::Group &gr = L.groups[g];
+        Items it{d_items + gr.item0, d_recs, gr.nitems};
+        it.persist = persist;
+        it.a1 = gr.a1;
+        it.a4 = gr.a4;
+        TRYE(cudaStreamWaitEvent(S.aux[g], ev_start, 0));
+        TRYE(cudaStreamWaitEvent(S.conv[g], ev_start, 0));
+        TRYE(launch_moments(gr.rep, it, S.aux[g]));
+        TRYE(cudaEventRecord(ev_mom(g), S.aux[g]));
+        TRYE(launch_patch_conv(gr.rep, it, S.conv[g]));
+        TRYE(cudaEventRecord(ev_conv(g), S.conv[g]));
+        TRYE(cudaStreamWaitEvent(S.aux[g], ev_conv(g), 0));
+        TRYE(launch_resid(gr.rep, it, S.aux[g]));
+        TRYE(cudaEventRecord(ev_res(g), S.aux[g]));
+    }
+    // per branch: the coarse charges and coarse solves of its problems, then
+    // (after the residuals of their groups) their boundary values
+    const int P = (int)plans.size();
+    for (int j = 0; j < P; ++j) {
+        cudaStream_t s = S.side[j % branches];
+        const int g = L.plan_group[j];
+        TRYE(cudaStreamWaitEvent(s, ev_conv(g), 0));
+        TRYE(cudaStreamWaitEvent(s, ev_mom(g), 0));
+        TRYE(launch_assemble(plans[L.order[j]], s));
+        TRYE(launch_coarse(plans[L.order[j]], s));
+    }
+    for (int j = 0; j < P; ++j) {
+        cudaStream_t s = S.side[j % branches];
+        TRYE(cudaStreamWaitEvent(s, ev_res(L.plan_group[j]), 0));
+        TRYE(launch_boundary(plans[L.order[j]], s));
+    }
+    const int nb = std::min(branches, P);
+    for (int b = 0; b < nb; ++b) TRYE(cudaEventRecord(ev_br(b), S.side[b]));
+    // Dirichlet solves of each group after every boundary step; join into st
+    for (int g = 0; g < G; ++g) {
+        const BatchLayout::Group &gr = L.groups[g];
+        Items it{d_items + gr.item0, d_recs, gr.nitems};
+        for (int b = 0; b < nb; ++b) TRYE(cudaStreamWaitEvent(S.conv[g], ev_br(b), 0));
+        TRYE(launch_dirichlet(gr.rep, it, S.conv[g]));
+        TRYE(cudaEventRecord(ev_dir(g), S.conv[g]));
+        TRYE(cudaStreamWaitEvent(st, ev_dir(g), 0));
+    }
+#undef TRYE
+    return cudaSuccess;
+}
+
+}  // namespace mlc
+
 namespace {
 
 struct BatchCtx {
-    std::vector<mlc_plan_t> plans;
+    std::vector<mlc_plan_t> plans;  // in call order
+    BatchLayout L;
     int2 *d_items = nullptr;
     PlanPtrs *d_plans = nullptr;
-    int nitems = 0;
+    std::vector<void *> scratch;  // per group: local-convolution scratch of one launch group
     cudaGraphExec_t exec = nullptr;
     int branches = 0;
     int persist = 0;
@@ -33,64 +190,25 @@ struct BatchCtx {
 std::mutex g_mu;
 std::map<std::vector<uintptr_t>, BatchCtx *> g_cache;
 
-#define TRYE(x)                            \
-    do {                                   \
-        cudaError_t _e = (x);              \
-        if (_e != cudaSuccess) return _e;  \
-    } while (0)
-
 cudaError_t capture(BatchCtx &c, int branches, int persist, cudaGraphExec_t *out) {
     cudaStream_t cap;
-    TRYE(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-    std::vector<cudaStream_t> side(branches + 1);  // coarse branches, then the moments / residual stream
-    std::vector<cudaEvent_t> ev(branches + 4);
-    for (auto &s : side) cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-    for (auto &e : ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
-    cudaStream_t aux = side[branches];
-    cudaEvent_t ev_start = ev[branches], ev_mom = ev[branches + 1], ev_conv = ev[branches + 2],
-                ev_res = ev[branches + 3];
-    const mlc_plan_s *rep = c.plans[0];
-    Items it{c.d_items, c.d_plans, c.nitems};
-    it.persist = persist;
-    cudaError_t err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    cudaError_t err = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (err != cudaSuccess) return err;
+    BatchStreams S;
+    err = S.ensure((int)c.L.groups.size(), branches);
+    if (err == cudaSuccess) err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    const bool began = err == cudaSuccess;
     g_capturing = true;
-    // moments beside the local convolutions; residuals beside the coarse steps
-    if (err == cudaSuccess) err = cudaEventRecord(ev_start, cap);
-    if (err == cudaSuccess) err = cudaStreamWaitEvent(aux, ev_start, 0);
-    if (err == cudaSuccess) err = launch_moments(rep, it, aux);
-    if (err == cudaSuccess) err = cudaEventRecord(ev_mom, aux);
-    if (err == cudaSuccess) err = launch_patch_conv(rep, it, cap);
-    if (err == cudaSuccess) err = cudaEventRecord(ev_conv, cap);
-    if (err == cudaSuccess) err = cudaStreamWaitEvent(aux, ev_conv, 0);
-    if (err == cudaSuccess) err = launch_resid(rep, it, aux);
-    if (err == cudaSuccess) err = cudaEventRecord(ev_res, aux);
-    for (int b = 0; b < branches && err == cudaSuccess; ++b) {
-        err = cudaStreamWaitEvent(side[b], ev_conv, 0);
-        if (err == cudaSuccess) err = cudaStreamWaitEvent(side[b], ev_mom, 0);
-    }
-    // per branch: the coarse charges and coarse solves of its problems, then
-    // (after the residuals) their boundary values
-    for (size_t k = 0; k < c.plans.size() && err == cudaSuccess; ++k) {
-        cudaStream_t s = side[k % branches];
-        err = launch_assemble(c.plans[k], s);
-        if (err == cudaSuccess) err = launch_coarse(c.plans[k], s);
-    }
-    for (int b = 0; b < branches && err == cudaSuccess; ++b) err = cudaStreamWaitEvent(side[b], ev_res, 0);
-    for (size_t k = 0; k < c.plans.size() && err == cudaSuccess; ++k)
-        err = launch_boundary(c.plans[k], side[k % branches]);
-    for (int b = 0; b < branches && err == cudaSuccess; ++b) {
-        err = cudaEventRecord(ev[b], side[b]);
-        if (err == cudaSuccess) err = cudaStreamWaitEvent(cap, ev[b], 0);
-    }
-    if (err == cudaSuccess) err = launch_dirichlet(rep, it, cap);
+    if (err == cudaSuccess) err = batch_enqueue(c.plans, c.L, c.d_items, c.d_plans, S, branches, persist, cap);
     g_capturing = false;
     cudaGraph_t graph = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
-    if (err == cudaSuccess) err = e2;
+    if (began) {
+        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (err == cudaSuccess) err = e2;
+    }
     if (err == cudaSuccess) err = cudaGraphInstantiate(out, graph, 0);
     if (graph) cudaGraphDestroy(graph);
-    for (auto &s : side) cudaStreamDestroy(s);
-    for (auto &e : ev) cudaEventDestroy(e);
+    S.release();
     cudaStreamDestroy(cap);
     return err;
 }
@@ -105,9 +223,10 @@ cudaError_t build_and_tune(BatchCtx &c, cudaStream_t st) {
         if (b == 1 || b <= nplans)
             for (int ps : {0, 1}) cand.push_back({b, ps});
     cudaEvent_t e0, e1;
-    TRYE(cudaEventCreate(&e0));
-    TRYE(cudaEventCreate(&e1));
-    cudaError_t err = cudaSuccess;
+    cudaError_t err = cudaEventCreate(&e0);
+    if (err != cudaSuccess) return err;
+    err = cudaEventCreate(&e1);
+    if (err != cudaSuccess) return err;
     for (auto bp : cand) {
         const int b = bp.first;
         cudaGraphExec_t ex = nullptr;
@@ -142,11 +261,6 @@ cudaError_t build_and_tune(BatchCtx &c, cudaStream_t st) {
     return err;
 }
 
-bool same_patch_geometry(const Geom &a, const Geom &b) {
-    return a.n == b.n && a.s == b.s && a.Q == b.Q && a.P == b.P && a.b == b.b && a.ga == b.ga &&
-           a.gb == b.gb && a.tier == b.tier && a.M == b.M;
-}
-
 }  // namespace
 
 extern "C" mlc_status mlc_batch_solve(int count, const mlc_plan_t *plans, const void *const *f,
@@ -155,7 +269,7 @@ extern "C" mlc_status mlc_batch_solve(int count, const mlc_plan_t *plans, const 
     if (count == 0) return MLC_OK;
     for (int k = 0; k < count; ++k) {
         if (!plans[k] || !f[k] || !phi[k] || f[k] == phi[k]) return MLC_ERR_INVALID_ARG;
-        if (!same_patch_geometry(plans[k]->g, plans[0]->g)) return MLC_ERR_INVALID_ARG;
+        if (plans[k]->device != plans[0]->device) return MLC_ERR_INVALID_ARG;
         for (int j = 0; j < k; ++j)
             if (plans[j] == plans[k]) return MLC_ERR_INVALID_ARG;
     }
@@ -174,18 +288,22 @@ extern "C" mlc_status mlc_batch_solve(int count, const mlc_plan_t *plans, const 
     } else {
         c = new BatchCtx();
         c->plans.assign(plans, plans + count);
-        std::vector<int2> items;
-        std::vector<PlanPtrs> recs;
-        for (int k = 0; k < count; ++k) {
-            PlanPtrs r = plans[k]->hptrs;
-            r.f = f[k];
-            r.phi = (double *)phi[k];
-            recs.push_back(r);
-            for (int p = 0; p < plans[k]->g.NP; ++p) items.push_back(make_int2(k, p));
-        }
-        c->nitems = (int)items.size();
+        batch_layout(count, plans, f, phi, c->L);
+        const auto &items = c->L.items;
+        const auto &recs = c->L.recs;
         cudaError_t e = cudaMalloc((void **)&c->d_items, items.size() * sizeof(int2));
         if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_plans, recs.size() * sizeof(PlanPtrs));
+        for (auto &gr : c->L.groups) {
+            if (e != cudaSuccess) break;
+            const Geom &G = gr.rep->g;
+            const long nit = std::min<long>(G.chunk, gr.nitems);
+            void *p = nullptr;
+            e = cudaMalloc(&p, conv_scratch_bytes(G, nit));
+            if (e != cudaSuccess) break;
+            c->scratch.push_back(p);
+            gr.a1 = p;
+            gr.a4 = (char *)p + conv_scratch_a4_offset(G, nit);
+        }
         if (e == cudaSuccess)
             e = cudaMemcpy(c->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
@@ -195,6 +313,7 @@ extern "C" mlc_status mlc_batch_solve(int count, const mlc_plan_t *plans, const 
             if (c->exec) cudaGraphExecDestroy(c->exec);
             cudaFree(c->d_items);
             cudaFree(c->d_plans);
+            for (void *p : c->scratch) cudaFree(p);
             delete c;
             return e == cudaErrorMemoryAllocation ? MLC_ERR_OOM : MLC_ERR_CUDA;
         }
@@ -215,6 +334,7 @@ void mlc_batch_forget(mlc_plan_t plan) {
             if (c->exec) cudaGraphExecDestroy(c->exec);
             cudaFree(c->d_items);
             cudaFree(c->d_plans);
+            for (void *p : c->scratch) cudaFree(p);
             delete c;
             it = g_cache.erase(it);
         } else {

@@ -259,13 +259,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
 }
 
 // Plan record and local patch index of a work item.
+// Item `item` of a launch covers patch p of its plan; the item index itself
+// is the slot of the item in the launch's local-convolution scratch.
 __device__ __forceinline__ const PlanPtrs &item_plan(const Items &it, int item, int &p) {
     if (it.items) {
         const int2 v = it.items[item];
         p = v.y;
         return it.plans[v.x];
     }
-    p = item;
+    p = item + it.first;
     return it.plans[0];
 }
 
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(256) k_fwd_x(FwdXArgs a) {
     if constexpr (PATCH) {
         const PlanPtrs &P = item_plan(a.it, slab / a.nin, p);
         src = P.f;
-        outp = P.a1;
+        outp = a.it.a1;
         N = P.N;
         np = P.np;
     }
@@ -340,10 +342,11 @@ __global__ void __launch_bounds__(256) k_fwd_x(FwdXArgs a) {
     __syncthreads();
     fft_dif<LOG2M>(buf, nl, LS, 1, s_tw, false);
     C *out = (C *)outp;
-    if (SLAB) {  // layout [p][kx][zi][yi]: one contiguous nin x nin block per (p, kx)
+    if (SLAB) {  // layout [item][kx][zi][yi]: one contiguous nin x nin block per (item, kx)
+        const long q = slab / a.nin;  // scratch slot: the item within this launch
         for (int e = threadIdx.x; e < nl * MH; e += blockDim.x) {
             const int kx = e / nl, l = e % nl;
-            out[(((long)p * MH + kx) * a.nin + zi) * a.nin + line0 + l] = buf[l * LS + brev_bits(kx, LOG2M)];
+            out[((q * MH + kx) * a.nin + zi) * a.nin + line0 + l] = buf[l * LS + brev_bits(kx, LOG2M)];
         }
     } else {     // layout [slab][line][kx]
         for (int e = threadIdx.x; e < nl * MH; e += blockDim.x) {
@@ -512,7 +515,8 @@ __global__ void __launch_bounds__(256) k_slab(SlabArgs a) {
     load_twiddles<LOG2M>(s_tw, (const C *)a.tw);
     for (int e = threadIdx.x; e < M * P; e += blockDim.x) S[e] = Cx<R>::mk(0, 0);
     __syncthreads();
-    const C *in = (const C *)PP.a1 + ((long)p * MH + kx) * nin * nin;
+    const long q = blockIdx.x / MH;  // scratch slot
+    const C *in = (const C *)a.it.a1 + (q * MH + kx) * nin * nin;
     for (int e = threadIdx.x; e < nin * nin; e += blockDim.x) {
         const int zi = e / nin, yi = e % nin;
         S[yi * P + zi] = in[e];
@@ -544,7 +548,7 @@ __global__ void __launch_bounds__(256) k_slab(SlabArgs a) {
     // output positions (out_off + t) mod M, t < W: one wrapped range starting at pos0
     const int n1 = (pos0 + W <= M) ? W : M - pos0;  // columns pos0 .. pos0+n1-1, then 0 ..
     fft_dit<LOG2M>(S + pos0, W, 1, P, s_tw, true, n1, -(pos0 + n1));
-    C *out = (C *)PP.a4 + (long)p * a.nz * a.blk;
+    C *out = (C *)a.it.a4 + q * a.nz * a.blk;
     for (int e = threadIdx.x; e < a.nz * W; e += blockDim.x) {
         const int jz = e / W, yo = e % W, zo = a.zrow[jz];
         int pz = (a.out_off + zo) % M, py = (a.out_off + yo) % M;
@@ -786,7 +790,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_slab64(SlabArgs
         const int kx = unit % MH;
         int p;
         const PlanPtrs &PP = item_plan(a.it, unit / MH, p);
-        const C *in = (const C *)PP.a1 + ((long)p * MH + kx) * nin * nin;
+        const long q = unit / MH;  // scratch slot
+        const C *in = (const C *)a.it.a1 + (q * MH + kx) * nin * nin;
         // (zi, yi) of element e stepped incrementally (one division per thread)
         for (int e = threadIdx.x, zi = e / nin, yi = e - zi * nin; e < nin * nin; e += blockDim.x) {
             S[zi * P + yi] = in[e];
@@ -854,7 +859,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_slab64(SlabArgs
                 if (valid) line[t + 8 * k2] = v[k2];
         }
         __syncthreads();
-        C *out = (C *)PP.a4 + (long)p * a.nz * a.blk + kx * W;
+        C *out = (C *)a.it.a4 + q * a.nz * a.blk + kx * W;
         for (int e = threadIdx.x, jz = e / W, yo = e - jz * W; jz < a.nz; e += blockDim.x) {
             out[(long)jz * a.blk + yo] = S[rowoff[jz] + ((a.out_off + yo) & (M - 1))];
             yo += d_out_y;
@@ -990,7 +995,8 @@ __global__ void __launch_bounds__(64, 6) k_slab64r(SlabArgs a) {
         const int kx = unit % MH;
         int p;
         const PlanPtrs &PP = item_plan(a.it, unit / MH, p);
-        const float2 *in = (const float2 *)PP.a1 + ((long)p * MH + kx) * nin * nin;
+        const long q = unit / MH;  // scratch slot
+        const float2 *in = (const float2 *)a.it.a1 + (q * MH + kx) * nin * nin;
         float2 v[64];
         // forward y: thread c < nin takes z row c
         if (c < nin) {
@@ -1030,7 +1036,7 @@ __global__ void __launch_bounds__(64, 6) k_slab64r(SlabArgs a) {
             for (int i = 0; i < 64; ++i) row[i] = v[i];
         }
         __syncthreads();
-        float2 *out = (float2 *)PP.a4 + (long)p * a.nz * a.blk + kx * W;
+        float2 *out = (float2 *)a.it.a4 + q * a.nz * a.blk + kx * W;
         for (int e = threadIdx.x; e < a.nz * W; e += blockDim.x) {
             const int jz = e / W, yo = e - jz * W;
             out[(long)jz * a.blk + yo] = S[rowoff[jz] + ((a.out_off + yo) & (M - 1))];
@@ -1073,7 +1079,7 @@ __global__ void __launch_bounds__(256) k_fwd_x64(FwdXArgs a) {
     const int n = a.n, nin = n + 1, N = PP.N, np = PP.np;
     const int i2 = p % np, i1 = (p / np) % np, i0 = p / (np * np);
     const TF *f = (const TF *)PP.f;
-    C *out = (C *)PP.a1 + (long)p * MH * nin * nin;
+    C *out = (C *)a.it.a1 + (long)blockIdx.x * MH * nin * nin;  // scratch slot = item
     const C *tw = (const C *)a.tw;  // M/2 entries; extend by w^(j+32) = -w^j
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
         C w = tw[j & 31];
@@ -1189,7 +1195,7 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
         if (j >= M / 2) { w.x = -w.x; w.y = -w.y; }
         tw[j] = w;
     }
-    const C *in = (const C *)PP.a4 + ((long)p * a.nz + jz) * a.blk;
+    const C *in = (const C *)a.it.a4 + ((long)(blockIdx.x / a.nz) * a.nz + jz) * a.blk;  // scratch slot = item
     // stage the contiguous block with one TMA bulk copy
     __shared__ unsigned long long bar;
     const unsigned bytes = (unsigned)(a.blk * sizeof(C));
@@ -1317,7 +1323,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 8 : 4) k_inv_x64(InvXPAr
         if (j >= M / 2) { w.x = -w.x; w.y = -w.y; }
         tw[j] = w;
     }
-    const C *in = (const C *)PP.a4 + ((long)p * a.nz + jz) * a.blk;
+    const C *in = (const C *)a.it.a4 + ((long)(blockIdx.x / a.nz) * a.nz + jz) * a.blk;  // scratch slot = item
     // stage the contiguous block with one TMA bulk copy
     __shared__ unsigned long long bar;
     const unsigned bytes = (unsigned)(a.blk * sizeof(C));
@@ -2354,7 +2360,9 @@ cudaError_t launch_moments(const mlc_plan_s *pl, const Items &it, cudaStream_t s
     return cudaGetLastError();
 }
 
-cudaError_t launch_patch_conv(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
+// The three local-convolution launches for one launch group of items (its
+// scratch in it.a1 / it.a4).
+cudaError_t launch_patch_conv_group(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
     const Geom &g = pl->g;
     const bool f32 = g.f32in;
     if (g.conv == CONV_F32) {  // split tiers: FP32 (tables tw_f, khat_f)
@@ -2368,6 +2376,21 @@ cudaError_t launch_patch_conv(const mlc_plan_s *pl, const Items &it, cudaStream_
         if (g.log2M == 6) return run_patch_conv_t<6, double>(pl, it, f32, pl->tw, st);
     }
     return cudaErrorInvalidValue;
+}
+
+// Local convolutions of all items, in launch groups of g.chunk items that
+// reuse one scratch (stream order keeps the groups apart).
+cudaError_t launch_patch_conv(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
+    const int chunk = pl->g.chunk;
+    for (int c0 = 0; c0 < it.nitems; c0 += chunk) {
+        Items ic = it;
+        ic.nitems = it.nitems - c0 < chunk ? it.nitems - c0 : chunk;
+        if (it.items) ic.items = it.items + c0;
+        else ic.first = it.first + c0;
+        const cudaError_t e = launch_patch_conv_group(pl, ic, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // Lagrange weights of I^H on the nodes k0-b .. k0+b+1 at t = k0 + r/4 (R4 reading).

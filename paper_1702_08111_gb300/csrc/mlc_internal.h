@@ -56,7 +56,17 @@ struct Geom {
                                      // (M/2+1) W rounded up to a multiple of 16 bytes
     int plane_n;                     // (N+1)^2 nodes per face plane
     long n_planes_total;             // 3 (np+1) (N+1)^2
+    int chunk;                       // patches per launch group of the local convolutions
+    size_t scr_a1, scr_a4;           // scratch bytes per patch: x-transformed charges, slab outputs
 };
+// Local-convolution scratch for `items` patches: the a1 part, then (from a
+// 256-byte boundary) the a4 part.
+inline size_t conv_scratch_a4_offset(const Geom &g, long items) {
+    return ((size_t)items * g.scr_a1 + 255) & ~(size_t)255;
+}
+inline size_t conv_scratch_bytes(const Geom &g, long items) {
+    return conv_scratch_a4_offset(g, items) + (size_t)items * g.scr_a4;
+}
 
 // Per-plan pointers and sizes read by the per-patch kernels.  A single solve
 // uses its plan's record; a batch passes one record per plan plus an item
@@ -64,7 +74,6 @@ struct Geom {
 // of every problem in the batch.
 struct PlanPtrs {
     const void *f;        // charge, N^3 (FP64 or FP32 by tier)
-    void *a1, *a4;        // local-convolution spectra workspace
     void *cl, *fp;        // local fields on the coarse lattice / alpha face planes
     const void *khat;     // patch kernel spectrum octant (working precision)
     const void *momw;     // 1D moment weights a_k(m) = w_m q_k(2m/n - 1), P x (n+1), FP64
@@ -81,11 +90,17 @@ struct PlanPtrs {
     int *err;             // the plan's error word
 };
 
+// The items of one launch.  Item q covers patch items[q].y of plan record
+// items[q].x (or, without an item table, patch first + q of plan record 0),
+// and owns slot q of the local-convolution scratch a1 / a4 of the launch.
 struct Items {
-    const int2 *items;    // (plan slot, local patch); nullptr: plan 0, item = patch
+    const int2 *items;    // (plan slot, local patch); nullptr: plan 0, item = first + index
     const PlanPtrs *plans;
     int nitems;
     int persist = 0;      // 1: launch the slab kernel persistently (one wave of resident CTAs)
+    int first = 0;        // patch of item 0 when there is no item table
+    void *a1 = nullptr;   // scratch: x-transformed charges, scr_a1 bytes per item
+    void *a4 = nullptr;   // scratch: slab outputs, scr_a4 bytes per item
 };
 
 }  // namespace mlc
@@ -119,7 +134,9 @@ struct mlc_plan_s {
     void *sinm;              // (n-1) x n/2 half DST-I matrix sin(pi k t / n), fine precision
     void *lam;               // (n-1)^3 (2/n)^3 h^2 / stencil eigenvalue, fine precision
     // workspace (device)
-    void *buf0, *buf1;       // ping-pong spectra for the patch convolutions (complex FP64 / FP32)
+    void *scratch = nullptr;       // own local-convolution scratch, min(chunk, NP) patches (a1
+                                   // then a4), allocated by the first solve that needs it
+    void *user_scratch = nullptr;  // caller-owned scratch (mlc_plan_set_scratch), if any
     void *cl;                // NP x nc^3 local fields on the coarse lattice of the field box (FP32 / double-float)
     void *fpl;               // NP x 3 npa x wa^2 local fields on the face planes inside alpha (FP32 / double-float)
     double *mom;             // NP x npad
@@ -136,9 +153,12 @@ struct mlc_plan_s {
     std::vector<void *> owned;  // device allocations to free
     mlc::PlanPtrs *dptrs = nullptr;  // device copy of this plan's PlanPtrs (f, phi filled per solve)
     mlc::PlanPtrs hptrs{};
-    // optional per-launch timing of the last solve (CUDA events on the solve stream)
+    // optional per-launch timing of the last solve (CUDA events on the solve
+    // stream): (slot, event) marks in launch order; a launch's time runs from
+    // its mark to the next one
     int timing = 0;
-    cudaEvent_t ev[mlc::kTimedLaunches + 1] = {};
+    mutable std::vector<cudaEvent_t> ev_pool;
+    mutable std::vector<std::pair<int, cudaEvent_t>> marks;
     // side stream of a solve: moments, then residuals, beside the main chain
     cudaStream_t side = nullptr;
     cudaEvent_t fork[4] = {};
@@ -184,6 +204,47 @@ cudaError_t basis_direct_sum(const double *G1, int L_table, const int *pts, int 
 
 namespace mlc {
 inline void mark(const mlc_plan_s *pl, int k, cudaStream_t st) {
-    if (pl && pl->timing && !g_capturing) cudaEventRecord(pl->ev[k], st);
+    if (!pl || !pl->timing || g_capturing) return;
+    const size_t i = pl->marks.size();
+    if (i >= pl->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        pl->ev_pool.push_back(e);
+    }
+    cudaEventRecord(pl->ev_pool[i], st);
+    pl->marks.push_back({k, pl->ev_pool[i]});
 }
+}  // namespace mlc
+
+namespace mlc {
+// ---- batched launches (batch.cu): shared by mlc_batch_solve and the server ----
+// Problems grouped by patch geometry and tier; record slot j (the j-th
+// PlanPtrs record) is problem order[j] of the call, in group plan_group[j].
+struct BatchLayout {
+    struct Group {
+        const mlc_plan_s *rep;  // a plan of the group (its geometry sizes the launches)
+        int item0, nitems;      // the group's range of the item table
+        void *a1 = nullptr, *a4 = nullptr;  // the group's local-convolution scratch
+                                            // (min(chunk, nitems) patches; set by the owner)
+    };
+    std::vector<int> order, plan_group;
+    std::vector<Group> groups;
+    std::vector<int2> items;     // (record slot, local patch), group by group
+    std::vector<PlanPtrs> recs;  // per record slot: the plan's pointers with its f and phi
+};
+// Streams and events of one batch launch sequence (created on first use).
+struct BatchStreams {
+    std::vector<cudaStream_t> conv, aux, side;
+    std::vector<cudaEvent_t> ev;
+    cudaError_t ensure(int ngroups, int nbranches);
+    void release();
+};
+bool same_patch_geometry(const Geom &a, const Geom &b);
+void batch_layout(int count, const mlc_plan_t *plans, const void *const *f, void *const *phi, BatchLayout &L);
+// Enqueue every launch of a batch (all groups, all problems) after earlier
+// work on st; st waits for all of it.  d_items / d_recs: device copies of
+// L.items / L.recs.  plans: the problems in call order.
+cudaError_t batch_enqueue(const std::vector<mlc_plan_t> &plans, const BatchLayout &L, const int2 *d_items,
+                          const PlanPtrs *d_recs, BatchStreams &S, int branches, int persist,
+                          cudaStream_t st);
 }  // namespace mlc

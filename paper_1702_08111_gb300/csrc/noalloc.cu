@@ -8,7 +8,9 @@
 // the local-convolution kernels (the patch spectra between the forward and the
 // inverse transforms, the largest scratch of a solve) from a file-scope static
 // device array instead of the plan's workspace, and it calls no allocating
-// routine at all.
+// routine at all.  Every step runs on the caller's stream (no side stream, so
+// the moments and residuals do not overlap the convolution chain as they do in
+// mlc_solve).
 //
 // The array is kNoAllocScratchBytes (64 MiB) on every GPU that loads this
 // library and is held until the process exits.  Every call shares it and
@@ -18,6 +20,7 @@
 // race on the array and must not be issued.  The first call on a device
 // resolves the array's device address (cudaGetSymbolAddress) with that device
 // current; make that first call before any stream capture begins.
+#include <algorithm>
 #include <mutex>
 
 #include "mlc_internal.h"
@@ -29,8 +32,9 @@ namespace {
 constexpr size_t kNoAllocScratchBytes = 64ull << 20;
 constexpr int kMaxDevices = 64;
 
-// Scratch of the local convolutions: the x-transformed charges of every patch
-// followed by the slab outputs (the layouts of the plan's own workspace).
+// Scratch of the local convolutions for one launch group of patches (the
+// plan's group size, or all its patches if fewer): the x-transformed charges
+// followed by the slab outputs (the layout of the plan's own scratch).
 static __device__ __align__(256) unsigned char g_scratch[kNoAllocScratchBytes];
 // The per-patch kernels read their plan record from device memory.
 static __device__ __align__(256) PlanPtrs g_record;
@@ -44,23 +48,12 @@ std::mutex g_addr_mu;
 
 __global__ void k_store_record(PlanPtrs *dst, PlanPtrs rec) { *dst = rec; }
 
-// Bytes of the two spectra buffers for this plan (as the plan sizes them),
-// each rounded up to 256 bytes.
-size_t scratch_bytes(const Geom &G, size_t *a1_bytes) {
-    const size_t rb = conv_real_bytes(G.tier);
-    const size_t A1 = (size_t)G.NP * G.nb * G.nb * G.Mh * 2 * rb;
-    const size_t A4 = (size_t)G.NP * G.nzr * G.a4blk * 2 * rb;
-    const size_t a1r = (A1 + 255) & ~(size_t)255;
-    *a1_bytes = a1r;
-    return a1r + ((A4 + 255) & ~(size_t)255);
-}
-
 }  // namespace
 
 extern "C" mlc_status mlc_solve_noalloc(mlc_plan_t pl, const void *f, void *phi, void *stream) {
     if (!pl || !f || !phi || f == phi) return MLC_ERR_INVALID_ARG;
-    size_t a1_bytes = 0;
-    if (scratch_bytes(pl->g, &a1_bytes) > kNoAllocScratchBytes) return MLC_ERR_INVALID_ARG;
+    const long items = std::min<long>(pl->g.chunk, pl->g.NP);  // patches per launch group
+    if (conv_scratch_bytes(pl->g, items) > kNoAllocScratchBytes) return MLC_ERR_INVALID_ARG;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MLC_ERR_CUDA;
     if (dev != pl->device) return MLC_ERR_INVALID_ARG;
@@ -80,11 +73,11 @@ extern "C" mlc_status mlc_solve_noalloc(mlc_plan_t pl, const void *f, void *phi,
     PlanPtrs rec = pl->hptrs;
     rec.f = f;
     rec.phi = (double *)phi;
-    rec.a1 = addr.scratch;
-    rec.a4 = addr.scratch + a1_bytes;
     k_store_record<<<1, 1, 0, st>>>(addr.record, rec);
     if (cudaGetLastError() != cudaSuccess) return MLC_ERR_CUDA;
-    const Items it{nullptr, addr.record, pl->g.NP};
+    Items it{nullptr, addr.record, pl->g.NP};
+    it.a1 = addr.scratch;
+    it.a4 = addr.scratch + conv_scratch_a4_offset(pl->g, items);
     if (launch_moments(pl, it, st) != cudaSuccess) return MLC_ERR_CUDA;
     if (launch_patch_conv(pl, it, st) != cudaSuccess) return MLC_ERR_CUDA;
     if (launch_resid(pl, it, st) != cudaSuccess) return MLC_ERR_CUDA;

@@ -1,5 +1,6 @@
 // Host side of the MLC library: parameter checks, plan geometry and index
 // tables (Sec. 4 regions), plan-time tables, the solve sequence and the C ABI.
+#include <algorithm>
 #include <array>
 #include <cmath>
 #include <cstring>
@@ -217,6 +218,12 @@ mlc_status derive_geometry(const mlc_params &pp, Geom &g) {
         const int cb = 2 * conv_real_bytes(g.tier);         // bytes per complex entry
         const int per16 = 16 / cb;                          // entries per 16 bytes
         g.a4blk = ((g.Mh * g.W + per16 - 1) / per16) * per16;
+    }
+    {
+        const size_t cb = 2 * (size_t)conv_real_bytes(g.tier);
+        g.scr_a1 = (size_t)g.Mh * g.nb * g.nb * cb;
+        g.scr_a4 = (size_t)g.nzr * g.a4blk * cb;
+        g.chunk = pp.conv_chunk > 0 ? pp.conv_chunk : 1024;
     }
     g.wa = g.n + 2 * g.ga + 1;
     g.wbx = g.n + 2 * g.gb + 1;
@@ -501,8 +508,7 @@ mlc_status get_dgf(int device, int Q, int nD, int zeta, int L, const double **pt
 void free_plan(mlc_plan_s *pl) {
     if (!pl) return;
     for (void *p : pl->owned) cudaFree(p);
-    for (auto &e : pl->ev)
-        if (e) cudaEventDestroy(e);
+    for (auto &e : pl->ev_pool) cudaEventDestroy(e);
     for (auto &e : pl->fork)
         if (e) cudaEventDestroy(e);
     if (pl->side) cudaStreamDestroy(pl->side);
@@ -530,7 +536,7 @@ mlc_status mlc_params_init(mlc_params *p, int N, int n, int s, int P, int Q) {
     if (!p) return MLC_ERR_INVALID_ARG;
     p->N = N; p->n = n; p->s = s; p->C = 4; p->P = P; p->Q = Q;
     p->g_beta = -1; p->b = -1; p->tier = MLC_TIER_FP64; p->mode = MLC_MODE_MLC;
-    p->dgf_nD = -1; p->dgf_zeta = -1;
+    p->dgf_nD = -1; p->dgf_zeta = -1; p->conv_chunk = -1;
     return MLC_OK;
 }
 
@@ -579,18 +585,14 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
             }
             TRY(dev_upload(pl, &pl->tw_c_df, tf));
         }
-        const size_t NP = G.NP, nb = G.nb, W = G.W, M = G.M, Mh = G.Mh;
-        (void)M;
-        (void)W;
+        const size_t NP = G.NP;
         const size_t rb = conv_real_bytes(G.tier);
-        const size_t A1 = NP * nb * nb * Mh, A4 = NP * (size_t)G.nzr * G.a4blk;
-        char *b0 = nullptr, *b1 = nullptr, *bc = nullptr, *bf = nullptr;
-        TRY(dev_alloc(pl, &b0, A1 * 2 * rb));   // [p][kx][zi][yi]
-        TRY(dev_alloc(pl, &b1, A4 * 2 * rb));   // [p][z row][kx][yo]
+        // the local-convolution scratch (a1 [item][kx][zi][yi], a4 [item][z
+        // row][kx][yo] for one launch group) is allocated by the first solve
+        // that needs it, unless the caller provides one (mlc_plan_set_scratch)
+        char *bc = nullptr, *bf = nullptr;
         TRY(dev_alloc(pl, &bc, NP * (size_t)G.nc * G.nc * G.nc * rb));
         TRY(dev_alloc(pl, &bf, NP * 3 * (size_t)G.npa * G.wa * G.wa * rb));
-        pl->buf0 = b0;
-        pl->buf1 = b1;
         pl->cl = bc;
         pl->fpl = bf;
         if (G.conv == CONV_DF) {
@@ -652,8 +654,6 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
         PlanPtrs &h = pl->hptrs;
         h.f = nullptr;
         h.phi = nullptr;
-        h.a1 = pl->buf0;
-        h.a4 = pl->buf1;
         h.cl = pl->cl;
         h.fp = pl->fpl;
         h.khat = G.conv == CONV_F32 ? (const void *)pl->khat_f
@@ -713,15 +713,40 @@ mlc_status mlc_plan_info(mlc_plan_t plan, int *o) {
     return MLC_OK;
 }
 
+mlc_status mlc_plan_scratch_bytes(mlc_plan_t pl, size_t *bytes) {
+    if (!pl || !bytes) return MLC_ERR_INVALID_ARG;
+    *bytes = conv_scratch_bytes(pl->g, std::min<long>(pl->g.chunk, pl->g.NP));
+    return MLC_OK;
+}
+
+mlc_status mlc_plan_set_scratch(mlc_plan_t pl, void *scratch, size_t bytes) {
+    if (!pl) return MLC_ERR_INVALID_ARG;
+    if (scratch) {
+        size_t need = 0;
+        mlc_plan_scratch_bytes(pl, &need);
+        if (bytes < need || ((uintptr_t)scratch & 255)) return MLC_ERR_INVALID_ARG;
+    }
+    pl->user_scratch = scratch;
+    return MLC_OK;
+}
+
 mlc_status mlc_solve(mlc_plan_t pl, const void *f, void *phi, void *stream) {
     if (!pl || !f || !phi || f == phi) return MLC_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
+    if (!pl->user_scratch && !pl->scratch) {  // first solve: the plan's own scratch
+        char *sc = nullptr;
+        TRY(dev_alloc(pl, &sc, conv_scratch_bytes(pl->g, std::min<long>(pl->g.chunk, pl->g.NP))));
+        pl->scratch = sc;
+    }
+    void *scr = pl->user_scratch ? pl->user_scratch : pl->scratch;
     if (pl->hptrs.f != f || pl->hptrs.phi != phi) {
         TRY_CUDA(launch_set_ptrs(pl->dptrs, f, (double *)phi, st));
         pl->hptrs.f = f;
         pl->hptrs.phi = (double *)phi;
     }
-    const Items it{nullptr, pl->dptrs, pl->g.NP};
+    Items it{nullptr, pl->dptrs, pl->g.NP};
+    it.a1 = scr;
+    it.a4 = (char *)scr + conv_scratch_a4_offset(pl->g, std::min<long>(pl->g.chunk, pl->g.NP));
     if (!pl->timing) {
         // Two streams: the moments (they read only f) and, once the local
         // fields exist, the face-plane residuals run on a side stream beside
@@ -750,9 +775,10 @@ mlc_status mlc_solve(mlc_plan_t pl, const void *f, void *phi, void *stream) {
         return MLC_OK;
     }
     // per-launch timing: the same launches in sequence on one stream
+    pl->marks.clear();
     mark(pl, 0, st);
     TRY_CUDA(launch_moments(pl, it, st));
-    TRY_CUDA(launch_patch_conv(pl, it, st));       // slots 1-3
+    TRY_CUDA(launch_patch_conv(pl, it, st));       // slots 1-3 (per launch group)
     mark(pl, 4, st);
     TRY_CUDA(launch_resid(pl, it, st));
     mark(pl, 5, st);
@@ -800,17 +826,21 @@ mlc_status mlc_plan_status(mlc_plan_t pl) {
 
 mlc_status mlc_debug_set_timing(mlc_plan_t pl, int enable) {
     if (!pl) return MLC_ERR_INVALID_ARG;
-    if (enable && !pl->ev[0])
-        for (auto &e : pl->ev) TRY_CUDA(cudaEventCreate(&e));
     pl->timing = enable ? 1 : 0;
+    pl->marks.clear();
     return MLC_OK;
 }
 
 mlc_status mlc_debug_timing(mlc_plan_t pl, float *ms, int count) {
-    if (!pl || !ms || count < kTimedLaunches || !pl->timing) return MLC_ERR_INVALID_ARG;
-    TRY_CUDA(cudaEventSynchronize(pl->ev[kTimedLaunches]));
-    for (int k = 0; k < kTimedLaunches; ++k)
-        TRY_CUDA(cudaEventElapsedTime(&ms[k], pl->ev[k], pl->ev[k + 1]));
+    if (!pl || !ms || count < kTimedLaunches || !pl->timing || pl->marks.size() < 2) return MLC_ERR_INVALID_ARG;
+    TRY_CUDA(cudaEventSynchronize(pl->marks.back().second));
+    for (int k = 0; k < kTimedLaunches; ++k) ms[k] = 0.f;
+    for (size_t i = 0; i + 1 < pl->marks.size(); ++i) {
+        float t = 0.f;
+        TRY_CUDA(cudaEventElapsedTime(&t, pl->marks[i].second, pl->marks[i + 1].second));
+        const int k = pl->marks[i].first;
+        if (k >= 0 && k < kTimedLaunches) ms[k] += t;
+    }
     return MLC_OK;
 }
 

@@ -26,7 +26,7 @@ EXPORTED = [
     "mlc_debug_stage_bytes", "mlc_debug_export", "mlc_plan_info", "mlc_server_create",
     "mlc_server_destroy", "mlc_server_enqueue", "mlc_server_wait", "mlc_status_string",
     "mlc_debug_set_timing", "mlc_debug_timing", "mlc_solve_noalloc", "mlc_plan_status",
-    "mlc_debug_batch_choice",
+    "mlc_debug_batch_choice", "mlc_plan_scratch_bytes", "mlc_plan_set_scratch",
 ]
 LAUNCH_NAMES = ["moments", "conv_fwd_x", "conv_slab", "conv_inv_x", "resid", "assemble",
                 "coarse_fwd_x", "coarse_fwd_y", "coarse_z_kernel", "coarse_inv_y", "coarse_inv_x",
@@ -41,7 +41,8 @@ class MLCError(RuntimeError):
 
 class mlc_params(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int) for k in
-                ("N", "n", "s", "C", "P", "Q", "g_beta", "b", "tier", "mode", "dgf_nD", "dgf_zeta")]
+                ("N", "n", "s", "C", "P", "Q", "g_beta", "b", "tier", "mode", "dgf_nD", "dgf_zeta",
+                 "conv_chunk")]
 
 
 class mlc_request(ctypes.Structure):
@@ -72,6 +73,8 @@ def load_library(path: str = LIB_PATH):
     lib.mlc_plan_create_ex.argtypes = [ctypes.POINTER(mlc_params), ctypes.POINTER(vp)]
     lib.mlc_plan_destroy.argtypes = [vp]
     lib.mlc_plan_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    lib.mlc_plan_scratch_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    lib.mlc_plan_set_scratch.argtypes = [vp, vp, ctypes.c_size_t]
     lib.mlc_solve.argtypes = [vp, vp, vp, vp]
     lib.mlc_solve_host.argtypes = [vp, vp, vp, vp]
     lib.mlc_solve_noalloc.argtypes = [vp, vp, vp, vp]
@@ -109,10 +112,11 @@ def _check(rc: int, what: str):
 
 
 def make_params(N, n, s, P=4, Q=4, C=4, g_beta=-1, b=-1, tier=MLC_TIER_FP64, mode=MLC_MODE_MLC,
-                dgf_nD=-1, dgf_zeta=-1) -> mlc_params:
+                dgf_nD=-1, dgf_zeta=-1, conv_chunk=-1) -> mlc_params:
     p = mlc_params()
     load_library().mlc_params_init(ctypes.byref(p), N, n, s, P, Q)
     p.C, p.g_beta, p.b, p.tier, p.mode, p.dgf_nD, p.dgf_zeta = C, g_beta, b, tier, mode, dgf_nD, dgf_zeta
+    p.conv_chunk = conv_chunk
     return p
 
 
@@ -182,6 +186,20 @@ class Plan:
         v = ctypes.c_size_t()
         _check(load_library().mlc_plan_workspace_bytes(self._h, ctypes.byref(v)), "workspace")
         return v.value
+
+    def scratch_bytes(self) -> int:
+        """Bytes of local-convolution scratch a solve needs (mlc_plan_scratch_bytes)."""
+        v = ctypes.c_size_t()
+        _check(load_library().mlc_plan_scratch_bytes(self._h, ctypes.byref(v)), "scratch_bytes")
+        return v.value
+
+    def set_scratch(self, buf=None):
+        """Use caller-owned device memory (a CUDA tensor, kept alive by the caller)
+        as the local-convolution scratch; None returns to the plan's own."""
+        ptr = None if buf is None else ctypes.c_void_p(buf.data_ptr())
+        nb = 0 if buf is None else buf.numel() * buf.element_size()
+        _check(load_library().mlc_plan_set_scratch(self._h, ptr, ctypes.c_size_t(nb)), "set_scratch")
+        self._scratch = buf
 
     def _check_tensors(self, f, phi):
         import torch

@@ -1,17 +1,28 @@
 """GPU tests of the batched entry point and the continuous-batching server.
 
-Batch: the per-patch steps of several problems share launches (captured in a
-CUDA graph); each result must equal the problem's standalone solve exactly
-(same kernels, same tables).  Server: each result is the same alone and in
-the mix, within the stated tolerance (exact equality is expected and
-checked; the bar is 1e-12 relative for FP64 and 1e-6 for the split tier).
+Batch: problems of several patch geometries and tiers in one mlc_batch_solve
+call (per-patch steps of each geometry group share launches, captured in a
+CUDA graph).  Each result must equal the problem's standalone solve exactly
+(same kernels, same tables) and match the CPU oracle: relative max-norm
+<= 1e-12 for the FP64-accurate tiers, <= 1e-6 for the split tiers.  Server:
+requests of both operators and all tiers are merged into batched launches;
+each result is the same alone and in the mix, and matches the oracle within
+the same tolerances.
 """
 import numpy as np
 import pytest
 
+from oracle import mlc_oracle as O
 from paper_1702_08111_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
+
+FP64, SPLIT, DF, SPLIT_DF = 0, 1, 2, 3
+F32_TIERS = (SPLIT, SPLIT_DF)
+
+
+def tol_of(tier):
+    return 1e-6 if tier in F32_TIERS else 1e-12
 
 
 @pytest.fixture(scope="module")
@@ -21,19 +32,41 @@ def torch_cuda():
     return torch
 
 
-def _charge(torch, N, seed, f32=False):
-    f = I.sample_bumps(N, I.draw_bumps(1 + seed % 5, 900 + seed))
-    t = torch.from_numpy(f.astype(np.float32) if f32 else f).cuda()
-    return t
+@pytest.fixture(scope="module")
+def G():
+    return {4: O.dgf_octant(4, 128, 2), 6: O.dgf_octant(6, 128, 2)}
 
 
-@pytest.mark.parametrize("tier", [0, 1, 2, 3])
+_ORACLE = {}
+
+
+def oracle_phi(G, N, n, s, Q, seed, nb):
+    """Oracle solve of the seeded bump charge (FP64 samples; the split tiers
+    solve the same samples rounded to FP32)."""
+    key = (N, n, s, Q, seed, nb)
+    if key not in _ORACLE:
+        f = I.sample_bumps(N, I.draw_bumps(nb, seed))
+        _ORACLE[key] = O.solve_open(O.Params(N=N, n=n, s=s, Q=Q), f, G1=G[Q])
+    return _ORACLE[key]
+
+
+def charge(torch, N, seed, nb, tier):
+    f = I.sample_bumps(N, I.draw_bumps(nb, seed))
+    return torch.from_numpy(f.astype(np.float32) if tier in F32_TIERS else f).cuda()
+
+
+def relmax(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+@pytest.mark.parametrize("tier", [FP64, SPLIT, DF, SPLIT_DF])
 def test_batch_equals_standalone(torch_cuda, tier):
     from paper_1702_08111_gb300 import mlc
     torch = torch_cuda
     sides = [32, 64, 48, 96, 32, 80]
     plans = [mlc.Plan(N, 16, 16, 4, 4, tier=tier) for N in sides]
-    fs = [_charge(torch, N, k, f32=(tier in (1, 3))) for k, N in enumerate(sides)]
+    fs = [charge(torch, N, 900 + k, 1 + k % 5, tier) for k, N in enumerate(sides)]
     alone = [p.solve(f).clone() for p, f in zip(plans, fs)]
     phis = [torch.empty_like(a) for a in alone]
     mlc.batch_solve(plans, fs, phis)
@@ -47,62 +80,90 @@ def test_batch_equals_standalone(torch_cuda, tier):
     assert ch["branches"] in (1, 4, 16)
 
 
-def test_batch_small_patches_and_errors(torch_cuda):
+# config 4's shape: uneven problems, patch 8 for side 32, 16 otherwise,
+# support = patch side, Q = 4, 1..16 bumps per problem
+MIXED = [(32, 8, 8, 4001, 3), (64, 16, 16, 4002, 9), (48, 16, 16, 4003, 1), (96, 16, 16, 4004, 16),
+         (32, 8, 8, 4005, 7), (64, 16, 16, 4006, 5)]
+
+
+@pytest.mark.parametrize("tier", [FP64, SPLIT, DF, SPLIT_DF])
+def test_batch_mixed_geometry_vs_oracle(torch_cuda, G, tier):
+    """n = 8 and n = 16 problems (two geometry groups) in one batch call:
+    every problem against the oracle element by element, and bit-identical
+    to its standalone solve."""
     from paper_1702_08111_gb300 import mlc
     torch = torch_cuda
-    plans = [mlc.Plan(32, 8, 8, 4, 4), mlc.Plan(40, 8, 8, 4, 4)]
-    fs = [_charge(torch, 32, 1), _charge(torch, 40, 2)]
+    plans = [mlc.Plan(N, n, s, 4, 4, tier=tier) for N, n, s, _, _ in MIXED]
+    fs = [charge(torch, N, seed, nb, tier) for N, _, _, seed, nb in MIXED]
+    phis = [torch.empty((N,) * 3, dtype=torch.float64, device="cuda") for N, *_ in MIXED]
+    mlc.batch_solve(plans, fs, phis)
+    torch.cuda.synchronize()
+    for p in plans:
+        p.status()
+    for (N, n, s, seed, nb), p, f, phi in zip(MIXED, plans, fs, phis):
+        ref = oracle_phi(G, N, n, s, 4, seed, nb)
+        err = relmax(phi.cpu().numpy(), ref)
+        assert err <= tol_of(tier), (N, n, tier, err)
+        assert torch.equal(p.solve(f), phi)
+
+
+def test_batch_mixed_tiers_and_errors(torch_cuda):
+    """Problems of different tiers share one call (one group per tier); a plan
+    may appear only once per call."""
+    from paper_1702_08111_gb300 import mlc
+    torch = torch_cuda
+    specs = [(32, FP64), (40, SPLIT), (32, DF), (48, SPLIT_DF)]
+    plans = [mlc.Plan(N, 8, 8, 4, 4, tier=t) for N, t in specs]
+    fs = [charge(torch, N, 300 + k, 2, t) for k, (N, t) in enumerate(specs)]
     alone = [p.solve(f).clone() for p, f in zip(plans, fs)]
     phis = [torch.empty_like(a) for a in alone]
     mlc.batch_solve(plans, fs, phis)
     torch.cuda.synchronize()
     for a, b in zip(alone, phis):
         assert torch.equal(a, b)
-    other = mlc.Plan(64, 16, 16, 4, 4)
-    with pytest.raises(mlc.MLCError) as e:
-        mlc.batch_solve([plans[0], other], [fs[0], _charge(torch, 64, 3)],
-                        [phis[0], torch.empty((64,) * 3, dtype=torch.float64, device="cuda")])
-    assert e.value.status == 1
     with pytest.raises(mlc.MLCError) as e:
         mlc.batch_solve([plans[0], plans[0]], [fs[0], fs[0]], [phis[0], torch.empty_like(phis[0])])
     assert e.value.status == 1
 
 
-def test_server_results_same_alone_and_in_mix(torch_cuda):
+# (N, Q, tier, bumps): both operators, all tiers; oracle-sized problems first
+SERVE = [(64, 4, FP64, 3), (48, 6, SPLIT, 5), (64, 6, DF, 2), (32, 4, SPLIT_DF, 1), (48, 4, DF, 4),
+         (64, 4, SPLIT, 6), (48, 6, FP64, 2), (64, 6, SPLIT_DF, 8),
+         (96, 4, SPLIT_DF, 7), (80, 4, DF, 3), (112, 6, FP64, 2), (96, 6, SPLIT, 4)]
+
+
+def test_server_results_same_alone_and_in_mix(torch_cuda, G):
     from paper_1702_08111_gb300 import mlc
     torch = torch_cuda
     reqs = []
-    for k, (N, Q, tier) in enumerate([(64, 4, 0), (48, 6, 1), (96, 4, 3), (64, 6, 2), (32, 4, 0),
-                                      (80, 4, 2), (64, 4, 1), (48, 4, 0), (112, 6, 0), (64, 4, 3)]):
-        f = _charge(torch, N, 20 + k, f32=(tier in (1, 3)))
-        reqs.append((N, Q, tier, f))
+    for k, (N, Q, tier, nb) in enumerate(SERVE):
+        reqs.append((N, Q, tier, nb, 20 + k, charge(torch, N, 20 + k, nb, tier)))
     srv = mlc.Server(64 << 30, max_batch=4)
     outs, tickets = [], []
-    for N, Q, tier, f in reqs:
+    for N, Q, tier, nb, seed, f in reqs:
         phi = torch.empty((N,) * 3, dtype=torch.float64, device="cuda")
         outs.append(phi)
         tickets.append(srv.enqueue(f, phi, N, 16, 16, 4, Q, tier=tier))
-    lat = []
     for t in tickets:
         st, l, q = srv.wait(t, 120000)
         assert st == 0
         assert l >= q >= 0
-        lat.append(l)
     srv.close()
-    for (N, Q, tier, f), phi in zip(reqs, outs):
+    for (N, Q, tier, nb, seed, f), phi in zip(reqs, outs):
         alone = mlc.Plan(N, 16, 16, 4, Q, tier=tier).solve(f)
         torch.cuda.synchronize()
-        tol = 1e-12 if tier in (0, 2) else 1e-6
-        err = float((phi - alone).abs().max() / alone.abs().max())
-        assert err <= tol
         assert torch.equal(phi, alone)
+        if N <= 64:  # oracle-sized requests: against the oracle
+            ref = oracle_phi(G, N, 16, 16, Q, seed, nb)
+            err = relmax(phi.cpu().numpy(), ref)
+            assert err <= tol_of(tier), (N, Q, tier, err)
 
 
 def test_server_admission_and_timeout(torch_cuda):
     from paper_1702_08111_gb300 import mlc
     torch = torch_cuda
     srv = mlc.Server(1 << 20, max_batch=2)  # 1 MiB: nothing fits
-    f = _charge(torch, 64, 5)
+    f = charge(torch, 64, 5, 2, FP64)
     phi = torch.empty_like(f)
     with pytest.raises(mlc.MLCError) as e:
         srv.enqueue(f, phi, 64, 16, 16, 4, 4)
@@ -111,3 +172,24 @@ def test_server_admission_and_timeout(torch_cuda):
         srv.wait(12345, 20)  # never issued: the wait runs out
     assert e.value.status == 6
     srv.close()
+
+
+def test_caller_scratch_and_small_launch_groups(torch_cuda):
+    """A plan solving with caller-owned scratch, and with local convolutions
+    in launch groups of 5 patches (a ragged last group), equals the default
+    solve bit for bit."""
+    from paper_1702_08111_gb300 import mlc
+    torch = torch_cuda
+    f = charge(torch, 64, 77, 4, FP64)
+    ref = mlc.Plan(64, 16, 16, 4, 4).solve(f).clone()
+    p = mlc.Plan(64, 16, 16, 4, 4, conv_chunk=5)
+    buf = torch.empty(p.scratch_bytes() // 8 + 64, dtype=torch.float64, device="cuda")
+    p.set_scratch(buf)
+    out = p.solve(f)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    with pytest.raises(mlc.MLCError) as e:
+        p.set_scratch(buf[:8])
+    assert e.value.status == 1
+    p.set_scratch(None)
+    assert torch.equal(p.solve(f), ref)
