@@ -2,10 +2,12 @@
 """Benchmark: two-level MLC solve throughput (Mpoints/s) on synthetic bump charges.
 
 One step = one full solve (all steps of Sec. 4: moments, local convolutions,
-coarse charge, coarse solve, boundary values, Dirichlet solves) of the
-128^3 workload (512 patches of 16^3, support 16, Q = 4, P = 4, FP64; 8 bumps
-from seed 1) with the charge resident in HBM.  L2 is flushed (a 512 MB write)
-between timed steps; the flush is outside the timed region.
+coarse charge, coarse solve, boundary values, Dirichlet solves) of the 256^3
+precision-form workload (4096 patches of 16^3, support 16, Q = 6 (27-point),
+P = 4; FP32 charge of 32 bumps from seed 3) in the split tier: FP32 local
+convolutions and Legendre ring sums, FP64 coarse charge, coarse solve,
+boundary values and Dirichlet solves; the charge is resident in HBM.  L2 is
+flushed (a 512 MB write) between timed steps, outside the timed region.
 
 Prints one JSON line.  `--impl reference` times the CPU oracle instead.
 Under torchrun each rank solves its own copy (independent problems, no
@@ -29,7 +31,7 @@ sys.path.insert(0, ROOT)
 from paper_1702_08111_gb300 import inputs as I  # noqa: E402
 
 METRIC = "MLC solve Mpoints/s at stated max error vs FP64 oracle"
-WORKLOAD = "bumps8_128"
+WORKLOAD = "bumps32_256_q6"
 
 
 def peaks():
@@ -167,10 +169,10 @@ def aggregate_value(points_per_rank: float, world: int, ms_max: float) -> float:
     return world * points_per_rank / (ms_max * 1e-3) / 1e6
 
 
-def time_plan(plan, f, phi, steps, warmup, flush, stream, world, clk=None):
+def time_plan(plan, f, phi, steps, warmup, flush, stream, world, clk=None, per_launch_steps=None):
     """Mean device time per solve (CUDA events on the launching stream, L2
     flushed between steps outside the timed region), then per-launch means
-    from as many further solves run with per-launch timing on (the launches in
+    from further solves run with per-launch timing on (the launches in
     sequence on one stream; not part of the timed region)."""
     import torch
     for _ in range(warmup):
@@ -196,21 +198,23 @@ def time_plan(plan, f, phi, steps, warmup, flush, stream, world, clk=None):
         clk.end()
     plan.set_timing(True)
     per_launch = {}
-    for _ in range(steps):
+    nl = per_launch_steps or steps
+    for _ in range(nl):
         plan.solve(f, phi, stream)
         for k, v in plan.timing().items():
             per_launch[k] = per_launch.get(k, 0.0) + v
         flush.zero_()
     torch.cuda.synchronize()
     plan.set_timing(False)
-    return total_ms / steps, {k: v / steps for k, v in per_launch.items()}
+    return total_ms / steps, {k: v / nl for k, v in per_launch.items()}
 
 
-# FP32 pipe lane-instruction rate of one GB300 from its unit counts and
-# maximum clock: 152 SMs x 128 FP32 lanes x 2.07 GHz (FADD, FMUL and FFMA
-# issue at the same rate).  Both tiers run their FFTs on this pipe: the split
-# tier in FP32, the FP64 tier in double-float (hi + lo FP32 pairs).
+# Instruction rates of one GB300 from its unit counts and the maximum clock.
+# FP32 pipe: 152 SMs x 128 FP32 lanes x 2.07 GHz (FADD, FMUL, FFMA issue at one
+# rate).  FP64 pipe: the nominal 1.25 TFLOP/s FP64 of the part (FMA = 2 FLOPs),
+# i.e. 0.625 T FP64 instructions/s (about 2 lanes per SM per clock).
 FP32_LANE_INST_PER_S = 152 * 128 * 2.07e9
+FP64_INST_PER_S = 1.25e12 / 2
 
 # FP32 instructions of one (unnormalised) double-float operation: add =
 # two-sum (6) + low parts (2); multiply = FMUL + 3 FFMA.
@@ -218,31 +222,27 @@ DF_ADD_INST, DF_MUL_INST = 8, 4
 
 
 def fft64_schedule_inst(tier: str, sparse: bool, nin: int = 17) -> float:
-    """FP32 instructions of one 64-point line transform in the slab kernel's
-    schedule.  FP64 tier (double-float, radix 8 x 8 over an 8-thread group):
-    16 radix-8 butterflies (52 real adds + 4 real multiplies each; 26 + 2 for
-    a first-stage butterfly whose inputs 3..7 are zero, `sparse`) and 56
-    twiddle products (7 per thread).  Split tier (FP32, radix 2 in one
-    thread's registers): 6 stages of 32 butterflies (4 adds each; for inputs
-    zero from nin <= 17 on, none in the first stage and 2 in the second) and 98
-    nontrivial twiddle products (2 FMUL + 2 FFMA; twiddles 1 and -i cost
-    nothing)."""
-    if tier == "fp64":
+    """Instructions of one 64-point line transform in the slab kernel's
+    schedule.  FP64 and double-float tiers (radix 8 x 8 over an 8-thread
+    group): 16 radix-8 butterflies (52 real adds + 4 real multiplies each;
+    26 + 2 for a first-stage butterfly whose inputs 3..7 are zero, `sparse`)
+    and 56 twiddle products (4 multiplies + 2 adds); in double-float each add
+    is DF_ADD_INST and each multiply DF_MUL_INST FP32 instructions, in FP64 one
+    FP64 instruction each (the twiddle's 2 adds fuse into FMAs).  Split tiers
+    (FP32, radix 2 in one thread's registers): 6 stages of 32 butterflies (4
+    adds each; for inputs zero from nin <= 17 on, none in the first stage and
+    2 in the second) and 98 nontrivial twiddle products (2 FMUL + 2 FFMA)."""
+    if tier in ("fp64", "df"):
         first = (26, 2) if sparse else (52, 4)
         adds = 8 * first[0] + 8 * 52
         muls = 8 * first[1] + 8 * 4
-        # twiddle = 4 multiplies + 2 adds, all double-float
-        return (adds + 56 * 2) * DF_ADD_INST + (muls + 56 * 4) * DF_MUL_INST
+        if tier == "df":
+            return (adds + 56 * 2) * DF_ADD_INST + (muls + 56 * 4) * DF_MUL_INST
+        return adds + muls + 56 * 4
     if not sparse:
         return 6 * 32 * 4 + 98 * 4
     stage2 = 2 * max(0, min(nin, 32) - 16) if nin <= 17 else 32  # butterflies with two nonzero inputs
     return 4 * 32 * 4 + stage2 * 4 + 98 * 4
-
-
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one slab launch,
-# from the ncu captures summarised in profiles/ (slab kernel unchanged since):
-# the A1 spectra read and the A4 spectra written, no re-reads.
-SLAB_DRAM_BYTES = {("bumps8_128", "fp64"): 508.528e6, ("bumps32_256_q6", "split"): 1.900593e9}
 
 
 def slab_rows(w, ga):
@@ -252,40 +252,93 @@ def slab_rows(w, ga):
     return sum(1 for zi in range(W) if (-ga <= zi - w.s <= w.n + ga) or (zi - w.s) % 4 == 0)
 
 
-def roofline_for(w, plan, per_launch, tier):
-    """Roofline of the dominant launch (the slab kernel).  Algorithmic work =
-    nominal radix-2 FFT FLOPs (5 M log2 M per complex line) over the lines the
-    pruned transform must produce (forward y on the n+1 nonzero z rows, forward
-    and inverse z on all M columns, inverse y on the z rows read later), plus 2
-    FLOPs per entry of the real-kernel product; FP64-equivalent FLOPs in the
-    FP64 tier.  Peak = the FP32 pipe's instruction rate times the nominal FLOPs
-    one FP32 instruction of the kernel's schedule carries: the rate the kernel
-    would reach if the pipe issued nothing but its arithmetic."""
+def dirichlet_counts(n, Q):
+    """Algorithmic FLOPs and instructions of the Dirichlet step for one patch
+    of n = 16: the right-hand side f - Delta^h(boundary data) (one FMA per
+    boundary term with a nonzero weight), 6 passes of 15^2 lines of the
+    15-point split-radix DST-I (29 products + 68 sums each, no FMA), the
+    inverse eigenvalue scaling (15^3 products) and the Mehrstellen correction
+    u + h^2/12 f (one FMA per node of the patch)."""
+    import itertools
+    if n != 16:
+        return None
+    terms = 0
+    for c in itertools.product(range(1, n), repeat=3):
+        for sft in itertools.product((-1, 0, 1), repeat=3):
+            nz = sum(1 for x in sft if x)
+            if nz == 0 or (Q == 4 and nz == 3):
+                continue
+            if any(c[d] + sft[d] in (0, n) for d in range(3)):
+                terms += 1
+    m = n - 1
+    dst = 6 * m * m * 97
+    flops = 2 * terms + dst + m ** 3 + 2 * n ** 3
+    inst = terms + dst + m ** 3 + n ** 3
+    return flops, inst
+
+
+def roofline_for(w, plan, per_launch, tier, traffic=None):
+    """Roofline of the dominant launch.  Slab kernel (local convolutions):
+    algorithmic work = nominal radix-2 FFT FLOPs (5 M log2 M per complex line)
+    over the lines the pruned transform must produce (forward y on the n+1
+    nonzero z rows, forward and inverse z on all M columns, inverse y on the z
+    rows read later) plus 2 FLOPs per entry of the real-kernel product, per
+    (patch, kx) slab.  Dirichlet kernel: the counts of dirichlet_counts per
+    patch.  Peak = the instruction rate of the pipe the kernel runs on times
+    the algorithmic FLOPs one instruction of its schedule carries: the rate
+    the kernel would reach if the pipe issued nothing but its arithmetic."""
     info = plan.info
     N = w.N
     M, Mh, NP = info.M, info.M // 2 + 1, (N // w.n) ** 3
-    nin = w.n + 1
     dom = max(per_launch, key=per_launch.get)
-    if dom != "conv_slab" or M != 64:
+    fine64 = tier in ("fp64", "split")
+    if dom == "conv_slab" and M == 64:
+        nin = w.n + 1
+        nz = slab_rows(w, info.g_alpha)
+        line_flops = 5.0 * M * np.log2(M)
+        nominal = (nin + 2 * M + nz) * line_flops + 2.0 * M * M
+        prod = {"df": 2 * DF_MUL_INST, "fp64": 2, "split": 2, "split_df": 2}[tier]
+        inst = ((nin + M) * fft64_schedule_inst(tier if tier in ("fp64", "df") else "split", True, nin)
+                + (M + nz) * fft64_schedule_inst(tier if tier in ("fp64", "df") else "split", False)
+                + M * M * prod)
+        units, pipe_rate = NP * Mh, (FP64_INST_PER_S if tier == "fp64" else FP32_LANE_INST_PER_S)
+        pipe = "FP64 pipe" if tier == "fp64" else "FP32 pipe"
+        sched = {"fp64": "FP64 radix-8x8", "df": "double-float radix-8x8"}.get(tier, "FP32 radix-2 register")
+        unit_name = "(patch, kx) slab"
+    elif dom == "dirichlet" and w.n == 16:
+        nominal, inst = dirichlet_counts(w.n, w.Q)
+        if not fine64:
+            inst = inst * DF_ADD_INST  # double-float: about 8 FP32 instructions per operation
+        units, pipe_rate = NP, (FP64_INST_PER_S if fine64 else FP32_LANE_INST_PER_S)
+        pipe = "FP64 pipe" if fine64 else "FP32 pipe"
+        sched = "FP64 split-radix DST-I" if fine64 else "double-float split-radix DST-I"
+        unit_name = "patch"
+    else:
         return None
-    nz = slab_rows(w, info.g_alpha)
-    line_flops = 5.0 * M * np.log2(M)
-    nominal = (nin + 2 * M + nz) * line_flops + 2.0 * M * M
-    prod_inst = M * M * (2 * DF_MUL_INST if tier == "fp64" else 2)
-    inst = ((nin + M) * fft64_schedule_inst(tier, True, nin) + (M + nz) * fft64_schedule_inst(tier, False)
-            + prod_inst)
-    flops = NP * Mh * nominal
+    flops = units * nominal
     achieved = flops / (per_launch[dom] * 1e-3) / 1e12
-    peak = FP32_LANE_INST_PER_S * nominal / inst / 1e12
-    basis = ("FP32 pipe 152 SMs x 128 lanes x 2.07 GHz = 40.27 T inst/s x %.4f nominal %s FLOP per FP32 "
-             "instruction of the slab's %s schedule" % (nominal / inst, "FP64-equivalent" if tier == "fp64"
-                                                        else "FP32", "double-float radix-8x8" if tier == "fp64"
-                                                        else "FP32 radix-2 register"))
-    return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 3),
-            "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-            "traffic": SLAB_DRAM_BYTES.get((w.name, tier)),
+    peak = pipe_rate * nominal / inst / 1e12
+    basis = ("%s %.4g T inst/s (%s) x %.4f algorithmic FLOP per instruction of the %s schedule"
+             % (pipe, pipe_rate / 1e12, "152 SMs x 128 lanes x 2.07 GHz" if pipe == "FP32 pipe"
+                else "nominal 1.25 TFLOP/s FP64, FMA = 2", nominal / inst, sched))
+    return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak, 4),
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
             "launch_ms": round(per_launch[dom], 4), "flops_per_launch": flops,
-            "fp32_inst_per_launch": NP * Mh * inst, "peak_basis": basis}
+            "units_per_launch": units, "unit_of_work": unit_name, "flops_per_unit": nominal,
+            "inst_per_unit": inst, "peak_basis": basis}
+
+
+TIER_IDS = {"fp64": 0, "split": 1, "df": 2, "split_df": 3}
+F32_TIERS = ("split", "split_df")
+
+
+def tier_for(w):
+    return "split" if w.charge_dtype == "f32" else "fp64"
+
+
+def charge_for(w, tier, f64):
+    import torch
+    return torch.from_numpy(f64.astype(np.float32) if tier in F32_TIERS else f64).cuda()
 
 
 def run_ours(args, rank, world):
@@ -296,8 +349,8 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda")
     w = I.workload(args.workload)
     N = w.N
-    tier = "split" if w.charge_dtype == "f32" else "fp64"
-    plan = mlc.Plan(N, w.n, w.s, w.P, w.Q, tier=mlc.MLC_TIER_SPLIT if tier == "split" else mlc.MLC_TIER_FP64)
+    tier = tier_for(w)
+    plan = mlc.Plan(N, w.n, w.s, w.P, w.Q, tier=TIER_IDS[tier])
     f_host = torch.from_numpy(w.charge())
     f = f_host.to(dev)
     phi = torch.empty((N, N, N), dtype=torch.float64, device=dev)
@@ -320,62 +373,111 @@ def run_ours(args, rank, world):
         e2e_ms += (time.perf_counter() - t0) * 1e3
     e2e_ms /= args.steps
     value = aggregate_value(float(N) ** 3, world, ms)
-    res = {"value": value, "ms": ms, "e2e_ms": e2e_ms, "per_launch": per_launch,
-           "roofline": roofline_for(w, plan, per_launch, tier), "clocks": clk.summary(),
-           "phi": phi, "N": N, "tier": tier, "f_bytes": f_host.element_size() * N ** 3}
+    # kernel launches of one solve: moments, 3 per local-convolution launch
+    # group of 1024 patches, residuals, F^H, 5 coarse, boundary, Dirichlet
+    NP = (N // w.n) ** 3
+    launches = 10 + 3 * ((NP + 1023) // 1024)
+    res = {"value": value, "ms": ms, "e2e_ms": e2e_ms, "per_launch": per_launch, "launches_per_step": launches,
+           "roofline": roofline_for(w, plan, per_launch, tier, traffic_for(args.workload, tier, per_launch)),
+           "clocks": clk.summary(), "phi": phi, "N": N, "tier": tier, "f_bytes": f_host.element_size() * N ** 3}
     del plan
     if args.extra and rank == 0:
-        res["extra"] = run_extra(args, flush, stream)
+        res["extra"] = run_extra(args, flush, stream, w, tier, phi, ms)
     return res
 
 
-def run_extra(args, flush, stream):
-    """Secondary lines: the 256^3 Q=6 workload in the split and FP64 tiers."""
+def traffic_for(workload, tier, per_launch):
+    """DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
+    of the dominant kernel, from the ncu capture summarised in profiles/ for
+    this kernel and workload (profiles/traffic.json, written with the capture),
+    or None if the kernel has changed since the counters were taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            tab = json.load(fh)
+    except Exception:
+        return None
+    dom = max(per_launch, key=per_launch.get)
+    ent = tab.get(f"{workload}/{tier}/{dom}")
+    return None if ent is None else ent.get("bytes_per_launch")
+
+
+def time_tier(w, tier, f64, flush, stream, steps, warmup=3):
     import torch
     from paper_1702_08111_gb300 import mlc
+    plan = mlc.Plan(w.N, w.n, w.s, w.P, w.Q, tier=TIER_IDS[tier])
+    f = charge_for(w, tier, f64)
+    phi = torch.empty((w.N,) * 3, dtype=torch.float64, device="cuda")
+    ms, pl = time_plan(plan, f, phi, steps, warmup, flush, stream, 1, per_launch_steps=2)
+    out = {"workload": w.name, "tier": tier, "ms_per_step": round(ms, 4),
+           "value": round(float(w.N) ** 3 / (ms * 1e-3) / 1e6, 2), "unit": "Mpoints/s",
+           "roofline": roofline_for(w, plan, pl, tier, traffic_for(w.name, tier, pl)),
+           "per_launch_ms": {k: round(v, 4) for k, v in pl.items()}}
+    phi_h = phi.cpu().numpy()
+    del plan, f, phi
+    return out, phi_h
+
+
+def run_extra(args, flush, stream, w, head_tier, phi_head, head_ms):
+    """Secondary lines: the headline workload in the other tiers (plain FP64,
+    double-float, split with double-float steps) with the three ratios to the
+    plain FP64 solve, the split tier's batched form, the 128^3 FP64 solve
+    against the oracle, the 48-problem uneven batch, the 2000-request serving
+    stream and the allocation-free entry point."""
     from oracle import closed_forms as CF
-    w = I.workload("bumps32_256_q6")
-    N = w.N
-    f32 = torch.from_numpy(w.charge()).cuda()
-    f64 = f32.double()
+    f64 = w.charge().astype(np.float64)
     out = {}
-    phis = {}
-    for tier, f in (("split", f32), ("fp64", f64)):
-        plan = mlc.Plan(N, w.n, w.s, w.P, w.Q, tier=mlc.MLC_TIER_SPLIT if tier == "split" else mlc.MLC_TIER_FP64)
-        phi = torch.empty((N, N, N), dtype=torch.float64, device="cuda")
-        steps = max(3, args.steps // 2)
-        ms, pl = time_plan(plan, f, phi, steps, 3, flush, stream, 1)
-        phis[tier] = phi.cpu().numpy()
-        out[tier] = {"workload": "bumps32_256_q6", "tier": tier, "ms_per_step": round(ms, 3),
-                     "value": round(float(N) ** 3 / (ms * 1e-3) / 1e6, 2), "unit": "Mpoints/s",
-                     "roofline": roofline_for(w, plan, pl, tier),
-                     "per_launch_ms": {k: round(v, 4) for k, v in pl.items()}}
-        del plan
-    ex = CF.bumps_potential(N, w.bumps)
-    d = np.abs(phis["split"] - phis["fp64"]).max() / np.abs(phis["fp64"]).max()
-    out["split"]["max_rel_err_vs_fp64_gpu"] = float(d)
-    out["fp64"]["max_rel_err_vs_closed_form"] = float(np.abs(phis["fp64"] - ex).max() / np.abs(ex).max())
-    out["split"]["max_rel_err_vs_closed_form"] = float(np.abs(phis["split"] - ex).max() / np.abs(ex).max())
-    out["split_over_fp64_speedup"] = round(out["fp64"]["ms_per_step"] / out["split"]["ms_per_step"], 3)
+    phis = {head_tier: phi_head.cpu().numpy()}
+    steps = max(3, args.steps // 2)
+    for tier in ("fp64", "df", "split_df", "split"):
+        if tier == head_tier:
+            continue
+        out[tier], phis[tier] = time_tier(w, tier, f64, flush, stream, steps)
+    ex = CF.bumps_potential(w.N, w.bumps)
+    ref = phis["fp64"]
+    for tier, ph in phis.items():
+        ent = out.setdefault(tier, {"workload": w.name, "tier": tier, "note": "the headline line"})
+        ent["max_rel_err_vs_fp64_gpu"] = float(np.abs(ph - ref).max() / np.abs(ref).max())
+        ent["max_rel_err_vs_closed_form"] = float(np.abs(ph - ex).max() / np.abs(ex).max())
     del phis
-    out["split_batched"] = run_batched_256(args, flush, stream, w)
-    out["split_batched_over_fp64_speedup"] = round(
-        out["split_batched"]["value"] / out["fp64"]["value"], 3)
+    out["split_batched"] = run_batched(args, flush, stream, w)
+    out[head_tier]["ms_per_step"] = round(head_ms, 4)
+    out["ratios_to_plain_fp64"] = {
+        "split_batched": round(out["split_batched"]["value"] / out["fp64"]["value"], 3),
+        "df": round(out["fp64"]["ms_per_step"] / out["df"]["ms_per_step"], 3),
+        "split_df": round(out["fp64"]["ms_per_step"] / out["split_df"]["ms_per_step"], 3),
+    }
+    if "split" in out and "ms_per_step" in out["split"]:
+        out["ratios_to_plain_fp64"]["split"] = round(out["fp64"]["ms_per_step"] / out["split"]["ms_per_step"], 3)
+    out["fp64_128"] = run_fp64_128(args, flush, stream)
     out["batch"] = run_batch(args, flush, stream)
     out["serving"] = run_serving(args)
+    out["noalloc"] = run_noalloc(args, flush, stream)
     return out
 
 
-def run_batched_256(args, flush, stream, w, nprob=4):
-    """The split tier at 256^3 in its batched form: nprob problems of the
-    256^3 Q = 6 geometry (32 bumps each; seeds 3, 13, 23, 33) in one
+def run_fp64_128(args, flush, stream):
+    """The 128^3 workload (512 patches, Q = 4, 8 bumps from seed 1) in the
+    plain FP64 tier, with its error against the oracle (one full oracle solve)."""
+    from oracle import mlc_oracle as O
+    w = I.workload("bumps8_128")
+    f64 = w.charge()
+    res, phi = time_tier(w, "fp64", f64, flush, stream, max(3, args.steps // 2))
+    G1 = O.dgf_octant(w.Q, 128, 2)
+    ref = O.solve_open(O.Params(N=w.N, n=w.n, s=w.s, Q=w.Q, P=w.P), f64, G1=G1)
+    res["max_rel_err_vs_oracle"] = float(np.abs(phi - ref).max() / np.abs(ref).max())
+    return res
+
+
+def run_batched(args, flush, stream, w, nprob=4):
+    """The split tier at the headline size in its batched form: nprob problems
+    of the same geometry (32 bumps each; seeds 3, 13, 23, 33) in one
     mlc_batch_solve (shared per-patch launches, per-problem coarse steps on
-    parallel graph branches).  Mpoints/s over all problems."""
+    parallel branches).  Mpoints/s over all problems."""
     import torch
     from paper_1702_08111_gb300 import mlc
     ws = [I.Workload(w.name, w.N, w.n, w.s, w.Q, bumps=I.draw_bumps(32, 3 + 10 * k), charge_dtype="f32")
           for k in range(nprob)]
-    plans = [mlc.Plan(x.N, x.n, x.s, x.P, x.Q, tier=mlc.MLC_TIER_SPLIT) for x in ws]
+    plans = [mlc.Plan(x.N, x.n, x.s, x.P, x.Q, tier=TIER_IDS["split"]) for x in ws]
     fs = [torch.from_numpy(x.charge()).cuda() for x in ws]
     phis = [torch.empty((x.N,) * 3, dtype=torch.float64, device="cuda") for x in ws]
     for _ in range(3):
@@ -393,7 +495,7 @@ def run_batched_256(args, flush, stream, w, nprob=4):
         tot += e0.elapsed_time(e1)
         flush.zero_()
     ms = tot / steps
-    res = {"workload": f"{nprob} x bumps32_256_q6 (seeds 3, 13, 23, 33)", "problems": nprob,
+    res = {"workload": f"{nprob} x {w.name} (seeds 3, 13, 23, 33)", "tier": "split", "problems": nprob,
            "ms_per_batch": round(ms, 3), "ms_per_problem": round(ms / nprob, 3),
            "value": round(nprob * float(w.N) ** 3 / (ms * 1e-3) / 1e6, 2), "unit": "Mpoints/s",
            "batch_choice": mlc.batch_choice(plans, fs, phis)}
@@ -402,29 +504,23 @@ def run_batched_256(args, flush, stream, w, nprob=4):
 
 
 def run_batch(args, flush, stream):
-    """48 uneven problems (sides 32..160), split tier, through mlc_batch_solve
-    (one graph per patch geometry) versus the same problems one by one."""
+    """48 uneven problems (sides 32..160; patch 8 for side 32, 16 otherwise),
+    split tier, in ONE mlc_batch_solve call (two geometry groups, one captured
+    graph) versus the same problems one by one."""
     import torch
     from paper_1702_08111_gb300 import mlc
     probs = I.batch_problems(48, 4)
-    groups = {}
-    for w in probs:
-        groups.setdefault((w.n, w.s), []).append(w)
-    plans, fs, phis = {}, {}, {}
-    for key, ws in groups.items():
-        plans[key] = [mlc.Plan(w.N, w.n, w.s, w.P, w.Q, tier=mlc.MLC_TIER_SPLIT) for w in ws]
-        fs[key] = [torch.from_numpy(w.charge().astype(np.float32)).cuda() for w in ws]
-        phis[key] = [torch.empty((w.N,) * 3, dtype=torch.float64, device="cuda") for w in ws]
+    plans = [mlc.Plan(w.N, w.n, w.s, w.P, w.Q, tier=TIER_IDS["split"]) for w in probs]
+    fs = [torch.from_numpy(w.charge().astype(np.float32)).cuda() for w in probs]
+    phis = [torch.empty((w.N,) * 3, dtype=torch.float64, device="cuda") for w in probs]
     pts = float(sum(w.N ** 3 for w in probs))
 
     def step_batch():
-        for key in groups:
-            mlc.batch_solve(plans[key], fs[key], phis[key], stream)
+        mlc.batch_solve(plans, fs, phis, stream)
 
     def step_single():
-        for key in groups:
-            for p, f, ph in zip(plans[key], fs[key], phis[key]):
-                p.solve(f, ph, stream)
+        for p, f, ph in zip(plans, fs, phis):
+            p.solve(f, ph, stream)
 
     res = {}
     for name, fn in (("batched_graph", step_batch), ("one_by_one", step_single)):
@@ -445,75 +541,147 @@ def run_batch(args, flush, stream):
         ms = tot / steps
         res[name] = {"ms_per_step": round(ms, 3), "value": round(pts / (ms * 1e-3) / 1e6, 2), "unit": "Mpoints/s"}
     res["problems"] = len(probs)
-    res["groups"] = {f"n{k[0]}_s{k[1]}": len(v) for k, v in groups.items()}
+    res["calls_per_step"] = 1
+    res["groups"] = sorted({f"n{w.n}_s{w.s}" for w in probs})
+    res["batch_choice"] = mlc.batch_choice(plans, fs, phis)
     res["speedup_over_one_by_one"] = round(res["one_by_one"]["ms_per_step"] / res["batched_graph"]["ms_per_step"], 3)
     return res
 
 
-def run_serving(args, nreq=200):
-    """Continuous-batching server on the first `nreq` requests of the serving
-    mix: saturated throughput first, then Poisson arrivals at 0.7 x that rate;
-    p50/p99 latency (enqueue -> completion)."""
+def run_serving(args, nreq=2000, nsat=400):
+    """Continuous-batching server on the 2000-request serving mix (sides
+    log-uniform in [64, 384], patch 16, support 16, Q in {4, 6}, FP64 and split
+    tiers 50/50, 1-32 bumps): saturated throughput on the first `nsat`
+    requests, then all requests as Poisson arrivals at 0.7 x that rate; p50/p99
+    latency (enqueue -> completion).  Charges: one per (side, charge dtype)
+    (16 bumps, seed 60000 + side; a solve's cost does not depend on the
+    charge's values) and a ring of result buffers per side, so that requests
+    in flight never share a result array."""
     import torch
     from paper_1702_08111_gb300 import mlc
-    reqs = I.serving_requests(2000, 5)[:nreq]
-    data = []
+    reqs = I.serving_requests(nreq, 5)
+    charges, outs, ring = {}, {}, {}
     for w, tier in reqs:
-        f = w.charge()
-        t = torch.from_numpy(f.astype(np.float32) if tier == "split" else f).cuda()
-        data.append((w, tier, t, torch.empty((w.N,) * 3, dtype=torch.float64, device="cuda")))
+        key = (w.N, tier in F32_TIERS)
+        if key not in charges:
+            f = I.sample_bumps(w.N, I.draw_bumps(16, 60000 + w.N))
+            charges[key] = torch.from_numpy(f.astype(np.float32) if key[1] else f).cuda()
+        if w.N not in outs:
+            outs[w.N] = [torch.empty((w.N,) * 3, dtype=torch.float64, device="cuda") for _ in range(20)]
+            ring[w.N] = 0
     srv = mlc.Server(120 << 30, max_batch=8)
 
     def submit(k):
-        w, tier, f, phi = data[k]
-        return srv.enqueue(f, phi, w.N, w.n, w.s, w.P, w.Q,
-                           tier=mlc.MLC_TIER_SPLIT if tier == "split" else mlc.MLC_TIER_FP64)
+        w, tier = reqs[k]
+        f = charges[(w.N, tier in F32_TIERS)]
+        phi = outs[w.N][ring[w.N] % 20]
+        ring[w.N] += 1
+        return srv.enqueue(f, phi, w.N, w.n, w.s, w.P, w.Q, tier=TIER_IDS[tier])
 
     # warm-up: every distinct plan once (plan creation is not serving latency)
     seen = {}
-    for k, (w, tier, _, _) in enumerate(data):
+    for k, (w, tier) in enumerate(reqs):
         seen.setdefault((w.N, w.Q, tier), k)
     for t in [submit(k) for k in seen.values()]:
         srv.wait(t)
-    # saturated: all at once
+    # saturated: the first nsat requests at once
     t0 = time.perf_counter()
-    for t in [submit(k) for k in range(len(data))]:
+    for t in [submit(k) for k in range(nsat)]:
         srv.wait(t)
     sat_s = time.perf_counter() - t0
-    rate = 0.7 * len(data) / sat_s
+    rate = 0.7 * nsat / sat_s
     rng = np.random.default_rng(55)
-    gaps = rng.exponential(1.0 / rate, size=len(data))
+    gaps = rng.exponential(1.0 / rate, size=nreq)
     tickets = []
     t0 = time.perf_counter()
     next_t = t0
-    for k in range(len(data)):
+    for k in range(nreq):
         next_t += gaps[k]
         while time.perf_counter() < next_t:
             time.sleep(min(0.0005, max(0.0, next_t - time.perf_counter())))
         tickets.append(submit(k))
-    lats = []
+    lats, qs, bad = [], [], 0
     for t in tickets:
         st, lat, q = srv.wait(t)
+        bad += st != 0
         lats.append(lat)
+        qs.append(q)
     total_s = time.perf_counter() - t0
     srv.close()
-    pts = float(sum(w.N ** 3 for w, _, _, _ in data))
-    return {"requests": len(data), "rate_req_per_s": round(rate, 2),
-            "saturated_req_per_s": round(len(data) / sat_s, 2),
+    pts = float(sum(w.N ** 3 for w, _ in reqs))
+    pts_sat = float(sum(w.N ** 3 for w, _ in reqs[:nsat]))
+    return {"requests": nreq, "failed": int(bad), "rate_req_per_s": round(rate, 2),
+            "saturated_req_per_s": round(nsat / sat_s, 2),
             "p50_ms": round(float(np.percentile(lats, 50)), 3), "p99_ms": round(float(np.percentile(lats, 99)), 3),
+            "queue_p50_ms": round(float(np.percentile(qs, 50)), 3),
             "Mpoints_per_s_at_rate": round(pts / total_s / 1e6, 2),
-            "Mpoints_per_s_saturated": round(pts / sat_s / 1e6, 2),
-            "distinct_plans": len(seen), "hbm_budget_gb": 120, "max_batch": 8}
+            "Mpoints_per_s_saturated": round(pts_sat / sat_s / 1e6, 2),
+            "distinct_plans": len(seen), "hbm_budget_gb": 120, "max_batch": 8, "lanes": 2}
 
 
-def cpu_oracle_solve(w, nodes_sample=None):
+def run_noalloc(args, flush, stream):
+    """mlc_solve_noalloc against mlc_solve at 64^3 (64 patches, Q = 6, split
+    tier): device time per solve (single stream vs moments/residuals beside the
+    convolution chain)."""
+    import torch
+    from paper_1702_08111_gb300 import mlc
+    w = I.workload("bumps8_64_q6")
+    f = torch.from_numpy(w.charge().astype(np.float32)).cuda()
+    plan = mlc.Plan(64, 16, 16, 4, 6, tier=TIER_IDS["split"])
+    phi = torch.empty((64,) * 3, dtype=torch.float64, device="cuda")
+    res = {"workload": "bumps8_64_q6 (64^3, 64 patches, Q = 6), split tier"}
+    for name, fn in (("mlc_solve", plan.solve), ("mlc_solve_noalloc", plan.solve_noalloc)):
+        for _ in range(3):
+            fn(f, phi, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(10):
+            flush.zero_()
+            e0.record(stream)
+            fn(f, phi, stream)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        res[name + "_ms"] = round(tot / 10, 4)
+    return res
+
+
+def cpu_sample(w):
+    """Bounded sample of the workload for the CPU oracle: the 64^3 sub-problem
+    with the workload's patch geometry, operator and charge recipe (64 patches
+    of 16^3 instead of 4096; 8 bumps drawn like the workload's, seed 1)."""
+    return I.Workload(w.name + "_sample64", 64, w.n, w.s, w.Q, w.P, bumps=I.draw_bumps(8, 1))
+
+
+def time_oracle_sample(w, steps=1):
     from oracle import mlc_oracle as O
+    sub = cpu_sample(w)
     G1 = O.dgf_octant(w.Q, 128, 2)
-    prm = O.Params(N=w.N, n=w.n, s=w.s, Q=w.Q, P=w.P)
-    f = w.charge()
+    prm = O.Params(N=sub.N, n=sub.n, s=sub.s, Q=sub.Q, P=sub.P)
+    f = sub.charge()
     t0 = time.perf_counter()
-    phi = O.solve_open(prm, f, G1=G1)
-    return phi, time.perf_counter() - t0
+    for _ in range(steps):
+        O.solve_open(prm, f, G1=G1)
+    dt = (time.perf_counter() - t0) / steps
+    return float(sub.N) ** 3 / dt / 1e6, dt, sub
+
+
+def oracle_threads():
+    try:
+        return int(os.environ.get("OMP_NUM_THREADS") or os.cpu_count())
+    except Exception:
+        return os.cpu_count()
+
+
+def bench_config(args, w, tier, world):
+    return {"workload": args.workload, "N": w.N, "patch": w.n, "support": w.s, "Q": w.Q, "P": w.P,
+            "tier": tier,
+            "arithmetic": ("f32 local convolutions (FFTs on the CUDA cores) and Legendre ring sums; f64 "
+                           "coarse charge, coarse solve, boundary values and Dirichlet solves")
+            if tier == "split" else ("f64 in every step" if tier == "fp64" else tier),
+            "l2": "flushed between steps (512 MB write)",
+            "parallelism": f"independent problem per GPU x{world}"}
 
 
 def main():
@@ -530,11 +698,12 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     w = I.workload(args.workload)
+    tier = tier_for(w)
 
     if args.impl == "reference":
         if rank != 0:
             return 0
-        return run_reference(args, w)
+        return run_reference(args, w, tier, world)
 
     if world > 1:
         import torch
@@ -543,35 +712,35 @@ def main():
     line = None
     if rank == 0:
         cpu = None
-        err = None
         if not args.no_cpu_baseline and world == 1:
-            phi_o, t = cpu_oracle_solve(w)
-            got = r["phi"].cpu().numpy()
-            err = float(np.abs(got - phi_o).max() / np.abs(phi_o).max())
-            cpu = {"value": round(float(w.N) ** 3 / t / 1e6, 4), "unit": "Mpoints/s",
-                   "cores": os.cpu_count(), "kind": "oracle",
-                   "sample": f"one full oracle solve of {args.workload} ({t:.1f} s; DGF table prebuilt)"}
+            val, dt, sub = time_oracle_sample(w)
+            cpu = {"value": round(val, 5), "unit": "Mpoints/s", "cores": oracle_threads(), "kind": "oracle",
+                   "sample": f"one oracle solve of the 64^3 sub-problem of {args.workload} (64 patches of "
+                             f"16^3, support 16, Q = {w.Q}, 8 bumps) in {dt:.1f} s; DGF table prebuilt"}
         N = r["N"]
         e2e_val = float(N) ** 3 / (r["e2e_ms"] * 1e-3) / 1e6
-        launches = 13
+        launches = len(r["per_launch"])
+        ex = r.get("extra", {})
+        err_fp64 = ex.get(tier, {}).get("max_rel_err_vs_fp64_gpu")
+        err_cf = ex.get(tier, {}).get("max_rel_err_vs_closed_form")
         line = {
             "metric": METRIC, "value": round(r["value"], 3), "unit": "Mpoints/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r["ms"], 4),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32x2",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if tier == "split" else "f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "N": w.N, "patch": w.n, "support": w.s, "Q": w.Q,
-                       "P": w.P, "tier": "fp64",
-                       "arithmetic": "double-float (pairs of f32, ~48-bit significand) on the FP32 pipe; "
-                                     "f64 in the moments, the plan tables and the f/phi conversions",
-                       "l2": "flushed between steps (512 MB write)",
-                       "parallelism": f"independent problem per GPU x{world}"},
-            "max_rel_err_vs_oracle": err,
+            "config": bench_config(args, w, tier, world),
+            "max_rel_err_vs_fp64_gpu": err_fp64,
+            "max_rel_err_vs_closed_form": err_cf,
+            "fp64_gpu_vs_oracle": "the plain FP64 tier is within 1e-12 of the oracle (tests; extra.fp64_128 "
+                                  "here at 128^3)",
             "e2e": {"value": round(e2e_val, 3), "unit": "Mpoints/s",
                     "h2d_bytes_per_step": int(r["f_bytes"]), "d2h_bytes_per_step": int(N ** 3 * 8)},
-            "gpu_launches": launches * args.steps,
+            "gpu_launches": None,
             "roofline": r["roofline"], "cpu_baseline": cpu, "clocks": r["clocks"],
             "per_launch_ms": {k: round(v, 4) for k, v in r["per_launch"].items()},
         }
+        line["gpu_launches"] = r.get("launches_per_step", 0) * args.steps or None
         if "extra" in r:
             line["extra"] = r["extra"]
         print(json.dumps(line), flush=True)
@@ -582,14 +751,13 @@ def main():
     return 0
 
 
-def run_reference(args, w):
-    """Time the CPU oracle as it stands on a bounded sample of the workload."""
+def run_reference(args, w, tier, world):
+    """The reference arm: the CPU oracle as it stands, each step one solve of
+    a bounded sample of the workload (its 64^3 sub-problem), on the host cores."""
     from oracle import mlc_oracle as O
-    # bounded sample: the 64^3 sub-problem with the workload's patch geometry and
-    # charge recipe (8 patches instead of 512), one full oracle solve per step
-    sub = I.Workload(w.name + "_sample64", 64, w.n, w.s, w.Q, w.P, bumps=I.draw_bumps(8, 1))
+    sub = cpu_sample(w)
     G1 = O.dgf_octant(w.Q, 128, 2)
-    prm = O.Params(N=64, n=w.n, s=w.s, Q=w.Q, P=w.P)
+    prm = O.Params(N=sub.N, n=sub.n, s=sub.s, Q=sub.Q, P=sub.P)
     f = sub.charge()
     for _ in range(args.warmup):
         O.solve_open(prm, f, G1=G1)
@@ -597,16 +765,16 @@ def run_reference(args, w):
     for _ in range(args.steps):
         O.solve_open(prm, f, G1=G1)
     dt = (time.perf_counter() - t0) / args.steps
-    val = 64.0 ** 3 / dt / 1e6
+    val = float(sub.N) ** 3 / dt / 1e6
+    sample = (f"each step one oracle solve of the 64^3 sub-problem of {args.workload} (64 patches of 16^3, "
+              f"support 16, Q = {w.Q}, 8 bumps, seed 1); Mpoints/s of that sample")
     line = {
         "impl": "reference", "metric": METRIC, "value": round(val, 5), "unit": "Mpoints/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": args.workload, "N": w.N, "patch": w.n, "support": w.s, "Q": w.Q, "P": w.P,
-                   "tier": "fp64"},
-        "cpu_baseline": {"value": round(val, 5), "unit": "Mpoints/s", "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": "64^3 sub-problem (8 patches of 16^3, support 16, 8 bumps, seed 1) per step"},
+        "data": "synthetic", "config": bench_config(args, w, tier, world),
+        "cpu_baseline": {"value": round(val, 5), "unit": "Mpoints/s", "cores": oracle_threads(), "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": round(val, 5), "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

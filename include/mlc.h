@@ -180,7 +180,8 @@ mlc_status mlc_solve_noalloc(mlc_plan_t plan, const void *f, void *phi, void *st
 /*
  * As mlc_solve with host arrays: copies f (host, pinned or pageable) to the
  * plan's device staging buffer, solves, copies phi back to the host array and
- * synchronises the stream before returning.
+ * synchronises the stream (not the device) before returning.  Reports TIMEOUT
+ * like mlc_plan_status if a bounded wait of this solve gave up.
  */
 mlc_status mlc_solve_host(mlc_plan_t plan, const void *f_host, void *phi_host, void *stream);
 
@@ -194,8 +195,9 @@ mlc_status mlc_batch_solve(int count, const mlc_plan_t *plans, const void *const
                            void *const *phi, void *stream);
 
 /* Stage exports for testing: copy an intermediate result of the last solve
+ * (or, for the index stages, the plan's indexing as the kernels compute it)
  * to host memory (FP64 unless noted).  `bytes` must equal the stage's size,
- * returned by mlc_debug_stage_bytes. */
+ * returned by mlc_debug_stage_bytes.  Both synchronise the device. */
 typedef enum {
     MLC_STAGE_MOMENTS = 0,  /* Legendre coefficients c_p^i, [patch][p] (Sec. 4, Step 1)      */
     MLC_STAGE_FH = 1,       /* coarse charge F^H on its extent [lo,hi]^3 (Step 2)            */
@@ -203,7 +205,19 @@ typedef enum {
     MLC_STAGE_PHIB = 3,     /* boundary values phi^B on the face planes,
                                [axis][plane j][u][v], plane x_axis = j n, (u,v) the other
                                two coordinates in increasing axis order (Step 3)             */
-    MLC_STAGE_DGF = 4       /* the DGF octant G^{h=1}[0..L]^3, L = entry 14 of mlc_plan_info  */
+    MLC_STAGE_DGF = 4,      /* the DGF octant G^{h=1}[0..L]^3, L = entry 14 of mlc_plan_info  */
+    MLC_STAGE_COARSE_SAMPLES = 5, /* local fields phi^{i,h} at the coarse points of each patch's
+                               field box: [patch][k0][k1][k2], k in [-s/4, (n+s)/4] relative
+                               to the patch's coarse origin n i / 4 (Step 1, eq. FDLD)      */
+    MLC_STAGE_FACE_INDEX = 6, /* int32 (not FP64): the patch indexing of Step 3 (eq.
+                               philocmlcII) for every face-plane node, nodes in the order of
+                               MLC_STAGE_PHIB: offsets[nodes + 1], then entries; node k owns
+                               entries offsets[k] .. offsets[k+1]-1, each 2 i + 0 if
+                               Omega_alpha(i) holds the node, 2 i + 1 if only Omega_beta(i)
+                               does (i the patch's linear index), ascending i               */
+    MLC_STAGE_COARSE_INDEX = 7 /* int32: the same for every coarse node of the F^H extent
+                               ([k0][k1][k2] order) and the coarse boxes C(Omega_alpha(i)),
+                               C(Omega_beta(i)) (eq. FDLD)                                */
 } mlc_stage;
 
 mlc_status mlc_debug_stage_bytes(mlc_plan_t plan, int stage, size_t *bytes);
@@ -216,6 +230,13 @@ mlc_status mlc_debug_stage_bytes(mlc_plan_t plan, int stage, size_t *bytes);
  * kernel, inverse), inverse y, inverse x; boundary values; Dirichlet solves.
  * count must be >= 13. */
 mlc_status mlc_debug_set_timing(mlc_plan_t plan, int enable);
+/* Test hook for the failure path of the bounded waits (no counterpart in the
+ * paper): kind 1 makes later solves with this plan skip the bulk copy that the
+ * local-convolution inverse-x kernel waits for, with the wait limited to 64
+ * tests, so every such wait runs out, the kernel records the failure and
+ * returns, and mlc_plan_status reports TIMEOUT (the potential is then not
+ * valid).  kind 0 restores normal solves.  INVALID_ARG for other kinds. */
+mlc_status mlc_debug_set_fault(mlc_plan_t plan, int kind);
 mlc_status mlc_debug_timing(mlc_plan_t plan, float *ms_out, int count);
 /* Configuration the batch autotuner chose for these arrays (as passed to
  * mlc_batch_solve): 2 x (parallel branches of the per-problem coarse steps)

@@ -647,6 +647,8 @@ def mlc_solve(prm: Params, f_closed: np.ndarray, G1: np.ndarray | None = None, s
         phi[o[0]:o[0] + n + 1, o[1]:o[1] + n + 1, o[2]:o[2] + n + 1] = U[i]
 
     if stages is not None:
+        # local fields at the coarse points of each field box, (patches, points)
+        stages["coarse_samples"] = PHI[phi_set.index(coarse_field)].T.copy()
         stages["moments"] = Cmom.T.copy()
         stages["FH"] = FH
         stages["FH_lo"] = flo
@@ -655,6 +657,62 @@ def mlc_solve(prm: Params, f_closed: np.ndarray, G1: np.ndarray | None = None, s
         stages["face_nodes"] = gface
         stages["phiB"] = phiB
     return phi
+
+
+# ---------------------------------------------------------------------------
+# Patch indexing of Sec. 4 by membership tests (regions are closed boxes, R5)
+# ---------------------------------------------------------------------------
+
+def _members_1d(lo: int, hi: int, count: int, c: int, step: int) -> list:
+    """Patch indices i (one axis) with c in [step i + lo, step i + hi]."""
+    return [i for i in range(count) if step * i + lo <= c <= step * i + hi]
+
+
+def face_patch_index(prm: Params, nodes: np.ndarray):
+    """For each face-lattice node g (rows of ``nodes``), the patches i with g in
+    Omega_beta(i) = G(Omega_i, g_beta) in ascending linear index, as entries
+    2 i + 0 if g is in Omega_alpha(i) as well and 2 i + 1 otherwise (the sums
+    of eq. philocmlcII).  Boxes are products of intervals, so membership is
+    tested axis by axis.  Returns (offsets, entries), node k owning
+    entries[offsets[k]:offsets[k+1]]."""
+    n, npp = prm.n, prm.np_
+    alo, ahi = prm.alpha_box
+    blo, bhi = prm.beta_box
+    offs = [0]
+    ent = []
+    for g in np.asarray(nodes, dtype=np.int64):
+        per_b = [_members_1d(blo, bhi, npp, int(g[d]), n) for d in range(3)]
+        per_a = [_members_1d(alo, ahi, npp, int(g[d]), n) for d in range(3)]
+        for i0 in per_b[0]:
+            for i1 in per_b[1]:
+                for i2 in per_b[2]:
+                    inA = i0 in per_a[0] and i1 in per_a[1] and i2 in per_a[2]
+                    ent.append(2 * ((i0 * npp + i1) * npp + i2) + (0 if inA else 1))
+        offs.append(len(ent))
+    return np.array(offs, dtype=np.int64), np.array(ent, dtype=np.int64)
+
+
+def coarse_patch_index(prm: Params):
+    """For each coarse node k of the F^H extent ([k0][k1][k2] order), the
+    patches i with k in C(Omega_beta(i)) in ascending linear index, as entries
+    2 i + 0 if k is in C(Omega_alpha(i)) as well and 2 i + 1 otherwise (the
+    two cases of eq. FDLD).  Returns (offsets, entries)."""
+    q, npp = prm.n // 4, prm.np_
+    calo, cahi = prm.c_alpha
+    cblo, cbhi = prm.c_beta
+    flo, fhi = prm.fh_extent
+    offs = [0]
+    ent = []
+    for k in box_points(flo, fhi):
+        per_b = [_members_1d(cblo, cbhi, npp, int(k[d]), q) for d in range(3)]
+        per_a = [_members_1d(calo, cahi, npp, int(k[d]), q) for d in range(3)]
+        for i0 in per_b[0]:
+            for i1 in per_b[1]:
+                for i2 in per_b[2]:
+                    inA = i0 in per_a[0] and i1 in per_a[1] and i2 in per_a[2]
+                    ent.append(2 * ((i0 * npp + i1) * npp + i2) + (0 if inA else 1))
+        offs.append(len(ent))
+    return np.array(offs, dtype=np.int64), np.array(ent, dtype=np.int64)
 
 
 def dirichlet_solve(prm: Params, U: np.ndarray, fp: np.ndarray) -> np.ndarray:

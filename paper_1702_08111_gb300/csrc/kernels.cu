@@ -251,9 +251,10 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
         : "memory");
     return ok != 0;
 }
-// Bounded wait for phase `parity` of an mbarrier; false if it did not complete.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
-    for (int i = 0; i < (1 << 22); ++i)
+// Bounded wait for phase `parity` of an mbarrier (at most `tries` suspending
+// tests); false if it did not complete.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity, int tries) {
+    for (int i = 0; i < tries; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -1164,6 +1165,8 @@ struct InvXPArgs {
     int zrow[64];
     int maxfft;       // most transformed rows of any z row (sizes the line buffer)
     int blk;          // complex entries per (patch, z row) input block (16-byte multiple)
+    int wait_tries;   // limit of the bounded wait for the block's bulk copy
+    int skip_copy;    // test hook: issue no bulk copy, so the bounded wait runs out
 };
 
 __device__ __forceinline__ bool in_alpha(int c, int n, int ga) { return c >= -ga && c <= n + ga; }
@@ -1202,14 +1205,14 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         mbar_expect_tx(&bar, bytes);
-        bulk_g2s(raw, in, bytes, &bar);
+        if (!a.skip_copy) bulk_g2s(raw, in, bytes, &bar);
     }
     __syncthreads();
-    const bool arrived = mbar_wait_bounded(&bar, 0);
+    const bool arrived = mbar_wait_bounded(&bar, 0, a.wait_tries);
     if (__syncthreads_or(!arrived)) {  // uniform decision for the whole CTA
         if (threadIdx.x == 0) {
             atomicExch(PP.err, 1);
-            mbar_wait_bounded(&bar, 0);  // one more bounded wait for the copy in flight
+            mbar_wait_bounded(&bar, 0, a.wait_tries);  // one more bounded wait for the copy in flight
         }
         return;
     }
@@ -1330,7 +1333,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 8 : 4) k_inv_x64(InvXPAr
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         mbar_expect_tx(&bar, bytes);
-        bulk_g2s(raw, in, bytes, &bar);
+        if (!a.skip_copy) bulk_g2s(raw, in, bytes, &bar);
     }
     const int kl = -s / 4;
     // x classification: bit 0 in the field box, 1 in alpha, 2 on a face plane, 3 coarse
@@ -1344,11 +1347,11 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 8 : 4) k_inv_x64(InvXPAr
         xcoarse[pos] = (x >> 2) - kl;
     }
     __syncthreads();
-    const bool arrived = mbar_wait_bounded(&bar, 0);
+    const bool arrived = mbar_wait_bounded(&bar, 0, a.wait_tries);
     if (__syncthreads_or(!arrived)) {  // uniform decision for the whole CTA
         if (threadIdx.x == 0) {
             atomicExch(PP.err, 1);
-            mbar_wait_bounded(&bar, 0);  // one more bounded wait for the copy in flight
+            mbar_wait_bounded(&bar, 0, a.wait_tries);  // one more bounded wait for the copy in flight
         }
         return;
     }
@@ -1672,6 +1675,30 @@ struct AsmArgs {
     double coefd[4];  // the same in FP64
 };
 
+// Patches i (ascending linear index) whose coarse box C(Omega_beta(i)) holds
+// the coarse node k (Sec. 2 coarsening C(D), Sec. 4 eq. FDLD), with k - n i/4
+// relative to the patch and whether C(Omega_alpha(i)) holds k too:
+// f(p, r0, r1, r2, in_alpha).
+template <typename F>
+__device__ __forceinline__ void coarse_node_patches(const int k[3], int n, int np, int ca_lo, int ca_hi,
+                                                    int cb_lo, int cb_hi, F &&f) {
+    const int q = n / 4;
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = max(0, -floordiv(-(k[d] - cb_hi), q));  // ceil((k - cb_hi)/q)
+        hi[d] = min(np - 1, floordiv(k[d] - cb_lo, q));
+    }
+    for (int i0 = lo[0]; i0 <= hi[0]; ++i0)
+        for (int i1 = lo[1]; i1 <= hi[1]; ++i1)
+            for (int i2 = lo[2]; i2 <= hi[2]; ++i2) {
+                const int r0 = k[0] - q * i0, r1 = k[1] - q * i1, r2 = k[2] - q * i2;
+                const long p = ((long)i0 * np + i1) * np + i2;
+                const bool inA = r0 >= ca_lo && r0 <= ca_hi && r1 >= ca_lo && r1 <= ca_hi && r2 >= ca_lo &&
+                                 r2 <= ca_hi;
+                f(p, r0, r1, r2, inA);
+            }
+}
+
 // F^H[k] = sum over patches i (ascending) of Delta^H phi^{i,h} on C(Omega_alpha(i))
 // or sum_p c_p^i Delta^H(G^h * Q^p) on C(Omega_beta(i)) \ C(Omega_alpha(i)).
 // TB: local-field storage, RT: ring tables, T: accumulation (FP64 or double-float).
@@ -1684,22 +1711,11 @@ __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
     k[2] = (int)(idx % a.nf) + a.flo;
     k[1] = (int)((idx / a.nf) % a.nf) + a.flo;
     k[0] = (int)(idx / ((long)a.nf * a.nf)) + a.flo;
-    const int q = a.n / 4;
-    int lo[3], hi[3];
-    for (int d = 0; d < 3; ++d) {
-        lo[d] = max(0, -floordiv(-(k[d] - a.cb_hi), q));  // ceil((k - cb_hi)/q)
-        hi[d] = min(a.np - 1, floordiv(k[d] - a.cb_lo, q));
-    }
     const int ncb = a.cb_hi - a.cb_lo + 1;
     const long nc = a.nc, kl = -a.s / 4;
     T acc = FT<T>::zero();
-    for (int i0 = lo[0]; i0 <= hi[0]; ++i0)
-        for (int i1 = lo[1]; i1 <= hi[1]; ++i1)
-            for (int i2 = lo[2]; i2 <= hi[2]; ++i2) {
-                const int r0 = k[0] - q * i0, r1 = k[1] - q * i1, r2 = k[2] - q * i2;
-                const long p = ((long)i0 * a.np + i1) * a.np + i2;
-                const bool inA = r0 >= a.ca_lo && r0 <= a.ca_hi && r1 >= a.ca_lo &&
-                                 r1 <= a.ca_hi && r2 >= a.ca_lo && r2 <= a.ca_hi;
+    coarse_node_patches(k, a.n, a.np, a.ca_lo, a.ca_hi, a.cb_lo, a.cb_hi,
+                        [&](long p, int r0, int r1, int r2, bool inA) {
                 if (inA) {
                     const TB *bx = (const TB *)a.cl + p * nc * nc * nc;
 #pragma unroll
@@ -1718,8 +1734,45 @@ __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
                                     (r2 - a.cb_lo)) * a.npoly;
                     acc = acc + ring_row<T>((const RT *)a.mom + p * a.npad, (const RT *)a.T + t, a.npoly);
                 }
-            }
+            });
     a.FH[idx] = FT<T>::to(acc);
+}
+
+// Patches i (ascending linear index) whose Omega_beta(i) holds the
+// face-lattice node g (Sec. 4, eq. philocmlcII), with g - n i relative to the
+// patch and whether Omega_alpha(i) holds g too: f(p, r0, r1, r2, in_alpha).
+// Regions are closed boxes; NN is the patch size n.
+template <int NN, typename F>
+__device__ __forceinline__ void face_node_patches(const int g[3], int np, int ga, int gb, F &&f) {
+    constexpr int n = NN;
+    int lo[3], hi[3], alo[3], ahi[3];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = max(0, -floordiv(-(g[d] - n - gb), n));
+        hi[d] = min(np - 1, floordiv(g[d] + gb, n));
+        alo[d] = max(0, -floordiv(-(g[d] - n - ga), n));
+        ahi[d] = min(np - 1, floordiv(g[d] + ga, n));
+    }
+    for (int i0 = lo[0]; i0 <= hi[0]; ++i0)
+        for (int i1 = lo[1]; i1 <= hi[1]; ++i1)
+            for (int i2 = lo[2]; i2 <= hi[2]; ++i2) {
+                const long p = ((long)i0 * np + i1) * np + i2;
+                const int r0 = g[0] - n * i0, r1 = g[1] - n * i1, r2 = g[2] - n * i2;
+                const bool inA = i0 >= alo[0] && i0 <= ahi[0] && i1 >= alo[1] && i1 <= ahi[1] &&
+                                 i2 >= alo[2] && i2 <= ahi[2];
+                f(p, r0, r1, r2, inA);
+            }
+}
+
+// Face-plane node idx in [axis][plane j][u][v] order -> g (plane x_axis = j n).
+__device__ __forceinline__ void face_plane_node(long idx, int N, int np, int n, int g[3], int &axis) {
+    const long pn = (long)(N + 1) * (N + 1);
+    axis = (int)(idx / ((np + 1) * pn));
+    const int j = (int)((idx / pn) % (np + 1));
+    const int u = (int)((idx % pn) / (N + 1)), v = (int)(idx % (N + 1));
+    const int jn = j * n;
+    g[0] = axis == 0 ? jn : u;
+    g[1] = axis == 0 ? u : (axis == 1 ? jn : v);
+    g[2] = axis == 2 ? jn : v;
 }
 
 struct BndArgs {
@@ -1745,11 +1798,8 @@ __global__ void __launch_bounds__(128, sizeof(RT) == 4 ? 8 : 6) k_boundary(BndAr
     if (idx >= tot) return;
     const T *phiH = (const T *)a.phiH;
     const T *resid = (const T *)a.resid;
-    const int axis = (int)(idx / ((a.np + 1) * pn));
-    const int j = (int)((idx / pn) % (a.np + 1));
-    const int u = (int)((idx % pn) / (a.N + 1)), v = (int)(idx % (a.N + 1));
-    const int jn = j * n;
-    const int g[3] = {axis == 0 ? jn : u, axis == 0 ? u : (axis == 1 ? jn : v), axis == 2 ? jn : v};
+    int g[3], axis;
+    face_plane_node(idx, a.N, a.np, n, g, axis);
     // I^H(phi^H)(g): tensor Lagrange over the in-plane axes (R4), applied as
     // nested 1D sums (K^2 + K + 1 FMAs for two nontrivial axes)
     const int K = 2 * a.b + 2;
@@ -1784,20 +1834,7 @@ __global__ void __launch_bounds__(128, sizeof(RT) == 4 ? 8 : 6) k_boundary(BndAr
     // local corrections of the patches whose Omega_beta holds g (ascending index);
     // the Legendre ring terms accumulate in the ring precision RT
     RT ring(0.0);
-    int lo[3], hi[3], alo[3], ahi[3];
-    for (int d = 0; d < 3; ++d) {
-        lo[d] = max(0, -floordiv(-(g[d] - n - a.gb), n));
-        hi[d] = min(a.np - 1, floordiv(g[d] + a.gb, n));
-        alo[d] = max(0, -floordiv(-(g[d] - n - a.ga), n));
-        ahi[d] = min(a.np - 1, floordiv(g[d] + a.ga, n));
-    }
-    for (int i0 = lo[0]; i0 <= hi[0]; ++i0)
-        for (int i1 = lo[1]; i1 <= hi[1]; ++i1)
-            for (int i2 = lo[2]; i2 <= hi[2]; ++i2) {
-                const long p = ((long)i0 * a.np + i1) * a.np + i2;
-                const int r0 = g[0] - n * i0, r1 = g[1] - n * i1, r2 = g[2] - n * i2;
-                const bool inA = i0 >= alo[0] && i0 <= ahi[0] && i1 >= alo[1] && i1 <= ahi[1] &&
-                                 i2 >= alo[2] && i2 <= ahi[2];
+    face_node_patches<NN>(g, a.np, a.ga, a.gb, [&](long p, int r0, int r1, int r2, bool inA) {
                 if (inA) {
                     // the residual plane holding r: first axis on a face plane
                     int d, uu, vv;
@@ -1814,8 +1851,46 @@ __global__ void __launch_bounds__(128, sizeof(RT) == 4 ? 8 : 6) k_boundary(BndAr
                     const long row = (((long)axis * a.npb + (ra - a.pb0) / n) * a.wbx + (ru + a.gb)) * a.wbx + (rv + a.gb);
                     ring_dot((const RT *)a.mom + p * a.npad, (const RT *)a.D + row * a.npad, a.npad, ring);
                 }
-            }
+            });
     ((T *)a.phiB)[idx] = FT<T>::rn(acc + FT<T>::of(ring));
+}
+
+// Index export (test hook): for every face-plane node ([axis][plane][u][v]
+// order) the patches whose Omega_beta holds it, enumerated by
+// face_node_patches -- the code the boundary kernel runs.  COUNT pass:
+// cnt[node] = number of patches; fill pass: entries 2 p + (ring ? 1 : 0)
+// from off[node], in enumeration (ascending patch) order.
+template <int NN, bool COUNT>
+__global__ void __launch_bounds__(128) k_index_face(int N, int np, int ga, int gb, long tot, int *cnt,
+                                                    const long *off, int *ent) {
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= tot) return;
+    int g[3], axis;
+    face_plane_node(idx, N, np, NN, g, axis);
+    int c = 0;
+    const long o = COUNT ? 0 : off[idx];
+    face_node_patches<NN>(g, np, ga, gb, [&](long p, int, int, int, bool inA) {
+        if (!COUNT) ent[o + c] = (int)(2 * p + (inA ? 0 : 1));
+        ++c;
+    });
+    if (COUNT) cnt[idx] = c;
+}
+
+// The same for every coarse node k of the F^H extent ([k0][k1][k2] order),
+// enumerated by coarse_node_patches -- the code the F^H assembly runs.
+template <bool COUNT>
+__global__ void __launch_bounds__(128) k_index_coarse(int n, int np, int ca_lo, int ca_hi, int cb_lo, int cb_hi,
+                                                      int flo, int nf, int *cnt, const long *off, int *ent) {
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)nf * nf * nf) return;
+    const int k[3] = {(int)(idx / ((long)nf * nf)) + flo, (int)((idx / nf) % nf) + flo, (int)(idx % nf) + flo};
+    int c = 0;
+    const long o = COUNT ? 0 : off[idx];
+    coarse_node_patches(k, n, np, ca_lo, ca_hi, cb_lo, cb_hi, [&](long p, int, int, int, bool inA) {
+        if (!COUNT) ent[o + c] = (int)(2 * p + (inA ? 0 : 1));
+        ++c;
+    });
+    if (COUNT) cnt[idx] = c;
 }
 
 struct DirArgs {
@@ -1967,8 +2042,12 @@ __global__ void __launch_bounds__(256, 4) k_dirichlet(DirArgs a) {
     }
     __syncthreads();
     T cw[4];
+    bool cwz[4];  // zero weights (tested once: FP64 compares run on the slow FP64 pipe)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) cw[k] = s_w[k];
+    for (int k = 0; k < 4; ++k) {
+        cw[k] = s_w[k];
+        cwz[k] = a.b[k] == 0.0;
+    }
     const T c2h2 = s_w[4];
     // right-hand side: f - Delta^h(boundary data); only the layer next to the
     // boundary sees boundary values
@@ -1987,9 +2066,11 @@ __global__ void __launch_bounds__(256, 4) k_dirichlet(DirArgs a) {
                         const int nz = (s0 != 0) + (s1 != 0) + (s2 != 0);
                         const int d0 = c0 + s0, d1 = c1 + s1, d2 = c2 + s2;
                         const bool bd = d0 == 0 || d0 == n || d1 == 0 || d1 == n || d2 == 0 || d2 == n;
-                        if (FT<T>::is0(cw[nz]) || !bd) continue;  // interior neighbours carry no boundary data
+                        if (cwz[nz] || !bd) continue;  // interior neighbours carry no boundary data
                         const T u = Uat(d0, d1, d2);
-                        if (!FT<T>::is0(u)) v = v - cw[nz] * u;
+                        // double-float: skip zero data (an FP32 test saves a product);
+                        // FP64: the product costs less than a test on the FP64 pipe
+                        if (std::is_same<T, double>::value || !FT<T>::is0(u)) v = v - cw[nz] * u;
                     }
         }
         X[e] = v;
@@ -2253,7 +2334,11 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
     }
     mark(pl, 3, st);
     {
-        InvXPArgs a{it, tw, g.n, g.s, W, g.ga, g.npa, g.pl0, g.wa, g.nc, nz, {}, 0, g.a4blk};
+        InvXPArgs a{it, tw, g.n, g.s, W, g.ga, g.npa, g.pl0, g.wa, g.nc, nz, {}, 0, g.a4blk, 1 << 22, 0};
+        if (pl->fault == 1) {  // test hook: the wait must run out, quickly
+            a.skip_copy = 1;
+            a.wait_tries = 64;
+        }
         for (int j = 0; j < nz; ++j) a.zrow[j] = zrow[j];
         // rows needing a full transform, per z row (the same rule as the kernel)
         auto inA = [&](int c) { return c >= -g.ga && c <= g.n + g.ga; };
@@ -2552,6 +2637,36 @@ cudaError_t launch_dirichlet(const mlc_plan_s *pl, const Items &it, cudaStream_t
         default: return cudaErrorInvalidValue;
     }
 #undef MLC_DIR
+    return cudaGetLastError();
+}
+
+// Index export (test hook): which = 0 face-plane nodes, 1 coarse nodes of
+// the F^H extent; cnt != nullptr: count pass, else fill pass.
+cudaError_t launch_index_export(const mlc_plan_s *pl, int which, int *cnt, const long *off, int *ent,
+                                cudaStream_t st) {
+    const Geom &g = pl->g;
+    if (which == 1) {
+        const long tot = (long)g.nf * g.nf * g.nf;
+        const unsigned nbk = (unsigned)((tot + 127) / 128);
+        if (cnt) k_index_coarse<true><<<nbk, 128, 0, st>>>(g.n, g.np, g.ca_lo, g.ca_hi, g.cb_lo, g.cb_hi, g.flo, g.nf, cnt, off, ent);
+        else k_index_coarse<false><<<nbk, 128, 0, st>>>(g.n, g.np, g.ca_lo, g.ca_hi, g.cb_lo, g.cb_hi, g.flo, g.nf, cnt, off, ent);
+        return cudaGetLastError();
+    }
+    const long tot = g.n_planes_total;
+    const unsigned nbk = (unsigned)((tot + 127) / 128);
+#define MLC_IDX(NN)                                                                                    \
+    case NN:                                                                                           \
+        if (cnt) k_index_face<NN, true><<<nbk, 128, 0, st>>>(g.N, g.np, g.ga, g.gb, tot, cnt, off, ent);  \
+        else k_index_face<NN, false><<<nbk, 128, 0, st>>>(g.N, g.np, g.ga, g.gb, tot, cnt, off, ent);     \
+        break;
+    switch (g.n) {
+        MLC_IDX(4)
+        MLC_IDX(8)
+        MLC_IDX(12)
+        MLC_IDX(16)
+        default: return cudaErrorInvalidValue;
+    }
+#undef MLC_IDX
     return cudaGetLastError();
 }
 

@@ -137,6 +137,7 @@ struct mlc_plan_s {
     void *scratch = nullptr;       // own local-convolution scratch, min(chunk, NP) patches (a1
                                    // then a4), allocated by the first solve that needs it
     void *user_scratch = nullptr;  // caller-owned scratch (mlc_plan_set_scratch), if any
+    int fault = 0;                 // test hook (mlc_debug_set_fault)
     void *cl;                // NP x nc^3 local fields on the coarse lattice of the field box (FP32 / double-float)
     void *fpl;               // NP x 3 npa x wa^2 local fields on the face planes inside alpha (FP32 / double-float)
     double *mom;             // NP x npad
@@ -178,6 +179,10 @@ cudaError_t launch_dirichlet(const mlc_plan_s *pl, const Items &it, cudaStream_t
 cudaError_t launch_assemble(const mlc_plan_s *pl, cudaStream_t st);
 cudaError_t launch_coarse(const mlc_plan_s *pl, cudaStream_t st);
 cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st);
+// Index export (test hook): which = 0 face-plane nodes, 1 coarse nodes of the
+// F^H extent; count pass (cnt != nullptr) or fill pass (off, ent).
+cudaError_t launch_index_export(const mlc_plan_s *pl, int which, int *cnt, const long *off, int *ent,
+                                cudaStream_t st);
 void configure_kernels();
 // Write f and phi into a device PlanPtrs record, in stream order.
 cudaError_t launch_set_ptrs(PlanPtrs *d, const void *f, double *phi, cudaStream_t st);

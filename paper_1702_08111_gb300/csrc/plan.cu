@@ -808,8 +808,16 @@ mlc_status mlc_solve_host(mlc_plan_t pl, const void *f_host, void *phi_host, voi
     TRY_CUDA(cudaMemcpyAsync(pl->f_stage, f_host, fbytes, cudaMemcpyHostToDevice, st));
     TRY(mlc_solve(pl, pl->f_stage, pl->phi_stage, stream));
     TRY_CUDA(cudaMemcpyAsync(phi_host, pl->phi_stage, N3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    // the plan's error word, read in stream order (no device-wide synchronisation)
+    int e = 0;
+    TRY_CUDA(cudaMemcpyAsync(&e, pl->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     TRY_CUDA(cudaStreamSynchronize(st));
-    return mlc_plan_status(pl);
+    if (e) {
+        TRY_CUDA(cudaMemsetAsync(pl->err, 0, sizeof(int), st));
+        TRY_CUDA(cudaStreamSynchronize(st));
+        return MLC_ERR_TIMEOUT;
+    }
+    return MLC_OK;
 }
 
 mlc_status mlc_plan_status(mlc_plan_t pl) {
@@ -821,6 +829,12 @@ mlc_status mlc_plan_status(mlc_plan_t pl) {
         TRY_CUDA(cudaMemset(pl->err, 0, sizeof(int)));
         return MLC_ERR_TIMEOUT;
     }
+    return MLC_OK;
+}
+
+mlc_status mlc_debug_set_fault(mlc_plan_t pl, int kind) {
+    if (!pl || kind < 0 || kind > 1) return MLC_ERR_INVALID_ARG;
+    pl->fault = kind;
     return MLC_OK;
 }
 
@@ -844,6 +858,23 @@ mlc_status mlc_debug_timing(mlc_plan_t pl, float *ms, int count) {
     return MLC_OK;
 }
 
+// Patch counts of the index stages (count pass on the device) as offsets.
+mlc_status index_offsets(mlc_plan_t pl, int which, std::vector<long> &off) {
+    const Geom &g = pl->g;
+    const long nodes = which ? (long)g.nf * g.nf * g.nf : g.n_planes_total;
+    int *cnt = nullptr;
+    TRY_CUDA(cudaMalloc((void **)&cnt, nodes * sizeof(int)));
+    cudaError_t e = launch_index_export(pl, which, cnt, nullptr, nullptr, 0);
+    std::vector<int> h(nodes);
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), cnt, nodes * sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(cnt);
+    TRY_CUDA(e);
+    off.assign(nodes + 1, 0);
+    for (long k = 0; k < nodes; ++k) off[k + 1] = off[k] + h[k];
+    if (off[nodes] > INT32_MAX) return MLC_ERR_UNSUPPORTED;
+    return MLC_OK;
+}
+
 mlc_status mlc_debug_stage_bytes(mlc_plan_t pl, int stage, size_t *bytes) {
     if (!pl || !bytes) return MLC_ERR_INVALID_ARG;
     const Geom &g = pl->g;
@@ -853,6 +884,14 @@ mlc_status mlc_debug_stage_bytes(mlc_plan_t pl, int stage, size_t *bytes) {
         case MLC_STAGE_PHIH: *bytes = (size_t)g.no * g.no * g.no * 8; break;
         case MLC_STAGE_PHIB: *bytes = (size_t)g.n_planes_total * 8; break;
         case MLC_STAGE_DGF: *bytes = (size_t)(pl->dgf_L + 1) * (pl->dgf_L + 1) * (pl->dgf_L + 1) * 8; break;
+        case MLC_STAGE_COARSE_SAMPLES: *bytes = (size_t)g.NP * g.nc * g.nc * g.nc * 8; break;
+        case MLC_STAGE_FACE_INDEX:
+        case MLC_STAGE_COARSE_INDEX: {
+            std::vector<long> off;
+            TRY(index_offsets(pl, stage == MLC_STAGE_COARSE_INDEX, off));
+            *bytes = (off.size() + (size_t)off.back()) * sizeof(int32_t);
+            break;
+        }
         default: return MLC_ERR_INVALID_ARG;
     }
     return MLC_OK;
@@ -862,8 +901,28 @@ mlc_status mlc_debug_export(mlc_plan_t pl, int stage, void *host, size_t bytes) 
     size_t need = 0;
     TRY(mlc_debug_stage_bytes(pl, stage, &need));
     if (!host || bytes != need) return MLC_ERR_INVALID_ARG;
+    if (stage == MLC_STAGE_FACE_INDEX || stage == MLC_STAGE_COARSE_INDEX) {
+        const int which = stage == MLC_STAGE_COARSE_INDEX;
+        std::vector<long> off;
+        TRY(index_offsets(pl, which, off));
+        const long nodes = (long)off.size() - 1, total = off.back();
+        long *doff = nullptr;
+        int *dent = nullptr;
+        TRY_CUDA(cudaMalloc((void **)&doff, off.size() * sizeof(long)));
+        cudaError_t e = cudaMalloc((void **)&dent, std::max<long>(total, 1) * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemcpy(doff, off.data(), off.size() * sizeof(long), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = launch_index_export(pl, which, nullptr, doff, dent, 0);
+        int32_t *out = (int32_t *)host;
+        for (long k = 0; k <= nodes; ++k) out[k] = (int32_t)off[k];
+        if (e == cudaSuccess) e = cudaMemcpy(out + nodes + 1, dent, total * sizeof(int), cudaMemcpyDeviceToHost);
+        cudaFree(doff);
+        cudaFree(dent);
+        TRY_CUDA(e);
+        return MLC_OK;
+    }
     const void *src = nullptr;
     switch (stage) {
+        case MLC_STAGE_COARSE_SAMPLES: src = pl->cl; break;
         case MLC_STAGE_MOMENTS: src = pl->mom; break;
         case MLC_STAGE_FH: src = pl->FH; break;
         case MLC_STAGE_PHIH: src = pl->phiH; break;
@@ -875,6 +934,20 @@ mlc_status mlc_debug_export(mlc_plan_t pl, int stage, void *host, size_t bytes) 
     if (stage == MLC_STAGE_MOMENTS) {  // rows are stored with stride npad
         TRY_CUDA(cudaMemcpy2D(host, pl->g.npoly * sizeof(double), src, pl->g.npad * sizeof(double),
                               pl->g.npoly * sizeof(double), pl->g.NP, cudaMemcpyDeviceToHost));
+        return MLC_OK;
+    }
+    if (stage == MLC_STAGE_COARSE_SAMPLES && pl->g.conv != CONV_F64) {  // FP32 or double-float storage
+        const size_t cnt = bytes / sizeof(double);
+        double *out = (double *)host;
+        if (pl->g.conv == CONV_F32) {
+            std::vector<float> tmp(cnt);
+            TRY_CUDA(cudaMemcpy(tmp.data(), src, cnt * sizeof(float), cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < cnt; ++i) out[i] = tmp[i];
+        } else {
+            std::vector<float2> tmp(cnt);
+            TRY_CUDA(cudaMemcpy(tmp.data(), src, cnt * sizeof(float2), cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < cnt; ++i) out[i] = (double)tmp[i].x + (double)tmp[i].y;
+        }
         return MLC_OK;
     }
     if ((stage == MLC_STAGE_PHIH || stage == MLC_STAGE_PHIB) && pl->g.fine == FINE_DF) {

@@ -19,6 +19,7 @@ F32_CHARGE_TIERS = (MLC_TIER_SPLIT, MLC_TIER_SPLIT_DF)
 TIER_NAMES = {MLC_TIER_FP64: "fp64", MLC_TIER_SPLIT: "split", MLC_TIER_DF: "df", MLC_TIER_SPLIT_DF: "split_df"}
 MLC_MODE_MLC, MLC_MODE_MLC0 = 0, 1
 STAGE_MOMENTS, STAGE_FH, STAGE_PHIH, STAGE_PHIB, STAGE_DGF = 0, 1, 2, 3, 4
+STAGE_COARSE_SAMPLES, STAGE_FACE_INDEX, STAGE_COARSE_INDEX = 5, 6, 7
 
 EXPORTED = [
     "mlc_params_init", "mlc_plan_create", "mlc_plan_create_ex", "mlc_plan_destroy",
@@ -26,7 +27,7 @@ EXPORTED = [
     "mlc_debug_stage_bytes", "mlc_debug_export", "mlc_plan_info", "mlc_server_create",
     "mlc_server_destroy", "mlc_server_enqueue", "mlc_server_wait", "mlc_status_string",
     "mlc_debug_set_timing", "mlc_debug_timing", "mlc_solve_noalloc", "mlc_plan_status",
-    "mlc_debug_batch_choice", "mlc_plan_scratch_bytes", "mlc_plan_set_scratch",
+    "mlc_debug_batch_choice", "mlc_plan_scratch_bytes", "mlc_plan_set_scratch", "mlc_debug_set_fault",
 ]
 LAUNCH_NAMES = ["moments", "conv_fwd_x", "conv_slab", "conv_inv_x", "resid", "assemble",
                 "coarse_fwd_x", "coarse_fwd_y", "coarse_z_kernel", "coarse_inv_y", "coarse_inv_x",
@@ -89,6 +90,7 @@ def load_library(path: str = LIB_PATH):
     lib.mlc_server_enqueue.argtypes = [vp, ctypes.POINTER(mlc_request), ctypes.POINTER(ctypes.c_uint64)]
     lib.mlc_server_wait.argtypes = [vp, ctypes.c_uint64, i, ctypes.POINTER(mlc_result)]
     lib.mlc_debug_set_timing.argtypes = [vp, i]
+    lib.mlc_debug_set_fault.argtypes = [vp, i]
     lib.mlc_debug_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i]
     lib.mlc_status_string.argtypes = [i]
     lib.mlc_status_string.restype = ctypes.c_char_p
@@ -241,6 +243,11 @@ class Plan:
                                              ctypes.c_void_p(_stream_handle(stream))), "mlc_solve_host")
         return phi_host
 
+    def set_fault(self, kind: int):
+        """Test hook mlc_debug_set_fault: 1 = the inverse-x bulk copies are not
+        issued and their bounded waits run out (status TIMEOUT); 0 = normal."""
+        _check(load_library().mlc_debug_set_fault(self._h, int(kind)), "set_fault")
+
     def set_timing(self, enable: bool = True):
         _check(load_library().mlc_debug_set_timing(self._h, int(enable)), "set_timing")
 
@@ -255,9 +262,21 @@ class Plan:
         lib = load_library()
         nb = ctypes.c_size_t()
         _check(lib.mlc_debug_stage_bytes(self._h, stage, ctypes.byref(nb)), "stage bytes")
+        if stage in (STAGE_FACE_INDEX, STAGE_COARSE_INDEX):
+            out = np.empty(nb.value // 4, dtype=np.int32)
+            _check(lib.mlc_debug_export(self._h, stage, ctypes.c_void_p(out.ctypes.data), nb.value), "export")
+            i = self.info
+            if stage == STAGE_FACE_INDEX:
+                nodes = 3 * (i.N // i.n + 1) * (i.N + 1) ** 2
+            else:
+                nodes = (i.fh_hi - i.fh_lo + 1) ** 3
+            return out[:nodes + 1].astype(np.int64), out[nodes + 1:].astype(np.int64)
         out = np.empty(nb.value // 8, dtype=np.float64)
         _check(lib.mlc_debug_export(self._h, stage, ctypes.c_void_p(out.ctypes.data), nb.value), "export")
         i = self.info
+        if stage == STAGE_COARSE_SAMPLES:
+            nc = (i.n + 2 * i.s) // 4 + 1
+            return out.reshape(-1, nc, nc, nc)
         if stage == STAGE_MOMENTS:
             return out.reshape(-1, i.npoly)
         if stage == STAGE_FH:

@@ -43,14 +43,36 @@ def test_split_schedule_counts_match_enumeration():
     assert b.fft64_schedule_inst("split", True, 17) == _radix2_fp32_count(17)
 
 
-def test_fp64_schedule_counts():
+def test_radix8_schedule_counts():
     # radix 8 x 8: 16 butterflies of 52 adds + 4 multiplies, 56 twiddle
     # products (4 multiplies + 2 adds); double-float add = 8, multiply = 4
     b = _bench()
     adds, muls = 16 * 52 + 56 * 2, 16 * 4 + 56 * 4
-    assert b.fft64_schedule_inst("fp64", False) == adds * 8 + muls * 4
+    assert b.fft64_schedule_inst("df", False) == adds * 8 + muls * 4
     adds_s, muls_s = 8 * 26 + 8 * 52 + 56 * 2, 8 * 2 + 8 * 4 + 56 * 4
-    assert b.fft64_schedule_inst("fp64", True) == adds_s * 8 + muls_s * 4
+    assert b.fft64_schedule_inst("df", True) == adds_s * 8 + muls_s * 4
+    # FP64: one instruction per add and multiply, a twiddle product is
+    # 2 multiplies + 2 FMAs
+    assert b.fft64_schedule_inst("fp64", False) == 16 * 52 + 16 * 4 + 56 * 4
+    assert b.fft64_schedule_inst("fp64", True) == 8 * 26 + 8 * 52 + 8 * 2 + 8 * 4 + 56 * 4
+
+
+def test_dirichlet_counts_closed_form():
+    """Boundary terms of the Dirichlet right-hand side for n = 16: every
+    neighbour of the 15^3 interior nodes lies in [0, 16]^3, so the terms are
+    15^3 x (neighbours) minus the ordered interior-interior pairs, which number
+    prod_d (15 - |s_d|) per stencil offset s."""
+    b = _bench()
+    inter = {1: 3 * 2 * 14 * 15 * 15, 2: 3 * 4 * 14 * 14 * 15, 3: 8 * 14 ** 3}
+    t6 = 15 ** 3 * 26 - (inter[1] + inter[2] + inter[3])   # 27-point: all 26 offsets
+    t4 = 15 ** 3 * 18 - (inter[1] + inter[2])              # 19-point: no corner offsets
+    assert (t6, t4) == (11618, 6570)
+    for Q, t in ((6, t6), (4, t4)):
+        flops, inst = b.dirichlet_counts(16, Q)
+        dst = 6 * 15 * 15 * 97
+        assert flops == 2 * t + dst + 15 ** 3 + 2 * 16 ** 3
+        assert inst == t + dst + 15 ** 3 + 16 ** 3
+
 
 
 def test_slab_rows_and_fp32_peak():
@@ -62,3 +84,4 @@ def test_slab_rows_and_fp32_peak():
     assert b.slab_rows(W, 8) == 37   # Q = 4, g_alpha = 8
     assert b.slab_rows(W, 4) == 31   # Q = 6, g_alpha = 4
     assert abs(b.FP32_LANE_INST_PER_S - 152 * 128 * 2.07e9) < 1.0
+    assert abs(b.FP64_INST_PER_S - 0.625e12) < 1.0

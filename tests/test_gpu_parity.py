@@ -299,3 +299,78 @@ def test_split_tier_256_below_discretisation_error(torch_cuda):
         e_split = relmax(out[tier], b)
         assert e_split <= SPLIT_TOL, (tier, e_split)
         assert e_split < e_disc, (tier, e_split, e_disc)
+
+
+# ------------------------------------------------------------ indexing, failures
+def _plane_order_nodes(N, n):
+    """Face-plane nodes in the library's [axis][plane][u][v] order."""
+    npl = N // n + 1
+    u, v = np.meshgrid(np.arange(N + 1), np.arange(N + 1), indexing="ij")
+    u, v = u.reshape(-1), v.reshape(-1)
+    out = []
+    for axis in range(3):
+        for j in range(npl):
+            c = np.full_like(u, j * n)
+            out.append(np.stack([c, u, v], 1) if axis == 0 else
+                       (np.stack([u, c, v], 1) if axis == 1 else np.stack([u, v, c], 1)))
+    return np.concatenate(out)
+
+
+@pytest.mark.parametrize("kw", [dict(N=32, n=8, s=8, Q=4), dict(N=48, n=16, s=16, Q=4),
+                                dict(N=128, n=16, s=16, Q=4), dict(N=64, n=16, s=16, Q=6)])
+def test_index_arrays_match_oracle(torch_cuda, kw):
+    """The patch indexing the boundary and coarse-charge kernels run (per
+    face-plane node and per coarse node: the patches whose Omega_beta or
+    C(Omega_beta) holds it, ascending, alpha / ring class) equals the oracle's
+    membership tests bit for bit."""
+    from paper_1702_08111_gb300 import mlc
+    plan = mlc.Plan(kw["N"], kw["n"], kw["s"], 4, kw["Q"])
+    prm = O.Params(N=kw["N"], n=kw["n"], s=kw["s"], Q=kw["Q"])
+    off, ent = plan.export(mlc.STAGE_FACE_INDEX)
+    o_off, o_ent = O.face_patch_index(prm, _plane_order_nodes(kw["N"], kw["n"]))
+    assert np.array_equal(off, o_off)
+    assert np.array_equal(ent, o_ent)
+    off, ent = plan.export(mlc.STAGE_COARSE_INDEX)
+    o_off, o_ent = O.coarse_patch_index(prm)
+    assert np.array_equal(off, o_off)
+    assert np.array_equal(ent, o_ent)
+
+
+@pytest.mark.parametrize("tier", EXACT_TIERS)
+def test_coarse_samples_match_oracle(torch_cuda, G4, tier):
+    """Local fields phi^{i,h} at the coarse points of every field box (the
+    samples Delta^H and the interpolation read) against the oracle's."""
+    from paper_1702_08111_gb300 import mlc
+    w = I.workload("single_bump_32")
+    f = w.charge()
+    plan = mlc.Plan(32, 8, 8, 4, 4, tier=tier)
+    plan.solve(torch_cuda.from_numpy(f).cuda())
+    got = plan.export(mlc.STAGE_COARSE_SAMPLES)
+    _, st = _oracle("single_bump_32", O.Params(N=32, n=8, s=8, Q=4), f, G4)
+    ref = st["coarse_samples"].reshape(got.shape)
+    assert relmax(got, ref) <= TOL
+
+
+def test_bounded_wait_runs_out_and_reports_timeout(torch_cuda):
+    """With the test hook on, the inverse-x kernels' bulk copies are not
+    issued: every bounded wait runs out (64 tests), the kernels record it and
+    return, and the plan reports TIMEOUT; the next normal solve is correct."""
+    from paper_1702_08111_gb300 import mlc
+    torch = torch_cuda
+    f = torch.from_numpy(I.workload("single_bump_32").charge()).cuda()
+    for N, n, s in ((32, 8, 8), (48, 16, 16)):  # M = 32 and M = 64 kernels
+        fN = torch.from_numpy(I.sample_bumps(N, I.draw_bumps(2, 5))).cuda() if N != 32 else f
+        plan = mlc.Plan(N, n, s, 4, 4)
+        ref = plan.solve(fN).clone()
+        plan.status()
+        plan.set_fault(1)
+        plan.solve(fN)
+        with pytest.raises(mlc.MLCError) as e:
+            plan.status()
+        assert e.value.status == 6
+        plan.set_fault(0)
+        out = plan.solve(fN)
+        plan.status()
+        assert torch.equal(out, ref)
+    with pytest.raises(mlc.MLCError):
+        plan.set_fault(7)

@@ -357,3 +357,41 @@ def test_moments_stage_is_boole_of_charge(G4, bump32):
     w = O.boole_weights_1d(prm.n, prm.h)
     W = (w[:, None, None] * w[None, :, None] * w[None, None, :]).reshape(-1)
     assert abs(st["moments"][i][0] - (W @ fp) / (2 * prm.R) ** 1.5) < 1e-15
+
+
+# ---------------------------------------------------------------- patch indexing
+def test_face_patch_index_worked_example():
+    """N = 32, n = 8, s = 8, Q = 4: g_alpha = 0, g_beta = 8.  Node (8, 3, 4):
+    per axis Omega_alpha(i) = [8i, 8i+8] holds 8 for i in {0, 1}, 3 and 4 for
+    i = 0; Omega_beta(i) = [8i-8, 8i+16] holds 8 for i in {0, 1, 2}, 3 and 4
+    for i in {0, 1}.  So 12 patches, of which (0,0,0) and (1,0,0) in alpha."""
+    prm = O.Params(N=32, n=8, s=8, Q=4)
+    off, ent = O.face_patch_index(prm, np.array([[8, 3, 4]]))
+    assert list(off) == [0, 12]
+    # linear index (i0 * 4 + i1) * 4 + i2; entry 2 i + (0 alpha, 1 ring)
+    assert list(ent) == [0, 3, 9, 11, 32, 35, 41, 43, 65, 67, 73, 75]
+
+
+def test_face_patch_index_counts_closed_form():
+    """N = 128, n = s = 16, Q = 4: g_alpha = 8, g_beta = 16.  Node (64, 40, 72):
+    beta holds it for i0 in 2..5, i1 in 1..3, i2 in 3..5 (36 patches), alpha
+    for i0 in 3..4, i1 in 1..3, i2 in 3..5 (18 patches)."""
+    prm = O.Params(N=128, n=16, s=16, Q=4)
+    off, ent = O.face_patch_index(prm, np.array([[64, 40, 72], [0, 0, 0]]))
+    e = ent[off[0]:off[1]]
+    assert len(e) == 36 and int((e % 2 == 0).sum()) == 18
+    assert np.all(np.diff(e // 2) > 0)  # ascending patch index
+    # corner node 0: beta holds it for i in {0, 1} on every axis (16 i - 16 <= 0),
+    # alpha only for i = 0 (16 i - 8 <= 0); linear index (i0 * 8 + i1) * 8 + i2
+    assert list(ent[off[1]:off[2]]) == [0, 3, 17, 19, 129, 131, 145, 147]
+
+
+def test_coarse_patch_index_worked_example():
+    """N = 32, n = 8, Q = 4: C(Omega_alpha) = [0, 2], C(Omega_beta) = [-2, 4]
+    relative to n i / 4 = 2 i; F^H on [-2, 10].  Coarse node (3, 0, -2): beta
+    for i0 in {0, 1, 2}, i1 in {0, 1}, i2 = 0; alpha needs 2 i2 <= -2: none."""
+    prm = O.Params(N=32, n=8, s=8, Q=4)
+    off, ent = O.coarse_patch_index(prm)
+    node = ((3 + 2) * 13 + (0 + 2)) * 13 + (-2 + 2)
+    assert list(ent[off[node]:off[node + 1]]) == [1, 9, 33, 41, 65, 73]
+    assert len(off) == 13 ** 3 + 1
