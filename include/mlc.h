@@ -109,6 +109,20 @@ mlc_status mlc_plan_create(int N, int patch, int support, int coarsening, int P,
 mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out);
 mlc_status mlc_plan_destroy(mlc_plan_t plan);
 
+/*
+ * Replace the plan's discrete Green's function G^{h=1} (Sec. 2 eq. dgf, App.
+ * A.1) by a caller-given table and rebuild every table derived from it (the
+ * Hockney kernel spectra of the local and coarse convolutions, App. A.2; the
+ * Legendre basis fields Delta^H(G^h * Q^p) of Sec. 4 Step 1), so that another
+ * implementation's table can be used as data for isolated parity checks.
+ * table: host array of (L+1)^3 FP64 values G^{h=1}[i][j][k] on the octant
+ * [0, L]^3, k fastest (the layout of MLC_STAGE_DGF); copied, the caller keeps
+ * it.  L must reach every lag the plan needs (the L that mlc_plan_info reports
+ * for the library's own table is enough), else INVALID_ARG and the plan is
+ * unchanged.  Synchronises the device; the handle stays valid.
+ */
+mlc_status mlc_plan_set_dgf(mlc_plan_t plan, const double *table, int L);
+
 /* Synchronise the device and report kernel-side failures of this plan's
  * solves since the last check: TIMEOUT if a bounded wait inside a kernel (the
  * staging of a block by an asynchronous bulk copy) gave up, so the result of

@@ -13,7 +13,9 @@
 //               I^H(phi^H) + sum_alpha (phi^i - I^H phi^i) + sum_ring c_p (B_p - I^H B_p)
 //   dirichlet   patch Dirichlet solves by DST-I (eq. last_step_fulldiscr) and
 //               the Mehrstellen correction (eq. mcapplicationfulldiscr)
+#include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <type_traits>
 
 #include "mlc_internal.h"
@@ -354,134 +356,6 @@ __global__ void __launch_bounds__(256) k_fwd_x(FwdXArgs a) {
             const int l = e / MH, kx = e % MH;
             out[((long)slab * a.nin + line0 + l) * MH + kx] = buf[l * LS + brev_bits(kx, LOG2M)];
         }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Transform along a strided axis; lines are contiguous columns.
-//   MODE 0: forward; input rows t < nin at positions t; all M rows out.
-//   MODE 1: inverse; all M rows in; rows t < nout out from positions
-//           (out_off + t) mod M.
-//   MODE 2: forward, multiply by the real-even kernel spectrum, inverse.
-// slab = blockIdx.x = p * S2 + q; blockIdx.y = column chunk.
-// ---------------------------------------------------------------------------
-struct ColArgs {
-    const void *in;
-    void *out;
-    int S2;
-    long in_sp, in_sq, in_row, out_sp, out_sq, out_row;
-    int ncols, cols_cta, nin, nout, out_off;
-    const void *khat;  // MODE 2: real R octant (M/2+1)^3, index (kx, ky = q, kz = row)
-    const void *tw;
-};
-
-template <int LOG2M, int MODE, typename R>
-__global__ void __launch_bounds__(256) k_col(ColArgs a) {
-    using C = typename Cx<R>::T;
-    constexpr int M = 1 << LOG2M, MH = M / 2 + 1;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *s_tw = (C *)smem_raw;
-    C *buf = s_tw + M / 2;
-    const int slab = blockIdx.x;
-    const int p = slab / a.S2, q = slab % a.S2;
-    const int c0 = blockIdx.y * a.cols_cta;
-    const int nc = min(a.cols_cta, a.ncols - c0);
-    const int CC = a.cols_cta;  // row stride in shared memory
-    load_twiddles<LOG2M>(s_tw, (const C *)a.tw);
-    const C *in = (const C *)a.in + p * a.in_sp + q * a.in_sq + c0;
-    if (MODE != 1)
-        for (int e = threadIdx.x; e < M * CC; e += blockDim.x) buf[e] = Cx<R>::mk(0, 0);
-    __syncthreads();
-    const int nrow_in = (MODE == 1) ? M : a.nin;
-    for (int e = threadIdx.x; e < nrow_in * nc; e += blockDim.x) {
-        const int r = e / nc, c = e % nc;
-        buf[r * CC + c] = in[r * a.in_row + c];
-    }
-    __syncthreads();
-    C *out = (C *)a.out + p * a.out_sp + q * a.out_sq + c0;
-    if (MODE == 0) {
-        fft_dif<LOG2M>(buf, nc, 1, CC, s_tw, false);
-        for (int e = threadIdx.x; e < M * nc; e += blockDim.x) {
-            const int r = e / nc, c = e % nc;
-            out[r * a.out_row + c] = buf[brev_bits(r, LOG2M) * CC + c];
-        }
-        return;
-    }
-    if (MODE == 1) {
-        fft_dif<LOG2M>(buf, nc, 1, CC, s_tw, true);
-    } else {
-        fft_dif<LOG2M>(buf, nc, 1, CC, s_tw, false);
-        const R *khat = (const R *)a.khat;
-        const int ky = q < M - q ? q : M - q;
-        for (int e = threadIdx.x; e < M * nc; e += blockDim.x) {
-            const int r = e / nc, c = e % nc;
-            const int kz0 = brev_bits(r, LOG2M);
-            const int kz = kz0 < M - kz0 ? kz0 : M - kz0;
-            const int kx0 = c0 + c;
-            const int kx = kx0 < M - kx0 ? kx0 : M - kx0;
-            const R k = khat[((long)kx * MH + ky) * MH + kz];
-            C v = buf[r * CC + c];
-            v.x *= k;
-            v.y *= k;
-            buf[r * CC + c] = v;
-        }
-        __syncthreads();
-        fft_dit<LOG2M>(buf, nc, 1, CC, s_tw, true);
-    }
-    for (int e = threadIdx.x; e < a.nout * nc; e += blockDim.x) {
-        const int t = e / nc, c = e % nc;
-        int pos = (a.out_off + t) % M;
-        if (pos < 0) pos += M;
-        const int sr = (MODE == 1) ? brev_bits(pos, LOG2M) : pos;
-        out[t * a.out_row + c] = buf[sr * CC + c];
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Inverse real transform along axis 2: lines are rows; the half spectrum
-// kx in [0, M/2] is extended by Hermitian symmetry; outputs t < nout from
-// positions (out_off + t) mod M.  out[(slab * nrow + row) * nout + t] (type TO).
-// ---------------------------------------------------------------------------
-struct InvXArgs {
-    const void *in;
-    void *out;
-    int nrow, nout, out_off, lines_cta;
-    const void *tw;
-};
-
-template <int LOG2M, typename R, typename TO>
-__global__ void __launch_bounds__(256) k_inv_x(InvXArgs a) {
-    using C = typename Cx<R>::T;
-    constexpr int M = 1 << LOG2M, MH = M / 2 + 1, LS = M + 1;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *s_tw = (C *)smem_raw;
-    C *buf = s_tw + M / 2;
-    const int slab = blockIdx.x;
-    const int r0 = blockIdx.y * a.lines_cta;
-    const int nl = min(a.lines_cta, a.nrow - r0);
-    load_twiddles<LOG2M>(s_tw, (const C *)a.tw);
-    {
-        const C *in = (const C *)a.in + ((long)slab * a.nrow + r0) * MH;
-        for (int e = threadIdx.x; e < nl * M; e += blockDim.x) {
-            const int l = e / M, k = e % M;
-            C v;
-            if (k < MH) {
-                v = in[l * MH + k];
-            } else {
-                v = in[l * MH + (M - k)];
-                v.y = -v.y;
-            }
-            buf[l * LS + k] = v;
-        }
-    }
-    __syncthreads();
-    fft_dif<LOG2M>(buf, nl, LS, 1, s_tw, true);
-    TO *out = (TO *)a.out + ((long)slab * a.nrow + r0) * a.nout;
-    for (int e = threadIdx.x; e < nl * a.nout; e += blockDim.x) {
-        const int l = e / a.nout, t = e % a.nout;
-        int pos = (a.out_off + t) % M;
-        if (pos < 0) pos += M;
-        out[l * a.nout + t] = (TO)buf[l * LS + brev_bits(pos, LOG2M)].x;
     }
 }
 
@@ -1764,10 +1638,10 @@ __device__ __forceinline__ void face_node_patches(const int g[3], int np, int ga
 }
 
 // Face-plane node idx in [axis][plane j][u][v] order -> g (plane x_axis = j n).
-__device__ __forceinline__ void face_plane_node(long idx, int N, int np, int n, int g[3], int &axis) {
+__device__ __forceinline__ void face_plane_node(long idx, int N, int np, int n, int g[3], int &axis, int &j) {
     const long pn = (long)(N + 1) * (N + 1);
     axis = (int)(idx / ((np + 1) * pn));
-    const int j = (int)((idx / pn) % (np + 1));
+    j = (int)((idx / pn) % (np + 1));
     const int u = (int)((idx % pn) / (N + 1)), v = (int)(idx % (N + 1));
     const int jn = j * n;
     g[0] = axis == 0 ? jn : u;
@@ -1775,8 +1649,57 @@ __device__ __forceinline__ void face_plane_node(long idx, int N, int np, int n, 
     g[2] = axis == 2 ? jn : v;
 }
 
+// First half of I^H(phi^H) on every face plane (R4: tensor Lagrange in the
+// plane, applied separably): for plane (axis a, j) with in-plane axes u < v,
+// every coarse row c_u of phi^H and every fine v in [0, N], the sum along v,
+//   Tpl[a][j][c_u - olo][v] = sum_e w_{v mod 4}(e) phi^H(c_a = j n/4, c_u, v/4 - b + e)
+// (or the coarse value itself when v mod 4 = 0).  The boundary kernel then
+// sums K of these along u: the same operations in the same order as the
+// nested sums at each node, done once per (plane, coarse row, v).
+struct LagW {
+    dfl lw[4][8];      // Lagrange weights for g mod 4 = r (row r), double-float
+    double lwd[4][8];  // the same in FP64
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_plane_interp(const void *phiH_, void *out_, int N, int n, int np, int b,
+                                                      int olo, int no, LagW w) {
+    const long tot = 3L * (np + 1) * no * (N + 1);
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= tot) return;
+    const T *phiH = (const T *)phiH_;
+    const int v = (int)(idx % (N + 1));
+    const int cu = (int)((idx / (N + 1)) % no);
+    const int pj = (int)(idx / ((long)(N + 1) * no));  // axis * (np + 1) + j
+    const int axis = pj / (np + 1), j = pj % (np + 1);
+    const int ca = j * n / 4 - olo, cuo = cu;  // offsets into phi^H
+    // phi^H at coarse (plane, c_u, c_v) for the plane's axis order
+    auto at = [&](int cv) -> T {
+        const int c = cv - olo;
+        long i;
+        if (axis == 0) i = ((long)ca * no + cuo) * no + c;
+        else if (axis == 1) i = ((long)cuo * no + ca) * no + c;
+        else i = ((long)cuo * no + c) * no + ca;
+        return phiH[i];
+    };
+    const int rv = v & 3;
+    T s;
+    if (rv == 0) {
+        s = at(v >> 2);
+    } else {
+        const int kb = (v >> 2) - b, K = 2 * b + 2;
+        s = FT<T>::zero();
+        for (int e = 0; e < K; ++e) {
+            const T x = axis == 2 ? FT<T>::rn(at(kb + e)) : at(kb + e);
+            s = FT<T>::fma(pick<T>(w.lw[rv][e], w.lwd[rv][e]), x, s);
+        }
+    }
+    ((T *)out_)[idx] = s;
+}
+
 struct BndArgs {
     const void *phiH, *resid;  // fine precision T
+    const void *tpl;           // k_plane_interp output, fine precision T
     const void *mom, *D;       // ring tables in the ring precision RT
     void *phiB;                // fine precision T
     int N, n, np, ga, gb, b, npoly, olo, no, wa, wbx, npa, pl0;
@@ -1790,7 +1713,7 @@ struct BndArgs {
 // Legendre ring sums (the local-convolution precision: FP32, double-float or
 // FP64); T: the interpolation and the accumulation (FP64 or double-float).
 template <typename RT, int NN, typename T>
-__global__ void __launch_bounds__(128, sizeof(RT) == 4 ? 8 : 6) k_boundary(BndArgs a) {
+__global__ void __launch_bounds__(128, 6) k_boundary(BndArgs a) {
     constexpr int n = NN;  // patch size as a constant: the index divisions become multiplies
     const long pn = (long)(a.N + 1) * (a.N + 1);
     const long tot = 3L * (a.np + 1) * pn;
@@ -1798,38 +1721,24 @@ __global__ void __launch_bounds__(128, sizeof(RT) == 4 ? 8 : 6) k_boundary(BndAr
     if (idx >= tot) return;
     const T *phiH = (const T *)a.phiH;
     const T *resid = (const T *)a.resid;
-    int g[3], axis;
-    face_plane_node(idx, a.N, a.np, n, g, axis);
-    // I^H(phi^H)(g): tensor Lagrange over the in-plane axes (R4), applied as
-    // nested 1D sums (K^2 + K + 1 FMAs for two nontrivial axes)
+    int g[3], axis, jp;
+    face_plane_node(idx, a.N, a.np, n, g, axis, jp);
+    // I^H(phi^H)(g): tensor Lagrange over the in-plane axes (R4), the sums
+    // along v precomputed per (plane, coarse row) by k_plane_interp; here the
+    // K-term sum along u (in-plane axes u < v)
+    (void)phiH;
     const int K = 2 * a.b + 2;
-    int kb[3], cnt[3], rr[3];
-    for (int d = 0; d < 3; ++d) {
-        rr[d] = g[d] & 3;
-        if (rr[d] == 0) {
-            kb[d] = g[d] >> 2;
-            cnt[d] = 1;
-        } else {
-            kb[d] = (g[d] >> 2) - a.b;
-            cnt[d] = K;
-        }
-    }
-    T acc = FT<T>::zero();
-    for (int e0 = 0; e0 < cnt[0]; ++e0) {
-        T s1 = FT<T>::zero();
-        for (int e1 = 0; e1 < cnt[1]; ++e1) {
-            const T *row = phiH + ((long)(kb[0] + e0 - a.olo) * a.no + (kb[1] + e1 - a.olo)) * a.no +
-                           (kb[2] - a.olo);
-            T s2;
-            if (rr[2]) {
-                s2 = FT<T>::zero();
-                for (int e2 = 0; e2 < K; ++e2) s2 = FT<T>::fma(pick<T>(a.lw[rr[2]][e2], a.lwd[rr[2]][e2]), row[e2], s2);
-            } else {
-                s2 = row[0];
-            }
-            s1 = rr[1] ? FT<T>::fma(pick<T>(a.lw[rr[1]][e1], a.lwd[rr[1]][e1]), FT<T>::rn(s2), s1) : s2;
-        }
-        acc = rr[0] ? FT<T>::fma(pick<T>(a.lw[rr[0]][e0], a.lwd[rr[0]][e0]), FT<T>::rn(s1), acc) : s1;
+    const int gu = axis == 0 ? g[1] : g[0], gv = axis == 2 ? g[1] : g[2];
+    const T *tpl = (const T *)a.tpl + ((long)(axis * (a.np + 1) + jp) * a.no) * (a.N + 1) + gv;
+    const int ru = gu & 3;
+    T acc;
+    if (ru == 0) {
+        acc = tpl[(long)((gu >> 2) - a.olo) * (a.N + 1)];
+    } else {
+        acc = FT<T>::zero();
+        const int kb = (gu >> 2) - a.b - a.olo;
+        for (int e = 0; e < K; ++e)
+            acc = FT<T>::fma(pick<T>(a.lw[ru][e], a.lwd[ru][e]), FT<T>::rn(tpl[(long)(kb + e) * (a.N + 1)]), acc);
     }
     // local corrections of the patches whose Omega_beta holds g (ascending index);
     // the Legendre ring terms accumulate in the ring precision RT
@@ -1865,8 +1774,8 @@ __global__ void __launch_bounds__(128) k_index_face(int N, int np, int ga, int g
                                                     const long *off, int *ent) {
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= tot) return;
-    int g[3], axis;
-    face_plane_node(idx, N, np, NN, g, axis);
+    int g[3], axis, jp;
+    face_plane_node(idx, N, np, NN, g, axis, jp);
     int c = 0;
     const long o = COUNT ? 0 : off[idx];
     face_node_patches<NN>(g, np, ga, gb, [&](long p, int, int, int, bool inA) {
@@ -2001,7 +1910,7 @@ __device__ __forceinline__ void dst15_fast(T (&x)[15], const T (&sv)[9]) {
 // loads and the final FP64 store, FP64 (the FP64 pipe) or double-float (the
 // FP32 pipe; GB300 issues FP64 on ~1/67 of the FP32 lanes).  TF: the charge.
 template <typename TF, int NN, typename T>
-__global__ void __launch_bounds__(256, 4) k_dirichlet(DirArgs a) {
+__global__ void __launch_bounds__(256, std::is_same<T, double>::value ? 3 : 4) k_dirichlet(DirArgs a) {
     extern __shared__ double sm[];
     constexpr int n = NN, nb = n + 1, m = n - 1, h = n / 2;
     T *U = (T *)sm;                    // boundary values on the 6 faces, nb^2 each (face 2 axis + side)
@@ -2049,33 +1958,52 @@ __global__ void __launch_bounds__(256, 4) k_dirichlet(DirArgs a) {
         cwz[k] = a.b[k] == 0.0;
     }
     const T c2h2 = s_w[4];
-    // right-hand side: f - Delta^h(boundary data); only the layer next to the
-    // boundary sees boundary values
+    // right-hand side: f - Delta^h(boundary data).  Only the layers next to the
+    // boundary see boundary values; they are subtracted in six face passes,
+    // one per (axis a, side): every interior node c of the layer c_a = 1 (or
+    // n - 1) and every stencil neighbour d with d_a = 0 (or n), except those
+    // with a boundary coordinate on an axis before a (counted in that axis's
+    // pass) -- each (node, boundary neighbour) pair once, with the threads of
+    // a warp on neighbouring nodes of one layer doing the same products.
     for (int e = threadIdx.x; e < m * m * m; e += blockDim.x) {
         const int c2 = e % m + 1, c1 = (e / m) % m + 1, c0 = e / (m * m) + 1;
         const int z = o0 + c0, y = o1 + c1, x = o2 + c2;
-        T v = (z < N && y < N && x < N) ? FT<T>::of(f[((long)z * N + y) * N + x]) : FT<T>::zero();
-        const bool near = c0 == 1 || c0 == m || c1 == 1 || c1 == m || c2 == 1 || c2 == m;
-        if (near) {
-#pragma unroll
-            for (int s0 = -1; s0 <= 1; ++s0)
-#pragma unroll
-                for (int s1 = -1; s1 <= 1; ++s1)
-#pragma unroll
-                    for (int s2 = -1; s2 <= 1; ++s2) {
-                        const int nz = (s0 != 0) + (s1 != 0) + (s2 != 0);
-                        const int d0 = c0 + s0, d1 = c1 + s1, d2 = c2 + s2;
-                        const bool bd = d0 == 0 || d0 == n || d1 == 0 || d1 == n || d2 == 0 || d2 == n;
-                        if (cwz[nz] || !bd) continue;  // interior neighbours carry no boundary data
-                        const T u = Uat(d0, d1, d2);
-                        // double-float: skip zero data (an FP32 test saves a product);
-                        // FP64: the product costs less than a test on the FP64 pipe
-                        if (std::is_same<T, double>::value || !FT<T>::is0(u)) v = v - cw[nz] * u;
-                    }
-        }
-        X[e] = v;
+        X[e] = (z < N && y < N && x < N) ? FT<T>::of(f[((long)z * N + y) * N + x]) : FT<T>::zero();
     }
     __syncthreads();
+    for (int fc = 0; fc < 6; ++fc) {
+        const int ax = fc >> 1, sa = (fc & 1) ? 1 : -1;  // neighbour offset along ax
+        const int ca = (fc & 1) ? m : 1, da = (fc & 1) ? n : 0;
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int cb = e / m + 1, cc = e % m + 1;  // the other two coordinates, increasing axis order
+            T acc = FT<T>::zero();
+#pragma unroll
+            for (int sb = -1; sb <= 1; ++sb)
+#pragma unroll
+                for (int sc = -1; sc <= 1; ++sc) {
+                    const int nz = 1 + (sb != 0) + (sc != 0);
+                    if (cwz[nz]) continue;
+                    const int db = cb + sb, dc = cc + sc;
+                    const bool bb = db == 0 || db == n, bc = dc == 0 || dc == n;
+                    // other axes: b is the lower of the two, c the higher
+                    const int axb = ax == 0 ? 1 : 0, axc = ax == 2 ? 1 : 2;
+                    if ((axb < ax && bb) || (axc < ax && bc)) continue;  // an earlier pass has it
+                    int d0, d1, d2;
+                    if (ax == 0) { d0 = da; d1 = db; d2 = dc; }
+                    else if (ax == 1) { d0 = db; d1 = da; d2 = dc; }
+                    else { d0 = db; d1 = dc; d2 = da; }
+                    acc = FT<T>::fma(cw[nz], Uat(d0, d1, d2), acc);
+                }
+            int c0, c1, c2;
+            if (ax == 0) { c0 = ca; c1 = cb; c2 = cc; }
+            else if (ax == 1) { c0 = cb; c1 = ca; c2 = cc; }
+            else { c0 = cb; c1 = cc; c2 = ca; }
+            T &xv = X[((c0 - 1) * m + (c1 - 1)) * m + (c2 - 1)];
+            xv = xv - acc;
+        }
+        (void)sa;
+        __syncthreads();  // the next pass may update the same edge nodes
+    }
     // DST-I along axes 2, 1, 0; scale by the inverse eigenvalues; DST-I along 2, 1, 0
     if constexpr (NN == 16) {
         // n = 16: one thread per line with the split-radix DST (dst15_fast)
@@ -2165,20 +2093,363 @@ __global__ void __launch_bounds__(256, 4) k_dirichlet(DirArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Coarse Hockney convolution (Step 2, App. A.2) with mixed-radix Stockham
+// FFTs: the period M is any even product of the radices 2, 3, 4, 5, so it can
+// be the smallest such length that the Hockney condition allows instead of
+// the next power of two (144 rather than 256 at N = 256, Q = 6).  Stockham's
+// autosort form keeps natural order in and out, ping-ponging between two
+// shared-memory buffers, one stage per radix.
+// ---------------------------------------------------------------------------
+struct RadixPlan {
+    int n;       // stages
+    int r[16];   // radix of each stage (product = M)
+};
+
+template <typename C, typename R>
+__device__ __forceinline__ C cscale(C a, R s) {
+    C r;
+    r.x = a.x * s;
+    r.y = a.y * s;
+    return r;
+}
+
+// In-register DFT of length rad in {2, 3, 4, 5} (natural order), forward
+// (exp(-2 pi i n k / rad)) or inverse (conjugate kernel).
+template <typename C, typename R>
+__device__ __forceinline__ void dft_small(C (&v)[5], int rad, bool inv) {
+    if (rad == 2) {
+        const C a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if (rad == 4) {
+        const C a = cadd(v[0], v[2]), b = csub(v[0], v[2]), c = cadd(v[1], v[3]);
+        const C d = mul_mi(csub(v[1], v[3]), inv);  // -i (x1 - x3), forward
+        v[0] = cadd(a, c);
+        v[2] = csub(a, c);
+        v[1] = cadd(b, d);
+        v[3] = csub(b, d);
+    } else if (rad == 3) {
+        // X1,2 = x0 - (x1 + x2)/2 -+ i sin(2 pi/3) (x1 - x2)
+        const R s3 = R(0.86602540378443864676), half = R(0.5);
+        const C t1 = cadd(v[1], v[2]);
+        const C t2 = csub(v[0], cscale(t1, half));
+        const C m = mul_mi(cscale(csub(v[1], v[2]), s3), inv);
+        v[0] = cadd(v[0], t1);
+        v[1] = cadd(t2, m);
+        v[2] = csub(t2, m);
+    } else {  // 5: c_k = cos(2 pi k / 5), s_k = sin(2 pi k / 5)
+        const R c1 = R(0.30901699437494742410), c2 = R(-0.80901699437494742410);
+        const R s1 = R(0.95105651629515357212), s2 = R(0.58778525229247312917);
+        const C a1 = cadd(v[1], v[4]), a2 = cadd(v[2], v[3]);
+        const C b1 = csub(v[1], v[4]), b2 = csub(v[2], v[3]);
+        const C t1 = cadd(v[0], cadd(cscale(a1, c1), cscale(a2, c2)));
+        const C t2 = cadd(v[0], cadd(cscale(a1, c2), cscale(a2, c1)));
+        const C m1 = mul_mi(cadd(cscale(b1, s1), cscale(b2, s2)), inv);
+        const C m2 = mul_mi(csub(cscale(b1, s2), cscale(b2, s1)), inv);
+        v[0] = cadd(v[0], cadd(a1, a2));
+        v[1] = cadd(t1, m1);
+        v[4] = csub(t1, m1);
+        v[2] = cadd(t2, m2);
+        v[3] = csub(t2, m2);
+    }
+}
+
+// Stockham FFT of nlines lines of length M in shared memory: line l at
+// src + l lstride, element i at + i estride; dst is scratch of the same
+// layout.  Stage with radix R and span Ns (product of the earlier radices):
+// for j < M/R, k = j mod Ns, x_r = src[j + r M/R] w^(r k M/(Ns R)),
+// y = DFT_R(x), dst[(j/Ns) Ns R + k + r Ns] = y_r.  tw: w^t = exp(-2 pi i t/M),
+// t < M (conjugated for the inverse).  Ends with __syncthreads; returns the
+// buffer that holds the result.
+template <typename C, typename R>
+__device__ C *fft_stockham(C *src, C *dst, int nlines, int lstride, int estride, int M, const RadixPlan &rp,
+                           const C *tw, bool inv) {
+    int Ns = 1;
+    for (int st = 0; st < rp.n; ++st) {
+        const int rad = rp.r[st], MR = M / rad, tstep = M / (Ns * rad);
+        for (int e = threadIdx.x; e < nlines * MR; e += blockDim.x) {
+            const int line = e % nlines, j = e / nlines;
+            const C *sl = src + line * lstride;
+            C *dl = dst + line * lstride;
+            const int k = j % Ns;
+            C v[5];
+#pragma unroll
+            for (int r = 0; r < 5; ++r) {
+                if (r < rad) {
+                    C x = renorm(sl[(j + r * MR) * estride]);
+                    if (r && k) {
+                        C w = tw[(r * k * tstep) % M];
+                        if (inv) w.y = -w.y;
+                        x = cmul(x, w);
+                    }
+                    v[r] = x;
+                }
+            }
+            dft_small<C, R>(v, rad, inv);
+            const int base = (j / Ns) * Ns * rad + k;
+#pragma unroll
+            for (int r = 0; r < 5; ++r)
+                if (r < rad) dl[(base + r * Ns) * estride] = v[r];
+        }
+        __syncthreads();
+        C *t = src;
+        src = dst;
+        dst = t;
+        Ns *= rad;
+    }
+    return src;
+}
+
+// Full twiddle table w^t = exp(-2 pi i t / M), t < M, from the half table (t < M/2).
+template <typename C>
+__device__ __forceinline__ void load_twiddles_full(C *s_tw, const C *tw, int M) {
+    for (int t = threadIdx.x; t < M; t += blockDim.x) {
+        C w = tw[t % (M / 2)];
+        if (t >= M / 2) { w.x = -w.x; w.y = -w.y; }
+        s_tw[t] = w;
+    }
+}
+
+struct CoarseArgs {
+    const void *in;
+    void *out;
+    const void *tw;      // M/2 twiddles exp(-2 pi i t / M) in R
+    const void *khat;    // real-even kernel spectrum octant (M/2+1)^3 in R (z pass)
+    int M, MH, nin, nout, out_off;
+    int lines_cta;       // x passes: lines per CTA
+    int cols_cta;        // column passes: columns per CTA
+    long in_sp, in_row, out_sp, out_row;  // column passes: slab and row strides (complex entries)
+    RadixPlan rp;
+};
+
+// Forward real transform along x of the dense coarse charge F^H (nin^3,
+// FP64): line (zi, yi) of nin samples, zero padded to M; half spectrum
+// kx <= M/2 to out[(zi nin + yi) MH + kx].
+template <typename R>
+__global__ void __launch_bounds__(256) k_cfft_x(CoarseArgs a) {
+    using C = typename Cx<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int M = a.M, LS = M + 1;
+    C *tw = (C *)smem_raw;
+    C *A = tw + M;
+    C *B = A + a.lines_cta * LS;
+    const int zi = blockIdx.x, y0 = blockIdx.y * a.lines_cta, nl = min(a.lines_cta, a.nin - y0);
+    load_twiddles_full(tw, (const C *)a.tw, M);
+    const double *F = (const double *)a.in;
+    for (int e = threadIdx.x; e < nl * M; e += blockDim.x) {
+        const int l = e / M, x = e % M;
+        C v = Cx<R>::mk(0, 0);
+        if (x < a.nin) v.x = R(F[((long)zi * a.nin + y0 + l) * a.nin + x]);
+        A[l * LS + x] = v;
+    }
+    __syncthreads();
+    const C *res = fft_stockham<C, R>(A, B, nl, LS, 1, M, a.rp, tw, false);
+    C *out = (C *)a.out;
+    for (int e = threadIdx.x; e < nl * a.MH; e += blockDim.x) {
+        const int l = e / a.MH, k = e % a.MH;
+        out[((long)zi * a.nin + y0 + l) * a.MH + k] = res[l * LS + k];
+    }
+}
+
+// Column transforms over slab blockIdx.x, columns kx of chunk blockIdx.y:
+//   MODE 0: forward; rows t < nin in, all M rows out.
+//   MODE 1: inverse; all M rows in; rows t < nout out from positions (out_off + t) mod M.
+//   MODE 2: forward (rows t < nin in), product with the real-even kernel
+//           spectrum at (kx, ky = slab, kz), inverse; rows as MODE 1.
+template <typename R, int MODE>
+__global__ void __launch_bounds__(256) k_cfft_col(CoarseArgs a) {
+    using C = typename Cx<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int M = a.M, CC = a.cols_cta;
+    C *tw = (C *)smem_raw;
+    C *A = tw + M;
+    C *B = A + M * CC;
+    const int q = blockIdx.x, c0 = blockIdx.y * CC, nc = min(CC, a.MH - c0);
+    load_twiddles_full(tw, (const C *)a.tw, M);
+    const C *in = (const C *)a.in + q * a.in_sp + c0;
+    const int nrow_in = MODE == 1 ? M : a.nin;
+    for (int e = threadIdx.x; e < M * CC; e += blockDim.x) {
+        const int r = e / CC, c = e % CC;
+        A[e] = (r < nrow_in && c < nc) ? in[r * a.in_row + c] : Cx<R>::mk(0, 0);
+    }
+    __syncthreads();
+    C *res;
+    if (MODE == 0) {
+        res = fft_stockham<C, R>(A, B, CC, 1, CC, M, a.rp, tw, false);
+        C *out = (C *)a.out + q * a.out_sp + c0;
+        for (int e = threadIdx.x; e < M * nc; e += blockDim.x) {
+            const int r = e / nc, c = e % nc;
+            out[r * a.out_row + c] = res[r * CC + c];
+        }
+        return;
+    }
+    if (MODE == 2) {
+        res = fft_stockham<C, R>(A, B, CC, 1, CC, M, a.rp, tw, false);
+        const R *khat = (const R *)a.khat;
+        const int ky = q < M - q ? q : M - q;
+        for (int e = threadIdx.x; e < M * CC; e += blockDim.x) {
+            const int r = e / CC, c = e % CC;
+            const int kz = r < M - r ? r : M - r;
+            const int kx0 = c0 + c, kx = kx0 < M - kx0 ? kx0 : M - kx0;
+            C v = res[e];
+            if (c < nc) {
+                const R k = khat[((long)kx * a.MH + ky) * a.MH + kz];
+                v.x = v.x * k;
+                v.y = v.y * k;
+            }
+            res[e] = v;
+        }
+        __syncthreads();
+        C *other = res == A ? B : A;
+        res = fft_stockham<C, R>(res, other, CC, 1, CC, M, a.rp, tw, true);
+    } else {
+        res = fft_stockham<C, R>(A, B, CC, 1, CC, M, a.rp, tw, true);
+    }
+    C *out = (C *)a.out + q * a.out_sp + c0;
+    for (int e = threadIdx.x; e < a.nout * nc; e += blockDim.x) {
+        const int t = e / nc, c = e % nc;
+        int pos = (a.out_off + t) % M;
+        if (pos < 0) pos += M;
+        out[t * a.out_row + c] = res[pos * CC + c];
+    }
+}
+
+// Inverse real transform along x: row (zo, yo) of the half spectrum,
+// extended by Hermitian symmetry; real outputs t < nout from positions
+// (out_off + t) mod M to out[(zo nout + yo) nout + t] (type R).
+template <typename R>
+__global__ void __launch_bounds__(256) k_cifft_x(CoarseArgs a) {
+    using C = typename Cx<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int M = a.M, LS = M + 1;
+    C *tw = (C *)smem_raw;
+    C *A = tw + M;
+    C *B = A + a.lines_cta * LS;
+    const int zo = blockIdx.x, y0 = blockIdx.y * a.lines_cta, nl = min(a.lines_cta, a.nout - y0);
+    load_twiddles_full(tw, (const C *)a.tw, M);
+    const C *in = (const C *)a.in + ((long)zo * a.nout + y0) * a.MH;
+    for (int e = threadIdx.x; e < nl * M; e += blockDim.x) {
+        const int l = e / M, k = e % M;
+        C v;
+        if (k < a.MH) {
+            v = in[l * a.MH + k];
+        } else {
+            v = in[l * a.MH + (M - k)];
+            v.y = -v.y;
+        }
+        A[l * LS + k] = v;
+    }
+    __syncthreads();
+    const C *res = fft_stockham<C, R>(A, B, nl, LS, 1, M, a.rp, tw, true);
+    R *out = (R *)a.out + ((long)zo * a.nout + y0) * a.nout;
+    for (int e = threadIdx.x; e < nl * a.nout; e += blockDim.x) {
+        const int l = e / a.nout, t = e % a.nout;
+        int pos = (a.out_off + t) % M;
+        if (pos < 0) pos += M;
+        out[l * a.nout + t] = res[l * LS + pos].x;
+    }
+}
+
+// Radix plan of M: radix-4 stages first, then 2, 3, 5 (n = 0 if M has
+// another factor).
+RadixPlan radix_plan(int M) {
+    RadixPlan rp{};
+    int m = M;
+    for (int r : {4, 2, 3, 5})
+        while (m % r == 0 && rp.n < 16) {
+            rp.r[rp.n++] = r;
+            m /= r;
+        }
+    if (m != 1) rp.n = 0;
+    return rp;
+}
+
+template <typename R>
+size_t coarse_smem(int M, int lines) { return ((size_t)M + 2 * (size_t)lines) * sizeof(typename Cx<R>::T); }
+
+template <typename R>
+void set_cfft_attrs() {
+    const int big = 220 * 1024;
+    cudaFuncSetAttribute(k_cfft_x<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_cfft_col<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_cfft_col<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_cfft_col<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_cifft_x<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
+
+// The coarse solve phi^H = G^H * F^H (5 launches): forward x, forward y,
+// z (forward, kernel spectrum, inverse), inverse y, inverse x.  b0, b1:
+// spectra buffers (complex R); F^H FP64 in, phi^H in R out.
+template <typename R>
+cudaError_t run_coarse_t(const mlc_plan_s *pl, const void *khat, const void *tw, cudaStream_t st) {
+    using C = typename Cx<R>::T;
+    const Geom &g = pl->g;
+    const int M = g.Mc, MH = g.Mhc, nin = g.nf, W = g.no;
+    CoarseArgs a{};
+    a.tw = tw;
+    a.khat = khat;
+    a.M = M;
+    a.MH = MH;
+    a.nin = nin;
+    a.nout = W;
+    a.out_off = g.olo - g.flo;
+    a.rp = radix_plan(M);
+    if (a.rp.n == 0) return cudaErrorInvalidValue;
+    const size_t budget = 200 * 1024 / sizeof(C);  // complex entries of shared memory
+    // rows per CTA of the x passes and columns per CTA of the column passes
+    a.lines_cta = (int)std::min<size_t>(16, (budget - M) / (2 * (size_t)(M + 1)));
+    a.cols_cta = (int)std::min<size_t>(16, (budget - M) / (2 * (size_t)M));
+    if (a.lines_cta < 1 || a.cols_cta < 1) return cudaErrorInvalidValue;
+    const int gx = (MH + a.cols_cta - 1) / a.cols_cta;
+    const size_t smx = coarse_smem<R>(M, a.lines_cta * (M + 1)), smc = coarse_smem<R>(M, M * a.cols_cta);
+    mark(pl, 6, st);
+    {   // 1. forward x: F^H [zi][yi][x] -> b0 [zi][yi][kx]
+        CoarseArgs b = a;
+        b.in = pl->FH;
+        b.out = pl->cbuf0;
+        k_cfft_x<R><<<dim3(nin, (nin + a.lines_cta - 1) / a.lines_cta), 256, smx, st>>>(b);
+    }
+    mark(pl, 7, st);
+    {   // 2. forward y: b0 [zi][yi][kx] -> b1 [zi][ky][kx]
+        CoarseArgs b = a;
+        b.in = pl->cbuf0;
+        b.out = pl->cbuf1;
+        b.in_sp = (long)nin * MH; b.in_row = MH;
+        b.out_sp = (long)M * MH; b.out_row = MH;
+        k_cfft_col<R, 0><<<dim3(nin, gx), 256, smc, st>>>(b);
+    }
+    mark(pl, 8, st);
+    {   // 3. z: b1 [zi][ky][kx] -> b0 [zo][ky][kx]
+        CoarseArgs b = a;
+        b.in = pl->cbuf1;
+        b.out = pl->cbuf0;
+        b.in_sp = MH; b.in_row = (long)M * MH;
+        b.out_sp = MH; b.out_row = (long)M * MH;
+        k_cfft_col<R, 2><<<dim3(M, gx), 256, smc, st>>>(b);
+    }
+    mark(pl, 9, st);
+    {   // 4. inverse y: b0 [zo][ky][kx] -> b1 [zo][yo][kx]
+        CoarseArgs b = a;
+        b.in = pl->cbuf0;
+        b.out = pl->cbuf1;
+        b.in_sp = (long)M * MH; b.in_row = MH;
+        b.out_sp = (long)W * MH; b.out_row = MH;
+        k_cfft_col<R, 1><<<dim3(W, gx), 256, smc, st>>>(b);
+    }
+    mark(pl, 10, st);
+    {   // 5. inverse x: b1 [zo][yo][kx] -> phi^H [zo][yo][xo]
+        CoarseArgs b = a;
+        b.in = pl->cbuf1;
+        b.out = pl->phiH;
+        k_cifft_x<R><<<dim3(W, (W + a.lines_cta - 1) / a.lines_cta), 256, smx, st>>>(b);
+    }
+    return cudaGetLastError();
+}
+
 template <typename R>
 inline size_t fft_smem_bytes(int M, int lines, int ls) {
     return ((size_t)(M / 2) + (size_t)lines * ls) * 2 * sizeof(R);
-}
-
-// Dense (coarse-grid) convolution pipeline kernels in working precision R.
-template <int LOG2M, typename R>
-void set_coarse_attrs() {
-    const int big = 200 * 1024;
-    cudaFuncSetAttribute(k_fwd_x<LOG2M, double, false, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_col<LOG2M, 0, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_col<LOG2M, 1, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_col<LOG2M, 2, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_inv_x<LOG2M, R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
 // Local-convolution (patch) kernels in working precision R.
@@ -2194,81 +2465,6 @@ void set_patch_attrs() {
     cudaFuncSetAttribute(k_slab64r<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_inv_x_pruned<LOG2M, R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_inv_x64<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-}
-
-// One Hockney convolution pipeline (5 launches) for `nbatch` problems with
-// nin input nodes per axis at positions [0, nin) and nout outputs per axis
-// from positions out_off + t.  R: working precision; output array of type R.
-struct ConvDesc {
-    int M, log2M, nbatch, nin, nout, out_off;
-    const void *src;     // fwd_x input (patch gather or dense FP64)
-    bool patch, f32;
-    int N, n, np;
-    void *b0, *b1;       // ping-pong spectra (complex R)
-    void *out;           // nbatch x nout^3, type R
-    const void *khat;    // real R
-    const void *tw;      // complex R
-    const mlc_plan_s *pl;  // timing events (slots ev0 .. ev0+4)
-    int ev0;
-};
-
-template <int LOG2M, typename R>
-cudaError_t run_conv_t(const ConvDesc &d, cudaStream_t st) {
-    constexpr int M = 1 << LOG2M, MH = M / 2 + 1;
-    const int nin = d.nin, W = d.nout;
-    mark(d.pl, d.ev0 + 0, st);
-    // 1. forward x: out A1[p][zi][yi][kx]
-    {
-        FwdXArgs a{d.src, d.b0, d.N, d.n, d.np, nin, 0, d.tw, Items{}};
-        a.lines_cta = (M <= 64) ? nin : 16;
-        a.lines_cta = a.lines_cta > nin ? nin : a.lines_cta;
-        dim3 grid(d.nbatch * nin, (nin + a.lines_cta - 1) / a.lines_cta);
-        size_t sm = fft_smem_bytes<R>(M, a.lines_cta, M + 1);
-        k_fwd_x<LOG2M, double, false, R><<<grid, 256, sm, st>>>(a);
-    }
-    const int CC = (M <= 64) ? MH : 16;
-    const int gx = (MH + CC - 1) / CC;
-    const size_t smc = fft_smem_bytes<R>(M, M, CC);
-    mark(d.pl, d.ev0 + 1, st);
-    // 2. forward y: A1[p][zi][yi][kx] -> A2[p][zi][ky][kx]
-    {
-        ColArgs a{};
-        a.in = d.b0; a.out = d.b1; a.S2 = nin;
-        a.in_sp = (long)nin * nin * MH; a.in_sq = (long)nin * MH; a.in_row = MH;
-        a.out_sp = (long)nin * M * MH; a.out_sq = (long)M * MH; a.out_row = MH;
-        a.ncols = MH; a.cols_cta = CC; a.nin = nin; a.nout = M; a.out_off = 0; a.tw = d.tw;
-        k_col<LOG2M, 0, R><<<dim3(d.nbatch * nin, gx), 256, smc, st>>>(a);
-    }
-    mark(d.pl, d.ev0 + 2, st);
-    // 3. z: forward, x kernel, inverse: A2[p][zi][ky][kx] -> A3[p][zo][ky][kx]
-    {
-        ColArgs a{};
-        a.in = d.b1; a.out = d.b0; a.S2 = M;
-        a.in_sp = (long)nin * M * MH; a.in_sq = MH; a.in_row = (long)M * MH;
-        a.out_sp = (long)W * M * MH; a.out_sq = MH; a.out_row = (long)M * MH;
-        a.ncols = MH; a.cols_cta = CC; a.nin = nin; a.nout = W; a.out_off = d.out_off;
-        a.khat = d.khat; a.tw = d.tw;
-        k_col<LOG2M, 2, R><<<dim3(d.nbatch * M, gx), 256, smc, st>>>(a);
-    }
-    mark(d.pl, d.ev0 + 3, st);
-    // 4. inverse y: A3[p][zo][ky][kx] -> A4[p][zo][yo][kx]
-    {
-        ColArgs a{};
-        a.in = d.b0; a.out = d.b1; a.S2 = W;
-        a.in_sp = (long)W * M * MH; a.in_sq = (long)M * MH; a.in_row = MH;
-        a.out_sp = (long)W * W * MH; a.out_sq = (long)W * MH; a.out_row = MH;
-        a.ncols = MH; a.cols_cta = CC; a.nin = M; a.nout = W; a.out_off = d.out_off; a.tw = d.tw;
-        k_col<LOG2M, 1, R><<<dim3(d.nbatch * W, gx), 256, smc, st>>>(a);
-    }
-    mark(d.pl, d.ev0 + 4, st);
-    // 5. inverse x (real): A4[p][zo][yo][kx] -> out[p][zo][yo][xo]
-    {
-        InvXArgs a{d.b1, d.out, W, W, d.out_off, 0, d.tw};
-        a.lines_cta = (M <= 64) ? W : 16;
-        dim3 grid(d.nbatch * W, (W + a.lines_cta - 1) / a.lines_cta);
-        k_inv_x<LOG2M, R, R><<<grid, 256, fft_smem_bytes<R>(M, a.lines_cta, M + 1), st>>>(a);  // phi^H in R
-    }
-    return cudaGetLastError();
 }
 
 // Local convolutions of a set of patches: forward x (real), fused slab (y,
@@ -2369,17 +2565,6 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
     return cudaGetLastError();
 }
 
-template <typename R>
-cudaError_t run_conv(const ConvDesc &d, cudaStream_t st) {
-    switch (d.log2M) {
-        case 5: return run_conv_t<5, R>(d, st);
-        case 6: return run_conv_t<6, R>(d, st);
-        case 7: return run_conv_t<7, R>(d, st);
-        case 8: return run_conv_t<8, R>(d, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
 void stencil_b(int Q, double b[4]) {
     if (Q == 4) {
         b[0] = -4.0; b[1] = 1.0 / 3.0; b[2] = 1.0 / 6.0; b[3] = 0.0;
@@ -2407,14 +2592,8 @@ void configure_kernels() {
     set_patch_attrs<6, float>();
     set_patch_attrs<5, double>();
     set_patch_attrs<6, double>();
-    set_coarse_attrs<5, dfl>();
-    set_coarse_attrs<6, dfl>();
-    set_coarse_attrs<7, dfl>();
-    set_coarse_attrs<8, dfl>();
-    set_coarse_attrs<5, double>();
-    set_coarse_attrs<6, double>();
-    set_coarse_attrs<7, double>();
-    set_coarse_attrs<8, double>();
+    set_cfft_attrs<dfl>();
+    set_cfft_attrs<double>();
     const int big = 200 * 1024;
 #define MLC_DIR_ATTR(NN)                                                                          \
     cudaFuncSetAttribute(k_dirichlet<double, NN, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
@@ -2563,19 +2742,9 @@ cudaError_t launch_assemble(const mlc_plan_s *pl, cudaStream_t st) {
 }
 
 cudaError_t launch_coarse(const mlc_plan_s *pl, cudaStream_t st) {
-    const Geom &g = pl->g;
-    ConvDesc d{};
-    d.M = g.Mc; d.log2M = g.log2Mc; d.nbatch = 1; d.nin = g.nf; d.nout = g.no;
-    d.out_off = g.olo - g.flo;
-    d.src = pl->FH; d.patch = false; d.f32 = false;
-    d.b0 = pl->cbuf0; d.b1 = pl->cbuf1; d.out = pl->phiH;
-    d.pl = pl; d.ev0 = 6;
-    if (g.fine == FINE_F64) {  // coarse FFTs in FP64
-        d.khat = pl->khat_c; d.tw = pl->tw_c;
-        return run_conv<double>(d, st);
-    }
-    d.khat = pl->khat_c_df; d.tw = pl->tw_c_df;
-    return run_conv<dfl>(d, st);  // coarse FFTs in double-float arithmetic
+    if (pl->g.fine == FINE_F64)  // coarse FFTs in FP64
+        return run_coarse_t<double>(pl, pl->khat_c, pl->tw_c, st);
+    return run_coarse_t<dfl>(pl, pl->khat_c_df, pl->tw_c_df, st);  // in double-float arithmetic
 }
 
 cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st) {
@@ -2591,6 +2760,18 @@ cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st) {
     a.npad = g.npad;
     lagrange_rows_df(g.b, a.lw);
     lagrange_rows(g.b, a.lwd);
+    a.tpl = pl->tpl;
+    {   // sums along v of I^H(phi^H) per (plane, coarse row)
+        const long tp = 3L * (g.np + 1) * g.no * (g.N + 1);
+        const unsigned nb2 = (unsigned)((tp + 255) / 256);
+        LagW w;
+        std::memcpy(w.lw, a.lw, sizeof(w.lw));
+        std::memcpy(w.lwd, a.lwd, sizeof(w.lwd));
+        if (g.fine == FINE_F64)
+            k_plane_interp<double><<<nb2, 256, 0, st>>>(pl->phiH, pl->tpl, g.N, g.n, g.np, g.b, g.olo, g.no, w);
+        else
+            k_plane_interp<dfl><<<nb2, 256, 0, st>>>(pl->phiH, pl->tpl, g.N, g.n, g.np, g.b, g.olo, g.no, w);
+    }
     const long tot = g.n_planes_total;
     const unsigned nbk = (unsigned)((tot + 127) / 128);
 #define MLC_BND(NN)                                                                   \

@@ -148,6 +148,7 @@ struct mlc_plan_s {
     double2 *cbuf0, *cbuf1;  // coarse spectra
     double *phiH;            // no^3 (fine precision, 8 bytes)
     double *phiB;            // face planes (fine precision, 8 bytes)
+    double *tpl;             // 3 (np+1) no (N+1): I^H(phi^H) summed along v per plane and coarse row
     void *f_stage, *phi_stage;  // device staging for mlc_solve_host
     int *err;                // device error word: nonzero if a bounded wait in a kernel gave up
     size_t ws_bytes;

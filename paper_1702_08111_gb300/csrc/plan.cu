@@ -202,10 +202,22 @@ mlc_status derive_geometry(const mlc_params &pp, Geom &g) {
     g.olo = -g.b; g.ohi = g.N / 4 + g.b;
     g.no = g.ohi - g.olo + 1;
     g.Lc = std::max(g.fhi - g.olo, g.ohi - g.flo);
-    g.Mc = next_pow2(std::max(2 * g.Lc, std::max(g.nf, g.no)));
-    g.log2Mc = ilog2(g.Mc);
+    // coarse Hockney period: the smallest even length >= 2 Lc (and >= the
+    // extents) whose only prime factors are 2, 3 and 5 (mixed-radix FFTs)
+    {
+        auto smooth = [](int m) {
+            for (int r : {2, 3, 5})
+                while (m % r == 0) m /= r;
+            return m == 1;
+        };
+        int mc = std::max(2 * g.Lc, std::max(g.nf, g.no));
+        mc += mc & 1;
+        while (!smooth(mc)) mc += 2;
+        g.Mc = mc;
+    }
+    g.log2Mc = 0;
     g.Mhc = g.Mc / 2 + 1;
-    if (g.M > 256 || g.Mc > 256 || g.M < 32) return MLC_ERR_UNSUPPORTED;
+    if (g.M > 256 || g.Mc > 512 || g.M < 32) return MLC_ERR_UNSUPPORTED;
     if (g.n > 16) return MLC_ERR_UNSUPPORTED;  // Dirichlet tile held in shared memory
     g.S = (2 * g.b + 2) * (2 * g.b + 2);
     g.nc = (g.n + 2 * g.s) / 4 + 1;
@@ -540,24 +552,45 @@ mlc_status mlc_params_init(mlc_params *p, int N, int n, int s, int P, int Q) {
     return MLC_OK;
 }
 
-mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
+}  // extern "C"
+
+namespace {
+
+// Plan creation; dgf_host (optional): the caller's DGF octant [0, dgf_Lh]^3
+// in place of the device's cached table.
+mlc_status create_plan(const mlc_params *params, const double *dgf_host, int dgf_Lh, mlc_plan_t *out) {
     if (!params || !out) return MLC_ERR_INVALID_ARG;
     *out = nullptr;
     Geom g;
     TRY(derive_geometry(*params, g));
     std::call_once(g_cfg_once, configure_kernels);
+    int device = 0;
+    TRY_CUDA(cudaGetDevice(&device));
     mlc_plan_s *pl = new (std::nothrow) mlc_plan_s();
     if (!pl) return MLC_ERR_OOM;
     pl->g = g;
     pl->params = *params;
-    TRY_CUDA(cudaGetDevice(&pl->device));
+    pl->device = device;
     // lag extent: local fields n + s, coarse Lc, basis fields (checked in build_tables)
     Geom &G = pl->g;
     G.L = std::max(G.n + G.s, G.Lc);
     const int Lbasis_bound = G.n + G.gb + 4 * G.b + 12;
     int Lneed = std::max(G.L, G.gb > G.ga ? Lbasis_bound : 0);
     if (Lneed >= G.zeta * G.nD) G.nD = (Lneed + G.zeta) / G.zeta + 1;
-    mlc_status st = get_dgf(pl->device, G.Q, G.nD, G.zeta, Lneed, &pl->dgf, &pl->dgf_L);
+    mlc_status st = MLC_OK;
+    if (dgf_host) {
+        if (dgf_Lh < Lneed) {
+            st = MLC_ERR_INVALID_ARG;
+        } else {
+            const size_t cnt = (size_t)(dgf_Lh + 1) * (dgf_Lh + 1) * (dgf_Lh + 1);
+            double *d = nullptr;
+            st = dev_upload(pl, &d, std::vector<double>(dgf_host, dgf_host + cnt));
+            pl->dgf = d;
+            pl->dgf_L = dgf_Lh;
+        }
+    } else {
+        st = get_dgf(pl->device, G.Q, G.nD, G.zeta, Lneed, &pl->dgf, &pl->dgf_L);
+    }
     if (st == MLC_OK) st = build_tables(pl);
     auto alloc_all = [&]() -> mlc_status {
         TRY(dev_alloc(pl, &pl->khat, (size_t)G.Mh * G.Mh * G.Mh, false));
@@ -645,6 +678,7 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
         TRY(dev_alloc(pl, &pl->cbuf1, std::max(nf * Mc * Mhc, no * no * Mhc)));
         TRY(dev_alloc(pl, &pl->phiH, no * no * no));
         TRY(dev_alloc(pl, &pl->phiB, (size_t)G.n_planes_total));
+        TRY(dev_alloc(pl, &pl->tpl, 3 * (size_t)(G.np + 1) * G.no * (G.N + 1)));
         TRY(dev_alloc(pl, &pl->err, 1, false));
         TRY_CUDA(cudaMemset(pl->err, 0, sizeof(int)));
         return MLC_OK;
@@ -679,6 +713,31 @@ mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
         return st;
     }
     *out = pl;
+    return MLC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mlc_status mlc_plan_create_ex(const mlc_params *params, mlc_plan_t *out) {
+    return create_plan(params, nullptr, 0, out);
+}
+
+mlc_status mlc_plan_set_dgf(mlc_plan_t pl, const double *table, int L) {
+    if (!pl || !table || L < 1) return MLC_ERR_INVALID_ARG;
+    int dev = -1;
+    TRY_CUDA(cudaGetDevice(&dev));
+    if (dev != pl->device) return MLC_ERR_INVALID_ARG;
+    mlc_plan_t np = nullptr;
+    TRY(create_plan(&pl->params, table, L, &np));
+    TRY_CUDA(cudaDeviceSynchronize());
+    mlc_batch_forget(pl);
+    np->user_scratch = pl->user_scratch;
+    np->fault = pl->fault;
+    np->timing = pl->timing;
+    std::swap(*pl, *np);  // the handle keeps its identity; np now holds the old tables
+    free_plan(np);
     return MLC_OK;
 }
 

@@ -102,6 +102,7 @@ def workload(name: str) -> Workload:
     single_bump_32: 32^3, 64 patches of 8^3, support 8, Q=4; one bump a=0.35 at the centre.
     bumps8_128:     128^3, 512 patches of 16^3, support 16, Q=4; 8 bumps from seed 1.
     bumps32_256_q6: 256^3, 4096 patches of 16^3, support 16, Q=6; 32 bumps from seed 3, FP32 charge.
+    bumps16_128_q6: 128^3, 512 patches of the same geometry, 16 bumps from seed 3, FP32 charge.
     """
     if name == "single_bump_32":
         return Workload(name, 32, 8, 8, 4, bumps=single_bump())
@@ -109,6 +110,9 @@ def workload(name: str) -> Workload:
         return Workload(name, 128, 16, 16, 4, bumps=draw_bumps(8, 1))
     if name == "bumps32_256_q6":
         return Workload(name, 256, 16, 16, 6, bumps=draw_bumps(32, 3), charge_dtype="f32")
+    if name == "bumps16_128_q6":
+        # profiling case: the per-patch kernels of bumps32_256_q6 on 512 patches
+        return Workload(name, 128, 16, 16, 6, bumps=draw_bumps(16, 3), charge_dtype="f32")
     if name == "bumps8_64_q6":
         # reduced-size case with the 27-point operator: same patch geometry as bumps32_256_q6
         return Workload(name, 64, 16, 16, 6, bumps=draw_bumps(8, 7))

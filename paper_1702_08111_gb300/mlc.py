@@ -28,6 +28,7 @@ EXPORTED = [
     "mlc_server_destroy", "mlc_server_enqueue", "mlc_server_wait", "mlc_status_string",
     "mlc_debug_set_timing", "mlc_debug_timing", "mlc_solve_noalloc", "mlc_plan_status",
     "mlc_debug_batch_choice", "mlc_plan_scratch_bytes", "mlc_plan_set_scratch", "mlc_debug_set_fault",
+    "mlc_plan_set_dgf",
 ]
 LAUNCH_NAMES = ["moments", "conv_fwd_x", "conv_slab", "conv_inv_x", "resid", "assemble",
                 "coarse_fwd_x", "coarse_fwd_y", "coarse_z_kernel", "coarse_inv_y", "coarse_inv_x",
@@ -91,6 +92,7 @@ def load_library(path: str = LIB_PATH):
     lib.mlc_server_wait.argtypes = [vp, ctypes.c_uint64, i, ctypes.POINTER(mlc_result)]
     lib.mlc_debug_set_timing.argtypes = [vp, i]
     lib.mlc_debug_set_fault.argtypes = [vp, i]
+    lib.mlc_plan_set_dgf.argtypes = [vp, vp, i]
     lib.mlc_debug_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i]
     lib.mlc_status_string.argtypes = [i]
     lib.mlc_status_string.restype = ctypes.c_char_p
@@ -242,6 +244,19 @@ class Plan:
                                              ctypes.c_void_p(phi_host.data_ptr()),
                                              ctypes.c_void_p(_stream_handle(stream))), "mlc_solve_host")
         return phi_host
+
+    def set_dgf(self, table):
+        """mlc_plan_set_dgf: use the DGF octant `table` ((L+1)^3 FP64 array,
+        k fastest) and rebuild the tables derived from it."""
+        import numpy as np
+        t = np.ascontiguousarray(table, dtype=np.float64)
+        L = t.shape[0] - 1
+        if t.shape != (L + 1,) * 3:
+            raise ValueError("table must be a cube (L+1)^3")
+        _check(load_library().mlc_plan_set_dgf(self._h, ctypes.c_void_p(t.ctypes.data), L), "set_dgf")
+        arr = (ctypes.c_int * 16)()
+        _check(load_library().mlc_plan_info(self._h, arr), "mlc_plan_info")
+        self.info = PlanInfo(*list(arr))
 
     def set_fault(self, kind: int):
         """Test hook mlc_debug_set_fault: 1 = the inverse-x bulk copies are not

@@ -374,3 +374,72 @@ def test_bounded_wait_runs_out_and_reports_timeout(torch_cuda):
         assert torch.equal(out, ref)
     with pytest.raises(mlc.MLCError):
         plan.set_fault(7)
+
+
+def _golden_256():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_bumps32_256_q6_samples.txt")
+    scale = None
+    rows = []
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("#"):
+                if "max |phi| =" in line:
+                    scale = float(line.split("max |phi| =")[1])
+                continue
+            a = line.split()
+            rows.append((int(a[0]), int(a[1]), int(a[2]), float(a[3])))
+    g = np.array([r[:3] for r in rows])
+    return g, np.array([r[3] for r in rows]), scale
+
+
+@pytest.mark.parametrize("tier", [FP64, DF, SPLIT, SPLIT_DF])
+def test_full_size_256_against_oracle_samples(torch_cuda, tier):
+    """The bench workload at full size (256^3, 4096 patches, Q = 6, FP32-rounded
+    charge) in every tier, in the launch configuration bench.py times, against
+    the oracle's potential at 4096 seeded nodes (tests/golden, written by
+    make_oracle_256_samples.py from oracle/ alone); errors relative to the
+    oracle's max |phi| over the whole grid."""
+    from paper_1702_08111_gb300 import mlc
+    torch = torch_cuda
+    g, ref, scale = _golden_256()
+    w = I.workload("bumps32_256_q6")
+    f32 = w.charge()
+    f = f32 if tier in (SPLIT, SPLIT_DF) else f32.astype(np.float64)
+    plan = mlc.Plan(256, 16, 16, 4, 6, tier=tier)
+    phi = plan.solve(torch.from_numpy(f).cuda())
+    torch.cuda.synchronize()
+    plan.status()
+    got = phi[g[:, 0], g[:, 1], g[:, 2]].cpu().numpy()
+    err = float(np.abs(got - ref).max() / scale)
+    assert err <= (TOL if tier in EXACT_TIERS else SPLIT_TOL), (tier, err)
+
+
+def test_set_dgf_uses_the_injected_table(torch_cuda, G4):
+    """mlc_plan_set_dgf: the oracle's DGF table injected as data gives the
+    oracle's result; a doubled table gives the oracle's result for the doubled
+    table (so the injected table, not the library's own, is what the solve
+    uses); a table too small for the plan is rejected and leaves it intact."""
+    from paper_1702_08111_gb300 import mlc
+    torch = torch_cuda
+    w = I.workload("single_bump_32")
+    f = w.charge()
+    ft = torch.from_numpy(f).cuda()
+    prm = O.Params(N=32, n=8, s=8, Q=4)
+    plan = mlc.Plan(32, 8, 8, 4, 4)
+    base = plan.solve(ft).clone()
+    L = plan.info.L
+    G = np.ascontiguousarray(G4[:L + 1, :L + 1, :L + 1])
+    plan.set_dgf(G)
+    a = plan.solve(ft).cpu().numpy()
+    assert relmax(a, O.solve_open(prm, f, G1=G4)) <= TOL
+    plan.set_dgf(2.0 * G)
+    b = plan.solve(ft).cpu().numpy()
+    ref2 = O.solve_open(prm, f, G1=2.0 * G4)
+    assert relmax(b, ref2) <= TOL
+    assert relmax(b, a) > 0.5
+    with pytest.raises(mlc.MLCError) as e:
+        plan.set_dgf(G[:9, :9, :9])
+    assert e.value.status == 1
+    plan.set_dgf(G)
+    assert relmax(plan.solve(ft).cpu().numpy(), base.cpu().numpy()) <= TOL
