@@ -1700,6 +1700,9 @@ __global__ void __launch_bounds__(256) k_plane_interp(const void *phiH_, void *o
 struct BndArgs {
     const void *phiH, *resid;  // fine precision T
     const void *tpl;           // k_plane_interp output, fine precision T
+    const float *ringR;        // RING: [patch][ring_rows_pad] ring terms of this launch's axis
+    long ring_rows_pad;
+    long idx0, idx1;           // face-plane nodes of this launch: [idx0, idx1)
     const void *mom, *D;       // ring tables in the ring precision RT
     void *phiB;                // fine precision T
     int N, n, np, ga, gb, b, npoly, olo, no, wa, wbx, npa, pl0;
@@ -1712,13 +1715,13 @@ struct BndArgs {
 // phi^B at every face-plane node (axis, plane j, u, v).  RT: precision of the
 // Legendre ring sums (the local-convolution precision: FP32, double-float or
 // FP64); T: the interpolation and the accumulation (FP64 or double-float).
-template <typename RT, int NN, typename T>
+// RING: the ring terms come from the ring GEMM (ringR) instead of per-node
+// dot products of the ring-table rows with the coefficients.
+template <typename RT, int NN, typename T, bool RING = false>
 __global__ void __launch_bounds__(128, 6) k_boundary(BndArgs a) {
     constexpr int n = NN;  // patch size as a constant: the index divisions become multiplies
-    const long pn = (long)(a.N + 1) * (a.N + 1);
-    const long tot = 3L * (a.np + 1) * pn;
-    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= tot) return;
+    const long idx = a.idx0 + (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= a.idx1) return;
     const T *phiH = (const T *)a.phiH;
     const T *resid = (const T *)a.resid;
     int g[3], axis, jp;
@@ -1757,8 +1760,13 @@ __global__ void __launch_bounds__(128, 6) k_boundary(BndArgs a) {
                     // dense ring row of (axis, plane, u, v): no index map to read
                     const int ra = axis == 0 ? r0 : (axis == 1 ? r1 : r2);
                     const int ru = axis == 0 ? r1 : r0, rv = axis == 2 ? r1 : r2;
-                    const long row = (((long)axis * a.npb + (ra - a.pb0) / n) * a.wbx + (ru + a.gb)) * a.wbx + (rv + a.gb);
-                    ring_dot((const RT *)a.mom + p * a.npad, (const RT *)a.D + row * a.npad, a.npad, ring);
+                    if constexpr (RING) {
+                        const long row = ((long)((ra - a.pb0) / n) * a.wbx + (ru + a.gb)) * a.wbx + (rv + a.gb);
+                        ring += a.ringR[p * a.ring_rows_pad + row];
+                    } else {
+                        const long row = (((long)axis * a.npb + (ra - a.pb0) / n) * a.wbx + (ru + a.gb)) * a.wbx + (rv + a.gb);
+                        ring_dot((const RT *)a.mom + p * a.npad, (const RT *)a.D + row * a.npad, a.npad, ring);
+                    }
                 }
             });
     ((T *)a.phiB)[idx] = FT<T>::rn(acc + FT<T>::of(ring));
@@ -2594,6 +2602,7 @@ void configure_kernels() {
     set_patch_attrs<6, double>();
     set_cfft_attrs<dfl>();
     set_cfft_attrs<double>();
+    configure_ring_gemm();
     const int big = 200 * 1024;
 #define MLC_DIR_ATTR(NN)                                                                          \
     cudaFuncSetAttribute(k_dirichlet<double, NN, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
@@ -2772,23 +2781,39 @@ cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st) {
         else
             k_plane_interp<dfl><<<nb2, 256, 0, st>>>(pl->phiH, pl->tpl, g.N, g.n, g.np, g.b, g.olo, g.no, w);
     }
-    const long tot = g.n_planes_total;
-    const unsigned nbk = (unsigned)((tot + 127) / 128);
-#define MLC_BND(NN)                                                                   \
-    case NN:                                                                          \
-        if (g.conv == CONV_F32 && g.fine == FINE_F64) k_boundary<float, NN, double><<<nbk, 128, 0, st>>>(a); \
-        else if (g.conv == CONV_F32) k_boundary<float, NN, dfl><<<nbk, 128, 0, st>>>(a);                      \
-        else if (g.conv == CONV_DF) k_boundary<dfl, NN, dfl><<<nbk, 128, 0, st>>>(a);                         \
-        else k_boundary<double, NN, double><<<nbk, 128, 0, st>>>(a);                                          \
-        break;
-    switch (g.n) {
-        MLC_BND(4)
-        MLC_BND(8)
-        MLC_BND(12)
-        MLC_BND(16)
-        default: return cudaErrorInvalidValue;
-    }
+    a.ringR = pl->ring_R;
+    a.ring_rows_pad = g.ring_rows_pad;
+    const long per_axis = (long)(g.np + 1) * g.plane_n;
+    // split tiers with a Legendre ring: one ring GEMM and one boundary launch
+    // per face-plane axis (the GEMM's output holds one axis at a time)
+    const bool gemm = g.conv == CONV_F32 && pl->ring_R != nullptr && pl->ring_aimg != nullptr;
+    for (int axis = 0; axis < 3; ++axis) {
+        if (!gemm && axis > 0) break;
+        a.idx0 = gemm ? axis * per_axis : 0;
+        a.idx1 = gemm ? (axis + 1) * per_axis : g.n_planes_total;
+        if (gemm) {
+            const cudaError_t e = launch_ring_gemm(pl, axis, st);
+            if (e != cudaSuccess) return e;
+        }
+        const unsigned nbk = (unsigned)((a.idx1 - a.idx0 + 127) / 128);
+#define MLC_BND(NN)                                                                                        \
+        case NN:                                                                                           \
+            if (gemm && g.fine == FINE_F64) k_boundary<float, NN, double, true><<<nbk, 128, 0, st>>>(a);   \
+            else if (gemm) k_boundary<float, NN, dfl, true><<<nbk, 128, 0, st>>>(a);                        \
+            else if (g.conv == CONV_F32 && g.fine == FINE_F64) k_boundary<float, NN, double><<<nbk, 128, 0, st>>>(a); \
+            else if (g.conv == CONV_F32) k_boundary<float, NN, dfl><<<nbk, 128, 0, st>>>(a);                 \
+            else if (g.conv == CONV_DF) k_boundary<dfl, NN, dfl><<<nbk, 128, 0, st>>>(a);                    \
+            else k_boundary<double, NN, double><<<nbk, 128, 0, st>>>(a);                                     \
+            break;
+        switch (g.n) {
+            MLC_BND(4)
+            MLC_BND(8)
+            MLC_BND(12)
+            MLC_BND(16)
+            default: return cudaErrorInvalidValue;
+        }
 #undef MLC_BND
+    }
     return cudaGetLastError();
 }
 

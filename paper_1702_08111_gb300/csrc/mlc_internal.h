@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -56,6 +57,8 @@ struct Geom {
                                      // (M/2+1) W rounded up to a multiple of 16 bytes
     int plane_n;                     // (N+1)^2 nodes per face plane
     long n_planes_total;             // 3 (np+1) (N+1)^2
+    int ring_rows, ring_ksteps;      // split tiers: ring-table rows per face-plane axis, K / 8 of the ring GEMM
+    long ring_rows_pad;              // ring_rows rounded up to the GEMM's row tile (128)
     int chunk;                       // patches per launch group of the local convolutions
     size_t scr_a1, scr_a4;           // scratch bytes per patch: x-transformed charges, slab outputs
 };
@@ -149,6 +152,8 @@ struct mlc_plan_s {
     double *phiH;            // no^3 (fine precision, 8 bytes)
     double *phiB;            // face planes (fine precision, 8 bytes)
     double *tpl;             // 3 (np+1) no (N+1): I^H(phi^H) summed along v per plane and coarse row
+    float *ring_aimg;        // split tiers: ring table as the tensor-core GEMM operand (TF32 hi/lo image)
+    float *ring_R;           // split tiers: [patch][ring_rows_pad] ring terms of one face-plane axis
     void *f_stage, *phi_stage;  // device staging for mlc_solve_host
     int *err;                // device error word: nonzero if a bounded wait in a kernel gave up
     size_t ws_bytes;
@@ -180,6 +185,21 @@ cudaError_t launch_dirichlet(const mlc_plan_s *pl, const Items &it, cudaStream_t
 cudaError_t launch_assemble(const mlc_plan_s *pl, cudaStream_t st);
 cudaError_t launch_coarse(const mlc_plan_s *pl, cudaStream_t st);
 cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st);
+// ring_gemm.cu: the Legendre ring terms of one face-plane axis as a tcgen05
+// GEMM (split tiers), and its plan-time operand image.
+cudaError_t launch_ring_gemm(const mlc_plan_s *pl, int axis, cudaStream_t st);
+void configure_ring_gemm();
+void ring_table_image(const std::vector<double> &Dd, int nrows_axis, int npad, int ksteps, long rows_pad,
+                      std::vector<float> &img);
+// Host rounding of a value to TF32 (10 stored mantissa bits), nearest, ties away from zero.
+inline float tf32_host(double v) {
+    float f = (float)v;
+    uint32_t b;
+    std::memcpy(&b, &f, 4);
+    b = (b + 0x1000u) & 0xFFFFE000u;
+    std::memcpy(&f, &b, 4);
+    return f;
+}
 // Index export (test hook): which = 0 face-plane nodes, 1 coarse nodes of the
 // F^H extent; count pass (cnt != nullptr) or fill pass (off, ent).
 cudaError_t launch_index_export(const mlc_plan_s *pl, int which, int *cnt, const long *off, int *ent,

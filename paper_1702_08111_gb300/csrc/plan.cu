@@ -421,6 +421,16 @@ mlc_status build_tables(mlc_plan_s *pl) {
                     }
         Dtab.swap(Dd);
     }
+    // split tiers: the ring table as the operand of the tensor-core ring GEMM
+    g.ring_rows = g.npb * g.wbx * g.wbx;
+    g.ring_ksteps = (g.npad + 7) / 8;
+    g.ring_rows_pad = ((long)g.ring_rows + 127) / 128 * 128;
+    if (ring && g.conv == CONV_F32) {
+        std::vector<float> img;
+        ring_table_image(Dtab, g.ring_rows, g.npad, g.ring_ksteps, g.ring_rows_pad, img);
+        TRY(dev_upload(pl, &pl->ring_aimg, img));
+        TRY(dev_alloc(pl, &pl->ring_R, (size_t)g.NP * g.ring_rows_pad));
+    }
     auto to_df = [](const std::vector<double> &v) {  // double-float (hi, lo) pairs
         std::vector<float2> o(v.size());
         for (size_t i = 0; i < v.size(); ++i) {
