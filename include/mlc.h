@@ -200,10 +200,17 @@ mlc_status mlc_solve_noalloc(mlc_plan_t plan, const void *f, void *phi, void *st
 mlc_status mlc_solve_host(mlc_plan_t plan, const void *f_host, void *phi_host, void *stream);
 
 /*
- * Solve `count` independent problems in one pass: the per-patch work of all
- * problems runs in shared launches (local convolutions, moments, boundary
- * and Dirichlet steps), each coarse solve on its own plan.  plans[k], f[k],
- * phi[k] as in mlc_solve; plans must be distinct and of the same tier.
+ * Solve `count` independent problems in one call (no counterpart in the
+ * paper: each problem is the solve of Sec. 4).  Problems are grouped by patch
+ * geometry and tier; the per-patch work of all problems of a group runs in
+ * shared launches (moments, local convolutions, residuals, Dirichlet steps),
+ * the groups concurrently, and each problem's coarse charge, coarse solve and
+ * boundary values on parallel branches.  The launch sequence is captured as a
+ * CUDA graph per (plans, f, phi) set, tuned on the first call (branches, slab
+ * launch shape, patches per convolution launch group) and replayed on later
+ * calls.  plans[k], f[k], phi[k] as in mlc_solve; plans must be distinct
+ * (INVALID_ARG otherwise) and on the current device.  The first call with a
+ * set allocates its item tables and convolution scratch.
  */
 mlc_status mlc_batch_solve(int count, const mlc_plan_t *plans, const void *const *f,
                            void *const *phi, void *stream);
@@ -257,6 +264,10 @@ mlc_status mlc_debug_timing(mlc_plan_t plan, float *ms_out, int count);
  * + 1 if the local-convolution slab kernel runs persistently; 0 if this set
  * has not been solved yet. */
 int mlc_debug_batch_choice(int count, const mlc_plan_t *plans, const void *const *f, void *const *phi);
+/* Patches per local-convolution launch group (the number of patches whose
+ * pencils one set of convolution launches transforms) that the autotuner
+ * chose for these arrays, from {512, 1024, 2048}; 0 if not solved yet. */
+int mlc_debug_batch_chunk(int count, const mlc_plan_t *plans, const void *const *f, void *const *phi);
 mlc_status mlc_debug_export(mlc_plan_t plan, int stage, void *host, size_t bytes);
 /* Geometry of the plan: out[0..15] = N, n, s, b, g_alpha, g_beta, P, npoly,
  * fh_lo, fh_hi, phih_lo, phih_hi, M (patch FFT), Mc (coarse FFT), L (DGF

@@ -107,7 +107,7 @@ void BatchStreams::release() {
 
 cudaError_t batch_enqueue(const std::vector<mlc_plan_t> &plans, const BatchLayout &L, const int2 *d_items,
                           const PlanPtrs *d_recs, BatchStreams &S, int branches, int persist,
-                          cudaStream_t st) {
+                          cudaStream_t st, int chunk) {
     const int G = (int)L.groups.size();
     cudaError_t err = S.ensure(G, branches);
     if (err != cudaSuccess) return err;
@@ -128,6 +128,7 @@ cudaError_t batch_enqueue(const std::vector<mlc_plan_t> &plans, const BatchLayou
         const BatchLayout::Group &gr = L.groups[g];
         Items it{d_items + gr.item0, d_recs, gr.nitems};
         it.persist = persist;
+        it.chunk = chunk;
         it.a1 = gr.a1;
         it.a4 = gr.a4;
         TRYE(cudaStreamWaitEvent(S.aux[g], ev_start, 0));
@@ -184,13 +185,15 @@ struct BatchCtx {
     cudaGraphExec_t exec = nullptr;
     int branches = 0;
     int persist = 0;
+    int chunk = 0;                // patches per local-convolution launch group (tuned)
     float tuned_ms = 0.f;
 };
 
 std::mutex g_mu;
 std::map<std::vector<uintptr_t>, BatchCtx *> g_cache;
+constexpr int kBatchMaxChunk = 2048;  // largest local-convolution launch group the tuner tries
 
-cudaError_t capture(BatchCtx &c, int branches, int persist, cudaGraphExec_t *out) {
+cudaError_t capture(BatchCtx &c, int branches, int persist, int chunk, cudaGraphExec_t *out) {
     cudaStream_t cap;
     cudaError_t err = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
     if (err != cudaSuccess) return err;
@@ -199,7 +202,7 @@ cudaError_t capture(BatchCtx &c, int branches, int persist, cudaGraphExec_t *out
     if (err == cudaSuccess) err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     const bool began = err == cudaSuccess;
     g_capturing = true;
-    if (err == cudaSuccess) err = batch_enqueue(c.plans, c.L, c.d_items, c.d_plans, S, branches, persist, cap);
+    if (err == cudaSuccess) err = batch_enqueue(c.plans, c.L, c.d_items, c.d_plans, S, branches, persist, cap, chunk);
     g_capturing = false;
     cudaGraph_t graph = nullptr;
     if (began) {
@@ -214,23 +217,29 @@ cudaError_t capture(BatchCtx &c, int branches, int persist, cudaGraphExec_t *out
 }
 
 // Time a few replays of each candidate (parallel branches for the coarse
-// steps x persistent or one-CTA-per-slab local convolutions) and keep the
-// fastest.
+// steps x persistent or one-CTA-per-slab slab launches x patches per
+// local-convolution launch group, the batch of pencils one launch
+// transforms) and keep the fastest.
 cudaError_t build_and_tune(BatchCtx &c, cudaStream_t st) {
     const int nplans = (int)c.plans.size();
-    std::vector<std::pair<int, int>> cand;
+    int maxitems = 0;
+    for (auto &gr : c.L.groups) maxitems = std::max(maxitems, gr.nitems);
+    struct Cand { int b, ps, chunk; };
+    std::vector<Cand> cand;
     for (int b : {1, 4, 16})
         if (b == 1 || b <= nplans)
-            for (int ps : {0, 1}) cand.push_back({b, ps});
+            for (int ps : {0, 1})
+                for (int ch : {512, 1024, kBatchMaxChunk})
+                    if (ch == 1024 || ch / 2 < maxitems) cand.push_back({b, ps, ch});
     cudaEvent_t e0, e1;
     cudaError_t err = cudaEventCreate(&e0);
     if (err != cudaSuccess) return err;
     err = cudaEventCreate(&e1);
     if (err != cudaSuccess) return err;
     for (auto bp : cand) {
-        const int b = bp.first;
+        const int b = bp.b;
         cudaGraphExec_t ex = nullptr;
-        err = capture(c, b, bp.second, &ex);
+        err = capture(c, b, bp.ps, bp.chunk, &ex);
         if (err != cudaSuccess) break;
         float best = 1e30f;
         for (int r = 0; r < 4 && err == cudaSuccess; ++r) {
@@ -250,7 +259,8 @@ cudaError_t build_and_tune(BatchCtx &c, cudaStream_t st) {
             if (c.exec) cudaGraphExecDestroy(c.exec);
             c.exec = ex;
             c.branches = b;
-            c.persist = bp.second;
+            c.persist = bp.ps;
+            c.chunk = bp.chunk;
             c.tuned_ms = best;
         } else {
             cudaGraphExecDestroy(ex);
@@ -296,7 +306,7 @@ extern "C" mlc_status mlc_batch_solve(int count, const mlc_plan_t *plans, const 
         for (auto &gr : c->L.groups) {
             if (e != cudaSuccess) break;
             const Geom &G = gr.rep->g;
-            const long nit = std::min<long>(G.chunk, gr.nitems);
+            const long nit = std::min<long>(kBatchMaxChunk, gr.nitems);  // room for every candidate group size
             void *p = nullptr;
             e = cudaMalloc(&p, conv_scratch_bytes(G, nit));
             if (e != cudaSuccess) break;
@@ -356,4 +366,19 @@ extern "C" int mlc_debug_batch_choice(int count, const mlc_plan_t *plans, const 
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_cache.find(key);
     return it == g_cache.end() ? 0 : it->second->branches * 2 + it->second->persist;
+}
+
+// Patches per local-convolution launch group the autotuner chose for this
+// batch (0 if the batch is unknown).
+extern "C" int mlc_debug_batch_chunk(int count, const mlc_plan_t *plans, const void *const *f,
+                                     void *const *phi) {
+    std::vector<uintptr_t> key;
+    for (int k = 0; k < count; ++k) {
+        key.push_back((uintptr_t)plans[k]);
+        key.push_back((uintptr_t)f[k]);
+        key.push_back((uintptr_t)phi[k]);
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cache.find(key);
+    return it == g_cache.end() ? 0 : it->second->chunk;
 }

@@ -2654,7 +2654,7 @@ cudaError_t launch_patch_conv_group(const mlc_plan_s *pl, const Items &it, cudaS
 // Local convolutions of all items, in launch groups of g.chunk items that
 // reuse one scratch (stream order keeps the groups apart).
 cudaError_t launch_patch_conv(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
-    const int chunk = pl->g.chunk;
+    const int chunk = it.chunk > 0 ? it.chunk : pl->g.chunk;
     for (int c0 = 0; c0 < it.nitems; c0 += chunk) {
         Items ic = it;
         ic.nitems = it.nitems - c0 < chunk ? it.nitems - c0 : chunk;

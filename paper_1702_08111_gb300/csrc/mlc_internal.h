@@ -102,6 +102,7 @@ struct Items {
     int nitems;
     int persist = 0;      // 1: launch the slab kernel persistently (one wave of resident CTAs)
     int first = 0;        // patch of item 0 when there is no item table
+    int chunk = 0;        // items per local-convolution launch group (0: the plan's conv_chunk)
     void *a1 = nullptr;   // scratch: x-transformed charges, scr_a1 bytes per item
     void *a4 = nullptr;   // scratch: slab outputs, scr_a4 bytes per item
 };
@@ -272,5 +273,5 @@ void batch_layout(int count, const mlc_plan_t *plans, const void *const *f, void
 // L.items / L.recs.  plans: the problems in call order.
 cudaError_t batch_enqueue(const std::vector<mlc_plan_t> &plans, const BatchLayout &L, const int2 *d_items,
                           const PlanPtrs *d_recs, BatchStreams &S, int branches, int persist,
-                          cudaStream_t st);
+                          cudaStream_t st, int chunk = 0);
 }  // namespace mlc

@@ -28,7 +28,7 @@ EXPORTED = [
     "mlc_server_destroy", "mlc_server_enqueue", "mlc_server_wait", "mlc_status_string",
     "mlc_debug_set_timing", "mlc_debug_timing", "mlc_solve_noalloc", "mlc_plan_status",
     "mlc_debug_batch_choice", "mlc_plan_scratch_bytes", "mlc_plan_set_scratch", "mlc_debug_set_fault",
-    "mlc_plan_set_dgf",
+    "mlc_plan_set_dgf", "mlc_debug_batch_chunk",
 ]
 LAUNCH_NAMES = ["moments", "conv_fwd_x", "conv_slab", "conv_inv_x", "resid", "assemble",
                 "coarse_fwd_x", "coarse_fwd_y", "coarse_z_kernel", "coarse_inv_y", "coarse_inv_x",
@@ -83,6 +83,7 @@ def load_library(path: str = LIB_PATH):
     lib.mlc_plan_status.argtypes = [vp]
     lib.mlc_debug_batch_choice.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]
     lib.mlc_batch_solve.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    lib.mlc_debug_batch_chunk.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]
     lib.mlc_debug_stage_bytes.argtypes = [vp, i, ctypes.POINTER(ctypes.c_size_t)]
     lib.mlc_debug_export.argtypes = [vp, i, vp, ctypes.c_size_t]
     lib.mlc_plan_info.argtypes = [vp, ip]
@@ -316,7 +317,8 @@ def batch_choice(plans, fs, phis) -> dict:
     F = (ctypes.c_void_p * k)(*[f.data_ptr() for f in fs])
     P = (ctypes.c_void_p * k)(*[p.data_ptr() for p in phis])
     v = load_library().mlc_debug_batch_choice(k, H, F, P)
-    return {"branches": v // 2, "persistent_slab": bool(v & 1)}
+    ch = load_library().mlc_debug_batch_chunk(k, H, F, P)
+    return {"branches": v // 2, "persistent_slab": bool(v & 1), "patches_per_conv_launch": ch}
 
 
 def batch_solve(plans, fs, phis, stream=None):
