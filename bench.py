@@ -301,7 +301,9 @@ def roofline_for(w, plan, per_launch, tier, traffic=None):
         inst = ((nin + M) * fft64_schedule_inst(tier if tier in ("fp64", "df") else "split", True, nin)
                 + (M + nz) * fft64_schedule_inst(tier if tier in ("fp64", "df") else "split", False)
                 + M * M * prod)
-        units, pipe_rate = NP * Mh, (FP64_INST_PER_S if tier == "fp64" else FP32_LANE_INST_PER_S)
+        # one launch per group of CONV_CHUNK patches (the library's default group size)
+        nlaunch = -(-NP // CONV_CHUNK)
+        units, pipe_rate = min(NP, CONV_CHUNK) * Mh, (FP64_INST_PER_S if tier == "fp64" else FP32_LANE_INST_PER_S)
         pipe = "FP64 pipe" if tier == "fp64" else "FP32 pipe"
         sched = {"fp64": "FP64 radix-8x8", "df": "double-float radix-8x8"}.get(tier, "FP32 radix-2 register")
         unit_name = "(patch, kx) slab"
@@ -309,6 +311,7 @@ def roofline_for(w, plan, per_launch, tier, traffic=None):
         nominal, inst = dirichlet_counts(w.n, w.Q)
         if not fine64:
             inst = inst * DF_ADD_INST  # double-float: about 8 FP32 instructions per operation
+        nlaunch = 1
         units, pipe_rate = NP, (FP64_INST_PER_S if fine64 else FP32_LANE_INST_PER_S)
         pipe = "FP64 pipe" if fine64 else "FP32 pipe"
         sched = "FP64 split-radix DST-I" if fine64 else "double-float split-radix DST-I"
@@ -316,19 +319,21 @@ def roofline_for(w, plan, per_launch, tier, traffic=None):
     else:
         return None
     flops = units * nominal
-    achieved = flops / (per_launch[dom] * 1e-3) / 1e12
+    launch_ms = per_launch[dom] / nlaunch  # mean duration of one launch
+    achieved = flops / (launch_ms * 1e-3) / 1e12
     peak = pipe_rate * nominal / inst / 1e12
     basis = ("%s %.4g T inst/s (%s) x %.4f algorithmic FLOP per instruction of the %s schedule"
              % (pipe, pipe_rate / 1e12, "152 SMs x 128 lanes x 2.07 GHz" if pipe == "FP32 pipe"
                 else "nominal 1.25 TFLOP/s FP64, FMA = 2", nominal / inst, sched))
     return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak, 4),
             "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-            "launch_ms": round(per_launch[dom], 4), "flops_per_launch": flops,
+            "launch_ms": round(launch_ms, 4), "launches_per_step": nlaunch, "flops_per_launch": flops,
             "units_per_launch": units, "unit_of_work": unit_name, "flops_per_unit": nominal,
             "inst_per_unit": inst, "peak_basis": basis}
 
 
 TIER_IDS = {"fp64": 0, "split": 1, "df": 2, "split_df": 3}
+CONV_CHUNK = 1024  # patches per local-convolution launch group (the plans' default conv_chunk)
 F32_TIERS = ("split", "split_df")
 
 
