@@ -606,11 +606,13 @@ def run_serving(args, nreq=2000, nsat=400):
             time.sleep(min(0.0005, max(0.0, next_t - time.perf_counter())))
         tickets.append(submit(k))
     lats, qs, bad = [], [], 0
-    for t in tickets:
+    by_tier = {}
+    for k, t in enumerate(tickets):
         st, lat, q = srv.wait(t)
         bad += st != 0
         lats.append(lat)
         qs.append(q)
+        by_tier.setdefault(reqs[k][1], []).append(lat)
     total_s = time.perf_counter() - t0
     srv.close()
     pts = float(sum(w.N ** 3 for w, _ in reqs))
@@ -619,9 +621,11 @@ def run_serving(args, nreq=2000, nsat=400):
             "saturated_req_per_s": round(nsat / sat_s, 2),
             "p50_ms": round(float(np.percentile(lats, 50)), 3), "p99_ms": round(float(np.percentile(lats, 99)), 3),
             "queue_p50_ms": round(float(np.percentile(qs, 50)), 3),
+            "by_tier": {t: {"requests": len(v), "p50_ms": round(float(np.percentile(v, 50)), 3),
+                            "p99_ms": round(float(np.percentile(v, 99)), 3)} for t, v in by_tier.items()},
             "Mpoints_per_s_at_rate": round(pts / total_s / 1e6, 2),
             "Mpoints_per_s_saturated": round(pts_sat / sat_s / 1e6, 2),
-            "distinct_plans": len(seen), "hbm_budget_gb": 120, "max_batch": 8, "lanes": 2}
+            "distinct_plans": len(seen), "hbm_budget_gb": 120, "max_batch": 8, "lanes": 3}
 
 
 def run_noalloc(args, flush, stream):

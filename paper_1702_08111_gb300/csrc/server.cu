@@ -6,14 +6,22 @@
 // max_batch requests), and the batch runs as one batched launch sequence
 // (batch.cu): the per-patch steps of all its requests share launches, grouped
 // by patch geometry and tier, and the per-request coarse steps run on
-// parallel branches.  Two batches can be in flight at once, each on its own
-// lane (stream, launch streams, item tables and local-convolution scratch),
-// so requests that arrive while one batch runs are admitted into the next as
-// soon as a lane is free -- continuous batching, not a queue of whole solves.
+// parallel branches.  Up to kLanes batches are in flight at once, each on its
+// own lane (stream, launch streams, item tables and local-convolution
+// scratch), so requests that arrive while batches run are admitted into the
+// next one as soon as a lane is free -- continuous batching, not a queue of
+// whole solves.
 // Plans (DGF tables, kernel spectra, basis tables, per-patch arrays) stay
 // resident in a cache keyed by the problem parameters and are reused; the
 // local-convolution scratch belongs to the lanes, not to the plans.  Idle
 // plans are evicted only when the memory budget needs the room.
+//
+// Batches are formed by estimated cost (points x a per-tier weight from the
+// measured tier rates): the requests of a batch complete together, so a
+// request whose estimate is above kHeavyMs runs as a batch of its own, light
+// requests are batched up to kBatchMs of estimated work, and the last lane
+// takes light batches only, so light requests never wait behind two heavy
+// solves.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -31,7 +39,19 @@ using namespace mlc;
 namespace {
 
 using Clock = std::chrono::steady_clock;
-constexpr int kLanes = 2;
+constexpr int kLanes = 3;           // lanes 0 .. kLanes-2 take any batch, the last light batches only
+constexpr double kHeavyMs = 20.0;   // estimated solve time above which a request runs alone
+constexpr double kBatchMs = 10.0;   // estimated work of a light batch
+
+// Estimated solve time (ms): N^3 points at the measured rate of each tier at
+// 256^3 on one GB300 (split 2700, split-DF 3600, double-float 1100, FP64 270
+// Mpoints/s).
+double estimate_ms(const mlc_params &p) {
+    const double pts = (double)p.N * p.N * p.N;
+    const int t = p.tier < 0 ? MLC_TIER_FP64 : p.tier;
+    const double rate = t == MLC_TIER_SPLIT ? 2700.0 : (t == MLC_TIER_SPLIT_DF ? 3600.0 : (t == MLC_TIER_DF ? 1100.0 : 270.0));
+    return pts / (rate * 1e3);
+}
 
 struct Key {
     int v[13];
@@ -50,7 +70,8 @@ struct Pending {
     uint64_t ticket;
     mlc_request req;
     Clock::time_point t_enq;
-    size_t est;
+    size_t est;      // device bytes of its plan (bound)
+    double est_ms;   // estimated solve time
 };
 
 // Upper bound of the device bytes a plan with these parameters holds (its
@@ -72,6 +93,11 @@ size_t estimate_bytes(const mlc_params &p) {
     bytes += 3L * nf * Mc * (Mc / 2 + 1) * 16 + 2L * nf * nf * nf * 8;
     bytes += 3L * (np + 1) * (N + 1) * (N + 1) * 8;           // boundary planes
     bytes += (Mh * Mh * Mh + (Mc / 2 + 1) * (Mc / 2 + 1) * (Mc / 2 + 1)) * 12;
+    if (rb == 4) {  // split tiers: ring terms of one face-plane axis for the ring GEMM
+        const long gb = p.g_beta >= 0 ? p.g_beta : (p.Q == 4 ? n : (9 * n + 7) / 8);
+        const long wbx = n + 2 * gb + 1, npb = (n + 2 * gb) / n + 2;
+        bytes += NP * ((npb * wbx * wbx + 127) / 128 * 128) * 4;
+    }
     bytes += 32L << 20;                                        // basis tables, index maps, slack
     return (size_t)bytes;
 }
@@ -116,7 +142,7 @@ struct mlc_server_s {
     std::thread worker;
 
     void run();
-    bool form_and_launch(Lane &ln, std::unique_lock<std::mutex> &lk);
+    bool form_and_launch(Lane &ln, bool heavy_ok, std::unique_lock<std::mutex> &lk);
     void retire(Lane &ln);
     cudaError_t launch(Lane &ln);
 };
@@ -126,14 +152,18 @@ struct mlc_server_s {
 // idle cache; a key with no resident plan, or with room in the budget for a
 // second one, gets a new plan (idle plans of other keys are evicted first if
 // the budget needs it).
-bool mlc_server_s::form_and_launch(Lane &ln, std::unique_lock<std::mutex> &lk) {
+bool mlc_server_s::form_and_launch(Lane &ln, bool heavy_ok, std::unique_lock<std::mutex> &lk) {
     ln.reqs.clear();
     ln.plans.clear();
     ln.keys.clear();
     ln.bytes.clear();
     std::vector<size_t> taken;
+    double cost = 0.0;
     for (size_t i = 0; i < queue.size() && (int)ln.reqs.size() < max_batch; ++i) {
         Pending &pd = queue[i];
+        const bool heavy = pd.est_ms > kHeavyMs;
+        if (heavy && (!heavy_ok || !ln.reqs.empty())) continue;   // heavy: alone, on a heavy lane
+        if (!ln.reqs.empty() && cost + pd.est_ms > kBatchMs) continue;
         const Key k = key_of(pd.req.params);
         mlc_plan_t plan = nullptr;
         size_t bytes = 0;
@@ -176,6 +206,8 @@ bool mlc_server_s::form_and_launch(Lane &ln, std::unique_lock<std::mutex> &lk) {
         ln.keys.push_back(k);
         ln.bytes.push_back(bytes);
         taken.push_back(i);
+        cost += pd.est_ms;
+        if (heavy) break;
     }
     for (size_t j = taken.size(); j-- > 0;) queue.erase(queue.begin() + (long)taken[j]);
     if (ln.reqs.empty()) return false;
@@ -281,8 +313,8 @@ void mlc_server_s::run() {
             }
         if (retired) cv_done.notify_all();
         // fill free lanes with the next batches
-        for (Lane &ln : lanes)
-            if (!ln.busy && !queue.empty()) form_and_launch(ln, lk);
+        for (int l = 0; l < kLanes; ++l)
+            if (!lanes[l].busy && !queue.empty()) form_and_launch(lanes[l], l < kLanes - 1, lk);
         any_busy = false;
         for (Lane &ln : lanes) any_busy |= ln.busy;
         if (!any_busy && queue.empty()) {
@@ -352,7 +384,7 @@ mlc_status mlc_server_enqueue(mlc_server_t s, const mlc_request *req, uint64_t *
     if (est > s->budget) return MLC_ERR_ADMISSION;
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) return MLC_ERR_INVALID_ARG;
-    Pending pd{s->next_ticket++, *req, Clock::now(), est};
+    Pending pd{s->next_ticket++, *req, Clock::now(), est, estimate_ms(p)};
     *ticket = pd.ticket;
     s->queue.push_back(pd);
     s->cv_work.notify_all();
