@@ -372,7 +372,7 @@ struct SlabArgs {
     int nin, nout, out_off;
     Items it;  // per item: in = a1, out = a4, khat of its plan
     int nz;    // output z rows: zrow[j] in [0, nout), the rows the inverse-x step reads
-    int zrow[64];
+    int zrow[128];
     int blk;   // complex entries per (patch, z row) output block (16-byte multiple)
 };
 
@@ -1036,7 +1036,7 @@ struct InvXPArgs {
     const void *tw;   // M/2 twiddles exp(-2 pi i j / M)
     int n, s, W, ga, npa, pl0, wa, nc;
     int nz;           // z rows with outputs; zrow[j] = their index zo in [0, W)
-    int zrow[64];
+    int zrow[128];
     int maxfft;       // most transformed rows of any z row (sizes the line buffer)
     int blk;          // complex entries per (patch, z row) input block (16-byte multiple)
     int wait_tries;   // limit of the bounded wait for the block's bulk copy
@@ -1054,9 +1054,9 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
     constexpr int M = 1 << LOG2M, MH = M / 2 + 1;
     constexpr int LP = LOG2M == 6 ? Pitch64<R>::P : M + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int rows[64];
+    __shared__ int rows[128];
     __shared__ int nfft_s;
-    __shared__ unsigned wmask[2];
+    __shared__ unsigned wmask[4];
     const int W = a.W, n = a.n, s = a.s, ga = a.ga, pl0 = a.pl0, wa = a.wa, nc = a.nc;
     C *tw = (C *)smem_raw;        // M twiddles
     C *raw = tw + M;              // MH x W (block of a.blk entries, 16-byte aligned)
@@ -1091,8 +1091,8 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
         return;
     }
     const bool zP = on_plane(z, n, ga, pl0), zA = in_alpha(z, n, ga), zC = (z & 3) == 0;
-    // rows of this z that need a full transform, compacted with warp ballots (W <= 64)
-    if (threadIdx.x < 64) {
+    // rows of this z that need a full transform, compacted with warp ballots (W <= 128)
+    if (threadIdx.x < 128) {
         const int yi = threadIdx.x, y = yi - s;
         const bool yA = in_alpha(y, n, ga), yP = on_plane(y, n, ga, pl0), yC = (y & 3) == 0;
         const bool need = yi < W && ((zP && yA) || (yP && zA) || (zC && yC));
@@ -1100,16 +1100,15 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
         if ((threadIdx.x & 31) == 0) wmask[threadIdx.x >> 5] = m;
     }
     __syncthreads();
-    if (threadIdx.x < 64) {
-        const int yi = threadIdx.x;
-        const unsigned m0 = wmask[0], m1 = wmask[1];
-        const unsigned mine = yi < 32 ? m0 : m1;
-        const int lane = yi & 31;
+    if (threadIdx.x < 128) {
+        const int yi = threadIdx.x, w = yi >> 5, lane = yi & 31;
+        const unsigned mine = wmask[w];
         if ((mine >> lane) & 1u) {
-            const int before = (yi < 32 ? 0 : __popc(m0)) + __popc(mine & ((1u << lane) - 1u));
+            int before = __popc(mine & ((1u << lane) - 1u));
+            for (int q = 0; q < w; ++q) before += __popc(wmask[q]);
             rows[before] = yi;
         }
-        if (yi == 0) nfft_s = __popc(m0) + __popc(m1);
+        if (yi == 0) nfft_s = __popc(wmask[0]) + __popc(wmask[1]) + __popc(wmask[2]) + __popc(wmask[3]);
     }
     __syncthreads();
     const int nfft = nfft_s;
@@ -1344,34 +1343,38 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 8 : 4) k_inv_x64(InvXPAr
 // (Boole weight times orthonormal Legendre polynomial, one axis),
 //   c_p = R^{-3/2} sum_m0 a_p0(m0) sum_m1 a_p1(m1) sum_m2 a_p2(m2) f(m0,m1,m2),
 // evaluated as three 1D contractions.  RM: arithmetic precision (FP64 or FP32
-// for the split tier, whose last stage and output are FP64).
+// for the split tier, whose last stage and output are FP64).  The charge is
+// staged ns planes m0 at a time (all of them for small patches).
 template <typename TF, typename RM>
-__global__ void __launch_bounds__(256) k_moments(Items it, int n, int P, int npoly, int npad) {
+__global__ void __launch_bounds__(256) k_moments(Items it, int n, int P, int npoly, int npad, int ns) {
     extern __shared__ double msm[];
     int pch;
     const PlanPtrs &PP = item_plan(it, blockIdx.x, pch);
     const int nb = n + 1, N = PP.N, np = PP.np;
     const int i2 = pch % np, i1 = (pch / np) % np, i0 = pch / (np * np);
-    RM *F = (RM *)msm;                 // nb^3 charge of the closed patch
-    RM *T1 = F + nb * nb * nb;         // [p2][m0][m1]
+    RM *F = (RM *)msm;                 // ns planes m0 of the closed patch's charge
+    RM *T1 = F + ns * nb * nb;         // [p2][m0][m1]
     RM *T2 = T1 + P * nb * nb;         // [p1][p2][m0]
     RM *A = T2 + P * P * nb;           // [k][m] 1D weights
     const double *a1d = (const double *)PP.momw;
     for (int e = threadIdx.x; e < P * nb; e += blockDim.x) A[e] = (RM)a1d[e];
     const TF *f = (const TF *)PP.f;
-    for (int e = threadIdx.x; e < nb * nb * nb; e += blockDim.x) {
-        const int m2 = e % nb, m1 = (e / nb) % nb, m0 = e / (nb * nb);
-        const int z = i0 * n + m0, y = i1 * n + m1, x = i2 * n + m2;
-        F[e] = (z < N && y < N && x < N) ? (RM)f[((long)z * N + y) * N + x] : (RM)0;
+    for (int s0 = 0; s0 < nb; s0 += ns) {
+        const int sn = min(ns, nb - s0);
+        for (int e = threadIdx.x; e < sn * nb * nb; e += blockDim.x) {
+            const int m2 = e % nb, m1 = (e / nb) % nb, m0 = s0 + e / (nb * nb);
+            const int z = i0 * n + m0, y = i1 * n + m1, x = i2 * n + m2;
+            F[e] = (z < N && y < N && x < N) ? (RM)f[((long)z * N + y) * N + x] : (RM)0;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < P * sn * nb; e += blockDim.x) {
+            const int p2 = e / (sn * nb), r = e % (sn * nb);  // r = (m0 - s0) nb + m1
+            RM acc = 0;
+            for (int m2 = 0; m2 < nb; ++m2) acc = fma(A[p2 * nb + m2], F[r * nb + m2], acc);
+            T1[(p2 * nb + s0) * nb + r] = acc;
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < P * nb * nb; e += blockDim.x) {
-        const int p2 = e / (nb * nb), r = e % (nb * nb);
-        RM acc = 0;
-        for (int m2 = 0; m2 < nb; ++m2) acc = fma(A[p2 * nb + m2], F[r * nb + m2], acc);
-        T1[e] = acc;
-    }
-    __syncthreads();
     for (int e = threadIdx.x; e < P * P * nb; e += blockDim.x) {
         const int p1 = e / (P * nb), p2 = (e / nb) % P, m0 = e % nb;
         if (p1 + p2 >= P) continue;
@@ -1917,13 +1920,16 @@ __device__ __forceinline__ void dst15_fast(T (&x)[15], const T (&sv)[9]) {
 // all three axes, then phi = u + (h^2/12) f.  T: the arithmetic between the
 // loads and the final FP64 store, FP64 (the FP64 pipe) or double-float (the
 // FP32 pipe; GB300 issues FP64 on ~1/67 of the FP32 lanes).  TF: the charge.
+// Patches up to n = 24 keep their m^3 work array in shared memory; larger
+// ones (BIG) keep it in the plan's global Dirichlet workspace (the same code
+// on global memory; the patch's 238 KB stay in L2 between the passes).
 template <typename TF, int NN, typename T>
-__global__ void __launch_bounds__(256, std::is_same<T, double>::value ? 3 : 4) k_dirichlet(DirArgs a) {
+__global__ void __launch_bounds__(256, NN > 16 ? 1 : (std::is_same<T, double>::value ? 3 : 4))
+    k_dirichlet(DirArgs a) {
     extern __shared__ double sm[];
     constexpr int n = NN, nb = n + 1, m = n - 1, h = n / 2;
+    constexpr bool BIG = NN > 24;
     T *U = (T *)sm;                    // boundary values on the 6 faces, nb^2 each (face 2 axis + side)
-    T *X = U + 6 * nb * nb;            // m^3 work
-    T *Sh = X + m * m * m;             // (n-1) x n/2 half sine table
     // boundary value at node (c0, c1, c2) of the closed patch, one coordinate 0 or n
     auto Uat = [&](int c0, int c1, int c2) -> T {
         if (c0 == 0 || c0 == n) return U[((c0 ? 1 : 0) * nb + c1) * nb + c2];
@@ -1932,6 +1938,8 @@ __global__ void __launch_bounds__(256, std::is_same<T, double>::value ? 3 : 4) k
     };
     int p;
     const PlanPtrs &PP = item_plan(a.it, blockIdx.x, p);
+    T *X = BIG ? (T *)PP.dscr + (long)p * m * m * m : U + 6 * nb * nb;  // m^3 work
+    T *Sh = BIG ? U + 6 * nb * nb : X + m * m * m;                       // (n-1) x n/2 half sine table
     const int np = PP.np, N = PP.N;
     const int i2 = p % np, i1 = (p / np) % np, i0 = p / (np * np);
     const int o0 = i0 * n, o1 = i1 * n, o2 = i2 * n;
@@ -2496,7 +2504,7 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
             else k_fwd_x<LOG2M, double, true, R, true><<<grid, 256, sm, st>>>(a);
         }
     }
-    int nz = 0, zrow[64];
+    int nz = 0, zrow[128];
     for (int zi = 0; zi < W; ++zi) {
         const int z = zi - g.s;
         if ((z >= -g.ga && z <= g.n + g.ga) || (z % 4 == 0)) zrow[nz++] = zi;
@@ -2600,6 +2608,7 @@ void configure_kernels() {
     set_patch_attrs<6, float>();
     set_patch_attrs<5, double>();
     set_patch_attrs<6, double>();
+    set_patch_attrs<7, float>();
     set_cfft_attrs<dfl>();
     set_cfft_attrs<double>();
     configure_ring_gemm();
@@ -2613,6 +2622,8 @@ void configure_kernels() {
     MLC_DIR_ATTR(8)
     MLC_DIR_ATTR(12)
     MLC_DIR_ATTR(16)
+    MLC_DIR_ATTR(24)
+    MLC_DIR_ATTR(32)
 #undef MLC_DIR_ATTR
     cudaFuncSetAttribute(k_resid<dfl, dfl>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_resid<float, dfl>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -2625,11 +2636,13 @@ void configure_kernels() {
 cudaError_t launch_moments(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
     const Geom &g = pl->g;
     const int nb = g.n + 1;
-    const size_t words = (size_t)nb * nb * nb + (size_t)g.P * nb * nb + (size_t)g.P * g.P * nb + (size_t)g.P * nb;
+    // charge planes staged at once: the whole patch while it takes <= 48 KB
+    const int ns = std::max(1, std::min(nb, (int)((48u << 10) / ((g.f32in ? 4 : 8) * (size_t)nb * nb))));
+    const size_t words = (size_t)ns * nb * nb + (size_t)g.P * nb * nb + (size_t)g.P * g.P * nb + (size_t)g.P * nb;
     if (g.f32in)
-        k_moments<float, float><<<it.nitems, 256, words * sizeof(float), st>>>(it, g.n, g.P, g.npoly, g.npad);
+        k_moments<float, float><<<it.nitems, 256, words * sizeof(float), st>>>(it, g.n, g.P, g.npoly, g.npad, ns);
     else
-        k_moments<double, double><<<it.nitems, 256, words * sizeof(double), st>>>(it, g.n, g.P, g.npoly, g.npad);
+        k_moments<double, double><<<it.nitems, 256, words * sizeof(double), st>>>(it, g.n, g.P, g.npoly, g.npad, ns);
     return cudaGetLastError();
 }
 
@@ -2641,6 +2654,7 @@ cudaError_t launch_patch_conv_group(const mlc_plan_s *pl, const Items &it, cudaS
     if (g.conv == CONV_F32) {  // split tiers: FP32 (tables tw_f, khat_f)
         if (g.log2M == 5) return run_patch_conv_t<5, float>(pl, it, f32, pl->tw_f, st);
         if (g.log2M == 6) return run_patch_conv_t<6, float>(pl, it, f32, pl->tw_f, st);
+        if (g.log2M == 7) return run_patch_conv_t<7, float>(pl, it, f32, pl->tw_f, st);
     } else if (g.conv == CONV_DF) {  // double-float (tables tw_df, khat_df)
         if (g.log2M == 5) return run_patch_conv_t<5, dfl>(pl, it, f32, pl->tw_df, st);
         if (g.log2M == 6) return run_patch_conv_t<6, dfl>(pl, it, f32, pl->tw_df, st);
@@ -2810,6 +2824,8 @@ cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st) {
             MLC_BND(8)
             MLC_BND(12)
             MLC_BND(16)
+            MLC_BND(24)
+            MLC_BND(32)
             default: return cudaErrorInvalidValue;
         }
 #undef MLC_BND
@@ -2824,7 +2840,7 @@ cudaError_t launch_dirichlet(const mlc_plan_s *pl, const Items &it, cudaStream_t
     stencil_b(g.Q, a.b);
     a.sinm = pl->sinm;
     const int nb = g.n + 1, m = g.n - 1;
-    const size_t sm = 8 * (6 * (size_t)nb * nb + (size_t)m * m * m + (size_t)m * (g.n / 2));
+    const size_t sm = 8 * (6 * (size_t)nb * nb + (g.n > 24 ? 0 : (size_t)m * m * m) + (size_t)m * (g.n / 2));
 #define MLC_DIR(NN)                                                                               \
     case NN:                                                                                      \
         if (g.fine == FINE_F64) {                                                                 \
@@ -2840,6 +2856,8 @@ cudaError_t launch_dirichlet(const mlc_plan_s *pl, const Items &it, cudaStream_t
         MLC_DIR(8)
         MLC_DIR(12)
         MLC_DIR(16)
+        MLC_DIR(24)
+        MLC_DIR(32)
         default: return cudaErrorInvalidValue;
     }
 #undef MLC_DIR
@@ -2870,6 +2888,8 @@ cudaError_t launch_index_export(const mlc_plan_s *pl, int which, int *cnt, const
         MLC_IDX(8)
         MLC_IDX(12)
         MLC_IDX(16)
+        MLC_IDX(24)
+        MLC_IDX(32)
         default: return cudaErrorInvalidValue;
     }
 #undef MLC_IDX

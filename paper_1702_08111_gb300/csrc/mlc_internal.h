@@ -90,6 +90,7 @@ struct PlanPtrs {
     const void *lam;      // Dirichlet inverse eigenvalues (2/n)^3 h^2 / lambda (FP64 or double-float)
     int N, np;
     double c2h2, inv_h2;  // h^2 / 12, 1 / h^2
+    void *dscr;           // Dirichlet workspace (n > 24): [patch][(n-1)^3] in the fine precision
     int *err;             // the plan's error word
 };
 
@@ -155,6 +156,7 @@ struct mlc_plan_s {
     double *tpl;             // 3 (np+1) no (N+1): I^H(phi^H) summed along v per plane and coarse row
     float *ring_aimg;        // split tiers: ring table as the tensor-core GEMM operand (TF32 hi/lo image)
     float *ring_R;           // split tiers: [patch][ring_rows_pad] ring terms of one face-plane axis
+    void *dscr = nullptr;    // n > 24: Dirichlet workspace [patch][(n-1)^3] (fine precision)
     void *f_stage, *phi_stage;  // device staging for mlc_solve_host
     int *err;                // device error word: nonzero if a bounded wait in a kernel gave up
     size_t ws_bytes;

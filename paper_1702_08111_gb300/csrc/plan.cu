@@ -217,8 +217,13 @@ mlc_status derive_geometry(const mlc_params &pp, Geom &g) {
     }
     g.log2Mc = 0;
     g.Mhc = g.Mc / 2 + 1;
-    if (g.M > 256 || g.Mc > 512 || g.M < 32) return MLC_ERR_UNSUPPORTED;
-    if (g.n > 16) return MLC_ERR_UNSUPPORTED;  // Dirichlet tile held in shared memory
+    // patch sizes with a Dirichlet kernel instantiation; patch periods up to 64
+    // (128 in the split tiers, whose FP32 slab of 128 x 129 complex entries
+    // still fits in shared memory); n > 16 needs the FP32 patch charge of the
+    // moments in shared memory too
+    if (g.n != 4 && g.n != 8 && g.n != 12 && g.n != 16 && g.n != 24 && g.n != 32) return MLC_ERR_UNSUPPORTED;
+    if (g.M < 32 || g.M > (g.conv == CONV_F32 ? 128 : 64) || g.Mc > 512) return MLC_ERR_UNSUPPORTED;
+    if (g.n > 16 && g.conv != CONV_F32) return MLC_ERR_UNSUPPORTED;
     g.S = (2 * g.b + 2) * (2 * g.b + 2);
     g.nc = (g.n + 2 * g.s) / 4 + 1;
     g.nzr = 0;
@@ -689,6 +694,11 @@ mlc_status create_plan(const mlc_params *params, const double *dgf_host, int dgf
         TRY(dev_alloc(pl, &pl->phiH, no * no * no));
         TRY(dev_alloc(pl, &pl->phiB, (size_t)G.n_planes_total));
         TRY(dev_alloc(pl, &pl->tpl, 3 * (size_t)(G.np + 1) * G.no * (G.N + 1)));
+        if (G.n > 24) {  // Dirichlet workspace of patches too large for shared memory
+            double *d = nullptr;
+            TRY(dev_alloc(pl, &d, NP * (size_t)(G.n - 1) * (G.n - 1) * (G.n - 1)));
+            pl->dscr = d;
+        }
         TRY(dev_alloc(pl, &pl->err, 1, false));
         TRY_CUDA(cudaMemset(pl->err, 0, sizeof(int)));
         return MLC_OK;
@@ -715,6 +725,7 @@ mlc_status create_plan(const mlc_params *params, const double *dgf_host, int dgf
         h.c2h2 = G.h * G.h / 12.0;
         h.inv_h2 = 1.0 / (G.h * G.h);
         h.err = pl->err;
+        h.dscr = pl->dscr;
         st = dev_upload(pl, &pl->dptrs, std::vector<PlanPtrs>{h});
     }
     if (st == MLC_OK) st = to_status(cudaDeviceSynchronize());

@@ -72,6 +72,36 @@ def sample_bumps(N: int, bumps: Bumps, nodes: int | None = None, dtype=np.float6
     return f.astype(dtype, copy=False)
 
 
+def _radial_samples(N: int, nodes: int | None, centre, Ro: float):
+    """r = |x - centre| / Ro at the nodes g h, g in [0, nodes)^3."""
+    nodes = N if nodes is None else nodes
+    x = np.arange(nodes, dtype=np.float64) / N
+    return np.sqrt((x[:, None, None] - centre[0]) ** 2 + (x[None, :, None] - centre[1]) ** 2
+                   + (x[None, None, :] - centre[2]) ** 2) / Ro
+
+
+def paper_smooth_charge(N: int, nodes: int | None = None, dtype=np.float64) -> np.ndarray:
+    """The smooth test charge of Sec. 7.1: (r - r^2)^4 for r < 1, r = |x - 1/2| / R_o,
+    R_o = 1/4 (no random draw)."""
+    r = _radial_samples(N, nodes, (0.5, 0.5, 0.5), 0.25)
+    return np.where(r < 1.0, (r - r * r) ** 4, 0.0).astype(dtype, copy=False)
+
+
+PAPER_OSC_CENTRES = ((3 / 16, 7 / 16, 13 / 16), (7 / 16, 13 / 16, 3 / 16), (13 / 16, 3 / 16, 7 / 16))
+
+
+def paper_oscillatory_charge(N: int, nodes: int | None = None, dtype=np.float64) -> np.ndarray:
+    """The oscillatory test charge of Sec. 7.3: three copies of
+    (1/R_o^3) (r - r^2)^2 sin^2(gamma r / 2), r < 1, with R_o = 0.05,
+    gamma = 4 mu pi, mu = 7, at the three centres the paper gives."""
+    Ro, gamma = 0.05, 28.0 * math.pi
+    f = 0.0
+    for c in PAPER_OSC_CENTRES:
+        r = _radial_samples(N, nodes, c, Ro)
+        f = f + np.where(r < 1.0, (r - r * r) ** 2 * np.sin(0.5 * gamma * r) ** 2, 0.0) / Ro ** 3
+    return np.asarray(f).astype(dtype, copy=False)
+
+
 # ---------------------------------------------------------------------------
 # Named workloads.  Each is (solver sizes, charge recipe).  The solver sizes
 # follow the problem statement: N nodes per axis, patch side n, support s

@@ -18,6 +18,8 @@ MLC_TIER_FP64, MLC_TIER_SPLIT, MLC_TIER_DF, MLC_TIER_SPLIT_DF = 0, 1, 2, 3
 F32_CHARGE_TIERS = (MLC_TIER_SPLIT, MLC_TIER_SPLIT_DF)
 TIER_NAMES = {MLC_TIER_FP64: "fp64", MLC_TIER_SPLIT: "split", MLC_TIER_DF: "df", MLC_TIER_SPLIT_DF: "split_df"}
 MLC_MODE_MLC, MLC_MODE_MLC0 = 0, 1
+(MLC_OK, MLC_ERR_INVALID_ARG, MLC_ERR_UNSUPPORTED, MLC_ERR_OOM, MLC_ERR_CUDA, MLC_ERR_ADMISSION,
+ MLC_ERR_TIMEOUT) = range(7)
 STAGE_MOMENTS, STAGE_FH, STAGE_PHIH, STAGE_PHIB, STAGE_DGF = 0, 1, 2, 3, 4
 STAGE_COARSE_SAMPLES, STAGE_FACE_INDEX, STAGE_COARSE_INDEX = 5, 6, 7
 

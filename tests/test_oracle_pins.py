@@ -242,6 +242,62 @@ def test_closed_form_smooth_charge_sec71():
     assert sp.simplify((sp.diff(phi_in, r) - sp.diff(phi_out, r)).subs(r, 1)) == 0
 
 
+def test_closed_form_oscillatory_charge_sec73():
+    # Sec. 7.3: the radial Laplacian of the interior potential is the charge,
+    # value and slope match the monopole at r = 1 (gamma = 28 pi), the centre
+    # value is the r -> 0 limit, and the monopole strength is minus the charge
+    # over 4 pi; then the oracle's numpy form against the symbolic one
+    sp = pytest.importorskip("sympy")
+    r, g = sp.symbols("r gamma", positive=True)
+    phi_in = (r ** 6 / 84 - r ** 5 / 30 + r ** 4 / 40 + 60 / g ** 6 - 9 / g ** 4 - sp.Rational(1, 120)
+              + 120 / (g ** 6 * r)
+              + (-120 / (g ** 6 * r) - 9 / g ** 4 + 300 / g ** 6 + 36 * r / g ** 4 + r ** 2 / (2 * g ** 2)
+                 - 30 * r ** 2 / g ** 4 - r ** 3 / g ** 2 + r ** 4 / (2 * g ** 2)) * sp.cos(g * r)
+              + (12 / (g ** 5 * r) - 360 / (g ** 7 * r) - 96 / g ** 5 + 120 * r / g ** 5 - 3 * r / g ** 3
+                 + 8 * r ** 2 / g ** 3 - 5 * r ** 3 / g ** 3) * sp.sin(g * r))
+    phi_out = (-sp.Rational(1, 210) - 12 / g ** 4 + 360 / g ** 6) / r
+    f = (r - r ** 2) ** 2 * sp.sin(g * r / 2) ** 2
+    lap = sp.diff(r ** 2 * sp.diff(phi_in, r), r) / r ** 2 - f
+    assert sp.simplify(sp.expand(sp.expand_trig(lap.rewrite(sp.exp)))) == 0
+    gam = 28 * sp.pi
+    assert sp.simplify((phi_in - phi_out).subs(r, 1).subs(g, gam)) == 0
+    assert sp.simplify((sp.diff(phi_in, r) - sp.diff(phi_out, r)).subs(r, 1).subs(g, gam)) == 0
+    assert sp.simplify(sp.limit(phi_in, r, 0) - (-sp.Rational(1, 120) - 6 / g ** 4)) == 0
+    q = sp.integrate(r ** 2 * f, (r, 0, 1))  # total charge / (4 pi) in scaled units
+    assert sp.simplify((phi_out * r + q).subs(g, gam)) == 0
+    Ro = 0.05
+    rr = np.array([0.0, 0.013, 0.37, 0.9, 1.0, 1.6])
+    v = CF.oscillatory_potential(rr, Ro)
+    for k, x in enumerate(rr):
+        expr = phi_in.subs(g, gam) if 0 < x < 1 else phi_out.subs(g, gam)
+        want = float(-sp.Rational(1, 120) - 6 / gam ** 4) if x == 0 else float(expr.subs(r, x))
+        assert abs(v[k] - want / Ro) <= 1e-13 * abs(want / Ro), (x, v[k], want / Ro)
+
+
+def test_paper_charges_sample_the_sec7_densities():
+    # the shared input module's samplers of the Sec. 7.1 / 7.3 charges at
+    # hand-picked nodes, and the closed-form potentials on the same grid
+    N = 64
+    fs = I.paper_smooth_charge(N)
+    assert fs[32, 32, 32] == 0.0                                    # r = 0
+    r = (8 / 64) / 0.25                                             # node 8 h from the centre
+    assert abs(fs[40, 32, 32] - (r - r * r) ** 4) < 1e-16
+    assert fs[0, 0, 0] == 0.0
+    fo = I.paper_oscillatory_charge(N)
+    c = (12, 28, 52)                                                # 3/16, 7/16, 13/16 at N = 64
+    assert fo[c] == 0.0
+    r = (1 / 64) / 0.05
+    want = (r - r * r) ** 2 * np.sin(14 * np.pi * r) ** 2 / 0.05 ** 3
+    assert abs(fo[13, 28, 52] - want) <= 1e-12 * abs(want)
+    ps = CF.smooth_potential_grid(N)
+    assert abs(ps[32, 32, 32] - 0.25 ** 2 * (-1 / 1260)) < 1e-18
+    po = CF.oscillatory_potential_grid(N)
+    # a centre node: its own charge's centre value plus the other two (exterior) charges
+    others = sum(CF.oscillatory_potential(np.array([np.linalg.norm(np.array(c) / 64 - np.array(e)) / 0.05]), 0.05)[0]
+                 for e in CF.OSC_CENTRES[1:])
+    assert abs(po[c] - ((-1 / 120 - 6 / CF.OSC_GAMMA ** 4) / 0.05 + others)) < 1e-12
+
+
 # ---------------------------------------------------------------- local field and whole solve
 
 def test_local_field_solves_patch_problem(G4):
