@@ -48,6 +48,21 @@ R6  phi^H is evaluated on the coarse nodes [-b, N/4 + b]^3, the nodes the
     interpolation reads.
 R7  Delta^H is the same Mehrstellen operator at spacing H = C h applied to the
     fine field sampled at coarse nodes; G^H = H^{-1} G^{h=1}.
+R8  Multilevel MLC (Sec. 5), levels > 2: with every level covering the whole
+    grid, chi-tilde vanishes, and the level-l charge of patch i is the coarse
+    charge F^{h_l} (the sum of the finer patches' contributions, eq. FDLD)
+    restricted to the patch, as the fine charge is in Sec. 4.  The downward
+    pass, the level-0 solve and the upward pass are then, level by level, the
+    two-level steps with the global coarse solve phi^H = G^H * F^H replaced by
+    the MLC solve of F^H on the coarse grid: its domain is the smallest box of
+    whole patches from min(F^H lo, phi^H lo) that holds the support of F^H and
+    the nodes phi^H is needed on (the proper nesting of eq.
+    propernesting2fdiscr), with the same n, s, P, Q, b, g_beta and mode.  The
+    upward pass interpolates the uncorrected coarse solution (eq.
+    mlcmultilevel); the Mehrstellen correction (eq.
+    mcapplicationfullmultipole) adds C2 h_l^2 times the level's own charge
+    term chi-tilde f, zero on the coarse levels, so only the finest level is
+    corrected.
 """
 from __future__ import annotations
 
@@ -91,6 +106,9 @@ class Params:
     mode: str = "mlc"  # "mlc" (alpha < beta) or "mlc0" (alpha = beta)
     nD: int = 128
     zeta: int = 2
+    levels: int = 2          # Sec. 5: number of levels (2: the two-level algorithm of Sec. 4)
+    h_level: float | None = None   # mesh spacing of this level (default 1/N, the finest level)
+    correction: bool = True  # add C2 h^2 f at the end (eq. mcapplicationfulldiscr); R8
 
     def __post_init__(self):
         if self.Q not in STENCIL_B:
@@ -103,7 +121,9 @@ class Params:
             self.b = 2 if self.Q == 4 else 3
         if self.beta is None:
             self.beta = 3.0 if self.Q == 4 else 3.25
-        self.h = 1.0 / self.N
+        if self.levels < 2:
+            raise ValueError("levels >= 2")
+        self.h = 1.0 / self.N if self.h_level is None else float(self.h_level)
         self.H = self.C * self.h
         self.R = self.n * self.h / 2.0
         self.np_ = self.N // self.n
@@ -581,7 +601,11 @@ def mlc_solve(prm: Params, f_closed: np.ndarray, G1: np.ndarray | None = None, s
     # ---- Step 2: global coarse solve phi^H = G^H * F^H, G^H = H^{-1} G^{h=1}
     olo, ohi = prm.phih_extent
     no = ohi - olo + 1
-    phiH = direct_sum(G1, FH, (flo,) * 3, (olo,) * 3, (no,) * 3, H * H)
+    if prm.levels > 2:
+        # Sec. 5 (R8): the coarse solve is itself an MLC solve of F^H
+        phiH = coarse_level_solve(prm, FH, G1)
+    else:
+        phiH = direct_sum(G1, FH, (flo,) * 3, (olo,) * 3, (no,) * 3, H * H)
 
     # ---- Step 3: boundary values by local corrections (eqs. philocmlcII, mlcfulldiscr)
     gpts = box_points(0, N)
@@ -640,7 +664,8 @@ def mlc_solve(prm: Params, f_closed: np.ndarray, G1: np.ndarray | None = None, s
         o = origins[i]
         fp[i] = f_closed[o[0]:o[0] + n + 1, o[1]:o[1] + n + 1, o[2]:o[2] + n + 1]
     U = dirichlet_solve(prm, U, fp)
-    U += C2 * h * h * fp
+    if prm.correction:
+        U += C2 * h * h * fp
     phi = np.zeros((N + 1,) * 3)
     for i in range(NP):
         o = origins[i]
@@ -657,6 +682,34 @@ def mlc_solve(prm: Params, f_closed: np.ndarray, G1: np.ndarray | None = None, s
         stages["face_nodes"] = gface
         stages["phiB"] = phiB
     return phi
+
+
+def coarse_level_params(prm: Params):
+    """Sec. 5 (R8): origin c0 (in coarse nodes of this level) and parameters
+    of the next coarser level's MLC problem."""
+    flo, fhi = prm.fh_extent
+    olo, ohi = prm.phih_extent
+    c0 = min(flo, olo)
+    top = max(fhi, ohi)
+    Nc = prm.n * (-(-(top - c0 + 1) // prm.n))  # whole patches; node c0 + Nc carries no charge
+    child = Params(N=Nc, n=prm.n, s=prm.s, P=prm.P, Q=prm.Q, C=prm.C, beta=prm.beta, b=prm.b,
+                   mode=prm.mode, nD=prm.nD, zeta=prm.zeta, levels=prm.levels - 1,
+                   h_level=prm.H, correction=False)
+    assert child.g_beta == prm.g_beta and child.g_alpha == prm.g_alpha
+    return c0, child
+
+
+def coarse_level_solve(prm: Params, FH: np.ndarray, G1: np.ndarray) -> np.ndarray:
+    """phi^H on [olo, ohi]^3 by the MLC solve of F^H on the coarser level (R8)."""
+    flo, _ = prm.fh_extent
+    olo, ohi = prm.phih_extent
+    c0, child = coarse_level_params(prm)
+    fc = np.zeros((child.N + 1,) * 3)
+    a, nf = flo - c0, FH.shape[0]
+    fc[a:a + nf, a:a + nf, a:a + nf] = FH
+    phic = mlc_solve(child, fc, G1=G1)
+    a, no = olo - c0, ohi - olo + 1
+    return phic[a:a + no, a:a + no, a:a + no].copy()
 
 
 # ---------------------------------------------------------------------------

@@ -451,3 +451,52 @@ def test_coarse_patch_index_worked_example():
     node = ((3 + 2) * 13 + (0 + 2)) * 13 + (-2 + 2)
     assert list(ent[off[node]:off[node + 1]]) == [1, 9, 33, 41, 65, 73]
     assert len(off) == 13 ** 3 + 1
+
+
+# ---------------------------------------------------------------- multilevel (Sec. 5)
+
+def test_coarse_level_params_worked_example():
+    # N = 32, n = 8, Q = 4 (b = 2), MLC-0: s = 12 -> g_alpha = 4, F^H on
+    # [floor(-4/4), 3*2 + ceil(12/4)] = [-1, 9], phi^H on [-2, 10]: the coarse
+    # problem starts at -2 and needs 13 nodes -> two patches of 8 (N = 16).
+    # s = 24 -> g_alpha = 16: F^H on [-4, 12], phi^H on [-2, 10] -> c0 = -4,
+    # 17 nodes -> 24.
+    for s, c0_want, N_want in ((12, -2, 16), (24, -4, 24)):
+        prm = O.Params(N=32, n=8, s=s, nD=ND, mode="mlc0", levels=3)
+        c0, child = O.coarse_level_params(prm)
+        assert (c0, child.N) == (c0_want, N_want)
+        assert child.h == prm.H and child.levels == 2 and not child.correction
+        assert (child.g_alpha, child.g_beta, child.b) == (prm.g_alpha, prm.g_beta, prm.b)
+
+
+def test_multilevel_mlc0_error_insensitive_to_levels(G4, bump32):
+    # Sec. 7.2: the MLC-0 error does not depend on the number of levels (Table 8
+    # against Table 4); and it still falls with the correction radius
+    N, bumps, f = bump32
+    plain = O.plain_solution(O.Params(N=N, n=8, s=8, nD=ND), f, G1=G4)
+    errs = {}
+    for s in (16, 24):
+        for L in (2, 3, 4):
+            phi = O.mlc_solve(O.Params(N=N, n=8, s=s, nD=ND, mode="mlc0", levels=L), f, G1=G4)
+            errs[s, L] = np.abs(phi - plain).max() / np.abs(plain).max()
+    for s in (16, 24):
+        for L in (3, 4):
+            assert errs[s, 2] / 1.5 < errs[s, L] < 1.5 * errs[s, 2], (s, L, errs)
+    assert errs[24, 3] < errs[16, 3] / 50
+
+
+def test_coarse_level_solve_approximates_coarse_convolution(G4, bump32):
+    # the level below solves Delta^H phi = F^H by MLC: against the direct sum
+    # G^H * F^H its error is that level's own barrier, falling with s
+    N, bumps, f = bump32
+    diffs = []
+    for s in (16, 24):
+        prm = O.Params(N=N, n=8, s=s, nD=ND, mode="mlc0", levels=3)
+        st = {}
+        O.mlc_solve(prm, f, G1=G4, stages=st)
+        flo, (olo, ohi) = st["FH_lo"], prm.phih_extent
+        no = ohi - olo + 1
+        direct = O.direct_sum(G4, st["FH"], (flo,) * 3, (olo,) * 3, (no,) * 3, prm.H * prm.H)
+        assert np.array_equal(st["phiH"], O.coarse_level_solve(prm, st["FH"], G4))
+        diffs.append(np.abs(st["phiH"] - direct).max() / np.abs(direct).max())
+    assert diffs[0] < 1e-4 and diffs[1] < diffs[0] / 5, diffs
