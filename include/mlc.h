@@ -86,11 +86,21 @@ typedef struct {
     int conv_chunk; /* patches per launch group of the local convolutions: their spectra
                        (the scratch between the forward and inverse transforms) exist
                        for one group at a time; -1: the library's choice (1024)        */
+    int levels;     /* number of levels of the multilevel MLC (Sec. 5); -1: 2, the
+                       two-level algorithm of Sec. 4.  With levels > 2 the global coarse
+                       solve phi^H = G^H * F^H becomes the MLC solve of F^H on the next
+                       coarser level (spacing H = C h; the same n, s, P, Q, b, g_beta,
+                       mode and tier; a box of whole patches from min(F^H low corner,
+                       phi^H low corner) that holds the support of F^H and the nodes
+                       phi^H is read on), recursively, down to a two-level solve whose
+                       coarse solve is Hockney's; the Mehrstellen correction
+                       (eq. mcapplicationfullmultipole) is added on the finest level
+                       only.  2 <= levels <= 6                                         */
 } mlc_params;
 
 typedef struct mlc_plan_s *mlc_plan_t;
 
-/* Fill *p with N, n, s, P, Q as given, C = 4 and every other field -1/default. */
+/* Fill *p with N, n, s, P, Q as given, C = 4 and every other field -1 (default). */
 mlc_status mlc_params_init(mlc_params *p, int N, int n, int s, int P, int Q);
 
 /*
@@ -100,9 +110,13 @@ mlc_status mlc_params_init(mlc_params *p, int N, int n, int s, int P, int Q);
  * kernel spectra for the Hockney convolutions (App. A.2), the Legendre
  * basis-field tables Delta^H(G^h * Q^p) (Sec. 4, Step 1) and the index tables,
  * and allocates the workspace.  Synchronises the device.
- * INVALID_ARG if: out is NULL; N, n, s, C, P, Q break the rules above;
- * g_beta < s - C b.  UNSUPPORTED if the patch FFT length 2(n+s) or the coarse
- * FFT length is above 256.
+ * INVALID_ARG if: out is NULL; N, n, s, C, P, Q, levels break the rules
+ * above; g_beta < s - C b.  UNSUPPORTED if: n is not one of 4, 8, 12, 16, 24,
+ * 32; the patch FFT length (the power of two >= 2(n+s)) is above 64 (128 in
+ * the split tiers); n > 16 outside the split tiers; the coarse FFT length
+ * (the smallest even 2^a 3^b 5^c >= twice the largest coarse lag) is above
+ * 512.  With levels > 2 the plan of the next coarser level is created with
+ * it, with its scratch, so that no solve allocates.
  */
 mlc_status mlc_plan_create(int N, int patch, int support, int coarsening, int P, int Q,
                            mlc_plan_t *out);

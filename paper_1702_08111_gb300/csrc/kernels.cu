@@ -2764,7 +2764,57 @@ cudaError_t launch_assemble(const mlc_plan_s *pl, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Sec. 5: F^H (nf^3 from flo) into the coarser level's charge array (node
+// off = flo - c0 of its grid, side Nc), in that level's charge precision.
+template <typename TF>
+__global__ void __launch_bounds__(256) k_fh_to_level(const double *FH, int nf, int off, int Nc, TF *fc) {
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)nf * nf * nf) return;
+    const int x = (int)(idx % nf), y = (int)((idx / nf) % nf), z = (int)(idx / ((long)nf * nf));
+    fc[((long)(z + off) * Nc + (y + off)) * Nc + (x + off)] = (TF)FH[idx];
+}
+
+// phi^H (no^3 from olo) from the coarser level's result (node off = olo - c0).
+template <typename T>
+__global__ void __launch_bounds__(256) k_level_to_phiH(const double *pc, int Nc, int off, int no, T *phiH) {
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)no * no * no) return;
+    const int x = (int)(idx % no), y = (int)((idx / no) % no), z = (int)(idx / ((long)no * no));
+    phiH[idx] = FT<T>::of(pc[((long)(z + off) * Nc + (y + off)) * Nc + (x + off)]);
+}
+
+// Sec. 5: the coarse solve of a multilevel plan, an MLC solve of F^H on the
+// next coarser level (its own plan, on this stream).
+cudaError_t run_coarse_level(const mlc_plan_s *pl, cudaStream_t st) {
+    const Geom &g = pl->g;
+    mlc_plan_s *ch = pl->child;
+    const int Nc = ch->g.N;
+    mark(pl, 6, st);
+    const long nf3 = (long)g.nf * g.nf * g.nf, no3 = (long)g.no * g.no * g.no;
+    const int off_f = g.flo - pl->child_c0, off_o = g.olo - pl->child_c0;
+    if (g.f32in)
+        k_fh_to_level<float><<<(unsigned)((nf3 + 255) / 256), 256, 0, st>>>(pl->FH, g.nf, off_f, Nc, (float *)pl->child_f);
+    else
+        k_fh_to_level<double><<<(unsigned)((nf3 + 255) / 256), 256, 0, st>>>(pl->FH, g.nf, off_f, Nc, (double *)pl->child_f);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (mlc_solve(ch, pl->child_f, pl->child_phi, st) != MLC_OK) {
+        e = cudaGetLastError();
+        return e != cudaSuccess ? e : cudaErrorUnknown;
+    }
+    mark(pl, 7, st);
+    if (g.fine == FINE_F64)
+        k_level_to_phiH<double><<<(unsigned)((no3 + 255) / 256), 256, 0, st>>>(pl->child_phi, Nc, off_o, g.no, (double *)pl->phiH);
+    else
+        k_level_to_phiH<dfl><<<(unsigned)((no3 + 255) / 256), 256, 0, st>>>(pl->child_phi, Nc, off_o, g.no, (dfl *)pl->phiH);
+    mark(pl, 8, st);
+    mark(pl, 9, st);
+    mark(pl, 10, st);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_coarse(const mlc_plan_s *pl, cudaStream_t st) {
+    if (pl->child) return run_coarse_level(pl, st);
     if (pl->g.fine == FINE_F64)  // coarse FFTs in FP64
         return run_coarse_t<double>(pl, pl->khat_c, pl->tw_c, st);
     return run_coarse_t<dfl>(pl, pl->khat_c_df, pl->tw_c_df, st);  // in double-float arithmetic

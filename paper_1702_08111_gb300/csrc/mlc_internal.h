@@ -37,6 +37,7 @@ struct Geom {
     int N, n, s, C, P, Q, b, ga, gb, np, NP, npoly, nb, W, M, log2M, Mh;
     int npad;                        // npoly rounded up to a multiple of 4 (row stride of moments, D)
     int tier, mode;
+    int levels;                      // Sec. 5: 2 = two-level; > 2: the coarse solve is an MLC solve
     int conv, fine;                  // ConvPrec, FinePrec of the tier
     bool f32in;                      // FP32 charge
     double h, H, R;
@@ -172,6 +173,14 @@ struct mlc_plan_s {
     // side stream of a solve: moments, then residuals, beside the main chain
     cudaStream_t side = nullptr;
     cudaEvent_t fork[4] = {};
+    // Sec. 5 (levels > 2): the plan of the next coarser level solves
+    // Delta^H phi = F^H by MLC in place of the Hockney coarse solve
+    mlc_plan_s *child = nullptr;
+    void *child_f = nullptr;       // its charge (FP32 or FP64 by tier): F^H at offset flo - child_c0
+    double *child_phi = nullptr;   // its result (child N^3)
+    int child_c0 = 0;              // its node 0 in this level's coarse nodes
+    double h_level = 0.0;          // mesh spacing given at creation (0: 1/N)
+    bool correction = true;        // Mehrstellen correction C2 h^2 f (off on the coarser levels)
 };
 
 namespace mlc {

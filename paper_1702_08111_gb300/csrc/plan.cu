@@ -164,6 +164,8 @@ mlc_status derive_geometry(const mlc_params &pp, Geom &g) {
     g.ga = g.s - g.C * g.b;
     if (g.ga < 0) return MLC_ERR_INVALID_ARG;
     g.mode = pp.mode < 0 ? MLC_MODE_MLC : pp.mode;
+    g.levels = pp.levels < 0 ? 2 : pp.levels;
+    if (g.levels < 2 || g.levels > 6) return MLC_ERR_INVALID_ARG;
     g.tier = pp.tier < 0 ? MLC_TIER_FP64 : pp.tier;
     if (!tier_valid(g.tier)) return MLC_ERR_INVALID_ARG;
     g.conv = tier_conv(g.tier);
@@ -534,12 +536,28 @@ mlc_status get_dgf(int device, int Q, int nD, int zeta, int L, const double **pt
 
 void free_plan(mlc_plan_s *pl) {
     if (!pl) return;
+    free_plan(pl->child);
     for (void *p : pl->owned) cudaFree(p);
     for (auto &e : pl->ev_pool) cudaEventDestroy(e);
     for (auto &e : pl->fork)
         if (e) cudaEventDestroy(e);
     if (pl->side) cudaStreamDestroy(pl->side);
     delete pl;
+}
+
+// What a solve needs besides the plan's tables: the local-convolution
+// scratch (unless the caller gave one) and the side stream with its events.
+mlc_status prepare_solve(mlc_plan_s *pl) {
+    if (!pl->user_scratch && !pl->scratch) {
+        char *sc = nullptr;
+        TRY(dev_alloc(pl, &sc, conv_scratch_bytes(pl->g, std::min<long>(pl->g.chunk, pl->g.NP))));
+        pl->scratch = sc;
+    }
+    if (!pl->side) {
+        TRY_CUDA(cudaStreamCreateWithFlags(&pl->side, cudaStreamNonBlocking));
+        for (auto &e : pl->fork) TRY_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    return MLC_OK;
 }
 
 }  // namespace
@@ -563,7 +581,7 @@ mlc_status mlc_params_init(mlc_params *p, int N, int n, int s, int P, int Q) {
     if (!p) return MLC_ERR_INVALID_ARG;
     p->N = N; p->n = n; p->s = s; p->C = 4; p->P = P; p->Q = Q;
     p->g_beta = -1; p->b = -1; p->tier = MLC_TIER_FP64; p->mode = MLC_MODE_MLC;
-    p->dgf_nD = -1; p->dgf_zeta = -1; p->conv_chunk = -1;
+    p->dgf_nD = -1; p->dgf_zeta = -1; p->conv_chunk = -1; p->levels = -1;
     return MLC_OK;
 }
 
@@ -573,11 +591,21 @@ namespace {
 
 // Plan creation; dgf_host (optional): the caller's DGF octant [0, dgf_Lh]^3
 // in place of the device's cached table.
-mlc_status create_plan(const mlc_params *params, const double *dgf_host, int dgf_Lh, mlc_plan_t *out) {
+mlc_status make_coarser_level(mlc_plan_s *pl, const double *dgf_host, int dgf_Lh);
+
+// h_level > 0: the mesh spacing of a coarser level of a multilevel solve (in
+// place of 1/N); correction: add the Mehrstellen correction C2 h^2 f.
+mlc_status create_plan(const mlc_params *params, const double *dgf_host, int dgf_Lh, mlc_plan_t *out,
+                       double h_level = 0.0, bool correction = true) {
     if (!params || !out) return MLC_ERR_INVALID_ARG;
     *out = nullptr;
     Geom g;
     TRY(derive_geometry(*params, g));
+    if (h_level > 0.0) {
+        g.h = h_level;
+        g.H = g.C * g.h;
+        g.R = g.n * g.h / 2.0;
+    }
     std::call_once(g_cfg_once, configure_kernels);
     int device = 0;
     TRY_CUDA(cudaGetDevice(&device));
@@ -586,6 +614,8 @@ mlc_status create_plan(const mlc_params *params, const double *dgf_host, int dgf
     pl->g = g;
     pl->params = *params;
     pl->device = device;
+    pl->h_level = h_level;
+    pl->correction = correction;
     // lag extent: local fields n + s, coarse Lc, basis fields (checked in build_tables)
     Geom &G = pl->g;
     G.L = std::max(G.n + G.s, G.Lc);
@@ -722,18 +752,54 @@ mlc_status create_plan(const mlc_params *params, const double *dgf_host, int dgf
         h.lam = pl->lam;
         h.N = G.N;
         h.np = G.np;
-        h.c2h2 = G.h * G.h / 12.0;
+        h.c2h2 = correction ? G.h * G.h / 12.0 : 0.0;
         h.inv_h2 = 1.0 / (G.h * G.h);
         h.err = pl->err;
         h.dscr = pl->dscr;
         st = dev_upload(pl, &pl->dptrs, std::vector<PlanPtrs>{h});
     }
+    if (st == MLC_OK && G.levels > 2) st = make_coarser_level(pl, dgf_host, dgf_Lh);
     if (st == MLC_OK) st = to_status(cudaDeviceSynchronize());
     if (st != MLC_OK) {
         free_plan(pl);
         return st;
     }
     *out = pl;
+    return MLC_OK;
+}
+
+// Sec. 5: the next coarser level of a multilevel solve.  Its problem is
+// Delta^H phi = F^H on a box of whole patches (spacing H) starting at
+// min(flo, olo) that holds the support of F^H and the nodes phi^H is read
+// on; same n, s, P, Q, b, g_beta, mode, tier; no Mehrstellen correction.  Its
+// charge array stays zero outside the F^H box (written once here), and its
+// scratch and side stream exist before the first solve, so that solves
+// allocate nothing (and can be captured in a graph).
+mlc_status make_coarser_level(mlc_plan_s *pl, const double *dgf_host, int dgf_Lh) {
+    const Geom &G = pl->g;
+    const int c0 = std::min(G.flo, G.olo), top = std::max(G.fhi, G.ohi);
+    const int Nc = G.n * ((top - c0 + G.n) / G.n);
+    mlc_params cp = pl->params;
+    cp.N = Nc;
+    cp.levels = G.levels - 1;
+    mlc_plan_t ch = nullptr;
+    TRY(create_plan(&cp, dgf_host, dgf_Lh, &ch, G.H, false));
+    pl->child = ch;
+    pl->child_c0 = c0;
+    const size_t n3 = (size_t)Nc * Nc * Nc;
+    if (G.f32in) {
+        float *f = nullptr;
+        TRY(dev_alloc(pl, &f, n3));
+        pl->child_f = f;
+    } else {
+        double *f = nullptr;
+        TRY(dev_alloc(pl, &f, n3));
+        pl->child_f = f;
+    }
+    TRY_CUDA(cudaMemset(pl->child_f, 0, n3 * (G.f32in ? sizeof(float) : sizeof(double))));
+    TRY(dev_alloc(pl, &pl->child_phi, n3));
+    TRY(prepare_solve(ch));
+    pl->ws_bytes += ch->ws_bytes;
     return MLC_OK;
 }
 
@@ -751,7 +817,7 @@ mlc_status mlc_plan_set_dgf(mlc_plan_t pl, const double *table, int L) {
     TRY_CUDA(cudaGetDevice(&dev));
     if (dev != pl->device) return MLC_ERR_INVALID_ARG;
     mlc_plan_t np = nullptr;
-    TRY(create_plan(&pl->params, table, L, &np));
+    TRY(create_plan(&pl->params, table, L, &np, pl->h_level, pl->correction));
     TRY_CUDA(cudaDeviceSynchronize());
     mlc_batch_forget(pl);
     np->user_scratch = pl->user_scratch;
@@ -813,11 +879,7 @@ mlc_status mlc_plan_set_scratch(mlc_plan_t pl, void *scratch, size_t bytes) {
 mlc_status mlc_solve(mlc_plan_t pl, const void *f, void *phi, void *stream) {
     if (!pl || !f || !phi || f == phi) return MLC_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    if (!pl->user_scratch && !pl->scratch) {  // first solve: the plan's own scratch
-        char *sc = nullptr;
-        TRY(dev_alloc(pl, &sc, conv_scratch_bytes(pl->g, std::min<long>(pl->g.chunk, pl->g.NP))));
-        pl->scratch = sc;
-    }
+    TRY(prepare_solve(pl));  // first solve: the plan's own scratch and side stream
     void *scr = pl->user_scratch ? pl->user_scratch : pl->scratch;
     if (pl->hptrs.f != f || pl->hptrs.phi != phi) {
         TRY_CUDA(launch_set_ptrs(pl->dptrs, f, (double *)phi, st));
@@ -832,10 +894,6 @@ mlc_status mlc_solve(mlc_plan_t pl, const void *f, void *phi, void *stream) {
         // fields exist, the face-plane residuals run on a side stream beside
         // the local convolutions and the coarse-charge assembly and coarse
         // solve; the boundary step joins both.
-        if (!pl->side) {
-            TRY_CUDA(cudaStreamCreateWithFlags(&pl->side, cudaStreamNonBlocking));
-            for (auto &e : pl->fork) TRY_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        }
         cudaStream_t s2 = pl->side;
         TRY_CUDA(cudaEventRecord(pl->fork[0], st));
         TRY_CUDA(cudaStreamWaitEvent(s2, pl->fork[0], 0));

@@ -54,14 +54,14 @@ double estimate_ms(const mlc_params &p) {
 }
 
 struct Key {
-    int v[13];
+    int v[14];
     bool operator<(const Key &o) const { return std::memcmp(v, o.v, sizeof(v)) < 0; }
 };
 
 Key key_of(const mlc_params &p) {
     Key k;
-    const int v[13] = {p.N, p.n, p.s, p.C, p.P, p.Q, p.g_beta, p.b, p.tier, p.mode, p.dgf_nD, p.dgf_zeta,
-                       p.conv_chunk};
+    const int v[14] = {p.N, p.n, p.s, p.C, p.P, p.Q, p.g_beta, p.b, p.tier, p.mode, p.dgf_nD, p.dgf_zeta,
+                       p.conv_chunk, p.levels};
     std::memcpy(k.v, v, sizeof(v));
     return k;
 }

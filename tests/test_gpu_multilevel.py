@@ -1,0 +1,190 @@
+"""Multilevel MLC (Sec. 5) on the GPU: plans with levels > 2 solve the coarse
+problem Delta^H phi = F^H by an MLC solve on the next coarser level (a plan
+of its own, created with the fine plan).  Every stage and the potential are
+compared with the multilevel oracle (relative max-norm 1e-12 for the
+FP64-accurate tiers, 1e-6 for the split tiers); the batched and no-alloc
+entry points must give the standalone solve's bits; and the 3-level rows of
+Tables 8-9 (N = 512, n = 32) are soft pins against the Sec. 7.1 closed form.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import closed_forms as CF
+from oracle import mlc_oracle as O
+from paper_1702_08111_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+FP64, SPLIT, DF, SPLIT_DF = 0, 1, 2, 3
+F32_TIERS = (SPLIT, SPLIT_DF)
+
+
+def tol_of(tier):
+    return 1e-6 if tier in F32_TIERS else 1e-12
+
+
+def relmax(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def G():
+    return {4: O.dgf_octant(4, 128, 2), 6: O.dgf_octant(6, 128, 2)}
+
+
+_ORACLE = {}
+
+
+def _oracle(kw, f64, G1):
+    key = repr(sorted(kw.items()))
+    if key not in _ORACLE:
+        mode = "mlc0" if kw.get("mode", 0) else "mlc"
+        prm = O.Params(N=kw["N"], n=kw["n"], s=kw["s"], P=kw["P"], Q=kw["Q"], mode=mode,
+                       levels=kw["levels"])
+        st = {}
+        phi = O.solve_open(prm, f64, G1=G1, stages=st)
+        _ORACLE[key] = (prm, phi, st)
+    return _ORACLE[key]
+
+
+def _phiB_from_planes(planes, nodes, n):
+    out = np.empty(len(nodes))
+    for a, g in enumerate(nodes):
+        for d in range(3):
+            if g[d] % n == 0:
+                u, v = [g[e] for e in range(3) if e != d]
+                out[a] = planes[d, g[d] // n, u, v]
+                break
+    return out
+
+
+CASES = [
+    dict(N=32, n=8, s=12, P=4, Q=4, levels=3),            # MLC with the Legendre ring
+    dict(N=32, n=8, s=16, P=4, Q=4, levels=4, mode=1),    # MLC-0, two coarser levels
+    dict(N=64, n=16, s=16, P=4, Q=6, levels=3),           # 27-point operator, n = 16
+]
+
+
+@pytest.mark.parametrize("tier", [FP64, DF, SPLIT])
+@pytest.mark.parametrize("kw", CASES, ids=["mlc_l3", "mlc0_l4", "q6_l3"])
+def test_multilevel_against_oracle(torch_cuda, G, kw, tier):
+    from paper_1702_08111_gb300 import mlc
+    torch = torch_cuda
+    N = kw["N"]
+    f64 = I.sample_bumps(N, I.draw_bumps(5, 300 + N))
+    if tier in F32_TIERS:
+        f64 = f64.astype(np.float32).astype(np.float64)
+    prm, phi_o, st = _oracle(kw, f64, G[kw["Q"]]) if tier not in F32_TIERS else \
+        _oracle(dict(kw, f32=1), f64, G[kw["Q"]])
+    pk = {k: v for k, v in kw.items() if k not in ("N", "n", "s", "P", "Q")}
+    plan = mlc.Plan(N, kw["n"], kw["s"], kw["P"], kw["Q"], tier=tier, **pk)
+    f = torch.from_numpy(f64.astype(np.float32) if tier in F32_TIERS else f64).cuda()
+    phi = plan.solve(f)
+    torch.cuda.synchronize()
+    plan.status()
+    tol = tol_of(tier)
+    assert relmax(plan.export(mlc.STAGE_MOMENTS), st["moments"]) <= tol
+    assert relmax(plan.export(mlc.STAGE_FH), st["FH"]) <= tol
+    assert relmax(plan.export(mlc.STAGE_PHIH), st["phiH"]) <= tol
+    pb = _phiB_from_planes(plan.export(mlc.STAGE_PHIB), st["face_nodes"], prm.n)
+    assert relmax(pb, st["phiB"]) <= tol
+    err = relmax(phi.cpu().numpy(), phi_o)
+    assert err <= tol, err
+    # a coarser level changes phi^H only by that level's own barrier error
+    # (largest for the 27-point case: g_alpha = 4 under an 8-point stencil)
+    two = mlc.Plan(N, kw["n"], kw["s"], kw["P"], kw["Q"], tier=tier,
+                   **{k: v for k, v in pk.items() if k != "levels"})
+    phi2 = two.solve(f).cpu().numpy()
+    assert 0.0 < relmax(phi.cpu().numpy(), phi2) < 1e-2
+
+
+def test_multilevel_batch_and_noalloc_bits(torch_cuda):
+    """The batched entry point (captured graph, coarse levels inside it) and
+    the no-alloc entry point give the standalone solve's bits."""
+    from paper_1702_08111_gb300 import mlc
+    torch = torch_cuda
+    plans, fs, ref = [], [], []
+    for k, (N, lv, tier) in enumerate([(32, 3, FP64), (64, 3, SPLIT), (32, 2, FP64), (48, 4, FP64)]):
+        f64 = I.sample_bumps(N, I.draw_bumps(3, 700 + k))
+        p = mlc.Plan(N, 8, 12, 4, 4, tier=tier, levels=lv)
+        f = torch.from_numpy(f64.astype(np.float32) if tier in F32_TIERS else f64).cuda()
+        plans.append(p)
+        fs.append(f)
+        ref.append(p.solve(f).clone())
+    torch.cuda.synchronize()
+    phis = [torch.empty_like(r) for r in ref]
+    for _ in range(2):  # first call tunes and captures, second replays
+        mlc.batch_solve(plans, fs, phis)
+        torch.cuda.synchronize()
+        for a, b in zip(phis, ref):
+            assert torch.equal(a, b)
+    out = torch.empty_like(ref[0])
+    plans[0].solve_noalloc(fs[0], out)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref[0])
+
+
+def test_multilevel_set_dgf_and_invalid_levels(torch_cuda, G):
+    """mlc_plan_set_dgf rebuilds the coarser levels with the injected table;
+    levels outside [2, 6] are INVALID_ARG."""
+    from paper_1702_08111_gb300 import mlc
+    torch = torch_cuda
+    N = 32
+    f64 = I.sample_bumps(N, I.draw_bumps(4, 811))
+    p = mlc.Plan(N, 8, 12, 4, 4, levels=3)
+    p.solve(torch.from_numpy(f64).cuda())
+    G2 = 1.5 * G[4]  # not a DGF: the result must be the oracle's with the same table
+    p.set_dgf(G2)
+    got = p.solve(torch.from_numpy(f64).cuda()).cpu().numpy()
+    ref = O.solve_open(O.Params(N=N, n=8, s=12, levels=3), f64, G1=G2)
+    assert relmax(got, ref) <= 1e-12
+    for lv in (1, 7):
+        with pytest.raises(mlc.MLCError) as e:
+            mlc.Plan(N, 8, 12, 4, 4, levels=lv)
+        assert e.value.status == mlc.MLC_ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------- Tables 8-9 at N = 512
+
+# (row, Q, s, b, mode, g_beta, P, the paper's 3-level scaled max error at
+# N = 512 on the finest level l = 2)
+ML_ROWS = [
+    ("T8 MLC-0 beta=2", 6, 28, 3, 1, -1, 4, 1.30594e-7),
+    ("T9 alpha=1.75 P=1", 6, 24, 3, 0, 36, 1, 5.2600e-7),
+    ("T9 alpha=1.75 P=4", 6, 24, 3, 0, 36, 4, 1.0782e-6),
+    ("T9 alpha=1.75 P=6", 6, 24, 3, 0, 36, 6, 1.1101e-6),
+]
+
+
+@pytest.fixture(scope="module")
+def smooth_512():
+    return I.paper_smooth_charge(512, dtype=np.float32), CF.smooth_potential_grid(512)
+
+
+@pytest.mark.parametrize("row", ML_ROWS, ids=[r[0] for r in ML_ROWS])
+def test_paper_three_level_rows_512(torch_cuda, smooth_512, row):
+    """Soft pin (order of magnitude, factor 5): 3-level MLC at N = 512, n = 32,
+    split tier, against the exact potential of the Sec. 7.1 smooth charge."""
+    from paper_1702_08111_gb300 import mlc
+    torch = torch_cuda
+    name, Q, s, b, mode, gb, P, paper = row
+    f, ex = smooth_512
+    plan = mlc.Plan(512, 32, s, P, Q, b=b, mode=mode, g_beta=gb, tier=SPLIT, levels=3)
+    phi = plan.solve(torch.from_numpy(f).cuda())
+    torch.cuda.synchronize()
+    plan.status()
+    err = relmax(phi.cpu().numpy(), ex)
+    del plan, phi
+    print(f"{name}: error {err:.5e}, paper {paper:.5e}, ratio {err / paper:.3f}")
+    assert paper / 5 <= err <= 5 * paper, (name, err, paper)
