@@ -434,6 +434,81 @@ __global__ void __launch_bounds__(256) k_slab(SlabArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// The same slab for 16-byte complex entries (FP64, double-float) at M = 128,
+// whose M x M slab does not fit in shared memory: after the forward y
+// transform of the nin input z columns, the ky rows go through the forward z
+// transform, the kernel spectrum and the inverse z transform rb rows at a
+// time in a row buffer, and each row keeps only the nz output z positions,
+// written back over its own input; the inverse y transform then runs on those
+// nz columns.  S: M rows of sw >= max(nin, nz) entries.  Same arithmetic per
+// entry as k_slab (the z transforms of a row do not depend on the others).
+// ---------------------------------------------------------------------------
+template <int LOG2M, typename R>
+__global__ void __launch_bounds__(256) k_slab_rows(SlabArgs a, int sw, int rb) {
+    using C = typename Cx<R>::T;
+    constexpr int M = 1 << LOG2M, MH = M / 2 + 1, P = M + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *s_tw = (C *)smem_raw;
+    C *S = s_tw + M / 2;
+    C *B = S + M * sw;  // rb rows of P
+    const int kx = blockIdx.x % MH;
+    int p;
+    const PlanPtrs &PP = item_plan(a.it, blockIdx.x / MH, p);
+    const int nin = a.nin, W = a.nout, nz = a.nz;
+    load_twiddles<LOG2M>(s_tw, (const C *)a.tw);
+    for (int e = threadIdx.x; e < M * nin; e += blockDim.x) S[(e / nin) * sw + e % nin] = Cx<R>::mk(0, 0);
+    __syncthreads();
+    const long q = blockIdx.x / MH;  // scratch slot
+    const C *in = (const C *)a.it.a1 + (q * MH + kx) * nin * nin;
+    for (int e = threadIdx.x; e < nin * nin; e += blockDim.x) {
+        const int zi = e / nin, yi = e % nin;
+        S[yi * sw + zi] = in[e];
+    }
+    __syncthreads();
+    // forward y on the nin z columns (natural in, bit-reversed ky rows out)
+    fft_dif<LOG2M>(S, nin, 1, sw, s_tw, false);
+    const R *khat = (const R *)PP.khat;
+    int pos0 = a.out_off % M;
+    if (pos0 < 0) pos0 += M;
+    for (int r0 = 0; r0 < M; r0 += rb) {
+        const int nr = min(rb, M - r0);
+        for (int e = threadIdx.x; e < nr * M; e += blockDim.x) {
+            const int l = e / M, c = e % M;
+            B[l * P + c] = c < nin ? S[(r0 + l) * sw + c] : Cx<R>::mk(0, 0);
+        }
+        __syncthreads();
+        fft_dif<LOG2M>(B, nr, P, 1, s_tw, false);  // forward z (bit-reversed kz)
+        for (int e = threadIdx.x; e < nr * M; e += blockDim.x) {
+            const int l = e / M, c = e % M;
+            const int ky0 = brev_bits(r0 + l, LOG2M), kz0 = brev_bits(c, LOG2M);
+            const int ky = ky0 < M - ky0 ? ky0 : M - ky0;
+            const int kz = kz0 < M - kz0 ? kz0 : M - kz0;
+            const R k = khat[((long)kx * MH + ky) * MH + kz];
+            C v = B[l * P + c];
+            v.x *= k;
+            v.y *= k;
+            B[l * P + c] = v;
+        }
+        __syncthreads();
+        fft_dit<LOG2M>(B, nr, P, 1, s_tw, true);  // inverse z (natural z)
+        for (int e = threadIdx.x; e < nr * nz; e += blockDim.x) {
+            const int l = e / nz, jz = e % nz;
+            const int pz = (pos0 + a.zrow[jz]) % M;
+            S[(r0 + l) * sw + jz] = B[l * P + pz];
+        }
+        __syncthreads();
+    }
+    // inverse y on the nz output columns (bit-reversed ky in, natural y out)
+    fft_dit<LOG2M>(S, nz, 1, sw, s_tw, true);
+    C *out = (C *)a.it.a4 + q * a.nz * a.blk;
+    for (int e = threadIdx.x; e < nz * W; e += blockDim.x) {
+        const int jz = e / W, yo = e % W;
+        const int py = (pos0 + yo) % M;
+        out[(long)jz * a.blk + kx * W + yo] = S[py * sw + jz];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // 64-point FFT of one line by 8 threads (radix 8 x 8, registers + one
 // exchange through the line's own shared-memory storage).  n = 8 n2 + n1,
 // k = k1 + 8 k2:  Y[n1][k1] = w64^(n1 k1) sum_n2 x[8 n2 + n1] w8^(n2 k1),
@@ -1041,6 +1116,7 @@ struct InvXPArgs {
     int blk;          // complex entries per (patch, z row) input block (16-byte multiple)
     int wait_tries;   // limit of the bounded wait for the block's bulk copy
     int skip_copy;    // test hook: issue no bulk copy, so the bounded wait runs out
+    int rb;           // k_inv_x_pruned: transformed rows per pass through the line buffer
 };
 
 __device__ __forceinline__ bool in_alpha(int c, int n, int ga) { return c >= -ga && c <= n + ga; }
@@ -1112,8 +1188,14 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
     }
     __syncthreads();
     const int nfft = nfft_s;
-    for (int e = threadIdx.x; e < nfft * M; e += blockDim.x) {
-        const int l = e / M, k = e % M, yi = rows[l];
+    TO *cl = (TO *)PP.cl + (long)p * nc * nc * nc;
+    TO *fp = (TO *)PP.fp + (long)p * 3 * a.npa * wa * wa;
+    const int kl = -s / 4;
+    // the transformed rows, a.rb at a time through the line buffer
+    for (int l0 = 0; l0 < nfft; l0 += a.rb) {
+    const int nl = min(a.rb, nfft - l0);
+    for (int e = threadIdx.x; e < nl * M; e += blockDim.x) {
+        const int l = e / M, k = e % M, yi = rows[l0 + l];
         C v;
         if (k < MH) {
             v = raw[k * W + yi];
@@ -1124,14 +1206,11 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
         buf[l * LP + k] = v;
     }
     __syncthreads();
-    if (LOG2M == 6) fft64_lines<C, R>(buf, nfft, LP, 1, M, tw, true, xs);
-    else fft_dif<LOG2M>(buf, nfft, LP, 1, tw, true);
-    TO *cl = (TO *)PP.cl + (long)p * nc * nc * nc;
-    TO *fp = (TO *)PP.fp + (long)p * 3 * a.npa * wa * wa;
-    const int kl = -s / 4;
+    if (LOG2M == 6) fft64_lines<C, R>(buf, nl, LP, 1, M, tw, true, xs);
+    else fft_dif<LOG2M>(buf, nl, LP, 1, tw, true);
     // outputs of the transformed rows
-    for (int e = threadIdx.x; e < nfft * W; e += blockDim.x) {
-        const int l = e / W, xi = e % W, yi = rows[l];
+    for (int e = threadIdx.x; e < nl * W; e += blockDim.x) {
+        const int l = e / W, xi = e % W, yi = rows[l0 + l];
         const int x = xi - s, y = yi - s;
         const bool yA = in_alpha(y, n, ga), yP = on_plane(y, n, ga, pl0), yC = (y & 3) == 0;
         const bool xA = in_alpha(x, n, ga), xP = on_plane(x, n, ga, pl0), xC = (x & 3) == 0;
@@ -1144,6 +1223,8 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
         if (w0) fp[(((long)(0 * a.npa + (z - pl0) / n)) * wa + (y + ga)) * wa + (x + ga)] = v;
         if (w1) fp[(((long)(1 * a.npa + (y - pl0) / n)) * wa + (z + ga)) * wa + (x + ga)] = v;
         if (w2) fp[(((long)(2 * a.npa + (x - pl0) / n)) * wa + (z + ga)) * wa + (y + ga)] = v;
+    }
+    __syncthreads();  // the buffer is refilled by the next pass
     }
     // rows that only need x on the face planes: direct sums over the half spectrum
     if (zA) {
@@ -2469,9 +2550,21 @@ inline size_t fft_smem_bytes(int M, int lines, int ls) {
 }
 
 // Local-convolution (patch) kernels in working precision R.
+// Largest dynamic shared memory of the 16-byte-entry M = 128 slab and
+// inverse-x launches: the 227 KB opt-in limit of an sm_100-class SM less room
+// for the kernels' static shared memory (the attribute cannot exceed the
+// difference).
+constexpr size_t kSlabRowsSmem = 225 * 1024;
+
 template <int LOG2M, typename R>
 void set_patch_attrs() {
     const int big = 200 * 1024;
+    if constexpr (LOG2M == 7 && !std::is_same<R, float>::value) {
+        cudaFuncSetAttribute(k_slab_rows<LOG2M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlabRowsSmem);
+        cudaFuncSetAttribute(k_inv_x_pruned<LOG2M, R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlabRowsSmem);
+        cudaFuncSetAttribute(k_fwd_x<LOG2M, double, true, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        return;
+    }
     cudaFuncSetAttribute(k_fwd_x<LOG2M, double, true, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_fwd_x<LOG2M, float, true, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_slab<LOG2M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -2541,8 +2634,17 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
                 k_slab64<R><<<grid, 256, sm, st>>>(a);
             }
         }
-        else
-            k_slab<LOG2M, R><<<nb * MH, 256, fft_smem_bytes<R>(M, M, M + 1), st>>>(a);
+        else {
+            if constexpr (LOG2M == 7 && sizeof(R) == 8) {  // 16-byte entries: row-streamed slab
+                const int sw = std::max(nin, nz);
+                const size_t csz = 2 * sizeof(R), fixed = ((size_t)M / 2 + (size_t)M * sw) * csz;
+                const int rb = (int)std::min<size_t>(M, (kSlabRowsSmem - fixed) / ((M + 1) * csz));
+                if (rb < 1) return cudaErrorInvalidValue;
+                k_slab_rows<LOG2M, R><<<nb * MH, 256, fixed + (size_t)rb * (M + 1) * csz, st>>>(a, sw, rb);
+            } else {
+                k_slab<LOG2M, R><<<nb * MH, 256, fft_smem_bytes<R>(M, M, M + 1), st>>>(a);
+            }
+        }
     }
     mark(pl, 3, st);
     {
@@ -2566,7 +2668,14 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
         }
         const int LPh = LOG2M == 6 ? Pitch64<R>::P : M + 1;
         const size_t xsn = (LOG2M == 6 && UseXs<R>::v) ? 32 * 72 : 0;
-        const size_t sm = ((size_t)M + (size_t)g.a4blk + (size_t)a.maxfft * LPh + xsn) * 2 * sizeof(R);
+        // transformed rows per pass: all of them unless the line buffer would
+        // not fit beside the staged block (16-byte entries at M = 128)
+        const size_t fixed = ((size_t)M + (size_t)g.a4blk + xsn) * 2 * sizeof(R);
+        const size_t line = (size_t)LPh * 2 * sizeof(R);
+        a.rb = a.maxfft;
+        if (fixed + (size_t)a.rb * line > kSlabRowsSmem) a.rb = (int)((kSlabRowsSmem - fixed) / line);
+        if (a.rb < 1) return cudaErrorInvalidValue;
+        const size_t sm = fixed + (size_t)a.rb * line;
         // local fields leave in the working precision: FP32 (split tier) or
         // double-float pairs (FP64 tier)
         if (LOG2M == 6) {
@@ -2609,6 +2718,8 @@ void configure_kernels() {
     set_patch_attrs<5, double>();
     set_patch_attrs<6, double>();
     set_patch_attrs<7, float>();
+    set_patch_attrs<7, double>();
+    set_patch_attrs<7, dfl>();
     set_cfft_attrs<dfl>();
     set_cfft_attrs<double>();
     configure_ring_gemm();
@@ -2658,9 +2769,11 @@ cudaError_t launch_patch_conv_group(const mlc_plan_s *pl, const Items &it, cudaS
     } else if (g.conv == CONV_DF) {  // double-float (tables tw_df, khat_df)
         if (g.log2M == 5) return run_patch_conv_t<5, dfl>(pl, it, f32, pl->tw_df, st);
         if (g.log2M == 6) return run_patch_conv_t<6, dfl>(pl, it, f32, pl->tw_df, st);
+        if (g.log2M == 7) return run_patch_conv_t<7, dfl>(pl, it, f32, pl->tw_df, st);
     } else {  // FP64 (tables tw, khat)
         if (g.log2M == 5) return run_patch_conv_t<5, double>(pl, it, f32, pl->tw, st);
         if (g.log2M == 6) return run_patch_conv_t<6, double>(pl, it, f32, pl->tw, st);
+        if (g.log2M == 7) return run_patch_conv_t<7, double>(pl, it, f32, pl->tw, st);
     }
     return cudaErrorInvalidValue;
 }

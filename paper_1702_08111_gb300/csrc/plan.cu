@@ -219,13 +219,10 @@ mlc_status derive_geometry(const mlc_params &pp, Geom &g) {
     }
     g.log2Mc = 0;
     g.Mhc = g.Mc / 2 + 1;
-    // patch sizes with a Dirichlet kernel instantiation; patch periods up to 64
-    // (128 in the split tiers, whose FP32 slab of 128 x 129 complex entries
-    // still fits in shared memory); n > 16 needs the FP32 patch charge of the
-    // moments in shared memory too
+    // patch sizes with a Dirichlet kernel instantiation; patch periods 32 to
+    // 128 (at 128 the FP64 and double-float slabs stream their rows)
     if (g.n != 4 && g.n != 8 && g.n != 12 && g.n != 16 && g.n != 24 && g.n != 32) return MLC_ERR_UNSUPPORTED;
-    if (g.M < 32 || g.M > (g.conv == CONV_F32 ? 128 : 64) || g.Mc > 512) return MLC_ERR_UNSUPPORTED;
-    if (g.n > 16 && g.conv != CONV_F32) return MLC_ERR_UNSUPPORTED;
+    if (g.M < 32 || g.M > 128 || g.Mc > 512) return MLC_ERR_UNSUPPORTED;
     g.S = (2 * g.b + 2) * (2 * g.b + 2);
     g.nc = (g.n + 2 * g.s) / 4 + 1;
     g.nzr = 0;

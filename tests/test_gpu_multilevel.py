@@ -169,22 +169,28 @@ ML_ROWS = [
 
 @pytest.fixture(scope="module")
 def smooth_512():
-    return I.paper_smooth_charge(512, dtype=np.float32), CF.smooth_potential_grid(512)
+    return I.paper_smooth_charge(512), CF.smooth_potential_grid(512)
 
 
 @pytest.mark.parametrize("row", ML_ROWS, ids=[r[0] for r in ML_ROWS])
 def test_paper_three_level_rows_512(torch_cuda, smooth_512, row):
     """Soft pin (order of magnitude, factor 5): 3-level MLC at N = 512, n = 32,
-    split tier, against the exact potential of the Sec. 7.1 smooth charge."""
+    FP64 tier, against the exact potential of the Sec. 7.1 smooth charge; the
+    split tier within 1e-6 of the FP64 tier."""
     from paper_1702_08111_gb300 import mlc
     torch = torch_cuda
     name, Q, s, b, mode, gb, P, paper = row
-    f, ex = smooth_512
-    plan = mlc.Plan(512, 32, s, P, Q, b=b, mode=mode, g_beta=gb, tier=SPLIT, levels=3)
-    phi = plan.solve(torch.from_numpy(f).cuda())
-    torch.cuda.synchronize()
-    plan.status()
-    err = relmax(phi.cpu().numpy(), ex)
-    del plan, phi
-    print(f"{name}: error {err:.5e}, paper {paper:.5e}, ratio {err / paper:.3f}")
+    f64, ex = smooth_512
+    out = {}
+    for tier in (FP64, SPLIT):
+        plan = mlc.Plan(512, 32, s, P, Q, b=b, mode=mode, g_beta=gb, tier=tier, levels=3)
+        f = f64.astype(np.float32) if tier == SPLIT else f64
+        out[tier] = plan.solve(torch.from_numpy(f).cuda()).cpu().numpy()
+        torch.cuda.synchronize()
+        plan.status()
+        del plan
+    err = relmax(out[FP64], ex)
+    dsplit = relmax(out[SPLIT], out[FP64])
+    print(f"{name}: error {err:.5e}, paper {paper:.5e}, ratio {err / paper:.3f}, split-fp64 {dsplit:.2e}")
     assert paper / 5 <= err <= 5 * paper, (name, err, paper)
+    assert dsplit <= 1e-6
