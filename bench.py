@@ -426,8 +426,9 @@ def run_extra(args, flush, stream, w, head_tier, phi_head, head_ms):
     """Secondary lines: the headline workload in the other tiers (plain FP64,
     double-float, split with double-float steps) with the three ratios to the
     plain FP64 solve, the split tier's batched form, the 128^3 FP64 solve
-    against the oracle, the 48-problem uneven batch, the 2000-request serving
-    stream and the allocation-free entry point."""
+    against the oracle, the paper's own n = 32 settings (two- and three-level),
+    the 48-problem uneven batch, the 2000-request serving stream and the
+    allocation-free entry point."""
     from oracle import closed_forms as CF
     f64 = w.charge().astype(np.float64)
     out = {}
@@ -454,9 +455,43 @@ def run_extra(args, flush, stream, w, head_tier, phi_head, head_ms):
     if "split" in out and "ms_per_step" in out["split"]:
         out["ratios_to_plain_fp64"]["split"] = round(out["fp64"]["ms_per_step"] / out["split"]["ms_per_step"], 3)
     out["fp64_128"] = run_fp64_128(args, flush, stream)
+    out["paper_params"] = run_paper_params(args, flush, stream)
     out["batch"] = run_batch(args, flush, stream)
     out["serving"] = run_serving(args)
     out["noalloc"] = run_noalloc(args, flush, stream)
+    return out
+
+
+def run_paper_params(args, flush, stream):
+    """The paper's own settings (Sec. 7: n = 32, H/R = 1/4, the Sec. 7.1 smooth
+    charge): the two-level 27-point solve with alpha = 1.75, beta = 3.25,
+    P = 4 (the Table 7 row) at 256^3 in the split and plain FP64 tiers, and
+    the three-level solve of the Table 9 row at 512^3 in the split tier;
+    Mpoints/s and the scaled max error against the closed form."""
+    import torch
+    from oracle import closed_forms as CF
+    from paper_1702_08111_gb300 import mlc
+    out = {}
+    steps = max(3, args.steps // 4)
+    kw = dict(b=3, g_beta=36)
+    cases = [("n32_256_split", 256, "split", 2, 1.96490e-7), ("n32_256_fp64", 256, "fp64", 2, 1.96490e-7),
+             ("n32_512_3level_split", 512, "split", 3, 1.0782e-6)]
+    exact = {}
+    for name, N, tier, levels, paper in cases:
+        f64 = I.paper_smooth_charge(N)
+        f = torch.from_numpy(f64.astype(np.float32) if tier in ("split", "split_df") else f64).cuda()
+        plan = mlc.Plan(N, 32, 24, 4, 6, tier=TIER_IDS[tier], levels=levels, **kw)
+        phi = torch.empty((N,) * 3, dtype=torch.float64, device="cuda")
+        ms, pl = time_plan(plan, f, phi, steps, 3, flush, stream, 1, per_launch_steps=1)
+        if N not in exact:
+            exact[N] = CF.smooth_potential_grid(N)
+        ph = phi.cpu().numpy()
+        err = float(np.abs(ph - exact[N]).max() / np.abs(exact[N]).max())
+        out[name] = {"N": N, "n": 32, "s": 24, "g_beta": 36, "P": 4, "Q": 6, "levels": levels, "tier": tier,
+                     "ms_per_step": round(ms, 4), "value": round(float(N) ** 3 / (ms * 1e-3) / 1e6, 2),
+                     "unit": "Mpoints/s", "max_rel_err_vs_closed_form": err, "paper_error": paper,
+                     "per_launch_ms": {k: round(v, 4) for k, v in pl.items()}}
+        del plan, f, phi, ph
     return out
 
 

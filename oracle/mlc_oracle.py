@@ -48,7 +48,7 @@ R6  phi^H is evaluated on the coarse nodes [-b, N/4 + b]^3, the nodes the
     interpolation reads.
 R7  Delta^H is the same Mehrstellen operator at spacing H = C h applied to the
     fine field sampled at coarse nodes; G^H = H^{-1} G^{h=1}.
-R8  Multilevel MLC (Sec. 5), levels > 2: with every level covering the whole
+R16 Multilevel MLC (Sec. 5), levels > 2: with every level covering the whole
     grid, chi-tilde vanishes, and the level-l charge of patch i is the coarse
     charge F^{h_l} (the sum of the finer patches' contributions, eq. FDLD)
     restricted to the patch, as the fine charge is in Sec. 4.  The downward
@@ -108,7 +108,7 @@ class Params:
     zeta: int = 2
     levels: int = 2          # Sec. 5: number of levels (2: the two-level algorithm of Sec. 4)
     h_level: float | None = None   # mesh spacing of this level (default 1/N, the finest level)
-    correction: bool = True  # add C2 h^2 f at the end (eq. mcapplicationfulldiscr); R8
+    correction: bool = True  # add C2 h^2 f at the end (eq. mcapplicationfulldiscr); R16
 
     def __post_init__(self):
         if self.Q not in STENCIL_B:
@@ -602,7 +602,7 @@ def mlc_solve(prm: Params, f_closed: np.ndarray, G1: np.ndarray | None = None, s
     olo, ohi = prm.phih_extent
     no = ohi - olo + 1
     if prm.levels > 2:
-        # Sec. 5 (R8): the coarse solve is itself an MLC solve of F^H
+        # Sec. 5 (R16): the coarse solve is itself an MLC solve of F^H
         phiH = coarse_level_solve(prm, FH, G1)
     else:
         phiH = direct_sum(G1, FH, (flo,) * 3, (olo,) * 3, (no,) * 3, H * H)
@@ -685,7 +685,7 @@ def mlc_solve(prm: Params, f_closed: np.ndarray, G1: np.ndarray | None = None, s
 
 
 def coarse_level_params(prm: Params):
-    """Sec. 5 (R8): origin c0 (in coarse nodes of this level) and parameters
+    """Sec. 5 (R16): origin c0 (in coarse nodes of this level) and parameters
     of the next coarser level's MLC problem."""
     flo, fhi = prm.fh_extent
     olo, ohi = prm.phih_extent
@@ -700,7 +700,7 @@ def coarse_level_params(prm: Params):
 
 
 def coarse_level_solve(prm: Params, FH: np.ndarray, G1: np.ndarray) -> np.ndarray:
-    """phi^H on [olo, ohi]^3 by the MLC solve of F^H on the coarser level (R8)."""
+    """phi^H on [olo, ohi]^3 by the MLC solve of F^H on the coarser level (R16)."""
     flo, _ = prm.fh_extent
     olo, ohi = prm.phih_extent
     c0, child = coarse_level_params(prm)

@@ -2745,6 +2745,7 @@ void configure_kernels() {
 }
 
 cudaError_t launch_moments(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
+    NvtxRange nvtx("mlc:moments");
     const Geom &g = pl->g;
     const int nb = g.n + 1;
     // charge planes staged at once: the whole patch while it takes <= 48 KB
@@ -2760,6 +2761,7 @@ cudaError_t launch_moments(const mlc_plan_s *pl, const Items &it, cudaStream_t s
 // The three local-convolution launches for one launch group of items (its
 // scratch in it.a1 / it.a4).
 cudaError_t launch_patch_conv_group(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
+    NvtxRange nvtx("mlc:local_convolutions");
     const Geom &g = pl->g;
     const bool f32 = g.f32in;
     if (g.conv == CONV_F32) {  // split tiers: FP32 (tables tw_f, khat_f)
@@ -2831,6 +2833,7 @@ const void *ring_moments(const mlc_plan_s *pl) {
 }
 
 cudaError_t launch_resid(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
+    NvtxRange nvtx("mlc:residuals");
     const Geom &g = pl->g;
     ResArgs a{};
     a.it = it; a.n = g.n; a.s = g.s; a.ga = g.ga; a.b = g.b;
@@ -2851,6 +2854,7 @@ cudaError_t launch_resid(const mlc_plan_s *pl, const Items &it, cudaStream_t st)
 }
 
 cudaError_t launch_assemble(const mlc_plan_s *pl, cudaStream_t st) {
+    NvtxRange nvtx("mlc:coarse_charge");
     const Geom &g = pl->g;
     AsmArgs a{};
     a.cl = pl->cl; a.FH = pl->FH;
@@ -2927,6 +2931,7 @@ cudaError_t run_coarse_level(const mlc_plan_s *pl, cudaStream_t st) {
 }
 
 cudaError_t launch_coarse(const mlc_plan_s *pl, cudaStream_t st) {
+    NvtxRange nvtx("mlc:coarse_solve");
     if (pl->child) return run_coarse_level(pl, st);
     if (pl->g.fine == FINE_F64)  // coarse FFTs in FP64
         return run_coarse_t<double>(pl, pl->khat_c, pl->tw_c, st);
@@ -2934,6 +2939,7 @@ cudaError_t launch_coarse(const mlc_plan_s *pl, cudaStream_t st) {
 }
 
 cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st) {
+    NvtxRange nvtx("mlc:boundary");
     const Geom &g = pl->g;
     BndArgs a{};
     a.phiH = pl->phiH; a.resid = pl->resid;
@@ -2997,6 +3003,7 @@ cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st) {
 }
 
 cudaError_t launch_dirichlet(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
+    NvtxRange nvtx("mlc:dirichlet");
     const Geom &g = pl->g;
     DirArgs a{};
     a.it = it; a.n = g.n;

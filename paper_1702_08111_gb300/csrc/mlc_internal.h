@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <cstring>
@@ -184,6 +185,17 @@ struct mlc_plan_s {
 };
 
 namespace mlc {
+
+// NVTX range around the host code that enqueues one step (a profiler shows
+// the kernels each step launched under its name, e.g. ncu --nvtx
+// --nvtx-include "mlc:boundary/"); costs a function-pointer test when no tool
+// is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // kernels.cu
 // Record the timing event of launch slot k (no-op unless timing is enabled).

@@ -877,6 +877,7 @@ mlc_status mlc_solve(mlc_plan_t pl, const void *f, void *phi, void *stream) {
     if (!pl || !f || !phi || f == phi) return MLC_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     TRY(prepare_solve(pl));  // first solve: the plan's own scratch and side stream
+    NvtxRange nvtx(pl->correction ? "mlc:solve" : "mlc:coarser_level_solve");
     void *scr = pl->user_scratch ? pl->user_scratch : pl->scratch;
     if (pl->hptrs.f != f || pl->hptrs.phi != phi) {
         TRY_CUDA(launch_set_ptrs(pl->dptrs, f, (double *)phi, st));

@@ -229,9 +229,12 @@ def test_invalid_arguments(torch_cuda):
         with pytest.raises(mlc.MLCError) as e:
             mlc.Plan(**kw)
         assert e.value.status == 1
-    with pytest.raises(mlc.MLCError) as e:
-        mlc.Plan(N=32, n=32, s=32)
-    assert e.value.status == 2
+    # legal for the method, not built: a local period above 128, a patch size
+    # without a Dirichlet kernel
+    for kw in [dict(N=64, n=32, s=36), dict(N=40, n=20, s=8)]:
+        with pytest.raises(mlc.MLCError) as e:
+            mlc.Plan(**kw)
+        assert e.value.status == 2
 
 
 # ------------------------------------------------------------------ split tiers
