@@ -16,6 +16,7 @@ collective): weak scaling.
 from __future__ import annotations
 
 import argparse
+from types import SimpleNamespace
 import json
 import os
 import subprocess
@@ -307,6 +308,29 @@ def roofline_for(w, plan, per_launch, tier, traffic=None):
         pipe = "FP64 pipe" if tier == "fp64" else "FP32 pipe"
         sched = {"fp64": "FP64 radix-8x8", "df": "double-float radix-8x8"}.get(tier, "FP32 radix-2 register")
         unit_name = "(patch, kx) slab"
+    elif dom == "conv_slab" and M == 128:
+        # the 128-point slabs (n = 24, 32): shared-memory radix-2 stages, 8
+        # instructions per butterfly (4 adds, 2 multiplies + 2 FMAs for the
+        # twiddle), no pruning of the forward passes; the FP32 kernel (k_slab)
+        # runs the inverse y on all W output columns, the 16-byte one
+        # (k_slab_rows) on the nz columns read later
+        nin = w.n + 1
+        nz = slab_rows(w, info.g_alpha)
+        W = w.n + 2 * w.s + 1
+        line_flops = 5.0 * M * np.log2(M)
+        nominal = (nin + 2 * M + nz) * line_flops + 2.0 * M * M
+        line_inst = (M // 2) * np.log2(M) * 8
+        inv_y = W if tier in ("split", "split_df") else nz
+        inst = (nin + 2 * M + inv_y) * line_inst + 2.0 * M * M * (DF_MUL_INST if tier == "df" else 1)
+        if tier == "df":
+            inst = (nin + 2 * M + inv_y) * (M // 2) * np.log2(M) * (4 * DF_ADD_INST + 4 * DF_MUL_INST) \
+                + 2.0 * M * M * DF_MUL_INST
+        nlaunch = -(-NP // CONV_CHUNK)
+        units, pipe_rate = min(NP, CONV_CHUNK) * Mh, (FP64_INST_PER_S if tier == "fp64" else FP32_LANE_INST_PER_S)
+        pipe = "FP64 pipe" if tier == "fp64" else "FP32 pipe"
+        sched = {"fp64": "FP64 shared-memory radix-2 (row-streamed)",
+                 "df": "double-float shared-memory radix-2 (row-streamed)"}.get(tier, "FP32 shared-memory radix-2")
+        unit_name = "(patch, kx) slab"
     elif dom == "dirichlet" and w.n == 16:
         nominal, inst = dirichlet_counts(w.n, w.Q)
         if not fine64:
@@ -483,6 +507,8 @@ def run_paper_params(args, flush, stream):
         plan = mlc.Plan(N, 32, 24, 4, 6, tier=TIER_IDS[tier], levels=levels, **kw)
         phi = torch.empty((N,) * 3, dtype=torch.float64, device="cuda")
         ms, pl = time_plan(plan, f, phi, steps, 3, flush, stream, 1, per_launch_steps=1)
+        wl = SimpleNamespace(N=N, n=32, s=24, Q=6, name=name)
+        roof = roofline_for(wl, plan, pl, tier)
         if N not in exact:
             exact[N] = CF.smooth_potential_grid(N)
         ph = phi.cpu().numpy()
@@ -490,6 +516,7 @@ def run_paper_params(args, flush, stream):
         out[name] = {"N": N, "n": 32, "s": 24, "g_beta": 36, "P": 4, "Q": 6, "levels": levels, "tier": tier,
                      "ms_per_step": round(ms, 4), "value": round(float(N) ** 3 / (ms * 1e-3) / 1e6, 2),
                      "unit": "Mpoints/s", "max_rel_err_vs_closed_form": err, "paper_error": paper,
+                     "roofline": roof,
                      "per_launch_ms": {k: round(v, 4) for k, v in pl.items()}}
         del plan, f, phi, ph
     return out

@@ -995,6 +995,206 @@ __global__ void __launch_bounds__(64, 6) k_slab64r(SlabArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// 128-point lines in FP32 by 8-lane groups, radix 16 x 8: with n = 8 n2 + n1
+// and k = k1 + 16 k2, lane t = n1 forms Y[t][k1] = w128^(t k1) sum_n2
+// x[8 n2 + t] w16^(n2 k1) in registers; after one exchange through the
+// group's scratch, lane t takes k1 = t and t + 8 and forms X[k1 + 16 k2] =
+// sum_n1 Y[n1][k1] w8^(n1 k2).  Lane t holds x[8 j + t] in v[j] on entry and
+// X[8 j + t] in v[j] on exit (natural order both ways), so a forward
+// transform, a pointwise product and an inverse transform chain in registers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 w16mul(float2 d, int j, bool inv) {
+    // exp(-+ 2 pi i j / 16), j a compile-time constant after unrolling
+    constexpr float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f, c2 = 0.70710678118654752440f;
+    const float cr[8] = {1.f, c1, c2, s1, 0.f, -s1, -c2, -c1};
+    const float si[8] = {0.f, s1, c2, c1, 1.f, c1, c2, s1};
+    if (j == 0) return d;
+    const float wr = cr[j], wi = inv ? si[j] : -si[j];
+    return make_float2(fmaf(d.x, wr, -d.y * wi), fmaf(d.x, wi, d.y * wr));
+}
+
+// 16-point DFT in registers, natural order in and out; SPARSE: v[8..15] zero.
+template <bool SPARSE>
+__device__ __forceinline__ void dft16(float2 (&v)[16], bool inv) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if (SPARSE) {
+            v[i + 8] = w16mul(v[i], i, inv);
+        } else {
+            const float2 a = v[i], b = v[i + 8];
+            v[i] = make_float2(a.x + b.x, a.y + b.y);
+            v[i + 8] = w16mul(make_float2(a.x - b.x, a.y - b.y), i, inv);
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < 16; g += 8)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 a = v[g + i], b = v[g + i + 4];
+            v[g + i] = make_float2(a.x + b.x, a.y + b.y);
+            v[g + i + 4] = w16mul(make_float2(a.x - b.x, a.y - b.y), 2 * i, inv);
+        }
+#pragma unroll
+    for (int g = 0; g < 16; g += 4)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const float2 a = v[g + i], b = v[g + i + 2];
+            v[g + i] = make_float2(a.x + b.x, a.y + b.y);
+            v[g + i + 2] = w16mul(make_float2(a.x - b.x, a.y - b.y), 4 * i, inv);
+        }
+#pragma unroll
+    for (int g = 0; g < 16; g += 2) {
+        const float2 a = v[g], b = v[g + 1];
+        v[g] = make_float2(a.x + b.x, a.y + b.y);
+        v[g + 1] = make_float2(a.x - b.x, a.y - b.y);
+    }
+    // bit-reversed (4 bits) -> natural
+    float2 t;
+    t = v[1]; v[1] = v[8]; v[8] = t;
+    t = v[2]; v[2] = v[4]; v[4] = t;
+    t = v[3]; v[3] = v[12]; v[12] = t;
+    t = v[5]; v[5] = v[10]; v[10] = t;
+    t = v[7]; v[7] = v[14]; v[14] = t;
+    t = v[11]; v[11] = v[13]; v[13] = t;
+}
+
+// One 128-point line transform by an 8-lane group (layout above).  tw: M
+// twiddles exp(-2 pi i j / 128) in shared memory; xs: the group's scratch
+// (16 x 9 entries); gm: the group's lane mask.
+template <bool SPARSE>
+__device__ __forceinline__ void line128_regs(float2 (&v)[16], int t, const float2 *tw, bool inv, float2 *xs,
+                                             unsigned gm) {
+    dft16<SPARSE>(v, inv);
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) {
+        float2 w = tw[(t * k1) & 127];
+        if (inv) w.y = -w.y;
+        v[k1] = cmul(v[k1], w);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) xs[9 * k1 + t] = v[k1];
+    __syncwarp(gm);
+    float2 a[8], b[8];
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) {
+        a[n1] = xs[9 * t + n1];
+        b[n1] = xs[9 * (t + 8) + n1];
+    }
+    __syncwarp(gm);
+    dft8<float2, float>(a, inv);
+    dft8<float2, float>(b, inv);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) {
+        v[2 * k2] = a[k2];
+        v[2 * k2 + 1] = b[k2];
+    }
+}
+
+// Split-tier slab for M = 128 (same contract as k_slab): 8-lane groups take
+// one line each (forward y on the nin input z rows; per ky column forward z,
+// kernel product and inverse z in registers, storing only the z positions
+// read later, into compact rows in position order; inverse y on those rows);
+// the slab holds max(nin, nz) rows.  Requires nin <= 64, W <= 128.
+__global__ void __launch_bounds__(256, 2) k_slab128r(SlabArgs a) {
+    constexpr int M = 128, MH = 65, P = 129;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *tw = (float2 *)smem_raw;                 // M twiddles
+    float2 *xs_all = tw + M;                         // 32 groups x 144
+    float2 *S = xs_all + 32 * 144;                   // S[row][ky], pitch P
+    __shared__ int rowc[128];                        // output z row jz -> compact row
+    __shared__ unsigned long long mask_s[2];         // output z positions
+    const int nin = a.nin, W = a.nout, nz = a.nz;
+    const int grp = threadIdx.x >> 3, t = threadIdx.x & 7, ngrp = blockDim.x >> 3;
+    const unsigned gm = 0xffu << (threadIdx.x & 24);
+    float2 *xs = xs_all + grp * 144;
+    const float2 *twg = (const float2 *)a.tw;        // M/2 entries; w^(j+64) = -w^j
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        float2 w = twg[j & 63];
+        if (j >= 64) { w.x = -w.x; w.y = -w.y; }
+        tw[j] = w;
+    }
+    if (threadIdx.x < 2) {
+        unsigned long long m = 0;
+        for (int j = 0; j < nz; ++j) {
+            const int pz = (a.out_off + a.zrow[j]) & (M - 1);
+            if ((pz >> 6) == (int)threadIdx.x) m |= 1ull << (pz & 63);
+        }
+        mask_s[threadIdx.x] = m;
+    }
+    __syncthreads();
+    const unsigned long long m0 = mask_s[0], m1 = mask_s[1];
+    const int c0 = __popcll(m0);
+    // compact row of output position pos (position order)
+    auto crow = [&](int pos) -> int {
+        return pos < 64 ? __popcll(m0 & ((1ull << pos) - 1ull)) : c0 + __popcll(m1 & ((1ull << (pos - 64)) - 1ull));
+    };
+    for (int j = threadIdx.x; j < nz; j += blockDim.x) rowc[j] = crow((a.out_off + a.zrow[j]) & (M - 1));
+    __syncthreads();
+    const int nunits = a.it.nitems * MH;
+    for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
+        const int kx = unit % MH;
+        int p;
+        const PlanPtrs &PP = item_plan(a.it, unit / MH, p);
+        const long q = unit / MH;  // scratch slot
+        const float2 *in = (const float2 *)a.it.a1 + (q * MH + kx) * nin * nin;
+        float2 v[16];
+        // forward y: group g takes input z row g (natural ky columns out)
+        for (int r = grp; r < nin; r += ngrp) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int pos = 8 * j + t;
+                v[j] = (j < 8 && pos < nin) ? in[r * nin + pos] : make_float2(0.f, 0.f);
+            }
+            line128_regs<true>(v, t, tw, false, xs, gm);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) S[r * P + 8 * j + t] = v[j];
+        }
+        __syncthreads();
+        // ky column c: forward z, kernel product, inverse z
+        for (int c = grp; c < M; c += ngrp) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int pos = 8 * j + t;
+                v[j] = (j < 8 && pos < nin) ? S[pos * P + c] : make_float2(0.f, 0.f);
+            }
+            line128_regs<true>(v, t, tw, false, xs, gm);
+            const float *kk = (const float *)PP.khat + ((long)kx * MH + (c < M - c ? c : M - c)) * MH;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int kz0 = 8 * j + t, kz = kz0 < M - kz0 ? kz0 : M - kz0;
+                const float k = kk[kz];
+                v[j].x *= k;
+                v[j].y *= k;
+            }
+            line128_regs<false>(v, t, tw, true, xs, gm);
+            // the group's loads of column c are done (exchange above)
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int pos = 8 * j + t;
+                const bool need = pos < 64 ? ((m0 >> pos) & 1ull) : ((m1 >> (pos - 64)) & 1ull);
+                if (need) S[crow(pos) * P + c] = v[j];
+            }
+        }
+        __syncthreads();
+        // inverse y on the output rows (compact row r)
+        for (int r = grp; r < nz; r += ngrp) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = S[r * P + 8 * j + t];
+            line128_regs<false>(v, t, tw, true, xs, gm);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) S[r * P + 8 * j + t] = v[j];
+        }
+        __syncthreads();
+        float2 *out = (float2 *)a.it.a4 + q * nz * a.blk + kx * W;
+        for (int e = threadIdx.x; e < nz * W; e += blockDim.x) {
+            const int jz = e / W, yo = e - jz * W;
+            out[(long)jz * a.blk + yo] = S[rowc[jz] * P + ((a.out_off + yo) & (M - 1))];
+        }
+        __syncthreads();  // S is rewritten by the next unit
+    }
+}
+
 // Lane shuffles of complex values within the 8-thread line group.
 __device__ __forceinline__ float2 shfl8(float2 v, int src) {
     return make_float2(__shfl_sync(0xffffffffu, v.x, src, 8), __shfl_sync(0xffffffffu, v.y, src, 8));
@@ -2163,15 +2363,12 @@ __global__ void __launch_bounds__(256, NN > 16 ? 1 : (std::is_same<T, double>::v
                     const int k = 2 * j + 1 + par;  // output index 1..m
                     if (k > m) break;
                     const T *row = Sh + (k - 1) * h;
-                    // h products summed as a balanced tree: independent chains
-                    T pr[h];
+                    // h products accumulated by fused multiply-adds in four
+                    // independent chains (t mod 4), then summed
+                    T acc[4] = {FT<T>::zero(), FT<T>::zero(), FT<T>::zero(), FT<T>::zero()};
 #pragma unroll
-                    for (int t = 1; t <= h; ++t) pr[t - 1] = row[t - 1] * u[t];
-#pragma unroll
-                    for (int w = 1; w < h; w *= 2)
-#pragma unroll
-                        for (int t = 0; t + w < h; t += 2 * w) pr[t] = pr[t] + pr[t + w];
-                    T v = pr[0];
+                    for (int t = 1; t <= h; ++t) acc[(t - 1) & 3] = FT<T>::fma(row[t - 1], u[t], acc[(t - 1) & 3]);
+                    T v = (acc[0] + acc[1]) + (acc[2] + acc[3]);
                     if (pass == 2) v = v * lam[base + (k - 1) * str];
                     X[base + (k - 1) * str] = v;
                 }
@@ -2635,7 +2832,19 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
             }
         }
         else {
-            if constexpr (LOG2M == 7 && sizeof(R) == 8) {  // 16-byte entries: row-streamed slab
+            if constexpr (LOG2M == 7 && std::is_same<R, float>::value) {  // FP32: register lines
+                const size_t sm = ((size_t)M + 32 * 144 + (size_t)std::max(nin, nz) * (M + 1)) * sizeof(float2);
+                int gr = nb * MH;
+                if (it.persist) {
+                    int dev = 0, nsm = 0, occ = 0;
+                    cudaGetDevice(&dev);
+                    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_slab128r, 256, sm);
+                    const int wave = nsm * (occ > 0 ? occ : 1);
+                    gr = gr < wave ? gr : wave;
+                }
+                k_slab128r<<<gr, 256, sm, st>>>(a);
+            } else if constexpr (LOG2M == 7 && sizeof(R) == 8) {  // 16-byte entries: row-streamed slab
                 const int sw = std::max(nin, nz);
                 const size_t csz = 2 * sizeof(R), fixed = ((size_t)M / 2 + (size_t)M * sw) * csz;
                 const int rb = (int)std::min<size_t>(M, (kSlabRowsSmem - fixed) / ((M + 1) * csz));
@@ -2718,6 +2927,7 @@ void configure_kernels() {
     set_patch_attrs<5, double>();
     set_patch_attrs<6, double>();
     set_patch_attrs<7, float>();
+    cudaFuncSetAttribute(k_slab128r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlabRowsSmem);
     set_patch_attrs<7, double>();
     set_patch_attrs<7, dfl>();
     set_cfft_attrs<dfl>();
