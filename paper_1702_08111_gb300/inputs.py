@@ -120,9 +120,12 @@ class Workload:
     C: int = 4
     bumps: Bumps = field(default=None, repr=False)
     charge_dtype: str = "f64"
+    charge_kind: str = "bumps"  # or "paper_smooth" (Sec. 7.1 charge, no random draw)
 
     def charge(self, nodes: int | None = None) -> np.ndarray:
         dt = np.float32 if self.charge_dtype == "f32" else np.float64
+        if self.charge_kind == "paper_smooth":
+            return paper_smooth_charge(self.N, nodes=nodes, dtype=dt)
         return sample_bumps(self.N, self.bumps, nodes=nodes, dtype=dt)
 
 
@@ -133,6 +136,8 @@ def workload(name: str) -> Workload:
     bumps8_128:     128^3, 512 patches of 16^3, support 16, Q=4; 8 bumps from seed 1.
     bumps32_256_q6: 256^3, 4096 patches of 16^3, support 16, Q=6; 32 bumps from seed 3, FP32 charge.
     bumps16_128_q6: 128^3, 512 patches of the same geometry, 16 bumps from seed 3, FP32 charge.
+    paper_smooth_128_n32: 128^3, 64 patches of 32^3 (the paper's n), support 24, Q=6, the
+                    Sec. 7.1 smooth charge in FP32 (profiling case of the 128-point kernels).
     """
     if name == "single_bump_32":
         return Workload(name, 32, 8, 8, 4, bumps=single_bump())
@@ -143,6 +148,8 @@ def workload(name: str) -> Workload:
     if name == "bumps16_128_q6":
         # profiling case: the per-patch kernels of bumps32_256_q6 on 512 patches
         return Workload(name, 128, 16, 16, 6, bumps=draw_bumps(16, 3), charge_dtype="f32")
+    if name == "paper_smooth_128_n32":
+        return Workload(name, 128, 32, 24, 6, charge_dtype="f32", charge_kind="paper_smooth")
     if name == "bumps8_64_q6":
         # reduced-size case with the 27-point operator: same patch geometry as bumps32_256_q6
         return Workload(name, 64, 16, 16, 6, bumps=draw_bumps(8, 7))
