@@ -2196,6 +2196,74 @@ __device__ __forceinline__ void dst15_fast(T (&x)[15], const T (&sv)[9]) {
     for (int k = 1; k < 16; ++k) x[k - 1] = y[k];
 }
 
+// sin(pi m / 32) for integer m as (index into sv[0..16] = sin(pi i / 32), sign),
+// resolved at compile time.
+__host__ __device__ constexpr int sin32_idx(int m) {
+    return ((m % 64 + 64) % 64) % 32 <= 16 ? ((m % 64 + 64) % 64) % 32 : 32 - ((m % 64 + 64) % 64) % 32;
+}
+__host__ __device__ constexpr bool sin32_neg(int m) { return ((m % 64 + 64) % 64) >= 32; }
+template <int M32, typename T>
+__device__ __forceinline__ T fma_sin32(T v, T acc, const T (&sv)[17]) {
+    return FT<T>::fma(sv[sin32_idx(M32)], sin32_neg(M32) ? -v : v, acc);
+}
+
+// DST-I of 31 values (n = 32), y_k = sum_t x_t sin(pi k t / 32), by one
+// symmetric split: with s_t = x_t + x_{32-t} and d_t = x_t - x_{32-t}
+// (t = 1..15), the even outputs are the 15-point DST-I of d (dst15_fast,
+// sin(pi j t / 16) = sin(pi 2 j t / 32)), and the odd outputs pair up as
+// y_{2j+1} = P_j + Q_j + (-1)^j x_16, y_{31-2j} = P_j - Q_j - (-1)^j x_16
+// (j = 0..7) with P_j, Q_j the sums of s_t sin(pi (2j+1) t / 32) over odd and
+// even t (sin(pi (32 - k) t / 32) = -(-1)^t sin(pi k t / 32)).  120 fused
+// products and about 130 sums instead of 496 products for the direct sums.
+// x[t-1] = x_t in, y_k out in x[k-1].
+template <int J, typename T>
+__device__ __forceinline__ void dst31_odd_pair(const T (&sp)[16], T c, const T (&sv)[17], T (&x)[31]) {
+    T P = FT<T>::zero(), Q = FT<T>::zero();
+    P = fma_sin32<(2 * J + 1) * 1>(sp[1], P, sv);
+    P = fma_sin32<(2 * J + 1) * 3>(sp[3], P, sv);
+    P = fma_sin32<(2 * J + 1) * 5>(sp[5], P, sv);
+    P = fma_sin32<(2 * J + 1) * 7>(sp[7], P, sv);
+    P = fma_sin32<(2 * J + 1) * 9>(sp[9], P, sv);
+    P = fma_sin32<(2 * J + 1) * 11>(sp[11], P, sv);
+    P = fma_sin32<(2 * J + 1) * 13>(sp[13], P, sv);
+    P = fma_sin32<(2 * J + 1) * 15>(sp[15], P, sv);
+    Q = fma_sin32<(2 * J + 1) * 2>(sp[2], Q, sv);
+    Q = fma_sin32<(2 * J + 1) * 4>(sp[4], Q, sv);
+    Q = fma_sin32<(2 * J + 1) * 6>(sp[6], Q, sv);
+    Q = fma_sin32<(2 * J + 1) * 8>(sp[8], Q, sv);
+    Q = fma_sin32<(2 * J + 1) * 10>(sp[10], Q, sv);
+    Q = fma_sin32<(2 * J + 1) * 12>(sp[12], Q, sv);
+    Q = fma_sin32<(2 * J + 1) * 14>(sp[14], Q, sv);
+    const T cs = (J & 1) ? -c : c;
+    x[2 * J] = (P + Q) + cs;       // y_{2J+1}
+    x[30 - 2 * J] = (P - Q) - cs;  // y_{31-2J}
+}
+template <typename T>
+__device__ __forceinline__ void dst31_fast(T (&x)[31], const T (&sv)[17]) {
+    T sp[16], dm[15];
+#pragma unroll
+    for (int t = 1; t < 16; ++t) {
+        sp[t] = x[t - 1] + x[31 - t];
+        dm[t - 1] = x[t - 1] - x[31 - t];
+    }
+    sp[0] = FT<T>::zero();
+    const T c = x[15];
+    dst31_odd_pair<0>(sp, c, sv, x);
+    dst31_odd_pair<1>(sp, c, sv, x);
+    dst31_odd_pair<2>(sp, c, sv, x);
+    dst31_odd_pair<3>(sp, c, sv, x);
+    dst31_odd_pair<4>(sp, c, sv, x);
+    dst31_odd_pair<5>(sp, c, sv, x);
+    dst31_odd_pair<6>(sp, c, sv, x);
+    dst31_odd_pair<7>(sp, c, sv, x);
+    T s16[9];
+#pragma unroll
+    for (int i = 0; i <= 8; ++i) s16[i] = sv[2 * i];  // sin(pi i / 16)
+    dst15_fast(dm, s16);
+#pragma unroll
+    for (int j = 1; j <= 15; ++j) x[2 * j - 1] = dm[j - 1];  // y_{2j}
+}
+
 // Local Dirichlet solve of one patch (Sec. 4, final step): the (Q-th order)
 // stencil problem on the closed patch with boundary data phi^B, by DST-I in
 // all three axes, then phi = u + (h^2/12) f.  T: the arithmetic between the
@@ -2326,6 +2394,33 @@ __global__ void __launch_bounds__(256, NN > 16 ? 1 : (std::is_same<T, double>::v
                 }
 #pragma unroll
                 for (int t = 0; t < 15; ++t) X[base + t * str] = x[t];
+            }
+            __syncthreads();
+        }
+    } else if constexpr (NN == 32) {
+        // n = 32: one thread per line with the split DST (dst31_fast)
+        T sv[17];
+        sv[0] = FT<T>::zero();
+#pragma unroll
+        for (int i = 1; i <= 16; ++i) sv[i] = Sh[i - 1];  // sin(pi i / 32)
+        for (int pass = 0; pass < 6; ++pass) {
+            const int axis = 2 - (pass % 3);
+            for (int l = threadIdx.x; l < m * m; l += blockDim.x) {
+                const int q1 = l % m, q0 = l / m;
+                int base, str;
+                if (axis == 2) { base = (q0 * m + q1) * m; str = 1; }
+                else if (axis == 1) { base = q0 * m * m + q1; str = m; }
+                else { base = q0 * m + q1; str = m * m; }
+                T x[31];
+#pragma unroll
+                for (int t = 0; t < 31; ++t) x[t] = FT<T>::rn(X[base + t * str]);
+                dst31_fast(x, sv);
+                if (pass == 2) {
+#pragma unroll
+                    for (int t = 0; t < 31; ++t) x[t] = x[t] * lam[base + t * str];
+                }
+#pragma unroll
+                for (int t = 0; t < 31; ++t) X[base + t * str] = x[t];
             }
             __syncthreads();
         }
