@@ -255,13 +255,20 @@ def slab_rows(w, ga):
 
 def dirichlet_counts(n, Q):
     """Algorithmic FLOPs and instructions of the Dirichlet step for one patch
-    of n = 16: the right-hand side f - Delta^h(boundary data) (one FMA per
-    boundary term with a nonzero weight), 6 passes of 15^2 lines of the
-    15-point split-radix DST-I (29 products + 68 sums each, no FMA), the
-    inverse eigenvalue scaling (15^3 products) and the Mehrstellen correction
-    u + h^2/12 f (one FMA per node of the patch)."""
+    (n = 16 or 32): the right-hand side f - Delta^h(boundary data) (one FMA
+    per boundary term with a nonzero weight), 6 passes of (n-1)^2 lines of
+    the split DST-I (n = 16: 29 products + 68 sums per line, no FMA; n = 32:
+    15 + 15 sums and differences, the 15-point DST of the differences, and
+    8 pairs of odd outputs of 15 FMAs + 4 sums each), the inverse eigenvalue
+    scaling ((n-1)^3 products) and the Mehrstellen correction u + h^2/12 f
+    (one FMA per node of the patch)."""
     import itertools
-    if n != 16:
+    if n == 16:
+        line_flops = line_inst = 97
+    elif n == 32:
+        line_inst = 30 + 97 + 8 * (15 + 4)
+        line_flops = 30 + 97 + 8 * (2 * 15 + 4)
+    else:
         return None
     terms = 0
     for c in itertools.product(range(1, n), repeat=3):
@@ -272,9 +279,8 @@ def dirichlet_counts(n, Q):
             if any(c[d] + sft[d] in (0, n) for d in range(3)):
                 terms += 1
     m = n - 1
-    dst = 6 * m * m * 97
-    flops = 2 * terms + dst + m ** 3 + 2 * n ** 3
-    inst = terms + dst + m ** 3 + n ** 3
+    flops = 2 * terms + 6 * m * m * line_flops + m ** 3 + 2 * n ** 3
+    inst = terms + 6 * m * m * line_inst + m ** 3 + n ** 3
     return flops, inst
 
 
@@ -309,36 +315,40 @@ def roofline_for(w, plan, per_launch, tier, traffic=None):
         sched = {"fp64": "FP64 radix-8x8", "df": "double-float radix-8x8"}.get(tier, "FP32 radix-2 register")
         unit_name = "(patch, kx) slab"
     elif dom == "conv_slab" and M == 128:
-        # the 128-point slabs (n = 24, 32): shared-memory radix-2 stages, 8
-        # instructions per butterfly (4 adds, 2 multiplies + 2 FMAs for the
-        # twiddle), no pruning of the forward passes; the FP32 kernel (k_slab)
-        # runs the inverse y on all W output columns, the 16-byte one
-        # (k_slab_rows) on the nz columns read later
+        # the 128-point slabs (n = 24, 32).  Split tiers (k_slab128r): radix
+        # 16 x 8 over 8-lane groups, per lane and line a 16-point DFT (196
+        # FP32 instructions; 164 when the inputs 8..15 are zero, the forward
+        # passes), 15 twiddle products (60) and two 8-point DFTs (112); the
+        # kernel product is 2 instructions per entry.  FP64 / double-float
+        # (k_slab_rows): shared-memory radix-2 stages, 8 operations per
+        # butterfly (4 adds, 2 multiplies + 2 FMAs for the twiddle), no
+        # pruning, inverse y on the nz columns read later.
         nin = w.n + 1
         nz = slab_rows(w, info.g_alpha)
-        W = w.n + 2 * w.s + 1
         line_flops = 5.0 * M * np.log2(M)
         nominal = (nin + 2 * M + nz) * line_flops + 2.0 * M * M
-        line_inst = (M // 2) * np.log2(M) * 8
-        inv_y = W if tier in ("split", "split_df") else nz
-        inst = (nin + 2 * M + inv_y) * line_inst + 2.0 * M * M * (DF_MUL_INST if tier == "df" else 1)
-        if tier == "df":
-            inst = (nin + 2 * M + inv_y) * (M // 2) * np.log2(M) * (4 * DF_ADD_INST + 4 * DF_MUL_INST) \
-                + 2.0 * M * M * DF_MUL_INST
+        if tier in ("split", "split_df"):
+            sparse_line, full_line = 8 * (164 + 60 + 112), 8 * (196 + 60 + 112)
+            inst = (nin + M) * sparse_line + (M + nz) * full_line + 2.0 * M * M
+            sched = "FP32 radix-16x8 register"
+        else:
+            bfly = (M // 2) * np.log2(M)
+            per_op = 1 if tier == "fp64" else (4 * DF_ADD_INST + 4 * DF_MUL_INST) / 8.0
+            inst = (nin + 2 * M + nz) * bfly * 8 * per_op + 2.0 * M * M * (DF_MUL_INST if tier == "df" else 1)
+            sched = {"fp64": "FP64 shared-memory radix-2 (row-streamed)",
+                     "df": "double-float shared-memory radix-2 (row-streamed)"}[tier]
         nlaunch = -(-NP // CONV_CHUNK)
         units, pipe_rate = min(NP, CONV_CHUNK) * Mh, (FP64_INST_PER_S if tier == "fp64" else FP32_LANE_INST_PER_S)
         pipe = "FP64 pipe" if tier == "fp64" else "FP32 pipe"
-        sched = {"fp64": "FP64 shared-memory radix-2 (row-streamed)",
-                 "df": "double-float shared-memory radix-2 (row-streamed)"}.get(tier, "FP32 shared-memory radix-2")
         unit_name = "(patch, kx) slab"
-    elif dom == "dirichlet" and w.n == 16:
+    elif dom == "dirichlet" and w.n in (16, 32):
         nominal, inst = dirichlet_counts(w.n, w.Q)
         if not fine64:
             inst = inst * DF_ADD_INST  # double-float: about 8 FP32 instructions per operation
         nlaunch = 1
         units, pipe_rate = NP, (FP64_INST_PER_S if fine64 else FP32_LANE_INST_PER_S)
         pipe = "FP64 pipe" if fine64 else "FP32 pipe"
-        sched = "FP64 split-radix DST-I" if fine64 else "double-float split-radix DST-I"
+        sched = "FP64 split DST-I" if fine64 else "double-float split DST-I"
         unit_name = "patch"
     else:
         return None

@@ -72,6 +72,15 @@ def test_dirichlet_counts_closed_form():
         dst = 6 * 15 * 15 * 97
         assert flops == 2 * t + dst + 15 ** 3 + 2 * 16 ** 3
         assert inst == t + dst + 15 ** 3 + 16 ** 3
+    # n = 32, 27-point: 31^3 x 26 neighbours minus the interior pairs
+    inter32 = {1: 3 * 2 * 30 * 31 * 31, 2: 3 * 4 * 30 * 30 * 31, 3: 8 * 30 ** 3}
+    t32 = 31 ** 3 * 26 - (inter32[1] + inter32[2] + inter32[3])
+    assert t32 == 50786
+    flops, inst = b.dirichlet_counts(32, 6)
+    line_f, line_i = 30 + 97 + 8 * 34, 30 + 97 + 8 * 19  # sums/differences, DST-15, 8 odd pairs
+    assert flops == 2 * t32 + 6 * 31 * 31 * line_f + 31 ** 3 + 2 * 32 ** 3
+    assert inst == t32 + 6 * 31 * 31 * line_i + 31 ** 3 + 32 ** 3
+    assert b.dirichlet_counts(24, 6) is None
 
 
 
