@@ -1060,15 +1060,17 @@ __device__ __forceinline__ void dft16(float2 (&v)[16], bool inv) {
 }
 
 // One 128-point line transform by an 8-lane group (layout above).  tw: M
-// twiddles exp(-2 pi i j / 128) in shared memory; xs: the group's scratch
-// (16 x 9 entries); gm: the group's lane mask.
+// twiddles exp(-2 pi i j / 128) in shared memory, entry j at j + j / 8 (the
+// padding spreads the lanes' reads of w^(t k1) over distinct banks); xs: the
+// group's scratch (16 x 9 entries); gm: the group's lane mask.
 template <bool SPARSE>
 __device__ __forceinline__ void line128_regs(float2 (&v)[16], int t, const float2 *tw, bool inv, float2 *xs,
                                              unsigned gm) {
     dft16<SPARSE>(v, inv);
 #pragma unroll
     for (int k1 = 1; k1 < 16; ++k1) {
-        float2 w = tw[(t * k1) & 127];
+        const int j = (t * k1) & 127;
+        float2 w = tw[j + (j >> 3)];
         if (inv) w.y = -w.y;
         v[k1] = cmul(v[k1], w);
     }
@@ -1095,24 +1097,30 @@ __device__ __forceinline__ void line128_regs(float2 (&v)[16], int t, const float
 // one line each (forward y on the nin input z rows; per ky column forward z,
 // kernel product and inverse z in registers, storing only the z positions
 // read later, into compact rows in position order; inverse y on those rows);
-// the slab holds max(nin, nz) rows.  Requires nin <= 64, W <= 128.
+// the slab holds max(nin, nz) rows.  Requires nin <= 64, W <= 128, 256
+// threads.  Bank spreading: the two groups of a half-warp take rows or
+// columns 8 apart (row pitch 129: 16 banks apart), and the groups' exchange
+// scratch sits 152 entries apart (also 16 banks).
 __global__ void __launch_bounds__(256, 2) k_slab128r(SlabArgs a) {
-    constexpr int M = 128, MH = 65, P = 129;
+    constexpr int M = 128, MH = 65, P = 129, XP = 152;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *tw = (float2 *)smem_raw;                 // M twiddles
-    float2 *xs_all = tw + M;                         // 32 groups x 144
-    float2 *S = xs_all + 32 * 144;                   // S[row][ky], pitch P
+    float2 *tw = (float2 *)smem_raw;                 // M twiddles, padded (144 entries)
+    float2 *xs_all = tw + 144;                       // 32 groups x XP
+    float2 *S = xs_all + 32 * XP;                    // S[row][ky], pitch P
     __shared__ int rowc[128];                        // output z row jz -> compact row
     __shared__ unsigned long long mask_s[2];         // output z positions
     const int nin = a.nin, W = a.nout, nz = a.nz;
-    const int grp = threadIdx.x >> 3, t = threadIdx.x & 7, ngrp = blockDim.x >> 3;
+    const int grp = threadIdx.x >> 3, t = threadIdx.x & 7;
+    // this group's first row / column: a bijection of 0..31 pairing the two
+    // groups of each half-warp 8 apart
+    const int g0 = ((grp >> 1) & 7) + 8 * (grp & 1) + 16 * (grp >> 4);
     const unsigned gm = 0xffu << (threadIdx.x & 24);
-    float2 *xs = xs_all + grp * 144;
+    float2 *xs = xs_all + grp * XP;
     const float2 *twg = (const float2 *)a.tw;        // M/2 entries; w^(j+64) = -w^j
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
         float2 w = twg[j & 63];
         if (j >= 64) { w.x = -w.x; w.y = -w.y; }
-        tw[j] = w;
+        tw[j + (j >> 3)] = w;
     }
     if (threadIdx.x < 2) {
         unsigned long long m = 0;
@@ -1139,8 +1147,8 @@ __global__ void __launch_bounds__(256, 2) k_slab128r(SlabArgs a) {
         const long q = unit / MH;  // scratch slot
         const float2 *in = (const float2 *)a.it.a1 + (q * MH + kx) * nin * nin;
         float2 v[16];
-        // forward y: group g takes input z row g (natural ky columns out)
-        for (int r = grp; r < nin; r += ngrp) {
+        // forward y: one input z row per group (natural ky columns out)
+        for (int r = g0; r < nin; r += 32) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int pos = 8 * j + t;
@@ -1152,7 +1160,7 @@ __global__ void __launch_bounds__(256, 2) k_slab128r(SlabArgs a) {
         }
         __syncthreads();
         // ky column c: forward z, kernel product, inverse z
-        for (int c = grp; c < M; c += ngrp) {
+        for (int c = g0; c < M; c += 32) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int pos = 8 * j + t;
@@ -1178,7 +1186,7 @@ __global__ void __launch_bounds__(256, 2) k_slab128r(SlabArgs a) {
         }
         __syncthreads();
         // inverse y on the output rows (compact row r)
-        for (int r = grp; r < nz; r += ngrp) {
+        for (int r = g0; r < nz; r += 32) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] = S[r * P + 8 * j + t];
             line128_regs<false>(v, t, tw, true, xs, gm);
@@ -2928,7 +2936,7 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
         }
         else {
             if constexpr (LOG2M == 7 && std::is_same<R, float>::value) {  // FP32: register lines
-                const size_t sm = ((size_t)M + 32 * 144 + (size_t)std::max(nin, nz) * (M + 1)) * sizeof(float2);
+                const size_t sm = ((size_t)144 + 32 * 152 + (size_t)std::max(nin, nz) * (M + 1)) * sizeof(float2);
                 int gr = nb * MH;
                 if (it.persist) {
                     int dev = 0, nsm = 0, occ = 0;
