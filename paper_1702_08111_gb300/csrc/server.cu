@@ -98,6 +98,21 @@ size_t estimate_bytes(const mlc_params &p) {
         const long wbx = n + 2 * gb + 1, npb = (n + 2 * gb) / n + 2;
         bytes += NP * ((npb * wbx * wbx + 127) / 128 * 128) * 4;
     }
+    if (n > 24) bytes += NP * (n - 1) * (n - 1) * (n - 1) * 8;  // Dirichlet workspace
+    if (p.levels > 2) {
+        // the next coarser level: its own plan (with its local-convolution
+        // scratch, allocated at creation) and its charge and result arrays
+        const long gb = p.g_beta >= 0 ? p.g_beta : (p.Q == 4 ? n : (9 * n + 7) / 8);
+        const long b = p.b >= 0 ? p.b : (p.Q == 4 ? 2 : 3);
+        const long span = N / 4 + 2 * (gb / 4 + b + 2);
+        mlc_params c = p;
+        c.N = (int)(n * ((span + n - 1) / n));
+        c.levels = p.levels - 1;
+        const long Nc = c.N, npc = Nc / n, NPc = npc * npc * npc;
+        const long chunk = std::min<long>(p.conv_chunk > 0 ? p.conv_chunk : 1024, NPc);
+        bytes += (long)estimate_bytes(c) + Nc * Nc * Nc * 12 +
+                 chunk * (Mh * (n + 1) * (n + 1) + W * Mh * W) * 2 * rb;
+    }
     bytes += 32L << 20;                                        // basis tables, index maps, slack
     return (size_t)bytes;
 }

@@ -194,3 +194,29 @@ def test_paper_three_level_rows_512(torch_cuda, smooth_512, row):
     print(f"{name}: error {err:.5e}, paper {paper:.5e}, ratio {err / paper:.3f}, split-fp64 {dsplit:.2e}")
     assert paper / 5 <= err <= 5 * paper, (name, err, paper)
     assert dsplit <= 1e-6
+
+
+def test_server_serves_multilevel_and_n32_requests(torch_cuda):
+    """The continuous-batching server with a three-level request and an
+    n = 32 request beside a two-level one: each result equals the standalone
+    solve bit for bit."""
+    from paper_1702_08111_gb300 import mlc
+    torch = torch_cuda
+    cases = [dict(N=32, n=8, s=12, P=4, Q=4, levels=3, tier=FP64),
+             dict(N=64, n=32, s=20, P=4, Q=6, tier=SPLIT),
+             dict(N=64, n=16, s=16, P=4, Q=4, tier=FP64)]
+    srv = mlc.Server(8 << 30, max_batch=4)
+    out = []
+    for k, kw in enumerate(cases):
+        kw = dict(kw)
+        N, tier = kw["N"], kw["tier"]
+        f64 = I.sample_bumps(N, I.draw_bumps(3, 900 + k))
+        f = torch.from_numpy(f64.astype(np.float32) if tier in F32_TIERS else f64).cuda()
+        ref = mlc.Plan(**kw).solve(f).clone()
+        phi = torch.empty((N,) * 3, dtype=torch.float64, device="cuda")
+        t = srv.enqueue(f, phi, **kw)
+        out.append((t, phi, ref))
+    for t, phi, ref in out:
+        srv.wait(t, 60000)
+        assert torch.equal(phi, ref)
+    srv.close()
