@@ -2907,7 +2907,6 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
         SlabArgs a{tw, nin, W, -g.s, it, nz, {}, g.a4blk};
         for (int j = 0; j < nz; ++j) a.zrow[j] = zrow[j];
         if (LOG2M == 6) {
-            if (nin > 24) return cudaErrorInvalidValue;  // k_slab64's sparse forward passes
             int dev = 0, nsm = 0, occ = 0;
             if (it.persist) {  // one wave of resident CTAs walking all slabs
                 cudaGetDevice(&dev);
@@ -2923,7 +2922,9 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
                 }
                 if (nin <= 17) k_slab64r<17><<<gr, 64, smr, st>>>(a);
                 else k_slab64r<32><<<gr, 64, smr, st>>>(a);
-            } else {  // FP64 tier: double-float radix-8 x 8 over 8-thread groups
+            } else if (nin > 24) {  // k_slab64's sparse forward passes take nin <= 24 (n = 24)
+                k_slab<LOG2M, R><<<nb * MH, 256, fft_smem_bytes<R>(M, M, M + 1), st>>>(a);
+            } else {  // FP64 and double-float: radix 8 x 8 over 8-thread groups
                 const size_t sm = (size_t)(M + M * Pitch64<R>::P + 32 * 72) * sizeof(typename Cx<R>::T) + 64 * sizeof(int);
                 int grid = nb * MH;
                 if (it.persist) {

@@ -446,3 +446,45 @@ def test_set_dgf_uses_the_injected_table(torch_cuda, G4):
     assert e.value.status == 1
     plan.set_dgf(G)
     assert relmax(plan.solve(ft).cpu().numpy(), base.cpu().numpy()) <= TOL
+
+
+# ------------------------------------------------------------------ other patch sizes
+_SIZES = [
+    dict(N=48, n=24, s=12, P=4, Q=4),            # n = 24, local period 128, Legendre ring
+    dict(N=48, n=24, s=8, P=4, Q=4, mode=1),     # n = 24, local period 64, MLC-0
+    dict(N=48, n=12, s=12, P=4, Q=4),            # n = 12 (generic Dirichlet lines)
+    dict(N=16, n=4, s=8, P=2, Q=4),              # n = 4, local period 32
+]
+
+
+@pytest.mark.parametrize("tier", [FP64, DF, SPLIT])
+@pytest.mark.parametrize("kw", _SIZES, ids=["n24_ring", "n24_mlc0", "n12", "n4"])
+def test_patch_sizes_against_oracle(torch_cuda, G4, kw, tier):
+    """Patch sizes 4, 12 and 24 (every Dirichlet instantiation besides 16 and
+    32) in the FP64, double-float and split tiers, every stage against the
+    oracle (1e-12; 1e-6 for the split tier)."""
+    from paper_1702_08111_gb300 import mlc
+    kw = dict(kw)
+    key = "sizes" + repr(sorted(kw.items()))
+    N = kw["N"]
+    mode = kw.pop("mode", 0)
+    f64 = I.sample_bumps(N, I.draw_bumps(4, 500 + N + kw["n"]))
+    if tier == SPLIT:
+        f64 = f64.astype(np.float32).astype(np.float64)
+        key += "f32"
+    torch = torch_cuda
+    plan = mlc.Plan(**kw, mode=mode, tier=tier)
+    f = torch.from_numpy(f64.astype(np.float32) if tier == SPLIT else f64).cuda()
+    phi = plan.solve(f)
+    torch.cuda.synchronize()
+    plan.status()
+    prm = O.Params(N=N, n=kw["n"], s=kw["s"], P=kw["P"], Q=kw["Q"], mode="mlc0" if mode else "mlc")
+    phi_o, st = _oracle(key, prm, f64, G4)
+    tol = SPLIT_TOL if tier == SPLIT else TOL
+    assert relmax(plan.export(mlc.STAGE_MOMENTS), st["moments"]) <= tol
+    assert relmax(plan.export(mlc.STAGE_FH), st["FH"]) <= tol
+    assert relmax(plan.export(mlc.STAGE_PHIH), st["phiH"]) <= tol
+    pb = _phiB_from_planes(plan.export(mlc.STAGE_PHIB), st["face_nodes"], prm.n)
+    assert relmax(pb, st["phiB"]) <= tol
+    _check_plane_duplicates(plan.export(mlc.STAGE_PHIB), N, prm.n)
+    assert relmax(phi.cpu().numpy(), phi_o) <= tol
