@@ -41,7 +41,10 @@ typedef enum {
     MLC_ERR_OOM = 3,         /* a device or host allocation failed */
     MLC_ERR_CUDA = 4,        /* a CUDA runtime call or kernel failed */
     MLC_ERR_ADMISSION = 5,   /* server: request exceeds the memory budget */
-    MLC_ERR_TIMEOUT = 6      /* server: wait timed out / request cancelled */
+    MLC_ERR_TIMEOUT = 6,     /* server: wait timed out / request cancelled; a bounded wait
+                                inside a kernel gave up                                    */
+    MLC_ERR_INDEX = 7        /* checked builds only (-DMLC_CHECKED): a computed index fell
+                                outside its array; the access was skipped                  */
 } mlc_status;
 
 /* Arithmetic of a plan.  "Double-float" is an unevaluated sum hi + lo of two
@@ -143,6 +146,9 @@ mlc_status mlc_plan_set_dgf(mlc_plan_t plan, const double *table, int L);
  * that solve is not valid; the flag is then cleared.  mlc_solve_host calls it
  * before returning. */
 mlc_status mlc_plan_status(mlc_plan_t plan);
+/* (In a library built with -DMLC_CHECKED the kernels test their computed
+ * indices before use: a bad one is skipped and mlc_plan_status reports
+ * MLC_ERR_INDEX; normal builds compile the tests out.) */
 
 /* Bytes of device workspace the plan holds now (tables excluded; the plan's
  * own local-convolution scratch counts once a solve has allocated it). */

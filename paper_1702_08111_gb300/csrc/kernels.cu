@@ -24,6 +24,21 @@ namespace mlc {
 
 namespace {
 
+// Checked builds (-DMLC_CHECKED; a debugging aid standing in for a memory
+// checker): computed indices into the plan's arrays are tested before use; a
+// bad one is not accessed, and the plan's error word records code 2, which
+// mlc_plan_status reports as MLC_ERR_INDEX.  In normal builds the test is
+// compiled out.
+#ifdef MLC_CHECKED
+__device__ __forceinline__ bool in_range(long i, long n, int *err) {
+    if (i >= 0 && i < n) return true;
+    atomicCAS(err, 0, 2);
+    return false;
+}
+#else
+__device__ __forceinline__ bool in_range(long, long, int *) { return true; }
+#endif
+
 __device__ __forceinline__ int brev_bits(int i, int log2m) {
     return (int)(__brev((unsigned)i) >> (32 - log2m));
 }
@@ -1427,10 +1442,23 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
         int pos = x % M;
         if (pos < 0) pos += M;
         const TO v = (TO)buf[l * LP + (LOG2M == 6 ? pos : brev_bits(pos, LOG2M))].x;
-        if (wC) cl[((long)((z >> 2) - kl) * nc + ((y >> 2) - kl)) * nc + ((x >> 2) - kl)] = v;
-        if (w0) fp[(((long)(0 * a.npa + (z - pl0) / n)) * wa + (y + ga)) * wa + (x + ga)] = v;
-        if (w1) fp[(((long)(1 * a.npa + (y - pl0) / n)) * wa + (z + ga)) * wa + (x + ga)] = v;
-        if (w2) fp[(((long)(2 * a.npa + (x - pl0) / n)) * wa + (z + ga)) * wa + (y + ga)] = v;
+        const long ncl = (long)nc * nc * nc, nfp = 3L * a.npa * wa * wa;
+        if (wC) {
+            const long i = ((long)((z >> 2) - kl) * nc + ((y >> 2) - kl)) * nc + ((x >> 2) - kl);
+            if (in_range(i, ncl, PP.err)) cl[i] = v;
+        }
+        if (w0) {
+            const long i = (((long)(0 * a.npa + (z - pl0) / n)) * wa + (y + ga)) * wa + (x + ga);
+            if (in_range(i, nfp, PP.err)) fp[i] = v;
+        }
+        if (w1) {
+            const long i = (((long)(1 * a.npa + (y - pl0) / n)) * wa + (z + ga)) * wa + (x + ga);
+            if (in_range(i, nfp, PP.err)) fp[i] = v;
+        }
+        if (w2) {
+            const long i = (((long)(2 * a.npa + (x - pl0) / n)) * wa + (z + ga)) * wa + (y + ga);
+            if (in_range(i, nfp, PP.err)) fp[i] = v;
+        }
     }
     __syncthreads();  // the buffer is refilled by the next pass
     }
@@ -1451,7 +1479,8 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
                 const R re = X.x * w.x + X.y * w.y;
                 acc += (k == 0 || 2 * k == M) ? re : R(2.0) * re;
             }
-            fp[(((long)(2 * a.npa + j)) * wa + (z + ga)) * wa + (y + ga)] = (TO)acc;
+            const long i = (((long)(2 * a.npa + j)) * wa + (z + ga)) * wa + (y + ga);
+            if (in_range(i, 3L * a.npa * wa * wa, PP.err)) fp[i] = (TO)acc;
         }
     }
 }
@@ -1598,10 +1627,23 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 8 : 4) k_inv_x64(InvXPAr
         const bool wC = zC && yC && xC, w0 = zP && yA && xA, w1 = yP && zA && xA, w2 = zA && yA && xP;
         if (!(wC || w0 || w1 || w2)) continue;
         const R val = rbuf[l * RP + pos];
-        if (wC) cl[((long)zc * nc + ((y >> 2) - kl)) * nc + xcoarse[pos]] = val;
-        if (w0) fp[(((long)jz0) * wa + (y + ga)) * wa + (x + ga)] = val;
-        if (w1) fp[(((long)(a.npa + (yf >> 3))) * wa + (z + ga)) * wa + (x + ga)] = val;
-        if (w2) fp[(((long)(2 * a.npa + xplane[pos])) * wa + (z + ga)) * wa + (y + ga)] = val;
+        const long ncl = (long)nc * nc * nc, nfp = 3L * a.npa * wa * wa;
+        if (wC) {
+            const long i = ((long)zc * nc + ((y >> 2) - kl)) * nc + xcoarse[pos];
+            if (in_range(i, ncl, PP.err)) cl[i] = val;
+        }
+        if (w0) {
+            const long i = (((long)jz0) * wa + (y + ga)) * wa + (x + ga);
+            if (in_range(i, nfp, PP.err)) fp[i] = val;
+        }
+        if (w1) {
+            const long i = (((long)(a.npa + (yf >> 3))) * wa + (z + ga)) * wa + (x + ga);
+            if (in_range(i, nfp, PP.err)) fp[i] = val;
+        }
+        if (w2) {
+            const long i = (((long)(2 * a.npa + xplane[pos])) * wa + (z + ga)) * wa + (y + ga);
+            if (in_range(i, nfp, PP.err)) fp[i] = val;
+        }
     }
     // rows that only need x on the face planes: direct sums over the half spectrum
     if (zA) {
@@ -1737,6 +1779,8 @@ __global__ void __launch_bounds__(256) k_resid(ResArgs a) {
         if (axis == 0) { i0 = c4; i1 = ka; i2 = kb; }
         else if (axis == 1) { i0 = ka; i1 = c4; i2 = kb; }
         else { i0 = ka; i1 = kb; i2 = c4; }
+        if (!(in_range(i0 - kl, nc, PP.err) & in_range(i1 - kl, nc, PP.err) & in_range(i2 - kl, nc, PP.err)))
+            return FT<T>::zero();
         return FT<T>::of(cl[((long)(i0 - kl) * nc + (i1 - kl)) * nc + (i2 - kl)]);
     };
     for (int e = threadIdx.x; e < nk * wa; e += blockDim.x) {
@@ -1832,6 +1876,7 @@ __device__ __forceinline__ void ring_dot(const double *c, const double *d, int n
 }
 
 struct AsmArgs {
+    int *err;                // plan error word (checked builds)
     const void *cl;          // coarse lattice of the local fields, nc^3 per patch (TB)
     const void *mom, *T;     // ring tables in the ring precision RT
     double *FH;
@@ -1893,12 +1938,15 @@ __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
                                 const int nz = (s0 != 0) + (s1 != 0) + (s2 != 0);
                                 if (a.coefd[nz] == 0.0) continue;
                                 const long x0 = r0 + s0 - kl, x1 = r1 + s1 - kl, x2 = r2 + s2 - kl;
-                                acc = FT<T>::fma(pick<T>(a.coef[nz], a.coefd[nz]), FT<T>::of(bx[(x0 * nc + x1) * nc + x2]), acc);
+                                if (in_range(x0, nc, a.err) & in_range(x1, nc, a.err) & in_range(x2, nc, a.err))
+                                    acc = FT<T>::fma(pick<T>(a.coef[nz], a.coefd[nz]), FT<T>::of(bx[(x0 * nc + x1) * nc + x2]), acc);
                             }
                 } else {
                     const long t = (((long)(r0 - a.cb_lo) * ncb + (r1 - a.cb_lo)) * ncb +
                                     (r2 - a.cb_lo)) * a.npoly;
-                    acc = acc + ring_row<T>((const RT *)a.mom + p * a.npad, (const RT *)a.T + t, a.npoly);
+                    if (in_range(r0 - a.cb_lo, ncb, a.err) & in_range(r1 - a.cb_lo, ncb, a.err) &
+                        in_range(r2 - a.cb_lo, ncb, a.err))
+                        acc = acc + ring_row<T>((const RT *)a.mom + p * a.npad, (const RT *)a.T + t, a.npoly);
                 }
             });
     a.FH[idx] = FT<T>::to(acc);
@@ -1955,7 +2003,7 @@ struct LagW {
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_plane_interp(const void *phiH_, void *out_, int N, int n, int np, int b,
-                                                      int olo, int no, LagW w) {
+                                                      int olo, int no, LagW w, int *err) {
     const long tot = 3L * (np + 1) * no * (N + 1);
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= tot) return;
@@ -1968,6 +2016,7 @@ __global__ void __launch_bounds__(256) k_plane_interp(const void *phiH_, void *o
     // phi^H at coarse (plane, c_u, c_v) for the plane's axis order
     auto at = [&](int cv) -> T {
         const int c = cv - olo;
+        if (!(in_range(c, no, err) & in_range(ca, no, err) & in_range(cuo, no, err))) return FT<T>::zero();
         long i;
         if (axis == 0) i = ((long)ca * no + cuo) * no + c;
         else if (axis == 1) i = ((long)cuo * no + ca) * no + c;
@@ -1990,6 +2039,7 @@ __global__ void __launch_bounds__(256) k_plane_interp(const void *phiH_, void *o
 }
 
 struct BndArgs {
+    int *err;                  // plan error word (checked builds)
     const void *phiH, *resid;  // fine precision T
     const void *tpl;           // k_plane_interp output, fine precision T
     const float *ringR;        // RING: [patch][ring_rows_pad] ring terms of this launch's axis
@@ -2033,7 +2083,8 @@ __global__ void __launch_bounds__(128, 6) k_boundary(BndArgs a) {
         acc = FT<T>::zero();
         const int kb = (gu >> 2) - a.b - a.olo;
         for (int e = 0; e < K; ++e)
-            acc = FT<T>::fma(pick<T>(a.lw[ru][e], a.lwd[ru][e]), FT<T>::rn(tpl[(long)(kb + e) * (a.N + 1)]), acc);
+            if (in_range(kb + e, a.no, a.err))
+                acc = FT<T>::fma(pick<T>(a.lw[ru][e], a.lwd[ru][e]), FT<T>::rn(tpl[(long)(kb + e) * (a.N + 1)]), acc);
     }
     // local corrections of the patches whose Omega_beta holds g (ascending index);
     // the Legendre ring terms accumulate in the ring precision RT
@@ -2047,17 +2098,21 @@ __global__ void __launch_bounds__(128, 6) k_boundary(BndArgs a) {
                     else { d = 2; uu = r0; vv = r1; }
                     const int rr = d == 0 ? r0 : (d == 1 ? r1 : r2);
                     const long slot = (long)d * a.npa + (rr - a.pl0) / n;
-                    acc = acc + resid[((p * 3 * a.npa + slot) * a.wa + (uu + a.ga)) * a.wa + (vv + a.ga)];
+                    if (in_range((rr - a.pl0) / n, a.npa, a.err) & in_range(uu + a.ga, a.wa, a.err) &
+                        in_range(vv + a.ga, a.wa, a.err))
+                        acc = acc + resid[((p * 3 * a.npa + slot) * a.wa + (uu + a.ga)) * a.wa + (vv + a.ga)];
                 } else {
                     // dense ring row of (axis, plane, u, v): no index map to read
                     const int ra = axis == 0 ? r0 : (axis == 1 ? r1 : r2);
                     const int ru = axis == 0 ? r1 : r0, rv = axis == 2 ? r1 : r2;
+                    const bool ok = in_range((ra - a.pb0) / n, a.npb, a.err) & in_range(ru + a.gb, a.wbx, a.err) &
+                                    in_range(rv + a.gb, a.wbx, a.err);
                     if constexpr (RING) {
                         const long row = ((long)((ra - a.pb0) / n) * a.wbx + (ru + a.gb)) * a.wbx + (rv + a.gb);
-                        ring += a.ringR[p * a.ring_rows_pad + row];
+                        if (ok) ring += a.ringR[p * a.ring_rows_pad + row];
                     } else {
                         const long row = (((long)axis * a.npb + (ra - a.pb0) / n) * a.wbx + (ru + a.gb)) * a.wbx + (rv + a.gb);
-                        ring_dot((const RT *)a.mom + p * a.npad, (const RT *)a.D + row * a.npad, a.npad, ring);
+                        if (ok) ring_dot((const RT *)a.mom + p * a.npad, (const RT *)a.D + row * a.npad, a.npad, ring);
                     }
                 }
             });
@@ -2120,6 +2175,8 @@ __device__ __forceinline__ T phiB_at(const PlanPtrs &a, int n, int g0, int g1, i
     } else {
         axis = 2; j = g2 / n; u = g0; v = g1;
     }
+    if (!(in_range(j, a.np + 1, a.err) & in_range(u, a.N + 1, a.err) & in_range(v, a.N + 1, a.err)))
+        return FT<T>::zero();
     return ((const T *)a.phiB)[((long)axis * (a.np + 1) + j) * pn + (long)u * (a.N + 1) + v];
 }
 
@@ -3171,6 +3228,7 @@ cudaError_t launch_assemble(const mlc_plan_s *pl, cudaStream_t st) {
     NvtxRange nvtx("mlc:coarse_charge");
     const Geom &g = pl->g;
     AsmArgs a{};
+    a.err = pl->err;
     a.cl = pl->cl; a.FH = pl->FH;
     a.mom = ring_moments(pl);
     a.T = pl->Ttab;
@@ -3198,20 +3256,22 @@ cudaError_t launch_assemble(const mlc_plan_s *pl, cudaStream_t st) {
 // Sec. 5: F^H (nf^3 from flo) into the coarser level's charge array (node
 // off = flo - c0 of its grid, side Nc), in that level's charge precision.
 template <typename TF>
-__global__ void __launch_bounds__(256) k_fh_to_level(const double *FH, int nf, int off, int Nc, TF *fc) {
+__global__ void __launch_bounds__(256) k_fh_to_level(const double *FH, int nf, int off, int Nc, TF *fc, int *err) {
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long)nf * nf * nf) return;
     const int x = (int)(idx % nf), y = (int)((idx / nf) % nf), z = (int)(idx / ((long)nf * nf));
-    fc[((long)(z + off) * Nc + (y + off)) * Nc + (x + off)] = (TF)FH[idx];
+    if (in_range(z + off, Nc, err) & in_range(y + off, Nc, err) & in_range(x + off, Nc, err))
+        fc[((long)(z + off) * Nc + (y + off)) * Nc + (x + off)] = (TF)FH[idx];
 }
 
 // phi^H (no^3 from olo) from the coarser level's result (node off = olo - c0).
 template <typename T>
-__global__ void __launch_bounds__(256) k_level_to_phiH(const double *pc, int Nc, int off, int no, T *phiH) {
+__global__ void __launch_bounds__(256) k_level_to_phiH(const double *pc, int Nc, int off, int no, T *phiH, int *err) {
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long)no * no * no) return;
     const int x = (int)(idx % no), y = (int)((idx / no) % no), z = (int)(idx / ((long)no * no));
-    phiH[idx] = FT<T>::of(pc[((long)(z + off) * Nc + (y + off)) * Nc + (x + off)]);
+    if (in_range(z + off, Nc, err) & in_range(y + off, Nc, err) & in_range(x + off, Nc, err))
+        phiH[idx] = FT<T>::of(pc[((long)(z + off) * Nc + (y + off)) * Nc + (x + off)]);
 }
 
 // Sec. 5: the coarse solve of a multilevel plan, an MLC solve of F^H on the
@@ -3224,9 +3284,9 @@ cudaError_t run_coarse_level(const mlc_plan_s *pl, cudaStream_t st) {
     const long nf3 = (long)g.nf * g.nf * g.nf, no3 = (long)g.no * g.no * g.no;
     const int off_f = g.flo - pl->child_c0, off_o = g.olo - pl->child_c0;
     if (g.f32in)
-        k_fh_to_level<float><<<(unsigned)((nf3 + 255) / 256), 256, 0, st>>>(pl->FH, g.nf, off_f, Nc, (float *)pl->child_f);
+        k_fh_to_level<float><<<(unsigned)((nf3 + 255) / 256), 256, 0, st>>>(pl->FH, g.nf, off_f, Nc, (float *)pl->child_f, pl->err);
     else
-        k_fh_to_level<double><<<(unsigned)((nf3 + 255) / 256), 256, 0, st>>>(pl->FH, g.nf, off_f, Nc, (double *)pl->child_f);
+        k_fh_to_level<double><<<(unsigned)((nf3 + 255) / 256), 256, 0, st>>>(pl->FH, g.nf, off_f, Nc, (double *)pl->child_f, pl->err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (mlc_solve(ch, pl->child_f, pl->child_phi, st) != MLC_OK) {
@@ -3235,9 +3295,9 @@ cudaError_t run_coarse_level(const mlc_plan_s *pl, cudaStream_t st) {
     }
     mark(pl, 7, st);
     if (g.fine == FINE_F64)
-        k_level_to_phiH<double><<<(unsigned)((no3 + 255) / 256), 256, 0, st>>>(pl->child_phi, Nc, off_o, g.no, (double *)pl->phiH);
+        k_level_to_phiH<double><<<(unsigned)((no3 + 255) / 256), 256, 0, st>>>(pl->child_phi, Nc, off_o, g.no, (double *)pl->phiH, pl->err);
     else
-        k_level_to_phiH<dfl><<<(unsigned)((no3 + 255) / 256), 256, 0, st>>>(pl->child_phi, Nc, off_o, g.no, (dfl *)pl->phiH);
+        k_level_to_phiH<dfl><<<(unsigned)((no3 + 255) / 256), 256, 0, st>>>(pl->child_phi, Nc, off_o, g.no, (dfl *)pl->phiH, pl->err);
     mark(pl, 8, st);
     mark(pl, 9, st);
     mark(pl, 10, st);
@@ -3256,6 +3316,7 @@ cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st) {
     NvtxRange nvtx("mlc:boundary");
     const Geom &g = pl->g;
     BndArgs a{};
+    a.err = pl->err;
     a.phiH = pl->phiH; a.resid = pl->resid;
     a.mom = ring_moments(pl);
     a.D = pl->Dtab;
@@ -3274,9 +3335,9 @@ cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st) {
         std::memcpy(w.lw, a.lw, sizeof(w.lw));
         std::memcpy(w.lwd, a.lwd, sizeof(w.lwd));
         if (g.fine == FINE_F64)
-            k_plane_interp<double><<<nb2, 256, 0, st>>>(pl->phiH, pl->tpl, g.N, g.n, g.np, g.b, g.olo, g.no, w);
+            k_plane_interp<double><<<nb2, 256, 0, st>>>(pl->phiH, pl->tpl, g.N, g.n, g.np, g.b, g.olo, g.no, w, pl->err);
         else
-            k_plane_interp<dfl><<<nb2, 256, 0, st>>>(pl->phiH, pl->tpl, g.N, g.n, g.np, g.b, g.olo, g.no, w);
+            k_plane_interp<dfl><<<nb2, 256, 0, st>>>(pl->phiH, pl->tpl, g.N, g.n, g.np, g.b, g.olo, g.no, w, pl->err);
     }
     a.ringR = pl->ring_R;
     a.ring_rows_pad = g.ring_rows_pad;

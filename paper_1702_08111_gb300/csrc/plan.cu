@@ -542,6 +542,16 @@ void free_plan(mlc_plan_s *pl) {
     delete pl;
 }
 
+// Point a plan (and its coarser levels) at another error word.
+mlc_status share_error_word(mlc_plan_s *pl, int *err) {
+    for (; pl; pl = pl->child) {
+        pl->err = err;
+        pl->hptrs.err = err;
+        TRY_CUDA(cudaMemcpy(pl->dptrs, &pl->hptrs, sizeof(PlanPtrs), cudaMemcpyHostToDevice));
+    }
+    return MLC_OK;
+}
+
 // What a solve needs besides the plan's tables: the local-convolution
 // scratch (unless the caller gave one) and the side stream with its events.
 mlc_status prepare_solve(mlc_plan_s *pl) {
@@ -570,6 +580,7 @@ const char *mlc_status_string(mlc_status s) {
         case MLC_ERR_CUDA: return "CUDA error";
         case MLC_ERR_ADMISSION: return "request exceeds the memory budget";
         case MLC_ERR_TIMEOUT: return "timed out";
+        case MLC_ERR_INDEX: return "index out of range (checked build)";
     }
     return "unknown status";
 }
@@ -796,6 +807,7 @@ mlc_status make_coarser_level(mlc_plan_s *pl, const double *dgf_host, int dgf_Lh
     TRY_CUDA(cudaMemset(pl->child_f, 0, n3 * (G.f32in ? sizeof(float) : sizeof(double))));
     TRY(dev_alloc(pl, &pl->child_phi, n3));
     TRY(prepare_solve(ch));
+    TRY(share_error_word(ch, pl->err));  // a coarser level's failures show on this plan
     pl->ws_bytes += ch->ws_bytes;
     return MLC_OK;
 }
@@ -951,7 +963,7 @@ mlc_status mlc_solve_host(mlc_plan_t pl, const void *f_host, void *phi_host, voi
     if (e) {
         TRY_CUDA(cudaMemsetAsync(pl->err, 0, sizeof(int), st));
         TRY_CUDA(cudaStreamSynchronize(st));
-        return MLC_ERR_TIMEOUT;
+        return e == 2 ? MLC_ERR_INDEX : MLC_ERR_TIMEOUT;
     }
     return MLC_OK;
 }
@@ -963,7 +975,7 @@ mlc_status mlc_plan_status(mlc_plan_t pl) {
     TRY_CUDA(cudaMemcpy(&e, pl->err, sizeof(int), cudaMemcpyDeviceToHost));
     if (e) {
         TRY_CUDA(cudaMemset(pl->err, 0, sizeof(int)));
-        return MLC_ERR_TIMEOUT;
+        return e == 2 ? MLC_ERR_INDEX : MLC_ERR_TIMEOUT;
     }
     return MLC_OK;
 }

@@ -12,14 +12,16 @@ import os
 from dataclasses import dataclass
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_lib", "libmlc_gb300.so")
+# MLC_GB300_LIBRARY selects another build of the same library (the checked
+# debugging variant, libmlc_gb300_checked.so)
+LIB_PATH = os.environ.get("MLC_GB300_LIBRARY") or os.path.join(HERE, "_lib", "libmlc_gb300.so")
 
 MLC_TIER_FP64, MLC_TIER_SPLIT, MLC_TIER_DF, MLC_TIER_SPLIT_DF = 0, 1, 2, 3
 F32_CHARGE_TIERS = (MLC_TIER_SPLIT, MLC_TIER_SPLIT_DF)
 TIER_NAMES = {MLC_TIER_FP64: "fp64", MLC_TIER_SPLIT: "split", MLC_TIER_DF: "df", MLC_TIER_SPLIT_DF: "split_df"}
 MLC_MODE_MLC, MLC_MODE_MLC0 = 0, 1
 (MLC_OK, MLC_ERR_INVALID_ARG, MLC_ERR_UNSUPPORTED, MLC_ERR_OOM, MLC_ERR_CUDA, MLC_ERR_ADMISSION,
- MLC_ERR_TIMEOUT) = range(7)
+ MLC_ERR_TIMEOUT, MLC_ERR_INDEX) = range(8)
 STAGE_MOMENTS, STAGE_FH, STAGE_PHIH, STAGE_PHIB, STAGE_DGF = 0, 1, 2, 3, 4
 STAGE_COARSE_SAMPLES, STAGE_FACE_INDEX, STAGE_COARSE_INDEX = 5, 6, 7
 
@@ -66,7 +68,10 @@ def load_library(path: str = LIB_PATH):
     if _lib is not None:
         return _lib
     from . import build as _build
-    if _build.needs_build():
+    if os.path.abspath(path) == os.path.abspath(_build.LIB_CHECKED):
+        if _build.needs_build(_build.LIB_CHECKED):
+            _build.build(checked=True)
+    elif _build.needs_build():
         _build.build()
     if not os.path.exists(path):
         raise RuntimeError(f"MLC CUDA library not found at {path}")
