@@ -226,11 +226,13 @@ mlc_status mlc_solve_host(mlc_plan_t plan, const void *f_host, void *phi_host, v
  * shared launches (moments, local convolutions, residuals, Dirichlet steps),
  * the groups concurrently, and each problem's coarse charge, coarse solve and
  * boundary values on parallel branches.  The launch sequence is captured as a
- * CUDA graph per (plans, f, phi) set, tuned on the first call (branches, slab
- * launch shape, patches per convolution launch group) and replayed on later
- * calls.  plans[k], f[k], phi[k] as in mlc_solve; plans must be distinct
- * (INVALID_ARG otherwise) and on the current device.  The first call with a
- * set allocates its item tables and convolution scratch.
+ * CUDA graph per set of plans, tuned on the first call (branches, slab launch
+ * shape, patches per convolution launch group) and replayed on later calls;
+ * a later call with other f / phi arrays for the same plans rewrites the
+ * graph's problem records on `stream` (after the earlier replays finish) and
+ * replays the same graph.  plans[k], f[k], phi[k] as in mlc_solve; plans must
+ * be distinct (INVALID_ARG otherwise) and on the current device.  The first
+ * call with a set of plans allocates its item tables and convolution scratch.
  */
 mlc_status mlc_batch_solve(int count, const mlc_plan_t *plans, const void *const *f,
                            void *const *phi, void *stream);
@@ -279,14 +281,15 @@ mlc_status mlc_debug_set_timing(mlc_plan_t plan, int enable);
  * valid).  kind 0 restores normal solves.  INVALID_ARG for other kinds. */
 mlc_status mlc_debug_set_fault(mlc_plan_t plan, int kind);
 mlc_status mlc_debug_timing(mlc_plan_t plan, float *ms_out, int count);
-/* Configuration the batch autotuner chose for these arrays (as passed to
- * mlc_batch_solve): 2 x (parallel branches of the per-problem coarse steps)
- * + 1 if the local-convolution slab kernel runs persistently; 0 if this set
- * has not been solved yet. */
+/* Configuration the batch autotuner chose for this set of plans (f, phi as
+ * passed to mlc_batch_solve; the choice does not depend on them): 2 x
+ * (parallel branches of the per-problem coarse steps) + 1 if the
+ * local-convolution slab kernel runs persistently; 0 if this set has not been
+ * solved yet. */
 int mlc_debug_batch_choice(int count, const mlc_plan_t *plans, const void *const *f, void *const *phi);
 /* Patches per local-convolution launch group (the number of patches whose
  * pencils one set of convolution launches transforms) that the autotuner
- * chose for these arrays, from {512, 1024, 2048}; 0 if not solved yet. */
+ * chose for this set of plans, from {512, 1024, 2048}; 0 if not solved yet. */
 int mlc_debug_batch_chunk(int count, const mlc_plan_t *plans, const void *const *f, void *const *phi);
 mlc_status mlc_debug_export(mlc_plan_t plan, int stage, void *host, size_t bytes);
 /* Geometry of the plan: out[0..15] = N, n, s, b, g_alpha, g_beta, P, npoly,

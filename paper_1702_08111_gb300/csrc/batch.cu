@@ -187,7 +187,25 @@ struct BatchCtx {
     int persist = 0;
     int chunk = 0;                // patches per local-convolution launch group (tuned)
     float tuned_ms = 0.f;
+    // the arrays the device records point at; a call with other arrays for
+    // the same plans rewrites the records (stream-ordered) and replays the
+    // same graph: no new capture and no new tuning
+    std::vector<uintptr_t> bufs;
+    PlanPtrs *h_recs = nullptr;   // pinned staging of the records
+    cudaEvent_t done = nullptr;   // after the last replay
+    cudaEvent_t copied = nullptr; // after the last record upload
 };
+
+void free_ctx(BatchCtx *c) {
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    cudaFree(c->d_items);
+    cudaFree(c->d_plans);
+    for (void *p : c->scratch) cudaFree(p);
+    if (c->h_recs) cudaFreeHost(c->h_recs);
+    if (c->done) cudaEventDestroy(c->done);
+    if (c->copied) cudaEventDestroy(c->copied);
+    delete c;
+}
 
 std::mutex g_mu;
 std::map<std::vector<uintptr_t>, BatchCtx *> g_cache;
@@ -284,17 +302,31 @@ extern "C" mlc_status mlc_batch_solve(int count, const mlc_plan_t *plans, const 
             if (plans[j] == plans[k]) return MLC_ERR_INVALID_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    std::vector<uintptr_t> key;
+    std::vector<uintptr_t> key, bufs;
     for (int k = 0; k < count; ++k) {
         key.push_back((uintptr_t)plans[k]);
-        key.push_back((uintptr_t)f[k]);
-        key.push_back((uintptr_t)phi[k]);
+        bufs.push_back((uintptr_t)f[k]);
+        bufs.push_back((uintptr_t)phi[k]);
     }
     std::lock_guard<std::mutex> lk(g_mu);
     BatchCtx *c = nullptr;
     auto found = g_cache.find(key);
     if (found != g_cache.end()) {
         c = found->second;
+        if (c->bufs != bufs) {  // same plans, other arrays: new records, same graph
+            BatchLayout L;
+            batch_layout(count, plans, f, phi, L);
+            cudaError_t e = cudaStreamWaitEvent(st, c->done, 0);  // replays still reading them
+            if (e == cudaSuccess) e = cudaEventSynchronize(c->copied);  // the staging buffer is free
+            if (e == cudaSuccess) {
+                std::memcpy(c->h_recs, L.recs.data(), L.recs.size() * sizeof(PlanPtrs));
+                e = cudaMemcpyAsync(c->d_plans, c->h_recs, L.recs.size() * sizeof(PlanPtrs),
+                                    cudaMemcpyHostToDevice, st);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(c->copied, st);
+            if (e != cudaSuccess) return MLC_ERR_CUDA;
+            c->bufs = bufs;
+        }
     } else {
         c = new BatchCtx();
         c->plans.assign(plans, plans + count);
@@ -318,18 +350,20 @@ extern "C" mlc_status mlc_batch_solve(int count, const mlc_plan_t *plans, const 
             e = cudaMemcpy(c->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
             e = cudaMemcpy(c->d_plans, recs.data(), recs.size() * sizeof(PlanPtrs), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_recs, recs.size() * sizeof(PlanPtrs));
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->copied, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(c->copied, st);
         if (e == cudaSuccess) e = build_and_tune(*c, st);
         if (e != cudaSuccess) {
-            if (c->exec) cudaGraphExecDestroy(c->exec);
-            cudaFree(c->d_items);
-            cudaFree(c->d_plans);
-            for (void *p : c->scratch) cudaFree(p);
-            delete c;
+            free_ctx(c);
             return e == cudaErrorMemoryAllocation ? MLC_ERR_OOM : MLC_ERR_CUDA;
         }
+        c->bufs = bufs;
         g_cache[key] = c;
     }
     cudaError_t e = cudaGraphLaunch(c->exec, st);
+    if (e == cudaSuccess) e = cudaEventRecord(c->done, st);
     return e == cudaSuccess ? MLC_OK : MLC_ERR_CUDA;
 }
 
@@ -340,12 +374,7 @@ void mlc_batch_forget(mlc_plan_t plan) {
         bool uses = false;
         for (auto *p : it->second->plans) uses |= (p == plan);
         if (uses) {
-            BatchCtx *c = it->second;
-            if (c->exec) cudaGraphExecDestroy(c->exec);
-            cudaFree(c->d_items);
-            cudaFree(c->d_plans);
-            for (void *p : c->scratch) cudaFree(p);
-            delete c;
+            free_ctx(it->second);
             it = g_cache.erase(it);
         } else {
             ++it;
@@ -357,12 +386,10 @@ void mlc_batch_forget(mlc_plan_t plan) {
 // arrays: parallel branches * 2 + persistent flag (0 if the batch is unknown).
 extern "C" int mlc_debug_batch_choice(int count, const mlc_plan_t *plans, const void *const *f,
                                       void *const *phi) {
+    (void)f;
+    (void)phi;  // a batch is tuned once per set of plans, whatever arrays it solves
     std::vector<uintptr_t> key;
-    for (int k = 0; k < count; ++k) {
-        key.push_back((uintptr_t)plans[k]);
-        key.push_back((uintptr_t)f[k]);
-        key.push_back((uintptr_t)phi[k]);
-    }
+    for (int k = 0; k < count; ++k) key.push_back((uintptr_t)plans[k]);
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_cache.find(key);
     return it == g_cache.end() ? 0 : it->second->branches * 2 + it->second->persist;
@@ -372,12 +399,10 @@ extern "C" int mlc_debug_batch_choice(int count, const mlc_plan_t *plans, const 
 // batch (0 if the batch is unknown).
 extern "C" int mlc_debug_batch_chunk(int count, const mlc_plan_t *plans, const void *const *f,
                                      void *const *phi) {
+    (void)f;
+    (void)phi;  // a batch is tuned once per set of plans, whatever arrays it solves
     std::vector<uintptr_t> key;
-    for (int k = 0; k < count; ++k) {
-        key.push_back((uintptr_t)plans[k]);
-        key.push_back((uintptr_t)f[k]);
-        key.push_back((uintptr_t)phi[k]);
-    }
+    for (int k = 0; k < count; ++k) key.push_back((uintptr_t)plans[k]);
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_cache.find(key);
     return it == g_cache.end() ? 0 : it->second->chunk;

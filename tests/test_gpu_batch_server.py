@@ -193,3 +193,25 @@ def test_caller_scratch_and_small_launch_groups(torch_cuda):
     assert e.value.status == 1
     p.set_scratch(None)
     assert torch.equal(p.solve(f), ref)
+
+
+def test_batch_new_arrays_reuse_the_graph(torch_cuda):
+    """A batch solved again with other f / phi arrays for the same plans
+    replays the tuned graph with rewritten problem records: every result
+    equals the standalone solve of the new charge, on another stream too."""
+    from paper_1702_08111_gb300 import mlc
+    torch = torch_cuda
+    plans = [mlc.Plan(32, 8, 8, 4, 4), mlc.Plan(64, 16, 16, 4, 6, tier=SPLIT)]
+    tiers = [FP64, SPLIT]
+    Ns = [32, 64]
+    for rnd, stream in enumerate([None, torch.cuda.Stream(), None]):
+        fs = [charge(torch, N, 40 + 10 * rnd + k, 3, t) for k, (N, t) in enumerate(zip(Ns, tiers))]
+        phis = [torch.empty((N,) * 3, dtype=torch.float64, device="cuda") for N in Ns]
+        mlc.batch_solve(plans, fs, phis, stream=stream)
+        torch.cuda.synchronize()
+        choice = mlc.batch_choice(plans, fs, phis)
+        if rnd == 0:
+            first = choice
+        assert choice == first  # tuned once for the set of plans
+        for p, f, ph in zip(plans, fs, phis):
+            assert torch.equal(ph, p.solve(f).clone())
