@@ -115,11 +115,10 @@ mlc_status mlc_params_init(mlc_params *p, int N, int n, int s, int P, int Q);
  * and allocates the workspace.  Synchronises the device.
  * INVALID_ARG if: out is NULL; N, n, s, C, P, Q, levels break the rules
  * above; g_beta < s - C b.  UNSUPPORTED if: n is not one of 4, 8, 12, 16, 24,
- * 32; the patch FFT length (the power of two >= 2(n+s)) is above 64 (128 in
- * the split tiers); n > 16 outside the split tiers; the coarse FFT length
- * (the smallest even 2^a 3^b 5^c >= twice the largest coarse lag) is above
- * 512.  With levels > 2 the plan of the next coarser level is created with
- * it, with its scratch, so that no solve allocates.
+ * 32; the patch FFT length (the power of two >= 2(n+s)) is above 128; the
+ * coarse FFT length (the smallest even 2^a 3^b 5^c >= twice the largest
+ * coarse lag) is above 512.  With levels > 2 the plan of the next coarser
+ * level is created with it, with its scratch, so that no solve allocates.
  */
 mlc_status mlc_plan_create(int N, int patch, int support, int coarsening, int P, int Q,
                            mlc_plan_t *out);
