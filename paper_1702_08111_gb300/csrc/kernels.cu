@@ -1759,18 +1759,19 @@ struct ResArgs {
 // FP64 by tier); T: arithmetic of the interpolation and the difference, where
 // cancellation needs the extra bits (FP64 or double-float).  The residual
 // leaves in T.
-template <typename TB, typename T>
+template <typename TB, typename T, int K>
 __global__ void __launch_bounds__(256) k_resid(ResArgs a) {
     extern __shared__ double rsm[];
     const int slot = blockIdx.y;
     int p;
     const PlanPtrs &PP = item_plan(a.it, blockIdx.x, p);
     const int axis = slot / a.npa, c4 = (a.pl0 + (slot % a.npa) * a.n) / 4;
-    const int K = 2 * a.b + 2, wa = a.wa, nc = a.nc, kl = -a.s / 4;
+    const int wa = a.wa, nc = a.nc, kl = -a.s / 4;  // K = 2b + 2 stencil points
     const int klo = -a.ga / 4 - a.b;  // coarse rows the stencils reach (4 | ga, 4 | n)
     const int khi = (a.n + a.ga) / 4 + a.b;
     const int nk = khi - klo + 1;
     T *Tv = (T *)rsm;                 // nk x wa: interpolated along v on coarse rows u = 4k
+    T *Cv = Tv + nk * wa;             // nk x nk: phi^i at the plane's coarse points (u, v) = 4 (ka, kb)
     const TB *cl = (const TB *)PP.cl + (long)p * nc * nc * nc;
     const TB *fp = (const TB *)PP.fp + ((long)p * gridDim.y + slot) * wa * wa;
     // phi^i at the coarse point (u, v) = (4 ka, 4 kb) of this plane
@@ -1783,16 +1784,21 @@ __global__ void __launch_bounds__(256) k_resid(ResArgs a) {
             return FT<T>::zero();
         return FT<T>::of(cl[((long)(i0 - kl) * nc + (i1 - kl)) * nc + (i2 - kl)]);
     };
+    // the plane's coarse values, loaded once (independent loads, one per thread)
+    for (int e = threadIdx.x; e < nk * nk; e += blockDim.x) Cv[e] = clp(klo + e / nk, klo + e % nk);
+    __syncthreads();
     for (int e = threadIdx.x; e < nk * wa; e += blockDim.x) {
-        const int k = klo + e / wa, v = e % wa - a.ga;
+        const int kr = e / wa, v = e % wa - a.ga;
         const int rv = v & 3;
+        const T *crow = Cv + kr * nk - klo;
         T t;
         if (rv == 0) {
-            t = clp(k, v >> 2);
+            t = crow[v >> 2];
         } else {
             const int k0 = (v >> 2) - a.b;
             t = FT<T>::zero();
-            for (int j = 0; j < K; ++j) t = FT<T>::fma(pick<T>(a.lw[rv][j], a.lwd[rv][j]), clp(k, k0 + j), t);
+#pragma unroll
+            for (int j = 0; j < K; ++j) t = FT<T>::fma(pick<T>(a.lw[rv][j], a.lwd[rv][j]), crow[k0 + j], t);
         }
         Tv[e] = t;
     }
@@ -1807,6 +1813,7 @@ __global__ void __launch_bounds__(256) k_resid(ResArgs a) {
         } else {
             const int k0 = (u >> 2) - a.b;
             iv = FT<T>::zero();
+#pragma unroll
             for (int j = 0; j < K; ++j)
                 iv = FT<T>::fma(pick<T>(a.lw[ru][j], a.lwd[ru][j]), FT<T>::rn(Tv[(k0 + j - klo) * wa + (v + a.ga)]), iv);
         }
@@ -3107,10 +3114,15 @@ void configure_kernels() {
     MLC_DIR_ATTR(24)
     MLC_DIR_ATTR(32)
 #undef MLC_DIR_ATTR
-    cudaFuncSetAttribute(k_resid<dfl, dfl>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_resid<float, dfl>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_resid<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_resid<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+#define MLC_RES_ATTR(KK)                                                                            \
+    cudaFuncSetAttribute(k_resid<dfl, dfl, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);    \
+    cudaFuncSetAttribute(k_resid<float, dfl, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);  \
+    cudaFuncSetAttribute(k_resid<float, double, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
+    cudaFuncSetAttribute(k_resid<double, double, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    MLC_RES_ATTR(4)
+    MLC_RES_ATTR(6)
+    MLC_RES_ATTR(8)
+#undef MLC_RES_ATTR
     cudaFuncSetAttribute(k_moments<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_moments<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
@@ -3212,15 +3224,23 @@ cudaError_t launch_resid(const mlc_plan_s *pl, const Items &it, cudaStream_t st)
     lagrange_rows_df(g.b, a.lw);
     lagrange_rows(g.b, a.lwd);
     const int nk = (g.n + 2 * g.ga) / 4 + 2 * g.b + 1;
-    const size_t sm = 8 * (size_t)nk * g.wa;
+    const size_t sm = 8 * (size_t)nk * (g.wa + nk);
     dim3 grid(it.nitems, 3 * g.npa);
-    if (g.fine == FINE_F64) {
-        if (g.conv == CONV_F32) k_resid<float, double><<<grid, 256, sm, st>>>(a);
-        else k_resid<double, double><<<grid, 256, sm, st>>>(a);
-    } else {
-        if (g.conv == CONV_F32) k_resid<float, dfl><<<grid, 256, sm, st>>>(a);
-        else k_resid<dfl, dfl><<<grid, 256, sm, st>>>(a);
+#define MLC_RES(KK)                                                                         \
+    if (g.fine == FINE_F64) {                                                               \
+        if (g.conv == CONV_F32) k_resid<float, double, KK><<<grid, 256, sm, st>>>(a);       \
+        else k_resid<double, double, KK><<<grid, 256, sm, st>>>(a);                         \
+    } else {                                                                                \
+        if (g.conv == CONV_F32) k_resid<float, dfl, KK><<<grid, 256, sm, st>>>(a);          \
+        else k_resid<dfl, dfl, KK><<<grid, 256, sm, st>>>(a);                               \
     }
+    switch (2 * g.b + 2) {
+        case 4: MLC_RES(4) break;
+        case 6: MLC_RES(6) break;
+        case 8: MLC_RES(8) break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef MLC_RES
     return cudaGetLastError();
 }
 
