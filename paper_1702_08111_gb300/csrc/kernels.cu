@@ -2089,8 +2089,10 @@ __global__ void __launch_bounds__(128, 6) k_boundary(BndArgs a) {
     } else {
         acc = FT<T>::zero();
         const int kb = (gu >> 2) - a.b - a.olo;
-        for (int e = 0; e < K; ++e)
-            if (in_range(kb + e, a.no, a.err))
+        // unrolled to the largest stencil (b = 3) so the K loads issue together
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            if (e < K && in_range(kb + e, a.no, a.err))
                 acc = FT<T>::fma(pick<T>(a.lw[ru][e], a.lwd[ru][e]), FT<T>::rn(tpl[(long)(kb + e) * (a.N + 1)]), acc);
     }
     // local corrections of the patches whose Omega_beta holds g (ascending index);
