@@ -99,6 +99,9 @@ typedef struct {
                        coarse solve is Hockney's; the Mehrstellen correction
                        (eq. mcapplicationfullmultipole) is added on the finest level
                        only.  2 <= levels <= 6                                         */
+    int coarse_s;   /* support s of the coarser levels' patches, i.e. their inner radius
+                       (g_alpha = coarse_s - C b; Sec. 7.4 raises alpha at coarser levels);
+                       -1: s.  Same rules as s                                          */
 } mlc_params;
 
 typedef struct mlc_plan_s *mlc_plan_t;

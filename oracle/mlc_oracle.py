@@ -57,7 +57,9 @@ R16 Multilevel MLC (Sec. 5), levels > 2: with every level covering the whole
     the MLC solve of F^H on the coarse grid: its domain is the smallest box of
     whole patches from min(F^H lo, phi^H lo) that holds the support of F^H and
     the nodes phi^H is needed on (the proper nesting of eq.
-    propernesting2fdiscr), with the same n, s, P, Q, b, g_beta and mode.  The
+    propernesting2fdiscr), with the same n, P, Q, b, g_beta and mode, and
+    the support s, or coarse_s where given (a larger inner radius alpha at
+    the coarser levels, as Sec. 7.4 suggests).  The
     upward pass interpolates the uncorrected coarse solution (eq.
     mlcmultilevel); the Mehrstellen correction (eq.
     mcapplicationfullmultipole) adds C2 h_l^2 times the level's own charge
@@ -107,6 +109,7 @@ class Params:
     nD: int = 128
     zeta: int = 2
     levels: int = 2          # Sec. 5: number of levels (2: the two-level algorithm of Sec. 4)
+    coarse_s: int | None = None  # support s of the coarser levels (R16; None: s)
     h_level: float | None = None   # mesh spacing of this level (default 1/N, the finest level)
     correction: bool = True  # add C2 h^2 f at the end (eq. mcapplicationfulldiscr); R16
 
@@ -692,10 +695,11 @@ def coarse_level_params(prm: Params):
     c0 = min(flo, olo)
     top = max(fhi, ohi)
     Nc = prm.n * (-(-(top - c0 + 1) // prm.n))  # whole patches; node c0 + Nc carries no charge
-    child = Params(N=Nc, n=prm.n, s=prm.s, P=prm.P, Q=prm.Q, C=prm.C, beta=prm.beta, b=prm.b,
+    cs = prm.s if prm.coarse_s is None else prm.coarse_s
+    child = Params(N=Nc, n=prm.n, s=cs, P=prm.P, Q=prm.Q, C=prm.C, beta=prm.beta, b=prm.b,
                    mode=prm.mode, nD=prm.nD, zeta=prm.zeta, levels=prm.levels - 1,
-                   h_level=prm.H, correction=False)
-    assert child.g_beta == prm.g_beta and child.g_alpha == prm.g_alpha
+                   h_level=prm.H, correction=False, coarse_s=prm.coarse_s)
+    assert child.g_beta == prm.g_beta or prm.mode == "mlc0"
     return c0, child
 
 

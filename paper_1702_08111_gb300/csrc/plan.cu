@@ -589,7 +589,7 @@ mlc_status mlc_params_init(mlc_params *p, int N, int n, int s, int P, int Q) {
     if (!p) return MLC_ERR_INVALID_ARG;
     p->N = N; p->n = n; p->s = s; p->C = 4; p->P = P; p->Q = Q;
     p->g_beta = -1; p->b = -1; p->tier = MLC_TIER_FP64; p->mode = MLC_MODE_MLC;
-    p->dgf_nD = -1; p->dgf_zeta = -1; p->conv_chunk = -1; p->levels = -1;
+    p->dgf_nD = -1; p->dgf_zeta = -1; p->conv_chunk = -1; p->levels = -1; p->coarse_s = -1;
     return MLC_OK;
 }
 
@@ -790,6 +790,7 @@ mlc_status make_coarser_level(mlc_plan_s *pl, const double *dgf_host, int dgf_Lh
     mlc_params cp = pl->params;
     cp.N = Nc;
     cp.levels = G.levels - 1;
+    if (cp.coarse_s > 0) cp.s = cp.coarse_s;  // the coarser levels' inner radius
     mlc_plan_t ch = nullptr;
     TRY(create_plan(&cp, dgf_host, dgf_Lh, &ch, G.H, false));
     pl->child = ch;

@@ -54,14 +54,14 @@ double estimate_ms(const mlc_params &p) {
 }
 
 struct Key {
-    int v[14];
+    int v[15];
     bool operator<(const Key &o) const { return std::memcmp(v, o.v, sizeof(v)) < 0; }
 };
 
 Key key_of(const mlc_params &p) {
     Key k;
-    const int v[14] = {p.N, p.n, p.s, p.C, p.P, p.Q, p.g_beta, p.b, p.tier, p.mode, p.dgf_nD, p.dgf_zeta,
-                       p.conv_chunk, p.levels};
+    const int v[15] = {p.N, p.n, p.s, p.C, p.P, p.Q, p.g_beta, p.b, p.tier, p.mode, p.dgf_nD, p.dgf_zeta,
+                       p.conv_chunk, p.levels, p.coarse_s};
     std::memcpy(k.v, v, sizeof(v));
     return k;
 }
@@ -108,6 +108,7 @@ size_t estimate_bytes(const mlc_params &p) {
         mlc_params c = p;
         c.N = (int)(n * ((span + n - 1) / n));
         c.levels = p.levels - 1;
+        if (c.coarse_s > 0) c.s = c.coarse_s;
         const long Nc = c.N, npc = Nc / n, NPc = npc * npc * npc;
         const long chunk = std::min<long>(p.conv_chunk > 0 ? p.conv_chunk : 1024, NPc);
         bytes += (long)estimate_bytes(c) + Nc * Nc * Nc * 12 +

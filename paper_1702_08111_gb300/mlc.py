@@ -48,7 +48,7 @@ class MLCError(RuntimeError):
 class mlc_params(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int) for k in
                 ("N", "n", "s", "C", "P", "Q", "g_beta", "b", "tier", "mode", "dgf_nD", "dgf_zeta",
-                 "conv_chunk", "levels")]
+                 "conv_chunk", "levels", "coarse_s")]
 
 
 class mlc_request(ctypes.Structure):
@@ -124,12 +124,13 @@ def _check(rc: int, what: str):
 
 
 def make_params(N, n, s, P=4, Q=4, C=4, g_beta=-1, b=-1, tier=MLC_TIER_FP64, mode=MLC_MODE_MLC,
-                dgf_nD=-1, dgf_zeta=-1, conv_chunk=-1, levels=-1) -> mlc_params:
+                dgf_nD=-1, dgf_zeta=-1, conv_chunk=-1, levels=-1, coarse_s=-1) -> mlc_params:
     p = mlc_params()
     load_library().mlc_params_init(ctypes.byref(p), N, n, s, P, Q)
     p.C, p.g_beta, p.b, p.tier, p.mode, p.dgf_nD, p.dgf_zeta = C, g_beta, b, tier, mode, dgf_nD, dgf_zeta
     p.conv_chunk = conv_chunk
     p.levels = levels
+    p.coarse_s = coarse_s
     return p
 
 

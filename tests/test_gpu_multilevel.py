@@ -51,7 +51,7 @@ def _oracle(kw, f64, G1):
     if key not in _ORACLE:
         mode = "mlc0" if kw.get("mode", 0) else "mlc"
         prm = O.Params(N=kw["N"], n=kw["n"], s=kw["s"], P=kw["P"], Q=kw["Q"], mode=mode,
-                       levels=kw["levels"])
+                       levels=kw["levels"], coarse_s=kw.get("coarse_s"))
         st = {}
         phi = O.solve_open(prm, f64, G1=G1, stages=st)
         _ORACLE[key] = (prm, phi, st)
@@ -73,11 +73,12 @@ CASES = [
     dict(N=32, n=8, s=12, P=4, Q=4, levels=3),            # MLC with the Legendre ring
     dict(N=32, n=8, s=16, P=4, Q=4, levels=4, mode=1),    # MLC-0, two coarser levels
     dict(N=64, n=16, s=16, P=4, Q=6, levels=3),           # 27-point operator, n = 16
+    dict(N=32, n=8, s=12, P=4, Q=4, levels=3, coarse_s=16),  # wider inner radius below
 ]
 
 
 @pytest.mark.parametrize("tier", [FP64, DF, SPLIT])
-@pytest.mark.parametrize("kw", CASES, ids=["mlc_l3", "mlc0_l4", "q6_l3"])
+@pytest.mark.parametrize("kw", CASES, ids=["mlc_l3", "mlc0_l4", "q6_l3", "coarse_s"])
 def test_multilevel_against_oracle(torch_cuda, G, kw, tier):
     from paper_1702_08111_gb300 import mlc
     torch = torch_cuda
@@ -104,7 +105,7 @@ def test_multilevel_against_oracle(torch_cuda, G, kw, tier):
     # a coarser level changes phi^H only by that level's own barrier error
     # (largest for the 27-point case: g_alpha = 4 under an 8-point stencil)
     two = mlc.Plan(N, kw["n"], kw["s"], kw["P"], kw["Q"], tier=tier,
-                   **{k: v for k, v in pk.items() if k != "levels"})
+                   **{k: v for k, v in pk.items() if k not in ("levels", "coarse_s")})
     phi2 = two.solve(f).cpu().numpy()
     assert 0.0 < relmax(phi.cpu().numpy(), phi2) < 1e-2
 

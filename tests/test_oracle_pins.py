@@ -500,3 +500,26 @@ def test_coarse_level_solve_approximates_coarse_convolution(G4, bump32):
         assert np.array_equal(st["phiH"], O.coarse_level_solve(prm, st["FH"], G4))
         diffs.append(np.abs(st["phiH"] - direct).max() / np.abs(direct).max())
     assert diffs[0] < 1e-4 and diffs[1] < diffs[0] / 5, diffs
+
+
+def test_coarse_level_takes_coarse_support(G4, bump32):
+    # coarse_s sets the coarser levels' support (their inner radius): the
+    # coarse problem's parameters carry it, and with coarse_s = s the solve is
+    # the same as without it; a larger coarse radius brings the coarse-level
+    # solve closer to the direct coarse convolution
+    N, bumps, f = bump32
+    base = O.Params(N=N, n=8, s=12, nD=ND, mode="mlc0", levels=3)
+    same = O.Params(N=N, n=8, s=12, nD=ND, mode="mlc0", levels=3, coarse_s=12)
+    wide = O.Params(N=N, n=8, s=12, nD=ND, mode="mlc0", levels=3, coarse_s=24)
+    _, child = O.coarse_level_params(wide)
+    assert (child.s, child.g_alpha, child.coarse_s) == (24, 16, 24)
+    assert np.array_equal(O.mlc_solve(base, f, G1=G4), O.mlc_solve(same, f, G1=G4))
+    diffs = []
+    for prm in (base, wide):
+        st = {}
+        O.mlc_solve(prm, f, G1=G4, stages=st)
+        olo, ohi = prm.phih_extent
+        no = ohi - olo + 1
+        direct = O.direct_sum(G4, st["FH"], (st["FH_lo"],) * 3, (olo,) * 3, (no,) * 3, prm.H * prm.H)
+        diffs.append(np.abs(st["phiH"] - direct).max() / np.abs(direct).max())
+    assert diffs[1] < diffs[0] / 5, diffs
