@@ -100,7 +100,7 @@ typedef struct {
                        (eq. mcapplicationfullmultipole) is added on the finest level
                        only.  2 <= levels <= 6                                         */
     int coarse_s;   /* support s of the coarser levels' patches, i.e. their inner radius
-                       (g_alpha = coarse_s - C b; Sec. 7.4 raises alpha at coarser levels);
+                       (g_alpha = coarse_s - C b; Sec. 7.2 raises alpha at coarser levels);
                        -1: s.  Same rules as s                                          */
 } mlc_params;
 

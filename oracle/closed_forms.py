@@ -50,7 +50,7 @@ def smooth_potential_grid(N: int, nodes: int | None = None, Ro: float = 0.25, ce
     return smooth_potential(r, Ro)
 
 
-# Sec. 7.3: oscillatory charge (1/R_o^3) (r - r^2)^2 sin^2(gamma r / 2) on r < 1,
+# Sec. 7.2: oscillatory charge (1/R_o^3) (r - r^2)^2 sin^2(gamma r / 2) on r < 1,
 # gamma = 4 mu pi with mu = 7, three copies of radius R_o = 0.05.
 OSC_GAMMA = 28.0 * np.pi
 OSC_RADIUS = 0.05
@@ -58,7 +58,7 @@ OSC_CENTRES = ((3 / 16, 7 / 16, 13 / 16), (7 / 16, 13 / 16, 3 / 16), (13 / 16, 3
 
 
 def oscillatory_potential(r: np.ndarray, Ro: float, gamma: float = OSC_GAMMA) -> np.ndarray:
-    """Sec. 7.3 exact potential of one oscillatory charge, r = |x - x_o| / R_o.
+    """Sec. 7.2 exact potential of one oscillatory charge, r = |x - x_o| / R_o.
 
     Inside, a polynomial in r plus 1/r terms and cos(gamma r), sin(gamma r)
     terms whose 1/r parts cancel as r -> 0 (the value at r = 0 is the limit);
@@ -81,7 +81,7 @@ def oscillatory_potential(r: np.ndarray, Ro: float, gamma: float = OSC_GAMMA) ->
 
 def oscillatory_potential_grid(N: int, nodes: int | None = None, Ro: float = OSC_RADIUS,
                                centres=OSC_CENTRES, gamma: float = OSC_GAMMA) -> np.ndarray:
-    """Superposed Sec. 7.3 potential of the three charges at the nodes g h, g in [0, nodes)^3."""
+    """Superposed Sec. 7.2 potential of the three charges at the nodes g h, g in [0, nodes)^3."""
     nodes = N if nodes is None else nodes
     x = np.arange(nodes, dtype=np.float64) / N
     phi = np.zeros((nodes,) * 3)

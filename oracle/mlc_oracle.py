@@ -59,7 +59,7 @@ R16 Multilevel MLC (Sec. 5), levels > 2: with every level covering the whole
     the nodes phi^H is needed on (the proper nesting of eq.
     propernesting2fdiscr), with the same n, P, Q, b, g_beta and mode, and
     the support s, or coarse_s where given (a larger inner radius alpha at
-    the coarser levels, as Sec. 7.4 suggests).  The
+    the coarser levels, as Sec. 7.2 suggests).  The
     upward pass interpolates the uncorrected coarse solution (eq.
     mlcmultilevel); the Mehrstellen correction (eq.
     mcapplicationfullmultipole) adds C2 h_l^2 times the level's own charge

@@ -91,7 +91,7 @@ PAPER_OSC_CENTRES = ((3 / 16, 7 / 16, 13 / 16), (7 / 16, 13 / 16, 3 / 16), (13 /
 
 
 def paper_oscillatory_charge(N: int, nodes: int | None = None, dtype=np.float64) -> np.ndarray:
-    """The oscillatory test charge of Sec. 7.3: three copies of
+    """The oscillatory test charge of Sec. 7.2: three copies of
     (1/R_o^3) (r - r^2)^2 sin^2(gamma r / 2), r < 1, with R_o = 0.05,
     gamma = 4 mu pi, mu = 7, at the three centres the paper gives."""
     Ro, gamma = 0.05, 28.0 * math.pi

@@ -1,5 +1,5 @@
 """The paper's own test parameters on the GPU: patches of n = 32 nodes per side
-(H/R = 1/4, Sec. 7), the Sec. 7.1 smooth and Sec. 7.3 oscillatory charges,
+(H/R = 1/4, Sec. 7), the Sec. 7.1 smooth and Sec. 7.2 oscillatory charges,
 and the N = 256 two-level rows of Tables 1-7 as soft pins.
 
 Parameter mapping (Sec. 4, Sec. 7): R = n h / 2 = 16 h, so a correction
@@ -97,7 +97,7 @@ def test_n32_mlc0_against_oracle(torch_cuda, tier):
 
 def test_n32_mlc_oscillatory_against_oracle(torch_cuda):
     """n = 32, MLC with the Legendre ring (alpha = 1.5, beta = 2, P = 4,
-    27-point): 64^3 with the Sec. 7.3 oscillatory charge."""
+    27-point): 64^3 with the Sec. 7.2 oscillatory charge."""
     G6 = O.dgf_octant(6, 128, 2)
     f = I.paper_oscillatory_charge(64)
     kw = dict(N=64, n=32, s=20, P=4, Q=6, g_beta=16)
@@ -105,7 +105,7 @@ def test_n32_mlc_oscillatory_against_oracle(torch_cuda):
 
 
 def test_oscillatory_charge_fp64_against_oracle(torch_cuda):
-    """The Sec. 7.3 charge through the FP64 tier (n = 16) at the FP64 bar."""
+    """The Sec. 7.2 charge through the FP64 tier (n = 16) at the FP64 bar."""
     from paper_1702_08111_gb300 import mlc
     torch = torch_cuda
     G6 = O.dgf_octant(6, 128, 2)

@@ -243,7 +243,7 @@ def test_closed_form_smooth_charge_sec71():
 
 
 def test_closed_form_oscillatory_charge_sec73():
-    # Sec. 7.3: the radial Laplacian of the interior potential is the charge,
+    # Sec. 7.2: the radial Laplacian of the interior potential is the charge,
     # value and slope match the monopole at r = 1 (gamma = 28 pi), the centre
     # value is the r -> 0 limit, and the monopole strength is minus the charge
     # over 4 pi; then the oracle's numpy form against the symbolic one
@@ -470,7 +470,7 @@ def test_coarse_level_params_worked_example():
 
 
 def test_multilevel_mlc0_error_insensitive_to_levels(G4, bump32):
-    # Sec. 7.2: the MLC-0 error does not depend on the number of levels (Table 8
+    # Sec. 7.1.2: the MLC-0 error does not depend on the number of levels (Table 8
     # against Table 4); and it still falls with the correction radius
     N, bumps, f = bump32
     plain = O.plain_solution(O.Params(N=N, n=8, s=8, nD=ND), f, G1=G4)
