@@ -500,8 +500,9 @@ def run_paper_params(args, flush, stream):
     """The paper's own settings (Sec. 7: n = 32, H/R = 1/4, the Sec. 7.1 smooth
     charge): the two-level 27-point solve with alpha = 1.75, beta = 3.25,
     P = 4 (the Table 7 row) at 256^3 in the split and plain FP64 tiers, and
-    the three-level solve of the Table 9 row at 512^3 in the split tier;
-    Mpoints/s and the scaled max error against the closed form."""
+    the three-level solve of the Table 9 row at 512^3 and 1024^3 in the split
+    tier; Mpoints/s and (up to 512^3) the scaled max error against the closed
+    form."""
     import torch
     from oracle import closed_forms as CF
     from paper_1702_08111_gb300 import mlc
@@ -509,7 +510,8 @@ def run_paper_params(args, flush, stream):
     steps = max(3, args.steps // 4)
     kw = dict(b=3, g_beta=36)
     cases = [("n32_256_split", 256, "split", 2, 1.96490e-7), ("n32_256_fp64", 256, "fp64", 2, 1.96490e-7),
-             ("n32_512_3level_split", 512, "split", 3, 1.0782e-6)]
+             ("n32_512_3level_split", 512, "split", 3, 1.0782e-6),
+             ("n32_1024_3level_split", 1024, "split", 3, 1.6596e-7)]
     exact = {}
     for name, N, tier, levels, paper in cases:
         f64 = I.paper_smooth_charge(N)
@@ -519,16 +521,20 @@ def run_paper_params(args, flush, stream):
         ms, pl = time_plan(plan, f, phi, steps, 3, flush, stream, 1, per_launch_steps=1)
         wl = SimpleNamespace(N=N, n=32, s=24, Q=6, name=name)
         roof = roofline_for(wl, plan, pl, tier)
-        if N not in exact:
-            exact[N] = CF.smooth_potential_grid(N)
-        ph = phi.cpu().numpy()
-        err = float(np.abs(ph - exact[N]).max() / np.abs(exact[N]).max())
+        err = None  # 1024^3: the closed form takes a minute of host time; the tests pin it
+        if N <= 512:
+            if N not in exact:
+                exact[N] = CF.smooth_potential_grid(N)
+            ph = phi.cpu().numpy()
+            err = float(np.abs(ph - exact[N]).max() / np.abs(exact[N]).max())
+            del ph
         out[name] = {"N": N, "n": 32, "s": 24, "g_beta": 36, "P": 4, "Q": 6, "levels": levels, "tier": tier,
                      "ms_per_step": round(ms, 4), "value": round(float(N) ** 3 / (ms * 1e-3) / 1e6, 2),
                      "unit": "Mpoints/s", "max_rel_err_vs_closed_form": err, "paper_error": paper,
                      "roofline": roof,
                      "per_launch_ms": {k: round(v, 4) for k, v in pl.items()}}
-        del plan, f, phi, ph
+        del plan, f, phi
+        torch.cuda.empty_cache()
     return out
 
 

@@ -222,7 +222,9 @@ mlc_status derive_geometry(const mlc_params &pp, Geom &g) {
     // patch sizes with a Dirichlet kernel instantiation; patch periods 32 to
     // 128 (at 128 the FP64 and double-float slabs stream their rows)
     if (g.n != 4 && g.n != 8 && g.n != 12 && g.n != 16 && g.n != 24 && g.n != 32) return MLC_ERR_UNSUPPORTED;
-    if (g.M < 32 || g.M > 128 || g.Mc > 512) return MLC_ERR_UNSUPPORTED;
+    // (a multilevel plan's own coarse period is never used: its coarse solve
+    // is the next level's MLC solve)
+    if (g.M < 32 || g.M > 128 || (g.levels <= 2 && g.Mc > 512)) return MLC_ERR_UNSUPPORTED;
     g.S = (2 * g.b + 2) * (2 * g.b + 2);
     g.nc = (g.n + 2 * g.s) / 4 + 1;
     g.nzr = 0;
@@ -474,7 +476,7 @@ mlc_status build_tables(mlc_plan_s *pl) {
         return tw;
     };
     TRY(dev_upload(pl, &pl->tw, twiddles(g.M)));
-    TRY(dev_upload(pl, &pl->tw_c, twiddles(g.Mc)));
+    if (g.levels <= 2) TRY(dev_upload(pl, &pl->tw_c, twiddles(g.Mc)));  // coarse Hockney solve
 
     // Dirichlet tables: half DST-I matrix and eigenvalues of the stencil / h^2
     const int m = n - 1, hn = n / 2;
@@ -626,7 +628,7 @@ mlc_status create_plan(const mlc_params *params, const double *dgf_host, int dgf
     pl->correction = correction;
     // lag extent: local fields n + s, coarse Lc, basis fields (checked in build_tables)
     Geom &G = pl->g;
-    G.L = std::max(G.n + G.s, G.Lc);
+    G.L = std::max(G.n + G.s, G.levels > 2 ? 0 : G.Lc);  // a multilevel plan convolves no coarse lags
     const int Lbasis_bound = G.n + G.gb + 4 * G.b + 12;
     int Lneed = std::max(G.L, G.gb > G.ga ? Lbasis_bound : 0);
     if (Lneed >= G.zeta * G.nD) G.nD = (Lneed + G.zeta) / G.zeta + 1;
@@ -647,12 +649,15 @@ mlc_status create_plan(const mlc_params *params, const double *dgf_host, int dgf
     if (st == MLC_OK) st = build_tables(pl);
     auto alloc_all = [&]() -> mlc_status {
         TRY(dev_alloc(pl, &pl->khat, (size_t)G.Mh * G.Mh * G.Mh, false));
-        TRY(dev_alloc(pl, &pl->khat_c, (size_t)G.Mhc * G.Mhc * G.Mhc, false));
         TRY_CUDA(build_even_spectrum(pl->dgf, pl->dgf_L, G.M, std::min(G.n + G.s, G.M / 2),
                                      G.h * G.h / ((double)G.M * G.M * G.M), pl->khat));
-        TRY_CUDA(build_even_spectrum(pl->dgf, pl->dgf_L, G.Mc, G.Lc,
-                                     G.H * G.H / ((double)G.Mc * G.Mc * G.Mc), pl->khat_c));
-        if (G.fine == FINE_DF) {   // double-float copies for the coarse convolution: v = hi + lo
+        const bool hockney = G.levels <= 2;  // this plan runs the coarse Hockney solve itself
+        if (hockney) {
+            TRY(dev_alloc(pl, &pl->khat_c, (size_t)G.Mhc * G.Mhc * G.Mhc, false));
+            TRY_CUDA(build_even_spectrum(pl->dgf, pl->dgf_L, G.Mc, G.Lc,
+                                         G.H * G.H / ((double)G.Mc * G.Mc * G.Mc), pl->khat_c));
+        }
+        if (hockney && G.fine == FINE_DF) {   // double-float copies for the coarse convolution: v = hi + lo
             auto split = [](double v) {
                 const float h = (float)v;
                 return make_float2(h, (float)(v - (double)h));
@@ -727,8 +732,10 @@ mlc_status create_plan(const mlc_params *params, const double *dgf_host, int dgf
         }
         const size_t nf = G.nf, no = G.no, Mc = G.Mc, Mhc = G.Mhc;
         TRY(dev_alloc(pl, &pl->FH, nf * nf * nf));
-        TRY(dev_alloc(pl, &pl->cbuf0, std::max(nf * nf * Mhc, no * Mc * Mhc)));
-        TRY(dev_alloc(pl, &pl->cbuf1, std::max(nf * Mc * Mhc, no * no * Mhc)));
+        if (hockney) {
+            TRY(dev_alloc(pl, &pl->cbuf0, std::max(nf * nf * Mhc, no * Mc * Mhc)));
+            TRY(dev_alloc(pl, &pl->cbuf1, std::max(nf * Mc * Mhc, no * no * Mhc)));
+        }
         TRY(dev_alloc(pl, &pl->phiH, no * no * no));
         TRY(dev_alloc(pl, &pl->phiB, (size_t)G.n_planes_total));
         TRY(dev_alloc(pl, &pl->tpl, 3 * (size_t)(G.np + 1) * G.no * (G.N + 1)));

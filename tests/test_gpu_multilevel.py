@@ -221,3 +221,21 @@ def test_server_serves_multilevel_and_n32_requests(torch_cuda):
         srv.wait(t, 60000)
         assert torch.equal(phi, ref)
     srv.close()
+
+
+def test_paper_three_level_row_1024(torch_cuda):
+    """Table 9 at N = 1024 (1.07 G nodes on one GPU, 32768 patches of 32^3,
+    three levels, alpha = 1.75, beta = 3.25, P = 4), FP64 tier, against the
+    Sec. 7.1 closed form: within a factor of 5 of the printed 1.6596e-7."""
+    from paper_1702_08111_gb300 import mlc
+    torch = torch_cuda
+    N, paper = 1024, 1.6596e-7
+    f64 = I.paper_smooth_charge(N)
+    plan = mlc.Plan(N, 32, 24, 4, 6, b=3, g_beta=36, tier=FP64, levels=3)
+    phi = plan.solve(torch.from_numpy(f64).cuda()).cpu().numpy()
+    plan.status()
+    del plan
+    ex = CF.smooth_potential_grid(N)
+    err = relmax(phi, ex)
+    print(f"T9 N=1024 P=4: error {err:.5e}, paper {paper:.5e}, ratio {err / paper:.3f}")
+    assert paper / 5 <= err <= 5 * paper, err
