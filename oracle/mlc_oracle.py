@@ -88,7 +88,30 @@ STENCIL_B = {
     4: (-4.0, 1.0 / 3.0, 1.0 / 6.0, 0.0),  # L19, q = 4
     6: (-64.0 / 15.0, 7.0 / 15.0, 1.0 / 10.0, 1.0 / 30.0),  # L27, q = 6
 }
-C2 = 1.0 / 12.0  # Sec. 2, eq. (msCorr4)
+C2 = 1.0 / 12.0  # Sec. 2, eq. (msCorr4), for L19 and L27
+
+# R18 (Sec. 8): a q = 10 Mehrstellen operator in the 5 x 5 x 5 block (s = 2).
+# a_j depends on the orbit of j under the cube's symmetries, named by the
+# sorted absolute components.  These are the six orbits with the smallest
+# offsets for which the six conditions of Sec. 2 (eq. mehrstellenTau with
+# q = 10) have a solution: sum a_j = 0; sum a_j j_0^2 = 2 (consistency); and
+# sum a_j p(j) = 0 for every harmonic homogeneous polynomial p of degree 4, 6,
+# 8 and 10 (so the truncation error vanishes on harmonic functions up to
+# h^10).  Exact rationals; derived by oracle/derive_q10.py (sympy).
+STENCIL_ORBITS = {
+    10: {(0, 0, 0): Fraction(-1079, 210), (1, 0, 0): Fraction(24, 35), (1, 1, 0): Fraction(17, 210),
+         (1, 1, 1): Fraction(11, 420), (2, 0, 0): Fraction(-1, 60), (2, 1, 0): Fraction(-1, 420)},
+}
+# C2 of eq. (mehrstellenTau) for each operator: the h^2 term of the truncation
+# error is C2 h^2 Delta^2 phi, C2 = sum a_j j_0^4 / 4!  (1/12 for L19 and L27,
+# 2/35 for the q = 10 operator); the 4th-order correction adds C2 h^2 f.
+C2_OF = {4: 1.0 / 12.0, 6: 1.0 / 12.0, 10: 2.0 / 35.0}
+QS = (4, 6, 10)
+
+
+def stencil_reach(Q: int) -> int:
+    """Largest |offset component| of the operator (s of eq. discreteLaplacian)."""
+    return 2 if Q in STENCIL_ORBITS else 1
 
 
 # ---------------------------------------------------------------------------
@@ -114,18 +137,20 @@ class Params:
     correction: bool = True  # add C2 h^2 f at the end (eq. mcapplicationfulldiscr); R16
 
     def __post_init__(self):
-        if self.Q not in STENCIL_B:
-            raise ValueError("Q must be 4 or 6")
+        if self.Q not in QS:
+            raise ValueError("Q must be 4, 6 or 10")
         if self.C != 4:
             raise ValueError("coarsening ratio is 4 (Sec. 2)")
         if self.N % self.n or self.n % 4 or self.s % 4:
             raise ValueError("need n | N, 4 | n, 4 | s")
-        if self.b is None:
-            self.b = 2 if self.Q == 4 else 3
-        if self.beta is None:
-            self.beta = 3.0 if self.Q == 4 else 3.25
+        if self.b is None:  # q_I = 2b + 2 = q + 2 (Sec. 7)
+            self.b = {4: 2, 6: 3, 10: 5}[self.Q]
+        if self.beta is None:  # equal barrier terms beta^-q (Sec. 7): 3^4 ~ 2^6 ~ 2^10 / 16
+            self.beta = {4: 3.0, 6: 3.25, 10: 2.0}[self.Q]
         if self.levels < 2:
             raise ValueError("levels >= 2")
+        if self.Q == 10 and self.levels != 2:
+            raise ValueError("the q = 10 operator runs two levels (R18)")
         self.h = 1.0 / self.N if self.h_level is None else float(self.h_level)
         self.H = self.C * self.h
         self.R = self.n * self.h / 2.0
@@ -169,7 +194,14 @@ class Params:
 
     @property
     def phih_extent(self):
-        return (-self.b, self.N // 4 + self.b)
+        # R6; R18: the second boundary layer (one node off the face planes)
+        # reaches one coarse node further
+        e = self.b + (1 if stencil_reach(self.Q) > 1 else 0)
+        return (-e, self.N // 4 + e)
+
+    @property
+    def c2(self):
+        return C2_OF[self.Q]
 
     @property
     def npatch(self):
@@ -187,9 +219,18 @@ def patch_origin(prm: Params, i: int) -> np.ndarray:
 # ---------------------------------------------------------------------------
 
 def stencil(Q: int):
-    """List of (offset, b_{|offset|}) over [-1,1]^3 with nonzero coefficient."""
-    b = STENCIL_B[Q]
+    """List of (offset, a_offset) (h = 1) over [-s,s]^3 with nonzero coefficient."""
     out = []
+    if Q in STENCIL_ORBITS:
+        orb = STENCIL_ORBITS[Q]
+        for s0 in range(-2, 3):
+            for s1 in range(-2, 3):
+                for s2 in range(-2, 3):
+                    key = tuple(sorted((abs(s0), abs(s1), abs(s2)), reverse=True))
+                    if key in orb:
+                        out.append(((s0, s1, s2), float(orb[key])))
+        return out
+    b = STENCIL_B[Q]
     for s0 in (-1, 0, 1):
         for s1 in (-1, 0, 1):
             for s2 in (-1, 0, 1):
@@ -200,17 +241,29 @@ def stencil(Q: int):
 
 
 def apply_laplacian(phi: np.ndarray, Q: int, h: float) -> np.ndarray:
-    """Eq. (discreteLaplacian) on the interior G(D,-1) of the array's box."""
+    """Eq. (discreteLaplacian) on the interior G(D,-s) of the array's box."""
+    r = stencil_reach(Q)
     n0, n1, n2 = phi.shape
-    out = np.zeros((n0 - 2, n1 - 2, n2 - 2))
+    out = np.zeros((n0 - 2 * r, n1 - 2 * r, n2 - 2 * r))
     for (s0, s1, s2), c in stencil(Q):
-        out += c * phi[1 + s0:n0 - 1 + s0, 1 + s1:n1 - 1 + s1, 1 + s2:n2 - 1 + s2]
+        out += c * phi[r + s0:n0 - r + s0, r + s1:n1 - r + s1, r + s2:n2 - r + s2]
     return out / (h * h)
 
 
 def symbol(Q: int, c0, c1, c2):
     """Eigenvalue (h = 1) of the stencil on the product of 1D modes whose
-    shift-pair eigenvalues are 2 c_d."""
+    shift-pair eigenvalues are 2 c_d: sum_j a_j prod_d cos(j_d theta_d) with
+    cos(2 theta) = 2 c^2 - 1."""
+    if Q in STENCIL_ORBITS:
+        cs = (c0, c1, c2)
+        lam = 0.0
+        for off, a in stencil(Q):
+            t = a
+            for d in range(3):
+                k = abs(off[d])
+                t = t * (1.0 if k == 0 else (cs[d] if k == 1 else 2.0 * cs[d] * cs[d] - 1.0))
+            lam = lam + t
+        return lam
     b0, b1, b2, b3 = STENCIL_B[Q]
     return (b0 + 2 * b1 * (c0 + c1 + c2) + 4 * b2 * (c0 * c1 + c0 * c2 + c1 * c2)
             + 8 * b3 * c0 * c1 * c2)
@@ -224,6 +277,8 @@ def dgf_full(Q: int, nD: int, zeta: int) -> np.ndarray:
     """Solve L G = delta_0 on G(D_zeta,-1), G = -1/(4 pi |g|) on the boundary of
     D_zeta = [-zeta nD, zeta nD]^3; returns G on all of D_zeta."""
     M = zeta * nD
+    if stencil_reach(Q) > 1:
+        return _dgf_full_wide(Q, M)
     x = np.arange(-M, M + 1, dtype=np.float64)
     G = np.zeros((2 * M + 1,) * 3)
     # boundary values: exact free-space Green's function
@@ -244,6 +299,39 @@ def dgf_full(Q: int, nD: int, zeta: int) -> np.ndarray:
     del rhs
     uh /= lam
     u = scipy.fft.idstn(uh, type=1, workers=os.cpu_count())
+    G[1:-1, 1:-1, 1:-1] += u
+    return G
+
+
+def _dgf_full_wide(Q: int, M: int) -> np.ndarray:
+    """R18: the DGF of a two-layer operator (s = 2) on D_zeta = [-M, M]^3.
+
+    Residual-correction form with the free-space kernel w = -1/(4 pi |g|)
+    (w(0) = 0) as the reference field on the whole box: L u = delta - L w on
+    the nodes |g|_inf <= M - 1, u = 0 on |g|_inf = M, and G = w + u.  DST-I
+    continues u oddly across the boundary, so where the stencil reaches the
+    second layer |g|_inf = M + 1 it reads w minus the mirrored u; u = G - w
+    is O(|g|^-5) there (1e-12 of G at M = 256), far below the O((zeta nD)^-4)
+    effect of the boundary values themselves (App. A.1)."""
+    x = np.arange(-M - 1, M + 2, dtype=np.float64)
+    W = np.empty((2 * M + 3,) * 3)
+    for i, xi in enumerate(x):
+        r = np.sqrt(xi * xi + x[:, None] ** 2 + x[None, :] ** 2)
+        with np.errstate(divide="ignore"):
+            W[i] = -1.0 / (4.0 * math.pi * r)
+    W[M + 1, M + 1, M + 1] = 0.0
+    rhs = -apply_laplacian(W, Q, 1.0)  # nodes [-M+1, M-1]^3
+    rhs[M - 1, M - 1, M - 1] += 1.0
+    K = 2 * M - 1
+    c = np.cos(np.pi * np.arange(1, K + 1) / (2 * M))
+    lam = symbol(Q, c[:, None, None], c[None, :, None], c[None, None, :])
+    uh = scipy.fft.dstn(rhs, type=1, workers=os.cpu_count())
+    del rhs
+    uh /= lam
+    u = scipy.fft.idstn(uh, type=1, workers=os.cpu_count())
+    del uh
+    G = W[1:-1, 1:-1, 1:-1].copy()
+    del W
     G[1:-1, 1:-1, 1:-1] += u
     return G
 
@@ -480,6 +568,66 @@ def stencils_for(prm: Params, nodes: np.ndarray):
     return P.reshape(A, K * K, 3), W.reshape(A, K * K)
 
 
+def offplane_mask(pts: np.ndarray, n: int) -> np.ndarray:
+    """R18: nodes one step off a face plane along some axis (a coordinate that
+    is 1 or n-1 modulo n)."""
+    m = np.asarray(pts) % n
+    return np.any((m == 1) | (m == n - 1), axis=1)
+
+
+def outer_nodes(prm: Params) -> np.ndarray:
+    """R18: the second boundary layer of the s = 2 operator, globally: the
+    nodes on the planes n j -+ 1 (j in [0, N/n]) of some axis whose other two
+    coordinates lie in [0, N] (patch i reads the plane n i_d - 1 and
+    n i_d + n + 1 over its closed face), sorted."""
+    N, n = prm.N, prm.n
+    r = np.arange(0, N + 1, dtype=np.int64)
+    u, v = np.meshgrid(r, r, indexing="ij")
+    out = []
+    for d in range(3):
+        e1, e2 = [e for e in range(3) if e != d]
+        for c in sorted({n * j + sg for j in range(prm.np_ + 1) for sg in (-1, 1)}):
+            g = np.empty((u.size, 3), dtype=np.int64)
+            g[:, d] = c
+            g[:, e1] = u.ravel()
+            g[:, e2] = v.ravel()
+            out.append(g)
+    return np.unique(np.concatenate(out), axis=0)
+
+
+def stencils3_for(prm: Params, nodes: np.ndarray):
+    """R18: I^H stencils at nodes off the face planes: R4's tensor-product
+    Lagrange factor on every axis (the coarse node alone where the coordinate
+    is a multiple of 4, else the 2b+2 coarse nodes k0-b .. k0+b+1, k0 =
+    floor(g/4)); trivial axes carry weights (1, 0, ...) at a repeated node.
+    Returns coarse points (A, K^3, 3) and weights (A, K^3), K = 2b+2."""
+    b = prm.b
+    K = 2 * b + 2
+    g = np.asarray(nodes, dtype=np.int64)
+    A = g.shape[0]
+    kn = np.zeros((A, 3, K), dtype=np.int64)
+    wt = np.zeros((A, 3, K))
+    j = np.arange(K)
+    for d in range(3):
+        gd = g[:, d]
+        triv = (gd % 4) == 0
+        k0 = gd // 4
+        r = (gd - 4 * k0).astype(np.float64) / 4.0
+        w = np.ones((A, K))
+        for jj in range(K):
+            for ll in range(K):
+                if ll != jj:
+                    w[:, jj] *= (r + b - ll) / float(jj - ll)
+        kn[:, d, :] = np.where(triv[:, None], k0[:, None], k0[:, None] - b + j[None, :])
+        wt[:, d, :] = np.where(triv[:, None], (j[None, :] == 0).astype(np.float64), w)
+    P = np.empty((A, K, K, K, 3), dtype=np.int64)
+    P[..., 0] = kn[:, 0, :][:, :, None, None]
+    P[..., 1] = kn[:, 1, :][:, None, :, None]
+    P[..., 2] = kn[:, 2, :][:, None, None, :]
+    W = wt[:, 0, :][:, :, None, None] * wt[:, 1, :][:, None, :, None] * wt[:, 2, :][:, None, None, :]
+    return P.reshape(A, K ** 3, 3), W.reshape(A, K ** 3)
+
+
 class PointSet:
     """A set of relative integer points with a dense lookup map over a box."""
 
@@ -548,6 +696,7 @@ def mlc_solve(prm: Params, f_closed: np.ndarray, G1: np.ndarray | None = None, s
         Fcols[:, i] = f_closed[g[:, 0], g[:, 1], g[:, 2]]
 
     lap = stencil(prm.Q)
+    wide = stencil_reach(prm.Q) > 1  # R18: a second boundary layer one node off the faces
     ga_lo, ga_hi = prm.alpha_box
     gb_lo, gb_hi = prm.beta_box
 
@@ -555,7 +704,12 @@ def mlc_solve(prm: Params, f_closed: np.ndarray, G1: np.ndarray | None = None, s
     fb_lo, fb_hi = prm.field_box
     face_alpha = face_nodes_in_box(prm, ga_lo, ga_hi)
     coarse_field = box_points(fb_lo, fb_hi, 4)
-    phi_set = PointSet(np.concatenate([coarse_field, face_alpha]))
+    pts_list = [coarse_field, face_alpha]
+    if wide:
+        bx = box_points(ga_lo, ga_hi)
+        outer_alpha = bx[offplane_mask(bx, n)]
+        pts_list.append(outer_alpha)
+    phi_set = PointSet(np.concatenate(pts_list))
     Kphi = green_matrix(G1, phi_set.pts, src) * (h * h) * chi[None, :]
     PHI = Kphi @ Fcols  # (points, patches)
     del Kphi
@@ -577,7 +731,15 @@ def mlc_solve(prm: Params, f_closed: np.ndarray, G1: np.ndarray | None = None, s
         st_ring_P, st_ring_W = stencils_for(prm, face_ring)
         # points at which the basis fields G^h * P^h are needed
         lap_pts = (4 * (ck_ring[:, None, :] + np.array([o for o, _ in lap])[None, :, :])).reshape(-1, 3)
-        B_set = PointSet(np.concatenate([lap_pts, face_ring, 4 * st_ring_P.reshape(-1, 3)]))
+        b_list = [lap_pts, face_ring, 4 * st_ring_P.reshape(-1, 3)]
+        if wide:
+            bxb = box_points(gb_lo, gb_hi)
+            ob = bxb[offplane_mask(bxb, n)]
+            outer_ring = ob[~np.all((ob >= ga_lo) & (ob <= ga_hi), axis=1)]
+            # every coarse point a 3D stencil of a beta-box node can reach
+            k_lo, k_hi = gb_lo // 4 - prm.b - 1, -(-gb_hi // 4) + prm.b + 1
+            b_list += [outer_ring, 4 * box_points(k_lo, k_hi)]
+        B_set = PointSet(np.concatenate(b_list))
         Lcharge = (legendre_patch(prm) * chi[None, :]).T  # (src, npoly)
         BV = (green_matrix(G1, B_set.pts, src) * (h * h)) @ Lcharge  # (points, npoly)
 
@@ -654,21 +816,80 @@ def mlc_solve(prm: Params, f_closed: np.ndarray, G1: np.ndarray | None = None, s
         phiB[a0:a1] = loc_self[a0:a1] + np.sum(stG_W * (phiH_at - loc_st[a0:a1]), axis=1)
     del loc_st
 
+    if wide:
+        # ---- R18: the same eqs. (philocmlcII, mlcfulldiscr) on the second
+        # ---- boundary layer, with the interpolation stencil on all three axes
+        gout = outer_nodes(prm)
+        omap = -np.ones((N + 3,) * 3, dtype=np.int64)  # nodes [-1, N+1]^3
+        omap[gout[:, 0] + 1, gout[:, 1] + 1, gout[:, 2] + 1] = np.arange(len(gout))
+        K3 = (2 * prm.b + 2) ** 3
+        oself = np.zeros(len(gout))
+        ost = np.zeros((len(gout), K3))
+        st3A_P, _ = stencils3_for(prm, outer_alpha)
+        i_selfA = phi_set.index(outer_alpha)
+        i_stA = phi_set.index(4 * st3A_P)  # (|outerA|, K3)
+        del st3A_P
+        if ring:
+            st3R_P, _ = stencils3_for(prm, outer_ring)
+            BVo_self = BV[B_set.index(outer_ring)]
+            i_stR = B_set.index(4 * st3R_P)
+            del st3R_P
+
+        def in_outer(g):
+            ok = np.all((g >= -1) & (g <= N + 1), axis=1)
+            gi = -np.ones(len(g), dtype=np.int64)
+            gi[ok] = omap[g[ok, 0] + 1, g[ok, 1] + 1, g[ok, 2] + 1]
+            return gi >= 0, gi
+
+        for i in range(NP):
+            org = origins[i]
+            ok, gi = in_outer(outer_alpha + org)
+            oself[gi[ok]] += PHI[i_selfA[ok], i]
+            ost[gi[ok]] += PHI[i_stA[ok], i]
+            if ring:
+                ok, gi = in_outer(outer_ring + org)
+                oself[gi[ok]] += BVo_self[ok] @ Cmom[:, i]
+                ost[gi[ok]] += BV[i_stR[ok]] @ Cmom[:, i]
+        phiB_out = np.empty(len(gout))
+        for a0 in range(0, len(gout), 4096):
+            a1 = min(len(gout), a0 + 4096)
+            P3, W3 = stencils3_for(prm, gout[a0:a1])
+            q = P3 - olo
+            phiB_out[a0:a1] = oself[a0:a1] + np.sum(W3 * (phiH[q[..., 0], q[..., 1], q[..., 2]] - ost[a0:a1]),
+                                                     axis=1)
+        del ost
+
     # ---- Dirichlet problems on each patch (eq. last_step_fulldiscr) and the
     # ---- Mehrstellen correction (eq. mcapplicationfulldiscr)
-    U = np.zeros((NP,) + (n + 1,) * 3)
-    bnd = np.zeros((n + 1,) * 3, dtype=bool)
-    bnd[0, :, :] = bnd[-1, :, :] = bnd[:, 0, :] = bnd[:, -1, :] = bnd[:, :, 0] = bnd[:, :, -1] = True
-    bl = np.argwhere(bnd)
-    gb = origins[:, None, :] + bl[None, :, :]  # (NP, |bnd|, 3)
-    U[:, bnd] = phiB[gmap[gb[..., 0], gb[..., 1], gb[..., 2]]]
-    fp = np.empty_like(U)
+    fp = np.empty((NP,) + (n + 1,) * 3)
     for i in range(NP):
         o = origins[i]
         fp[i] = f_closed[o[0]:o[0] + n + 1, o[1]:o[1] + n + 1, o[2]:o[2] + n + 1]
-    U = dirichlet_solve(prm, U, fp)
+    if wide:
+        # R18: the two boundary layers of [-1, n+1]^3: the closed faces (phi^B)
+        # and the layer one node outside them (phi^B on the outer nodes)
+        U2 = np.zeros((NP,) + (n + 3,) * 3)
+        rel = box_points(-1, n + 1)
+        inside = np.all((rel >= 0) & (rel <= n), axis=1)
+        face = inside & np.any((rel == 0) | (rel == n), axis=1)
+        ext = (np.sum((rel == -1) | (rel == n + 1), axis=1) == 1) & \
+            (np.sum((rel >= 0) & (rel <= n), axis=1) == 2)
+        for i in range(NP):
+            g = rel[face] + origins[i]
+            U2[i][tuple((rel[face] + 1).T)] = phiB[gmap[g[:, 0], g[:, 1], g[:, 2]]]
+            g = rel[ext] + origins[i]
+            U2[i][tuple((rel[ext] + 1).T)] = phiB_out[omap[g[:, 0] + 1, g[:, 1] + 1, g[:, 2] + 1]]
+        U = dirichlet_solve_wide(prm, U2, fp)
+    else:
+        U = np.zeros((NP,) + (n + 1,) * 3)
+        bnd = np.zeros((n + 1,) * 3, dtype=bool)
+        bnd[0, :, :] = bnd[-1, :, :] = bnd[:, 0, :] = bnd[:, -1, :] = bnd[:, :, 0] = bnd[:, :, -1] = True
+        bl = np.argwhere(bnd)
+        gb = origins[:, None, :] + bl[None, :, :]  # (NP, |bnd|, 3)
+        U[:, bnd] = phiB[gmap[gb[..., 0], gb[..., 1], gb[..., 2]]]
+        U = dirichlet_solve(prm, U, fp)
     if prm.correction:
-        U += C2 * h * h * fp
+        U += prm.c2 * h * h * fp
     phi = np.zeros((N + 1,) * 3)
     for i in range(NP):
         o = origins[i]
@@ -684,6 +905,9 @@ def mlc_solve(prm: Params, f_closed: np.ndarray, G1: np.ndarray | None = None, s
         stages["phiH_lo"] = olo
         stages["face_nodes"] = gface
         stages["phiB"] = phiB
+        if wide:
+            stages["outer_nodes"] = gout
+            stages["phiB_outer"] = phiB_out
     return phi
 
 
@@ -797,6 +1021,45 @@ def dirichlet_solve(prm: Params, U: np.ndarray, fp: np.ndarray) -> np.ndarray:
     return out
 
 
+def dirichlet_solve_wide(prm: Params, U: np.ndarray, fp: np.ndarray) -> np.ndarray:
+    """R18: Delta^h u = f on the patch interior [1, n-1]^3 of an s = 2
+    operator, u = U on the two boundary layers (the closed faces and the layer
+    one node outside them), by a sparse LU factorisation of the operator on
+    the interior nodes (eq. last_step_fulldiscr with the second layer).
+
+    U: (patches, n+3, n+3, n+3) over the relative nodes [-1, n+1]^3 (entries
+    off the two layers are never read); fp: (patches, n+1, n+1, n+1) over
+    [0, n]^3.  Returns u on [0, n]^3 with the faces taken from U."""
+    import scipy.sparse
+    import scipy.sparse.linalg
+    n, h = prm.n, prm.h
+    m = n - 1
+    lap = stencil(prm.Q)
+    for off, _ in lap:  # only offsets the two layers hold: at most one component of size 2
+        assert sum(abs(c) == 2 for c in off) <= 1
+    idx = np.arange(m ** 3).reshape(m, m, m)
+    rows, cols, vals = [], [], []
+    for (s0, s1, s2), c in lap:
+        a0, a1 = max(0, -s0), min(m, m - s0)
+        b0, b1 = max(0, -s1), min(m, m - s1)
+        c0, c1 = max(0, -s2), min(m, m - s2)
+        rows.append(idx[a0:a1, b0:b1, c0:c1].ravel())
+        cols.append(idx[a0 + s0:a1 + s0, b0 + s1:b1 + s1, c0 + s2:c1 + s2].ravel())
+        vals.append(np.full(rows[-1].size, c / (h * h)))
+    A = scipy.sparse.csc_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                                shape=(m ** 3, m ** 3))
+    Ub = U.copy()
+    Ub[:, 2:m + 2, 2:m + 2, 2:m + 2] = 0.0  # boundary-layer values only
+    rhs = fp[:, 1:-1, 1:-1, 1:-1].copy()
+    for (s0, s1, s2), c in lap:
+        rhs -= (c / (h * h)) * Ub[:, 2 + s0:m + 2 + s0, 2 + s1:m + 2 + s1, 2 + s2:m + 2 + s2]
+    lu = scipy.sparse.linalg.splu(A)
+    u = lu.solve(rhs.reshape(rhs.shape[0], -1).T).T
+    out = U[:, 1:n + 2, 1:n + 2, 1:n + 2].copy()
+    out[:, 1:n, 1:n, 1:n] = u.reshape(-1, m, m, m)
+    return out
+
+
 def plain_solution(prm: Params, f_closed: np.ndarray, G1: np.ndarray | None = None) -> np.ndarray:
     """The plain definition G^h * f^h + C2 h^2 f^h on [0,N]^3 (eq. msCorr4),
     by a global direct sum."""
@@ -804,7 +1067,7 @@ def plain_solution(prm: Params, f_closed: np.ndarray, G1: np.ndarray | None = No
     if G1 is None:
         G1 = dgf_octant(prm.Q, prm.nD, prm.zeta)
     conv = direct_sum(G1, f_closed, (0, 0, 0), (0, 0, 0), (N + 1,) * 3, h * h)
-    return conv + C2 * h * h * f_closed
+    return conv + prm.c2 * h * h * f_closed
 
 
 def solve_open(prm: Params, f: np.ndarray, **kw) -> np.ndarray:
