@@ -77,10 +77,16 @@ typedef struct {
                        grown by s nodes (eq. initiallocalproblemsmlcII); 4 | s, s >= C b */
     int C;          /* coarsening ratio N_ref; must be 4 (Sec. 2)                       */
     int P;          /* Legendre orders: |p|_1 <= P-1 (eq. led3d); 1 <= P <= 6           */
-    int Q;          /* Mehrstellen order: 4 -> 19-point, 6 -> 27-point (App. A.1)       */
+    int Q;          /* Mehrstellen order: 4 -> 19-point, 6 -> 27-point (App. A.1),
+                       10 -> the 57-point q = 10 operator in the 5x5x5 block (Sec. 8):
+                       a_j by orbit of j (sorted |j_d|): (0,0,0) -1079/210, (1,0,0)
+                       24/35, (1,1,0) 17/210, (1,1,1) 11/420, (2,0,0) -1/60, (2,1,0)
+                       -1/420; C2 = 2/35.  Its Dirichlet step has a second boundary
+                       layer one node outside the faces (MLC_STAGE_PHIB_OUTER)          */
     int g_beta;     /* outer growth ceil((beta-1) n/2) (Sec. 4); -1: beta = 3 (Q=4),
-                       3.25 (Q=6)                                                       */
-    int b;          /* interpolation stencil radius; -1: 2 for Q=4, 3 for Q=6 (Sec. 7)  */
+                       3.25 (Q=6), 2 (Q=10: beta^-10 ~ 3.25^-6)                          */
+    int b;          /* interpolation stencil radius, 1..5 (q_I = 2b+2); -1: 2 for Q=4,
+                       3 for Q=6, 5 for Q=10 (q_I = q + 2, Sec. 7)                       */
     int tier;       /* mlc_tier                                                         */
     int mode;       /* mlc_mode                                                         */
     int dgf_nD;     /* DGF table built on [-zeta nD, zeta nD]^3 (App. A.1); -1: 128,
@@ -120,7 +126,9 @@ mlc_status mlc_params_init(mlc_params *p, int N, int n, int s, int P, int Q);
  * above; g_beta < s - C b.  UNSUPPORTED if: n is not one of 4, 8, 12, 16, 24,
  * 32; the patch FFT length (the power of two >= 2(n+s)) is above 128; the
  * coarse FFT length (the smallest even 2^a 3^b 5^c >= twice the largest
- * coarse lag) is above 512.  With levels > 2 the plan of the next coarser
+ * coarse lag) is above 512; Q = 10 with levels > 2, n > 16 or a
+ * double-float tier (its boundary and Dirichlet steps run in FP64: tiers FP64
+ * and SPLIT).  With levels > 2 the plan of the next coarser
  * level is created with it, with its scratch, so that no solve allocates.
  */
 mlc_status mlc_plan_create(int N, int patch, int support, int coarsening, int P, int Q,
@@ -260,9 +268,13 @@ typedef enum {
                                entries offsets[k] .. offsets[k+1]-1, each 2 i + 0 if
                                Omega_alpha(i) holds the node, 2 i + 1 if only Omega_beta(i)
                                does (i the patch's linear index), ascending i               */
-    MLC_STAGE_COARSE_INDEX = 7 /* int32: the same for every coarse node of the F^H extent
+    MLC_STAGE_COARSE_INDEX = 7, /* int32: the same for every coarse node of the F^H extent
                                ([k0][k1][k2] order) and the coarse boxes C(Omega_alpha(i)),
                                C(Omega_beta(i)) (eq. FDLD)                                */
+    MLC_STAGE_PHIB_OUTER = 8 /* Q = 10 only: boundary values on the second layer, the planes
+                               one node off the face planes, [axis][plane j][side][u][v],
+                               x_axis = j n - 1 (side 0) or j n + 1 (side 1), j in [0, N/n],
+                               (u,v) in [0, N]^2 as for MLC_STAGE_PHIB (Sec. 8)            */
 } mlc_stage;
 
 mlc_status mlc_debug_stage_bytes(mlc_plan_t plan, int stage, size_t *bytes);

@@ -48,6 +48,58 @@ __global__ void k_dgf_rhs(double *r, int MD, double b0, double b1, double b2, do
     r[idx] = acc;
 }
 
+// Q = 10 (R18): the reference field of the residual-correction form is the
+// free-space kernel w(y) = -1/(4 pi |y|) (w(0) = 0) on the whole box, so the
+// right-hand side delta_0 - L w is needed at every node of the octant; the
+// stencil reads w up to two nodes beyond the boundary |y|_inf = MD.
+__device__ __forceinline__ double dgf_w(int y0, int y1, int y2) {
+    if (y0 == 0 && y1 == 0 && y2 == 0) return 0.0;
+    return -1.0 / (4.0 * M_PI * sqrt((double)y0 * y0 + (double)y1 * y1 + (double)y2 * y2));
+}
+__global__ void k_dgf_rhs_wide(double *r, int MD) {
+    long total = (long)MD * MD * MD;
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    int x2 = (int)(idx % MD);
+    int x1 = (int)((idx / MD) % MD);
+    int x0 = (int)(idx / ((long)MD * MD));
+    double acc = 0.0;
+    for (int s0 = -2; s0 <= 2; ++s0)
+        for (int s1 = -2; s1 <= 2; ++s1)
+            for (int s2 = -2; s2 <= 2; ++s2) {
+                const double c = stencil_coef(10, s0, s1, s2);
+                if (c != 0.0) acc = fma(c, dgf_w(x0 + s0, x1 + s1, x2 + s2), acc);
+            }
+    r[idx] = ((x0 == 0 && x1 == 0 && x2 == 0) ? 1.0 : 0.0) - acc;
+}
+__global__ void k_dgf_div_wide(double *u, int MD, const double *cosv) {
+    long total = (long)MD * MD * MD;
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const double c[3] = {cosv[idx / ((long)MD * MD)], cosv[(idx / MD) % MD], cosv[idx % MD]};
+    double lam = 0.0;
+    for (int s0 = -2; s0 <= 2; ++s0)
+        for (int s1 = -2; s1 <= 2; ++s1)
+            for (int s2 = -2; s2 <= 2; ++s2) {
+                const double a = stencil_coef(10, s0, s1, s2);
+                if (a == 0.0) continue;
+                const int ss[3] = {s0, s1, s2};
+                double t = a;
+                for (int d = 0; d < 3; ++d) {
+                    const int k = ss[d] < 0 ? -ss[d] : ss[d];
+                    t *= k == 0 ? 1.0 : (k == 1 ? c[d] : 2.0 * c[d] * c[d] - 1.0);
+                }
+                lam += t;
+            }
+    u[idx] /= lam;
+}
+__global__ void k_dgf_add_w(double *G, int Lp) {
+    long total = (long)Lp * Lp * Lp;
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    G[idx] += dgf_w((int)(idx / ((long)Lp * Lp)), (int)((idx / Lp) % Lp), (int)(idx % Lp));
+}
+
 // Divide the cosine coefficients by the stencil's eigenvalue.
 __global__ void k_dgf_div(double *u, int MD, const double *cosv, double b0, double b1, double b2,
                           double b3) {
@@ -191,13 +243,15 @@ cudaError_t build_dgf_octant(int Q, int nD, int zeta, int L, double **out) {
     cudaStream_t st = 0;
     int threads = 256;
     long blocks = (vol + threads - 1) / threads;
-    k_dgf_rhs<<<(unsigned)blocks, threads, 0, st>>>(r, MD, bq[0], bq[1], bq[2], bq[3]);
+    if (Q == 10) k_dgf_rhs_wide<<<(unsigned)blocks, threads, 0, st>>>(r, MD);
+    else k_dgf_rhs<<<(unsigned)blocks, threads, 0, st>>>(r, MD, bq[0], bq[1], bq[2], bq[3]);
     MLC_TRY(cudaGetLastError());
     // forward cosine transform along axes 2, 1, 0
     MLC_TRY(axis_apply(dCf, MD, r, MD, MD, MD, 2, t, st));
     MLC_TRY(axis_apply(dCf, MD, t, MD, MD, MD, 1, r, st));
     MLC_TRY(axis_apply(dCf, MD, r, MD, MD, MD, 0, t, st));
-    k_dgf_div<<<(unsigned)blocks, threads, 0, st>>>(t, MD, dcos, bq[0], bq[1], bq[2], bq[3]);
+    if (Q == 10) k_dgf_div_wide<<<(unsigned)blocks, threads, 0, st>>>(t, MD, dcos);
+    else k_dgf_div<<<(unsigned)blocks, threads, 0, st>>>(t, MD, dcos, bq[0], bq[1], bq[2], bq[3]);
     MLC_TRY(cudaGetLastError());
     // inverse transform, keeping only x in [0, L]
     const int Lp = L + 1;
@@ -206,6 +260,11 @@ cudaError_t build_dgf_octant(int Q, int nD, int zeta, int L, double **out) {
     double *res = nullptr;
     MLC_TRY(cudaMalloc((void **)&res, (size_t)Lp * Lp * Lp * sizeof(double)));
     cudaError_t e = axis_apply(dCi, Lp, t, MD, Lp, Lp, 0, res, st);  // Lp^3
+    if (e == cudaSuccess && Q == 10) {  // G = w + u
+        const long v3 = (long)Lp * Lp * Lp;
+        k_dgf_add_w<<<(unsigned)((v3 + 255) / 256), 256, 0, st>>>(res, Lp);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         cudaFree(res);

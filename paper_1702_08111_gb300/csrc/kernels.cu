@@ -1340,11 +1340,24 @@ struct InvXPArgs {
     int wait_tries;   // limit of the bounded wait for the block's bulk copy
     int skip_copy;    // test hook: issue no bulk copy, so the bounded wait runs out
     int rb;           // k_inv_x_pruned: transformed rows per pass through the line buffer
+    int outer;        // Q = 10 (R18): every alpha row is transformed, and the values one node
+                      // off the alpha face planes go to fp2 as well
 };
 
 __device__ __forceinline__ bool in_alpha(int c, int n, int ga) { return c >= -ga && c <= n + ga; }
 __device__ __forceinline__ bool on_plane(int c, int n, int ga, int pl0) {
     return in_alpha(c, n, ga) && ((c - pl0) % n) == 0;
+}
+// R18: slot 2 j + side of a coordinate one node off the alpha face plane
+// pl0 + j n (side 0: c = plane - 1, side 1: c = plane + 1), or -1.  With 4 | n
+// and 4 | ga every such c inside the alpha box has its plane inside it too.
+__device__ __forceinline__ int off_slot(int c, int n, int ga, int pl0, int npa) {
+    if (!in_alpha(c, n, ga)) return -1;
+    int d = c + 1 - pl0;
+    if (d >= 0 && d % n == 0 && d / n < npa) return 2 * (d / n);
+    d = c - 1 - pl0;
+    if (d >= 0 && d % n == 0 && d / n < npa) return 2 * (d / n) + 1;
+    return -1;
 }
 
 template <int LOG2M, typename R, typename TO>
@@ -1394,7 +1407,7 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
     if (threadIdx.x < 128) {
         const int yi = threadIdx.x, y = yi - s;
         const bool yA = in_alpha(y, n, ga), yP = on_plane(y, n, ga, pl0), yC = (y & 3) == 0;
-        const bool need = yi < W && ((zP && yA) || (yP && zA) || (zC && yC));
+        const bool need = yi < W && (a.outer ? ((zA && yA) || (zC && yC)) : ((zP && yA) || (yP && zA) || (zC && yC)));
         const unsigned m = __ballot_sync(0xffffffffu, need);
         if ((threadIdx.x & 31) == 0) wmask[threadIdx.x >> 5] = m;
     }
@@ -1438,7 +1451,13 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
         const bool yA = in_alpha(y, n, ga), yP = on_plane(y, n, ga, pl0), yC = (y & 3) == 0;
         const bool xA = in_alpha(x, n, ga), xP = on_plane(x, n, ga, pl0), xC = (x & 3) == 0;
         const bool wC = zC && yC && xC, w0 = zP && yA && xA, w1 = yP && zA && xA, w2 = zA && yA && xP;
-        if (!(wC || w0 || w1 || w2)) continue;
+        int o0 = -1, o1 = -1, o2 = -1;
+        if (a.outer && xA && yA && zA) {
+            o0 = off_slot(z, n, ga, pl0, a.npa);
+            o1 = off_slot(y, n, ga, pl0, a.npa);
+            o2 = off_slot(x, n, ga, pl0, a.npa);
+        }
+        if (!(wC || w0 || w1 || w2 || o0 >= 0 || o1 >= 0 || o2 >= 0)) continue;
         int pos = x % M;
         if (pos < 0) pos += M;
         const TO v = (TO)buf[l * LP + (LOG2M == 6 ? pos : brev_bits(pos, LOG2M))].x;
@@ -1459,11 +1478,27 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
             const long i = (((long)(2 * a.npa + (x - pl0) / n)) * wa + (z + ga)) * wa + (y + ga);
             if (in_range(i, nfp, PP.err)) fp[i] = v;
         }
+        if (a.outer) {  // [patch][axis][j][side][u][v], in-plane (u, v) as for fp
+            TO *f2 = (TO *)PP.fp2 + (long)p * 6 * a.npa * wa * wa;
+            const long nf2 = 6L * a.npa * wa * wa;
+            if (o0 >= 0) {
+                const long i = ((long)(0 * 2 * a.npa + o0) * wa + (y + ga)) * wa + (x + ga);
+                if (in_range(i, nf2, PP.err)) f2[i] = v;
+            }
+            if (o1 >= 0) {
+                const long i = ((long)(1 * 2 * a.npa + o1) * wa + (z + ga)) * wa + (x + ga);
+                if (in_range(i, nf2, PP.err)) f2[i] = v;
+            }
+            if (o2 >= 0) {
+                const long i = ((long)(2 * 2 * a.npa + o2) * wa + (z + ga)) * wa + (y + ga);
+                if (in_range(i, nf2, PP.err)) f2[i] = v;
+            }
+        }
     }
     __syncthreads();  // the buffer is refilled by the next pass
     }
     // rows that only need x on the face planes: direct sums over the half spectrum
-    if (zA) {
+    if (zA && !a.outer) {
         for (int e = threadIdx.x; e < W * a.npa; e += blockDim.x) {
             const int yi = e / a.npa, j = e % a.npa;
             const int y = yi - s;
@@ -1551,7 +1586,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 8 : 4) k_inv_x64(InvXPAr
     if (threadIdx.x < 64) {
         const int yi = threadIdx.x, y = yi - s;
         const bool yA = in_alpha(y, n, ga), yP = on_plane(y, n, ga, pl0), yC = (y & 3) == 0;
-        const bool need = yi < W && ((zP && yA) || (yP && zA) || (zC && yC));
+        const bool need = yi < W && (a.outer ? ((zA && yA) || (zC && yC)) : ((zP && yA) || (yP && zA) || (zC && yC)));
         const unsigned m = __ballot_sync(0xffffffffu, need);
         if ((threadIdx.x & 31) == 0) wmask[threadIdx.x >> 5] = m;
     }
@@ -1625,7 +1660,13 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 8 : 4) k_inv_x64(InvXPAr
         const bool yA = yf & 1, yP = yf & 2, yC = yf & 4;
         const bool xA = xf & 2, xP = xf & 4, xC = xf & 8;
         const bool wC = zC && yC && xC, w0 = zP && yA && xA, w1 = yP && zA && xA, w2 = zA && yA && xP;
-        if (!(wC || w0 || w1 || w2)) continue;
+        int o0 = -1, o1 = -1, o2 = -1;
+        if (a.outer && xA && yA && zA) {
+            o0 = off_slot(z, n, ga, pl0, a.npa);
+            o1 = off_slot(y, n, ga, pl0, a.npa);
+            o2 = off_slot(x, n, ga, pl0, a.npa);
+        }
+        if (!(wC || w0 || w1 || w2 || o0 >= 0 || o1 >= 0 || o2 >= 0)) continue;
         const R val = rbuf[l * RP + pos];
         const long ncl = (long)nc * nc * nc, nfp = 3L * a.npa * wa * wa;
         if (wC) {
@@ -1750,8 +1791,8 @@ template <> __device__ __forceinline__ double pick<double>(const dfl &, const do
 struct ResArgs {
     Items it;  // per item: cl, fp -> resid of its plan
     int n, s, ga, b, npa, pl0, wa, nc;
-    dfl lw[4][8];     // Lagrange weights for g mod 4 = r (row r), double-float
-    double lwd[4][8]; // the same in FP64
+    dfl lw[4][12];     // Lagrange weights for g mod 4 = r (row r), double-float
+    double lwd[4][12]; // the same in FP64
 };
 
 // r^i = phi^i - I^H(phi^i) on the face planes inside Omega_alpha (one CTA per
@@ -1891,6 +1932,8 @@ struct AsmArgs {
     int ca_lo, ca_hi, cb_lo, cb_hi;
     dfl coef[4];      // b_k / H^2, double-float
     double coefd[4];  // the same in FP64
+    int wide;         // Q = 10: the 5 x 5 x 5 operator (stencil_coef), FP64 tiers only
+    double invH2;     // 1 / H^2
 };
 
 // Patches i (ascending linear index) whose coarse box C(Omega_beta(i)) holds
@@ -1934,7 +1977,21 @@ __global__ void __launch_bounds__(128) k_assemble(AsmArgs a) {
     T acc = FT<T>::zero();
     coarse_node_patches(k, a.n, a.np, a.ca_lo, a.ca_hi, a.cb_lo, a.cb_hi,
                         [&](long p, int r0, int r1, int r2, bool inA) {
-                if (inA) {
+                if (inA && a.wide) {
+                    const TB *bx = (const TB *)a.cl + p * nc * nc * nc;
+#pragma unroll
+                    for (int s0 = -2; s0 <= 2; ++s0)
+#pragma unroll
+                        for (int s1 = -2; s1 <= 2; ++s1)
+#pragma unroll
+                            for (int s2 = -2; s2 <= 2; ++s2) {
+                                const double c = stencil_coef(10, s0, s1, s2);
+                                if (c == 0.0) continue;
+                                const long x0 = r0 + s0 - kl, x1 = r1 + s1 - kl, x2 = r2 + s2 - kl;
+                                if (in_range(x0, nc, a.err) & in_range(x1, nc, a.err) & in_range(x2, nc, a.err))
+                                    acc = FT<T>::fma(FT<T>::of(c * a.invH2), FT<T>::of(bx[(x0 * nc + x1) * nc + x2]), acc);
+                            }
+                } else if (inA) {
                     const TB *bx = (const TB *)a.cl + p * nc * nc * nc;
 #pragma unroll
                     for (int s0 = -1; s0 <= 1; ++s0)
@@ -2004,8 +2061,8 @@ __device__ __forceinline__ void face_plane_node(long idx, int N, int np, int n, 
 // sums K of these along u: the same operations in the same order as the
 // nested sums at each node, done once per (plane, coarse row, v).
 struct LagW {
-    dfl lw[4][8];      // Lagrange weights for g mod 4 = r (row r), double-float
-    double lwd[4][8];  // the same in FP64
+    dfl lw[4][12];      // Lagrange weights for g mod 4 = r (row r), double-float
+    double lwd[4][12];  // the same in FP64
 };
 
 template <typename T>
@@ -2057,8 +2114,8 @@ struct BndArgs {
     int N, n, np, ga, gb, b, npoly, olo, no, wa, wbx, npa, pl0;
     int pb0, npb;     // face planes of Omega_beta (relative): pb0 + j n, j < npb
     int npad;         // row stride of the ring tables (npoly rounded up to 4; zero padding)
-    dfl lw[4][8];     // Lagrange weights for g mod 4 = r (row r), 2b+2 entries
-    double lwd[4][8];
+    dfl lw[4][12];     // Lagrange weights for g mod 4 = r (row r), 2b+2 entries
+    double lwd[4][12];
 };
 
 // phi^B at every face-plane node (axis, plane j, u, v).  RT: precision of the
@@ -2089,11 +2146,15 @@ __global__ void __launch_bounds__(128, 6) k_boundary(BndArgs a) {
     } else {
         acc = FT<T>::zero();
         const int kb = (gu >> 2) - a.b - a.olo;
-        // unrolled to the largest stencil (b = 3) so the K loads issue together
+        // unrolled to b = 3 so the K loads issue together; b = 4, 5 continue
 #pragma unroll
         for (int e = 0; e < 8; ++e)
             if (e < K && in_range(kb + e, a.no, a.err))
                 acc = FT<T>::fma(pick<T>(a.lw[ru][e], a.lwd[ru][e]), FT<T>::rn(tpl[(long)(kb + e) * (a.N + 1)]), acc);
+        if (K > 8)
+            for (int e = 8; e < K; ++e)
+                if (in_range(kb + e, a.no, a.err))
+                    acc = FT<T>::fma(pick<T>(a.lw[ru][e], a.lwd[ru][e]), FT<T>::rn(tpl[(long)(kb + e) * (a.N + 1)]), acc);
     }
     // local corrections of the patches whose Omega_beta holds g (ascending index);
     // the Legendre ring terms accumulate in the ring precision RT
@@ -3033,6 +3094,7 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
             a.wait_tries = 64;
         }
         for (int j = 0; j < nz; ++j) a.zrow[j] = zrow[j];
+        a.outer = g.wide ? 1 : 0;
         // rows needing a full transform, per z row (the same rule as the kernel)
         auto inA = [&](int c) { return c >= -g.ga && c <= g.n + g.ga; };
         auto onP = [&](int c) { return inA(c) && ((c - g.pl0) % g.n) == 0; };
@@ -3041,7 +3103,9 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
             int cnt = 0;
             for (int yi = 0; yi < W; ++yi) {
                 const int y = yi - g.s;
-                if ((onP(z) && inA(y)) || (onP(y) && inA(z)) || ((z & 3) == 0 && (y & 3) == 0)) ++cnt;
+                if (g.wide ? ((inA(z) && inA(y)) || ((z & 3) == 0 && (y & 3) == 0))
+                           : ((onP(z) && inA(y)) || (onP(y) && inA(z)) || ((z & 3) == 0 && (y & 3) == 0)))
+                    ++cnt;
             }
             a.maxfft = cnt > a.maxfft ? cnt : a.maxfft;
         }
@@ -3057,7 +3121,7 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
         const size_t sm = fixed + (size_t)a.rb * line;
         // local fields leave in the working precision: FP32 (split tier) or
         // double-float pairs (FP64 tier)
-        if (LOG2M == 6) {
+        if (LOG2M == 6 && !g.wide) {
             const int thr = 128;  // 16 line groups: one pass over the row pairs of a z row
             const size_t sm64 = ((size_t)M + (size_t)g.a4blk + (thr / 8) * 72) * sizeof(typename Cx<R>::T) +
                                 (size_t)a.maxfft * 68 * sizeof(R);
@@ -3124,9 +3188,12 @@ void configure_kernels() {
     MLC_RES_ATTR(4)
     MLC_RES_ATTR(6)
     MLC_RES_ATTR(8)
+    MLC_RES_ATTR(10)
+    MLC_RES_ATTR(12)
 #undef MLC_RES_ATTR
     cudaFuncSetAttribute(k_moments<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_moments<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    configure_wide();
 }
 
 cudaError_t launch_moments(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
@@ -3181,10 +3248,10 @@ cudaError_t launch_patch_conv(const mlc_plan_s *pl, const Items &it, cudaStream_
 }
 
 // Lagrange weights of I^H on the nodes k0-b .. k0+b+1 at t = k0 + r/4 (R4 reading).
-void lagrange_rows(int b, double lw[4][8]) {
+void lagrange_rows(int b, double lw[4][12]) {
     const int K = 2 * b + 2;
     for (int r = 0; r < 4; ++r)
-        for (int j = 0; j < 8; ++j) lw[r][j] = 0.0;
+        for (int j = 0; j < 12; ++j) lw[r][j] = 0.0;
     for (int r = 1; r < 4; ++r)
         for (int j = 0; j < K; ++j) {
             double w = 1.0;
@@ -3196,11 +3263,11 @@ void lagrange_rows(int b, double lw[4][8]) {
 }
 
 // Lagrange weights as double-float pairs (host).
-void lagrange_rows_df(int b, dfl out[4][8]) {
-    double lw[4][8];
+void lagrange_rows_df(int b, dfl out[4][12]) {
+    double lw[4][12];
     lagrange_rows(b, lw);
     for (int r = 0; r < 4; ++r)
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < 12; ++j) {
             const float hi = (float)lw[r][j];
             out[r][j] = dfl(hi, (float)(lw[r][j] - (double)hi));
         }
@@ -3240,10 +3307,14 @@ cudaError_t launch_resid(const mlc_plan_s *pl, const Items &it, cudaStream_t st)
         case 4: MLC_RES(4) break;
         case 6: MLC_RES(6) break;
         case 8: MLC_RES(8) break;
+        case 10: MLC_RES(10) break;
+        case 12: MLC_RES(12) break;
         default: return cudaErrorInvalidValue;
     }
 #undef MLC_RES
-    return cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_resid_outer(pl, it, st);  // Q = 10: the second layer (no-op otherwise)
 }
 
 cudaError_t launch_assemble(const mlc_plan_s *pl, cudaStream_t st) {
@@ -3262,6 +3333,8 @@ cudaError_t launch_assemble(const mlc_plan_s *pl, cudaStream_t st) {
         a.coef[k] = host_df(b[k] / (g.H * g.H));
         a.coefd[k] = b[k] / (g.H * g.H);
     }
+    a.wide = g.wide ? 1 : 0;
+    a.invH2 = 1.0 / (g.H * g.H);
     const long tot = (long)g.nf * g.nf * g.nf;
     const unsigned nbk = (unsigned)((tot + 127) / 128);
     if (g.conv == CONV_F32) {
@@ -3396,10 +3469,13 @@ cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st) {
         }
 #undef MLC_BND
     }
-    return cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_boundary_outer(pl, st);  // Q = 10: the second layer (no-op otherwise)
 }
 
 cudaError_t launch_dirichlet(const mlc_plan_s *pl, const Items &it, cudaStream_t st) {
+    if (pl->g.wide) return launch_dirichlet_wide(pl, it, st);
     NvtxRange nvtx("mlc:dirichlet");
     const Geom &g = pl->g;
     DirArgs a{};
@@ -3462,5 +3538,7 @@ cudaError_t launch_index_export(const mlc_plan_s *pl, int which, int *cnt, const
 #undef MLC_IDX
     return cudaGetLastError();
 }
+
+#include "wide.cuh"
 
 }  // namespace mlc

@@ -31,6 +31,38 @@ inline bool tier_f32_charge(int t) { return t == MLC_TIER_SPLIT || t == MLC_TIER
 inline int conv_real_bytes(int t) { return tier_conv(t) == CONV_F32 ? 4 : 8; }
 
 // ---------------------------------------------------------------------------
+// Mehrstellen operators (Sec. 2, App. A.1, Sec. 8).  Q = 4 (L19) and Q = 6
+// (L27) reach one node (a_j = b_{|j|}, |j| the nonzero components); Q = 10 is
+// the q = 10 operator in the 5 x 5 x 5 block, one coefficient per orbit of
+// offsets under the cube's symmetries (sorted absolute components):
+// (0,0,0) (1,0,0) (1,1,0) (1,1,1) (2,0,0) (2,1,0), the solution of the six
+// conditions of eq. mehrstellenTau with q = 10 (sum a_j = 0, sum a_j j_0^2 =
+// 2, and sum a_j p(j) = 0 for the harmonic polynomials of degree 4-10).
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int stencil_reach(int Q) { return Q == 10 ? 2 : 1; }
+// C2 of the h^2 term C2 h^2 Delta^2 phi of the truncation error (the
+// 4th-order correction adds C2 h^2 f): sum_j a_j j_0^4 / 4!.
+inline double stencil_c2(int Q) { return Q == 10 ? 2.0 / 35.0 : 1.0 / 12.0; }
+// a_j at h = 1 for |j_d| <= stencil_reach(Q) (0 off the stencil).
+__host__ __device__ inline double stencil_coef(int Q, int s0, int s1, int s2) {
+    int a = s0 < 0 ? -s0 : s0, b = s1 < 0 ? -s1 : s1, c = s2 < 0 ? -s2 : s2;
+    if (Q != 10) {
+        if (a > 1 || b > 1 || c > 1) return 0.0;
+        const int nz = a + b + c;
+        if (Q == 4) return nz == 0 ? -4.0 : (nz == 1 ? 1.0 / 3.0 : (nz == 2 ? 1.0 / 6.0 : 0.0));
+        return nz == 0 ? -64.0 / 15.0 : (nz == 1 ? 7.0 / 15.0 : (nz == 2 ? 1.0 / 10.0 : 1.0 / 30.0));
+    }
+    // sort descending: a >= b >= c
+    if (a < b) { const int t = a; a = b; b = t; }
+    if (b < c) { const int t = b; b = c; c = t; }
+    if (a < b) { const int t = a; a = b; b = t; }
+    if (a == 0) return -1079.0 / 210.0;
+    if (a == 1) return b == 0 ? 24.0 / 35.0 : (c == 0 ? 17.0 / 210.0 : 11.0 / 420.0);
+    if (a == 2 && c == 0) return b == 0 ? -1.0 / 60.0 : (b == 1 ? -1.0 / 420.0 : 0.0);
+    return 0.0;
+}
+
+// ---------------------------------------------------------------------------
 // Plan geometry (Sec. 4): every size below is derived from (N, n, s, C, P, Q,
 // g_beta, b) on the host and is identical for every patch.
 // ---------------------------------------------------------------------------
@@ -62,6 +94,8 @@ struct Geom {
     int ring_rows, ring_ksteps;      // split tiers: ring-table rows per face-plane axis, K / 8 of the ring GEMM
     long ring_rows_pad;              // ring_rows rounded up to the GEMM's row tile (128)
     int chunk;                       // patches per launch group of the local convolutions
+    bool wide;                       // Q = 10 (s = 2): a second boundary layer one node off the
+                                     // face planes (fp2, resid2, phiB2 below); R18
     size_t scr_a1, scr_a4;           // scratch bytes per patch: x-transformed charges, slab outputs
 };
 // Local-convolution scratch for `items` patches: the a1 part, then (from a
@@ -94,6 +128,12 @@ struct PlanPtrs {
     double c2h2, inv_h2;  // h^2 / 12, 1 / h^2
     void *dscr;           // Dirichlet workspace (n > 24): [patch][(n-1)^3] in the fine precision
     int *err;             // the plan's error word
+    // Q = 10 (R18): local fields and residuals on the planes one node off the
+    // alpha face planes, [patch][axis][j][side][u][v] (side 0: plane - 1,
+    // 1: plane + 1), and the boundary values of the second layer,
+    // [axis][j][side][u][v] over the global planes n j -+ 1, u, v in [0, N]
+    void *fp2, *resid2;
+    const double *phiB2;
 };
 
 // The items of one launch.  Item q covers patch items[q].y of plan record
@@ -159,6 +199,12 @@ struct mlc_plan_s {
     float *ring_aimg;        // split tiers: ring table as the tensor-core GEMM operand (TF32 hi/lo image)
     float *ring_R;           // split tiers: [patch][ring_rows_pad] ring terms of one face-plane axis
     void *dscr = nullptr;    // n > 24: Dirichlet workspace [patch][(n-1)^3] (fine precision)
+    // Q = 10 (R18): the second boundary layer
+    void *fp2 = nullptr;     // NP x 3 npa 2 x wa^2 local fields one node off the alpha face planes
+    double *resid2 = nullptr;  // NP x 3 npa 2 x wa^2 their residuals (FP64)
+    double *phiB2 = nullptr;   // 3 (np+1) 2 (N+1)^2 boundary values on the planes n j -+ 1
+    double *tpl2 = nullptr;    // 3 (np+1) 2 no (N+1): I^H(phi^H) on those planes summed along v
+    void *D2tab = nullptr;     // [axis][npb][2][wbx][wbx][npad] ring rows of the off-face nodes
     void *f_stage, *phi_stage;  // device staging for mlc_solve_host
     int *err;                // device error word: nonzero if a bounded wait in a kernel gave up
     size_t ws_bytes;
@@ -209,6 +255,14 @@ cudaError_t launch_dirichlet(const mlc_plan_s *pl, const Items &it, cudaStream_t
 cudaError_t launch_assemble(const mlc_plan_s *pl, cudaStream_t st);
 cudaError_t launch_coarse(const mlc_plan_s *pl, cudaStream_t st);
 cudaError_t launch_boundary(const mlc_plan_s *pl, cudaStream_t st);
+// wide.cuh (Q = 10, R18; part of kernels.cu): residuals and boundary values of the second layer,
+// and the Dirichlet solve with two boundary layers.
+cudaError_t launch_resid_outer(const mlc_plan_s *pl, const Items &it, cudaStream_t st);
+cudaError_t launch_boundary_outer(const mlc_plan_s *pl, cudaStream_t st);
+cudaError_t launch_dirichlet_wide(const mlc_plan_s *pl, const Items &it, cudaStream_t st);
+void configure_wide();
+// Lagrange weights of I^H (R4) for g mod 4 = r, row r, 2b+2 <= 12 entries.
+void lagrange_rows(int b, double lw[4][12]);
 // ring_gemm.cu: the Legendre ring terms of one face-plane axis as a tcgen05
 // GEMM (split tiers), and its plan-time operand image.
 cudaError_t launch_ring_gemm(const mlc_plan_s *pl, int axis, cudaStream_t st);

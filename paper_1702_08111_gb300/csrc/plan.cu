@@ -42,6 +42,24 @@ void stencil_b(int Q, double b[4]) {
 }
 
 double symbol(int Q, double c0, double c1, double c2) {
+    if (Q == 10) {  // sum_j a_j prod_d cos(j_d theta_d), cos(2 theta) = 2 c^2 - 1
+        const double c[3] = {c0, c1, c2};
+        double lam = 0.0;
+        for (int s0 = -2; s0 <= 2; ++s0)
+            for (int s1 = -2; s1 <= 2; ++s1)
+                for (int s2 = -2; s2 <= 2; ++s2) {
+                    const double a = stencil_coef(10, s0, s1, s2);
+                    if (a == 0.0) continue;
+                    double t = a;
+                    const int ss[3] = {s0, s1, s2};
+                    for (int d = 0; d < 3; ++d) {
+                        const int k = std::abs(ss[d]);
+                        t *= k == 0 ? 1.0 : (k == 1 ? c[d] : 2.0 * c[d] * c[d] - 1.0);
+                    }
+                    lam += t;
+                }
+        return lam;
+    }
     double b[4];
     stencil_b(Q, b);
     return b[0] + 2.0 * b[1] * (c0 + c1 + c2) + 4.0 * b[2] * (c0 * c1 + c0 * c2 + c1 * c2) +
@@ -156,11 +174,12 @@ mlc_status derive_geometry(const mlc_params &pp, Geom &g) {
     g = Geom{};
     g.N = pp.N; g.n = pp.n; g.s = pp.s; g.C = pp.C; g.P = pp.P; g.Q = pp.Q;
     if (g.C != 4) return MLC_ERR_INVALID_ARG;
-    if (g.Q != 4 && g.Q != 6) return MLC_ERR_INVALID_ARG;
+    if (g.Q != 4 && g.Q != 6 && g.Q != 10) return MLC_ERR_INVALID_ARG;
+    g.wide = stencil_reach(g.Q) > 1;
     if (g.N <= 0 || g.n <= 0 || g.s < 0 || g.P < 1 || g.P > 6) return MLC_ERR_INVALID_ARG;
     if (g.N % g.n || g.n % 4 || g.s % 4) return MLC_ERR_INVALID_ARG;
-    g.b = pp.b < 0 ? (g.Q == 4 ? 2 : 3) : pp.b;
-    if (g.b < 1 || g.b > 3) return MLC_ERR_INVALID_ARG;
+    g.b = pp.b < 0 ? (g.Q == 4 ? 2 : (g.Q == 6 ? 3 : 5)) : pp.b;  // q_I = 2b + 2 = q + 2
+    if (g.b < 1 || g.b > 5) return MLC_ERR_INVALID_ARG;
     g.ga = g.s - g.C * g.b;
     if (g.ga < 0) return MLC_ERR_INVALID_ARG;
     g.mode = pp.mode < 0 ? MLC_MODE_MLC : pp.mode;
@@ -176,8 +195,8 @@ mlc_status derive_geometry(const mlc_params &pp, Geom &g) {
     } else if (pp.g_beta >= 0) {
         g.gb = pp.g_beta;
     } else {
-        // beta = 3 (Q = 4) or 13/4 (Q = 6): g_beta = ceil((beta - 1) n / 2)
-        g.gb = (g.Q == 4) ? g.n : ceildiv(9 * g.n, 8);
+        // beta = 3 (Q = 4), 13/4 (Q = 6) or 2 (Q = 10): g_beta = ceil((beta - 1) n / 2)
+        g.gb = (g.Q == 4) ? g.n : (g.Q == 6 ? ceildiv(9 * g.n, 8) : ceildiv(g.n, 2));
     }
     if (g.gb < g.ga) return MLC_ERR_INVALID_ARG;
     g.h = 1.0 / g.N;
@@ -201,7 +220,8 @@ mlc_status derive_geometry(const mlc_params &pp, Geom &g) {
     g.flo = g.cb_lo;
     g.fhi = (g.np - 1) * (g.n / 4) + g.cb_hi;
     g.nf = g.fhi - g.flo + 1;
-    g.olo = -g.b; g.ohi = g.N / 4 + g.b;
+    // R6; R18: the second boundary layer's stencils reach one coarse node further
+    g.olo = -g.b - (g.wide ? 1 : 0); g.ohi = g.N / 4 + g.b + (g.wide ? 1 : 0);
     g.no = g.ohi - g.olo + 1;
     g.Lc = std::max(g.fhi - g.olo, g.ohi - g.flo);
     // coarse Hockney period: the smallest even length >= 2 Lc (and >= the
@@ -225,6 +245,10 @@ mlc_status derive_geometry(const mlc_params &pp, Geom &g) {
     // (a multilevel plan's own coarse period is never used: its coarse solve
     // is the next level's MLC solve)
     if (g.M < 32 || g.M > 128 || (g.levels <= 2 && g.Mc > 512)) return MLC_ERR_UNSUPPORTED;
+    // Q = 10 (R18): two levels, FP64 boundary and Dirichlet steps (tiers FP64
+    // and SPLIT), and patches whose two-layer Dirichlet arrays fit shared memory
+    if (g.wide && (g.levels != 2 || g.fine != FINE_F64 || g.n > 16)) return MLC_ERR_UNSUPPORTED;
+    if (g.wide && g.b < 2) return MLC_ERR_INVALID_ARG;  // Delta^H reaches two coarse nodes past C(alpha)
     g.S = (2 * g.b + 2) * (2 * g.b + 2);
     g.nc = (g.n + 2 * g.s) / 4 + 1;
     g.nzr = 0;
@@ -307,6 +331,11 @@ mlc_status build_tables(mlc_plan_s *pl) {
     const int ncb = g.cb_hi - g.cb_lo + 1;
     std::vector<double> Ttab;
     std::vector<double> Dtab;
+    // R18 (Q = 10): ring rows of the nodes one node off the face planes
+    std::vector<int> omap(g.wide ? (size_t)g.wbx * g.wbx * g.wbx : 0, -1), oself;
+    std::vector<std::vector<int>> ost;
+    std::vector<std::vector<double>> ow;
+    std::vector<double> Dout;
     if (ring) {
         for (int x0 = -g.gb; x0 <= n + g.gb; ++x0)
             for (int x1 = -g.gb; x1 <= n + g.gb; ++x1)
@@ -343,8 +372,33 @@ mlc_status build_tables(mlc_plan_s *pl) {
             rn_self[r] = add(ring_nodes[r][0], ring_nodes[r][1], ring_nodes[r][2]);
             for (auto &k : ring_st[r]) rn_st[r].push_back(add(4 * k[0], 4 * k[1], 4 * k[2]));
         }
-        double bq[4];
-        stencil_b(g.Q, bq);
+        // R18: ring nodes one node off the face planes (the second boundary
+        // layer of Q = 10), with the interpolation stencil on every axis
+        if (g.wide) {
+            for (int x0 = -g.gb; x0 <= n + g.gb; ++x0)
+                for (int x1 = -g.gb; x1 <= n + g.gb; ++x1)
+                    for (int x2 = -g.gb; x2 <= n + g.gb; ++x2) {
+                        const int gg[3] = {x0, x1, x2};
+                        bool off = false;
+                        for (int d = 0; d < 3; ++d) {
+                            const int m = fmod_pos(gg[d], n);
+                            off = off || m == 1 || m == n - 1;
+                        }
+                        if (!off) continue;
+                        const bool inA = x0 >= -g.ga && x0 <= n + g.ga && x1 >= -g.ga &&
+                                         x1 <= n + g.ga && x2 >= -g.ga && x2 <= n + g.ga;
+                        if (inA) continue;
+                        omap[((size_t)(x0 + g.gb) * g.wbx + (x1 + g.gb)) * g.wbx + (x2 + g.gb)] =
+                            (int)oself.size();
+                        oself.push_back(add(x0, x1, x2));
+                        face_stencil(gg, g.b, sp, sw);
+                        std::vector<int> st_;
+                        for (auto &k : sp) st_.push_back(add(4 * k[0], 4 * k[1], 4 * k[2]));
+                        ost.push_back(st_);
+                        ow.push_back(sw);
+                    }
+        }
+        const int reach = stencil_reach(g.Q);
         std::vector<std::vector<std::pair<int, double>>> lapT((size_t)ncb * ncb * ncb);
         for (int k0 = g.cb_lo; k0 <= g.cb_hi; ++k0)
             for (int k1 = g.cb_lo; k1 <= g.cb_hi; ++k1)
@@ -353,13 +407,13 @@ mlc_status build_tables(mlc_plan_s *pl) {
                                      k1 <= g.ca_hi && k2 >= g.ca_lo && k2 <= g.ca_hi;
                     if (inA) continue;
                     auto &lst = lapT[((size_t)(k0 - g.cb_lo) * ncb + (k1 - g.cb_lo)) * ncb + (k2 - g.cb_lo)];
-                    for (int s0 = -1; s0 <= 1; ++s0)
-                        for (int s1 = -1; s1 <= 1; ++s1)
-                            for (int s2 = -1; s2 <= 1; ++s2) {
-                                const int nz = (s0 != 0) + (s1 != 0) + (s2 != 0);
-                                if (bq[nz] == 0.0) continue;
+                    for (int s0 = -reach; s0 <= reach; ++s0)
+                        for (int s1 = -reach; s1 <= reach; ++s1)
+                            for (int s2 = -reach; s2 <= reach; ++s2) {
+                                const double c = stencil_coef(g.Q, s0, s1, s2);
+                                if (c == 0.0) continue;
                                 lst.push_back({add(4 * (k0 + s0), 4 * (k1 + s1), 4 * (k2 + s2)),
-                                               bq[nz] / (g.H * g.H)});
+                                               c / (g.H * g.H)});
                             }
                 }
         // lag extent needed by the basis sums
@@ -400,6 +454,13 @@ mlc_status build_tables(mlc_plan_s *pl) {
                 for (size_t j = 0; j < rn_st[r].size(); ++j)
                     iv += ring_w[r][j] * B[(size_t)rn_st[r][j] * np_ + p];
                 Dtab[r * g.npad + p] = B[(size_t)rn_self[r] * np_ + p] - iv;
+            }
+        Dout.assign(oself.size() * g.npad, 0.0);
+        for (size_t r = 0; r < oself.size(); ++r)
+            for (int p = 0; p < np_; ++p) {
+                double iv = 0.0;
+                for (size_t j = 0; j < ost[r].size(); ++j) iv += ow[r][j] * B[(size_t)ost[r][j] * np_ + p];
+                Dout[r * g.npad + p] = B[(size_t)oself[r] * np_ + p] - iv;
             }
     }
     g.nr_face = (int)ring_nodes.size();
@@ -445,6 +506,37 @@ mlc_status build_tables(mlc_plan_s *pl) {
         }
         return o;
     };
+    // R18: dense rows [axis][j][side][u][v] of the off-face ring nodes, plane
+    // pb0 + (j - 1) n for j in [0, npb + 2) (a node of Omega_beta one step off
+    // a face plane can belong to the plane just outside it), normal coordinate
+    // plane - 1 (side 0) or plane + 1 (side 1)
+    if (ring && g.wide) {
+        std::vector<double> Do((size_t)6 * (g.npb + 2) * g.wbx * g.wbx * g.npad, 0.0);
+        for (int ax = 0; ax < 3; ++ax)
+            for (int j = 0; j < g.npb + 2; ++j)
+                for (int sd = 0; sd < 2; ++sd)
+                    for (int u = 0; u < g.wbx; ++u)
+                        for (int v = 0; v < g.wbx; ++v) {
+                            int r[3];
+                            r[ax] = g.pb0 + (j - 1) * n + (sd ? 1 : -1);
+                            r[ax == 0 ? 1 : 0] = u - g.gb;
+                            r[ax == 2 ? 1 : 2] = v - g.gb;
+                            if (r[ax] < -g.gb || r[ax] > n + g.gb) continue;
+                            const int ri = omap[((size_t)(r[0] + g.gb) * g.wbx + (r[1] + g.gb)) * g.wbx + (r[2] + g.gb)];
+                            if (ri < 0) continue;
+                            const size_t row = ((((size_t)ax * (g.npb + 2) + j) * 2 + sd) * g.wbx + u) * g.wbx + v;
+                            for (int k = 0; k < g.npad; ++k) Do[row * g.npad + k] = Dout[(size_t)ri * g.npad + k];
+                        }
+        if (g.conv == CONV_F32) {
+            float *d = nullptr;
+            TRY(dev_upload(pl, &d, std::vector<float>(Do.begin(), Do.end())));
+            pl->D2tab = d;
+        } else {
+            double *d = nullptr;
+            TRY(dev_upload(pl, &d, Do));
+            pl->D2tab = d;
+        }
+    }
     // ring tables in the ring precision: the local-convolution arithmetic
     if (g.conv == CONV_F32) {
         float *d = nullptr, *t = nullptr;
@@ -739,6 +831,15 @@ mlc_status create_plan(const mlc_params *params, const double *dgf_host, int dgf
         TRY(dev_alloc(pl, &pl->phiH, no * no * no));
         TRY(dev_alloc(pl, &pl->phiB, (size_t)G.n_planes_total));
         TRY(dev_alloc(pl, &pl->tpl, 3 * (size_t)(G.np + 1) * G.no * (G.N + 1)));
+        if (G.wide) {  // R18: the second boundary layer
+            char *f2 = nullptr;
+            const size_t per = NP * 6 * (size_t)G.npa * G.wa * G.wa;
+            TRY(dev_alloc(pl, &f2, per * rb));
+            pl->fp2 = f2;
+            TRY(dev_alloc(pl, &pl->resid2, per));
+            TRY(dev_alloc(pl, &pl->phiB2, 2 * (size_t)G.n_planes_total));
+            TRY(dev_alloc(pl, &pl->tpl2, 6 * (size_t)(G.np + 1) * G.no * (G.N + 1)));
+        }
         if (G.n > 24) {  // Dirichlet workspace of patches too large for shared memory
             double *d = nullptr;
             TRY(dev_alloc(pl, &d, NP * (size_t)(G.n - 1) * (G.n - 1) * (G.n - 1)));
@@ -767,10 +868,13 @@ mlc_status create_plan(const mlc_params *params, const double *dgf_host, int dgf
         h.lam = pl->lam;
         h.N = G.N;
         h.np = G.np;
-        h.c2h2 = correction ? G.h * G.h / 12.0 : 0.0;
+        h.c2h2 = correction ? stencil_c2(G.Q) * G.h * G.h : 0.0;
         h.inv_h2 = 1.0 / (G.h * G.h);
         h.err = pl->err;
         h.dscr = pl->dscr;
+        h.fp2 = pl->fp2;
+        h.resid2 = pl->resid2;
+        h.phiB2 = pl->phiB2;
         st = dev_upload(pl, &pl->dptrs, std::vector<PlanPtrs>{h});
     }
     if (st == MLC_OK && G.levels > 2) st = make_coarser_level(pl, dgf_host, dgf_Lh);
@@ -1039,6 +1143,10 @@ mlc_status mlc_debug_stage_bytes(mlc_plan_t pl, int stage, size_t *bytes) {
         case MLC_STAGE_FH: *bytes = (size_t)g.nf * g.nf * g.nf * 8; break;
         case MLC_STAGE_PHIH: *bytes = (size_t)g.no * g.no * g.no * 8; break;
         case MLC_STAGE_PHIB: *bytes = (size_t)g.n_planes_total * 8; break;
+        case MLC_STAGE_PHIB_OUTER:
+            if (!g.wide) return MLC_ERR_INVALID_ARG;
+            *bytes = 2 * (size_t)g.n_planes_total * 8;
+            break;
         case MLC_STAGE_DGF: *bytes = (size_t)(pl->dgf_L + 1) * (pl->dgf_L + 1) * (pl->dgf_L + 1) * 8; break;
         case MLC_STAGE_COARSE_SAMPLES: *bytes = (size_t)g.NP * g.nc * g.nc * g.nc * 8; break;
         case MLC_STAGE_FACE_INDEX:
@@ -1083,6 +1191,7 @@ mlc_status mlc_debug_export(mlc_plan_t pl, int stage, void *host, size_t bytes) 
         case MLC_STAGE_FH: src = pl->FH; break;
         case MLC_STAGE_PHIH: src = pl->phiH; break;
         case MLC_STAGE_PHIB: src = pl->phiB; break;
+        case MLC_STAGE_PHIB_OUTER: src = pl->phiB2; break;
         case MLC_STAGE_DGF: src = pl->dgf; break;
         default: return MLC_ERR_INVALID_ARG;
     }

@@ -24,6 +24,7 @@ MLC_MODE_MLC, MLC_MODE_MLC0 = 0, 1
  MLC_ERR_TIMEOUT, MLC_ERR_INDEX) = range(8)
 STAGE_MOMENTS, STAGE_FH, STAGE_PHIH, STAGE_PHIB, STAGE_DGF = 0, 1, 2, 3, 4
 STAGE_COARSE_SAMPLES, STAGE_FACE_INDEX, STAGE_COARSE_INDEX = 5, 6, 7
+STAGE_PHIB_OUTER = 8  # Q = 10: boundary values one node off the face planes
 
 EXPORTED = [
     "mlc_params_init", "mlc_plan_create", "mlc_plan_create_ex", "mlc_plan_destroy",
@@ -313,6 +314,9 @@ class Plan:
         if stage == STAGE_PHIB:
             npl = i.N // i.n + 1
             return out.reshape(3, npl, i.N + 1, i.N + 1)
+        if stage == STAGE_PHIB_OUTER:
+            npl = i.N // i.n + 1
+            return out.reshape(3, npl, 2, i.N + 1, i.N + 1)
         if stage == STAGE_DGF:
             m = i.L + 1
             return out.reshape(m, m, m)

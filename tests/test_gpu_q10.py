@@ -1,0 +1,168 @@
+"""The q = 10 operator on the GPU (Sec. 8; reading R18): the DGF table, every
+stage of the solve and the potential against the oracle (relative max-norm
+1e-12 for the FP64 tier, 1e-6 for the split tier), including the boundary
+values of the second layer one node off the face planes; the batched and
+no-alloc entry points give the standalone solve's bits; plans the library
+does not run are refused with UNSUPPORTED.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import mlc_oracle as O
+from paper_1702_08111_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+FP64, SPLIT, DF, SPLIT_DF = 0, 1, 2, 3
+
+
+def relmax(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def G10():
+    return O.dgf_octant(10, 128, 2)
+
+
+def test_q10_dgf_table_matches_oracle(torch_cuda, G10):
+    from paper_1702_08111_gb300 import mlc
+    plan = mlc.Plan(32, 8, 20, 4, 10)
+    T = plan.export(mlc.STAGE_DGF)
+    L = min(T.shape[0], G10.shape[0])
+    assert relmax(T[:L, :L, :L], G10[:L, :L, :L]) <= 1e-13
+
+
+def _phiB_from_planes(planes, nodes, n):
+    out = np.empty(len(nodes))
+    for a, g in enumerate(nodes):
+        for d in range(3):
+            if g[d] % n == 0:
+                u, v = [g[e] for e in range(3) if e != d]
+                out[a] = planes[d, g[d] // n, u, v]
+                break
+    return out
+
+
+def _outer_from_planes(planes, nodes, n, N):
+    """GPU second-layer values at the oracle's outer nodes: every plane slot
+    that holds the node (a node one step off the face planes of two axes is
+    in two), as a list of (oracle index, value)."""
+    out = []
+    for a, g in enumerate(nodes):
+        for d in range(3):
+            r = g[d] % n
+            if r not in (1, n - 1):
+                continue
+            u, v = [g[e] for e in range(3) if e != d]
+            if not (0 <= u <= N and 0 <= v <= N):
+                continue
+            side = 1 if r == 1 else 0
+            j = (g[d] - 1) // n if side else (g[d] + 1) // n
+            out.append((a, planes[d, j, side, u, v]))
+    return out
+
+
+_ORACLE = {}
+
+CASES = [
+    dict(N=32, n=8, s=20),                      # b = 5 (q_I = 12), alpha = 1, beta = 2: Legendre ring
+    dict(N=32, n=8, s=16, b=3, mode=1),         # MLC-0, b = 3, g_alpha = 4
+    dict(N=64, n=16, s=24),                     # n = 16, M = 128, g_alpha = 4, g_beta = 8
+]
+
+
+@pytest.mark.parametrize("tier", [FP64, SPLIT])
+@pytest.mark.parametrize("kw", CASES, ids=["n8_b5_ring", "n8_b3_mlc0", "n16_b5"])
+def test_q10_solve_against_oracle(torch_cuda, G10, kw, tier):
+    from paper_1702_08111_gb300 import mlc
+    torch = torch_cuda
+    N, n = kw["N"], kw["n"]
+    f64 = I.sample_bumps(N, I.draw_bumps(5, 1000 + N + kw["s"]))
+    if tier == SPLIT:
+        f64 = f64.astype(np.float32).astype(np.float64)
+    key = (repr(sorted(kw.items())), tier)
+    if key not in _ORACLE:
+        prm = O.Params(N=N, n=n, s=kw["s"], P=4, Q=10, b=kw.get("b"),
+                       mode="mlc0" if kw.get("mode", 0) else "mlc")
+        st = {}
+        phi = O.solve_open(prm, f64, G1=G10, stages=st)
+        _ORACLE[key] = (prm, phi, st)
+    prm, phi_o, st = _ORACLE[key]
+    pk = {k: v for k, v in kw.items() if k not in ("N", "n", "s")}
+    plan = mlc.Plan(N, n, kw["s"], 4, 10, tier=tier, **pk)
+    f = torch.from_numpy(f64.astype(np.float32) if tier == SPLIT else f64).cuda()
+    phi = plan.solve(f)
+    torch.cuda.synchronize()
+    plan.status()
+    tol = 1e-6 if tier == SPLIT else 1e-12
+    assert relmax(plan.export(mlc.STAGE_FH), st["FH"]) <= tol
+    assert relmax(plan.export(mlc.STAGE_PHIH), st["phiH"]) <= tol
+    pb = _phiB_from_planes(plan.export(mlc.STAGE_PHIB), st["face_nodes"], n)
+    assert relmax(pb, st["phiB"]) <= tol
+    outer = plan.export(mlc.STAGE_PHIB_OUTER)
+    pairs = _outer_from_planes(outer, st["outer_nodes"], n, N)
+    assert len({a for a, _ in pairs}) == len(st["outer_nodes"])  # every oracle node has a GPU value
+    idx = np.array([a for a, _ in pairs])
+    got = np.array([v for _, v in pairs])
+    assert relmax(got, st["phiB_outer"][idx]) <= tol
+    err = relmax(phi.cpu().numpy(), phi_o)
+    assert err <= tol, err
+
+
+def test_q10_batch_and_noalloc_bits(torch_cuda):
+    """Q = 10 plans in one batched call with a Q = 6 plan, and the no-alloc
+    entry point: the standalone solve's bits."""
+    from paper_1702_08111_gb300 import mlc
+    torch = torch_cuda
+    specs = [dict(N=32, n=8, s=20, Q=10, tier=FP64), dict(N=48, n=8, s=20, Q=10, tier=FP64),
+             dict(N=32, n=8, s=12, Q=6, tier=FP64), dict(N=64, n=16, s=24, Q=10, tier=SPLIT)]
+    plans, fs, ref = [], [], []
+    for k, sp in enumerate(specs):
+        N = sp["N"]
+        f64 = I.sample_bumps(N, I.draw_bumps(3, 1700 + k))
+        p = mlc.Plan(N, sp["n"], sp["s"], 4, sp["Q"], tier=sp["tier"])
+        f = torch.from_numpy(f64.astype(np.float32) if sp["tier"] == SPLIT else f64).cuda()
+        plans.append(p)
+        fs.append(f)
+        ref.append(p.solve(f).clone())
+    torch.cuda.synchronize()
+    phis = [torch.empty_like(r) for r in ref]
+    for _ in range(2):
+        mlc.batch_solve(plans, fs, phis)
+        torch.cuda.synchronize()
+        for a, b in zip(phis, ref):
+            assert torch.equal(a, b)
+    out = torch.empty_like(ref[0])
+    plans[0].solve_noalloc(fs[0], out)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref[0])
+
+
+def test_q10_unsupported_configurations(torch_cuda):
+    from paper_1702_08111_gb300 import mlc
+    for kw in (dict(tier=DF), dict(tier=SPLIT_DF), dict(levels=3)):
+        with pytest.raises(mlc.MLCError) as e:
+            mlc.Plan(64, 8, 20, 4, 10, **kw)
+        assert e.value.status == mlc.MLC_ERR_UNSUPPORTED
+    with pytest.raises(mlc.MLCError) as e:
+        mlc.Plan(64, 32, 24, 4, 10)
+    assert e.value.status == mlc.MLC_ERR_UNSUPPORTED
+    with pytest.raises(mlc.MLCError) as e:
+        mlc.Plan(64, 8, 24, 4, 10, b=6)
+    assert e.value.status == mlc.MLC_ERR_INVALID_ARG
+    # the second-layer stage exists for Q = 10 plans only
+    p = mlc.Plan(32, 8, 12, 4, 6)
+    with pytest.raises(mlc.MLCError):
+        p.export(mlc.STAGE_PHIB_OUTER)
