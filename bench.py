@@ -284,6 +284,44 @@ def dirichlet_counts(n, Q):
     return flops, inst
 
 
+Q10_ORBITS = ((0, 0, 0), (1, 0, 0), (1, 1, 0), (1, 1, 1), (2, 0, 0), (2, 1, 0))
+WIDE_DIRICHLET_ITERS = 10  # fixed-point steps after the first solve (the library's count)
+
+
+def dirichlet_wide_counts(n, iters=WIDE_DIRICHLET_ITERS):
+    """Algorithmic FLOPs and instructions of the Q = 10 Dirichlet step for one
+    patch (two boundary layers, the fixed point u = L_odd^-1 (b - E u)): the
+    boundary terms of b (a product and a sum each), 1 + iters DST-I solves (6
+    passes of (n-1)^2 lines: n = 16 the split-radix 15-point DST, 97
+    operations; otherwise dense sums, m FMAs per output; (n-1)^3 eigenvalue
+    products), iters corrections E u (a product and a sum per mirrored term)
+    and the Mehrstellen correction (one FMA per node)."""
+    import itertools
+    offs = [s for s in itertools.product(range(-2, 3), repeat=3)
+            if tuple(sorted(map(abs, s), reverse=True)) in Q10_ORBITS]
+    m = n - 1
+    tb = tc = 0
+    for c in itertools.product(range(1, n), repeat=3):
+        for sft in offs:
+            t = [c[d] + sft[d] for d in range(3)]
+            if all(1 <= x <= m for x in t):
+                continue
+            tb += 1
+            if any(x in (-1, n + 1) for x in t):
+                mir = [1 if x == -1 else (m if x == n + 1 else x) for x in t]
+                if all(1 <= x <= m for x in mir):
+                    tc += 1
+    if n == 16:
+        line_flops = line_inst = 97
+    else:
+        line_flops, line_inst = 2 * m * m, m * m
+    solve_f = 6 * m * m * line_flops + m ** 3
+    solve_i = 6 * m * m * line_inst + m ** 3
+    flops = 2 * tb + (1 + iters) * solve_f + iters * 2 * tc + 2 * n ** 3
+    inst = 2 * tb + (1 + iters) * solve_i + iters * 2 * tc + n ** 3
+    return flops, inst
+
+
 def roofline_for(w, plan, per_launch, tier, traffic=None):
     """Roofline of the dominant launch.  Slab kernel (local convolutions):
     algorithmic work = nominal radix-2 FFT FLOPs (5 M log2 M per complex line)
@@ -341,6 +379,13 @@ def roofline_for(w, plan, per_launch, tier, traffic=None):
         units, pipe_rate = min(NP, CONV_CHUNK) * Mh, (FP64_INST_PER_S if tier == "fp64" else FP32_LANE_INST_PER_S)
         pipe = "FP64 pipe" if tier == "fp64" else "FP32 pipe"
         unit_name = "(patch, kx) slab"
+    elif dom == "dirichlet" and getattr(w, "Q", 0) == 10:
+        nominal, inst = dirichlet_wide_counts(w.n)
+        nlaunch = 1
+        units, pipe_rate = NP, FP64_INST_PER_S
+        pipe = "FP64 pipe"
+        sched = "FP64 two-layer fixed point on DST-I"
+        unit_name = "patch"
     elif dom == "dirichlet" and w.n in (16, 32):
         nominal, inst = dirichlet_counts(w.n, w.Q)
         if not fine64:
@@ -490,6 +535,7 @@ def run_extra(args, flush, stream, w, head_tier, phi_head, head_ms):
         out["ratios_to_plain_fp64"]["split"] = round(out["fp64"]["ms_per_step"] / out["split"]["ms_per_step"], 3)
     out["fp64_128"] = run_fp64_128(args, flush, stream)
     out["paper_params"] = run_paper_params(args, flush, stream)
+    out["q10"] = run_q10(args, flush, stream)
     out["batch"] = run_batch(args, flush, stream)
     out["serving"] = run_serving(args)
     out["noalloc"] = run_noalloc(args, flush, stream)
@@ -534,6 +580,47 @@ def run_paper_params(args, flush, stream):
                      "roofline": roof,
                      "per_launch_ms": {k: round(v, 4) for k, v in pl.items()}}
         del plan, f, phi
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_q10(args, flush, stream):
+    """The q = 10 operator (Sec. 8) on the Sec. 7.1 smooth charge at 256^3,
+    n = 16: the library's default (s = 24, b = 5, beta = 2) in the split tier,
+    and MLC-0 at the same outer radius g_beta = 16 for Q = 10 (s = 36, b = 5)
+    and Q = 6 (s = 28, b = 3) in the plain FP64 tier (and Q = 10 split), so
+    the two operators' barrier errors compare at one radius; Mpoints/s,
+    per-launch times, the roofline of the dominant launch and the scaled max
+    error against the closed form."""
+    import torch
+    from oracle import closed_forms as CF
+    from paper_1702_08111_gb300 import mlc
+    out = {}
+    steps = max(3, args.steps // 4)
+    cases = [("q10_default_256_split", 256, 10, 24, "split", {}),
+             ("q10_mlc0_gb16_256_split", 256, 10, 36, "split", {"mode": 1}),
+             ("q10_mlc0_gb16_256_fp64", 256, 10, 36, "fp64", {"mode": 1}),
+             ("q6_mlc0_gb16_256_fp64", 256, 6, 28, "fp64", {"mode": 1})]
+    exact = {}
+    for name, N, Q, s_, tier, kw in cases:
+        f64 = I.paper_smooth_charge(N)
+        f = torch.from_numpy(f64.astype(np.float32) if tier == "split" else f64).cuda()
+        plan = mlc.Plan(N, 16, s_, 4, Q, tier=TIER_IDS[tier], **kw)
+        phi = torch.empty((N,) * 3, dtype=torch.float64, device="cuda")
+        ms, pl = time_plan(plan, f, phi, steps, 3, flush, stream, 1, per_launch_steps=1)
+        wl = SimpleNamespace(N=N, n=16, s=s_, Q=Q, name=name)
+        if N not in exact:
+            exact[N] = CF.smooth_potential_grid(N)
+        ph = phi.cpu().numpy()
+        err = float(np.abs(ph - exact[N]).max() / np.abs(exact[N]).max())
+        info = plan.info
+        out[name] = {"N": N, "n": 16, "s": s_, "Q": Q, "b": info.b, "g_alpha": info.g_alpha,
+                     "g_beta": info.g_beta, "M": info.M, "tier": tier, "mode": "mlc0" if kw else "mlc",
+                     "ms_per_step": round(ms, 4), "value": round(float(N) ** 3 / (ms * 1e-3) / 1e6, 2),
+                     "unit": "Mpoints/s", "max_rel_err_vs_closed_form": err,
+                     "roofline": roofline_for(wl, plan, pl, tier),
+                     "per_launch_ms": {k: round(v, 4) for k, v in pl.items()}}
+        del plan, f, phi, ph
         torch.cuda.empty_cache()
     return out
 

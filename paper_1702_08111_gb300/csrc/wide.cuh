@@ -279,6 +279,10 @@ __global__ void __launch_bounds__(256) k_dirichlet_wide(DirWArgs a) {
     __syncthreads();
     // X <- L_odd^-1 X: three DST-I passes, the eigenvalue scaling (lam holds
     // (2/n)^3 h^2 / lambda), three more passes
+    double sv16[9];  // n = 16: sin(pi i / 16), i = 0..8
+    sv16[0] = 0.0;
+#pragma unroll
+    for (int i = 1; i <= 8; ++i) sv16[i] = NN == 16 ? a.sinm[i - 1] : 0.0;
     auto solve = [&]() {
         for (int pass = 0; pass < 6; ++pass) {
             const int axis = 2 - (pass % 3);
@@ -291,13 +295,19 @@ __global__ void __launch_bounds__(256) k_dirichlet_wide(DirWArgs a) {
                 double x[m];
 #pragma unroll
                 for (int t = 0; t < m; ++t) x[t] = X[base + t * str];
+                if constexpr (NN == 16) {  // the split-radix 15-point DST-I
+                    dst15_fast(x, sv16);
 #pragma unroll
-                for (int k = 0; k < m; ++k) {
-                    double acc = 0.0;
+                    for (int k = 0; k < m; ++k) X[base + k * str] = pass == 2 ? x[k] * lam[base + k * str] : x[k];
+                } else {
 #pragma unroll
-                    for (int t = 0; t < m; ++t) acc = fma(S[k * m + t], x[t], acc);
-                    if (pass == 2) acc *= lam[base + k * str];
-                    X[base + k * str] = acc;
+                    for (int k = 0; k < m; ++k) {
+                        double acc = 0.0;
+#pragma unroll
+                        for (int t = 0; t < m; ++t) acc = fma(S[k * m + t], x[t], acc);
+                        if (pass == 2) acc *= lam[base + k * str];
+                        X[base + k * str] = acc;
+                    }
                 }
             }
             __syncthreads();
