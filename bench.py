@@ -293,7 +293,8 @@ def dirichlet_wide_counts(n, iters=WIDE_DIRICHLET_ITERS):
     patch (two boundary layers, the fixed point u = L_odd^-1 (b - E u)): the
     boundary terms of b (a product and a sum each), 1 + iters DST-I solves (6
     passes of (n-1)^2 lines: n = 16 the split-radix 15-point DST, 97
-    operations; otherwise dense sums, m FMAs per output; (n-1)^3 eigenvalue
+    operations; n = 32 the split 31-point DST; otherwise dense sums, m FMAs
+    per output; (n-1)^3 eigenvalue
     products), iters corrections E u (a product and a sum per mirrored term)
     and the Mehrstellen correction (one FMA per node)."""
     import itertools
@@ -313,6 +314,9 @@ def dirichlet_wide_counts(n, iters=WIDE_DIRICHLET_ITERS):
                     tc += 1
     if n == 16:
         line_flops = line_inst = 97
+    elif n == 32:  # the split 31-point DST (as in dirichlet_counts)
+        line_inst = 30 + 97 + 8 * (15 + 4)
+        line_flops = 30 + 97 + 8 * (2 * 15 + 4)
     else:
         line_flops, line_inst = 2 * m * m, m * m
     solve_f = 6 * m * m * line_flops + m ** 3
@@ -585,37 +589,37 @@ def run_paper_params(args, flush, stream):
 
 
 def run_q10(args, flush, stream):
-    """The q = 10 operator (Sec. 8) on the Sec. 7.1 smooth charge at 256^3,
-    n = 16: the library's default (s = 24, b = 5, beta = 2) in the split tier,
-    and MLC-0 at the same outer radius g_beta = 16 for Q = 10 (s = 36, b = 5)
-    and Q = 6 (s = 28, b = 3) in the plain FP64 tier (and Q = 10 split), so
-    the two operators' barrier errors compare at one radius; Mpoints/s,
-    per-launch times, the roofline of the dominant launch and the scaled max
-    error against the closed form."""
+    """The q = 10 operator (Sec. 8) against the 27-point one on the Sec. 7.1
+    smooth charge at 256^3 with the paper's patch size n = 32: the two-level
+    solve at alpha = 2, beta = 3.25 (Q = 6: s = 28, b = 3; Q = 10: s = 32,
+    b = 4) in the plain FP64 tier and (Q = 10) the split tier, and Q = 10 at
+    the Table 7 inner radius alpha = 1.75 (s = 28, b = 4), where the wider
+    coarse stencil loses; Mpoints/s, per-launch times, the roofline of the
+    dominant launch and the scaled max error against the closed form."""
     import torch
     from oracle import closed_forms as CF
     from paper_1702_08111_gb300 import mlc
     out = {}
     steps = max(3, args.steps // 4)
-    cases = [("q10_default_256_split", 256, 10, 24, "split", {}),
-             ("q10_mlc0_gb16_256_split", 256, 10, 36, "split", {"mode": 1}),
-             ("q10_mlc0_gb16_256_fp64", 256, 10, 36, "fp64", {"mode": 1}),
-             ("q6_mlc0_gb16_256_fp64", 256, 6, 28, "fp64", {"mode": 1})]
+    cases = [("q6_n32_alpha2_256_fp64", 256, 6, 28, "fp64", dict(b=3, g_beta=36)),
+             ("q10_n32_alpha2_256_fp64", 256, 10, 32, "fp64", dict(b=4, g_beta=36)),
+             ("q10_n32_alpha2_256_split", 256, 10, 32, "split", dict(b=4, g_beta=36)),
+             ("q10_n32_alpha175_256_fp64", 256, 10, 28, "fp64", dict(b=4, g_beta=36))]
     exact = {}
     for name, N, Q, s_, tier, kw in cases:
         f64 = I.paper_smooth_charge(N)
         f = torch.from_numpy(f64.astype(np.float32) if tier == "split" else f64).cuda()
-        plan = mlc.Plan(N, 16, s_, 4, Q, tier=TIER_IDS[tier], **kw)
+        plan = mlc.Plan(N, 32, s_, 4, Q, tier=TIER_IDS[tier], **kw)
         phi = torch.empty((N,) * 3, dtype=torch.float64, device="cuda")
         ms, pl = time_plan(plan, f, phi, steps, 3, flush, stream, 1, per_launch_steps=1)
-        wl = SimpleNamespace(N=N, n=16, s=s_, Q=Q, name=name)
+        wl = SimpleNamespace(N=N, n=32, s=s_, Q=Q, name=name)
         if N not in exact:
             exact[N] = CF.smooth_potential_grid(N)
         ph = phi.cpu().numpy()
         err = float(np.abs(ph - exact[N]).max() / np.abs(exact[N]).max())
         info = plan.info
-        out[name] = {"N": N, "n": 16, "s": s_, "Q": Q, "b": info.b, "g_alpha": info.g_alpha,
-                     "g_beta": info.g_beta, "M": info.M, "tier": tier, "mode": "mlc0" if kw else "mlc",
+        out[name] = {"N": N, "n": 32, "s": s_, "Q": Q, "b": info.b, "g_alpha": info.g_alpha,
+                     "g_beta": info.g_beta, "M": info.M, "tier": tier,
                      "ms_per_step": round(ms, 4), "value": round(float(N) ** 3 / (ms * 1e-3) / 1e6, 2),
                      "unit": "Mpoints/s", "max_rel_err_vs_closed_form": err,
                      "roofline": roofline_for(wl, plan, pl, tier),

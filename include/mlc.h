@@ -84,9 +84,9 @@ typedef struct {
                        -1/420; C2 = 2/35.  Its Dirichlet step has a second boundary
                        layer one node outside the faces (MLC_STAGE_PHIB_OUTER)          */
     int g_beta;     /* outer growth ceil((beta-1) n/2) (Sec. 4); -1: beta = 3 (Q=4),
-                       3.25 (Q=6), 2 (Q=10: beta^-10 ~ 3.25^-6)                          */
+                       3.25 (Q=6, Q=10)                                                  */
     int b;          /* interpolation stencil radius, 1..5 (q_I = 2b+2); -1: 2 for Q=4,
-                       3 for Q=6, 5 for Q=10 (q_I = q + 2, Sec. 7)                       */
+                       3 for Q=6 (q_I = q + 2, Sec. 7), 4 for Q=10                       */
     int tier;       /* mlc_tier                                                         */
     int mode;       /* mlc_mode                                                         */
     int dgf_nD;     /* DGF table built on [-zeta nD, zeta nD]^3 (App. A.1); -1: 128,
@@ -126,9 +126,8 @@ mlc_status mlc_params_init(mlc_params *p, int N, int n, int s, int P, int Q);
  * above; g_beta < s - C b.  UNSUPPORTED if: n is not one of 4, 8, 12, 16, 24,
  * 32; the patch FFT length (the power of two >= 2(n+s)) is above 128; the
  * coarse FFT length (the smallest even 2^a 3^b 5^c >= twice the largest
- * coarse lag) is above 512; Q = 10 with levels > 2, n > 16 or a
- * double-float tier (its boundary and Dirichlet steps run in FP64: tiers FP64
- * and SPLIT).  With levels > 2 the plan of the next coarser
+ * coarse lag) is above 512; Q = 10 with levels > 2 or a double-float tier
+ * (its boundary and Dirichlet steps run in FP64: tiers FP64 and SPLIT).  With levels > 2 the plan of the next coarser
  * level is created with it, with its scratch, so that no solve allocates.
  */
 mlc_status mlc_plan_create(int N, int patch, int support, int coarsening, int P, int Q,

@@ -143,10 +143,10 @@ class Params:
             raise ValueError("coarsening ratio is 4 (Sec. 2)")
         if self.N % self.n or self.n % 4 or self.s % 4:
             raise ValueError("need n | N, 4 | n, 4 | s")
-        if self.b is None:  # q_I = 2b + 2 = q + 2 (Sec. 7)
-            self.b = {4: 2, 6: 3, 10: 5}[self.Q]
-        if self.beta is None:  # equal barrier terms beta^-q (Sec. 7): 3^4 ~ 2^6 ~ 2^10 / 16
-            self.beta = {4: 3.0, 6: 3.25, 10: 2.0}[self.Q]
+        if self.b is None:  # q_I = 2b + 2 = q + 2 (Sec. 7); b = 4 for q = 10 (R18)
+            self.b = {4: 2, 6: 3, 10: 4}[self.Q]
+        if self.beta is None:  # Sec. 7 settings; q = 10 as L27 (R18)
+            self.beta = {4: 3.0, 6: 3.25, 10: 3.25}[self.Q]
         if self.levels < 2:
             raise ValueError("levels >= 2")
         if self.Q == 10 and self.levels != 2:

@@ -178,7 +178,8 @@ mlc_status derive_geometry(const mlc_params &pp, Geom &g) {
     g.wide = stencil_reach(g.Q) > 1;
     if (g.N <= 0 || g.n <= 0 || g.s < 0 || g.P < 1 || g.P > 6) return MLC_ERR_INVALID_ARG;
     if (g.N % g.n || g.n % 4 || g.s % 4) return MLC_ERR_INVALID_ARG;
-    g.b = pp.b < 0 ? (g.Q == 4 ? 2 : (g.Q == 6 ? 3 : 5)) : pp.b;  // q_I = 2b + 2 = q + 2
+    // q_I = 2b + 2 = q + 2 for L19 and L27 (Sec. 7); b = 4 for Q = 10 (R18)
+    g.b = pp.b < 0 ? (g.Q == 4 ? 2 : (g.Q == 6 ? 3 : 4)) : pp.b;
     if (g.b < 1 || g.b > 5) return MLC_ERR_INVALID_ARG;
     g.ga = g.s - g.C * g.b;
     if (g.ga < 0) return MLC_ERR_INVALID_ARG;
@@ -195,8 +196,8 @@ mlc_status derive_geometry(const mlc_params &pp, Geom &g) {
     } else if (pp.g_beta >= 0) {
         g.gb = pp.g_beta;
     } else {
-        // beta = 3 (Q = 4), 13/4 (Q = 6) or 2 (Q = 10): g_beta = ceil((beta - 1) n / 2)
-        g.gb = (g.Q == 4) ? g.n : (g.Q == 6 ? ceildiv(9 * g.n, 8) : ceildiv(g.n, 2));
+        // beta = 3 (Q = 4) or 13/4 (Q = 6, and Q = 10 by R18): g_beta = ceil((beta - 1) n / 2)
+        g.gb = (g.Q == 4) ? g.n : ceildiv(9 * g.n, 8);
     }
     if (g.gb < g.ga) return MLC_ERR_INVALID_ARG;
     g.h = 1.0 / g.N;
@@ -247,7 +248,7 @@ mlc_status derive_geometry(const mlc_params &pp, Geom &g) {
     if (g.M < 32 || g.M > 128 || (g.levels <= 2 && g.Mc > 512)) return MLC_ERR_UNSUPPORTED;
     // Q = 10 (R18): two levels, FP64 boundary and Dirichlet steps (tiers FP64
     // and SPLIT), and patches whose two-layer Dirichlet arrays fit shared memory
-    if (g.wide && (g.levels != 2 || g.fine != FINE_F64 || g.n > 16)) return MLC_ERR_UNSUPPORTED;
+    if (g.wide && (g.levels != 2 || g.fine != FINE_F64)) return MLC_ERR_UNSUPPORTED;
     if (g.wide && g.b < 2) return MLC_ERR_INVALID_ARG;  // Delta^H reaches two coarse nodes past C(alpha)
     g.S = (2 * g.b + 2) * (2 * g.b + 2);
     g.nc = (g.n + 2 * g.s) / 4 + 1;
@@ -840,9 +841,9 @@ mlc_status create_plan(const mlc_params *params, const double *dgf_host, int dgf
             TRY(dev_alloc(pl, &pl->phiB2, 2 * (size_t)G.n_planes_total));
             TRY(dev_alloc(pl, &pl->tpl2, 6 * (size_t)(G.np + 1) * G.no * (G.N + 1)));
         }
-        if (G.n > 24) {  // Dirichlet workspace of patches too large for shared memory
-            double *d = nullptr;
-            TRY(dev_alloc(pl, &d, NP * (size_t)(G.n - 1) * (G.n - 1) * (G.n - 1)));
+        if (G.n > 24 || (G.wide && G.n > 16)) {  // Dirichlet workspace of patches too large for shared memory
+            double *d = nullptr;                     // (Q = 10: right-hand side, iterate and work array)
+            TRY(dev_alloc(pl, &d, NP * (G.wide ? 3 : 1) * (size_t)(G.n - 1) * (G.n - 1) * (G.n - 1)));
             pl->dscr = d;
         }
         TRY(dev_alloc(pl, &pl->err, 1, false));

@@ -94,19 +94,21 @@ size_t estimate_bytes(const mlc_params &p) {
     bytes += 3L * (np + 1) * (N + 1) * (N + 1) * 8;           // boundary planes
     bytes += (Mh * Mh * Mh + (Mc / 2 + 1) * (Mc / 2 + 1) * (Mc / 2 + 1)) * 12;
     if (rb == 4) {  // split tiers: ring terms of one face-plane axis for the ring GEMM
-        const long gb = p.g_beta >= 0 ? p.g_beta : (p.Q == 4 ? n : (p.Q == 6 ? (9 * n + 7) / 8 : (n + 1) / 2));
+        const long gb = p.g_beta >= 0 ? p.g_beta : (p.Q == 4 ? n : (9 * n + 7) / 8);
         const long wbx = n + 2 * gb + 1, npb = (n + 2 * gb) / n + 2;
         bytes += NP * ((npb * wbx * wbx + 127) / 128 * 128) * 4;
     }
     if (n > 24) bytes += NP * (n - 1) * (n - 1) * (n - 1) * 8;  // Dirichlet workspace
+    if (p.Q == 10 && n > 16) bytes += NP * 2 * (n - 1) * (n - 1) * (n - 1) * 8;  // two-layer Dirichlet arrays
+    if (p.Q == 10 && n > 16 && n <= 24) bytes += NP * (n - 1) * (n - 1) * (n - 1) * 8;
     if (p.Q == 10)  // the second boundary layer: off-face local fields and residuals, planes
         bytes += NP * 12 * W * W * (rb + 8) + 6L * (np + 1) * (N + 1) * (N + 1) * 8 +
                  6L * (np + 1) * (nf + 4) * (N + 1) * 8;
     if (p.levels > 2) {
         // the next coarser level: its own plan (with its local-convolution
         // scratch, allocated at creation) and its charge and result arrays
-        const long gb = p.g_beta >= 0 ? p.g_beta : (p.Q == 4 ? n : (p.Q == 6 ? (9 * n + 7) / 8 : (n + 1) / 2));
-        const long b = p.b >= 0 ? p.b : (p.Q == 4 ? 2 : (p.Q == 6 ? 3 : 5));
+        const long gb = p.g_beta >= 0 ? p.g_beta : (p.Q == 4 ? n : (9 * n + 7) / 8);
+        const long b = p.b >= 0 ? p.b : (p.Q == 4 ? 2 : (p.Q == 6 ? 3 : 4));
         const long span = N / 4 + 2 * (gb / 4 + b + 2);
         mlc_params c = p;
         c.N = (int)(n * ((span + n - 1) / n));

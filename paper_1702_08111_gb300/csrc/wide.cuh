@@ -225,20 +225,29 @@ struct DirWArgs {
 template <typename TF, int NN>
 __global__ void __launch_bounds__(256) k_dirichlet_wide(DirWArgs a) {
     constexpr int n = NN, m = n - 1, m3 = m * m * m, h = n / 2;
+    constexpr bool BIG = NN > 16;  // the three arrays in the plan's global workspace (L2-resident)
     extern __shared__ double smw[];
-    double *B = smw;       // right-hand side with the boundary data
-    double *U = B + m3;    // current iterate
-    double *X = U + m3;    // transform work array
-    double *S = X + m3;    // S[k][t] = sin(pi (k+1)(t+1) / n)
     int p;
     const PlanPtrs &PP = item_plan(a.it, blockIdx.x, p);
+    double *B, *U, *X, *S;  // right-hand side, current iterate, transform work array, DST-I matrix
+    if constexpr (BIG) {
+        B = (double *)PP.dscr + (long)p * 3 * m3;
+        U = B + m3;
+        X = U + m3;
+        S = smw;
+    } else {
+        B = smw;
+        U = B + m3;
+        X = U + m3;
+        S = X + m3;
+    }
     const int N = PP.N, np = PP.np;
     const int i0 = p / (np * np), i1 = (p / np) % np, i2 = p % np;
     const int o0 = i0 * n, o1 = i1 * n, o2 = i2 * n;
     const TF *f = (const TF *)PP.f;
     const double ih2 = PP.inv_h2;
     const double *lam = (const double *)PP.lam;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    for (int e = threadIdx.x; e < m * m && NN != 16 && NN != 32; e += blockDim.x) {  // dense lines only
         const int k = e / m, T = e % m + 1;
         // sin(pi K (n - T') / n) = (-1)^(K+1) sin(pi K T' / n), K = k + 1
         S[e] = T <= h ? a.sinm[k * h + (T - 1)] : ((k & 1) ? -1.0 : 1.0) * a.sinm[k * h + (n - T - 1)];
@@ -283,6 +292,10 @@ __global__ void __launch_bounds__(256) k_dirichlet_wide(DirWArgs a) {
     sv16[0] = 0.0;
 #pragma unroll
     for (int i = 1; i <= 8; ++i) sv16[i] = NN == 16 ? a.sinm[i - 1] : 0.0;
+    double sv32[17];  // n = 32: sin(pi i / 32), i = 0..16
+    sv32[0] = 0.0;
+#pragma unroll
+    for (int i = 1; i <= 16; ++i) sv32[i] = NN == 32 ? a.sinm[i - 1] : 0.0;
     auto solve = [&]() {
         for (int pass = 0; pass < 6; ++pass) {
             const int axis = 2 - (pass % 3);
@@ -295,8 +308,9 @@ __global__ void __launch_bounds__(256) k_dirichlet_wide(DirWArgs a) {
                 double x[m];
 #pragma unroll
                 for (int t = 0; t < m; ++t) x[t] = X[base + t * str];
-                if constexpr (NN == 16) {  // the split-radix 15-point DST-I
-                    dst15_fast(x, sv16);
+                if constexpr (NN == 16 || NN == 32) {  // the split-radix 15-point / split 31-point DST-I
+                    if constexpr (NN == 16) dst15_fast(x, sv16);
+                    else dst31_fast(x, sv32);
 #pragma unroll
                     for (int k = 0; k < m; ++k) X[base + k * str] = pass == 2 ? x[k] * lam[base + k * str] : x[k];
                 } else {
@@ -318,32 +332,29 @@ __global__ void __launch_bounds__(256) k_dirichlet_wide(DirWArgs a) {
     solve();
     for (int e = threadIdx.x; e < m3; e += blockDim.x) U[e] = X[e];
     __syncthreads();
+    // E u on the layer next to a face: the offsets that leave the interior
+    // through the face are (-+2, 0, 0) and (-+2, +-1, 0), (-+2, 0, +-1) along
+    // its normal; their mirror images lie in the same layer, at the node
+    // itself and its four in-layer neighbours (zero on the faces)
+    const double e200 = stencil_coef(10, 2, 0, 0) * ih2, e210 = stencil_coef(10, 2, 1, 0) * ih2;
+    auto Uin = [&](int q0, int q1, int q2) -> double {
+        return (q0 < 1 || q0 > m || q1 < 1 || q1 > m || q2 < 1 || q2 > m) ? 0.0
+                                                                         : U[((q0 - 1) * m + (q1 - 1)) * m + (q2 - 1)];
+    };
     for (int it = 0; it < a.iters; ++it) {
         for (int e = threadIdx.x; e < m3; e += blockDim.x) {
             const int q2 = e % m + 1, q1 = (e / m) % m + 1, q0 = e / (m * m) + 1;
             double r = B[e];
-            if (q0 == 1 || q0 == m || q1 == 1 || q1 == m || q2 == 1 || q2 == m) {
-#pragma unroll
-                for (int s0 = -2; s0 <= 2; ++s0)
-#pragma unroll
-                    for (int s1 = -2; s1 <= 2; ++s1)
-#pragma unroll
-                        for (int s2 = -2; s2 <= 2; ++s2) {
-                            const double c = stencil_coef(10, s0, s1, s2);
-                            if (c == 0.0) continue;
-                            int t0 = q0 + s0, t1 = q1 + s1, t2 = q2 + s2;
-                            const bool out0 = t0 == -1 || t0 == n + 1, out1 = t1 == -1 || t1 == n + 1,
-                                       out2 = t2 == -1 || t2 == n + 1;
-                            if (!(out0 || out1 || out2)) continue;
-                            // the mirror image through the face (u = 0 on the faces)
-                            t0 = t0 == -1 ? 1 : (t0 == n + 1 ? m : t0);
-                            t1 = t1 == -1 ? 1 : (t1 == n + 1 ? m : t1);
-                            t2 = t2 == -1 ? 1 : (t2 == n + 1 ? m : t2);
-                            if (t0 < 1 || t0 > m || t1 < 1 || t1 > m || t2 < 1 || t2 > m) continue;
-                            r -= c * ih2 * U[((t0 - 1) * m + (t1 - 1)) * m + (t2 - 1)];
-                        }
-            }
-            X[e] = r;
+            if (q0 == 1 || q0 == m)
+                r -= e200 * U[e] + e210 * (Uin(q0, q1 - 1, q2) + Uin(q0, q1 + 1, q2) + Uin(q0, q1, q2 - 1) +
+                                           Uin(q0, q1, q2 + 1));
+            if (q1 == 1 || q1 == m)
+                r -= e200 * U[e] + e210 * (Uin(q0 - 1, q1, q2) + Uin(q0 + 1, q1, q2) + Uin(q0, q1, q2 - 1) +
+                                           Uin(q0, q1, q2 + 1));
+            if (q2 == 1 || q2 == m)
+                r -= e200 * U[e] + e210 * (Uin(q0 - 1, q1, q2) + Uin(q0 + 1, q1, q2) + Uin(q0, q1 - 1, q2) +
+                                           Uin(q0, q1 + 1, q2));
+        X[e] = r;
         }
         __syncthreads();
         solve();
@@ -422,6 +433,8 @@ cudaError_t launch_boundary_outer(const mlc_plan_s *pl, cudaStream_t st) {
         MLC_BNDO(8)
         MLC_BNDO(12)
         MLC_BNDO(16)
+        MLC_BNDO(24)
+        MLC_BNDO(32)
         default: return cudaErrorInvalidValue;
     }
 #undef MLC_BNDO
@@ -440,7 +453,8 @@ cudaError_t launch_dirichlet_wide(const mlc_plan_s *pl, const Items &it, cudaStr
     a.sinm = (const double *)pl->sinm;
     a.iters = kWideDirichletIters;
     const int m = g.n - 1;
-    const size_t sm = 8 * (3 * (size_t)m * m * m + (size_t)m * m);
+    // n > 16: the arrays live in the plan's workspace; shared memory holds the dense DST-I matrix
+    const size_t sm = 8 * ((g.n > 16 ? 0 : 3 * (size_t)m * m * m) + (size_t)m * m);
 #define MLC_DIRW(NN)                                                                                      \
     case NN:                                                                                              \
         if (g.f32in) k_dirichlet_wide<float, NN><<<it.nitems, 256, sm, st>>>(a);                          \
@@ -451,6 +465,8 @@ cudaError_t launch_dirichlet_wide(const mlc_plan_s *pl, const Items &it, cudaStr
         MLC_DIRW(8)
         MLC_DIRW(12)
         MLC_DIRW(16)
+        MLC_DIRW(24)
+        MLC_DIRW(32)
         default: return cudaErrorInvalidValue;
     }
 #undef MLC_DIRW
@@ -466,6 +482,8 @@ void configure_wide() {
     MLC_DIRW_ATTR(8)
     MLC_DIRW_ATTR(12)
     MLC_DIRW_ATTR(16)
+    MLC_DIRW_ATTR(24)
+    MLC_DIRW_ATTR(32)
 #undef MLC_DIRW_ATTR
 #define MLC_RESO_ATTR(KK)                                                                                   \
     cudaFuncSetAttribute(k_resid_outer<float, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);      \
