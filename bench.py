@@ -464,7 +464,7 @@ def run_ours(args, rank, world):
     # kernel launches of one solve: moments, 3 per local-convolution launch
     # group of 1024 patches, residuals, F^H, 5 coarse, boundary, Dirichlet
     NP = (N // w.n) ** 3
-    launches = 10 + 3 * ((NP + 1023) // 1024)
+    launches = 10 + 3 * ((NP + 1023) // 1024) + (3 if w.Q == 10 else 0)  # Q = 10: the second layer's 3
     res = {"value": value, "ms": ms, "e2e_ms": e2e_ms, "per_launch": per_launch, "launches_per_step": launches,
            "roofline": roofline_for(w, plan, per_launch, tier, traffic_for(args.workload, tier, per_launch)),
            "clocks": clk.summary(), "phi": phi, "N": N, "tier": tier, "f_bytes": f_host.element_size() * N ** 3}

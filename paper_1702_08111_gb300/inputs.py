@@ -138,6 +138,8 @@ def workload(name: str) -> Workload:
     bumps16_128_q6: 128^3, 512 patches of the same geometry, 16 bumps from seed 3, FP32 charge.
     paper_smooth_128_n32: 128^3, 64 patches of 32^3 (the paper's n), support 24, Q=6, the
                     Sec. 7.1 smooth charge in FP32 (profiling case of the 128-point kernels).
+    paper_smooth_256_n32_q10: 256^3, 512 patches of 32^3, support 32, the q = 10 operator
+                    (b = 4: alpha = 2, beta = 3.25), the Sec. 7.1 smooth charge in FP32.
     """
     if name == "single_bump_32":
         return Workload(name, 32, 8, 8, 4, bumps=single_bump())
@@ -150,6 +152,8 @@ def workload(name: str) -> Workload:
         return Workload(name, 128, 16, 16, 6, bumps=draw_bumps(16, 3), charge_dtype="f32")
     if name == "paper_smooth_128_n32":
         return Workload(name, 128, 32, 24, 6, charge_dtype="f32", charge_kind="paper_smooth")
+    if name == "paper_smooth_256_n32_q10":
+        return Workload(name, 256, 32, 32, 10, charge_dtype="f32", charge_kind="paper_smooth")
     if name == "bumps8_64_q6":
         # reduced-size case with the 27-point operator: same patch geometry as bumps32_256_q6
         return Workload(name, 64, 16, 16, 6, bumps=draw_bumps(8, 7))
