@@ -1407,7 +1407,11 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
     if (threadIdx.x < 128) {
         const int yi = threadIdx.x, y = yi - s;
         const bool yA = in_alpha(y, n, ga), yP = on_plane(y, n, ga, pl0), yC = (y & 3) == 0;
-        const bool need = yi < W && (a.outer ? ((zA && yA) || (zC && yC)) : ((zP && yA) || (yP && zA) || (zC && yC)));
+        // outer: the rows one node off a face plane too (their x values off the
+        // face planes come from direct sums below, like the face-plane ones)
+        const bool zQ = zP || (a.outer && off_slot(z, n, ga, pl0, a.npa) >= 0);
+        const bool yQ = yP || (a.outer && off_slot(y, n, ga, pl0, a.npa) >= 0);
+        const bool need = yi < W && ((zQ && yA) || (yQ && zA) || (zC && yC));
         const unsigned m = __ballot_sync(0xffffffffu, need);
         if ((threadIdx.x & 31) == 0) wmask[threadIdx.x >> 5] = m;
     }
@@ -1497,14 +1501,19 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
     }
     __syncthreads();  // the buffer is refilled by the next pass
     }
-    // rows that only need x on the face planes: direct sums over the half spectrum
-    if (zA && !a.outer) {
-        for (int e = threadIdx.x; e < W * a.npa; e += blockDim.x) {
-            const int yi = e / a.npa, j = e % a.npa;
+    // rows that only need x on the face planes (outer: and one node off them):
+    // direct sums over the half spectrum
+    const bool zO = a.outer && off_slot(z, n, ga, pl0, a.npa) >= 0;
+    const int nxs = a.outer ? 3 : 1;  // x = plane, plane - 1, plane + 1
+    if (zA) {
+        for (int e = threadIdx.x; e < W * a.npa * nxs; e += blockDim.x) {
+            const int yi = e / (a.npa * nxs), j = (e / nxs) % a.npa, sub = e % nxs;
             const int y = yi - s;
             const bool yA = in_alpha(y, n, ga), yP = on_plane(y, n, ga, pl0), yC = (y & 3) == 0;
-            if (!yA || zP || yP || (zC && yC)) continue;  // not needed, or done by an FFT row
-            const int x = pl0 + j * n;
+            const bool yO = a.outer && off_slot(y, n, ga, pl0, a.npa) >= 0;
+            if (!yA || zP || yP || zO || yO || (zC && yC)) continue;  // not needed, or done by an FFT row
+            const int x = pl0 + j * n + (sub == 1 ? -1 : (sub == 2 ? 1 : 0));
+            if (sub && !in_alpha(x, n, ga)) continue;
             int pos = x % M;
             if (pos < 0) pos += M;
             R acc = R(0.0);
@@ -1514,8 +1523,14 @@ __global__ void __launch_bounds__(256) k_inv_x_pruned(InvXPArgs a) {
                 const R re = X.x * w.x + X.y * w.y;
                 acc += (k == 0 || 2 * k == M) ? re : R(2.0) * re;
             }
-            const long i = (((long)(2 * a.npa + j)) * wa + (z + ga)) * wa + (y + ga);
-            if (in_range(i, 3L * a.npa * wa * wa, PP.err)) fp[i] = (TO)acc;
+            if (sub == 0) {
+                const long i = (((long)(2 * a.npa + j)) * wa + (z + ga)) * wa + (y + ga);
+                if (in_range(i, 3L * a.npa * wa * wa, PP.err)) fp[i] = (TO)acc;
+            } else {  // off-plane slot 2 j + side of axis 2
+                TO *f2 = (TO *)PP.fp2 + (long)p * 6 * a.npa * wa * wa;
+                const long i = ((long)(2 * 2 * a.npa + 2 * j + (sub == 2 ? 1 : 0)) * wa + (z + ga)) * wa + (y + ga);
+                if (in_range(i, 6L * a.npa * wa * wa, PP.err)) f2[i] = (TO)acc;
+            }
         }
     }
 }
@@ -1586,7 +1601,11 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 8 : 4) k_inv_x64(InvXPAr
     if (threadIdx.x < 64) {
         const int yi = threadIdx.x, y = yi - s;
         const bool yA = in_alpha(y, n, ga), yP = on_plane(y, n, ga, pl0), yC = (y & 3) == 0;
-        const bool need = yi < W && (a.outer ? ((zA && yA) || (zC && yC)) : ((zP && yA) || (yP && zA) || (zC && yC)));
+        // outer: the rows one node off a face plane too (their x values off the
+        // face planes come from direct sums below, like the face-plane ones)
+        const bool zQ = zP || (a.outer && off_slot(z, n, ga, pl0, a.npa) >= 0);
+        const bool yQ = yP || (a.outer && off_slot(y, n, ga, pl0, a.npa) >= 0);
+        const bool need = yi < W && ((zQ && yA) || (yQ && zA) || (zC && yC));
         const unsigned m = __ballot_sync(0xffffffffu, need);
         if ((threadIdx.x & 31) == 0) wmask[threadIdx.x >> 5] = m;
     }
@@ -3098,13 +3117,18 @@ cudaError_t run_patch_conv_t(const mlc_plan_s *pl, const Items &it, bool f32, co
         // rows needing a full transform, per z row (the same rule as the kernel)
         auto inA = [&](int c) { return c >= -g.ga && c <= g.n + g.ga; };
         auto onP = [&](int c) { return inA(c) && ((c - g.pl0) % g.n) == 0; };
+        auto onO = [&](int c) {  // one node off an alpha face plane (the kernel's off_slot)
+            if (!g.wide || !inA(c)) return false;
+            for (int d : {c + 1 - g.pl0, c - 1 - g.pl0})
+                if (d >= 0 && d % g.n == 0 && d / g.n < g.npa) return true;
+            return false;
+        };
         for (int j = 0; j < nz; ++j) {
             const int z = zrow[j] - g.s;
             int cnt = 0;
             for (int yi = 0; yi < W; ++yi) {
                 const int y = yi - g.s;
-                if (g.wide ? ((inA(z) && inA(y)) || ((z & 3) == 0 && (y & 3) == 0))
-                           : ((onP(z) && inA(y)) || (onP(y) && inA(z)) || ((z & 3) == 0 && (y & 3) == 0)))
+                if (((onP(z) || onO(z)) && inA(y)) || ((onP(y) || onO(y)) && inA(z)) || ((z & 3) == 0 && (y & 3) == 0))
                     ++cnt;
             }
             a.maxfft = cnt > a.maxfft ? cnt : a.maxfft;
