@@ -398,7 +398,7 @@ mlc_status mlc_server_destroy(mlc_server_t s) {
 mlc_status mlc_server_enqueue(mlc_server_t s, const mlc_request *req, uint64_t *ticket) {
     if (!s || !req || !ticket || !req->f || !req->phi) return MLC_ERR_INVALID_ARG;
     const mlc_params &p = req->params;
-    if (p.N <= 0 || p.n <= 0 || p.N % p.n || p.n % 4 || p.s % 4 || (p.Q != 4 && p.Q != 6) || p.C != 4 ||
+    if (p.N <= 0 || p.n <= 0 || p.N % p.n || p.n % 4 || p.s % 4 || (p.Q != 4 && p.Q != 6 && p.Q != 10) || p.C != 4 ||
         (p.tier >= 0 && !tier_valid(p.tier)))
         return MLC_ERR_INVALID_ARG;
     const size_t est = estimate_bytes(p);

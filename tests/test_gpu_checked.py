@@ -4,7 +4,8 @@ the plan's error word (mlc_plan_status -> MLC_ERR_INDEX) instead of touching
 memory.  Solves covering every kernel family (local convolutions at 32-, 64-
 and 128-point periods, the ring GEMM, residuals, coarse charge, coarse solve,
 the coarser level of a multilevel plan, boundary values, Dirichlet solves of
-four patch sizes) run on the checked library in a child process: no check may
+four patch sizes, the q = 10 operator's second layer and two-layer Dirichlet
+solves) run on the checked library in a child process: no check may
 fire, and every result must carry the bits of the normal build (the checks
 change no arithmetic)."""
 import json
@@ -30,6 +31,8 @@ CASES = [
     dict(N=48, n=24, s=8, P=4, Q=4, tier=0, mode=1),          # n = 24
     dict(N=32, n=8, s=12, P=4, Q=4, tier=0, levels=3),        # coarser level
     dict(N=16, n=4, s=8, P=2, Q=4, tier=3),                   # n = 4, split with double-float
+    dict(N=32, n=8, s=16, P=4, Q=10, tier=0),                 # q = 10: second layer, ring, period 64
+    dict(N=64, n=32, s=12, P=4, Q=10, tier=1, b=3, mode=1),   # q = 10, n = 32: workspace Dirichlet
 ]
 
 CHILD = r"""

@@ -194,3 +194,25 @@ def test_q10_against_l27_on_the_smooth_charge_256(torch_cuda):
     e6s, e10s = err(6, 24, 3), err(10, 28, 4)
     print(f"alpha = 1.75: L27 {e6s:.3e}, q = 10 {e10s:.3e}")
     assert e10s > 3 * e6s
+
+
+def test_q10_server_request(torch_cuda):
+    """The continuous-batching server with a q = 10 request beside a 27-point
+    one: each result equals its standalone solve bit for bit."""
+    from paper_1702_08111_gb300 import mlc
+    torch = torch_cuda
+    cases = [dict(N=32, n=8, s=16, P=4, Q=10, tier=FP64), dict(N=32, n=8, s=12, P=4, Q=6, tier=FP64),
+             dict(N=64, n=16, s=24, P=4, Q=10, tier=SPLIT)]
+    srv = mlc.Server(8 << 30, max_batch=4)
+    out = []
+    for k, kw in enumerate(cases):
+        N, tier = kw["N"], kw["tier"]
+        f64 = I.sample_bumps(N, I.draw_bumps(3, 2100 + k))
+        f = torch.from_numpy(f64.astype(np.float32) if tier == SPLIT else f64).cuda()
+        ref = mlc.Plan(**kw).solve(f).clone()
+        phi = torch.empty((N,) * 3, dtype=torch.float64, device="cuda")
+        out.append((srv.enqueue(f, phi, **kw), phi, ref))
+    for t, phi, ref in out:
+        srv.wait(t, 60000)
+        assert torch.equal(phi, ref)
+    srv.close()
