@@ -65,6 +65,16 @@ R16 Multilevel MLC (Sec. 5), levels > 2: with every level covering the whole
     mcapplicationfullmultipole) adds C2 h_l^2 times the level's own charge
     term chi-tilde f, zero on the coarse levels, so only the finest level is
     corrected.
+R18 The q = 10 operator of Sec. 8 (Q = 10): the six-orbit, 57-point solution
+    of the q = 10 conditions of eq. mehrstellenTau (STENCIL_ORBITS, derived in
+    derive_q10.py), C2 = 2/35.  Its DGF takes the free-space kernel as the
+    residual-correction reference field on the whole box (_dgf_full_wide).
+    The final Dirichlet step has a second boundary layer, one node outside
+    the closed faces.  Its boundary values come from eqs. philocmlcII and
+    mlcfulldiscr with the R4 interpolation factor on all three axes
+    (outer_nodes, stencils3_for), and the step is a sparse LU solve with two
+    layers (dirichlet_solve_wide).  phi^H is kept one coarse node further out.
+    Defaults b = 4, beta = 3.25 (measured, see the design notes).
 """
 from __future__ import annotations
 
