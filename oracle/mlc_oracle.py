@@ -19,8 +19,7 @@ step, in the paper's notation, with the plainest computation for each step:
   (mlcfulldiscr): phi^{loc,g} is accumulated at g and at every point of its
   interpolation stencil, then phi^B = phi^loc + I^H(phi^H - phi^loc).
 
-Readings of points where the paper is silent or garbled (each is also listed
-in the design notes of the repository):
+Readings of points where the paper is silent or garbled:
 
 R1  Grid: unit cube, h = 1/N, nodes [0, N]^3; patches are the closed cubes
     n i + [0, n]^3, i in [0, N/n)^3 (Sec. 4).  The charge is given on
@@ -74,7 +73,9 @@ R18 The q = 10 operator of Sec. 8 (Q = 10): the six-orbit, 57-point solution
     mlcfulldiscr with the R4 interpolation factor on all three axes
     (outer_nodes, stencils3_for), and the step is a sparse LU solve with two
     layers (dirichlet_solve_wide).  phi^H is kept one coarse node further out.
-    Defaults b = 4, beta = 3.25 (measured, see the design notes).
+    Defaults b = 4, beta = 3.25: on the Sec. 7.1 charge at 256^3, n = 32, the
+    q = 10 solve beats L27 only from g_alpha = 16 on, and b = 5 (q_I = q + 2)
+    leaves no room for that inside a period-128 field box.
 """
 from __future__ import annotations
 
