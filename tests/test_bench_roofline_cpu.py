@@ -94,3 +94,36 @@ def test_slab_rows_and_fp32_peak():
     assert b.slab_rows(W, 4) == 31   # Q = 6, g_alpha = 4
     assert abs(b.FP32_LANE_INST_PER_S - 152 * 128 * 2.07e9) < 1.0
     assert abs(b.FP64_INST_PER_S - 0.625e12) < 1.0
+
+
+def test_dirichlet_wide_counts_closed_form():
+    """The q = 10 Dirichlet counts (bench.py dirichlet_wide_counts) against
+    closed forms: a stencil offset s leaves the interior [1, n-1]^3 from
+    m^3 - prod_d (m - |s_d|) nodes (m = n - 1), so that many boundary terms;
+    an offset with one component of size 2 reaches the outer layer from the
+    nodes next to the face, and its mirror image is interior from
+    prod_{e != d} (m - |s_e|) of them (the fixed-point corrections)."""
+    import itertools
+    b = _bench()
+    orbits = {(0, 0, 0), (1, 0, 0), (1, 1, 0), (1, 1, 1), (2, 0, 0), (2, 1, 0)}
+    offs = [s for s in itertools.product(range(-2, 3), repeat=3)
+            if tuple(sorted(map(abs, s), reverse=True)) in orbits]
+    assert len(offs) == 57
+    for n in (8, 16, 32):
+        m = n - 1
+        tb = sum(m ** 3 - np.prod([m - abs(c) for c in s]) for s in offs)
+        tc = 0
+        for s in offs:
+            two = [d for d in range(3) if abs(s[d]) == 2]
+            if len(two) == 1:
+                tc += np.prod([m - abs(s[e]) for e in range(3) if e != two[0]])
+        it = b.WIDE_DIRICHLET_ITERS
+        if n == 16:
+            lf = li = 97
+        elif n == 32:
+            li, lf = 30 + 97 + 8 * 19, 30 + 97 + 8 * 34
+        else:
+            lf, li = 2 * m * m, m * m
+        flops = 2 * tb + (1 + it) * (6 * m * m * lf + m ** 3) + it * 2 * tc + 2 * n ** 3
+        inst = 2 * tb + (1 + it) * (6 * m * m * li + m ** 3) + it * 2 * tc + n ** 3
+        assert b.dirichlet_wide_counts(n) == (flops, inst), n
