@@ -214,8 +214,10 @@ __global__ void __launch_bounds__(128) k_boundary_outer(BndOutArgs a) {
 // E u(g) = sum over the offsets that leave the layer next to a face through
 // it of a_s u(mirror(g + s)) (L reads zero there, L_odd minus the mirrored
 // value).  u_0 = L_odd^-1 b, u_{k+1} = L_odd^-1 (b - E u_k).  One CTA per
-// patch; b, u, the work array and the DST-I matrix in shared memory; each
-// DST pass gives a line of m = n-1 values to one thread (dense m x m sums).
+// patch; b, u and the work array in shared memory up to n = 16, in the
+// plan's workspace above; each DST pass gives a line of m = n-1 values to one
+// thread (n = 16: the split-radix 15-point DST; n = 32: the split 31-point
+// DST; other n: dense m x m sums with the matrix in shared memory).
 struct DirWArgs {
     Items it;
     const double *sinm;  // (n-1) x n/2 half DST-I matrix sin(pi k t / n), t in [1, n/2]
